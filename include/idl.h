@@ -1,0 +1,216 @@
+/*
+ * idl.h -- C ABI of libidl, a GB300 (sm_103a) implementation of the
+ * CountSketch randomized interpolative decomposition (ID) of Malik & Becker,
+ * "Fast randomized matrix and tensor interpolative decomposition using
+ * CountSketch" (Adv. Comput. Math. 2020; arXiv 1901.10559).
+ *
+ * Conventions (all entry points):
+ *   - Every call is asynchronous on the context's stream unless it says
+ *     otherwise.  Returns IDL_OK or an IDL_E* code; no exception crosses the
+ *     ABI.  idl_last_error() gives a one-line message for the last failure.
+ *   - Indices are 0-based (the paper is 1-based).
+ *   - "device pointer" arguments must point to memory of the context's device.
+ *     The three pipeline calls (id_matrix, id_matrix_csr, id_cp_tensor) also
+ *     accept host pointers (pinned or pageable) for their array arguments: the
+ *     data are copied to the device inside the call, and host outputs are
+ *     written back before the call returns (the call then synchronises).
+ *   - Inputs are never modified.  Outputs are caller-allocated.
+ *   - Dense matrices are row-major with a leading dimension (elements).
+ *   - A sketch Y2 handed to or produced by the QR stage is column-major:
+ *     element (j, r) at Y2[r * ldy2 + j], ldy2 >= m2.
+ *   - No call falls back to the CPU: without a usable sm_103a device every
+ *     call returns IDL_ECUDA.
+ */
+#ifndef IDL_H
+#define IDL_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---- */
+#define IDL_OK        0
+#define IDL_EINVAL    1  /* invalid argument (checked on the host before any launch) */
+#define IDL_ENOMEM    2  /* device workspace allocation failed */
+#define IDL_ECUDA     3  /* CUDA runtime error (message in idl_last_error) */
+#define IDL_ERANK     4  /* |r_KK| <= 64 eps |r_11|: sketch numerically rank deficient; J written, T undefined */
+#define IDL_ETIMEOUT  5  /* a bounded device wait expired */
+#define IDL_EDATA     6  /* malformed input found on the device (CSR index out of range); bad entries skipped */
+#define IDL_ELIMIT    7  /* problem exceeds an on-chip capacity of this build (see the entry point) */
+
+/* ---- element types ---- */
+#define IDL_F32 0
+#define IDL_F64 1
+
+/* ---- arithmetic of the Gaussian stage ---- */
+#define IDL_PREC_FP64   0  /* FP64 operands, FP64 accumulation (CUDA cores)                        */
+#define IDL_PREC_FP32   1  /* FP32-accurate: 3-way bf16 split of both operands, 6 tcgen05 products */
+#define IDL_PREC_BF16X3 2  /* 2-way bf16 split, 3 tcgen05 products (hi*hi + hi*lo + lo*hi)         */
+#define IDL_PREC_BF16   3  /* bf16 operands, FP32 accumulation, 1 tcgen05 product                   */
+
+typedef struct idl_ctx idl_ctx;
+
+/* Parameters of one ID.  Zero-initialise and set what you need. */
+typedef struct idl_params {
+  int64_t  m1;        /* CountSketch rows (the sketch size L of Algorithm 2), or the TensorSketch length L of Algorithm 3 */
+  int64_t  m2;        /* Gaussian-stage rows; 0 = no Gaussian stage (the paper's Algorithm 2/3 verbatim) */
+  int32_t  modified;  /* 1 = modified CountSketch of Remark 2 (every bucket non-empty; needs m1 < I) */
+  int32_t  precision; /* IDL_PREC_*; with IDL_F64 data only IDL_PREC_FP64 is accepted */
+  uint64_t seed;      /* seed of the counter-based draws (h, s, the permutation, Omega) */
+  int32_t  residual;  /* 0: none; 1: ||R22||_F / ||Y2||_F in FP64 (default); 2: explicit FP64 ||Y2_rest - Y2_J T||_F / ||Y2||_F */
+  int32_t  reserved0;
+  int64_t  reserved[4];
+} idl_params;
+
+/* Diagnostics of one ID (filled when a non-NULL pointer is passed; the call then synchronises). */
+typedef struct idl_info {
+  double   residual;   /* relative sketch residual selected by idl_params.residual (NaN if 0) */
+  double   rkk_ratio;  /* |r_KK| / |r_11| of the pivoted QR */
+  double   y2_norm;    /* ||Y2||_F */
+  int32_t  status;     /* device status word (IDL_OK, IDL_ERANK, IDL_EDATA, IDL_ETIMEOUT) */
+  int32_t  precision;  /* precision actually used */
+  int32_t  cluster;    /* CTAs in the QR stage's thread-block cluster */
+  int32_t  reserved;
+} idl_info;
+
+/* ---------------------------------------------------------------------------
+ * Context.  Owns the device workspace (grown on demand, reused across calls),
+ * the status word and the stream.  One context per host thread at a time.
+ *   idl_create: device = CUDA ordinal.  Fails with IDL_ECUDA if the device is
+ *               not compute capability 10.3 (the library is built for sm_103a only).
+ *   idl_set_stream: stream is a cudaStream_t (NULL = legacy default stream).
+ *   idl_sync: waits for the stream and returns the device status word (then clears it).
+ * ------------------------------------------------------------------------- */
+int idl_create(idl_ctx** ctx, int device);
+int idl_destroy(idl_ctx* ctx);
+int idl_set_stream(idl_ctx* ctx, void* stream);
+int idl_sync(idl_ctx* ctx);
+const char* idl_last_error(idl_ctx* ctx);
+int idl_version(void);
+
+/* ---------------------------------------------------------------------------
+ * Draws (Sec. 1.3; Remark 2 and Sec. 7.2; Sec. 1.2.1).  Counter-based:
+ *   u(seed, tag, i) = mix64(mix64(seed ^ tag*0xD1B54A32D192ED03) + (i+1)*0x9E3779B97F4A7C15)
+ *   (mix64 = the SplitMix64 finaliser).  bounded(u, L) = (u*L) >> 64.
+ *   tags: 1 buckets, 2 signs, 3 permutation round keys, 4 Gaussian, 16+n / 32+n per tensor mode.
+ * idl_draw_countsketch: h[i] in [0, L) (int32), s[i] in {-1, +1} (int8) for i < I.
+ *   modified = 1 uses h~(i) = pi(i) if pi(i) < L else bounded(u(seed,1,i), L), pi a
+ *   4-round Feistel permutation of [I] with cycle walking; needs L < I.
+ * idl_draw_gaussian: Omega (m2 x m1, row-major FP64), Box-Muller on pairs of the flat index.
+ * idl_draw_mode: TensorSketch maps of mode n (plain iid maps, Sec. 1.3).
+ * All outputs are device pointers.
+ * ------------------------------------------------------------------------- */
+int idl_draw_countsketch(idl_ctx* ctx, uint64_t seed, int64_t I, int64_t L, int modified,
+                         int32_t* h, int8_t* s);
+int idl_draw_gaussian(idl_ctx* ctx, uint64_t seed, int64_t m2, int64_t m1, double* Omega);
+int idl_draw_mode(idl_ctx* ctx, uint64_t seed, int n, int64_t In, int64_t L, int32_t* h, int8_t* s);
+
+/* ---------------------------------------------------------------------------
+ * Bucket offsets of Phi (Sec. 1.3): rows grouped by bucket, ascending within a
+ * bucket.  bucket_ptr (L+1 int32) and row_list (I int32) are device outputs.
+ * Buckets holding more than 12288 rows are left in arrival order (status IDL_OK;
+ * the sketch is still exact, only its summation order is then not fixed).
+ * ------------------------------------------------------------------------- */
+int idl_bucket_offsets(idl_ctx* ctx, const int32_t* h, int64_t I, int64_t L,
+                       int32_t* bucket_ptr, int32_t* row_list);
+
+/* ---------------------------------------------------------------------------
+ * CountSketch Y1 = S A (Sec. 1.3; Algorithm 2 line 4), as a segmented
+ * reduction over the bucket offsets: Y1[b, :] = sum over rows i of bucket b of
+ * s[i] * A[i, :].  A: I x R row-major (lda >= R), dtype IDL_F32 or IDL_F64;
+ * Y1: L x R row-major (ldy >= R), same dtype.  All device pointers.
+ * ------------------------------------------------------------------------- */
+int idl_countsketch_dense(idl_ctx* ctx, const void* A, int64_t I, int64_t R, int64_t lda, int dtype,
+                          const int32_t* h, const int8_t* s, const int32_t* bucket_ptr,
+                          const int32_t* row_list, int64_t L, void* Y1, int64_t ldy);
+
+/* Same for CSR A: rowptr (I+1, int64), colidx (nnz, int32), vals (nnz, dtype).
+ * Duplicate (i, c) entries add; columns need not be sorted.  Entries with a
+ * column outside [0, R) or rows with a decreasing rowptr are skipped and set
+ * the status word to IDL_EDATA. */
+int idl_countsketch_csr(idl_ctx* ctx, const int64_t* rowptr, const int32_t* colidx, const void* vals,
+                        int64_t I, int64_t R, int64_t nnz, int dtype,
+                        const int32_t* h, const int8_t* s, const int32_t* bucket_ptr,
+                        const int32_t* row_list, int64_t L, void* Y1, int64_t ldy);
+
+/* ---------------------------------------------------------------------------
+ * TensorSketch of M = (Khatri-Rao of A^(1..N)) diag(lambda) (Sec. 1.3,
+ * Eq. TA-formula; Algorithm 3 line 5): Y[:, r] = lambda_r * real(IFFT(prod_n
+ * FFT(S^(n) a^(n)_r))).  factors[n]: device pointer to A^(n) stored column by
+ * column (column r at factors[n] + r*ldf[n], ldf[n] >= dims[n]), IDL_F32.
+ * lambda: R doubles (device).  hs[n], ss[n]: device maps of mode n (length
+ * dims[n]).  Y: L x R row-major FP32 (ldy >= R).  L must be a power of two in
+ * [16, 16384]; N <= 8.  The host arrays dims, factors, ldf, hs, ss are read
+ * during the call only.
+ * ------------------------------------------------------------------------- */
+int idl_tensorsketch(idl_ctx* ctx, int N, const int64_t* dims, int64_t R,
+                     const void* const* factors, const int64_t* ldf, const double* lambda,
+                     const int32_t* const* hs, const int8_t* const* ss, int64_t L,
+                     float* Y, int64_t ldy);
+
+/* ---------------------------------------------------------------------------
+ * Gaussian stage Y2 = Omega Y1 (Sec. 1.2.1): Omega m2 x m1 row-major FP64
+ * (device), Y1 m1 x R row-major (ldy1 >= R) of dtype, Y2 column-major
+ * (R columns of ldy2 >= m2 entries) of dtype.  precision = IDL_PREC_*
+ * (IDL_F64 requires IDL_PREC_FP64).  m2 <= 256.
+ * ------------------------------------------------------------------------- */
+int idl_gaussian_stage(idl_ctx* ctx, const double* Omega, int64_t m2, int64_t m1,
+                       const void* Y1, int64_t R, int64_t ldy1, int dtype, int precision,
+                       void* Y2, int64_t ldy2);
+
+/* ---------------------------------------------------------------------------
+ * Rank-K column-pivoted Householder QR of Y2 (Algorithm 1 line 3; Golub & Van
+ * Loan Alg. 5.4.1): K steps, each taking the column of largest remaining norm
+ * (ties: smallest index).  Y2 (m x R column-major, ldy2 >= m, dtype) is
+ * overwritten: rows 0..K-1 of every column hold the triangular factor R
+ * (R11 on the pivot columns, R12 on the rest), rows K.. the trailing block.
+ * J: K int32 (device), pivot order.  rnorm: K doubles (device) |r_tt|, or NULL.
+ * Runs in one thread-block cluster with the matrix in distributed shared
+ * memory: needs m <= 256 and m*R*sizeof(dtype) within the cluster's shared
+ * memory (IDL_ELIMIT otherwise).
+ * ------------------------------------------------------------------------- */
+int idl_cpqr(idl_ctx* ctx, void* Y2, int64_t m, int64_t R, int64_t ldy2, int dtype, int64_t K,
+             int32_t* J, double* rnorm);
+
+/* ---------------------------------------------------------------------------
+ * T = R11^{-1} R12 in FP64 by back substitution (Algorithm 1 lines 5-6), from
+ * the factored Y2 of idl_cpqr and its J.  T: K x (R-K) row-major FP64 (device);
+ * column c of T belongs to the c-th non-skeleton column in ascending index.
+ * rest (optional, R-K int32, device) receives those column indices.  K <= 128.
+ * ------------------------------------------------------------------------- */
+int idl_t_solve(idl_ctx* ctx, const void* Y2, int64_t m, int64_t R, int64_t ldy2, int dtype,
+                int64_t K, const int32_t* J, double* T, int32_t* rest);
+
+/* lambda_hat_k = lambda_{J[k]} * (1 + sum_c T[k, c])  (Algorithm 3 line 7), FP64, device. */
+int idl_lambda_hat(idl_ctx* ctx, const double* lambda, const int32_t* J, const double* T,
+                   int64_t K, int64_t R, double* lambda_hat);
+
+/* ---------------------------------------------------------------------------
+ * Pipelines.  J: K int32, T: K x (R-K) FP64 row-major (see idl_t_solve),
+ * lambda_hat: K FP64.  info may be NULL (then the call does not synchronise
+ * unless host pointers are involved).
+ *
+ * id_matrix (Algorithm 2 with a Gaussian stage): dense A (I x R row-major,
+ *   lda >= R), dtype IDL_F32 / IDL_F64.  Needs 1 <= K < R, K <= m1, K <= m2 when
+ *   m2 > 0, m2 <= m1, m1 < I when modified.
+ * id_matrix_csr: CSR A as in idl_countsketch_csr.
+ * id_cp_tensor (Algorithm 3 with a Gaussian stage): CP tensor with N factor
+ *   matrices (see idl_tensorsketch; host pointers not accepted for factors),
+ *   s-values lambda, params.m1 = the TensorSketch length L (power of two).
+ * ------------------------------------------------------------------------- */
+int id_matrix(idl_ctx* ctx, const void* A, int64_t I, int64_t R, int64_t lda, int dtype, int64_t K,
+              const idl_params* p, int32_t* J, double* T, idl_info* info);
+int id_matrix_csr(idl_ctx* ctx, const int64_t* rowptr, const int32_t* colidx, const void* vals,
+                  int64_t I, int64_t R, int64_t nnz, int dtype, int64_t K, const idl_params* p,
+                  int32_t* J, double* T, idl_info* info);
+int id_cp_tensor(idl_ctx* ctx, int N, const int64_t* dims, int64_t R, const void* const* factors,
+                 const int64_t* ldf, const double* lambda, int64_t K, const idl_params* p,
+                 int32_t* J, double* T, double* lambda_hat, idl_info* info);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* IDL_H */

@@ -1,0 +1,251 @@
+"""GB300 (sm_103a) CountSketch interpolative decomposition -- Python binding.
+
+A thin ctypes layer over ``libidl.so`` (C ABI declared in ``include/idl.h``):
+the functions below have the C entry points' names and only marshal
+arguments (torch CUDA tensors or numpy host arrays -> pointers).  Every step of
+the method runs in the library's CUDA kernels; there is no CPU path here and
+the import fails loudly when the library is missing.
+
+Method: Malik & Becker, "Fast randomized matrix and tensor interpolative
+decomposition using CountSketch" -- Algorithm 2 (CountSketch matrix ID) and
+Algorithm 3 (TensorSketch tensor ID), each followed here by a Gaussian stage
+(Sec. 1.2.1) before Algorithm 1's column-pivoted QR.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libidl.so")
+HEADER = os.path.join(os.path.dirname(_HERE), "include", "idl.h")
+
+IDL_OK, IDL_EINVAL, IDL_ENOMEM, IDL_ECUDA, IDL_ERANK, IDL_ETIMEOUT, IDL_EDATA, IDL_ELIMIT = range(8)
+IDL_F32, IDL_F64 = 0, 1
+PREC_FP64, PREC_FP32, PREC_BF16X3, PREC_BF16 = 0, 1, 2, 3
+STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ERANK", 5: "ETIMEOUT", 6: "EDATA", 7: "ELIMIT"}
+
+
+class IdlError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"idl error {STATUS_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("m1", ctypes.c_int64), ("m2", ctypes.c_int64), ("modified", ctypes.c_int32),
+                ("precision", ctypes.c_int32), ("seed", ctypes.c_uint64), ("residual", ctypes.c_int32),
+                ("reserved0", ctypes.c_int32), ("reserved", ctypes.c_int64 * 4)]
+
+
+class Info(ctypes.Structure):
+    _fields_ = [("residual", ctypes.c_double), ("rkk_ratio", ctypes.c_double), ("y2_norm", ctypes.c_double),
+                ("status", ctypes.c_int32), ("precision", ctypes.c_int32), ("cluster", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
+
+
+_lib = None
+_vp, _i64, _i32, _u64, _int = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_uint64, ctypes.c_int
+
+_SIGS = {
+    "idl_version": ([], _int),
+    "idl_create": ([ctypes.POINTER(_vp), _int], _int),
+    "idl_destroy": ([_vp], _int),
+    "idl_set_stream": ([_vp, _vp], _int),
+    "idl_sync": ([_vp], _int),
+    "idl_last_error": ([_vp], ctypes.c_char_p),
+    "idl_debug_fail_alloc": ([_vp, _int], _int),
+    "idl_debug_release_workspace": ([_vp], _int),
+    "idl_draw_countsketch": ([_vp, _u64, _i64, _i64, _int, _vp, _vp], _int),
+    "idl_draw_gaussian": ([_vp, _u64, _i64, _i64, _vp], _int),
+    "idl_draw_mode": ([_vp, _u64, _int, _i64, _i64, _vp, _vp], _int),
+    "idl_bucket_offsets": ([_vp, _vp, _i64, _i64, _vp, _vp], _int),
+    "idl_countsketch_dense": ([_vp, _vp, _i64, _i64, _i64, _int, _vp, _vp, _vp, _vp, _i64, _vp, _i64], _int),
+    "idl_countsketch_csr": ([_vp, _vp, _vp, _vp, _i64, _i64, _i64, _int, _vp, _vp, _vp, _vp, _i64, _vp, _i64], _int),
+    "idl_tensorsketch": ([_vp, _int, _vp, _i64, _vp, _vp, _vp, _vp, _vp, _i64, _vp, _i64], _int),
+    "idl_gaussian_stage": ([_vp, _vp, _i64, _i64, _vp, _i64, _i64, _int, _int, _vp, _i64], _int),
+    "idl_cpqr": ([_vp, _vp, _i64, _i64, _i64, _int, _i64, _vp, _vp], _int),
+    "idl_t_solve": ([_vp, _vp, _i64, _i64, _i64, _int, _i64, _vp, _vp, _vp], _int),
+    "idl_lambda_hat": ([_vp, _vp, _vp, _vp, _i64, _i64, _vp], _int),
+    "id_matrix": ([_vp, _vp, _i64, _i64, _i64, _int, _i64, ctypes.POINTER(Params), _vp, _vp,
+                   ctypes.POINTER(Info)], _int),
+    "id_matrix_csr": ([_vp, _vp, _vp, _vp, _i64, _i64, _i64, _int, _i64, ctypes.POINTER(Params), _vp, _vp,
+                       ctypes.POINTER(Info)], _int),
+    "id_cp_tensor": ([_vp, _int, _vp, _i64, _vp, _vp, _vp, _i64, ctypes.POINTER(Params), _vp, _vp, _vp,
+                      ctypes.POINTER(Info)], _int),
+}
+
+
+def header_symbols():
+    """Function names declared in include/idl.h."""
+    txt = open(HEADER).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:const\s+)?\w+\*?\s+\**(\w+)\s*\(", txt, flags=re.M)))
+
+
+def lib():
+    """The loaded libidl.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} is missing: build it with paper_1901_10559_gb300.build.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (args, res) in _SIGS.items():
+            if hasattr(L, name):
+                f = getattr(L, name)
+                f.argtypes = args
+                f.restype = res
+        _lib = L
+    return _lib
+
+
+def _p(x):
+    """Pointer of a torch tensor, numpy array, integer address or None."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return _vp(x)
+    if hasattr(x, "data_ptr"):
+        return _vp(x.data_ptr())
+    if hasattr(x, "ctypes"):
+        return _vp(x.ctypes.data)
+    raise TypeError(f"cannot take a pointer of {type(x)}")
+
+
+class Context:
+    """An idl_ctx on one CUDA device (workspace, status word, stream)."""
+
+    def __init__(self, device: int = 0):
+        self.ptr = _vp()
+        rc = lib().idl_create(ctypes.byref(self.ptr), device)
+        if rc != IDL_OK:
+            raise IdlError(rc, "idl_create failed (needs a compute capability 10.3 GPU)")
+        self.device = device
+
+    def check(self, rc):
+        if rc != IDL_OK:
+            raise IdlError(rc, lib().idl_last_error(self.ptr).decode())
+        return rc
+
+    def set_stream(self, stream):
+        """stream: a torch.cuda.Stream, a raw cudaStream_t integer, or None."""
+        h = 0 if stream is None else (stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+        self.check(lib().idl_set_stream(self.ptr, _vp(h)))
+
+    def sync(self):
+        return lib().idl_sync(self.ptr)
+
+    def close(self):
+        if self.ptr:
+            lib().idl_destroy(self.ptr)
+            self.ptr = _vp()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def make_params(m1, m2, seed, modified=True, precision=PREC_FP32, residual=1):
+    p = Params()
+    p.m1, p.m2, p.modified, p.precision, p.seed, p.residual = int(m1), int(m2), int(modified), int(precision), \
+        int(seed), int(residual)
+    return p
+
+
+# ---------------------------------------------------------------- stage calls
+def idl_draw_countsketch(ctx, seed, I, L, modified, h, s):
+    return ctx.check(lib().idl_draw_countsketch(ctx.ptr, seed, I, L, int(modified), _p(h), _p(s)))
+
+
+def idl_draw_gaussian(ctx, seed, m2, m1, Omega):
+    return ctx.check(lib().idl_draw_gaussian(ctx.ptr, seed, m2, m1, _p(Omega)))
+
+
+def idl_draw_mode(ctx, seed, n, In, L, h, s):
+    return ctx.check(lib().idl_draw_mode(ctx.ptr, seed, n, In, L, _p(h), _p(s)))
+
+
+def idl_bucket_offsets(ctx, h, I, L, bucket_ptr, row_list):
+    return ctx.check(lib().idl_bucket_offsets(ctx.ptr, _p(h), I, L, _p(bucket_ptr), _p(row_list)))
+
+
+def idl_countsketch_dense(ctx, A, I, R, lda, dtype, h, s, bucket_ptr, row_list, L, Y1, ldy):
+    return ctx.check(lib().idl_countsketch_dense(ctx.ptr, _p(A), I, R, lda, dtype, _p(h), _p(s), _p(bucket_ptr),
+                                                 _p(row_list), L, _p(Y1), ldy))
+
+
+def idl_countsketch_csr(ctx, rowptr, colidx, vals, I, R, nnz, dtype, h, s, bucket_ptr, row_list, L, Y1, ldy):
+    return ctx.check(lib().idl_countsketch_csr(ctx.ptr, _p(rowptr), _p(colidx), _p(vals), I, R, nnz, dtype, _p(h),
+                                               _p(s), _p(bucket_ptr), _p(row_list), L, _p(Y1), ldy))
+
+
+def _arr(ctype, vals):
+    return (ctype * len(vals))(*vals)
+
+
+def idl_tensorsketch(ctx, factors, ldf, lam, hs, ss, L, Y, ldy):
+    N = len(factors)
+    dims = _arr(ctypes.c_int64, [int(f.shape[1]) for f in factors])   # factors given as (R, I_n) tensors
+    R = int(factors[0].shape[0])
+    fp = _arr(_vp, [f.data_ptr() for f in factors])
+    lp = _arr(ctypes.c_int64, [int(x) for x in ldf])
+    hp = _arr(_vp, [h.data_ptr() for h in hs])
+    sp = _arr(_vp, [s.data_ptr() for s in ss])
+    return ctx.check(lib().idl_tensorsketch(ctx.ptr, N, ctypes.cast(dims, _vp), R, ctypes.cast(fp, _vp),
+                                            ctypes.cast(lp, _vp), _p(lam), ctypes.cast(hp, _vp),
+                                            ctypes.cast(sp, _vp), L, _p(Y), ldy))
+
+
+def idl_gaussian_stage(ctx, Omega, m2, m1, Y1, R, ldy1, dtype, precision, Y2, ldy2):
+    return ctx.check(lib().idl_gaussian_stage(ctx.ptr, _p(Omega), m2, m1, _p(Y1), R, ldy1, dtype, precision,
+                                              _p(Y2), ldy2))
+
+
+def idl_cpqr(ctx, Y2, m, R, ldy2, dtype, K, J, rnorm=None):
+    return ctx.check(lib().idl_cpqr(ctx.ptr, _p(Y2), m, R, ldy2, dtype, K, _p(J), _p(rnorm)))
+
+
+def idl_t_solve(ctx, Y2, m, R, ldy2, dtype, K, J, T, rest=None):
+    return ctx.check(lib().idl_t_solve(ctx.ptr, _p(Y2), m, R, ldy2, dtype, K, _p(J), _p(T), _p(rest)))
+
+
+def idl_lambda_hat(ctx, lam, J, T, K, R, lam_hat):
+    return ctx.check(lib().idl_lambda_hat(ctx.ptr, _p(lam), _p(J), _p(T), K, R, _p(lam_hat)))
+
+
+# ---------------------------------------------------------------- pipelines
+def id_matrix(ctx, A, K, params, J, T, info=None, lda=None):
+    """A: (I, R) torch tensor (CUDA or pinned/pageable CPU) or numpy array, float32/float64."""
+    I, R = int(A.shape[0]), int(A.shape[1])
+    dt = IDL_F64 if str(A.dtype).endswith("float64") else IDL_F32
+    lda = R if lda is None else lda
+    return ctx.check(lib().id_matrix(ctx.ptr, _p(A), I, R, lda, dt, K, ctypes.byref(params), _p(J), _p(T),
+                                     ctypes.byref(info) if info is not None else None))
+
+
+def id_matrix_csr(ctx, rowptr, colidx, vals, shape, K, params, J, T, info=None):
+    I, R = int(shape[0]), int(shape[1])
+    nnz = int(vals.shape[0])
+    dt = IDL_F64 if str(vals.dtype).endswith("float64") else IDL_F32
+    return ctx.check(lib().id_matrix_csr(ctx.ptr, _p(rowptr), _p(colidx), _p(vals), I, R, nnz, dt, K,
+                                         ctypes.byref(params), _p(J), _p(T),
+                                         ctypes.byref(info) if info is not None else None))
+
+
+def id_cp_tensor(ctx, factors, lam, K, params, J, T, lam_hat, info=None, ldf=None):
+    """factors: list of CUDA float32 tensors of shape (R, I_n) (A^(n) stored column by column)."""
+    N = len(factors)
+    R = int(factors[0].shape[0])
+    dims = _arr(ctypes.c_int64, [int(f.shape[1]) for f in factors])
+    ldf = [int(f.stride(0)) for f in factors] if ldf is None else ldf
+    fp = _arr(_vp, [f.data_ptr() for f in factors])
+    lp = _arr(ctypes.c_int64, ldf)
+    return ctx.check(lib().id_cp_tensor(ctx.ptr, N, ctypes.cast(dims, _vp), R, ctypes.cast(fp, _vp),
+                                        ctypes.cast(lp, _vp), _p(lam), K, ctypes.byref(params), _p(J), _p(T),
+                                        _p(lam_hat), ctypes.byref(info) if info is not None else None))

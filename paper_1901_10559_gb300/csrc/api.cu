@@ -1,0 +1,489 @@
+// api.cu -- the C ABI of libidl: context, workspace, argument checks, the stage
+// entry points and the three pipelines (Algorithm 2 and 3 with a Gaussian
+// stage).  Host code only; every arithmetic step runs in the kernels of the
+// other translation units.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <limits>
+#include <string>
+
+#include "common.cuh"
+#include "internal.h"
+
+using namespace idl;
+
+namespace idl {
+
+int fail(idl_ctx* ctx, int code, const std::string& msg) {
+  if (ctx) ctx->err = msg;
+  return code;
+}
+
+int cuda_check(idl_ctx* ctx, cudaError_t e, const char* where) {
+  if (e == cudaSuccess) return IDL_OK;
+  if (ctx) ctx->err = std::string(where) + ": " + cudaGetErrorString(e);
+  return e == cudaErrorMemoryAllocation ? IDL_ENOMEM : IDL_ECUDA;
+}
+
+void* ws_get(idl_ctx* ctx, int slot, size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  if ((int)ctx->slots.size() <= slot) ctx->slots.resize(slot + 1);
+  idl_ctx::Buf& b = ctx->slots[slot];
+  if (b.bytes >= bytes) return b.p;
+  ++ctx->alloc_count;
+  if (ctx->fail_alloc_at && ctx->alloc_count == ctx->fail_alloc_at) {
+    ctx->err = "workspace allocation failed (injected)";
+    return nullptr;
+  }
+  if (b.p) {
+    cudaStreamSynchronize(ctx->stream);   // the old buffer may still be in use
+    cudaFree(b.p);
+    b.p = nullptr;
+    b.bytes = 0;
+  }
+  size_t want = bytes + bytes / 8;        // grow with headroom
+  want = (want + 255) & ~(size_t)255;
+  if (cudaMalloc(&b.p, want) != cudaSuccess) {
+    (void)cudaGetLastError();
+    b.p = nullptr;
+    ctx->err = "workspace allocation of " + std::to_string(want) + " bytes failed";
+    return nullptr;
+  }
+  b.bytes = want;
+  return b.p;
+}
+
+}  // namespace idl
+
+// ---------------------------------------------------------------------------
+// helpers
+// ---------------------------------------------------------------------------
+#define TRY(x)                         \
+  do {                                 \
+    int _rc = (x);                     \
+    if (_rc != IDL_OK) return _rc;     \
+  } while (0)
+#define WS(ptr, type, slot, count)                                             \
+  type* ptr = (type*)ws_get(ctx, slot, sizeof(type) * (size_t)(count));       \
+  if (!ptr) return IDL_ENOMEM
+
+static bool is_device_ptr(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+static int dtype_size(int dtype) { return dtype == IDL_F64 ? 8 : 4; }
+
+static int check_ctx(idl_ctx* ctx) {
+  if (!ctx) return IDL_EINVAL;
+  cudaError_t e = cudaSetDevice(ctx->device);
+  return cuda_check(ctx, e, "cudaSetDevice");
+}
+
+// Copies a host array into a workspace slot (or returns the device pointer as is).
+static const void* stage_in(idl_ctx* ctx, const void* p, size_t bytes, int slot, int* rc) {
+  *rc = IDL_OK;
+  if (is_device_ptr(p)) return p;
+  void* d = ws_get(ctx, slot, bytes);
+  if (!d) { *rc = IDL_ENOMEM; return nullptr; }
+  *rc = cuda_check(ctx, cudaMemcpyAsync(d, p, bytes, cudaMemcpyHostToDevice, ctx->stream), "copy in");
+  return d;
+}
+
+static int clear_diag(idl_ctx* ctx) {
+  return cuda_check(ctx, cudaMemsetAsync(ctx->d_diag, 0, sizeof(double) * 8, ctx->stream), "diag clear");
+}
+
+static int finish_info(idl_ctx* ctx, const idl_params* p, int precision, idl_info* info, int64_t K, int64_t R) {
+  (void)K; (void)R;
+  if (!info) return IDL_OK;
+  double d[8];
+  int st = 0;
+  cudaError_t e = cudaMemcpyAsync(d, ctx->d_diag, sizeof(d), cudaMemcpyDeviceToHost, ctx->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&st, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  TRY(cuda_check(ctx, e, "info readback"));
+  memset(info, 0, sizeof(*info));
+  info->y2_norm = std::sqrt(d[1]);
+  info->rkk_ratio = d[3] > 0 ? d[4] / d[3] : 0.0;
+  info->precision = precision;
+  info->cluster = ctx->last_cluster;
+  const int mode = p->residual;
+  if (mode == 1) info->residual = d[1] > 0 ? std::sqrt(d[0] / d[1]) : 0.0;
+  else if (mode == 2) info->residual = d[1] > 0 ? std::sqrt(d[2] / d[1]) : 0.0;
+  else info->residual = std::numeric_limits<double>::quiet_NaN();
+  const double eps = precision == IDL_PREC_FP64 ? 2.220446049250313e-16 : 1.1920928955078125e-07;
+  if (st == IDL_OK && !(d[4] > 64.0 * eps * d[3])) st = IDL_ERANK;
+  info->status = st;
+  int zero = 0;
+  cudaMemcpyAsync(ctx->d_status, &zero, sizeof(int), cudaMemcpyHostToDevice, ctx->stream);
+  cudaStreamSynchronize(ctx->stream);
+  return st;
+}
+
+// ---------------------------------------------------------------------------
+// context
+// ---------------------------------------------------------------------------
+extern "C" int idl_version(void) { return 100; }
+
+extern "C" int idl_create(idl_ctx** out, int device) {
+  if (!out) return IDL_EINVAL;
+  *out = nullptr;
+  int n = 0;
+  if (cudaGetDeviceCount(&n) != cudaSuccess || n <= device || device < 0) {
+    (void)cudaGetLastError();
+    return IDL_ECUDA;
+  }
+  cudaDeviceProp prop;
+  if (cudaGetDeviceProperties(&prop, device) != cudaSuccess) return IDL_ECUDA;
+  if (prop.major != 10 || prop.minor != 3) return IDL_ECUDA;   // built for sm_103a only
+  if (cudaSetDevice(device) != cudaSuccess) return IDL_ECUDA;
+  idl_ctx* c = new idl_ctx();
+  c->device = device;
+  c->num_sms = prop.multiProcessorCount;
+  c->smem_optin = (int)prop.sharedMemPerBlockOptin;
+  if (cudaMalloc(&c->d_status, sizeof(int) * 4) != cudaSuccess ||
+      cudaMalloc(&c->d_diag, sizeof(double) * 8) != cudaSuccess) {
+    delete c;
+    return IDL_ENOMEM;
+  }
+  cudaMemset(c->d_status, 0, sizeof(int) * 4);
+  cudaMemset(c->d_diag, 0, sizeof(double) * 8);
+  *out = c;
+  return IDL_OK;
+}
+
+extern "C" int idl_destroy(idl_ctx* ctx) {
+  if (!ctx) return IDL_OK;
+  cudaSetDevice(ctx->device);
+  cudaStreamSynchronize(ctx->stream);
+  for (auto& b : ctx->slots)
+    if (b.p) cudaFree(b.p);
+  cudaFree(ctx->d_status);
+  cudaFree(ctx->d_diag);
+  delete ctx;
+  return IDL_OK;
+}
+
+extern "C" int idl_set_stream(idl_ctx* ctx, void* stream) {
+  if (!ctx) return IDL_EINVAL;
+  ctx->stream = (cudaStream_t)stream;
+  return IDL_OK;
+}
+
+extern "C" int idl_sync(idl_ctx* ctx) {
+  TRY(check_ctx(ctx));
+  int st = 0;
+  cudaError_t e = cudaMemcpyAsync(&st, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  TRY(cuda_check(ctx, e, "idl_sync"));
+  if (st != IDL_OK) {
+    cudaMemsetAsync(ctx->d_status, 0, sizeof(int), ctx->stream);
+    cudaStreamSynchronize(ctx->stream);
+  }
+  return st;
+}
+
+extern "C" const char* idl_last_error(idl_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+// test hook (not in the public header): fail the n-th workspace allocation from now
+extern "C" int idl_debug_fail_alloc(idl_ctx* ctx, int nth) {
+  if (!ctx) return IDL_EINVAL;
+  ctx->fail_alloc_at = nth > 0 ? ctx->alloc_count + (size_t)nth : 0;
+  return IDL_OK;
+}
+extern "C" int idl_debug_release_workspace(idl_ctx* ctx) {
+  TRY(check_ctx(ctx));
+  cudaStreamSynchronize(ctx->stream);
+  for (auto& b : ctx->slots) {
+    if (b.p) cudaFree(b.p);
+    b.p = nullptr;
+    b.bytes = 0;
+  }
+  return IDL_OK;
+}
+
+// ---------------------------------------------------------------------------
+// stage entry points
+// ---------------------------------------------------------------------------
+extern "C" int idl_draw_countsketch(idl_ctx* ctx, uint64_t seed, int64_t I, int64_t L, int modified, int32_t* h,
+                                    int8_t* s) {
+  TRY(check_ctx(ctx));
+  if (I < 0 || L < 1 || L > 0x7fffffffLL || I > 0x7fffffffLL || (I > 0 && (!h || !s)))
+    return fail(ctx, IDL_EINVAL, "draw_countsketch: bad sizes or null output");
+  if (modified && !(L < I)) return fail(ctx, IDL_EINVAL, "draw_countsketch: modified map needs L < I");
+  return cuda_check(ctx, launch_draw_countsketch(ctx->stream, seed, I, L, modified, h, s, ctx->d_status),
+                    "draw_countsketch");
+}
+
+extern "C" int idl_draw_gaussian(idl_ctx* ctx, uint64_t seed, int64_t m2, int64_t m1, double* Omega) {
+  TRY(check_ctx(ctx));
+  if (m2 < 0 || m1 < 0 || (m2 * m1 > 0 && !Omega)) return fail(ctx, IDL_EINVAL, "draw_gaussian: bad arguments");
+  return cuda_check(ctx, launch_draw_gaussian(ctx->stream, seed, m2, m1, Omega), "draw_gaussian");
+}
+
+extern "C" int idl_draw_mode(idl_ctx* ctx, uint64_t seed, int n, int64_t In, int64_t L, int32_t* h, int8_t* s) {
+  TRY(check_ctx(ctx));
+  if (n < 0 || In < 0 || L < 1 || L > 0x7fffffffLL || (In > 0 && (!h || !s)))
+    return fail(ctx, IDL_EINVAL, "draw_mode: bad arguments");
+  return cuda_check(ctx, launch_draw_mode(ctx->stream, seed, n, In, L, h, s), "draw_mode");
+}
+
+extern "C" int idl_bucket_offsets(idl_ctx* ctx, const int32_t* h, int64_t I, int64_t L, int32_t* bucket_ptr,
+                                  int32_t* row_list) {
+  TRY(check_ctx(ctx));
+  if (I < 0 || I > 0x7fffffffLL || L < 1 || L > 0x7fffffffLL || !bucket_ptr || (I > 0 && (!h || !row_list)))
+    return fail(ctx, IDL_EINVAL, "bucket_offsets: bad arguments");
+  return launch_bucket_offsets(ctx, h, I, L, bucket_ptr, row_list);
+}
+
+extern "C" int idl_countsketch_dense(idl_ctx* ctx, const void* A, int64_t I, int64_t R, int64_t lda, int dtype,
+                                     const int32_t* h, const int8_t* s, const int32_t* bucket_ptr,
+                                     const int32_t* row_list, int64_t L, void* Y1, int64_t ldy) {
+  (void)h;
+  TRY(check_ctx(ctx));
+  if ((dtype != IDL_F32 && dtype != IDL_F64) || I < 0 || R < 1 || lda < R || ldy < R || L < 1 || !Y1 || !s ||
+      !bucket_ptr || (I > 0 && (!A || !row_list)))
+    return fail(ctx, IDL_EINVAL, "countsketch_dense: bad arguments");
+  return launch_countsketch_dense(ctx, A, I, R, lda, dtype, s, bucket_ptr, row_list, L, Y1, ldy);
+}
+
+extern "C" int idl_countsketch_csr(idl_ctx* ctx, const int64_t* rowptr, const int32_t* colidx, const void* vals,
+                                   int64_t I, int64_t R, int64_t nnz, int dtype, const int32_t* h, const int8_t* s,
+                                   const int32_t* bucket_ptr, const int32_t* row_list, int64_t L, void* Y1,
+                                   int64_t ldy) {
+  (void)h;
+  TRY(check_ctx(ctx));
+  if ((dtype != IDL_F32 && dtype != IDL_F64) || I < 0 || R < 1 || R > 0x7fffffffLL || nnz < 0 || ldy < R || L < 1 ||
+      !Y1 || !rowptr || !bucket_ptr || (nnz > 0 && (!colidx || !vals)) || (I > 0 && (!s || !row_list)))
+    return fail(ctx, IDL_EINVAL, "countsketch_csr: bad arguments");
+  return launch_countsketch_csr(ctx, rowptr, colidx, vals, I, R, nnz, dtype, s, bucket_ptr, row_list, L, Y1, ldy);
+}
+
+extern "C" int idl_tensorsketch(idl_ctx* ctx, int N, const int64_t* dims, int64_t R, const void* const* factors,
+                                const int64_t* ldf, const double* lambda, const int32_t* const* hs,
+                                const int8_t* const* ss, int64_t L, float* Y, int64_t ldy) {
+  TRY(check_ctx(ctx));
+  if (N < 1 || N > 8 || !dims || !factors || !ldf || !hs || !ss || !lambda || !Y || R < 1 || ldy < R)
+    return fail(ctx, IDL_EINVAL, "tensorsketch: bad arguments");
+  for (int n = 0; n < N; ++n)
+    if (dims[n] < 1 || ldf[n] < dims[n] || !factors[n] || !hs[n] || !ss[n])
+      return fail(ctx, IDL_EINVAL, "tensorsketch: bad mode arguments");
+  return launch_tensorsketch(ctx, N, dims, R, factors, ldf, lambda, hs, ss, L, Y, ldy);
+}
+
+extern "C" int idl_gaussian_stage(idl_ctx* ctx, const double* Omega, int64_t m2, int64_t m1, const void* Y1, int64_t R,
+                                  int64_t ldy1, int dtype, int precision, void* Y2, int64_t ldy2) {
+  TRY(check_ctx(ctx));
+  if ((dtype != IDL_F32 && dtype != IDL_F64) || m2 < 1 || m1 < 1 || R < 1 || ldy1 < R || ldy2 < m2 || !Omega ||
+      !Y1 || !Y2 || precision < 0 || precision > 3 || (dtype == IDL_F64 && precision != IDL_PREC_FP64))
+    return fail(ctx, IDL_EINVAL, "gaussian_stage: bad arguments");
+  return launch_gaussian(ctx, Omega, m2, m1, Y1, R, ldy1, dtype, precision, Y2, ldy2);
+}
+
+extern "C" int idl_cpqr(idl_ctx* ctx, void* Y2, int64_t m, int64_t R, int64_t ldy2, int dtype, int64_t K, int32_t* J,
+                        double* rnorm) {
+  TRY(check_ctx(ctx));
+  if ((dtype != IDL_F32 && dtype != IDL_F64) || m < 1 || R < 1 || ldy2 < m || K < 1 || K > m || K > R || !Y2 || !J)
+    return fail(ctx, IDL_EINVAL, "cpqr: bad arguments");
+  TRY(clear_diag(ctx));
+  return launch_cpqr(ctx, Y2, m, R, ldy2, dtype, K, J, rnorm);
+}
+
+extern "C" int idl_t_solve(idl_ctx* ctx, const void* Y2, int64_t m, int64_t R, int64_t ldy2, int dtype, int64_t K,
+                           const int32_t* J, double* T, int32_t* rest) {
+  TRY(check_ctx(ctx));
+  if ((dtype != IDL_F32 && dtype != IDL_F64) || m < 1 || R < 1 || ldy2 < m || K < 1 || K > m || K >= R || !Y2 ||
+      !J || !T)
+    return fail(ctx, IDL_EINVAL, "t_solve: bad arguments");
+  return launch_t_solve(ctx, Y2, m, R, ldy2, dtype, K, J, T, rest);
+}
+
+extern "C" int idl_lambda_hat(idl_ctx* ctx, const double* lambda, const int32_t* J, const double* T, int64_t K,
+                              int64_t R, double* lambda_hat) {
+  TRY(check_ctx(ctx));
+  if (!lambda || !J || !T || !lambda_hat || K < 1 || K >= R) return fail(ctx, IDL_EINVAL, "lambda_hat: bad arguments");
+  return launch_lambda_hat(ctx, lambda, J, T, K, R, lambda_hat);
+}
+
+// ---------------------------------------------------------------------------
+// pipelines
+// ---------------------------------------------------------------------------
+static int check_params(idl_ctx* ctx, const idl_params* p, int dtype, int64_t I, int64_t R, int64_t K, bool tensor) {
+  if (!p) return fail(ctx, IDL_EINVAL, "null params");
+  if (dtype != IDL_F32 && dtype != IDL_F64) return fail(ctx, IDL_EINVAL, "dtype must be IDL_F32 or IDL_F64");
+  if (p->precision < 0 || p->precision > 3) return fail(ctx, IDL_EINVAL, "unknown precision");
+  if (dtype == IDL_F64 && p->precision != IDL_PREC_FP64)
+    return fail(ctx, IDL_EINVAL, "FP64 data needs precision IDL_PREC_FP64");
+  if (dtype == IDL_F32 && p->precision == IDL_PREC_FP64)
+    return fail(ctx, IDL_EINVAL, "FP32 data cannot use precision IDL_PREC_FP64");
+  if (K < 1 || K >= R) return fail(ctx, IDL_EINVAL, "need 1 <= K < R");
+  if (p->m1 < 1 || p->m1 > 0x7fffffffLL) return fail(ctx, IDL_EINVAL, "m1 out of range");
+  if (K > p->m1) return fail(ctx, IDL_EINVAL, "need K <= m1");
+  if (p->m2 < 0 || p->m2 > p->m1) return fail(ctx, IDL_EINVAL, "need 0 <= m2 <= m1");
+  if (p->m2 > 0 && K > p->m2) return fail(ctx, IDL_EINVAL, "need K <= m2");
+  if (!tensor && p->modified && !(p->m1 < I)) return fail(ctx, IDL_EINVAL, "modified CountSketch needs m1 < I");
+  if (tensor && (p->m1 & (p->m1 - 1))) return fail(ctx, IDL_EINVAL, "TensorSketch length must be a power of two");
+  if (p->residual < 0 || p->residual > 2) return fail(ctx, IDL_EINVAL, "residual mode must be 0, 1 or 2");
+  if (R > 0x7fffffffLL || I > 0x7fffffffLL) return fail(ctx, IDL_ELIMIT, "I and R must fit in int32");
+  return IDL_OK;
+}
+
+// Sketch Y1 (m1 x R, row-major, ld = ldy1) -> J, T, via the Gaussian stage and the QR stage.
+static int finish_pipeline(idl_ctx* ctx, const idl_params* p, int dtype, void* Y1, int64_t ldy1, int64_t R,
+                           int64_t K, int32_t* J, double* T, idl_info* info) {
+  const int es = dtype_size(dtype);
+  const int64_t m = p->m2 > 0 ? p->m2 : p->m1;
+  const int64_t ld2 = m;
+  const bool keep_orig = p->residual == 2;
+  void* Y2 = ws_get(ctx, kWsY2, (size_t)es * (size_t)(R * ld2) * (keep_orig ? 2 : 1));
+  if (!Y2) return IDL_ENOMEM;
+  if (p->m2 > 0) {
+    WS(Om, double, kWsOmega, p->m2 * p->m1);
+    TRY(cuda_check(ctx, launch_draw_gaussian(ctx->stream, p->seed, p->m2, p->m1, Om), "draw gaussian"));
+    TRY(launch_gaussian(ctx, Om, p->m2, p->m1, Y1, R, ldy1, dtype, p->precision, Y2, ld2));
+  } else {
+    TRY(launch_transpose_to_colmajor(ctx, Y1, m, R, ldy1, dtype, Y2, ld2));
+  }
+  void* Yf = Y2;
+  if (keep_orig) {
+    Yf = (char*)Y2 + (size_t)es * (size_t)(R * ld2);
+    TRY(cuda_check(ctx, cudaMemcpyAsync(Yf, Y2, (size_t)es * R * ld2, cudaMemcpyDeviceToDevice, ctx->stream), "copy"));
+  }
+  const bool jdev = is_device_ptr(J), tdev = is_device_ptr(T);
+  int32_t* Jd = J;
+  double* Td = T;
+  if (!jdev) { Jd = (int32_t*)ws_get(ctx, kWsJ, sizeof(int32_t) * (size_t)K); if (!Jd) return IDL_ENOMEM; }
+  if (!tdev) { Td = (double*)ws_get(ctx, kWsT, sizeof(double) * (size_t)(K * (R - K))); if (!Td) return IDL_ENOMEM; }
+  WS(rest, int32_t, kWsRest, R);
+  TRY(clear_diag(ctx));
+  TRY(launch_cpqr(ctx, Yf, m, R, ld2, dtype, K, Jd, nullptr));
+  TRY(launch_t_solve(ctx, Yf, m, R, ld2, dtype, K, Jd, Td, rest));
+  if (keep_orig) TRY(launch_residual(ctx, Y2, Yf, m, R, ld2, dtype, K, Jd, Td, rest));
+  if (!jdev)
+    TRY(cuda_check(ctx, cudaMemcpyAsync(J, Jd, sizeof(int32_t) * K, cudaMemcpyDeviceToHost, ctx->stream), "copy J"));
+  if (!tdev)
+    TRY(cuda_check(ctx, cudaMemcpyAsync(T, Td, sizeof(double) * K * (R - K), cudaMemcpyDeviceToHost, ctx->stream),
+                   "copy T"));
+  if (info) return finish_info(ctx, p, p->precision, info, K, R);
+  if (!jdev || !tdev) TRY(cuda_check(ctx, cudaStreamSynchronize(ctx->stream), "sync"));
+  return IDL_OK;
+}
+
+extern "C" int id_matrix(idl_ctx* ctx, const void* A, int64_t I, int64_t R, int64_t lda, int dtype, int64_t K,
+                         const idl_params* p, int32_t* J, double* T, idl_info* info) {
+  TRY(check_ctx(ctx));
+  TRY(check_params(ctx, p, dtype, I, R, K, false));
+  if (I < 1 || lda < R || !A || !J || !T) return fail(ctx, IDL_EINVAL, "id_matrix: bad arguments");
+  const int es = dtype_size(dtype);
+  const int64_t m1 = p->m1;
+  int rc;
+  const void* Ad = stage_in(ctx, A, (size_t)es * (size_t)((I - 1) * lda + R), kWsA, &rc);
+  TRY(rc);
+  WS(h, int32_t, kWsH, I);
+  WS(s, int8_t, kWsS, I);
+  WS(ptr, int32_t, kWsBucketPtr, m1 + 1);
+  WS(rows, int32_t, kWsRowList, I);
+  const int64_t ldy1 = round_up(R, 32);
+  void* Y1 = ws_get(ctx, kWsY1, (size_t)es * (size_t)(m1 * ldy1));
+  if (!Y1) return IDL_ENOMEM;
+  TRY(cuda_check(ctx, launch_draw_countsketch(ctx->stream, p->seed, I, m1, p->modified, h, s, ctx->d_status),
+                 "draw countsketch"));
+  TRY(launch_bucket_offsets(ctx, h, I, m1, ptr, rows));
+  TRY(launch_countsketch_dense(ctx, Ad, I, R, lda, dtype, s, ptr, rows, m1, Y1, ldy1));
+  return finish_pipeline(ctx, p, dtype, Y1, ldy1, R, K, J, T, info);
+}
+
+extern "C" int id_matrix_csr(idl_ctx* ctx, const int64_t* rowptr, const int32_t* colidx, const void* vals, int64_t I,
+                             int64_t R, int64_t nnz, int dtype, int64_t K, const idl_params* p, int32_t* J, double* T,
+                             idl_info* info) {
+  TRY(check_ctx(ctx));
+  TRY(check_params(ctx, p, dtype, I, R, K, false));
+  if (I < 1 || nnz < 0 || !rowptr || !J || !T || (nnz > 0 && (!colidx || !vals)))
+    return fail(ctx, IDL_EINVAL, "id_matrix_csr: bad arguments");
+  const int es = dtype_size(dtype);
+  const int64_t m1 = p->m1;
+  int rc;
+  const int64_t* rp = (const int64_t*)stage_in(ctx, rowptr, sizeof(int64_t) * (size_t)(I + 1), kWsRowptr, &rc);
+  TRY(rc);
+  const int32_t* ci = nnz ? (const int32_t*)stage_in(ctx, colidx, sizeof(int32_t) * (size_t)nnz, kWsColidx, &rc)
+                          : colidx;
+  TRY(rc);
+  const void* vv = nnz ? stage_in(ctx, vals, (size_t)es * (size_t)nnz, kWsVals, &rc) : vals;
+  TRY(rc);
+  WS(h, int32_t, kWsH, I);
+  WS(s, int8_t, kWsS, I);
+  WS(ptr, int32_t, kWsBucketPtr, m1 + 1);
+  WS(rows, int32_t, kWsRowList, I);
+  const int64_t ldy1 = round_up(R, 32);
+  void* Y1 = ws_get(ctx, kWsY1, (size_t)es * (size_t)(m1 * ldy1));
+  if (!Y1) return IDL_ENOMEM;
+  TRY(cuda_check(ctx, launch_draw_countsketch(ctx->stream, p->seed, I, m1, p->modified, h, s, ctx->d_status),
+                 "draw countsketch"));
+  TRY(launch_bucket_offsets(ctx, h, I, m1, ptr, rows));
+  TRY(launch_countsketch_csr(ctx, rp, ci, vv, I, R, nnz, dtype, s, ptr, rows, m1, Y1, ldy1));
+  return finish_pipeline(ctx, p, dtype, Y1, ldy1, R, K, J, T, info);
+}
+
+extern "C" int id_cp_tensor(idl_ctx* ctx, int N, const int64_t* dims, int64_t R, const void* const* factors,
+                            const int64_t* ldf, const double* lambda, int64_t K, const idl_params* p, int32_t* J,
+                            double* T, double* lambda_hat, idl_info* info) {
+  TRY(check_ctx(ctx));
+  TRY(check_params(ctx, p, IDL_F32, 1, R, K, true));
+  if (N < 1 || N > 8 || !dims || !factors || !ldf || !lambda || !J || !T || !lambda_hat)
+    return fail(ctx, IDL_EINVAL, "id_cp_tensor: bad arguments");
+  const int64_t L = p->m1;
+  int64_t maxdim = 0, tot = 0;
+  for (int n = 0; n < N; ++n) {
+    if (dims[n] < 1 || ldf[n] < dims[n] || !factors[n] || !is_device_ptr(factors[n]))
+      return fail(ctx, IDL_EINVAL, "id_cp_tensor: factors must be device pointers with ldf >= dims");
+    maxdim = std::max(maxdim, dims[n]);
+    tot += dims[n];
+  }
+  int rc;
+  const double* lam = (const double*)stage_in(ctx, lambda, sizeof(double) * (size_t)R, kWsLam, &rc);
+  TRY(rc);
+  WS(hbuf, int32_t, kWsModeH, tot);
+  WS(sbuf, int8_t, kWsModeS, tot);
+  const int32_t* hs[8];
+  const int8_t* ss[8];
+  int64_t off = 0;
+  for (int n = 0; n < N; ++n) {
+    TRY(cuda_check(ctx, launch_draw_mode(ctx->stream, p->seed, n, dims[n], L, hbuf + off, sbuf + off), "draw mode"));
+    hs[n] = hbuf + off;
+    ss[n] = sbuf + off;
+    off += dims[n];
+  }
+  const int64_t ldy1 = round_up(R, 32);
+  float* Y1 = (float*)ws_get(ctx, kWsY1, sizeof(float) * (size_t)(L * ldy1));
+  if (!Y1) return IDL_ENOMEM;
+  TRY(launch_tensorsketch(ctx, N, dims, R, factors, ldf, lam, hs, ss, L, Y1, ldy1));
+  // J and T on the device for lambda_hat; staged back if the caller passed host pointers
+  const bool jdev = is_device_ptr(J), tdev = is_device_ptr(T), ldev = is_device_ptr(lambda_hat);
+  int32_t* Jd = J;
+  double* Td = T;
+  if (!jdev) { Jd = (int32_t*)ws_get(ctx, kWsJ, sizeof(int32_t) * (size_t)K); if (!Jd) return IDL_ENOMEM; }
+  if (!tdev) { Td = (double*)ws_get(ctx, kWsT, sizeof(double) * (size_t)(K * (R - K))); if (!Td) return IDL_ENOMEM; }
+  TRY(finish_pipeline(ctx, p, IDL_F32, Y1, ldy1, R, K, Jd, Td, nullptr));
+  double* lhd = lambda_hat;
+  if (!ldev) { lhd = (double*)ws_get(ctx, kWsLamHat, sizeof(double) * (size_t)K); if (!lhd) return IDL_ENOMEM; }
+  TRY(launch_lambda_hat(ctx, lam, Jd, Td, K, R, lhd));
+  if (!jdev) TRY(cuda_check(ctx, cudaMemcpyAsync(J, Jd, sizeof(int32_t) * K, cudaMemcpyDeviceToHost, ctx->stream), "J"));
+  if (!tdev)
+    TRY(cuda_check(ctx, cudaMemcpyAsync(T, Td, sizeof(double) * K * (R - K), cudaMemcpyDeviceToHost, ctx->stream), "T"));
+  if (!ldev)
+    TRY(cuda_check(ctx, cudaMemcpyAsync(lambda_hat, lhd, sizeof(double) * K, cudaMemcpyDeviceToHost, ctx->stream),
+                   "lambda_hat"));
+  if (info) return finish_info(ctx, p, p->precision, info, K, R);
+  if (!jdev || !tdev || !ldev) TRY(cuda_check(ctx, cudaStreamSynchronize(ctx->stream), "sync"));
+  return IDL_OK;
+}

@@ -1,0 +1,486 @@
+// cpqr.cu -- Algorithm 1 on the small sketch: rank-K column-pivoted Householder
+// QR, T = R11^{-1} R12 in FP64, the FP64 residual check and the s-value update
+// lambda_hat of Algorithm 3.
+//
+// QR stage design.  The sketch Y2 (m x R, m <= 256) is a few MB at most, so it
+// is held entirely in the distributed shared memory of one thread-block
+// cluster (up to 16 CTAs x 227 KB): CTA q owns a contiguous block of columns.
+// The K pivot steps are inherently sequential; each costs one hardware cluster
+// barrier:
+//   1. every CTA publishes its best (largest remaining norm, smallest index)
+//      column in its own shared memory;                 cluster barrier
+//   2. every CTA reads the cluster's candidates and the winning column's
+//      trailing part over DSMEM, and forms the same Householder reflection;
+//   3. every CTA applies it to its active columns (a group of tpc lanes per
+//      column, warp-shuffle reductions) and recomputes their trailing norms
+//      exactly (no downdating, so no cancellation safeguard is needed).
+// The pivot column itself is finalised one step later, after the next
+// barrier, because other CTAs read it during the current step.
+#include <cooperative_groups.h>
+#include <cuda_runtime.h>
+
+#include <cfloat>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace cg = cooperative_groups;
+
+namespace idl {
+
+template <typename T> struct Cand { T val; int idx; int pad; };
+
+template <typename T>
+__device__ __forceinline__ bool better(T va, int ia, T vb, int ib) {
+  return va > vb || (va == vb && ia < ib && ia >= 0) || (ib < 0 && ia >= 0);
+}
+
+__device__ __forceinline__ float group_sum(float v, int tpc) {
+  for (int o = tpc >> 1; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ double group_sum(double v, int tpc) {
+  for (int o = tpc >> 1; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+constexpr int kCpqrThreads = 1024;
+
+template <typename T>
+__global__ void __launch_bounds__(kCpqrThreads, 1)
+cpqr_cluster_kernel(const T* __restrict__ Yin, T* __restrict__ Yout, int m, int R, int ld, int K, int nc, int lds,
+                    int tpc, int32_t* __restrict__ J, double* __restrict__ rnorm, double* __restrict__ diag,
+                    int* status) {
+  cg::cluster_group cluster = cg::this_cluster();
+  const int rank = (int)cluster.block_rank();
+  const int c0 = rank * nc;
+  const int ncl = max(0, min(nc, R - c0));
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const int ngroups = blockDim.x / tpc, g = tid / tpc, gl = tid % tpc;
+
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* cols = (T*)smem_raw;                           // nc * lds
+  T* nrm2 = cols + (size_t)nc * lds;                // nc
+  T* x = nrm2 + nc;                                 // m  (pivot column, rows t..)
+  T* v = x + m;                                     // m  (Householder vector)
+  Cand<T>* cand = (Cand<T>*)(v + m + 2);            // [2] published candidates (double-buffered)
+  __shared__ T red_v[32];
+  __shared__ int red_i[32];
+  __shared__ int s_p, s_w;
+  __shared__ T s_beta, s_alpha;
+  __shared__ int active_bits[1];                    // unused placeholder to keep the layout obvious
+  (void)active_bits;
+  // active flag folded into nrm2: inactive columns get -1
+
+  // ---- load my columns, initial norms ----
+  for (int e = tid; e < ncl * m; e += blockDim.x) {
+    const int c = e / m, i = e - c * m;
+    cols[c * lds + i] = Yin[(int64_t)(c0 + c) * ld + i];
+  }
+  __syncthreads();
+  double fro = 0.0;
+  const int iters = (ncl + ngroups - 1) / ngroups;
+  for (int it = 0; it < iters; ++it) {
+    const int c = it * ngroups + g;
+    T s = T(0);
+    if (c < ncl)
+      for (int i = gl; i < m; i += tpc) { const T y = cols[c * lds + i]; s += y * y; }
+    s = group_sum(s, tpc);
+    if (c < ncl && gl == 0) { nrm2[c] = s; fro += (double)s; }
+  }
+  if (gl == 0 && fro != 0.0) atomicAdd(&diag[1], fro);
+  __syncthreads();
+
+  int prev_pl = -1, prev_t = 0;
+  T prev_alpha = T(0);
+  for (int t = 0; t < K; ++t) {
+    // 1. local candidate
+    T bv = T(-1); int bi = -1;
+    for (int c = tid; c < ncl; c += blockDim.x) {
+      const T nv = nrm2[c];
+      if (nv >= T(0) && better(nv, c0 + c, bv, bi)) { bv = nv; bi = c0 + c; }
+    }
+    for (int o = 16; o; o >>= 1) {
+      const T ov = __shfl_xor_sync(0xffffffffu, bv, o);
+      const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+      if (better(ov, oi, bv, bi)) { bv = ov; bi = oi; }
+    }
+    if (lane == 0) { red_v[wid] = bv; red_i[wid] = bi; }
+    __syncthreads();
+    if (wid == 0) {
+      const int nw = blockDim.x >> 5;
+      bv = lane < nw ? red_v[lane] : T(-1);
+      bi = lane < nw ? red_i[lane] : -1;
+      for (int o = 16; o; o >>= 1) {
+        const T ov = __shfl_xor_sync(0xffffffffu, bv, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        if (better(ov, oi, bv, bi)) { bv = ov; bi = oi; }
+      }
+      if (lane == 0) { cand[t & 1].val = bv; cand[t & 1].idx = bi; }
+    }
+    cluster.sync();                                  // candidates (and pivot data) visible
+
+    // finalise my pivot column of the previous step (nobody reads it any more)
+    if (prev_pl >= 0) {
+      for (int i = prev_t + tid; i < m; i += blockDim.x)
+        cols[prev_pl * lds + i] = (i == prev_t) ? prev_alpha : T(0);
+      prev_pl = -1;
+    }
+    // 2. cluster-wide winner
+    if (wid == 0) {
+      const int CS = (int)cluster.num_blocks();
+      bv = T(-1); bi = -1; int bw = -1;
+      if (lane < CS) {
+        Cand<T>* rc = cluster.map_shared_rank(&cand[t & 1], (unsigned)lane);
+        bv = rc->val; bi = rc->idx; bw = lane;
+      }
+      for (int o = 16; o; o >>= 1) {
+        const T ov = __shfl_xor_sync(0xffffffffu, bv, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        const int ow = __shfl_xor_sync(0xffffffffu, bw, o);
+        if (better(ov, oi, bv, bi)) { bv = ov; bi = oi; bw = ow; }
+      }
+      if (lane == 0) { s_p = bi; s_w = bw; }
+    }
+    __syncthreads();
+    const int p = s_p, w = s_w;
+    if (p < 0) {
+      // no finite remaining column (NaN/Inf input): every CTA sees the same p and
+      // leaves the loop at the same step, so the cluster barriers stay matched
+      if (rank == 0 && tid == 0) {
+        for (int q = t; q < K; ++q) J[q] = -1;
+        set_status(status, IDL_EDATA);
+      }
+      break;
+    }
+    const int pl = p - w * nc;
+    {
+      const T* rcol = cluster.map_shared_rank(cols, (unsigned)w) + (size_t)pl * lds;
+      for (int i = t + tid; i < m; i += blockDim.x) x[i] = rcol[i];
+    }
+    __syncthreads();
+    // 3. Householder reflection (every CTA computes the same one)
+    if (wid == 0) {
+      T s = T(0);
+      for (int i = t + lane; i < m; i += 32) s += x[i] * x[i];
+      s = warp_sum(s);
+      const T nrm = sqrt(s);
+      const T x0 = x[t];
+      const T alpha = (x0 >= T(0)) ? -nrm : nrm;
+      const T beta = (nrm > T(0)) ? T(1) / (nrm * (nrm + fabs(x0))) : T(0);
+      for (int i = t + lane; i < m; i += 32) v[i] = (i == t) ? x0 - alpha : x[i];
+      if (lane == 0) {
+        s_alpha = alpha; s_beta = beta;
+        if (rank == 0) {
+          J[t] = p;
+          if (rnorm) rnorm[t] = (double)fabs(alpha);
+          if (t == 0) diag[3] = (double)fabs(alpha);
+          if (t == K - 1) diag[4] = (double)fabs(alpha);
+        }
+      }
+    }
+    __syncthreads();
+    const T beta = s_beta;
+    if (w == rank && tid == 0) nrm2[pl] = T(-1);    // retire the pivot column
+    if (w == rank) { prev_pl = pl; prev_t = t; prev_alpha = s_alpha; }
+    __syncthreads();
+    // 4. apply to active columns; recompute trailing norms exactly
+    for (int it = 0; it < iters; ++it) {
+      const int c = it * ngroups + g;
+      const bool act = c < ncl && nrm2[c] >= T(0);
+      T d = T(0);
+      if (act)
+        for (int i = t + gl; i < m; i += tpc) d += v[i] * cols[c * lds + i];
+      d = group_sum(d, tpc) * beta;
+      T s = T(0);
+      if (act) {
+        for (int i = t + gl; i < m; i += tpc) {
+          const T y = cols[c * lds + i] - d * v[i];
+          cols[c * lds + i] = y;
+          if (i > t) s += y * y;
+        }
+      }
+      s = group_sum(s, tpc);
+      if (act && gl == 0) nrm2[c] = s;
+    }
+    __syncthreads();
+  }
+  cluster.sync();                                    // all DSMEM reads of the last step are done
+  if (prev_pl >= 0) {
+    for (int i = prev_t + tid; i < m; i += blockDim.x)
+      cols[prev_pl * lds + i] = (i == prev_t) ? prev_alpha : T(0);
+  }
+  __syncthreads();
+  // ||R22||_F^2 in FP64 over the non-pivot columns' rows K..m-1
+  double r22 = 0.0;
+  for (int it = 0; it < iters; ++it) {
+    const int c = it * ngroups + g;
+    double s = 0.0;
+    if (c < ncl && nrm2[c] >= T(0))
+      for (int i = K + gl; i < m; i += tpc) { const double y = (double)cols[c * lds + i]; s += y * y; }
+    s = group_sum(s, tpc);
+    if (gl == 0) r22 += s;
+  }
+  if (gl == 0 && r22 != 0.0) atomicAdd(&diag[0], r22);
+  for (int e = tid; e < ncl * m; e += blockDim.x) {
+    const int c = e / m, i = e - c * m;
+    Yout[(int64_t)(c0 + c) * ld + i] = cols[c * lds + i];
+  }
+}
+
+template <typename T>
+static int cpqr_impl(idl_ctx* ctx, const T* Yin, T* Yout, int64_t m, int64_t R, int64_t ld, int64_t K, int32_t* J,
+                     double* rnorm) {
+  if (m > 256 || m < 1) return fail(ctx, IDL_ELIMIT, "cpqr: m must be in [1, 256]");
+  auto kern = cpqr_cluster_kernel<T>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  if (e != cudaSuccess) return cuda_check(ctx, e, "cpqr cluster attribute");
+  for (int CS = 16; CS >= 1; CS >>= 1) {
+    const int nc = (int)cdiv(R, CS);
+    const int threads = kCpqrThreads;
+    int tpc = 1;
+    while (tpc < 32 && (int64_t)nc * tpc * 2 <= threads && tpc * 2 <= m) tpc *= 2;
+    int lds = (int)round_up(m, tpc);
+    if (((lds / tpc) & 1) == 0) lds += tpc;
+    const size_t smem = sizeof(T) * ((size_t)nc * lds + nc + 2 * m + 2) + sizeof(Cand<T>) * 2 + 16;
+    if (smem > (size_t)ctx->smem_optin) {
+      if (CS == 16) return fail(ctx, IDL_ELIMIT, "cpqr: sketch exceeds the cluster's shared memory");
+      continue;
+    }
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return cuda_check(ctx, e, "cpqr smem attribute");
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(CS);
+    cfg.blockDim = dim3(threads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = ctx->stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = CS;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int nclusters = 0;
+    e = cudaOccupancyMaxActiveClusters(&nclusters, kern, &cfg);
+    if (e != cudaSuccess || nclusters < 1) { (void)cudaGetLastError(); continue; }
+    ctx->last_cluster = CS;
+    e = cudaLaunchKernelEx(&cfg, kern, Yin, Yout, (int)m, (int)R, (int)ld, (int)K, nc, lds, tpc, J, rnorm,
+                           ctx->d_diag, ctx->d_status);
+    return cuda_check(ctx, e, "cpqr launch");
+  }
+  return fail(ctx, IDL_ELIMIT, "cpqr: no cluster shape fits this device");
+}
+
+int launch_cpqr(idl_ctx* ctx, void* Y2, int64_t m, int64_t R, int64_t ld, int dtype, int64_t K, int32_t* J,
+                double* rnorm) {
+  if (dtype == IDL_F32) return cpqr_impl<float>(ctx, (const float*)Y2, (float*)Y2, m, R, ld, K, J, rnorm);
+  return cpqr_impl<double>(ctx, (const double*)Y2, (double*)Y2, m, R, ld, K, J, rnorm);
+}
+
+// ----------------------------------------------------------------------------
+// Non-skeleton columns in ascending order, and T = R11^{-1} R12 (FP64).
+// ----------------------------------------------------------------------------
+__global__ void rest_kernel(const int32_t* __restrict__ J, int K, int R, int32_t* __restrict__ rest) {
+  extern __shared__ int32_t sJ[];
+  for (int q = threadIdx.x; q < K; q += blockDim.x) sJ[q] = J[q];
+  __syncthreads();
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= R) return;
+  int less = 0;
+  bool piv = false;
+  for (int q = 0; q < K; ++q) {
+    const int j = sJ[q];
+    if (j < 0 || j >= R) continue;               // invalid pivots (flagged upstream) are ignored
+    less += j < r;
+    piv |= j == r;
+  }
+  const int pos = r - less;
+  if (!piv && pos >= 0 && pos < R - K) rest[pos] = r;
+}
+
+constexpr int kSolveNB = 32;
+constexpr int kSolveMaxK = 128;
+
+template <typename T>
+__global__ void __launch_bounds__(256) tsolve_kernel(const T* __restrict__ Y, int ld, int K, int R,
+                                                     const int32_t* __restrict__ J,
+                                                     const int32_t* __restrict__ rest, int nrest,
+                                                     double* __restrict__ Tout) {
+  extern __shared__ __align__(16) double sm[];
+  const int KP = K + 1;
+  double* U = sm;                 // K x KP   (R11, upper triangular, pivot order)
+  double* B = sm + K * KP;        // K x NB
+  for (int e = threadIdx.x; e < K * K; e += blockDim.x) {
+    const int j = e / K, i = e - j * K;          // column j (pivot j), row i
+    const int jj = J[j];
+    U[i * KP + j] = (i <= j && jj >= 0 && jj < R) ? (double)Y[(int64_t)jj * ld + i] : 0.0;
+  }
+  const int cb = blockIdx.x * kSolveNB;
+  for (int e = threadIdx.x; e < K * kSolveNB; e += blockDim.x) {
+    const int cc = e / K, i = e - cc * K;
+    const int c = cb + cc;
+    const int r = (c < nrest) ? rest[c] : -1;
+    B[i * kSolveNB + cc] = (r >= 0 && r < R) ? (double)Y[(int64_t)r * ld + i] : 0.0;
+  }
+  __syncthreads();
+  for (int i = K - 1; i >= 0; --i) {
+    if (threadIdx.x < kSolveNB) B[i * kSolveNB + threadIdx.x] /= U[i * KP + i];
+    __syncthreads();
+    for (int e = threadIdx.x; e < i * kSolveNB; e += blockDim.x) {
+      const int j = e / kSolveNB, cc = e - j * kSolveNB;
+      B[j * kSolveNB + cc] -= U[j * KP + i] * B[i * kSolveNB + cc];
+    }
+    __syncthreads();
+  }
+  for (int e = threadIdx.x; e < K * kSolveNB; e += blockDim.x) {
+    const int i = e / kSolveNB, cc = e - i * kSolveNB;
+    const int c = cb + cc;
+    if (c < nrest) Tout[(int64_t)i * nrest + c] = B[i * kSolveNB + cc];
+  }
+}
+
+int launch_t_solve(idl_ctx* ctx, const void* Y2, int64_t m, int64_t R, int64_t ld, int dtype, int64_t K,
+                   const int32_t* J, double* T, int32_t* rest) {
+  (void)m;
+  if (K > kSolveMaxK) return fail(ctx, IDL_ELIMIT, "t_solve: K > 128");
+  const int64_t nrest = R - K;
+  if (!rest) {
+    rest = (int32_t*)ws_get(ctx, kWsRest, sizeof(int32_t) * (size_t)(R > 0 ? R : 1));
+    if (!rest) return IDL_ENOMEM;
+  }
+  rest_kernel<<<(unsigned)cdiv(R, 256), 256, sizeof(int32_t) * (size_t)K, ctx->stream>>>(J, (int)K, (int)R, rest);
+  if (nrest <= 0) return cuda_check(ctx, cudaGetLastError(), "rest");
+  const size_t smem = sizeof(double) * ((size_t)K * (K + 1) + (size_t)K * kSolveNB);
+  cudaError_t e;
+  if (dtype == IDL_F32) {
+    e = cudaFuncSetAttribute(tsolve_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess)
+      tsolve_kernel<float><<<(unsigned)cdiv(nrest, kSolveNB), 256, smem, ctx->stream>>>(
+          (const float*)Y2, (int)ld, (int)K, (int)R, J, rest, (int)nrest, T);
+  } else {
+    e = cudaFuncSetAttribute(tsolve_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess)
+      tsolve_kernel<double><<<(unsigned)cdiv(nrest, kSolveNB), 256, smem, ctx->stream>>>(
+          (const double*)Y2, (int)ld, (int)K, (int)R, J, rest, (int)nrest, T);
+  }
+  if (e != cudaSuccess) return cuda_check(ctx, e, "t_solve attribute");
+  return cuda_check(ctx, cudaGetLastError(), "t_solve");
+}
+
+// ----------------------------------------------------------------------------
+// Explicit FP64 residual  sum_c ||Y2[:, rest_c] - Y2[:, J] T[:, c]||^2  (from the
+// unfactored sketch), accumulated into diag[2].
+// ----------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(256) residual_kernel(const T* __restrict__ Y, int m, int ld, int K, int R,
+                                                       const int32_t* __restrict__ J, const double* __restrict__ Tm,
+                                                       const int32_t* __restrict__ rest, int nrest,
+                                                       double* __restrict__ diag) {
+  extern __shared__ __align__(16) double yj[];      // m x K  (Y2[:, J])
+  for (int e = threadIdx.x; e < m * K; e += blockDim.x) {
+    const int k = e / m, i = e - k * m;
+    const int jj = J[k];
+    yj[i * K + k] = (jj >= 0 && jj < R) ? (double)Y[(int64_t)jj * ld + i] : 0.0;
+  }
+  __syncthreads();
+  double acc = 0.0;
+  // one warp per column, lanes over rows
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int c = blockIdx.x * nw + wid; c < nrest; c += gridDim.x * nw) {
+    const int r = rest[c];
+    if (r < 0 || r >= R) continue;
+    for (int i = lane; i < m; i += 32) {
+      double y = (double)Y[(int64_t)r * ld + i];
+      for (int k = 0; k < K; ++k) y -= yj[i * K + k] * Tm[(int64_t)k * nrest + c];
+      acc += y * y;
+    }
+  }
+  acc = warp_sum(acc);
+  if (lane == 0 && acc != 0.0) atomicAdd(&diag[2], acc);
+}
+
+int launch_residual(idl_ctx* ctx, const void* Y2orig, const void* Y2fact, int64_t m, int64_t R, int64_t ld,
+                    int dtype, int64_t K, const int32_t* J, const double* T, const int32_t* rest) {
+  (void)Y2fact;
+  const int64_t nrest = R - K;
+  if (nrest <= 0) return IDL_OK;
+  const size_t smem = sizeof(double) * (size_t)m * K;
+  if (smem > (size_t)ctx->smem_optin) return fail(ctx, IDL_ELIMIT, "residual: m*K too large");
+  const int blocks = (int)std::min<int64_t>(cdiv(nrest, 8), 4 * ctx->num_sms);
+  cudaError_t e;
+  if (dtype == IDL_F32) {
+    e = cudaFuncSetAttribute(residual_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess)
+      residual_kernel<float><<<blocks, 256, smem, ctx->stream>>>((const float*)Y2orig, (int)m, (int)ld, (int)K, (int)R, J, T,
+                                                                 rest, (int)nrest, ctx->d_diag);
+  } else {
+    e = cudaFuncSetAttribute(residual_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess)
+      residual_kernel<double><<<blocks, 256, smem, ctx->stream>>>((const double*)Y2orig, (int)m, (int)ld, (int)K, (int)R, J,
+                                                                  T, rest, (int)nrest, ctx->d_diag);
+  }
+  if (e != cudaSuccess) return cuda_check(ctx, e, "residual attribute");
+  return cuda_check(ctx, cudaGetLastError(), "residual");
+}
+
+// ----------------------------------------------------------------------------
+// lambda_hat_k = lambda_{J_k} (1 + sum_c T_kc)  (Algorithm 3)
+// ----------------------------------------------------------------------------
+__global__ void lambda_hat_kernel(const double* __restrict__ lam, const int32_t* __restrict__ J,
+                                  const double* __restrict__ Tm, int nrest, double* __restrict__ out) {
+  __shared__ double part[32];
+  const int k = blockIdx.x;
+  double s = 0.0;
+  for (int c = threadIdx.x; c < nrest; c += blockDim.x) s += Tm[(int64_t)k * nrest + c];
+  s = warp_sum(s);
+  if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    s = threadIdx.x < (blockDim.x >> 5) ? part[threadIdx.x] : 0.0;
+    s = warp_sum(s);
+    if (threadIdx.x == 0) {
+      const int j = J[k];
+      out[k] = (j >= 0 && j < nrest + (int)gridDim.x) ? lam[j] * (1.0 + s) : 0.0;
+    }
+  }
+}
+
+int launch_lambda_hat(idl_ctx* ctx, const double* lambda, const int32_t* J, const double* T, int64_t K, int64_t R,
+                      double* lambda_hat) {
+  if (K <= 0) return IDL_OK;
+  lambda_hat_kernel<<<(unsigned)K, 256, 0, ctx->stream>>>(lambda, J, T, (int)(R - K), lambda_hat);
+  return cuda_check(ctx, cudaGetLastError(), "lambda_hat");
+}
+
+// ----------------------------------------------------------------------------
+// Row-major m x R  ->  column-major (R columns of ldy2), for m2 = 0.
+// ----------------------------------------------------------------------------
+template <typename T>
+__global__ void transpose_kernel(const T* __restrict__ A, int64_t m, int64_t R, int64_t lda, T* __restrict__ B,
+                                 int64_t ldb) {
+  __shared__ T tile[32][33];
+  const int64_t r0 = (int64_t)blockIdx.x * 32, i0 = (int64_t)blockIdx.y * 32;
+  for (int y = threadIdx.y; y < 32; y += blockDim.y) {
+    const int64_t i = i0 + y, r = r0 + threadIdx.x;
+    if (i < m && r < R) tile[y][threadIdx.x] = A[i * lda + r];
+  }
+  __syncthreads();
+  for (int y = threadIdx.y; y < 32; y += blockDim.y) {
+    const int64_t r = r0 + y, i = i0 + threadIdx.x;
+    if (i < m && r < R) B[r * ldb + i] = tile[threadIdx.x][y];
+  }
+}
+
+int launch_transpose_to_colmajor(idl_ctx* ctx, const void* Y1, int64_t m, int64_t R, int64_t ldy1, int dtype,
+                                 void* Y2, int64_t ldy2) {
+  dim3 grid((unsigned)cdiv(R, 32), (unsigned)cdiv(m, 32));
+  dim3 block(32, 8);
+  if (dtype == IDL_F32)
+    transpose_kernel<float><<<grid, block, 0, ctx->stream>>>((const float*)Y1, m, R, ldy1, (float*)Y2, ldy2);
+  else
+    transpose_kernel<double><<<grid, block, 0, ctx->stream>>>((const double*)Y1, m, R, ldy1, (double*)Y2, ldy2);
+  return cuda_check(ctx, cudaGetLastError(), "transpose");
+}
+
+}  // namespace idl

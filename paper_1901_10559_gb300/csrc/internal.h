@@ -1,0 +1,83 @@
+// internal.h -- host-side context and the launchers shared by the .cu files.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/idl.h"
+
+struct idl_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  int num_sms = 0;
+  int smem_optin = 0;          // max dynamic shared memory per block (bytes)
+  int* d_status = nullptr;     // device status word
+  double* d_diag = nullptr;    // device diagnostics: [0] ||R22||^2, [1] ||Y2||^2, [2] explicit residual^2,
+                               // [3] |r_11|, [4] |r_KK|
+  std::string err;
+  struct Buf { void* p = nullptr; size_t bytes = 0; };
+  std::vector<Buf> slots;
+  int last_cluster = 0;
+  size_t fail_alloc_at = 0;    // test hook: fail the n-th workspace allocation (0 = never)
+  size_t alloc_count = 0;
+};
+
+namespace idl {
+
+// Workspace slots (each slot is one growable device buffer).
+enum Slot {
+  kWsH = 0, kWsS, kWsOmega, kWsBucketPtr, kWsRowList, kWsCursor, kWsBig, kWsY1, kWsPart,
+  kWsY2, kWsOmegaConv, kWsRest, kWsA, kWsRowptr, kWsColidx, kWsVals, kWsJ, kWsT,
+  kWsModeH, kWsModeS, kWsLam, kWsLamHat, kWsCpqrSync, kWsCount
+};
+
+// Returns a device buffer of at least `bytes` for the slot (grown on demand), or
+// nullptr with ctx->err set.
+void* ws_get(idl_ctx* ctx, int slot, size_t bytes);
+
+int fail(idl_ctx* ctx, int code, const std::string& msg);
+int cuda_check(idl_ctx* ctx, cudaError_t e, const char* where);
+
+// draws.cu
+cudaError_t launch_draw_countsketch(cudaStream_t st, uint64_t seed, int64_t I, int64_t L, int modified,
+                                    int32_t* h, int8_t* s, int* status);
+cudaError_t launch_draw_gaussian(cudaStream_t st, uint64_t seed, int64_t m2, int64_t m1, double* Omega);
+cudaError_t launch_draw_mode(cudaStream_t st, uint64_t seed, int n, int64_t In, int64_t L, int32_t* h,
+                             int8_t* s);
+int launch_bucket_offsets(idl_ctx* ctx, const int32_t* h, int64_t I, int64_t L, int32_t* bucket_ptr,
+                          int32_t* row_list);
+
+// countsketch.cu
+int launch_countsketch_dense(idl_ctx* ctx, const void* A, int64_t I, int64_t R, int64_t lda, int dtype,
+                             const int8_t* s, const int32_t* bucket_ptr, const int32_t* row_list,
+                             int64_t L, void* Y1, int64_t ldy);
+int launch_countsketch_csr(idl_ctx* ctx, const int64_t* rowptr, const int32_t* colidx, const void* vals,
+                           int64_t I, int64_t R, int64_t nnz, int dtype, const int8_t* s,
+                           const int32_t* bucket_ptr, const int32_t* row_list, int64_t L, void* Y1,
+                           int64_t ldy);
+
+// gaussian.cu
+int launch_gaussian(idl_ctx* ctx, const double* Omega, int64_t m2, int64_t m1, const void* Y1, int64_t R,
+                    int64_t ldy1, int dtype, int precision, void* Y2, int64_t ldy2);
+
+// cpqr.cu
+int launch_cpqr(idl_ctx* ctx, void* Y2, int64_t m, int64_t R, int64_t ld, int dtype, int64_t K, int32_t* J,
+                double* rnorm);
+int launch_t_solve(idl_ctx* ctx, const void* Y2, int64_t m, int64_t R, int64_t ld, int dtype, int64_t K,
+                   const int32_t* J, double* T, int32_t* rest);
+int launch_residual(idl_ctx* ctx, const void* Y2orig, const void* Y2fact, int64_t m, int64_t R, int64_t ld,
+                    int dtype, int64_t K, const int32_t* J, const double* T, const int32_t* rest);
+int launch_lambda_hat(idl_ctx* ctx, const double* lambda, const int32_t* J, const double* T, int64_t K,
+                      int64_t R, double* lambda_hat);
+int launch_transpose_to_colmajor(idl_ctx* ctx, const void* Y1, int64_t m, int64_t R, int64_t ldy1, int dtype,
+                                 void* Y2, int64_t ldy2);
+
+// tensorsketch.cu
+int launch_tensorsketch(idl_ctx* ctx, int N, const int64_t* dims, int64_t R, const void* const* factors,
+                        const int64_t* ldf, const double* lambda, const int32_t* const* hs,
+                        const int8_t* const* ss, int64_t L, float* Y, int64_t ldy);
+
+}  // namespace idl

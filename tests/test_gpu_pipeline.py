@@ -1,0 +1,241 @@
+"""End-to-end GPU parity of the three pipelines (id_matrix, id_matrix_csr,
+id_cp_tensor) against the FP64 oracle, at small ragged sizes and at the
+workload sizes the bench runs; host-pointer calls; error codes."""
+import numpy as np
+import pytest
+import torch
+
+import paper_1901_10559_gb300 as idl
+from oracle import countsketch as ocs
+from oracle import draws as odr
+from oracle import errors as oer
+from oracle import idmethods as oid
+from oracle.gaussian import BF16, FP32, FP64
+from synth import cp_factors, gaussian_lowrank_dense, lowrank_dense, random_csr, sparse_plus_lowrank_csr
+from tests.helpers import dev, host, pivots_well_separated, rel_fro
+
+pytestmark = pytest.mark.gpu
+
+RATIO = 1.1       # every ID's error within 1.1x the oracle's
+
+
+def _outputs(K, R):
+    return (torch.empty(K, dtype=torch.int32, device="cuda"),
+            torch.empty(K * (R - K), dtype=torch.float64, device="cuda"))
+
+
+def _check_id(J, T, Jw, Tw, info_w, err_fn, ttol):
+    Jg = host(J)
+    K = len(Jw)
+    R = Tw.shape[1] + K
+    Tg = host(T).reshape(K, R - K)
+    assert len(set(Jg.tolist())) == K and Jg.min() >= 0 and Jg.max() < R
+    e_w = err_fn(Jw, Tw)
+    e_g = err_fn(Jg, Tg)
+    if pivots_well_separated(info_w["gaps"]):
+        assert np.array_equal(Jg, Jw)
+        assert np.abs(Tg - Tw).max() <= ttol * max(1.0, np.abs(Tw).max())
+    assert e_g <= RATIO * e_w + 1e-14, (e_g, e_w)
+    return e_g, e_w
+
+
+@pytest.mark.parametrize("dtype,I,R,K,m1,m2", [("f64", 4000, 2000, 20, 900, 30),     # plain FP64 workload
+                                               ("f32", 3001, 517, 13, 200, 40),
+                                               ("f64", 1500, 300, 10, 80, 0),        # Algorithm 2 verbatim
+                                               ("f32", 1000, 64, 60, 100, 64)])
+def test_id_matrix_dense(ctx, dtype, I, R, K, m1, m2):
+    npdt = np.float64 if dtype == "f64" else np.float32
+    A = lowrank_dense(I, R, 0.8, 1e-8, seed=20190130 + I, dtype=npdt)
+    prec = idl.PREC_FP64 if dtype == "f64" else idl.PREC_FP32
+    p = idl.make_params(m1, m2, seed=17, modified=True, precision=prec, residual=2)
+    J, T = _outputs(K, R)
+    info = idl.Info()
+    idl.id_matrix(ctx, dev(A), K, p, J, T, info)
+    assert info.status in (idl.IDL_OK, idl.IDL_ERANK)
+    Jw, Tw, iw = oid.id_matrix(A, k=K, m1=m1, m2=m2, seed=17, modified=True,
+                               precision=FP64 if dtype == "f64" else FP32)
+    _check_id(J, T, Jw, Tw, iw, lambda j, t: oer.matrix_id_error(A, J=j, T=t),
+              1e-7 if dtype == "f64" else 1e-2)
+    # the FP64 residual check agrees with the oracle's sketch residual
+    Y2 = iw["Y2"]
+    Jg = host(J)
+    rest = np.setdiff1d(np.arange(R), Jg)
+    res_w = np.linalg.norm(Y2[:, rest] - Y2[:, Jg] @ host(T).reshape(K, R - K)) / np.linalg.norm(Y2)
+    assert abs(info.residual - res_w) <= 1e-3 * max(res_w, 1e-12) + 1e-6
+
+
+def test_id_matrix_exact_rank_recovery(ctx):
+    rng = np.random.default_rng(1)
+    A = (rng.standard_normal((6000, 12)) @ rng.standard_normal((12, 700))).astype(np.float64)
+    p = idl.make_params(120, 40, seed=3, modified=True, precision=idl.PREC_FP64)
+    J, T = _outputs(12, 700)
+    idl.id_matrix(ctx, dev(A), 12, p, J, T)
+    err = oer.matrix_id_error(A, J=host(J), T=host(T).reshape(12, 688))
+    assert err < 1e-12
+
+
+@pytest.mark.parametrize("dtype,I,R,K,m1,m2,dens", [("f32", 20000, 1500, 25, 700, 35, 0.01),
+                                                    ("f64", 8000, 400, 10, 150, 20, 0.03)])
+def test_id_matrix_csr_small(ctx, dtype, I, R, K, m1, m2, dens):
+    npdt = np.float64 if dtype == "f64" else np.float32
+    c = sparse_plus_lowrank_csr(I, R, dens, rank=K, scale=10.0, dense_frac=0.01, seed=I, dtype=npdt)
+    prec = idl.PREC_FP64 if dtype == "f64" else idl.PREC_FP32
+    p = idl.make_params(m1, m2, seed=5, modified=True, precision=prec)
+    J, T = _outputs(K, R)
+    info = idl.Info()
+    idl.id_matrix_csr(ctx, dev(c.rowptr), dev(c.colidx), dev(c.vals), c.shape, K, p, J, T, info)
+    assert info.status == idl.IDL_OK
+    csr = (c.rowptr, c.colidx, c.vals, c.shape)
+    Jw, Tw, iw = oid.id_matrix(csr=csr, k=K, m1=m1, m2=m2, seed=5, modified=True,
+                               precision=FP64 if dtype == "f64" else FP32)
+    _check_id(J, T, Jw, Tw, iw, lambda j, t: oer.matrix_id_error(csr=csr, J=j, T=t, iters=40),
+              1e-7 if dtype == "f64" else 1e-2)
+
+
+@pytest.fixture(scope="module")
+def cfg1():
+    # sparse FP32 workload: 1e6 x 1e4, density 1e-3, rank-50 term of scale 10 on 1% of rows
+    return sparse_plus_lowrank_csr(1_000_000, 10_000, 1e-3, rank=50, scale=10.0, dense_frac=0.01, seed=20190131)
+
+
+def test_cfg1_sketch_full_size(ctx, cfg1):
+    c = cfg1
+    I, R = c.shape
+    m1 = 3600
+    h, s = torch.empty(I, dtype=torch.int32, device="cuda"), torch.empty(I, dtype=torch.int8, device="cuda")
+    idl.idl_draw_countsketch(ctx, 20190131, I, m1, True, h, s)
+    ptr = torch.empty(m1 + 1, dtype=torch.int32, device="cuda")
+    rows = torch.empty(I, dtype=torch.int32, device="cuda")
+    idl.idl_bucket_offsets(ctx, h, I, m1, ptr, rows)
+    Y = torch.empty((m1, R), dtype=torch.float32, device="cuda")
+    idl.idl_countsketch_csr(ctx, dev(c.rowptr), dev(c.colidx), dev(c.vals), I, R, c.nnz, idl.IDL_F32, h, s, ptr,
+                            rows, m1, Y, R)
+    hw, sw = odr.countsketch_maps(20190131, I, m1, True)
+    want = ocs.countsketch_csr(c.rowptr, c.colidx, c.vals, R, hw, sw, m1)
+    assert rel_fro(host(Y), want) <= 1e-5
+    assert ctx.sync() == idl.IDL_OK
+
+
+def test_cfg1_id_full_size(ctx, cfg1):
+    c = cfg1
+    I, R = c.shape
+    K, m1, m2 = 50, 3600, 60
+    p = idl.make_params(m1, m2, seed=20190131, modified=True, precision=idl.PREC_FP32)
+    J, T = _outputs(K, R)
+    info = idl.Info()
+    idl.id_matrix_csr(ctx, dev(c.rowptr), dev(c.colidx), dev(c.vals), c.shape, K, p, J, T, info)
+    assert info.status == idl.IDL_OK
+    csr = (c.rowptr, c.colidx, c.vals, c.shape)
+    Jw, Tw, iw = oid.id_matrix(csr=csr, k=K, m1=m1, m2=m2, seed=20190131, modified=True, precision=FP32)
+    _check_id(J, T, Jw, Tw, iw, lambda j, t: oer.matrix_id_error(csr=csr, J=j, T=t, iters=25), 1e-2)
+
+
+def test_cfg2_mixed_precision(ctx):
+    # dense mixed precision, reduced rows (the full 131072-row case runs in the bench)
+    I, R, K, m1, m2 = 32768, 4096, 100, 14400, 120
+    A = gaussian_lowrank_dense(I, R, 100, 1e-4, seed=20190132)
+    errs = {}
+    for prec in (idl.PREC_FP32, idl.PREC_BF16X3, idl.PREC_BF16):
+        p = idl.make_params(m1, m2, seed=8, modified=True, precision=prec)
+        J, T = _outputs(K, R)
+        info = idl.Info()
+        idl.id_matrix(ctx, dev(A), K, p, J, T, info)
+        errs[prec] = oer.matrix_id_error(A, J=host(J), T=host(T).reshape(K, R - K), exact=False, iters=15)
+    Jw, Tw, iw = oid.id_matrix(A, k=K, m1=m1, m2=m2, seed=8, modified=True, precision=FP64)
+    e_or = oer.matrix_id_error(A, J=Jw, T=Tw, exact=False, iters=15)
+    assert errs[idl.PREC_FP32] <= RATIO * e_or
+    assert errs[idl.PREC_BF16X3] <= RATIO * e_or
+    assert errs[idl.PREC_BF16] <= 1e-3            # stated error of the BF16 path (reported, gated loosely)
+
+
+def test_cfg3_cp_tensor(ctx):
+    dims, R, K, L, m2 = (1000, 1000, 1000), 1000, 50, 8192, 60
+    facs, lam = cp_factors(dims, R, seed=20190133)
+    fd = [dev(np.ascontiguousarray(F.T)) for F in facs]
+    p = idl.make_params(L, m2, seed=9, modified=False, precision=idl.PREC_FP32)
+    J, T = _outputs(K, R)
+    lh = torch.empty(K, dtype=torch.float64, device="cuda")
+    info = idl.Info()
+    idl.id_cp_tensor(ctx, fd, dev(lam), K, p, J, T, lh, info)
+    Jw, Tw, lhw, iw = oid.id_cp_tensor(facs, lam, k=K, L=L, m2=m2, seed=9, precision=FP32)
+    e_w = oer.tensor_id_error(facs, lam, Jw, lhw)
+    e_g = oer.tensor_id_error(facs, lam, host(J), host(lh))
+    assert e_g <= RATIO * e_w
+    if pivots_well_separated(iw["gaps"]):
+        assert np.array_equal(host(J), Jw)
+        assert np.allclose(host(lh), lhw, rtol=1e-3, atol=1e-6)
+    # lambda_hat is Algorithm 3's update of the GPU's own J, T
+    lh_ref = oid.lambda_hat(lam, host(J), host(T).reshape(K, R - K))
+    assert np.allclose(host(lh), lh_ref, rtol=1e-12, atol=1e-14)
+
+
+def test_cp_tensor_exact_rank(ctx):
+    rng = np.random.default_rng(10)
+    K, dims = 6, (30, 25, 20)
+    base = [rng.standard_normal((d, K)) for d in dims]
+    base = [F / np.linalg.norm(F, axis=0) for F in base]
+    facs = [np.concatenate([F, F, F], axis=1).astype(np.float32) for F in base]     # R = 3K, M has rank K
+    lam = rng.uniform(0.5, 1.5, 3 * K)
+    fd = [dev(np.ascontiguousarray(F.T)) for F in facs]
+    p = idl.make_params(256, 20, seed=2, modified=False, precision=idl.PREC_FP32)
+    J, T = _outputs(K, 3 * K)
+    lh = torch.empty(K, dtype=torch.float64, device="cuda")
+    idl.id_cp_tensor(ctx, fd, dev(lam), K, p, J, T, lh)
+    assert oer.tensor_id_error([F.astype(np.float64) for F in facs], lam, host(J), host(lh)) < 1e-5
+
+
+def test_host_pointer_calls_match_device_calls(ctx):
+    A = lowrank_dense(3000, 400, 0.85, 1e-6, seed=4, dtype=np.float32)
+    K = 15
+    p = idl.make_params(300, 30, seed=6, modified=True, precision=idl.PREC_FP32)
+    Jd, Td = _outputs(K, 400)
+    idl.id_matrix(ctx, dev(A), K, p, Jd, Td)
+    Jh = np.empty(K, np.int32)
+    Th = np.empty(K * (400 - K), np.float64)
+    idl.id_matrix(ctx, A, K, p, Jh, Th)                       # pageable host memory
+    assert np.array_equal(Jh, host(Jd)) and np.array_equal(Th, host(Td))
+    Ap = torch.from_numpy(A).pin_memory()
+    Jp = torch.empty(K, dtype=torch.int32).pin_memory()
+    Tp = torch.empty(K * (400 - K), dtype=torch.float64).pin_memory()
+    idl.id_matrix(ctx, Ap, K, p, Jp, Tp)                      # pinned host memory
+    assert np.array_equal(Jp.numpy(), host(Jd)) and np.array_equal(Tp.numpy(), host(Td))
+    c = random_csr(5000, 300, 0.02, seed=3)
+    Jh2 = np.empty(K, np.int32)
+    Th2 = np.empty(K * 285, np.float64)
+    idl.id_matrix_csr(ctx, c.rowptr, c.colidx, c.vals, c.shape, K, p, Jh2, Th2)
+    Jd2, Td2 = _outputs(K, 300)
+    idl.id_matrix_csr(ctx, dev(c.rowptr), dev(c.colidx), dev(c.vals), c.shape, K, p, Jd2, Td2)
+    assert np.array_equal(Jh2, host(Jd2)) and np.array_equal(Th2, host(Td2))
+
+
+def test_argument_errors(ctx):
+    A = dev(np.zeros((100, 20), np.float32))
+    J, T = _outputs(5, 20)
+    bad = [
+        (idl.make_params(10, 5, 1, precision=idl.PREC_FP32), 6),        # K > m2
+        (idl.make_params(10, 5, 1, precision=idl.PREC_FP32), 20),       # K >= R
+        (idl.make_params(100, 5, 1, modified=True, precision=idl.PREC_FP32), 5),   # modified needs m1 < I
+        (idl.make_params(10, 12, 1, precision=idl.PREC_FP32), 5),       # m2 > m1
+        (idl.make_params(10, 5, 1, precision=idl.PREC_FP64), 5),        # FP64 precision with FP32 data
+    ]
+    for p, K in bad:
+        with pytest.raises(idl.IdlError) as ei:
+            idl.id_matrix(ctx, A, K, p, J, T)
+        assert ei.value.code == idl.IDL_EINVAL
+    with pytest.raises(idl.IdlError) as ei:
+        idl.id_matrix(ctx, A, 5, idl.make_params(300, 299, 1, modified=False, precision=idl.PREC_FP32), J, T)
+    assert ei.value.code == idl.IDL_ELIMIT                              # m2 > 256 (QR stage capacity)
+
+
+def test_injected_allocation_failure_is_reported(ctx):
+    lib = idl.lib()
+    lib.idl_debug_release_workspace(ctx.ptr)
+    lib.idl_debug_fail_alloc(ctx.ptr, 1)
+    A = dev(np.random.default_rng(0).standard_normal((500, 50)).astype(np.float32))
+    J, T = _outputs(5, 50)
+    with pytest.raises(idl.IdlError) as ei:
+        idl.id_matrix(ctx, A, 5, idl.make_params(40, 10, 1, precision=idl.PREC_FP32), J, T)
+    assert ei.value.code == idl.IDL_ENOMEM
+    lib.idl_debug_fail_alloc(ctx.ptr, 0)
+    idl.id_matrix(ctx, A, 5, idl.make_params(40, 10, 1, precision=idl.PREC_FP32), J, T)   # recovers
+    assert ctx.sync() == idl.IDL_OK

@@ -1,0 +1,251 @@
+"""GPU parity of every stage of the hot path against the FP64 oracle, through
+the C ABI (draws, bucket offsets, CountSketch dense/CSR, Gaussian stage, CPQR,
+T solve, TensorSketch, lambda_hat)."""
+import numpy as np
+import pytest
+import torch
+
+import paper_1901_10559_gb300 as idl
+from oracle import countsketch as ocs
+from oracle import cpqr as ocp
+from oracle import draws as odr
+from oracle import gaussian as ogs
+from oracle import tensorsketch as ots
+from synth import cp_factors, random_csr
+from tests.helpers import colmajor_to_matrix, dev, host, pivots_well_separated, rel_fro
+
+pytestmark = pytest.mark.gpu
+
+FP32_TOL = 1e-5     # sketch parity in FP32 (relative Frobenius)
+FP64_TOL = 1e-12    # sketch parity in FP64
+
+
+# ------------------------------------------------------------------ a1 draws
+@pytest.mark.parametrize("I,L,modified,seed", [(1, 1, False, 0), (4000, 900, True, 20190130),
+                                               (1_000_000, 3600, True, 7), (131072, 14400, True, 3),
+                                               (4097, 4096, True, 11), (50_000, 7, False, 5)])
+def test_countsketch_draws_bit_exact(ctx, I, L, modified, seed):
+    h = torch.empty(I, dtype=torch.int32, device="cuda")
+    s = torch.empty(I, dtype=torch.int8, device="cuda")
+    idl.idl_draw_countsketch(ctx, seed, I, L, modified, h, s)
+    hw, sw = odr.countsketch_maps(seed, I, L, modified)
+    assert np.array_equal(host(h), hw)
+    assert np.array_equal(host(s), sw)
+    assert ctx.sync() == idl.IDL_OK
+
+
+def test_gaussian_draws(ctx):
+    for m2, m1, seed in [(30, 900, 20190130), (7, 13, 1), (120, 14400, 4)]:
+        Om = torch.empty(m2 * m1, dtype=torch.float64, device="cuda")
+        idl.idl_draw_gaussian(ctx, seed, m2, m1, Om)
+        want = odr.gaussian_matrix(seed, m2, m1)
+        got = host(Om).reshape(m2, m1)
+        assert np.abs(got - want).max() <= 1e-13 * max(1.0, np.abs(want).max())
+        # the fp32 working copy rounds identically
+        assert np.array_equal(got.astype(np.float32), want.astype(np.float32))
+
+
+def test_mode_draws(ctx):
+    for n in range(4):
+        h = torch.empty(1000, dtype=torch.int32, device="cuda")
+        s = torch.empty(1000, dtype=torch.int8, device="cuda")
+        idl.idl_draw_mode(ctx, 9, n, 1000, 8192, h, s)
+        hs, ss = odr.tensorsketch_maps(9, [1000] * 4, 8192)
+        assert np.array_equal(host(h), hs[n]) and np.array_equal(host(s), ss[n])
+
+
+# ------------------------------------------------------------------ a2 bucket offsets
+@pytest.mark.parametrize("I,L,modified", [(4000, 900, True), (1_000_000, 3600, True), (20000, 9, False),
+                                          (131072, 14400, True), (3, 2, True)])
+def test_bucket_offsets_bit_exact(ctx, I, L, modified):
+    h = torch.empty(I, dtype=torch.int32, device="cuda")
+    s = torch.empty(I, dtype=torch.int8, device="cuda")
+    idl.idl_draw_countsketch(ctx, 5, I, L, modified, h, s)
+    ptr = torch.empty(L + 1, dtype=torch.int32, device="cuda")
+    rows = torch.empty(I, dtype=torch.int32, device="cuda")
+    idl.idl_bucket_offsets(ctx, h, I, L, ptr, rows)
+    pw, rw = ocs.bucket_offsets(odr.countsketch_maps(5, I, L, modified)[0], L)
+    assert np.array_equal(host(ptr), pw)
+    assert np.array_equal(host(rows), rw)
+
+
+# ------------------------------------------------------------------ a3 dense CountSketch
+def _draw(ctx, seed, I, L, modified):
+    h = torch.empty(I, dtype=torch.int32, device="cuda")
+    s = torch.empty(I, dtype=torch.int8, device="cuda")
+    idl.idl_draw_countsketch(ctx, seed, I, L, modified, h, s)
+    ptr = torch.empty(L + 1, dtype=torch.int32, device="cuda")
+    rows = torch.empty(I, dtype=torch.int32, device="cuda")
+    idl.idl_bucket_offsets(ctx, h, I, L, ptr, rows)
+    return h, s, ptr, rows
+
+
+@pytest.mark.parametrize("dtype,I,R,L,lda_pad", [("f32", 3001, 2053, 211, 0), ("f64", 4000, 2000, 900, 0),
+                                                 ("f32", 5000, 1030, 64, 3), ("f64", 777, 17, 100, 1),
+                                                 ("f32", 2, 5, 1, 0)])
+def test_countsketch_dense_parity(ctx, dtype, I, R, L, lda_pad):
+    rng = np.random.default_rng(I + R)
+    npdt = np.float32 if dtype == "f32" else np.float64
+    lda = R + lda_pad
+    Afull = rng.standard_normal((I, lda)).astype(npdt)
+    A = dev(Afull)
+    modified = L < I
+    h, s, ptr, rows = _draw(ctx, 13, I, L, modified)
+    ldy = R + 5
+    Y = torch.full((L, ldy), np.nan, dtype=A.dtype, device="cuda")
+    idl.idl_countsketch_dense(ctx, A, I, R, lda, idl.IDL_F32 if dtype == "f32" else idl.IDL_F64, h, s, ptr, rows,
+                              L, Y, ldy)
+    hw, sw = odr.countsketch_maps(13, I, L, modified)
+    want = ocs.countsketch_dense(Afull[:, :R], hw, sw, L)
+    got = host(Y)[:, :R]
+    tol = FP32_TOL if dtype == "f32" else FP64_TOL
+    assert rel_fro(got, want) <= tol
+    assert np.all(np.isnan(host(Y)[:, R:]))                 # padding untouched
+
+
+# ------------------------------------------------------------------ a4 CSR CountSketch
+@pytest.mark.parametrize("dtype,I,R,L,density", [("f32", 20000, 3000, 300, 0.01), ("f64", 5000, 700, 64, 0.05),
+                                                 ("f32", 100, 60000, 10, 0.01)])
+def test_countsketch_csr_parity(ctx, dtype, I, R, L, density):
+    npdt = np.float32 if dtype == "f32" else np.float64
+    c = random_csr(I, R, density, seed=I, dtype=npdt)
+    # dense rows + duplicate and unsorted columns in the first rows
+    cols = c.colidx.copy()
+    if c.nnz > 8:
+        cols[1] = cols[0]
+        cols[2], cols[3] = cols[3], cols[2]
+    rowptr, vals = c.rowptr, c.vals
+    h, s, ptr, rows = _draw(ctx, 21, I, L, True)
+    ldy = R
+    Y = torch.empty((L, ldy), dtype=torch.float32 if dtype == "f32" else torch.float64, device="cuda")
+    idl.idl_countsketch_csr(ctx, dev(rowptr), dev(cols), dev(vals), I, R, c.nnz,
+                            idl.IDL_F32 if dtype == "f32" else idl.IDL_F64, h, s, ptr, rows, L, Y, ldy)
+    hw, sw = odr.countsketch_maps(21, I, L, True)
+    want = ocs.countsketch_csr(rowptr, cols, vals, R, hw, sw, L)
+    tol = FP32_TOL if dtype == "f32" else FP64_TOL
+    assert rel_fro(host(Y), want) <= tol
+    assert ctx.sync() == idl.IDL_OK
+
+
+def test_countsketch_csr_flags_bad_column(ctx):
+    c = random_csr(1000, 50, 0.1, seed=1)
+    cols = c.colidx.copy()
+    cols[5] = 50          # out of range: skipped and flagged
+    cols[7] = -3
+    h, s, ptr, rows = _draw(ctx, 2, 1000, 20, True)
+    Y = torch.empty((20, 50), dtype=torch.float32, device="cuda")
+    idl.idl_countsketch_csr(ctx, dev(c.rowptr), dev(cols), dev(c.vals), 1000, 50, c.nnz, idl.IDL_F32, h, s, ptr,
+                            rows, 20, Y, 50)
+    assert ctx.sync() == idl.IDL_EDATA
+    keep = np.ones(c.nnz, bool)
+    keep[[5, 7]] = False
+    # reference without the two bad entries
+    rp = np.concatenate([[0], np.cumsum([keep[c.rowptr[i]:c.rowptr[i + 1]].sum() for i in range(1000)])])
+    hw, sw = odr.countsketch_maps(2, 1000, 20, True)
+    want = ocs.countsketch_csr(rp, cols[keep], c.vals[keep], 50, hw, sw, 20)
+    assert rel_fro(host(Y), want) <= FP32_TOL
+    assert ctx.sync() == idl.IDL_OK     # status cleared after it was read
+
+
+# ------------------------------------------------------------------ a6 Gaussian stage
+@pytest.mark.parametrize("prec,m2,m1,R", [(idl.PREC_FP64, 30, 900, 2000), (idl.PREC_FP32, 60, 3600, 1000),
+                                          (idl.PREC_BF16X3, 60, 3600, 1000), (idl.PREC_BF16, 120, 1440, 520),
+                                          (idl.PREC_FP32, 17, 100, 45)])
+def test_gaussian_stage_parity(ctx, prec, m2, m1, R):
+    rng = np.random.default_rng(m1)
+    f64 = prec == idl.PREC_FP64
+    npdt = np.float64 if f64 else np.float32
+    Y1 = rng.standard_normal((m1, R)).astype(npdt)
+    ldy1 = R + 3
+    Y1p = np.zeros((m1, ldy1), npdt)
+    Y1p[:, :R] = Y1
+    Om = torch.empty(m2 * m1, dtype=torch.float64, device="cuda")
+    idl.idl_draw_gaussian(ctx, 3, m2, m1, Om)
+    ldy2 = m2 + 1
+    Y2 = torch.empty(R * ldy2, dtype=torch.float64 if f64 else torch.float32, device="cuda")
+    idl.idl_gaussian_stage(ctx, Om, m2, m1, dev(Y1p), R, ldy1, idl.IDL_F64 if f64 else idl.IDL_F32, prec, Y2, ldy2)
+    want = ogs.gaussian_stage(odr.gaussian_matrix(3, m2, m1), Y1, prec)
+    got = colmajor_to_matrix(Y2, m2, R, ldy2)
+    tol = {idl.PREC_FP64: 1e-12, idl.PREC_FP32: FP32_TOL, idl.PREC_BF16X3: 2e-5, idl.PREC_BF16: 1e-5}[prec]
+    assert rel_fro(got, want) <= tol
+
+
+# ------------------------------------------------------------------ a7/a8 CPQR + T
+@pytest.mark.parametrize("dtype,m,R,K", [("f64", 30, 2000, 20), ("f32", 60, 10000, 50), ("f32", 120, 4096, 100),
+                                         ("f32", 60, 1000, 50), ("f64", 12, 40, 12), ("f32", 5, 3, 2)])
+def test_cpqr_and_t_parity(ctx, dtype, m, R, K):
+    rng = np.random.default_rng(m * R)
+    npdt = np.float32 if dtype == "f32" else np.float64
+    Y = (rng.standard_normal((m, R)) * rng.uniform(0.2, 5.0, R)[None, :]).astype(npdt)
+    ld = m + 2
+    buf = np.zeros((R, ld), npdt)
+    buf[:, :m] = Y.T
+    Yd = dev(buf)
+    J = torch.empty(K, dtype=torch.int32, device="cuda")
+    rn = torch.empty(K, dtype=torch.float64, device="cuda")
+    dt = idl.IDL_F32 if dtype == "f32" else idl.IDL_F64
+    idl.idl_cpqr(ctx, Yd, m, R, ld, dt, K, J, rn)
+    Jw, Tw, info = ocp.matrix_id(Y.astype(np.float64), K)
+    Jg = host(J)
+    if pivots_well_separated(info["gaps"]):
+        assert np.array_equal(Jg, Jw)
+    assert len(set(Jg.tolist())) == K and Jg.min() >= 0 and Jg.max() < R
+    assert np.allclose(host(rn), info["norms"][:K] if np.array_equal(Jg, Jw) else host(rn), rtol=1e-4)
+    if K < R:
+        T = torch.empty(K * (R - K), dtype=torch.float64, device="cuda")
+        rest = torch.empty(R - K, dtype=torch.int32, device="cuda")
+        idl.idl_t_solve(ctx, Yd, m, R, ld, dt, K, J, T, rest)
+        Tg = host(T).reshape(K, R - K)
+        restw = np.setdiff1d(np.arange(R), Jg)
+        assert np.array_equal(host(rest), restw)
+        # T is fixed by J: compare with the oracle's least-squares T for the GPU's J
+        Y64 = Y.astype(np.float64)
+        Tl = np.linalg.lstsq(Y64[:, Jg], Y64[:, restw], rcond=None)[0]
+        tol = 1e-9 if dtype == "f64" else 2e-3
+        assert np.abs(Tg - Tl).max() <= tol * max(1.0, np.abs(Tl).max())
+    assert ctx.sync() == idl.IDL_OK
+
+
+def test_cpqr_exact_rank_and_ties(ctx):
+    # duplicated columns (exact ties): the smallest index wins, like the oracle
+    base = np.random.default_rng(0).standard_normal((20, 8))
+    Y = np.concatenate([base, base], axis=1).astype(np.float64)
+    ld = 20
+    Yd = dev(np.ascontiguousarray(Y.T))
+    J = torch.empty(8, dtype=torch.int32, device="cuda")
+    idl.idl_cpqr(ctx, Yd, 20, 16, ld, idl.IDL_F64, 8, J)
+    Jw, _, _ = ocp.matrix_id(Y, 8)
+    assert np.array_equal(host(J), Jw)
+    assert host(J).max() < 8
+
+
+# ------------------------------------------------------------------ a5 TensorSketch + a9 lambda_hat
+@pytest.mark.parametrize("dims,R,L", [((1000, 1000, 1000), 100, 8192), ((6, 5, 4), 5, 16), ((200,) * 4, 51, 1024),
+                                      ((37, 41), 10, 64)])
+def test_tensorsketch_parity(ctx, dims, R, L):
+    facs, lam = cp_factors(dims, R, seed=len(dims) + R)
+    hs, ss = odr.tensorsketch_maps(4, dims, L)
+    want = ots.tensorsketch(facs, lam, hs, ss, L)
+    fd = [dev(np.ascontiguousarray(F.T)) for F in facs]            # (R, I_n): columns contiguous
+    hd = [torch.empty(d, dtype=torch.int32, device="cuda") for d in dims]
+    sd = [torch.empty(d, dtype=torch.int8, device="cuda") for d in dims]
+    for n, d in enumerate(dims):
+        idl.idl_draw_mode(ctx, 4, n, d, L, hd[n], sd[n])
+    ldy = R + 1
+    Y = torch.empty((L, ldy), dtype=torch.float32, device="cuda")
+    idl.idl_tensorsketch(ctx, fd, [d for d in dims], dev(lam), hd, sd, L, Y, ldy)
+    got = host(Y)[:, :R]
+    for r in range(R):       # per column: relative error of each sketched column
+        assert rel_fro(got[:, r], want[:, r]) <= FP32_TOL, r
+
+
+def test_lambda_hat_parity(ctx):
+    rng = np.random.default_rng(3)
+    K, R = 7, 40
+    T = rng.standard_normal((K, R - K))
+    J = rng.choice(R, K, replace=False).astype(np.int32)
+    lam = rng.uniform(0.1, 1, R)
+    out = torch.empty(K, dtype=torch.float64, device="cuda")
+    idl.idl_lambda_hat(ctx, dev(lam), dev(J), dev(T), K, R, out)
+    from oracle.idmethods import lambda_hat
+    assert np.allclose(host(out), lambda_hat(lam, J, T), rtol=1e-14, atol=1e-14)
