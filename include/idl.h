@@ -143,7 +143,7 @@ int idl_countsketch_csr(idl_ctx* ctx, const int64_t* rowptr, const int32_t* coli
  * column (column r at factors[n] + r*ldf[n], ldf[n] >= dims[n]), IDL_F32.
  * lambda: R doubles (device).  hs[n], ss[n]: device maps of mode n (length
  * dims[n]).  Y: L x R row-major FP32 (ldy >= R).  L must be a power of two in
- * [16, 16384]; N <= 8.  The host arrays dims, factors, ldf, hs, ss are read
+ * [16, 8192]; N <= 8.  The host arrays dims, factors, ldf, hs, ss are read
  * during the call only.
  * ------------------------------------------------------------------------- */
 int idl_tensorsketch(idl_ctx* ctx, int N, const int64_t* dims, int64_t R,

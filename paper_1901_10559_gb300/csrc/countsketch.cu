@@ -226,6 +226,8 @@ static int csr_impl(idl_ctx* ctx, const int64_t* rowptr, const int32_t* colidx, 
   const size_t head = csr_smem_header();
   const size_t want = head + sizeof(T) * (size_t)R;
   if (L > 0x7fffffffLL) return fail(ctx, IDL_ELIMIT, "countsketch csr: too many buckets");
+  // a batch of kCsrThreads rows is flattened with int offsets: bound the row width
+  if (R > 4000000) return fail(ctx, IDL_ELIMIT, "countsketch csr: R > 4e6");
   if (want <= (size_t)ctx->smem_optin) {
     auto k = cs_csr_kernel<T, true>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)want);

@@ -119,7 +119,8 @@ cudaError_t launch_draw_mode(cudaStream_t st, uint64_t seed, int n, int64_t In, 
 // ---------------------------------------------------------------------------
 constexpr int kHistSmem = 12288;  // buckets histogrammed in shared memory first
 
-__global__ void bucket_hist_kernel(const int32_t* __restrict__ h, int64_t I, int64_t L, int32_t* __restrict__ cnt) {
+__global__ void bucket_hist_kernel(const int32_t* __restrict__ h, int64_t I, int64_t L, int32_t* __restrict__ cnt,
+                                   int* status) {
   extern __shared__ int32_t sh[];
   const bool local = L <= kHistSmem;
   if (local) {
@@ -127,7 +128,8 @@ __global__ void bucket_hist_kernel(const int32_t* __restrict__ h, int64_t I, int
     __syncthreads();
   }
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < I; i += (int64_t)gridDim.x * blockDim.x) {
-    int b = h[i];
+    const int b = h[i];
+    if (b < 0 || (int64_t)b >= L) { set_status(status, IDL_EDATA); continue; }   // caller-supplied h out of range
     if (local) atomicAdd(&sh[b], 1); else atomicAdd(&cnt[b], 1);
   }
   if (local) {
@@ -175,11 +177,13 @@ __global__ void bucket_scan_kernel(const int32_t* cnt, int64_t L, int32_t* __res
   if (threadIdx.x == 0) ptr[L] = carry;
 }
 
-__global__ void bucket_scatter_kernel(const int32_t* __restrict__ h, int64_t I, int32_t* __restrict__ cursor,
-                                      int32_t* __restrict__ row_list) {
+__global__ void bucket_scatter_kernel(const int32_t* __restrict__ h, int64_t I, int64_t L,
+                                      int32_t* __restrict__ cursor, int32_t* __restrict__ row_list) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= I) return;
-  int pos = atomicAdd(&cursor[h[i]], 1);
+  const int b = h[i];
+  if (b < 0 || (int64_t)b >= L) return;        // flagged by the histogram pass
+  int pos = atomicAdd(&cursor[b], 1);
   row_list[pos] = (int32_t)i;
 }
 
@@ -244,10 +248,10 @@ int launch_bucket_offsets(idl_ctx* ctx, const int32_t* h, int64_t I, int64_t L, 
     if (blocks > 4 * ctx->num_sms) blocks = 4 * ctx->num_sms;
     if (blocks < 1) blocks = 1;
     size_t sm = L <= kHistSmem ? sizeof(int32_t) * (size_t)L : 0;
-    bucket_hist_kernel<<<(unsigned)blocks, threads, sm, st>>>(h, I, L, cursor);
+    bucket_hist_kernel<<<(unsigned)blocks, threads, sm, st>>>(h, I, L, cursor, ctx->d_status);
   }
   bucket_scan_kernel<<<1, 1024, 0, st>>>(cursor, L, bucket_ptr, cursor);
-  if (I > 0) bucket_scatter_kernel<<<(unsigned)cdiv(I, 256), 256, 0, st>>>(h, I, cursor, row_list);
+  if (I > 0) bucket_scatter_kernel<<<(unsigned)cdiv(I, 256), 256, 0, st>>>(h, I, L, cursor, row_list);
   {
     int warps = 8;
     bucket_sort_warp_kernel<<<(unsigned)cdiv(L, warps), warps * 32, sizeof(int32_t) * warps * kWarpSortCap, st>>>(

@@ -84,7 +84,9 @@ __global__ void __launch_bounds__(kTsThreads, 1) tensorsketch_kernel(TsArgs a, i
     const float* f1 = f0 + a.ldf[n];
     const int In = a.dims[n];
     for (int i = threadIdx.x; i < In; i += blockDim.x) {
-      const int pos = (int)(__brev((unsigned)a.h[n][i]) >> shift);
+      const unsigned hv = (unsigned)a.h[n][i];
+      if (hv >= (unsigned)L) continue;               // caller-supplied map out of range: entry skipped
+      const int pos = (int)(__brev(hv) >> shift);
       const float sg = a.s[n][i] < 0 ? -1.f : 1.f;
       atomicAdd(&z[pos].x, sg * f0[i]);
       if (two) atomicAdd(&z[pos].y, sg * f1[i]);
