@@ -92,6 +92,22 @@ const char* idl_last_error(idl_ctx* ctx);
 int idl_version(void);
 
 /* ---------------------------------------------------------------------------
+ * Instrumentation (the paper averages wall time over runs, Sec. 6; this adds
+ * device-side timing per stage).
+ *   idl_launch_count: kernels this library has launched in the process so far.
+ *   idl_profile: on != 0 makes every pipeline call record a CUDA event pair on
+ *     the context's stream around each stage.
+ *   idl_profile_read: waits for the stream, writes per-stage milliseconds summed
+ *     over the calls since the last read (ms[0..nstages)) and how many pairs were
+ *     summed (calls, may be NULL), then clears.  Stages: 0 draws, 1 bucket
+ *     offsets, 2 sketch (CountSketch / TensorSketch), 3 Gaussian stage, 4 pivoted
+ *     QR, 5 T solve, 6 checks (explicit residual, lambda_hat), 7 host->device copies.
+ * ------------------------------------------------------------------------- */
+long long idl_launch_count(void);
+int idl_profile(idl_ctx* ctx, int on);
+int idl_profile_read(idl_ctx* ctx, double* ms, long long* calls, int nstages);
+
+/* ---------------------------------------------------------------------------
  * Draws (Sec. 1.3; Remark 2 and Sec. 7.2; Sec. 1.2.1).  Counter-based:
  *   u(seed, tag, i) = mix64(mix64(seed ^ tag*0xD1B54A32D192ED03) + (i+1)*0x9E3779B97F4A7C15)
  *   (mix64 = the SplitMix64 finaliser).  bounded(u, L) = (u*L) >> 64.

@@ -24,6 +24,7 @@ HEADER = os.path.join(os.path.dirname(_HERE), "include", "idl.h")
 IDL_OK, IDL_EINVAL, IDL_ENOMEM, IDL_ECUDA, IDL_ERANK, IDL_ETIMEOUT, IDL_EDATA, IDL_ELIMIT = range(8)
 IDL_F32, IDL_F64 = 0, 1
 PREC_FP64, PREC_FP32, PREC_BF16X3, PREC_BF16 = 0, 1, 2, 3
+STAGES = ("draws", "buckets", "sketch", "gaussian", "cpqr", "tsolve", "check", "copy")
 STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ERANK", 5: "ETIMEOUT", 6: "EDATA", 7: "ELIMIT"}
 
 
@@ -58,6 +59,9 @@ _SIGS = {
     "idl_set_stream": ([_vp, _vp], _int),
     "idl_sync": ([_vp], _int),
     "idl_last_error": ([_vp], ctypes.c_char_p),
+    "idl_launch_count": ([], ctypes.c_longlong),
+    "idl_profile": ([_vp, _int], _int),
+    "idl_profile_read": ([_vp, _vp, _vp, _int], _int),
     "idl_debug_fail_alloc": ([_vp, _int], _int),
     "idl_debug_release_workspace": ([_vp], _int),
     "idl_draw_countsketch": ([_vp, _u64, _i64, _i64, _int, _vp, _vp], _int),
@@ -139,6 +143,16 @@ class Context:
     def sync(self):
         return lib().idl_sync(self.ptr)
 
+    def profile(self, on: bool):
+        self.check(lib().idl_profile(self.ptr, int(on)))
+
+    def profile_read(self):
+        """Per-stage device milliseconds and event-pair counts since the last read."""
+        ms = (ctypes.c_double * len(STAGES))()
+        n = (ctypes.c_longlong * len(STAGES))()
+        self.check(lib().idl_profile_read(self.ptr, ctypes.cast(ms, _vp), ctypes.cast(n, _vp), len(STAGES)))
+        return {name: (ms[i], n[i]) for i, name in enumerate(STAGES)}
+
     def close(self):
         if self.ptr:
             lib().idl_destroy(self.ptr)
@@ -149,6 +163,11 @@ class Context:
             self.close()
         except Exception:
             pass
+
+
+def launch_count() -> int:
+    """Kernels the library has launched in this process."""
+    return int(lib().idl_launch_count())
 
 
 def make_params(m1, m2, seed, modified=True, precision=PREC_FP32, residual=1):

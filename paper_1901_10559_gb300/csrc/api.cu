@@ -11,12 +11,17 @@
 #include <limits>
 #include <string>
 
+#include <atomic>
+
 #include "common.cuh"
 #include "internal.h"
 
 using namespace idl;
 
 namespace idl {
+
+static std::atomic<long long> g_launches{0};
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
 int fail(idl_ctx* ctx, int code, const std::string& msg) {
   if (ctx) ctx->err = msg;
@@ -71,6 +76,35 @@ void* ws_get(idl_ctx* ctx, int slot, size_t bytes) {
   type* ptr = (type*)ws_get(ctx, slot, sizeof(type) * (size_t)(count));       \
   if (!ptr) return IDL_ENOMEM
 
+// ---- per-stage event profiling ----
+enum { kStDraw = 0, kStBucket, kStSketch, kStGauss, kStQR, kStSolve, kStCheck, kStCopy, kStCount };
+
+static int prof_begin(idl_ctx* ctx, int stage) {
+  if (!ctx->prof_on) return -1;
+  if (ctx->prof_used == ctx->prof.size()) {
+    idl_ctx::ProfPair pp;
+    if (cudaEventCreate(&pp.a) != cudaSuccess || cudaEventCreate(&pp.b) != cudaSuccess) {
+      (void)cudaGetLastError();
+      return -1;
+    }
+    ctx->prof.push_back(pp);
+  }
+  idl_ctx::ProfPair& pp = ctx->prof[ctx->prof_used];
+  pp.stage = stage;
+  cudaEventRecord(pp.a, ctx->stream);
+  return (int)ctx->prof_used++;
+}
+static void prof_end(idl_ctx* ctx, int idx) {
+  if (idx >= 0) cudaEventRecord(ctx->prof[idx].b, ctx->stream);
+}
+#define STAGE(stage, expr)                  \
+  do {                                      \
+    int _pi = prof_begin(ctx, stage);       \
+    int _rc = (expr);                       \
+    prof_end(ctx, _pi);                     \
+    if (_rc != IDL_OK) return _rc;          \
+  } while (0)
+
 static bool is_device_ptr(const void* p) {
   if (!p) return false;
   cudaPointerAttributes a;
@@ -95,7 +129,9 @@ static const void* stage_in(idl_ctx* ctx, const void* p, size_t bytes, int slot,
   if (is_device_ptr(p)) return p;
   void* d = ws_get(ctx, slot, bytes);
   if (!d) { *rc = IDL_ENOMEM; return nullptr; }
+  const int pi = prof_begin(ctx, kStCopy);
   *rc = cuda_check(ctx, cudaMemcpyAsync(d, p, bytes, cudaMemcpyHostToDevice, ctx->stream), "copy in");
+  prof_end(ctx, pi);
   return d;
 }
 
@@ -168,6 +204,7 @@ extern "C" int idl_destroy(idl_ctx* ctx) {
   cudaStreamSynchronize(ctx->stream);
   for (auto& b : ctx->slots)
     if (b.p) cudaFree(b.p);
+  for (auto& pp : ctx->prof) { cudaEventDestroy(pp.a); cudaEventDestroy(pp.b); }
   cudaFree(ctx->d_status);
   cudaFree(ctx->d_diag);
   delete ctx;
@@ -194,6 +231,29 @@ extern "C" int idl_sync(idl_ctx* ctx) {
 }
 
 extern "C" const char* idl_last_error(idl_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+extern "C" long long idl_launch_count(void) { return g_launches.load(); }
+
+extern "C" int idl_profile(idl_ctx* ctx, int on) {
+  if (!ctx) return IDL_EINVAL;
+  ctx->prof_on = on != 0;
+  return IDL_OK;
+}
+
+extern "C" int idl_profile_read(idl_ctx* ctx, double* ms, long long* calls, int nstages) {
+  TRY(check_ctx(ctx));
+  if (!ms || nstages < 1) return fail(ctx, IDL_EINVAL, "profile_read: bad arguments");
+  TRY(cuda_check(ctx, cudaStreamSynchronize(ctx->stream), "profile sync"));
+  for (int q = 0; q < nstages; ++q) { ms[q] = 0.0; if (calls) calls[q] = 0; }
+  for (size_t i = 0; i < ctx->prof_used; ++i) {
+    const idl_ctx::ProfPair& pp = ctx->prof[i];
+    float t = 0.f;
+    if (cudaEventElapsedTime(&t, pp.a, pp.b) != cudaSuccess) { (void)cudaGetLastError(); continue; }
+    if (pp.stage < nstages) { ms[pp.stage] += t; if (calls) calls[pp.stage] += 1; }
+  }
+  ctx->prof_used = 0;
+  return IDL_OK;
+}
 
 // test hook (not in the public header): fail the n-th workspace allocation from now
 extern "C" int idl_debug_fail_alloc(idl_ctx* ctx, int nth) {
@@ -349,10 +409,10 @@ static int finish_pipeline(idl_ctx* ctx, const idl_params* p, int dtype, void* Y
   if (!Y2) return IDL_ENOMEM;
   if (p->m2 > 0) {
     WS(Om, double, kWsOmega, p->m2 * p->m1);
-    TRY(cuda_check(ctx, launch_draw_gaussian(ctx->stream, p->seed, p->m2, p->m1, Om), "draw gaussian"));
-    TRY(launch_gaussian(ctx, Om, p->m2, p->m1, Y1, R, ldy1, dtype, p->precision, Y2, ld2));
+    STAGE(kStDraw, cuda_check(ctx, launch_draw_gaussian(ctx->stream, p->seed, p->m2, p->m1, Om), "draw gaussian"));
+    STAGE(kStGauss, launch_gaussian(ctx, Om, p->m2, p->m1, Y1, R, ldy1, dtype, p->precision, Y2, ld2));
   } else {
-    TRY(launch_transpose_to_colmajor(ctx, Y1, m, R, ldy1, dtype, Y2, ld2));
+    STAGE(kStGauss, launch_transpose_to_colmajor(ctx, Y1, m, R, ldy1, dtype, Y2, ld2));
   }
   void* Yf = Y2;
   if (keep_orig) {
@@ -366,9 +426,9 @@ static int finish_pipeline(idl_ctx* ctx, const idl_params* p, int dtype, void* Y
   if (!tdev) { Td = (double*)ws_get(ctx, kWsT, sizeof(double) * (size_t)(K * (R - K))); if (!Td) return IDL_ENOMEM; }
   WS(rest, int32_t, kWsRest, R);
   TRY(clear_diag(ctx));
-  TRY(launch_cpqr(ctx, Yf, m, R, ld2, dtype, K, Jd, nullptr));
-  TRY(launch_t_solve(ctx, Yf, m, R, ld2, dtype, K, Jd, Td, rest));
-  if (keep_orig) TRY(launch_residual(ctx, Y2, Yf, m, R, ld2, dtype, K, Jd, Td, rest));
+  STAGE(kStQR, launch_cpqr(ctx, Yf, m, R, ld2, dtype, K, Jd, nullptr));
+  STAGE(kStSolve, launch_t_solve(ctx, Yf, m, R, ld2, dtype, K, Jd, Td, rest));
+  if (keep_orig) STAGE(kStCheck, launch_residual(ctx, Y2, Yf, m, R, ld2, dtype, K, Jd, Td, rest));
   if (!jdev)
     TRY(cuda_check(ctx, cudaMemcpyAsync(J, Jd, sizeof(int32_t) * K, cudaMemcpyDeviceToHost, ctx->stream), "copy J"));
   if (!tdev)
@@ -396,10 +456,10 @@ extern "C" int id_matrix(idl_ctx* ctx, const void* A, int64_t I, int64_t R, int6
   const int64_t ldy1 = round_up(R, 32);
   void* Y1 = ws_get(ctx, kWsY1, (size_t)es * (size_t)(m1 * ldy1));
   if (!Y1) return IDL_ENOMEM;
-  TRY(cuda_check(ctx, launch_draw_countsketch(ctx->stream, p->seed, I, m1, p->modified, h, s, ctx->d_status),
-                 "draw countsketch"));
-  TRY(launch_bucket_offsets(ctx, h, I, m1, ptr, rows));
-  TRY(launch_countsketch_dense(ctx, Ad, I, R, lda, dtype, s, ptr, rows, m1, Y1, ldy1));
+  STAGE(kStDraw, cuda_check(ctx, launch_draw_countsketch(ctx->stream, p->seed, I, m1, p->modified, h, s,
+                                                         ctx->d_status), "draw countsketch"));
+  STAGE(kStBucket, launch_bucket_offsets(ctx, h, I, m1, ptr, rows));
+  STAGE(kStSketch, launch_countsketch_dense(ctx, Ad, I, R, lda, dtype, s, ptr, rows, m1, Y1, ldy1));
   return finish_pipeline(ctx, p, dtype, Y1, ldy1, R, K, J, T, info);
 }
 
@@ -427,10 +487,10 @@ extern "C" int id_matrix_csr(idl_ctx* ctx, const int64_t* rowptr, const int32_t*
   const int64_t ldy1 = round_up(R, 32);
   void* Y1 = ws_get(ctx, kWsY1, (size_t)es * (size_t)(m1 * ldy1));
   if (!Y1) return IDL_ENOMEM;
-  TRY(cuda_check(ctx, launch_draw_countsketch(ctx->stream, p->seed, I, m1, p->modified, h, s, ctx->d_status),
-                 "draw countsketch"));
-  TRY(launch_bucket_offsets(ctx, h, I, m1, ptr, rows));
-  TRY(launch_countsketch_csr(ctx, rp, ci, vv, I, R, nnz, dtype, s, ptr, rows, m1, Y1, ldy1));
+  STAGE(kStDraw, cuda_check(ctx, launch_draw_countsketch(ctx->stream, p->seed, I, m1, p->modified, h, s,
+                                                         ctx->d_status), "draw countsketch"));
+  STAGE(kStBucket, launch_bucket_offsets(ctx, h, I, m1, ptr, rows));
+  STAGE(kStSketch, launch_countsketch_csr(ctx, rp, ci, vv, I, R, nnz, dtype, s, ptr, rows, m1, Y1, ldy1));
   return finish_pipeline(ctx, p, dtype, Y1, ldy1, R, K, J, T, info);
 }
 
@@ -458,7 +518,8 @@ extern "C" int id_cp_tensor(idl_ctx* ctx, int N, const int64_t* dims, int64_t R,
   const int8_t* ss[8];
   int64_t off = 0;
   for (int n = 0; n < N; ++n) {
-    TRY(cuda_check(ctx, launch_draw_mode(ctx->stream, p->seed, n, dims[n], L, hbuf + off, sbuf + off), "draw mode"));
+    STAGE(kStDraw, cuda_check(ctx, launch_draw_mode(ctx->stream, p->seed, n, dims[n], L, hbuf + off, sbuf + off),
+                              "draw mode"));
     hs[n] = hbuf + off;
     ss[n] = sbuf + off;
     off += dims[n];
@@ -466,7 +527,7 @@ extern "C" int id_cp_tensor(idl_ctx* ctx, int N, const int64_t* dims, int64_t R,
   const int64_t ldy1 = round_up(R, 32);
   float* Y1 = (float*)ws_get(ctx, kWsY1, sizeof(float) * (size_t)(L * ldy1));
   if (!Y1) return IDL_ENOMEM;
-  TRY(launch_tensorsketch(ctx, N, dims, R, factors, ldf, lam, hs, ss, L, Y1, ldy1));
+  STAGE(kStSketch, launch_tensorsketch(ctx, N, dims, R, factors, ldf, lam, hs, ss, L, Y1, ldy1));
   // J and T on the device for lambda_hat; staged back if the caller passed host pointers
   const bool jdev = is_device_ptr(J), tdev = is_device_ptr(T), ldev = is_device_ptr(lambda_hat);
   int32_t* Jd = J;
@@ -476,7 +537,7 @@ extern "C" int id_cp_tensor(idl_ctx* ctx, int N, const int64_t* dims, int64_t R,
   TRY(finish_pipeline(ctx, p, IDL_F32, Y1, ldy1, R, K, Jd, Td, nullptr));
   double* lhd = lambda_hat;
   if (!ldev) { lhd = (double*)ws_get(ctx, kWsLamHat, sizeof(double) * (size_t)K); if (!lhd) return IDL_ENOMEM; }
-  TRY(launch_lambda_hat(ctx, lam, Jd, Td, K, R, lhd));
+  STAGE(kStCheck, launch_lambda_hat(ctx, lam, Jd, Td, K, R, lhd));
   if (!jdev) TRY(cuda_check(ctx, cudaMemcpyAsync(J, Jd, sizeof(int32_t) * K, cudaMemcpyDeviceToHost, ctx->stream), "J"));
   if (!tdev)
     TRY(cuda_check(ctx, cudaMemcpyAsync(T, Td, sizeof(double) * K * (R - K), cudaMemcpyDeviceToHost, ctx->stream), "T"));

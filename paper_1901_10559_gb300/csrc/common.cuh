@@ -8,6 +8,9 @@
 
 namespace idl {
 
+// Process-wide count of kernel launches made by this library (idl_launch_count).
+void count_launch();
+
 // ----------------------------------------------------------------------------
 // Status word: kernels record the first error they see (atomicCAS from OK).
 // ----------------------------------------------------------------------------

@@ -103,9 +103,9 @@ static int dense_impl(idl_ctx* ctx, const T* A, int64_t R, int64_t lda, const in
   const bool vec = ((uintptr_t)A % 16 == 0) && ((uintptr_t)Y % 16 == 0) && ((lda * sizeof(T)) % 16 == 0) &&
                    ((ldy * sizeof(T)) % 16 == 0);
   if (vec)
-    cs_dense_kernel<T, true><<<(unsigned)blocks, threads, 0, ctx->stream>>>(A, lda, R, s, ptr, rows, Y, ldy, ntiles);
+    cs_dense_kernel<T, true><<<(unsigned)blocks, threads, 0, ctx->stream>>>(A, lda, R, s, ptr, rows, Y, ldy, ntiles), idl::count_launch();
   else
-    cs_dense_kernel<T, false><<<(unsigned)blocks, threads, 0, ctx->stream>>>(A, lda, R, s, ptr, rows, Y, ldy, ntiles);
+    cs_dense_kernel<T, false><<<(unsigned)blocks, threads, 0, ctx->stream>>>(A, lda, R, s, ptr, rows, Y, ldy, ntiles), idl::count_launch();
   return cuda_check(ctx, cudaGetLastError(), "countsketch dense");
 }
 
@@ -233,12 +233,12 @@ static int csr_impl(idl_ctx* ctx, const int64_t* rowptr, const int32_t* colidx, 
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)want);
     if (e != cudaSuccess) return cuda_check(ctx, e, "csr smem attribute");
     k<<<(unsigned)L, kCsrThreads, want, ctx->stream>>>(rowptr, colidx, vals, R, nnz, s, ptr, rows, Y, ldy,
-                                                       ctx->d_status);
+                                                       ctx->d_status), idl::count_launch();
   } else {
     cudaError_t e = cudaMemset2DAsync(Y, ldy * sizeof(T), 0, R * sizeof(T), L, ctx->stream);
     if (e != cudaSuccess) return cuda_check(ctx, e, "csr zero");
     cs_csr_kernel<T, false><<<(unsigned)L, kCsrThreads, head, ctx->stream>>>(rowptr, colidx, vals, R, nnz, s, ptr,
-                                                                              rows, Y, ldy, ctx->d_status);
+                                                                              rows, Y, ldy, ctx->d_status), idl::count_launch();
   }
   return cuda_check(ctx, cudaGetLastError(), "countsketch csr");
 }

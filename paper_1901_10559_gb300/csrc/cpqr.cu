@@ -267,6 +267,7 @@ static int cpqr_impl(idl_ctx* ctx, const T* Yin, T* Yout, int64_t m, int64_t R, 
     ctx->last_cluster = CS;
     e = cudaLaunchKernelEx(&cfg, kern, Yin, Yout, (int)m, (int)R, (int)ld, (int)K, nc, lds, tpc, J, rnorm,
                            ctx->d_diag, ctx->d_status);
+    idl::count_launch();
     return cuda_check(ctx, e, "cpqr launch");
   }
   return fail(ctx, IDL_ELIMIT, "cpqr: no cluster shape fits this device");
@@ -349,7 +350,7 @@ int launch_t_solve(idl_ctx* ctx, const void* Y2, int64_t m, int64_t R, int64_t l
     rest = (int32_t*)ws_get(ctx, kWsRest, sizeof(int32_t) * (size_t)(R > 0 ? R : 1));
     if (!rest) return IDL_ENOMEM;
   }
-  rest_kernel<<<(unsigned)cdiv(R, 256), 256, sizeof(int32_t) * (size_t)K, ctx->stream>>>(J, (int)K, (int)R, rest);
+  rest_kernel<<<(unsigned)cdiv(R, 256), 256, sizeof(int32_t) * (size_t)K, ctx->stream>>>(J, (int)K, (int)R, rest), idl::count_launch();
   if (nrest <= 0) return cuda_check(ctx, cudaGetLastError(), "rest");
   const size_t smem = sizeof(double) * ((size_t)K * (K + 1) + (size_t)K * kSolveNB);
   cudaError_t e;
@@ -357,12 +358,12 @@ int launch_t_solve(idl_ctx* ctx, const void* Y2, int64_t m, int64_t R, int64_t l
     e = cudaFuncSetAttribute(tsolve_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e == cudaSuccess)
       tsolve_kernel<float><<<(unsigned)cdiv(nrest, kSolveNB), 256, smem, ctx->stream>>>(
-          (const float*)Y2, (int)ld, (int)K, (int)R, J, rest, (int)nrest, T);
+          (const float*)Y2, (int)ld, (int)K, (int)R, J, rest, (int)nrest, T), idl::count_launch();
   } else {
     e = cudaFuncSetAttribute(tsolve_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e == cudaSuccess)
       tsolve_kernel<double><<<(unsigned)cdiv(nrest, kSolveNB), 256, smem, ctx->stream>>>(
-          (const double*)Y2, (int)ld, (int)K, (int)R, J, rest, (int)nrest, T);
+          (const double*)Y2, (int)ld, (int)K, (int)R, J, rest, (int)nrest, T), idl::count_launch();
   }
   if (e != cudaSuccess) return cuda_check(ctx, e, "t_solve attribute");
   return cuda_check(ctx, cudaGetLastError(), "t_solve");
@@ -413,12 +414,12 @@ int launch_residual(idl_ctx* ctx, const void* Y2orig, const void* Y2fact, int64_
     e = cudaFuncSetAttribute(residual_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e == cudaSuccess)
       residual_kernel<float><<<blocks, 256, smem, ctx->stream>>>((const float*)Y2orig, (int)m, (int)ld, (int)K, (int)R, J, T,
-                                                                 rest, (int)nrest, ctx->d_diag);
+                                                                 rest, (int)nrest, ctx->d_diag), idl::count_launch();
   } else {
     e = cudaFuncSetAttribute(residual_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e == cudaSuccess)
       residual_kernel<double><<<blocks, 256, smem, ctx->stream>>>((const double*)Y2orig, (int)m, (int)ld, (int)K, (int)R, J,
-                                                                  T, rest, (int)nrest, ctx->d_diag);
+                                                                  T, rest, (int)nrest, ctx->d_diag), idl::count_launch();
   }
   if (e != cudaSuccess) return cuda_check(ctx, e, "residual attribute");
   return cuda_check(ctx, cudaGetLastError(), "residual");
@@ -449,7 +450,7 @@ __global__ void lambda_hat_kernel(const double* __restrict__ lam, const int32_t*
 int launch_lambda_hat(idl_ctx* ctx, const double* lambda, const int32_t* J, const double* T, int64_t K, int64_t R,
                       double* lambda_hat) {
   if (K <= 0) return IDL_OK;
-  lambda_hat_kernel<<<(unsigned)K, 256, 0, ctx->stream>>>(lambda, J, T, (int)(R - K), lambda_hat);
+  lambda_hat_kernel<<<(unsigned)K, 256, 0, ctx->stream>>>(lambda, J, T, (int)(R - K), lambda_hat), idl::count_launch();
   return cuda_check(ctx, cudaGetLastError(), "lambda_hat");
 }
 
@@ -477,9 +478,9 @@ int launch_transpose_to_colmajor(idl_ctx* ctx, const void* Y1, int64_t m, int64_
   dim3 grid((unsigned)cdiv(R, 32), (unsigned)cdiv(m, 32));
   dim3 block(32, 8);
   if (dtype == IDL_F32)
-    transpose_kernel<float><<<grid, block, 0, ctx->stream>>>((const float*)Y1, m, R, ldy1, (float*)Y2, ldy2);
+    transpose_kernel<float><<<grid, block, 0, ctx->stream>>>((const float*)Y1, m, R, ldy1, (float*)Y2, ldy2), idl::count_launch();
   else
-    transpose_kernel<double><<<grid, block, 0, ctx->stream>>>((const double*)Y1, m, R, ldy1, (double*)Y2, ldy2);
+    transpose_kernel<double><<<grid, block, 0, ctx->stream>>>((const double*)Y1, m, R, ldy1, (double*)Y2, ldy2), idl::count_launch();
   return cuda_check(ctx, cudaGetLastError(), "transpose");
 }
 

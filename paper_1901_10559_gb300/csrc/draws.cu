@@ -72,7 +72,7 @@ cudaError_t launch_draw_countsketch(cudaStream_t st, uint64_t seed, int64_t I, i
   int threads = 256;
   int64_t blocks = cdiv(I, threads);
   draw_countsketch_kernel<<<(unsigned)blocks, threads, 0, st>>>(
-      stream_base(seed, kTagBucket), stream_base(seed, kTagSign), I, L, modified, half, mask, keys, h, s, status);
+      stream_base(seed, kTagBucket), stream_base(seed, kTagSign), I, L, modified, half, mask, keys, h, s, status), idl::count_launch();
   return cudaGetLastError();
 }
 
@@ -93,7 +93,7 @@ cudaError_t launch_draw_gaussian(cudaStream_t st, uint64_t seed, int64_t m2, int
   int64_t n = m2 * m1;
   if (n <= 0) return cudaSuccess;
   int threads = 256;
-  draw_gaussian_kernel<<<(unsigned)cdiv(n, threads), threads, 0, st>>>(stream_base(seed, kTagGauss), n, Omega);
+  draw_gaussian_kernel<<<(unsigned)cdiv(n, threads), threads, 0, st>>>(stream_base(seed, kTagGauss), n, Omega), idl::count_launch();
   return cudaGetLastError();
 }
 
@@ -110,7 +110,7 @@ cudaError_t launch_draw_mode(cudaStream_t st, uint64_t seed, int n, int64_t In, 
   if (In <= 0) return cudaSuccess;
   int threads = 256;
   draw_mode_kernel<<<(unsigned)cdiv(In, threads), threads, 0, st>>>(
-      stream_base(seed, kTagModeBucket + n), stream_base(seed, kTagModeSign + n), In, L, h, s);
+      stream_base(seed, kTagModeBucket + n), stream_base(seed, kTagModeSign + n), In, L, h, s), idl::count_launch();
   return cudaGetLastError();
 }
 
@@ -248,15 +248,15 @@ int launch_bucket_offsets(idl_ctx* ctx, const int32_t* h, int64_t I, int64_t L, 
     if (blocks > 4 * ctx->num_sms) blocks = 4 * ctx->num_sms;
     if (blocks < 1) blocks = 1;
     size_t sm = L <= kHistSmem ? sizeof(int32_t) * (size_t)L : 0;
-    bucket_hist_kernel<<<(unsigned)blocks, threads, sm, st>>>(h, I, L, cursor, ctx->d_status);
+    bucket_hist_kernel<<<(unsigned)blocks, threads, sm, st>>>(h, I, L, cursor, ctx->d_status), idl::count_launch();
   }
-  bucket_scan_kernel<<<1, 1024, 0, st>>>(cursor, L, bucket_ptr, cursor);
-  if (I > 0) bucket_scatter_kernel<<<(unsigned)cdiv(I, 256), 256, 0, st>>>(h, I, L, cursor, row_list);
+  bucket_scan_kernel<<<1, 1024, 0, st>>>(cursor, L, bucket_ptr, cursor), idl::count_launch();
+  if (I > 0) bucket_scatter_kernel<<<(unsigned)cdiv(I, 256), 256, 0, st>>>(h, I, L, cursor, row_list), idl::count_launch();
   {
     int warps = 8;
     bucket_sort_warp_kernel<<<(unsigned)cdiv(L, warps), warps * 32, sizeof(int32_t) * warps * kWarpSortCap, st>>>(
-        bucket_ptr, L, row_list, big, nbig);
-    bucket_sort_block_kernel<<<64, 512, sizeof(int32_t) * kBlockSortCap, st>>>(bucket_ptr, row_list, big, nbig);
+        bucket_ptr, L, row_list, big, nbig), idl::count_launch();
+    bucket_sort_block_kernel<<<64, 512, sizeof(int32_t) * kBlockSortCap, st>>>(bucket_ptr, row_list, big, nbig), idl::count_launch();
   }
   return cuda_check(ctx, cudaGetLastError(), "bucket offsets");
 }

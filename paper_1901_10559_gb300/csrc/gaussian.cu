@@ -101,7 +101,7 @@ template <typename T, int MQ>
 static void launch_simt(idl_ctx* ctx, const T* Om, int m2, int64_t m1, const T* Y1, int64_t R, int64_t ldy1,
                         T* part, int splits, int64_t kchunk, int MP, int rbf16) {
   dim3 grid((unsigned)cdiv(R, kGBN), (unsigned)splits);
-  gauss_simt_kernel<T, MQ><<<grid, kGThreads, 0, ctx->stream>>>(Om, m2, m1, Y1, R, ldy1, kchunk, part, MP, rbf16);
+  gauss_simt_kernel<T, MQ><<<grid, kGThreads, 0, ctx->stream>>>(Om, m2, m1, Y1, R, ldy1, kchunk, part, MP, rbf16), idl::count_launch();
 }
 
 template <typename T>
@@ -131,7 +131,7 @@ static int simt_impl(idl_ctx* ctx, const T* Om, int64_t m2, int64_t m1, const T*
     default: return fail(ctx, IDL_ELIMIT, "gaussian: m2 > 256");
   }
   const int64_t n = R * m2;
-  gauss_reduce_kernel<T><<<(unsigned)cdiv(n, 256), 256, 0, ctx->stream>>>(part, (int)splits, R, MP, (int)m2, Y2, ldy2);
+  gauss_reduce_kernel<T><<<(unsigned)cdiv(n, 256), 256, 0, ctx->stream>>>(part, (int)splits, R, MP, (int)m2, Y2, ldy2), idl::count_launch();
   return cuda_check(ctx, cudaGetLastError(), "gaussian simt");
 }
 
@@ -142,7 +142,7 @@ int launch_gaussian(idl_ctx* ctx, const double* Omega, int64_t m2, int64_t m1, c
     return simt_impl<double>(ctx, Omega, m2, m1, (const double*)Y1, R, ldy1, (double*)Y2, ldy2, 0);
   float* om32 = (float*)ws_get(ctx, kWsOmegaConv, sizeof(float) * (size_t)(m2 * m1));
   if (!om32) return IDL_ENOMEM;
-  omega_to_f32_kernel<<<(unsigned)cdiv(m2 * m1, 256), 256, 0, ctx->stream>>>(Omega, m2 * m1, om32);
+  omega_to_f32_kernel<<<(unsigned)cdiv(m2 * m1, 256), 256, 0, ctx->stream>>>(Omega, m2 * m1, om32), idl::count_launch();
   return simt_impl<float>(ctx, om32, m2, m1, (const float*)Y1, R, ldy1, (float*)Y2, ldy2,
                           precision == IDL_PREC_BF16 ? 1 : 0);
 }

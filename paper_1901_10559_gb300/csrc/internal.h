@@ -23,6 +23,11 @@ struct idl_ctx {
   int last_cluster = 0;
   size_t fail_alloc_at = 0;    // test hook: fail the n-th workspace allocation (0 = never)
   size_t alloc_count = 0;
+  // per-stage CUDA-event profiling (idl_profile / idl_profile_read)
+  bool prof_on = false;
+  struct ProfPair { cudaEvent_t a = nullptr, b = nullptr; int stage = 0; };
+  std::vector<ProfPair> prof;
+  size_t prof_used = 0;
 };
 
 namespace idl {

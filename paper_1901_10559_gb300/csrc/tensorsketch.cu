@@ -141,7 +141,7 @@ int launch_tensorsketch(idl_ctx* ctx, int N, const int64_t* dims, int64_t R, con
   const size_t smem = sizeof(float2) * (size_t)(2 * L + 2 * (L / 2 + 1));
   cudaError_t e = cudaFuncSetAttribute(tensorsketch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return cuda_check(ctx, e, "tensorsketch attribute");
-  tensorsketch_kernel<<<(unsigned)cdiv(R, 2), kTsThreads, smem, ctx->stream>>>(a, R, (int)L, logL, lambda, Y, ldy);
+  tensorsketch_kernel<<<(unsigned)cdiv(R, 2), kTsThreads, smem, ctx->stream>>>(a, R, (int)L, logL, lambda, Y, ldy), idl::count_launch();
   return cuda_check(ctx, cudaGetLastError(), "tensorsketch");
 }
 
