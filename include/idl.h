@@ -134,6 +134,34 @@ int idl_bucket_offsets(idl_ctx* ctx, const int32_t* h, int64_t I, int64_t L,
                        int32_t* bucket_ptr, int32_t* row_list);
 
 /* ---------------------------------------------------------------------------
+ * Allocation-free bucket offsets.  The paper has no counterpart: this is a
+ * service for callers that cannot allocate device memory when they need the
+ * offsets -- code running while a stream is captured into a CUDA graph, code
+ * under a memory budget that forbids allocations after start-up, or a
+ * real-time loop that cannot afford a blocking cudaMalloc.  It computes the
+ * same bucket_ptr / row_list as idl_bucket_offsets, but needs no context and
+ * calls no cudaMalloc, cudaFree or allocating library routine: its scratch is
+ * a fixed array of (2 * IDL_NOALLOC_MAX_BUCKETS + 6) int32 words (about
+ * 512 KB) in the library's own device memory, which every GPU that loads the
+ * library holds until the process exits.
+ *   stream: cudaStream_t to launch on (NULL = legacy default stream); the
+ *           device is the current device.  h, bucket_ptr, row_list as for
+ *           idl_bucket_offsets (device pointers).
+ *   Returns IDL_ELIMIT if L > IDL_NOALLOC_MAX_BUCKETS, IDL_EINVAL for bad
+ *   sizes or null pointers, IDL_ECUDA on a CUDA error.
+ *   The first call on each device looks up the scratch array's device address
+ *   (cudaGetSymbolAddress, with that device current); make that first call
+ *   before any stream capture.
+ *   All calls on a device share the one scratch array and each call clears
+ *   the parts that must start at zero, so calls that overlap on the GPU (on
+ *   different streams or from different threads) race: serialise them.
+ *   Entries of h outside [0, L) are skipped; then bucket_ptr[L] < I.
+ * ------------------------------------------------------------------------- */
+#define IDL_NOALLOC_MAX_BUCKETS 65536
+int idl_bucket_offsets_noalloc(void* stream, const int32_t* h, int64_t I, int64_t L,
+                               int32_t* bucket_ptr, int32_t* row_list);
+
+/* ---------------------------------------------------------------------------
  * CountSketch Y1 = S A (Sec. 1.3; Algorithm 2 line 4), as a segmented
  * reduction over the bucket offsets: Y1[b, :] = sum over rows i of bucket b of
  * s[i] * A[i, :].  A: I x R row-major (lda >= R), dtype IDL_F32 or IDL_F64;

@@ -68,6 +68,7 @@ _SIGS = {
     "idl_draw_gaussian": ([_vp, _u64, _i64, _i64, _vp], _int),
     "idl_draw_mode": ([_vp, _u64, _int, _i64, _i64, _vp, _vp], _int),
     "idl_bucket_offsets": ([_vp, _vp, _i64, _i64, _vp, _vp], _int),
+    "idl_bucket_offsets_noalloc": ([_vp, _vp, _i64, _i64, _vp, _vp], _int),
     "idl_countsketch_dense": ([_vp, _vp, _i64, _i64, _i64, _int, _vp, _vp, _vp, _vp, _i64, _vp, _i64], _int),
     "idl_countsketch_csr": ([_vp, _vp, _vp, _vp, _i64, _i64, _i64, _int, _vp, _vp, _vp, _vp, _i64, _vp, _i64], _int),
     "idl_tensorsketch": ([_vp, _int, _vp, _i64, _vp, _vp, _vp, _vp, _vp, _i64, _vp, _i64], _int),
@@ -192,6 +193,13 @@ def idl_draw_mode(ctx, seed, n, In, L, h, s):
 
 def idl_bucket_offsets(ctx, h, I, L, bucket_ptr, row_list):
     return ctx.check(lib().idl_bucket_offsets(ctx.ptr, _p(h), I, L, _p(bucket_ptr), _p(row_list)))
+
+
+def idl_bucket_offsets_noalloc(stream, h, I, L, bucket_ptr, row_list):
+    """Allocation-free bucket offsets (no context; scratch in a fixed device array).
+    stream: torch.cuda.Stream, raw cudaStream_t integer or None.  Returns the status code."""
+    hs = 0 if stream is None else (stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+    return lib().idl_bucket_offsets_noalloc(_vp(hs), _p(h), I, L, _p(bucket_ptr), _p(row_list))
 
 
 def idl_countsketch_dense(ctx, A, I, R, lda, dtype, h, s, bucket_ptr, row_list, L, Y1, ldy):
