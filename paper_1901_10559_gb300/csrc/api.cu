@@ -261,6 +261,11 @@ extern "C" int idl_debug_fail_alloc(idl_ctx* ctx, int nth) {
   ctx->fail_alloc_at = nth > 0 ? ctx->alloc_count + (size_t)nth : 0;
   return IDL_OK;
 }
+extern "C" int idl_debug_gemm_path(idl_ctx* ctx, int simt) {
+  if (!ctx) return IDL_EINVAL;
+  ctx->gemm_simt = simt != 0;
+  return IDL_OK;
+}
 extern "C" int idl_debug_release_workspace(idl_ctx* ctx) {
   TRY(check_ctx(ctx));
   cudaStreamSynchronize(ctx->stream);

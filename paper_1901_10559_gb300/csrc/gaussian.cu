@@ -3,9 +3,10 @@
 // Output is column-major (Y2 = (Y1^T Omega^T)^T, one contiguous column of m2
 // values per original column r), which is the layout the QR stage reads.
 //
-// This file holds the FP64 path and the reference-shaped FP32 path; the bf16
-// tensor-core paths live in gaussian_tc.cu.  Split-K over m1 with a second
-// pass that sums the partial products in a fixed order.
+// This file holds the FP64 path (CUDA cores) and a CUDA-core FP32 path kept
+// for comparison; FP32 data go to the tcgen05 path of gaussian_tc.cu by
+// default.  Split-K over m1 with a second pass that sums the partial products
+// in a fixed order.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -91,6 +92,14 @@ __global__ void gauss_reduce_kernel(const T* __restrict__ part, int splits, int6
   Y2[r * ldy2 + j] = s;
 }
 
+int launch_gaussian_reduce(idl_ctx* ctx, const float* part, int splits, int64_t R, int MP, int64_t m2, float* Y2,
+                           int64_t ldy2) {
+  const int64_t n = R * m2;
+  gauss_reduce_kernel<float><<<(unsigned)cdiv(n, 256), 256, 0, ctx->stream>>>(part, splits, R, MP, (int)m2, Y2, ldy2),
+      idl::count_launch();
+  return cuda_check(ctx, cudaGetLastError(), "gaussian reduce");
+}
+
 // Omega (FP64) -> working precision copy
 __global__ void omega_to_f32_kernel(const double* __restrict__ Om, int64_t n, float* __restrict__ out) {
   const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -140,6 +149,9 @@ int launch_gaussian(idl_ctx* ctx, const double* Omega, int64_t m2, int64_t m1, c
   if (m2 > 256) return fail(ctx, IDL_ELIMIT, "gaussian: m2 > 256");
   if (dtype == IDL_F64)
     return simt_impl<double>(ctx, Omega, m2, m1, (const double*)Y1, R, ldy1, (double*)Y2, ldy2, 0);
+  if (!ctx->gemm_simt)
+    return launch_gaussian_tc(ctx, Omega, m2, m1, (const float*)Y1, R, ldy1, precision, (float*)Y2, ldy2);
+  // CUDA-core path (kept for comparison): FP32 FMA, or bf16-rounded operands for IDL_PREC_BF16
   float* om32 = (float*)ws_get(ctx, kWsOmegaConv, sizeof(float) * (size_t)(m2 * m1));
   if (!om32) return IDL_ENOMEM;
   omega_to_f32_kernel<<<(unsigned)cdiv(m2 * m1, 256), 256, 0, ctx->stream>>>(Omega, m2 * m1, om32), idl::count_launch();

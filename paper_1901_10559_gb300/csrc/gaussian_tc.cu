@@ -1,0 +1,384 @@
+// gaussian_tc.cu -- the Gaussian stage Y2 = Omega Y1 (Sec. 1.2.1) on the
+// 5th-generation tensor cores (tcgen05, TMEM accumulators).
+//
+// Computed as D = Y1^T Omega^T: M = 128 columns r of Y1 per CTA, N = m2
+// rounded up to 16, K = m1 (split over CTAs, partial sums reduced in a fixed
+// order by gauss_reduce_kernel).  Both operands are K-major bf16 in shared
+// memory with the 128-byte swizzle:
+//   * A (Y1^T): every thread loads FP32 Y1 (coalesced along r), splits each
+//     value into bf16 planes x = hi + mid + lo (each the bf16 rounding of the
+//     remainder) and stores the planes already transposed into the K-major
+//     swizzled layout -- the conversion and the transpose cost no extra HBM
+//     traffic;
+//   * B (Omega^T): the planes of Omega are built once per call in global
+//     memory in exactly the shared-memory layout and fetched per K block with
+//     one cp.async.bulk (TMA engine) completing on an mbarrier.
+// One thread issues tcgen05.mma (kind::f16, FP32 accumulate) for every pair of
+// planes the precision mode keeps:
+//   BF16   : hi*hi                                (1 product,  8-bit operands)
+//   BF16X3 : hi*hi + hi*lo + lo*hi   (2 planes)   (3 products, ~16-bit operands)
+//   FP32   : hh + hm + mh + hl + mm + lh  (3 planes: the terms above 2^-24)
+// Two pipeline stages: the loads of K block i+1 are in flight while block i is
+// multiplied.  Every mbarrier wait is bounded (1 s); on a timeout the kernel
+// records IDL_ETIMEOUT, waits (bounded) for the MMAs it issued, frees TMEM
+// and returns.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace idl {
+
+namespace tc {
+
+constexpr int kThreads = 256;
+constexpr int kBM = 128;        // rows of D (columns r of Y1) per CTA
+constexpr int kBK = 64;         // K per stage (one 128-byte swizzle atom of bf16)
+constexpr int kStages = 2;
+constexpr uint64_t kTimeoutNs = 1000000000ull;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ uint64_t global_timer() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t done;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(done)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return done != 0;
+}
+
+// Bounded wait: true when the phase of the given parity completed, false after ~1 s.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = global_timer();
+  while (true) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if (global_timer() - t0 > kTimeoutNs) return false;
+  }
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void fence_barrier_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_alloc(uint32_t* slot, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(slot)), "r"(ncols)
+               : "memory");
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accum) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accum)
+      : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int q = 0; q < 16; ++q) v[q] = __uint_as_float(r[q]);
+}
+
+// K-major operand, 128-byte swizzle: 8-row atoms of 1024 B, rows 128 B apart.
+__device__ __forceinline__ uint64_t sw128_desc(const void* base) {
+  const uint32_t a = smem_u32(base);
+  return (uint64_t)((a >> 4) & 0x3FFF) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) | ((uint64_t)1 << 46) |
+         ((uint64_t)2 << 61);
+}
+
+// instruction descriptor: D FP32, A and B bf16, both K-major, M = 128, N = n
+__host__ __device__ constexpr uint32_t idesc_bf16(int n) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(kBM >> 4) << 24);
+}
+
+// byte offset of the 16-byte chunk (row, kc) in a K-major 128-byte-swizzled tile
+__host__ __device__ __forceinline__ uint32_t sw128_off(int row, int kc) {
+  return (uint32_t)((row >> 3) * 1024 + (row & 7) * 128 + ((kc ^ (row & 7)) << 4));
+}
+
+// split x into NP bf16 terms, each the rounding of what the previous ones left
+template <int NP>
+__device__ __forceinline__ void split_bf16(float x, __nv_bfloat16* out) {
+  float r = x;
+#pragma unroll
+  for (int p = 0; p < NP; ++p) {
+    const __nv_bfloat16 b = __float2bfloat16_rn(r);
+    out[p] = b;
+    r = r - __bfloat162float(b);
+  }
+}
+
+}  // namespace tc
+
+// Omega (m2 x m1, FP64) -> bf16 planes of Omega^T in the swizzled K-major tile layout:
+// [k block][plane][NT rows][64] with rows n = 0..NT-1 (zero beyond m2 / m1).
+template <int NP>
+__global__ void omega_planes_kernel(const double* __restrict__ Om, int m2, int64_t m1, int NT, int nkb,
+                                    __nv_bfloat16* __restrict__ out) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;     // (kb, n, kc)
+  const int64_t total = (int64_t)nkb * NT * 8;
+  if (e >= total) return;
+  const int kc = (int)(e & 7);
+  const int n = (int)((e >> 3) % NT);
+  const int kb = (int)(e / (8 * NT));
+  __nv_bfloat16 pl[NP][8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const int64_t k = (int64_t)kb * tc::kBK + kc * 8 + q;
+    const float x = (n < m2 && k < m1) ? (float)Om[(int64_t)n * m1 + k] : 0.f;
+    __nv_bfloat16 t[NP];
+    tc::split_bf16<NP>(x, t);
+#pragma unroll
+    for (int p = 0; p < NP; ++p) pl[p][q] = t[p];
+  }
+  unsigned char* tile = (unsigned char*)out + (size_t)kb * NP * NT * 128;
+#pragma unroll
+  for (int p = 0; p < NP; ++p)
+    *(uint4*)(tile + (size_t)p * NT * 128 + tc::sw128_off(n, kc)) = *(const uint4*)pl[p];
+}
+
+// Products (plane of A, plane of B) per precision mode, smallest terms first.
+__host__ __device__ constexpr int n_products(int np) { return np == 1 ? 1 : (np == 2 ? 3 : 6); }
+__host__ __device__ constexpr int prod_a(int np, int q) {
+  return np == 1 ? 0 : (np == 2 ? (q == 0 ? 1 : 0) : (q == 0 ? 2 : q == 1 ? 1 : q == 2 ? 0 : q == 3 ? 1 : 0));
+}
+__host__ __device__ constexpr int prod_b(int np, int q) {
+  return np == 1 ? 0 : (np == 2 ? (q == 1 ? 1 : 0) : (q == 0 ? 0 : q == 1 ? 1 : q == 2 ? 2 : q == 3 ? 0 : q == 4 ? 1 : 0));
+}
+
+template <int NP>
+__global__ void __launch_bounds__(tc::kThreads, 1)
+gauss_tc_kernel(const float* __restrict__ Y1, int64_t ldy1, int64_t R, int64_t m1, const __nv_bfloat16* __restrict__ Bpl,
+                int NT, int kb_per_cta, int nkb, float* __restrict__ part, int* status) {
+  using namespace tc;
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char* sm = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  const int a_plane = kBM * kBK * 2;                   // 16 KB
+  const int b_plane = NT * kBK * 2;
+  unsigned char* A = sm;                               // [stage][plane] a_plane
+  unsigned char* B = A + kStages * NP * a_plane;       // [stage][plane] b_plane
+  uint64_t* bars = (uint64_t*)(B + kStages * NP * b_plane);
+  uint64_t* mma_done = bars;                           // [2]
+  uint64_t* b_full = bars + 2;                         // [2]
+  uint32_t* tmem_slot = (uint32_t*)(bars + 4);
+  __shared__ int s_flag;
+
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int64_t r0 = (int64_t)blockIdx.x * kBM;
+  const int kb0 = blockIdx.y * kb_per_cta;
+  const int nk = min(nkb, kb0 + kb_per_cta) - kb0;
+  uint32_t tcols = 32;
+  while ((int)tcols < NT) tcols <<= 1;
+
+  if (tid == 0) {
+    mbar_init(&mma_done[0], 1);
+    mbar_init(&mma_done[1], 1);
+    mbar_init(&b_full[0], 1);
+    mbar_init(&b_full[1], 1);
+    fence_barrier_init();
+    s_flag = 0;
+  }
+  if (warp == 0) tmem_alloc(tmem_slot, tcols);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  if (nk <= 0) goto cleanup;
+  {
+    const uint32_t b_bytes = (uint32_t)(NP * b_plane);
+    if (tid == 0) {
+      mbar_expect_tx(&b_full[0], b_bytes);
+      bulk_g2s(B, Bpl + (size_t)kb0 * NP * NT * kBK, b_bytes, &b_full[0]);
+    }
+    const int m = tid & (kBM - 1);
+    const int kq = tid >> 7;                           // 0 or 1: k-chunks kq, kq+2, kq+4, kq+6
+    const bool col_ok = r0 + m < R;
+    float v[4][8];
+    auto load_block = [&](int kb) {
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const int kc = kq + 2 * c;
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+          const int64_t b = (int64_t)kb * kBK + kc * 8 + e;
+          v[c][e] = (col_ok && b < m1) ? __ldcs(Y1 + b * ldy1 + r0 + m) : 0.f;
+        }
+      }
+    };
+    load_block(kb0);
+    int last_commit = -1;
+    const uint32_t idesc = idesc_bf16(NT);
+    for (int i = 0; i < nk; ++i) {
+      const int s = i & 1;
+      if (i >= 2 && !mbar_wait(&mma_done[s], ((i - 2) >> 1) & 1)) s_flag = 1;     // stage s free
+      unsigned char* As = A + (size_t)s * NP * a_plane;
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const int kc = kq + 2 * c;
+        __nv_bfloat16 pl[NP][8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+          __nv_bfloat16 t[NP];
+          split_bf16<NP>(v[c][e], t);
+#pragma unroll
+          for (int p = 0; p < NP; ++p) pl[p][e] = t[p];
+        }
+#pragma unroll
+        for (int p = 0; p < NP; ++p) *(uint4*)(As + (size_t)p * a_plane + sw128_off(m, kc)) = *(const uint4*)pl[p];
+      }
+      fence_async_smem();
+      if (i + 1 < nk) load_block(kb0 + i + 1);         // next block's loads overlap this block's MMAs
+      __syncthreads();
+      if (s_flag) break;
+      if (tid == 0) {
+        tc_fence_after();
+        if (!mbar_wait(&b_full[s], (i >> 1) & 1)) {
+          s_flag = 1;
+        } else {
+          const unsigned char* Bs = B + (size_t)s * NP * b_plane;
+#pragma unroll
+          for (int ks = 0; ks < kBK / 16; ++ks) {
+#pragma unroll
+            for (int q = 0; q < n_products(NP); ++q) {
+              const uint64_t ad = sw128_desc(As + (size_t)prod_a(NP, q) * a_plane) + (uint64_t)(ks * 2);
+              const uint64_t bd = sw128_desc(Bs + (size_t)prod_b(NP, q) * b_plane) + (uint64_t)(ks * 2);
+              mma_bf16(tmem, ad, bd, idesc, (i > 0 || ks > 0 || q > 0) ? 1u : 0u);
+            }
+          }
+          mma_commit(&mma_done[s]);
+          last_commit = i;
+          // prefetch Omega^T planes of block i+1 into the other stage once its MMAs (block i-1) are done
+          if (i + 1 < nk) {
+            if (i >= 1 && !mbar_wait(&mma_done[s ^ 1], ((i - 1) >> 1) & 1)) {
+              s_flag = 1;
+            } else {
+              mbar_expect_tx(&b_full[s ^ 1], b_bytes);
+              bulk_g2s(B + (size_t)(s ^ 1) * NP * b_plane, Bpl + (size_t)(kb0 + i + 1) * NP * NT * kBK, b_bytes,
+                       &b_full[s ^ 1]);
+            }
+          }
+        }
+      }
+    }
+    // wait for the last MMAs this CTA issued (bounded), then read the accumulator
+    if (tid == 0 && last_commit >= 0) {
+      if (!mbar_wait(&mma_done[last_commit & 1], (last_commit >> 1) & 1)) s_flag = 2;
+    }
+    if (tid == 0 && last_commit < nk - 1) s_flag = s_flag ? s_flag : 1;
+    __syncthreads();
+    tc_fence_after();
+    if (s_flag == 0) {
+      // epilogue: warp w reads TMEM lanes 32*(w%4).. (rows of D); warps 0-3 and 4-7 split the columns
+      const int lane_base = (warp & 3) * 32;
+      const int64_t r = r0 + lane_base + (tid & 31);
+      float* prow = part + ((int64_t)blockIdx.y * R + r) * NT;
+      for (int q = warp >> 2; q < NT / 16; q += 2) {
+        float vals[16];
+        tmem_ld16(tmem + ((uint32_t)lane_base << 16) + (uint32_t)(q * 16), vals);
+        if (r < R) {
+#pragma unroll
+          for (int j = 0; j < 16; j += 4)
+            *(float4*)(prow + q * 16 + j) = make_float4(vals[j], vals[j + 1], vals[j + 2], vals[j + 3]);
+        }
+      }
+    }
+  }
+cleanup:
+  tc_fence_before();
+  __syncthreads();
+  if (tid == 0 && s_flag) set_status(status, IDL_ETIMEOUT);
+  if (warp == 0) tmem_dealloc(tmem, tcols);
+}
+
+template <int NP>
+static int tc_impl(idl_ctx* ctx, const double* Omega, int64_t m2, int64_t m1, const float* Y1, int64_t R, int64_t ldy1,
+                   float* Y2, int64_t ldy2) {
+  using namespace tc;
+  const int NT = (int)round_up(m2, 16);
+  const int nkb = (int)cdiv(m1, kBK);
+  const int mtiles = (int)cdiv(R, kBM);
+  const size_t a_plane = (size_t)kBM * kBK * 2, b_plane = (size_t)NT * kBK * 2;
+  const size_t smem = 1024 + kStages * NP * (a_plane + b_plane) + 64;
+  if (smem > (size_t)ctx->smem_optin) return fail(ctx, IDL_ELIMIT, "gaussian tc: shared memory");
+  // CTAs per SM by shared memory; aim for about two waves of CTAs over the SMs
+  const int per_sm = std::max(1, (int)(ctx->smem_optin / smem));
+  int splits = (int)std::max<int64_t>(1, cdiv((int64_t)ctx->num_sms * per_sm, mtiles));
+  splits = std::min(splits, nkb);
+  const int kbpc = (int)cdiv(nkb, splits);
+  splits = (int)cdiv(nkb, kbpc);
+  __nv_bfloat16* Bpl = (__nv_bfloat16*)ws_get(ctx, kWsOmegaConv, (size_t)nkb * NP * b_plane);
+  float* part = (float*)ws_get(ctx, kWsPart, sizeof(float) * (size_t)splits * R * NT);
+  if (!Bpl || !part) return IDL_ENOMEM;
+  {
+    const int64_t n = (int64_t)nkb * NT * 8;
+    omega_planes_kernel<NP><<<(unsigned)cdiv(n, 256), 256, 0, ctx->stream>>>(Omega, (int)m2, m1, NT, nkb, Bpl),
+        count_launch();
+  }
+  auto k = gauss_tc_kernel<NP>;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return cuda_check(ctx, e, "gaussian tc attribute");
+  dim3 grid((unsigned)mtiles, (unsigned)splits);
+  k<<<grid, kThreads, smem, ctx->stream>>>(Y1, ldy1, R, m1, Bpl, NT, kbpc, nkb, part, ctx->d_status), count_launch();
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_check(ctx, e, "gaussian tc");
+  return launch_gaussian_reduce(ctx, part, splits, R, NT, m2, Y2, ldy2);
+}
+
+int launch_gaussian_tc(idl_ctx* ctx, const double* Omega, int64_t m2, int64_t m1, const float* Y1, int64_t R,
+                       int64_t ldy1, int precision, float* Y2, int64_t ldy2) {
+  if (m2 > 256) return fail(ctx, IDL_ELIMIT, "gaussian tc: m2 > 256");
+  switch (precision) {
+    case IDL_PREC_BF16: return tc_impl<1>(ctx, Omega, m2, m1, Y1, R, ldy1, Y2, ldy2);
+    case IDL_PREC_BF16X3: return tc_impl<2>(ctx, Omega, m2, m1, Y1, R, ldy1, Y2, ldy2);
+    default: return tc_impl<3>(ctx, Omega, m2, m1, Y1, R, ldy1, Y2, ldy2);
+  }
+}
+
+}  // namespace idl

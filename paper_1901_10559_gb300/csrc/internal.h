@@ -21,6 +21,7 @@ struct idl_ctx {
   struct Buf { void* p = nullptr; size_t bytes = 0; };
   std::vector<Buf> slots;
   int last_cluster = 0;
+  int gemm_simt = 0;           // 1: Gaussian stage on CUDA cores instead of tcgen05 (comparison / tests)
   size_t fail_alloc_at = 0;    // test hook: fail the n-th workspace allocation (0 = never)
   size_t alloc_count = 0;
   // per-stage CUDA-event profiling (idl_profile / idl_profile_read)
@@ -67,6 +68,12 @@ int launch_countsketch_csr(idl_ctx* ctx, const int64_t* rowptr, const int32_t* c
 // gaussian.cu
 int launch_gaussian(idl_ctx* ctx, const double* Omega, int64_t m2, int64_t m1, const void* Y1, int64_t R,
                     int64_t ldy1, int dtype, int precision, void* Y2, int64_t ldy2);
+
+int launch_gaussian_reduce(idl_ctx* ctx, const float* part, int splits, int64_t R, int MP, int64_t m2, float* Y2,
+                           int64_t ldy2);
+// gaussian_tc.cu
+int launch_gaussian_tc(idl_ctx* ctx, const double* Omega, int64_t m2, int64_t m1, const float* Y1, int64_t R,
+                       int64_t ldy1, int precision, float* Y2, int64_t ldy2);
 
 // cpqr.cu
 int launch_cpqr(idl_ctx* ctx, void* Y2, int64_t m, int64_t R, int64_t ld, int dtype, int64_t K, int32_t* J,

@@ -249,3 +249,28 @@ def test_lambda_hat_parity(ctx):
     idl.idl_lambda_hat(ctx, dev(lam), dev(J), dev(T), K, R, out)
     from oracle.idmethods import lambda_hat
     assert np.allclose(host(out), lambda_hat(lam, J, T), rtol=1e-14, atol=1e-14)
+
+
+# ------------------------------------------------------------------ a6 on tcgen05: shapes and the CUDA-core path
+@pytest.mark.parametrize("m2,m1,R", [(1, 64, 128), (16, 65, 1), (17, 63, 130), (60, 3600, 1000), (120, 1000, 257),
+                                     (256, 200, 300), (33, 1, 5)])
+def test_gaussian_tc_shapes_and_simt_agreement(ctx, m2, m1, R):
+    rng = np.random.default_rng(m2 * 7 + m1)
+    Y1 = rng.standard_normal((m1, R)).astype(np.float32)
+    Om = torch.empty(m2 * m1, dtype=torch.float64, device="cuda")
+    idl.idl_draw_gaussian(ctx, 5, m2, m1, Om)
+    Omw = odr.gaussian_matrix(5, m2, m1)
+    for prec, tol in [(idl.PREC_FP32, FP32_TOL), (idl.PREC_BF16X3, 2e-5), (idl.PREC_BF16, 1e-5)]:
+        outs = []
+        for simt in (0, 1):
+            idl.lib().idl_debug_gemm_path(ctx.ptr, simt)
+            Y2 = torch.full((R * m2,), float("nan"), dtype=torch.float32, device="cuda")
+            idl.idl_gaussian_stage(ctx, Om, m2, m1, dev(Y1), R, R, idl.IDL_F32, prec, Y2, m2)
+            outs.append(colmajor_to_matrix(Y2, m2, R, m2))
+        idl.lib().idl_debug_gemm_path(ctx.ptr, 0)
+        want = ogs.gaussian_stage(Omw, Y1, prec)
+        assert np.all(np.isfinite(outs[0]))
+        assert rel_fro(outs[0], want) <= tol, (prec, rel_fro(outs[0], want))
+        if prec == idl.PREC_FP32:
+            assert rel_fro(outs[0], outs[1]) <= 2 * FP32_TOL
+    assert ctx.sync() == idl.IDL_OK
