@@ -196,12 +196,15 @@ __host__ __device__ constexpr int prod_b(int np, int q) {
 template <int NP>
 __global__ void __launch_bounds__(tc::kThreads, 1)
 gauss_tc_kernel(const float* __restrict__ Y1, int64_t ldy1, int64_t R, int64_t m1, const __nv_bfloat16* __restrict__ Bpl,
-                int NT, int kb_per_cta, int nkb, float* __restrict__ part, int* status) {
+                int NT, int NTc, int kb_per_cta, int nkb, float* __restrict__ part, int* status) {
+  // NT: rows of the Omega^T planes (= columns of part); this CTA computes columns
+  // [blockIdx.z * NTc, +NTc) of D
   using namespace tc;
   extern __shared__ unsigned char smem_raw[];
   unsigned char* sm = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   const int a_plane = kBM * kBK * 2;                   // 16 KB
-  const int b_plane = NT * kBK * 2;
+  const int b_plane = NTc * kBK * 2;
+  const int n0 = blockIdx.z * NTc;
   unsigned char* A = sm;                               // [stage][plane] a_plane
   unsigned char* B = A + kStages * NP * a_plane;       // [stage][plane] b_plane
   uint64_t* bars = (uint64_t*)(B + kStages * NP * b_plane);
@@ -215,7 +218,7 @@ gauss_tc_kernel(const float* __restrict__ Y1, int64_t ldy1, int64_t R, int64_t m
   const int kb0 = blockIdx.y * kb_per_cta;
   const int nk = min(nkb, kb0 + kb_per_cta) - kb0;
   uint32_t tcols = 32;
-  while ((int)tcols < NT) tcols <<= 1;
+  while ((int)tcols < NTc) tcols <<= 1;
 
   if (tid == 0) {
     mbar_init(&mma_done[0], 1);
@@ -233,10 +236,15 @@ gauss_tc_kernel(const float* __restrict__ Y1, int64_t ldy1, int64_t R, int64_t m
   if (nk <= 0) goto cleanup;
   {
     const uint32_t b_bytes = (uint32_t)(NP * b_plane);
-    if (tid == 0) {
-      mbar_expect_tx(&b_full[0], b_bytes);
-      bulk_g2s(B, Bpl + (size_t)kb0 * NP * NT * kBK, b_bytes, &b_full[0]);
-    }
+    // the NP planes' row chunks [n0, n0 + NTc) of K block kb into B stage st
+    auto fetch_b = [&](int kb, int st) {
+      mbar_expect_tx(&b_full[st], b_bytes);
+#pragma unroll
+      for (int p = 0; p < NP; ++p)
+        bulk_g2s(B + (size_t)(st * NP + p) * b_plane, Bpl + ((size_t)kb * NP * NT + (size_t)p * NT + n0) * kBK,
+                 (uint32_t)b_plane, &b_full[st]);
+    };
+    if (tid == 0) fetch_b(kb0, 0);
     const int m = tid & (kBM - 1);
     const int kq = tid >> 7;                           // 0 or 1: k-chunks kq, kq+2, kq+4, kq+6
     const bool col_ok = r0 + m < R;
@@ -254,7 +262,7 @@ gauss_tc_kernel(const float* __restrict__ Y1, int64_t ldy1, int64_t R, int64_t m
     };
     load_block(kb0);
     int last_commit = -1;
-    const uint32_t idesc = idesc_bf16(NT);
+    const uint32_t idesc = idesc_bf16(NTc);
     for (int i = 0; i < nk; ++i) {
       const int s = i & 1;
       if (i >= 2 && !mbar_wait(&mma_done[s], ((i - 2) >> 1) & 1)) s_flag = 1;     // stage s free
@@ -299,9 +307,7 @@ gauss_tc_kernel(const float* __restrict__ Y1, int64_t ldy1, int64_t R, int64_t m
             if (i >= 1 && !mbar_wait(&mma_done[s ^ 1], ((i - 1) >> 1) & 1)) {
               s_flag = 1;
             } else {
-              mbar_expect_tx(&b_full[s ^ 1], b_bytes);
-              bulk_g2s(B + (size_t)(s ^ 1) * NP * b_plane, Bpl + (size_t)(kb0 + i + 1) * NP * NT * kBK, b_bytes,
-                       &b_full[s ^ 1]);
+              fetch_b(kb0 + i + 1, s ^ 1);
             }
           }
         }
@@ -318,8 +324,8 @@ gauss_tc_kernel(const float* __restrict__ Y1, int64_t ldy1, int64_t R, int64_t m
       // epilogue: warp w reads TMEM lanes 32*(w%4).. (rows of D); warps 0-3 and 4-7 split the columns
       const int lane_base = (warp & 3) * 32;
       const int64_t r = r0 + lane_base + (tid & 31);
-      float* prow = part + ((int64_t)blockIdx.y * R + r) * NT;
-      for (int q = warp >> 2; q < NT / 16; q += 2) {
+      float* prow = part + ((int64_t)blockIdx.y * R + r) * NT + n0;
+      for (int q = warp >> 2; q < NTc / 16; q += 2) {
         float vals[16];
         tmem_ld16(tmem + ((uint32_t)lane_base << 16) + (uint32_t)(q * 16), vals);
         if (r < R) {
@@ -341,19 +347,28 @@ template <int NP>
 static int tc_impl(idl_ctx* ctx, const double* Omega, int64_t m2, int64_t m1, const float* Y1, int64_t R, int64_t ldy1,
                    float* Y2, int64_t ldy2) {
   using namespace tc;
-  const int NT = (int)round_up(m2, 16);
   const int nkb = (int)cdiv(m1, kBK);
   const int mtiles = (int)cdiv(R, kBM);
-  const size_t a_plane = (size_t)kBM * kBK * 2, b_plane = (size_t)NT * kBK * 2;
-  const size_t smem = 1024 + kStages * NP * (a_plane + b_plane) + 64;
+  const size_t a_plane = (size_t)kBM * kBK * 2;
+  // N chunks: the widest chunk (multiple of 16, <= 256) whose two stages fit in shared memory
+  const int NT0 = (int)round_up(m2, 16);
+  int nz = 1, NTc = NT0;
+  auto smem_for = [&](int ntc) { return 1024 + kStages * NP * (a_plane + (size_t)ntc * kBK * 2) + 64; };
+  while (smem_for(NTc) > (size_t)ctx->smem_optin && NTc > 16) {
+    ++nz;
+    NTc = (int)round_up(cdiv(NT0, nz), 16);
+  }
+  const size_t smem = smem_for(NTc);
   if (smem > (size_t)ctx->smem_optin) return fail(ctx, IDL_ELIMIT, "gaussian tc: shared memory");
-  // CTAs per SM by shared memory; aim for about two waves of CTAs over the SMs
+  const int NT = nz * NTc;                            // plane rows (zero beyond m2)
+  const size_t b_plane_full = (size_t)NT * kBK * 2;
+  // CTAs per SM by shared memory; aim for about one wave of CTAs over the SMs
   const int per_sm = std::max(1, (int)(ctx->smem_optin / smem));
-  int splits = (int)std::max<int64_t>(1, cdiv((int64_t)ctx->num_sms * per_sm, mtiles));
+  int splits = (int)std::max<int64_t>(1, cdiv((int64_t)ctx->num_sms * per_sm, (int64_t)mtiles * nz));
   splits = std::min(splits, nkb);
   const int kbpc = (int)cdiv(nkb, splits);
   splits = (int)cdiv(nkb, kbpc);
-  __nv_bfloat16* Bpl = (__nv_bfloat16*)ws_get(ctx, kWsOmegaConv, (size_t)nkb * NP * b_plane);
+  __nv_bfloat16* Bpl = (__nv_bfloat16*)ws_get(ctx, kWsOmegaConv, (size_t)nkb * NP * b_plane_full);
   float* part = (float*)ws_get(ctx, kWsPart, sizeof(float) * (size_t)splits * R * NT);
   if (!Bpl || !part) return IDL_ENOMEM;
   {
@@ -364,8 +379,9 @@ static int tc_impl(idl_ctx* ctx, const double* Omega, int64_t m2, int64_t m1, co
   auto k = gauss_tc_kernel<NP>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return cuda_check(ctx, e, "gaussian tc attribute");
-  dim3 grid((unsigned)mtiles, (unsigned)splits);
-  k<<<grid, kThreads, smem, ctx->stream>>>(Y1, ldy1, R, m1, Bpl, NT, kbpc, nkb, part, ctx->d_status), count_launch();
+  dim3 grid((unsigned)mtiles, (unsigned)splits, (unsigned)nz);
+  k<<<grid, kThreads, smem, ctx->stream>>>(Y1, ldy1, R, m1, Bpl, NT, NTc, kbpc, nkb, part, ctx->d_status),
+      count_launch();
   e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_check(ctx, e, "gaussian tc");
   return launch_gaussian_reduce(ctx, part, splits, R, NT, m2, Y2, ldy2);
