@@ -65,6 +65,7 @@ _SIGS = {
     "idl_debug_fail_alloc": ([_vp, _int], _int),
     "idl_debug_release_workspace": ([_vp], _int),
     "idl_debug_gemm_path": ([_vp, _int], _int),
+    "idl_debug_cpqr_path": ([_vp, _int], _int),
     "idl_draw_countsketch": ([_vp, _u64, _i64, _i64, _int, _vp, _vp], _int),
     "idl_draw_gaussian": ([_vp, _u64, _i64, _i64, _vp], _int),
     "idl_draw_mode": ([_vp, _u64, _int, _i64, _i64, _vp, _vp], _int),

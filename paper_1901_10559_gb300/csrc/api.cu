@@ -266,6 +266,11 @@ extern "C" int idl_debug_gemm_path(idl_ctx* ctx, int simt) {
   ctx->gemm_simt = simt != 0;
   return IDL_OK;
 }
+extern "C" int idl_debug_cpqr_path(idl_ctx* ctx, int smem_only) {
+  if (!ctx) return IDL_EINVAL;
+  ctx->cpqr_smem_only = smem_only != 0;
+  return IDL_OK;
+}
 extern "C" int idl_debug_release_workspace(idl_ctx* ctx) {
   TRY(check_ctx(ctx));
   cudaStreamSynchronize(ctx->stream);

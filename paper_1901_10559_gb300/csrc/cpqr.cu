@@ -228,10 +228,264 @@ cpqr_cluster_kernel(const T* __restrict__ Yin, T* __restrict__ Yout, int m, int 
   }
 }
 
+// ----------------------------------------------------------------------------
+// Register-resident variant (used whenever a cluster shape fits).  Each group
+// of tpc lanes keeps one column in registers (rows gl, gl + tpc, ...) and a
+// write-only mirror of it in shared memory.  Per pivot step:
+//   1. every warp reduces its columns' remaining norms to one candidate and
+//      pushes it into every CTA's candidate table (DSMEM stores);
+//   2. one hardware cluster barrier;
+//   3. warp 0 of every CTA reduces the table (same result everywhere), pulls
+//      the winning column's trailing part from its owner's mirror over DSMEM,
+//      and forms the Householder reflection (v in shared memory);
+//   4. one block barrier; every group applies the reflection to its column in
+//      registers and recomputes the trailing norm exactly.
+// The pivot column is retired, not modified, so its mirror stays valid while
+// other CTAs read it; its final values (alpha on the diagonal, zeros below)
+// are written only to the output.
+// ----------------------------------------------------------------------------
+// Threads per CTA each (type, values per lane, lanes per column) variant is
+// compiled for: sized so the column registers fit without spilling.
+template <typename T, int V, int TPC> struct RegCpqr {
+  static constexpr int kWords = V * (int)(sizeof(T) / 4);
+  static constexpr int kMaxThreads = kWords <= 16 ? 1024 : (kWords <= 32 ? (TPC == 1 ? 896 : 768)
+                                                                   : (TPC == 1 ? 640 : 512));
+};
+
+template <typename T, int V, int TPC>
+__global__ void __launch_bounds__(RegCpqr<T, V, TPC>::kMaxThreads, 1)
+cpqr_reg_kernel(const T* __restrict__ Yin, T* __restrict__ Yout, int m, int R, int ld, int K, int nc, int ldm,
+                int32_t* __restrict__ J, double* __restrict__ rnorm, double* __restrict__ diag, int* status) {
+  constexpr int tpc = TPC;
+  cg::cluster_group cluster = cg::this_cluster();
+  const int CS = (int)cluster.num_blocks();
+  const int rank = (int)cluster.block_rank();
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, NW = blockDim.x >> 5;
+  const int g = tid / tpc, gl = tid - g * tpc;
+  const int c0 = rank * nc;
+  const int ncl = max(0, min(nc, R - c0));
+  const bool own = g < ncl;
+  const int col = c0 + g;
+
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* mirror = (T*)smem_raw;                                        // nc * ldm
+  T* vs = mirror + (size_t)nc * ldm;                               // m
+  Cand<T>* cand = (Cand<T>*)(smem_raw + round_up((int64_t)sizeof(T) * ((int64_t)nc * ldm + m), 16));  // [2][CS*NW]
+  __shared__ T s_beta, s_alpha;
+  __shared__ int s_p, s_stop;
+  if (tid == 0) s_stop = 0;
+
+  T y[V];
+#pragma unroll
+  for (int j = 0; j < V; ++j) {
+    const int i = gl + tpc * j;
+    y[j] = (own && i < m) ? Yin[(int64_t)col * ld + i] : T(0);
+    if (own && i < m) mirror[g * ldm + i] = y[j];
+  }
+  T nn = T(0);
+#pragma unroll
+  for (int j = 0; j < V; ++j) nn += y[j] * y[j];
+  nn = group_sum(nn, tpc);
+  {
+    double f = (own && gl == 0) ? (double)nn : 0.0;
+    f = warp_sum(f);
+    if (lane == 0 && f != 0.0) atomicAdd(&diag[1], f);
+  }
+  T nrm2 = own ? nn : T(-1);          // < 0: retired or no column
+  int tp = -1;
+  T alpha_p = T(0);
+  const int ncand = CS * NW;
+  int t = 0;
+  for (; t < K; ++t) {
+    // 1. warp candidate -> every CTA's table
+    T bv = (gl == 0 && nrm2 >= T(0)) ? nrm2 : T(-1);
+    int bi = (gl == 0 && nrm2 >= T(0)) ? col : -1;
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+      const T ov = __shfl_xor_sync(0xffffffffu, bv, o);
+      const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+      if (better(ov, oi, bv, bi)) { bv = ov; bi = oi; }
+    }
+    Cand<T>* slot = cand + (size_t)(t & 1) * ncand + rank * NW + wid;
+    if (lane < CS) {
+      Cand<T>* dst = cluster.map_shared_rank(slot, (unsigned)lane);
+      dst->val = bv;
+      dst->idx = bi;
+    }
+    cluster.sync();                                                 // 2.
+    // 3. winner, pivot column, reflection (warp 0)
+    if (wid == 0) {
+      T v = T(-1);
+      int ix = -1;
+      const Cand<T>* tab = cand + (size_t)(t & 1) * ncand;
+      for (int q = lane; q < ncand; q += 32) {
+        const T cv = tab[q].val;
+        const int ci = tab[q].idx;
+        if (better(cv, ci, v, ix)) { v = cv; ix = ci; }
+      }
+#pragma unroll
+      for (int o = 16; o; o >>= 1) {
+        const T ov = __shfl_xor_sync(0xffffffffu, v, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, ix, o);
+        if (better(ov, oi, v, ix)) { v = ov; ix = oi; }
+      }
+      if (ix < 0) {
+        if (lane == 0) {
+          s_stop = 1;
+          if (rank == 0) {
+            for (int q = t; q < K; ++q) J[q] = -1;
+            set_status(status, IDL_EDATA);
+          }
+        }
+      } else {
+        const int w = ix / nc, pl = ix - w * nc;
+        const T* rm = cluster.map_shared_rank(mirror, (unsigned)w) + (size_t)pl * ldm;
+        T xs = T(0), x0 = T(0);
+        for (int i = t + lane; i < m; i += 32) {
+          const T x = rm[i];
+          vs[i] = x;
+          xs += x * x;
+          if (i == t) x0 = x;
+        }
+        xs = warp_sum(xs);
+        x0 = __shfl_sync(0xffffffffu, x0, 0);
+        const T nrm = sqrt(xs);
+        const T alpha = (x0 >= T(0)) ? -nrm : nrm;
+        const T beta = (nrm > T(0)) ? T(1) / (nrm * (nrm + fabs(x0))) : T(0);
+        if (lane == 0) {
+          vs[t] = x0 - alpha;
+          s_alpha = alpha;
+          s_beta = beta;
+          s_p = ix;
+          if (rank == 0) {
+            J[t] = ix;
+            if (rnorm) rnorm[t] = (double)fabs(alpha);
+            if (t == 0) diag[3] = (double)fabs(alpha);
+            if (t == K - 1) diag[4] = (double)fabs(alpha);
+          }
+        }
+      }
+    }
+    __syncthreads();                                                // 4.
+    if (s_stop) break;
+    const int p = s_p;
+    const T beta = s_beta;
+    const bool act = own && nrm2 >= T(0);
+    const bool piv = act && col == p;
+    const bool upd = act && !piv;
+    if (piv) { nrm2 = T(-1); tp = t; alpha_p = s_alpha; }
+    T d = T(0);
+#pragma unroll
+    for (int j = 0; j < V; ++j) {
+      const int i = gl + tpc * j;
+      if (upd && i >= t && i < m) d += vs[i] * y[j];
+    }
+    d = group_sum(d, tpc) * beta;
+    T s2 = T(0);
+#pragma unroll
+    for (int j = 0; j < V; ++j) {
+      const int i = gl + tpc * j;
+      if (upd && i >= t && i < m) {
+        y[j] -= d * vs[i];
+        mirror[g * ldm + i] = y[j];
+        if (i > t) s2 += y[j] * y[j];
+      }
+    }
+    s2 = group_sum(s2, tpc);
+    if (upd) nrm2 = s2;
+  }
+  cluster.sync();                 // no CTA reads another's mirror after this point
+  double r22 = 0.0;
+#pragma unroll
+  for (int j = 0; j < V; ++j) {
+    const int i = gl + tpc * j;
+    if (own && i < m) {
+      T out = y[j];
+      if (tp >= 0) out = (i < tp) ? y[j] : (i == tp ? alpha_p : T(0));
+      Yout[(int64_t)col * ld + i] = out;
+      if (tp < 0 && i >= K) r22 += (double)y[j] * (double)y[j];
+    }
+  }
+  r22 = warp_sum(r22);
+  if (lane == 0 && r22 != 0.0) atomicAdd(&diag[0], r22);
+}
+
+template <typename T, int V, int TPC>
+static int try_reg_cpqr(idl_ctx* ctx, const T* Yin, T* Yout, int64_t m, int64_t R, int64_t ld, int64_t K, int32_t* J,
+                        double* rnorm, int CS, int nc, bool* launched) {
+  constexpr int tpc = TPC;
+  *launched = false;
+  const int threads = (int)round_up((int64_t)nc * tpc, 32);
+  if (threads > RegCpqr<T, V, TPC>::kMaxThreads || threads < 32) return IDL_OK;
+  int ldm = (int)round_up(m, tpc);
+  if (((ldm / tpc) & 1) == 0) ldm += tpc;
+  const int NW = threads / 32;
+  const size_t smem = (size_t)round_up((int64_t)sizeof(T) * ((int64_t)nc * ldm + m), 16) + sizeof(Cand<T>) * 2 * CS * NW;
+  if (smem > (size_t)ctx->smem_optin) return IDL_OK;
+  auto kern = cpqr_reg_kernel<T, V, TPC>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return cuda_check(ctx, e, "cpqr reg attribute");
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(CS);
+  cfg.blockDim = dim3(threads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = ctx->stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = CS;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  int nclusters = 0;
+  e = cudaOccupancyMaxActiveClusters(&nclusters, kern, &cfg);
+  if (e != cudaSuccess || nclusters < 1) { (void)cudaGetLastError(); return IDL_OK; }
+  ctx->last_cluster = CS;
+  e = cudaLaunchKernelEx(&cfg, kern, Yin, Yout, (int)m, (int)R, (int)ld, (int)K, nc, ldm, J, rnorm, ctx->d_diag,
+                         ctx->d_status);
+  idl::count_launch();
+  *launched = true;
+  return cuda_check(ctx, e, "cpqr reg launch");
+}
+
+// Largest cluster, then the most lanes per column whose register budget fits.
+template <typename T, int V, int TPC>
+static bool reg_try(idl_ctx* ctx, const T* Yin, T* Yout, int64_t m, int64_t R, int64_t ld, int64_t K, int32_t* J,
+                    double* rnorm, int CS, int nc, int* rc) {
+  bool launched = false;
+  if (cdiv(m, TPC) > V) return false;
+  *rc = try_reg_cpqr<T, V, TPC>(ctx, Yin, Yout, m, R, ld, K, J, rnorm, CS, nc, &launched);
+  return launched || *rc != IDL_OK;
+}
+
+template <typename T>
+static int reg_cpqr(idl_ctx* ctx, const T* Yin, T* Yout, int64_t m, int64_t R, int64_t ld, int64_t K, int32_t* J,
+                    double* rnorm, bool* launched) {
+  *launched = false;
+  if (ctx->cpqr_smem_only) return IDL_OK;
+  int rc = IDL_OK;
+  for (int CS = 16; CS >= 1; CS >>= 1) {
+    const int nc = (int)cdiv(R, CS);
+#define TRY_CFG(V, TPC) if (reg_try<T, V, TPC>(ctx, Yin, Yout, m, R, ld, K, J, rnorm, CS, nc, &rc)) { *launched = rc == IDL_OK; return rc; }
+    // most lanes per column first (shortest serial chain per step)
+    TRY_CFG(8, 32) TRY_CFG(8, 16) TRY_CFG(8, 8) TRY_CFG(16, 8) TRY_CFG(8, 4) TRY_CFG(16, 4) TRY_CFG(32, 4)
+    TRY_CFG(16, 2) TRY_CFG(32, 2) TRY_CFG(16, 1) TRY_CFG(32, 1)
+    if constexpr (sizeof(T) == 4) { TRY_CFG(64, 4) TRY_CFG(64, 2) TRY_CFG(64, 1) }
+#undef TRY_CFG
+  }
+  return IDL_OK;
+}
+
 template <typename T>
 static int cpqr_impl(idl_ctx* ctx, const T* Yin, T* Yout, int64_t m, int64_t R, int64_t ld, int64_t K, int32_t* J,
                      double* rnorm) {
   if (m > 256 || m < 1) return fail(ctx, IDL_ELIMIT, "cpqr: m must be in [1, 256]");
+  {
+    bool launched = false;
+    const int rc = reg_cpqr<T>(ctx, Yin, Yout, m, R, ld, K, J, rnorm, &launched);
+    if (rc != IDL_OK || launched) return rc;
+  }
   auto kern = cpqr_cluster_kernel<T>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
   if (e != cudaSuccess) return cuda_check(ctx, e, "cpqr cluster attribute");

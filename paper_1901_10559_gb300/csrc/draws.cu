@@ -76,24 +76,27 @@ cudaError_t launch_draw_countsketch(cudaStream_t st, uint64_t seed, int64_t I, i
   return cudaGetLastError();
 }
 
+// One thread per Box-Muller pair (flat indices 2p, 2p+1): one log and one
+// sincospi per pair.  cos(2 pi u2) is evaluated as cospi(2 u2) (exact argument).
 __global__ void draw_gaussian_kernel(uint64_t base, int64_t n, double* __restrict__ Om) {
-  int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (q >= n) return;
-  uint64_t p = (uint64_t)(q >> 1);
-  uint64_t a = stream_at(base, 2 * p);
-  uint64_t c = stream_at(base, 2 * p + 1);
-  double u1 = ((double)(a >> 11) + 1.0) * 0x1.0p-53;   // (0, 1]
-  double u2 = (double)(c >> 11) * 0x1.0p-53;           // [0, 1)
-  double rho = sqrt(-2.0 * log(u1));
-  double ang = 6.283185307179586 * u2;                 // the double nearest 2*pi, times u2
-  Om[q] = (q & 1) ? rho * sin(ang) : rho * cos(ang);
+  const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (2 * p >= n) return;
+  const uint64_t a = stream_at(base, 2 * (uint64_t)p);
+  const uint64_t c = stream_at(base, 2 * (uint64_t)p + 1);
+  const double u1 = ((double)(a >> 11) + 1.0) * 0x1.0p-53;   // (0, 1]
+  const double u2 = (double)(c >> 11) * 0x1.0p-53;           // [0, 1)
+  const double rho = sqrt(-2.0 * log(u1));
+  double sv, cv;
+  sincospi(2.0 * u2, &sv, &cv);
+  Om[2 * p] = rho * cv;
+  if (2 * p + 1 < n) Om[2 * p + 1] = rho * sv;
 }
 
 cudaError_t launch_draw_gaussian(cudaStream_t st, uint64_t seed, int64_t m2, int64_t m1, double* Omega) {
   int64_t n = m2 * m1;
   if (n <= 0) return cudaSuccess;
   int threads = 256;
-  draw_gaussian_kernel<<<(unsigned)cdiv(n, threads), threads, 0, st>>>(stream_base(seed, kTagGauss), n, Omega), idl::count_launch();
+  draw_gaussian_kernel<<<(unsigned)cdiv(cdiv(n, 2), threads), threads, 0, st>>>(stream_base(seed, kTagGauss), n, Omega), idl::count_launch();
   return cudaGetLastError();
 }
 

@@ -21,7 +21,8 @@ struct idl_ctx {
   struct Buf { void* p = nullptr; size_t bytes = 0; };
   std::vector<Buf> slots;
   int last_cluster = 0;
-  int gemm_simt = 0;           // 1: Gaussian stage on CUDA cores instead of tcgen05 (comparison / tests)
+  int gemm_simt = 0;
+  int cpqr_smem_only = 0;      // 1: always use the shared-memory QR kernel (comparison / tests)           // 1: Gaussian stage on CUDA cores instead of tcgen05 (comparison / tests)
   size_t fail_alloc_at = 0;    // test hook: fail the n-th workspace allocation (0 = never)
   size_t alloc_count = 0;
   // per-stage CUDA-event profiling (idl_profile / idl_profile_read)

@@ -41,8 +41,9 @@ def test_gaussian_draws(ctx):
         want = odr.gaussian_matrix(seed, m2, m1)
         got = host(Om).reshape(m2, m1)
         assert np.abs(got - want).max() <= 1e-13 * max(1.0, np.abs(want).max())
-        # the fp32 working copy rounds identically
-        assert np.array_equal(got.astype(np.float32), want.astype(np.float32))
+        # the fp32 working copies agree to one fp32 ulp (the FP64 values differ in the last bits)
+        g32, w32 = got.astype(np.float32), want.astype(np.float32)
+        assert np.all(np.abs(g32 - w32) <= np.spacing(np.abs(w32)))
 
 
 def test_mode_draws(ctx):
@@ -273,4 +274,30 @@ def test_gaussian_tc_shapes_and_simt_agreement(ctx, m2, m1, R):
         assert rel_fro(outs[0], want) <= tol, (prec, rel_fro(outs[0], want))
         if prec == idl.PREC_FP32:
             assert rel_fro(outs[0], outs[1]) <= 2 * FP32_TOL
+    assert ctx.sync() == idl.IDL_OK
+
+
+@pytest.mark.parametrize("dtype,m,R,K", [("f32", 60, 10000, 50), ("f32", 120, 4096, 100), ("f64", 30, 2000, 20),
+                                         ("f32", 60, 1000, 50), ("f32", 200, 700, 150), ("f64", 7, 3, 3)])
+def test_cpqr_register_and_shared_memory_kernels_agree(ctx, dtype, m, R, K):
+    rng = np.random.default_rng(m + R)
+    npdt = np.float32 if dtype == "f32" else np.float64
+    Y = (rng.standard_normal((m, R)) * rng.uniform(0.2, 5.0, R)[None, :]).astype(npdt)
+    dt = idl.IDL_F32 if dtype == "f32" else idl.IDL_F64
+    outs = []
+    for smem_only in (0, 1):
+        idl.lib().idl_debug_cpqr_path(ctx.ptr, smem_only)
+        Yd = dev(np.ascontiguousarray(Y.T))
+        J = torch.empty(K, dtype=torch.int32, device="cuda")
+        idl.idl_cpqr(ctx, Yd, m, R, m, dt, K, J)
+        outs.append((host(J), host(Yd).reshape(R, m).T.astype(np.float64)))
+    idl.lib().idl_debug_cpqr_path(ctx.ptr, 0)
+    (J0, F0), (J1, F1) = outs
+    Jw, _, info = ocp.matrix_id(Y.astype(np.float64), K)
+    if pivots_well_separated(info["gaps"]):
+        assert np.array_equal(J0, Jw) and np.array_equal(J1, Jw)
+    if np.array_equal(J0, J1):
+        # the same reflections up to rounding: rows 0..K-1 of the factor agree
+        tol = 1e-3 if dtype == "f32" else 1e-10
+        assert np.abs(F0[:K] - F1[:K]).max() <= tol * np.abs(F1[:K]).max()
     assert ctx.sync() == idl.IDL_OK
