@@ -233,18 +233,18 @@ cpqr_cluster_kernel(const T* __restrict__ Yin, T* __restrict__ Yout, int m, int 
 // of TPC lanes keeps one column in registers (rows gl, gl + TPC, ...).  Per
 // pivot step:
 //   1. block argmax of the remaining norms (warp shuffles, one block barrier);
-//      warp 0 pushes the CTA's candidate into every CTA's table (DSMEM stores)
-//      and, after a second block barrier, the owning group copies that
-//      column's trailing part into a double-buffered staging slot;
+//      warp 0 publishes the CTA's candidate in its own shared memory and,
+//      after a second block barrier, the owning group copies that column's
+//      trailing part into a double-buffered staging slot;
 //   2. one hardware cluster barrier;
-//   3. warp 0 of every CTA reduces the table (same result everywhere), pulls
-//      the winner's staged column over DSMEM and forms the Householder
-//      reflection (v in shared memory);
+//   3. warp 0 of every CTA pulls the CS candidates (one DSMEM load per lane),
+//      reduces them (same result everywhere), pulls the winner's staged
+//      column and forms the Householder reflection (v in shared memory);
 //   4. one block barrier; every group applies the reflection to its column in
 //      registers and recomputes the trailing norm exactly.
 // Measured on GB300: cluster barrier ~580 cycles, DSMEM pull of a column
-// ~450, block barrier ~130; pushing from every warp instead of once per CTA
-// cost ~1800 cycles more per step.
+// ~450, block barrier ~130; remote stores before the barrier (a push model)
+// made its release wait ~2000 cycles, so candidates are pulled instead.
 // ----------------------------------------------------------------------------
 // Threads per CTA each (type, values per lane, lanes per column) variant is
 // compiled for: sized so the column registers fit without spilling.
@@ -271,13 +271,14 @@ cpqr_reg_kernel(const T* __restrict__ Yin, T* __restrict__ Yout, int m, int R, i
 
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* stage = (T*)smem_raw;                                          // [2][m] staged candidate column
-  T* vs = stage + 2 * m;                                            // m
-  Cand<T>* cand = (Cand<T>*)(smem_raw + round_up((int64_t)sizeof(T) * 3 * m, 16));   // [2][CS]
+  T* vs = stage + 2 * m;                                            // V*TPC: v, zero outside rows [t, m)
+  Cand<T>* cand = (Cand<T>*)(smem_raw + round_up((int64_t)sizeof(T) * (2 * m + V * TPC), 16));   // [2]
   __shared__ T red_v[32];
   __shared__ int red_i[32];
   __shared__ T s_beta, s_alpha;
   __shared__ int s_p, s_stop, s_best;
   if (tid == 0) s_stop = 0;
+  for (int i = tid; i < V * TPC; i += blockDim.x) vs[i] = T(0);
 
   T y[V];
 #pragma unroll
@@ -318,11 +319,10 @@ cpqr_reg_kernel(const T* __restrict__ Yin, T* __restrict__ Yout, int m, int R, i
         const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
         if (better(ov, oi, bv, bi)) { bv = ov; bi = oi; }
       }
-      if (lane == 0) s_best = bi;
-      if (lane < CS) {
-        Cand<T>* dst = cluster.map_shared_rank(cand + (t & 1) * CS + rank, (unsigned)lane);
-        dst->val = bv;
-        dst->idx = bi;
+      if (lane == 0) {
+        s_best = bi;
+        cand[t & 1].val = bv;          // published locally; the other CTAs pull it after the barrier
+        cand[t & 1].idx = bi;
       }
     }
     __syncthreads();
@@ -339,7 +339,11 @@ cpqr_reg_kernel(const T* __restrict__ Yin, T* __restrict__ Yout, int m, int R, i
     if (wid == 0) {
       T v = T(-1);
       int ix = -1;
-      if (lane < CS) { v = cand[(t & 1) * CS + lane].val; ix = cand[(t & 1) * CS + lane].idx; }
+      if (lane < CS) {
+        const Cand<T>* rc = cluster.map_shared_rank(cand + (t & 1), (unsigned)lane);
+        v = rc->val;
+        ix = rc->idx;
+      }
 #pragma unroll
       for (int o = 16; o; o >>= 1) {
         const T ov = __shfl_xor_sync(0xffffffffu, v, o);
@@ -356,6 +360,7 @@ cpqr_reg_kernel(const T* __restrict__ Yin, T* __restrict__ Yout, int m, int R, i
         }
       } else {
         const int w = ix / nc;
+        if (lane == 0 && t > 0) vs[t - 1] = T(0);                    // rows above t stay zero
         const T* rm = cluster.map_shared_rank(stage + (t & 1) * m, (unsigned)w);
         T xs = T(0), x0 = T(0);
         for (int i = t + lane; i < m; i += 32) {
@@ -391,23 +396,26 @@ cpqr_reg_kernel(const T* __restrict__ Yin, T* __restrict__ Yout, int m, int R, i
     const bool piv = act && col == p;
     const bool upd = act && !piv;
     if (piv) { nrm2 = T(-1); tp = t; alpha_p = s_alpha; }
-    T d = T(0);
+    // vs is zero outside rows [t, m): no per-row predicates in the dot product and the update
+    T d0 = T(0), d1 = T(0);
+#pragma unroll
+    for (int j = 0; j < V; j += 2) {
+      d0 = fma(vs[gl + tpc * j], y[j], d0);
+      if (j + 1 < V) d1 = fma(vs[gl + tpc * (j + 1)], y[j + 1], d1);
+    }
+    T d = group_sum(d0 + d1, tpc) * beta;
+    if (!upd) d = T(0);
+    __syncwarp();   // re-read v below instead of keeping all of it in registers
+    // trailing norm over rows > t: rows gl + tpc*j with j >= jt
+    const int jt = (t - gl) >= 0 ? (t - gl) / tpc + 1 : 0;
+    T s0 = T(0), s1 = T(0);
 #pragma unroll
     for (int j = 0; j < V; ++j) {
-      const int i = gl + tpc * j;
-      if (upd && i >= t && i < m) d += vs[i] * y[j];
+      y[j] = fma(-d, vs[gl + tpc * j], y[j]);
+      const T q = (j >= jt) ? y[j] * y[j] : T(0);
+      if (j & 1) s1 += q; else s0 += q;
     }
-    d = group_sum(d, tpc) * beta;
-    T s2 = T(0);
-#pragma unroll
-    for (int j = 0; j < V; ++j) {
-      const int i = gl + tpc * j;
-      if (upd && i >= t && i < m) {
-        y[j] -= d * vs[i];
-        if (i > t) s2 += y[j] * y[j];
-      }
-    }
-    s2 = group_sum(s2, tpc);
+    const T s2 = group_sum(s0 + s1, tpc);
     if (upd) nrm2 = s2;
   }
   cluster.sync();                 // no CTA reads another's staging slot after this point
@@ -427,13 +435,18 @@ cpqr_reg_kernel(const T* __restrict__ Yin, T* __restrict__ Yout, int m, int R, i
 }
 
 template <typename T, int V, int TPC>
+__host__ __device__ constexpr size_t reg_cpqr_smem(int m) {
+  return (size_t)(((int64_t)sizeof(T) * (2 * m + V * TPC) + 15) / 16 * 16) + sizeof(Cand<T>) * 2;
+}
+
+template <typename T, int V, int TPC>
 static int try_reg_cpqr(idl_ctx* ctx, const T* Yin, T* Yout, int64_t m, int64_t R, int64_t ld, int64_t K, int32_t* J,
                         double* rnorm, int CS, int nc, bool* launched) {
   constexpr int tpc = TPC;
   *launched = false;
   const int threads = (int)round_up((int64_t)nc * tpc, 32);
   if (threads > RegCpqr<T, V, TPC>::kMaxThreads || threads < 32) return IDL_OK;
-  const size_t smem = (size_t)round_up((int64_t)sizeof(T) * 3 * m, 16) + sizeof(Cand<T>) * 2 * CS;
+  const size_t smem = reg_cpqr_smem<T, V, TPC>((int)m);
   if (smem > (size_t)ctx->smem_optin) return IDL_OK;
   auto kern = cpqr_reg_kernel<T, V, TPC>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
