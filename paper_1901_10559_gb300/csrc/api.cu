@@ -263,7 +263,8 @@ extern "C" int idl_debug_fail_alloc(idl_ctx* ctx, int nth) {
 }
 extern "C" int idl_debug_gemm_path(idl_ctx* ctx, int simt) {
   if (!ctx) return IDL_EINVAL;
-  ctx->gemm_simt = simt != 0;
+  ctx->gemm_simt = simt == 1;
+  ctx->gemm_sync_loads = simt == 2;
   return IDL_OK;
 }
 extern "C" int idl_debug_cpqr_path(idl_ctx* ctx, int smem_only) {

@@ -18,8 +18,10 @@
 //   BF16   : hi*hi                                (1 product,  8-bit operands)
 //   BF16X3 : hi*hi + hi*lo + lo*hi   (2 planes)   (3 products, ~16-bit operands)
 //   FP32   : hh + hm + mh + hl + mm + lh  (3 planes: the terms above 2^-24)
-// Two pipeline stages: the loads of K block i+1 are in flight while block i is
-// multiplied.  Every mbarrier wait is bounded (1 s); on a timeout the kernel
+// Y1 tiles arrive by cp.async.bulk (one copy per row of 128 columns) into a
+// two-slot FP32 staging ring, two K blocks ahead of the conversion; rows not
+// 16-byte aligned fall back to register loads one block ahead.  Two stages of
+// bf16 planes let the MMAs of block i run while block i+1 is converted.  Every mbarrier wait is bounded (1 s); on a timeout the kernel
 // records IDL_ETIMEOUT, waits (bounded) for the MMAs it issued, frees TMEM
 // and returns.
 #include <cuda_bf16.h>
@@ -196,9 +198,10 @@ __host__ __device__ constexpr int prod_b(int np, int q) {
 template <int NP>
 __global__ void __launch_bounds__(tc::kThreads, 1)
 gauss_tc_kernel(const float* __restrict__ Y1, int64_t ldy1, int64_t R, int64_t m1, const __nv_bfloat16* __restrict__ Bpl,
-                int NT, int NTc, int kb_per_cta, int nkb, float* __restrict__ part, int* status) {
+                int NT, int NTc, int kb_per_cta, int nkb, float* __restrict__ part, int* status, int async_a) {
   // NT: rows of the Omega^T planes (= columns of part); this CTA computes columns
-  // [blockIdx.z * NTc, +NTc) of D
+  // [blockIdx.z * NTc, +NTc) of D.  async_a: Y1 tiles arrive by cp.async.bulk into an
+  // FP32 staging ring (needs 16-byte aligned rows) instead of register loads.
   using namespace tc;
   extern __shared__ unsigned char smem_raw[];
   unsigned char* sm = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -207,10 +210,12 @@ gauss_tc_kernel(const float* __restrict__ Y1, int64_t ldy1, int64_t R, int64_t m
   const int n0 = blockIdx.z * NTc;
   unsigned char* A = sm;                               // [stage][plane] a_plane
   unsigned char* B = A + kStages * NP * a_plane;       // [stage][plane] b_plane
-  uint64_t* bars = (uint64_t*)(B + kStages * NP * b_plane);
+  float* Sg = (float*)(B + kStages * NP * b_plane);    // [slot][kBK rows][kBM] FP32 staging (async_a)
+  uint64_t* bars = (uint64_t*)((unsigned char*)Sg + (async_a ? kStages * kBK * kBM * 4 : 0));
   uint64_t* mma_done = bars;                           // [2]
   uint64_t* b_full = bars + 2;                         // [2]
-  uint32_t* tmem_slot = (uint32_t*)(bars + 4);
+  uint64_t* a_full = bars + 4;                         // [2]
+  uint32_t* tmem_slot = (uint32_t*)(bars + 6);
   __shared__ int s_flag;
 
   const int tid = threadIdx.x, warp = tid >> 5;
@@ -225,6 +230,8 @@ gauss_tc_kernel(const float* __restrict__ Y1, int64_t ldy1, int64_t R, int64_t m
     mbar_init(&mma_done[1], 1);
     mbar_init(&b_full[0], 1);
     mbar_init(&b_full[1], 1);
+    mbar_init(&a_full[0], 1);
+    mbar_init(&a_full[1], 1);
     fence_barrier_init();
     s_flag = 0;
   }
@@ -260,12 +267,46 @@ gauss_tc_kernel(const float* __restrict__ Y1, int64_t ldy1, int64_t R, int64_t m
         }
       }
     };
-    load_block(kb0);
+    // async path: warp 0 copies the tile's rows (each <= 512 contiguous bytes) into staging slot sl
+    const int cnt = (int)min((int64_t)kBM, R - r0);
+    const uint32_t row_bytes = (uint32_t)(((cnt * 4) + 15) & ~15);
+    auto fetch_a = [&](int kb, int sl) {           // called by all lanes of warp 0
+      const int64_t b0 = (int64_t)kb * kBK;
+      const int rows = (int)min((int64_t)kBK, m1 - b0);
+      if ((tid & 31) == 0) mbar_expect_tx(&a_full[sl], row_bytes * (uint32_t)rows);
+      __syncwarp();
+      for (int rr = tid & 31; rr < rows; rr += 32)
+        bulk_g2s(Sg + ((size_t)sl * kBK + rr) * kBM, Y1 + (b0 + rr) * ldy1 + r0, row_bytes, &a_full[sl]);
+    };
+    int a_issued = 0, a_done = 0, b_issued = 1, b_done = 0;   // fills issued / completed (for the cleanup)
+    if (async_a) {
+      if (warp == 0) {
+        fetch_a(kb0, 0);
+        if (nk > 1) fetch_a(kb0 + 1, 1);
+      }
+      a_issued = nk > 1 ? 2 : 1;
+    } else {
+      load_block(kb0);
+    }
     int last_commit = -1;
     const uint32_t idesc = idesc_bf16(NTc);
     for (int i = 0; i < nk; ++i) {
       const int s = i & 1;
       if (i >= 2 && !mbar_wait(&mma_done[s], ((i - 2) >> 1) & 1)) s_flag = 1;     // stage s free
+      if (async_a) {
+        if (!mbar_wait(&a_full[s], (i >> 1) & 1)) s_flag = 1; else a_done = i + 1;
+        const float* sg = Sg + (size_t)s * kBK * kBM;
+        const int64_t b0 = (int64_t)(kb0 + i) * kBK;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          const int kc = kq + 2 * c;
+#pragma unroll
+          for (int e = 0; e < 8; ++e) {
+            const int rr = kc * 8 + e;
+            v[c][e] = (b0 + rr < m1) ? sg[rr * kBM + m] : 0.f;
+          }
+        }
+      }
       unsigned char* As = A + (size_t)s * NP * a_plane;
 #pragma unroll
       for (int c = 0; c < 4; ++c) {
@@ -282,14 +323,19 @@ gauss_tc_kernel(const float* __restrict__ Y1, int64_t ldy1, int64_t R, int64_t m
         for (int p = 0; p < NP; ++p) *(uint4*)(As + (size_t)p * a_plane + sw128_off(m, kc)) = *(const uint4*)pl[p];
       }
       fence_async_smem();
-      if (i + 1 < nk) load_block(kb0 + i + 1);         // next block's loads overlap this block's MMAs
+      if (!async_a && i + 1 < nk) load_block(kb0 + i + 1);   // next block's loads overlap this block's MMAs
       __syncthreads();
       if (s_flag) break;
+      if (async_a && i + 2 < nk) {
+        if (warp == 0) fetch_a(kb0 + i + 2, s);   // slot s was read by everyone above
+        a_issued = i + 3;
+      }
       if (tid == 0) {
         tc_fence_after();
         if (!mbar_wait(&b_full[s], (i >> 1) & 1)) {
           s_flag = 1;
         } else {
+          b_done = i + 1;
           const unsigned char* Bs = B + (size_t)s * NP * b_plane;
 #pragma unroll
           for (int ks = 0; ks < kBK / 16; ++ks) {
@@ -308,6 +354,7 @@ gauss_tc_kernel(const float* __restrict__ Y1, int64_t ldy1, int64_t R, int64_t m
               s_flag = 1;
             } else {
               fetch_b(kb0 + i + 1, s ^ 1);
+              b_issued = i + 2;
             }
           }
         }
@@ -316,6 +363,11 @@ gauss_tc_kernel(const float* __restrict__ Y1, int64_t ldy1, int64_t R, int64_t m
     // wait for the last MMAs this CTA issued (bounded), then read the accumulator
     if (tid == 0 && last_commit >= 0) {
       if (!mbar_wait(&mma_done[last_commit & 1], (last_commit >> 1) & 1)) s_flag = 2;
+    }
+    // after an early exit, wait (bounded) for the bulk copies still in flight into shared memory
+    if (tid == 0) {
+      for (int j = a_done; j < a_issued; ++j) (void)mbar_wait(&a_full[j & 1], (j >> 1) & 1);
+      for (int j = b_done; j < b_issued; ++j) (void)mbar_wait(&b_full[j & 1], (j >> 1) & 1);
     }
     if (tid == 0 && last_commit < nk - 1) s_flag = s_flag ? s_flag : 1;
     __syncthreads();
@@ -353,7 +405,11 @@ static int tc_impl(idl_ctx* ctx, const double* Omega, int64_t m2, int64_t m1, co
   // N chunks: the widest chunk (multiple of 16, <= 256) whose two stages fit in shared memory
   const int NT0 = (int)round_up(m2, 16);
   int nz = 1, NTc = NT0;
-  auto smem_for = [&](int ntc) { return 1024 + kStages * NP * (a_plane + (size_t)ntc * kBK * 2) + 64; };
+  const int async_a = ((uintptr_t)Y1 % 16 == 0) && (ldy1 % 4 == 0) && !ctx->gemm_sync_loads;
+  const size_t stage_bytes = async_a ? (size_t)kStages * kBK * kBM * 4 : 0;
+  auto smem_for = [&](int ntc) {
+    return 1024 + kStages * NP * (a_plane + (size_t)ntc * kBK * 2) + stage_bytes + 64;
+  };
   while (smem_for(NTc) > (size_t)ctx->smem_optin && NTc > 16) {
     ++nz;
     NTc = (int)round_up(cdiv(NT0, nz), 16);
@@ -380,7 +436,7 @@ static int tc_impl(idl_ctx* ctx, const double* Omega, int64_t m2, int64_t m1, co
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return cuda_check(ctx, e, "gaussian tc attribute");
   dim3 grid((unsigned)mtiles, (unsigned)splits, (unsigned)nz);
-  k<<<grid, kThreads, smem, ctx->stream>>>(Y1, ldy1, R, m1, Bpl, NT, NTc, kbpc, nkb, part, ctx->d_status),
+  k<<<grid, kThreads, smem, ctx->stream>>>(Y1, ldy1, R, m1, Bpl, NT, NTc, kbpc, nkb, part, ctx->d_status, async_a),
       count_launch();
   e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_check(ctx, e, "gaussian tc");

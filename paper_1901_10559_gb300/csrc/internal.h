@@ -22,6 +22,7 @@ struct idl_ctx {
   std::vector<Buf> slots;
   int last_cluster = 0;
   int gemm_simt = 0;
+  int gemm_sync_loads = 0;     // 1: Gaussian tc stage loads Y1 through registers (comparison / tests)
   int cpqr_smem_only = 0;      // 1: always use the shared-memory QR kernel (comparison / tests)           // 1: Gaussian stage on CUDA cores instead of tcgen05 (comparison / tests)
   size_t fail_alloc_at = 0;    // test hook: fail the n-th workspace allocation (0 = never)
   size_t alloc_count = 0;
