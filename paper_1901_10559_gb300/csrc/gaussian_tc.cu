@@ -18,10 +18,11 @@
 //   BF16   : hi*hi                                (1 product,  8-bit operands)
 //   BF16X3 : hi*hi + hi*lo + lo*hi   (2 planes)   (3 products, ~16-bit operands)
 //   FP32   : hh + hm + mh + hl + mm + lh  (3 planes: the terms above 2^-24)
-// Y1 tiles arrive by cp.async.bulk (one copy per row of 128 columns) into a
-// two-slot FP32 staging ring, two K blocks ahead of the conversion; rows not
-// 16-byte aligned fall back to register loads one block ahead.  Two stages of
-// bf16 planes let the MMAs of block i run while block i+1 is converted.  Every mbarrier wait is bounded (1 s); on a timeout the kernel
+// Warp-specialised pipeline (measured: with one block-wide barrier per K block
+// and the MMA issue on a converter thread, ncu showed ~25% barrier stalls and
+// the tensor pipe active 16% of the time): eight converter warps and one
+// MMA/producer warp hand over two stages of A planes and a 3-slot ring of
+// Omega^T planes through mbarriers only.  Every mbarrier wait is bounded (1 s); on a timeout the kernel
 // records IDL_ETIMEOUT, waits (bounded) for the MMAs it issued, frees TMEM
 // and returns.
 #include <cuda_bf16.h>
@@ -145,15 +146,27 @@ __host__ __device__ __forceinline__ uint32_t sw128_off(int row, int kc) {
   return (uint32_t)((row >> 3) * 1024 + (row & 7) * 128 + ((kc ^ (row & 7)) << 4));
 }
 
-// split x into NP bf16 terms, each the rounding of what the previous ones left
+// split x into NP bf16 terms.  NP <= 2: each term the round-to-nearest of what
+// the previous ones left (NP = 1 is the bf16 rounding the BF16 mode defines).
+// NP = 3: the top 8 mantissa bits of what is left, by truncation -- three terms
+// then hold all 24 bits of x exactly, and each step is one AND and one FSUB.
 template <int NP>
 __device__ __forceinline__ void split_bf16(float x, __nv_bfloat16* out) {
   float r = x;
+  if constexpr (NP == 3) {
 #pragma unroll
-  for (int p = 0; p < NP; ++p) {
-    const __nv_bfloat16 b = __float2bfloat16_rn(r);
-    out[p] = b;
-    r = r - __bfloat162float(b);
+    for (int p = 0; p < NP; ++p) {
+      const uint32_t hb = __float_as_uint(r) & 0xFFFF0000u;
+      out[p] = __ushort_as_bfloat16((unsigned short)(hb >> 16));
+      r = r - __uint_as_float(hb);
+    }
+  } else {
+#pragma unroll
+    for (int p = 0; p < NP; ++p) {
+      const __nv_bfloat16 b = __float2bfloat16_rn(r);
+      out[p] = b;
+      r = r - __bfloat162float(b);
+    }
   }
 }
 
@@ -195,13 +208,20 @@ __host__ __device__ constexpr int prod_b(int np, int q) {
   return np == 1 ? 0 : (np == 2 ? (q == 1 ? 1 : 0) : (q == 0 ? 0 : q == 1 ? 1 : q == 2 ? 2 : q == 3 ? 0 : q == 4 ? 1 : 0));
 }
 
+// Warp-specialised: warps 0-7 convert (load FP32 Y1 one K block ahead in
+// registers, split into bf16 planes, store them swizzled, arrive on a_ready);
+// warp 8 feeds Omega^T planes through a 3-slot ring of bulk copies and one of
+// its lanes issues the MMAs.  Stages are handed over with mbarriers only.
+constexpr int kConvThreads = 256;
+constexpr int kTcThreads = kConvThreads + 32;
+constexpr int kBSlots = 3;
+
 template <int NP>
-__global__ void __launch_bounds__(tc::kThreads, 1)
+__global__ void __launch_bounds__(kTcThreads, 1)
 gauss_tc_kernel(const float* __restrict__ Y1, int64_t ldy1, int64_t R, int64_t m1, const __nv_bfloat16* __restrict__ Bpl,
-                int NT, int NTc, int kb_per_cta, int nkb, float* __restrict__ part, int* status, int async_a) {
+                int NT, int NTc, int kb_per_cta, int nkb, float* __restrict__ part, int* status) {
   // NT: rows of the Omega^T planes (= columns of part); this CTA computes columns
-  // [blockIdx.z * NTc, +NTc) of D.  async_a: Y1 tiles arrive by cp.async.bulk into an
-  // FP32 staging ring (needs 16-byte aligned rows) instead of register loads.
+  // [blockIdx.z * NTc, +NTc) of D for K blocks [blockIdx.y * kb_per_cta, ...).
   using namespace tc;
   extern __shared__ unsigned char smem_raw[];
   unsigned char* sm = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -209,16 +229,16 @@ gauss_tc_kernel(const float* __restrict__ Y1, int64_t ldy1, int64_t R, int64_t m
   const int b_plane = NTc * kBK * 2;
   const int n0 = blockIdx.z * NTc;
   unsigned char* A = sm;                               // [stage][plane] a_plane
-  unsigned char* B = A + kStages * NP * a_plane;       // [stage][plane] b_plane
-  float* Sg = (float*)(B + kStages * NP * b_plane);    // [slot][kBK rows][kBM] FP32 staging (async_a)
-  uint64_t* bars = (uint64_t*)((unsigned char*)Sg + (async_a ? kStages * kBK * kBM * 4 : 0));
-  uint64_t* mma_done = bars;                           // [2]
-  uint64_t* b_full = bars + 2;                         // [2]
-  uint64_t* a_full = bars + 4;                         // [2]
-  uint32_t* tmem_slot = (uint32_t*)(bars + 6);
+  unsigned char* B = A + kStages * NP * a_plane;       // [slot][plane] b_plane
+  uint64_t* bars = (uint64_t*)(B + kBSlots * NP * b_plane);
+  uint64_t* a_ready = bars;                            // [kStages] 256 converter arrivals
+  uint64_t* mma_done = bars + 2;                       // [kStages] tcgen05.commit
+  uint64_t* b_full = bars + 4;                         // [kBSlots] bulk-copy bytes
+  uint64_t* b_free = bars + 7;                         // [kBSlots] tcgen05.commit
+  uint32_t* tmem_slot = (uint32_t*)(bars + 10);
   __shared__ int s_flag;
 
-  const int tid = threadIdx.x, warp = tid >> 5;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int64_t r0 = (int64_t)blockIdx.x * kBM;
   const int kb0 = blockIdx.y * kb_per_cta;
   const int nk = min(nkb, kb0 + kb_per_cta) - kb0;
@@ -226,12 +246,8 @@ gauss_tc_kernel(const float* __restrict__ Y1, int64_t ldy1, int64_t R, int64_t m
   while ((int)tcols < NTc) tcols <<= 1;
 
   if (tid == 0) {
-    mbar_init(&mma_done[0], 1);
-    mbar_init(&mma_done[1], 1);
-    mbar_init(&b_full[0], 1);
-    mbar_init(&b_full[1], 1);
-    mbar_init(&a_full[0], 1);
-    mbar_init(&a_full[1], 1);
+    for (int q = 0; q < kStages; ++q) { mbar_init(&a_ready[q], kConvThreads); mbar_init(&mma_done[q], 1); }
+    for (int q = 0; q < kBSlots; ++q) { mbar_init(&b_full[q], 1); mbar_init(&b_free[q], 1); }
     fence_barrier_init();
     s_flag = 0;
   }
@@ -240,18 +256,18 @@ gauss_tc_kernel(const float* __restrict__ Y1, int64_t ldy1, int64_t R, int64_t m
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
-  if (nk <= 0) goto cleanup;
-  {
-    const uint32_t b_bytes = (uint32_t)(NP * b_plane);
-    // the NP planes' row chunks [n0, n0 + NTc) of K block kb into B stage st
-    auto fetch_b = [&](int kb, int st) {
-      mbar_expect_tx(&b_full[st], b_bytes);
+  const uint32_t b_bytes = (uint32_t)(NP * b_plane);
+  // the NP planes' row chunks [n0, n0 + NTc) of K block kb into B slot sl
+  auto fetch_b = [&](int kb, int sl) {
+    mbar_expect_tx(&b_full[sl], b_bytes);
 #pragma unroll
-      for (int p = 0; p < NP; ++p)
-        bulk_g2s(B + (size_t)(st * NP + p) * b_plane, Bpl + ((size_t)kb * NP * NT + (size_t)p * NT + n0) * kBK,
-                 (uint32_t)b_plane, &b_full[st]);
-    };
-    if (tid == 0) fetch_b(kb0, 0);
+    for (int p = 0; p < NP; ++p)
+      bulk_g2s(B + (size_t)(sl * NP + p) * b_plane, Bpl + ((size_t)kb * NP * NT + (size_t)p * NT + n0) * kBK,
+               (uint32_t)b_plane, &b_full[sl]);
+  };
+
+  if (warp < 8) {
+    // ---------------- converters ----------------
     const int m = tid & (kBM - 1);
     const int kq = tid >> 7;                           // 0 or 1: k-chunks kq, kq+2, kq+4, kq+6
     const bool col_ok = r0 + m < R;
@@ -267,46 +283,11 @@ gauss_tc_kernel(const float* __restrict__ Y1, int64_t ldy1, int64_t R, int64_t m
         }
       }
     };
-    // async path: warp 0 copies the tile's rows (each <= 512 contiguous bytes) into staging slot sl
-    const int cnt = (int)min((int64_t)kBM, R - r0);
-    const uint32_t row_bytes = (uint32_t)(((cnt * 4) + 15) & ~15);
-    auto fetch_a = [&](int kb, int sl) {           // called by all lanes of warp 0
-      const int64_t b0 = (int64_t)kb * kBK;
-      const int rows = (int)min((int64_t)kBK, m1 - b0);
-      if ((tid & 31) == 0) mbar_expect_tx(&a_full[sl], row_bytes * (uint32_t)rows);
-      __syncwarp();
-      for (int rr = tid & 31; rr < rows; rr += 32)
-        bulk_g2s(Sg + ((size_t)sl * kBK + rr) * kBM, Y1 + (b0 + rr) * ldy1 + r0, row_bytes, &a_full[sl]);
-    };
-    int a_issued = 0, a_done = 0, b_issued = 1, b_done = 0;   // fills issued / completed (for the cleanup)
-    if (async_a) {
-      if (warp == 0) {
-        fetch_a(kb0, 0);
-        if (nk > 1) fetch_a(kb0 + 1, 1);
-      }
-      a_issued = nk > 1 ? 2 : 1;
-    } else {
-      load_block(kb0);
-    }
-    int last_commit = -1;
-    const uint32_t idesc = idesc_bf16(NTc);
+    if (nk > 0) load_block(kb0);
     for (int i = 0; i < nk; ++i) {
       const int s = i & 1;
-      if (i >= 2 && !mbar_wait(&mma_done[s], ((i - 2) >> 1) & 1)) s_flag = 1;     // stage s free
-      if (async_a) {
-        if (!mbar_wait(&a_full[s], (i >> 1) & 1)) s_flag = 1; else a_done = i + 1;
-        const float* sg = Sg + (size_t)s * kBK * kBM;
-        const int64_t b0 = (int64_t)(kb0 + i) * kBK;
-#pragma unroll
-        for (int c = 0; c < 4; ++c) {
-          const int kc = kq + 2 * c;
-#pragma unroll
-          for (int e = 0; e < 8; ++e) {
-            const int rr = kc * 8 + e;
-            v[c][e] = (b0 + rr < m1) ? sg[rr * kBM + m] : 0.f;
-          }
-        }
-      }
+      if (i >= 2 && !mbar_wait(&mma_done[s], ((i - 2) >> 1) & 1)) { s_flag = 1; break; }   // stage s free
+      if (*(volatile int*)&s_flag) break;
       unsigned char* As = A + (size_t)s * NP * a_plane;
 #pragma unroll
       for (int c = 0; c < 4; ++c) {
@@ -323,72 +304,66 @@ gauss_tc_kernel(const float* __restrict__ Y1, int64_t ldy1, int64_t R, int64_t m
         for (int p = 0; p < NP; ++p) *(uint4*)(As + (size_t)p * a_plane + sw128_off(m, kc)) = *(const uint4*)pl[p];
       }
       fence_async_smem();
-      if (!async_a && i + 1 < nk) load_block(kb0 + i + 1);   // next block's loads overlap this block's MMAs
-      __syncthreads();
-      if (s_flag) break;
-      if (async_a && i + 2 < nk) {
-        if (warp == 0) fetch_a(kb0 + i + 2, s);   // slot s was read by everyone above
-        a_issued = i + 3;
-      }
-      if (tid == 0) {
-        tc_fence_after();
-        if (!mbar_wait(&b_full[s], (i >> 1) & 1)) {
-          s_flag = 1;
-        } else {
-          b_done = i + 1;
-          const unsigned char* Bs = B + (size_t)s * NP * b_plane;
+      asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&a_ready[s])) : "memory");
+      if (i + 1 < nk) load_block(kb0 + i + 1);         // in flight while the MMA warp works
+    }
+  } else if (lane == 0) {
+    // ---------------- producer of Omega^T planes + MMA issue ----------------
+    int last_commit = -1, b_issued = 0, b_done = 0;
+    for (int q = 0; q < kBSlots && q < nk; ++q) { fetch_b(kb0 + q, q); b_issued = q + 1; }
+    const uint32_t idesc = idesc_bf16(NTc);
+    for (int i = 0; i < nk && !*(volatile int*)&s_flag; ++i) {
+      const int s = i & 1, sb = i % kBSlots;
+      if (!mbar_wait(&a_ready[s], (i >> 1) & 1)) { s_flag = 1; break; }
+      if (!mbar_wait(&b_full[sb], (i / kBSlots) & 1)) { s_flag = 1; break; }
+      b_done = i + 1;
+      tc_fence_after();
+      const unsigned char* As = A + (size_t)s * NP * a_plane;
+      const unsigned char* Bs = B + (size_t)sb * NP * b_plane;
 #pragma unroll
-          for (int ks = 0; ks < kBK / 16; ++ks) {
+      for (int ks = 0; ks < kBK / 16; ++ks) {
 #pragma unroll
-            for (int q = 0; q < n_products(NP); ++q) {
-              const uint64_t ad = sw128_desc(As + (size_t)prod_a(NP, q) * a_plane) + (uint64_t)(ks * 2);
-              const uint64_t bd = sw128_desc(Bs + (size_t)prod_b(NP, q) * b_plane) + (uint64_t)(ks * 2);
-              mma_bf16(tmem, ad, bd, idesc, (i > 0 || ks > 0 || q > 0) ? 1u : 0u);
-            }
-          }
-          mma_commit(&mma_done[s]);
-          last_commit = i;
-          // prefetch Omega^T planes of block i+1 into the other stage once its MMAs (block i-1) are done
-          if (i + 1 < nk) {
-            if (i >= 1 && !mbar_wait(&mma_done[s ^ 1], ((i - 1) >> 1) & 1)) {
-              s_flag = 1;
-            } else {
-              fetch_b(kb0 + i + 1, s ^ 1);
-              b_issued = i + 2;
-            }
-          }
+        for (int q = 0; q < n_products(NP); ++q) {
+          const uint64_t ad = sw128_desc(As + (size_t)prod_a(NP, q) * a_plane) + (uint64_t)(ks * 2);
+          const uint64_t bd = sw128_desc(Bs + (size_t)prod_b(NP, q) * b_plane) + (uint64_t)(ks * 2);
+          mma_bf16(tmem, ad, bd, idesc, (i > 0 || ks > 0 || q > 0) ? 1u : 0u);
         }
       }
+      mma_commit(&mma_done[s]);
+      mma_commit(&b_free[sb]);
+      last_commit = i;
+      // refill the B slot of block i-1 with block i+2 once block i-1's MMAs are done
+      if (i >= 1 && i + 2 < nk) {
+        const int so = (i - 1) % kBSlots;
+        if (!mbar_wait(&b_free[so], ((i - 1) / kBSlots) & 1)) { s_flag = 1; break; }
+        fetch_b(kb0 + i + 2, so);
+        b_issued = i + 3;
+      }
     }
-    // wait for the last MMAs this CTA issued (bounded), then read the accumulator
-    if (tid == 0 && last_commit >= 0) {
-      if (!mbar_wait(&mma_done[last_commit & 1], (last_commit >> 1) & 1)) s_flag = 2;
-    }
-    // after an early exit, wait (bounded) for the bulk copies still in flight into shared memory
-    if (tid == 0) {
-      for (int j = a_done; j < a_issued; ++j) (void)mbar_wait(&a_full[j & 1], (j >> 1) & 1);
-      for (int j = b_done; j < b_issued; ++j) (void)mbar_wait(&b_full[j & 1], (j >> 1) & 1);
-    }
-    if (tid == 0 && last_commit < nk - 1) s_flag = s_flag ? s_flag : 1;
-    __syncthreads();
-    tc_fence_after();
-    if (s_flag == 0) {
-      // epilogue: warp w reads TMEM lanes 32*(w%4).. (rows of D); warps 0-3 and 4-7 split the columns
-      const int lane_base = (warp & 3) * 32;
-      const int64_t r = r0 + lane_base + (tid & 31);
-      float* prow = part + ((int64_t)blockIdx.y * R + r) * NT + n0;
-      for (int q = warp >> 2; q < NTc / 16; q += 2) {
-        float vals[16];
-        tmem_ld16(tmem + ((uint32_t)lane_base << 16) + (uint32_t)(q * 16), vals);
-        if (r < R) {
+    // the accumulator is final once the last MMAs complete (bounded wait)
+    if (last_commit >= 0 && !mbar_wait(&mma_done[last_commit & 1], (last_commit >> 1) & 1)) s_flag = 2;
+    if (last_commit < nk - 1 && !s_flag) s_flag = 1;
+    // after an early exit, wait (bounded) for Omega^T copies still in flight
+    for (int j = b_done; j < b_issued; ++j) (void)mbar_wait(&b_full[j % kBSlots], (j / kBSlots) & 1);
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (s_flag == 0 && nk > 0 && warp < 8) {
+    // epilogue: warp w reads TMEM lanes 32*(w%4).. (rows of D); warps 0-3 and 4-7 split the columns
+    const int lane_base = (warp & 3) * 32;
+    const int64_t r = r0 + lane_base + lane;
+    float* prow = part + ((int64_t)blockIdx.y * R + r) * NT + n0;
+    for (int q = warp >> 2; q < NTc / 16; q += 2) {
+      float vals[16];
+      tmem_ld16(tmem + ((uint32_t)lane_base << 16) + (uint32_t)(q * 16), vals);
+      if (r < R) {
 #pragma unroll
-          for (int j = 0; j < 16; j += 4)
-            *(float4*)(prow + q * 16 + j) = make_float4(vals[j], vals[j + 1], vals[j + 2], vals[j + 3]);
-        }
+        for (int j = 0; j < 16; j += 4)
+          *(float4*)(prow + q * 16 + j) = make_float4(vals[j], vals[j + 1], vals[j + 2], vals[j + 3]);
       }
     }
   }
-cleanup:
   tc_fence_before();
   __syncthreads();
   if (tid == 0 && s_flag) set_status(status, IDL_ETIMEOUT);
@@ -405,10 +380,8 @@ static int tc_impl(idl_ctx* ctx, const double* Omega, int64_t m2, int64_t m1, co
   // N chunks: the widest chunk (multiple of 16, <= 256) whose two stages fit in shared memory
   const int NT0 = (int)round_up(m2, 16);
   int nz = 1, NTc = NT0;
-  const int async_a = ((uintptr_t)Y1 % 16 == 0) && (ldy1 % 4 == 0) && !ctx->gemm_sync_loads;
-  const size_t stage_bytes = async_a ? (size_t)kStages * kBK * kBM * 4 : 0;
   auto smem_for = [&](int ntc) {
-    return 1024 + kStages * NP * (a_plane + (size_t)ntc * kBK * 2) + stage_bytes + 64;
+    return 1024 + (size_t)kStages * NP * a_plane + (size_t)kBSlots * NP * ntc * kBK * 2 + 128;
   };
   while (smem_for(NTc) > (size_t)ctx->smem_optin && NTc > 16) {
     ++nz;
@@ -436,7 +409,7 @@ static int tc_impl(idl_ctx* ctx, const double* Omega, int64_t m2, int64_t m1, co
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return cuda_check(ctx, e, "gaussian tc attribute");
   dim3 grid((unsigned)mtiles, (unsigned)splits, (unsigned)nz);
-  k<<<grid, kThreads, smem, ctx->stream>>>(Y1, ldy1, R, m1, Bpl, NT, NTc, kbpc, nkb, part, ctx->d_status, async_a),
+  k<<<grid, kTcThreads, smem, ctx->stream>>>(Y1, ldy1, R, m1, Bpl, NT, NTc, kbpc, nkb, part, ctx->d_status),
       count_launch();
   e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_check(ctx, e, "gaussian tc");

@@ -263,7 +263,7 @@ def test_gaussian_tc_shapes_and_simt_agreement(ctx, m2, m1, R):
     Omw = odr.gaussian_matrix(5, m2, m1)
     for prec, tol in [(idl.PREC_FP32, FP32_TOL), (idl.PREC_BF16X3, 2e-5), (idl.PREC_BF16, 1e-5)]:
         outs = []
-        for simt in (0, 1, 2):          # tcgen05 with bulk-copy staging, CUDA cores, tcgen05 with register loads
+        for simt in (0, 1):             # tcgen05, CUDA cores
             idl.lib().idl_debug_gemm_path(ctx.ptr, simt)
             Y2 = torch.full((R * m2,), float("nan"), dtype=torch.float32, device="cuda")
             idl.idl_gaussian_stage(ctx, Om, m2, m1, dev(Y1), R, R, idl.IDL_F32, prec, Y2, m2)
@@ -274,8 +274,6 @@ def test_gaussian_tc_shapes_and_simt_agreement(ctx, m2, m1, R):
         assert rel_fro(outs[0], want) <= tol, (prec, rel_fro(outs[0], want))
         if prec == idl.PREC_FP32:
             assert rel_fro(outs[0], outs[1]) <= 2 * FP32_TOL
-        # same arithmetic; the two load paths may split K differently (shared memory per CTA differs)
-        assert rel_fro(outs[0], outs[2]) <= 1e-6
     assert ctx.sync() == idl.IDL_OK
 
 
