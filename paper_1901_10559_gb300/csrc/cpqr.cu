@@ -580,44 +580,86 @@ __global__ void rest_kernel(const int32_t* __restrict__ J, int K, int R, int32_t
   if (!piv && pos >= 0 && pos < R - K) rest[pos] = r;
 }
 
-constexpr int kSolveNB = 32;
 constexpr int kSolveMaxK = 128;
 
+// inv(R11) in FP64, R11 = rows 0..K-1 of the pivot columns in pivot order
+// (upper triangular).  One warp per column j of the inverse: column-oriented
+// back substitution of R11 x = e_j (x_i = b_i / u_ii, then b_k -= u_ki x_i for
+// k < i, lanes over k).  Output Rinv: K x K row-major, zero below the diagonal.
 template <typename T>
-__global__ void __launch_bounds__(256) tsolve_kernel(const T* __restrict__ Y, int ld, int K, int R,
-                                                     const int32_t* __restrict__ J,
-                                                     const int32_t* __restrict__ rest, int nrest,
-                                                     double* __restrict__ Tout) {
-  extern __shared__ __align__(16) double sm[];
+__global__ void __launch_bounds__(256) rinv_kernel(const T* __restrict__ Y, int ld, int K, int R,
+                                                   const int32_t* __restrict__ J, double* __restrict__ Rinv) {
+  extern __shared__ __align__(16) double U[];                         // K x (K+1)
   const int KP = K + 1;
-  double* U = sm;                 // K x KP   (R11, upper triangular, pivot order)
-  double* B = sm + K * KP;        // K x NB
   for (int e = threadIdx.x; e < K * K; e += blockDim.x) {
-    const int j = e / K, i = e - j * K;          // column j (pivot j), row i
+    const int j = e / K, i = e - j * K;                              // column j (pivot j), row i
     const int jj = J[j];
     U[i * KP + j] = (i <= j && jj >= 0 && jj < R) ? (double)Y[(int64_t)jj * ld + i] : 0.0;
   }
-  const int cb = blockIdx.x * kSolveNB;
-  for (int e = threadIdx.x; e < K * kSolveNB; e += blockDim.x) {
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const int nw = blockDim.x >> 5;
+  for (int j = blockIdx.x * nw + (threadIdx.x >> 5); j < K; j += gridDim.x * nw) {
+    double b[kSolveMaxK / 32];                                        // b_k for k = lane + 32 q
+#pragma unroll
+    for (int q = 0; q < kSolveMaxK / 32; ++q) b[q] = (lane + 32 * q == j) ? 1.0 : 0.0;
+    for (int i = j; i >= 0; --i) {
+      // owner lane of row i holds b_i
+      const int q = i >> 5;
+      double bi = 0.0;
+#pragma unroll
+      for (int qq = 0; qq < kSolveMaxK / 32; ++qq)
+        if (qq == q) bi = b[qq];
+      bi = __shfl_sync(0xffffffffu, bi, i & 31);
+      const double xi = bi / U[i * KP + i];
+#pragma unroll
+      for (int qq = 0; qq < kSolveMaxK / 32; ++qq) {
+        const int k = lane + 32 * qq;
+        if (k == i) b[qq] = xi;
+        else if (k < i) b[qq] -= U[k * KP + i] * xi;
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < kSolveMaxK / 32; ++q) {
+      const int k = lane + 32 * q;
+      if (k < K) Rinv[(int64_t)k * K + j] = (k <= j) ? b[q] : 0.0;
+    }
+  }
+}
+
+// T[:, c] = inv(R11) R12[:, c] for the non-skeleton columns c, FP64.  A block owns
+// 64 columns; inv(R11) and the block's R12 rows sit in shared memory; every
+// thread forms whole dot products (no sequential dependence between outputs).
+constexpr int kTNB = 64;
+template <typename T>
+__global__ void __launch_bounds__(256) tgemm_kernel(const T* __restrict__ Y, int ld, int K, int R,
+                                                    const double* __restrict__ Rinv, const int32_t* __restrict__ rest,
+                                                    int nrest, double* __restrict__ Tout) {
+  extern __shared__ __align__(16) double sh[];
+  double* Ri = sh;                         // K x K
+  double* B = sh + K * K;                  // K x (kTNB + 1)
+  const int BP = kTNB + 1;
+  for (int e = threadIdx.x; e < K * K; e += blockDim.x) Ri[e] = Rinv[e];
+  const int cb = blockIdx.x * kTNB;
+  for (int e = threadIdx.x; e < K * kTNB; e += blockDim.x) {
     const int cc = e / K, i = e - cc * K;
     const int c = cb + cc;
     const int r = (c < nrest) ? rest[c] : -1;
-    B[i * kSolveNB + cc] = (r >= 0 && r < R) ? (double)Y[(int64_t)r * ld + i] : 0.0;
+    B[i * BP + cc] = (r >= 0 && r < R) ? (double)Y[(int64_t)r * ld + i] : 0.0;
   }
   __syncthreads();
-  for (int i = K - 1; i >= 0; --i) {
-    if (threadIdx.x < kSolveNB) B[i * kSolveNB + threadIdx.x] /= U[i * KP + i];
-    __syncthreads();
-    for (int e = threadIdx.x; e < i * kSolveNB; e += blockDim.x) {
-      const int j = e / kSolveNB, cc = e - j * kSolveNB;
-      B[j * kSolveNB + cc] -= U[j * KP + i] * B[i * kSolveNB + cc];
+  // thread -> (column cc = tid % 64, rows i = tid / 64 + 4 q)
+  const int cc = threadIdx.x & (kTNB - 1);
+  const int c = cb + cc;
+  for (int i = threadIdx.x >> 6; i < K; i += blockDim.x >> 6) {
+    double acc0 = 0.0, acc1 = 0.0;
+    int k = i;
+    for (; k + 1 < K; k += 2) {
+      acc0 = fma(Ri[i * K + k], B[k * BP + cc], acc0);
+      acc1 = fma(Ri[i * K + k + 1], B[(k + 1) * BP + cc], acc1);
     }
-    __syncthreads();
-  }
-  for (int e = threadIdx.x; e < K * kSolveNB; e += blockDim.x) {
-    const int i = e / kSolveNB, cc = e - i * kSolveNB;
-    const int c = cb + cc;
-    if (c < nrest) Tout[(int64_t)i * nrest + c] = B[i * kSolveNB + cc];
+    if (k < K) acc0 = fma(Ri[i * K + k], B[k * BP + cc], acc0);
+    if (c < nrest) Tout[(int64_t)i * nrest + c] = acc0 + acc1;
   }
 }
 
@@ -630,20 +672,34 @@ int launch_t_solve(idl_ctx* ctx, const void* Y2, int64_t m, int64_t R, int64_t l
     rest = (int32_t*)ws_get(ctx, kWsRest, sizeof(int32_t) * (size_t)(R > 0 ? R : 1));
     if (!rest) return IDL_ENOMEM;
   }
-  rest_kernel<<<(unsigned)cdiv(R, 256), 256, sizeof(int32_t) * (size_t)K, ctx->stream>>>(J, (int)K, (int)R, rest), idl::count_launch();
-  if (nrest <= 0) return cuda_check(ctx, cudaGetLastError(), "rest");
-  const size_t smem = sizeof(double) * ((size_t)K * (K + 1) + (size_t)K * kSolveNB);
+  double* Rinv = (double*)ws_get(ctx, kWsRinv, sizeof(double) * (size_t)(K * K));
+  if (!Rinv) return IDL_ENOMEM;
+  rest_kernel<<<(unsigned)cdiv(R, 256), 256, sizeof(int32_t) * (size_t)K, ctx->stream>>>(J, (int)K, (int)R, rest),
+      idl::count_launch();
+  const size_t smem_inv = sizeof(double) * (size_t)K * (K + 1);
+  const size_t smem_t = sizeof(double) * ((size_t)K * K + (size_t)K * (kTNB + 1));
+  const unsigned inv_blocks = (unsigned)cdiv(K, 8);
   cudaError_t e;
   if (dtype == IDL_F32) {
-    e = cudaFuncSetAttribute(tsolve_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e == cudaSuccess)
-      tsolve_kernel<float><<<(unsigned)cdiv(nrest, kSolveNB), 256, smem, ctx->stream>>>(
-          (const float*)Y2, (int)ld, (int)K, (int)R, J, rest, (int)nrest, T), idl::count_launch();
+    e = cudaFuncSetAttribute(rinv_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_inv);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(tgemm_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_t);
+    if (e == cudaSuccess) {
+      rinv_kernel<float><<<inv_blocks, 256, smem_inv, ctx->stream>>>((const float*)Y2, (int)ld, (int)K, (int)R, J, Rinv),
+          idl::count_launch();
+      if (nrest > 0)
+        tgemm_kernel<float><<<(unsigned)cdiv(nrest, kTNB), 256, smem_t, ctx->stream>>>(
+            (const float*)Y2, (int)ld, (int)K, (int)R, Rinv, rest, (int)nrest, T), idl::count_launch();
+    }
   } else {
-    e = cudaFuncSetAttribute(tsolve_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e == cudaSuccess)
-      tsolve_kernel<double><<<(unsigned)cdiv(nrest, kSolveNB), 256, smem, ctx->stream>>>(
-          (const double*)Y2, (int)ld, (int)K, (int)R, J, rest, (int)nrest, T), idl::count_launch();
+    e = cudaFuncSetAttribute(rinv_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_inv);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(tgemm_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_t);
+    if (e == cudaSuccess) {
+      rinv_kernel<double><<<inv_blocks, 256, smem_inv, ctx->stream>>>((const double*)Y2, (int)ld, (int)K, (int)R, J,
+                                                                      Rinv), idl::count_launch();
+      if (nrest > 0)
+        tgemm_kernel<double><<<(unsigned)cdiv(nrest, kTNB), 256, smem_t, ctx->stream>>>(
+            (const double*)Y2, (int)ld, (int)K, (int)R, Rinv, rest, (int)nrest, T), idl::count_launch();
+    }
   }
   if (e != cudaSuccess) return cuda_check(ctx, e, "t_solve attribute");
   return cuda_check(ctx, cudaGetLastError(), "t_solve");

@@ -242,8 +242,10 @@ gauss_tc_kernel(const float* __restrict__ Y1, int64_t ldy1, int64_t R, int64_t m
   const int64_t r0 = (int64_t)blockIdx.x * kBM;
   const int kb0 = blockIdx.y * kb_per_cta;
   const int nk = min(nkb, kb0 + kb_per_cta) - kb0;
+  // two accumulators (columns [0, NTc) and [NTc, 2 NTc)) taken in turn, so consecutive
+  // MMAs do not depend on each other's result
   uint32_t tcols = 32;
-  while ((int)tcols < NTc) tcols <<= 1;
+  while ((int)tcols < 2 * NTc) tcols <<= 1;
 
   if (tid == 0) {
     for (int q = 0; q < kStages; ++q) { mbar_init(&a_ready[q], kConvThreads); mbar_init(&mma_done[q], 1); }
@@ -271,8 +273,9 @@ gauss_tc_kernel(const float* __restrict__ Y1, int64_t ldy1, int64_t R, int64_t m
     const int m = tid & (kBM - 1);
     const int kq = tid >> 7;                           // 0 or 1: k-chunks kq, kq+2, kq+4, kq+6
     const bool col_ok = r0 + m < R;
-    float v[4][8];
-    auto load_block = [&](int kb) {
+    // two register buffers: the loads of K block i+2 are in flight while block i is converted
+    float va[4][8], vb[4][8];
+    auto load_block = [&](float (&v)[4][8], int kb) {
 #pragma unroll
       for (int c = 0; c < 4; ++c) {
         const int kc = kq + 2 * c;
@@ -283,11 +286,11 @@ gauss_tc_kernel(const float* __restrict__ Y1, int64_t ldy1, int64_t R, int64_t m
         }
       }
     };
-    if (nk > 0) load_block(kb0);
-    for (int i = 0; i < nk; ++i) {
+    // convert block i from v into A stage i&1; false when the kernel is giving up
+    auto convert = [&](float (&v)[4][8], int i) -> bool {
       const int s = i & 1;
-      if (i >= 2 && !mbar_wait(&mma_done[s], ((i - 2) >> 1) & 1)) { s_flag = 1; break; }   // stage s free
-      if (*(volatile int*)&s_flag) break;
+      if (i >= 2 && !mbar_wait(&mma_done[s], ((i - 2) >> 1) & 1)) { s_flag = 1; return false; }   // stage s free
+      if (*(volatile int*)&s_flag) return false;
       unsigned char* As = A + (size_t)s * NP * a_plane;
 #pragma unroll
       for (int c = 0; c < 4; ++c) {
@@ -305,7 +308,16 @@ gauss_tc_kernel(const float* __restrict__ Y1, int64_t ldy1, int64_t R, int64_t m
       }
       fence_async_smem();
       asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&a_ready[s])) : "memory");
-      if (i + 1 < nk) load_block(kb0 + i + 1);         // in flight while the MMA warp works
+      return true;
+    };
+    if (nk > 0) load_block(va, kb0);
+    if (nk > 1) load_block(vb, kb0 + 1);
+    for (int i = 0; i < nk; i += 2) {
+      if (!convert(va, i)) break;
+      if (i + 2 < nk) load_block(va, kb0 + i + 2);
+      if (i + 1 >= nk) break;
+      if (!convert(vb, i + 1)) break;
+      if (i + 3 < nk) load_block(vb, kb0 + i + 3);
     }
   } else if (lane == 0) {
     // ---------------- producer of Omega^T planes + MMA issue ----------------
@@ -324,9 +336,11 @@ gauss_tc_kernel(const float* __restrict__ Y1, int64_t ldy1, int64_t R, int64_t m
       for (int ks = 0; ks < kBK / 16; ++ks) {
 #pragma unroll
         for (int q = 0; q < n_products(NP); ++q) {
+          const int u = (ks * n_products(NP) + q) & 1;           // accumulator of this MMA
           const uint64_t ad = sw128_desc(As + (size_t)prod_a(NP, q) * a_plane) + (uint64_t)(ks * 2);
           const uint64_t bd = sw128_desc(Bs + (size_t)prod_b(NP, q) * b_plane) + (uint64_t)(ks * 2);
-          mma_bf16(tmem, ad, bd, idesc, (i > 0 || ks > 0 || q > 0) ? 1u : 0u);
+          const bool first = i == 0 && ks * n_products(NP) + q < 2;
+          mma_bf16(tmem + (uint32_t)(u * NTc), ad, bd, idesc, first ? 0u : 1u);
         }
       }
       mma_commit(&mma_done[s]);
@@ -354,9 +368,16 @@ gauss_tc_kernel(const float* __restrict__ Y1, int64_t ldy1, int64_t R, int64_t m
     const int lane_base = (warp & 3) * 32;
     const int64_t r = r0 + lane_base + lane;
     float* prow = part + ((int64_t)blockIdx.y * R + r) * NT + n0;
+    const int uses = 4 * n_products(NP) * nk;        // MMAs issued; the second accumulator is used if > 1
     for (int q = warp >> 2; q < NTc / 16; q += 2) {
       float vals[16];
       tmem_ld16(tmem + ((uint32_t)lane_base << 16) + (uint32_t)(q * 16), vals);
+      if (uses > 1) {
+        float v2[16];
+        tmem_ld16(tmem + ((uint32_t)lane_base << 16) + (uint32_t)(NTc + q * 16), v2);
+#pragma unroll
+        for (int j = 0; j < 16; ++j) vals[j] += v2[j];
+      }
       if (r < R) {
 #pragma unroll
         for (int j = 0; j < 16; j += 4)
@@ -383,7 +404,8 @@ static int tc_impl(idl_ctx* ctx, const double* Omega, int64_t m2, int64_t m1, co
   auto smem_for = [&](int ntc) {
     return 1024 + (size_t)kStages * NP * a_plane + (size_t)kBSlots * NP * ntc * kBK * 2 + 128;
   };
-  while (smem_for(NTc) > (size_t)ctx->smem_optin && NTc > 16) {
+  // two accumulators of NTc columns must fit in TMEM's 512 columns: NTc <= 256 already; keep 2*NTc <= 512
+  while ((smem_for(NTc) > (size_t)ctx->smem_optin || 2 * NTc > 512) && NTc > 16) {
     ++nz;
     NTc = (int)round_up(cdiv(NT0, nz), 16);
   }

@@ -39,7 +39,7 @@ namespace idl {
 enum Slot {
   kWsH = 0, kWsS, kWsOmega, kWsBucketPtr, kWsRowList, kWsCursor, kWsBig, kWsY1, kWsPart,
   kWsY2, kWsOmegaConv, kWsRest, kWsA, kWsRowptr, kWsColidx, kWsVals, kWsJ, kWsT,
-  kWsModeH, kWsModeS, kWsLam, kWsLamHat, kWsCpqrSync, kWsCount
+  kWsModeH, kWsModeS, kWsLam, kWsLamHat, kWsCpqrSync, kWsRinv, kWsCount
 };
 
 // Returns a device buffer of at least `bytes` for the slot (grown on demand), or
