@@ -22,75 +22,20 @@
 
 #include "common.cuh"
 #include "internal.h"
+#include "sketch_dev.cuh"
 
 namespace idl {
 
 // ----------------------------------------------------------------------------
 // dense
 // ----------------------------------------------------------------------------
-template <typename T> __device__ __forceinline__ typename Vec4<T>::type ldcs_vec(const T* p);
-template <> __device__ __forceinline__ float4 ldcs_vec<float>(const float* p) { return __ldcs((const float4*)p); }
-template <> __device__ __forceinline__ double2 ldcs_vec<double>(const double* p) { return __ldcs((const double2*)p); }
-
-__device__ __forceinline__ void vadd(float4& a, const float4& v, bool neg) {
-  if (neg) { a.x -= v.x; a.y -= v.y; a.z -= v.z; a.w -= v.w; }
-  else     { a.x += v.x; a.y += v.y; a.z += v.z; a.w += v.w; }
-}
-__device__ __forceinline__ void vadd(double2& a, const double2& v, bool neg) {
-  if (neg) { a.x -= v.x; a.y -= v.y; } else { a.x += v.x; a.y += v.y; }
-}
-
 template <typename T, bool VEC>
 __global__ void __launch_bounds__(256) cs_dense_kernel(const T* __restrict__ A, int64_t lda, int64_t R,
                                                        const int8_t* __restrict__ s,
                                                        const int32_t* __restrict__ ptr,
                                                        const int32_t* __restrict__ rows, T* __restrict__ Y,
                                                        int64_t ldy, int ntiles) {
-  using V = typename Vec4<T>::type;
-  constexpr int W = 16 / sizeof(T);  // elements per vector
-  const int64_t b = blockIdx.x / ntiles;
-  const int tile = blockIdx.x % ntiles;
-  const int64_t c0 = ((int64_t)tile * blockDim.x + threadIdx.x) * W;
-  if (c0 >= R) return;
-  const int a0 = ptr[b], a1 = ptr[b + 1];
-  T* yrow = Y + b * ldy + c0;
-  if (VEC && c0 + W <= R) {
-    V acc;
-    if constexpr (W == 4) acc = make_float4(0.f, 0.f, 0.f, 0.f); else acc = make_double2(0.0, 0.0);
-    int j = a0;
-    for (; j + 4 <= a1; j += 4) {
-      const int r0 = rows[j], r1 = rows[j + 1], r2 = rows[j + 2], r3 = rows[j + 3];
-      const V v0 = ldcs_vec<T>(A + (int64_t)r0 * lda + c0);
-      const V v1 = ldcs_vec<T>(A + (int64_t)r1 * lda + c0);
-      const V v2 = ldcs_vec<T>(A + (int64_t)r2 * lda + c0);
-      const V v3 = ldcs_vec<T>(A + (int64_t)r3 * lda + c0);
-      vadd(acc, v0, s[r0] < 0);
-      vadd(acc, v1, s[r1] < 0);
-      vadd(acc, v2, s[r2] < 0);
-      vadd(acc, v3, s[r3] < 0);
-    }
-    for (; j < a1; ++j) {
-      const int r = rows[j];
-      vadd(acc, ldcs_vec<T>(A + (int64_t)r * lda + c0), s[r] < 0);
-    }
-    *(V*)yrow = acc;
-  } else {
-    const int w = (int)((R - c0) < W ? (R - c0) : W);
-    T acc[W];
-#pragma unroll
-    for (int q = 0; q < W; ++q) acc[q] = T(0);
-    for (int j = a0; j < a1; ++j) {
-      const int r = rows[j];
-      const bool neg = s[r] < 0;
-      const T* ap = A + (int64_t)r * lda + c0;
-#pragma unroll
-      for (int q = 0; q < W; ++q)
-        if (q < w) acc[q] += neg ? -ap[q] : ap[q];
-    }
-#pragma unroll
-    for (int q = 0; q < W; ++q)
-      if (q < w) yrow[q] = acc[q];
-  }
+  cs_dense_block<T, VEC>(A, lda, R, s, ptr, rows, Y, ldy, blockIdx.x / ntiles, blockIdx.x % ntiles);
 }
 
 template <typename T>

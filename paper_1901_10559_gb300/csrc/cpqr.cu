@@ -22,27 +22,11 @@
 #include <cfloat>
 
 #include "common.cuh"
+#include "cpqr_dev.cuh"
 #include "internal.h"
-
-namespace cg = cooperative_groups;
+#include "tsolve_dev.cuh"
 
 namespace idl {
-
-template <typename T> struct Cand { T val; int idx; int pad; };
-
-template <typename T>
-__device__ __forceinline__ bool better(T va, int ia, T vb, int ib) {
-  return va > vb || (va == vb && ia < ib && ia >= 0) || (ib < 0 && ia >= 0);
-}
-
-__device__ __forceinline__ float group_sum(float v, int tpc) {
-  for (int o = tpc >> 1; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
-__device__ __forceinline__ double group_sum(double v, int tpc) {
-  for (int o = tpc >> 1; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
 
 constexpr int kCpqrThreads = 1024;
 
@@ -228,215 +212,12 @@ cpqr_cluster_kernel(const T* __restrict__ Yin, T* __restrict__ Yout, int m, int 
   }
 }
 
-// ----------------------------------------------------------------------------
-// Register-resident variant (used whenever a cluster shape fits).  Each group
-// of TPC lanes keeps one column in registers (rows gl, gl + TPC, ...).  Per
-// pivot step:
-//   1. block argmax of the remaining norms (warp shuffles, one block barrier);
-//      warp 0 publishes the CTA's candidate in its own shared memory and,
-//      after a second block barrier, the owning group copies that column's
-//      trailing part into a double-buffered staging slot;
-//   2. one hardware cluster barrier;
-//   3. warp 0 of every CTA pulls the CS candidates (one DSMEM load per lane),
-//      reduces them (same result everywhere), pulls the winner's staged
-//      column and forms the Householder reflection (v in shared memory);
-//   4. one block barrier; every group applies the reflection to its column in
-//      registers and recomputes the trailing norm exactly.
-// Measured on GB300: cluster barrier ~580 cycles, DSMEM pull of a column
-// ~450, block barrier ~130; remote stores before the barrier (a push model)
-// made its release wait ~2000 cycles, so candidates are pulled instead.
-// ----------------------------------------------------------------------------
-// Threads per CTA each (type, values per lane, lanes per column) variant is
-// compiled for: sized so the column registers fit without spilling.
-template <typename T, int V, int TPC> struct RegCpqr {
-  static constexpr int kWords = V * (int)(sizeof(T) / 4);
-  static constexpr int kMaxThreads = kWords <= 16 ? 1024 : (kWords <= 32 ? (TPC == 1 ? 896 : 768)
-                                                                   : (TPC == 1 ? 640 : 512));
-};
-
 template <typename T, int V, int TPC>
 __global__ void __launch_bounds__(RegCpqr<T, V, TPC>::kMaxThreads, 1)
 cpqr_reg_kernel(const T* __restrict__ Yin, T* __restrict__ Yout, int m, int R, int ld, int K, int nc,
                 int32_t* __restrict__ J, double* __restrict__ rnorm, double* __restrict__ diag, int* status) {
-  constexpr int tpc = TPC;
-  cg::cluster_group cluster = cg::this_cluster();
-  const int CS = (int)cluster.num_blocks();
-  const int rank = (int)cluster.block_rank();
-  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, NW = blockDim.x >> 5;
-  const int g = tid / tpc, gl = tid - g * tpc;
-  const int c0 = rank * nc;
-  const int ncl = max(0, min(nc, R - c0));
-  const bool own = g < ncl;
-  const int col = c0 + g;
-
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* stage = (T*)smem_raw;                                          // [2][m] staged candidate column
-  T* vs = stage + 2 * m;                                            // V*TPC: v, zero outside rows [t, m)
-  Cand<T>* cand = (Cand<T>*)(smem_raw + round_up((int64_t)sizeof(T) * (2 * m + V * TPC), 16));   // [2]
-  __shared__ T red_v[32];
-  __shared__ int red_i[32];
-  __shared__ T s_beta, s_alpha;
-  __shared__ int s_p, s_stop, s_best;
-  if (tid == 0) s_stop = 0;
-  for (int i = tid; i < V * TPC; i += blockDim.x) vs[i] = T(0);
-
-  T y[V];
-#pragma unroll
-  for (int j = 0; j < V; ++j) {
-    const int i = gl + tpc * j;
-    y[j] = (own && i < m) ? Yin[(int64_t)col * ld + i] : T(0);
-  }
-  T nn = T(0);
-#pragma unroll
-  for (int j = 0; j < V; ++j) nn += y[j] * y[j];
-  nn = group_sum(nn, tpc);
-  {
-    double f = (own && gl == 0) ? (double)nn : 0.0;
-    f = warp_sum(f);
-    if (lane == 0 && f != 0.0) atomicAdd(&diag[1], f);
-  }
-  T nrm2 = own ? nn : T(-1);          // < 0: retired or no column
-  int tp = -1;
-  T alpha_p = T(0);
-  for (int t = 0; t < K; ++t) {
-    // 1. block candidate
-    T bv = (gl == 0 && nrm2 >= T(0)) ? nrm2 : T(-1);
-    int bi = (gl == 0 && nrm2 >= T(0)) ? col : -1;
-#pragma unroll
-    for (int o = 16; o; o >>= 1) {
-      const T ov = __shfl_xor_sync(0xffffffffu, bv, o);
-      const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-      if (better(ov, oi, bv, bi)) { bv = ov; bi = oi; }
-    }
-    if (lane == 0) { red_v[wid] = bv; red_i[wid] = bi; }
-    __syncthreads();
-    if (wid == 0) {
-      bv = lane < NW ? red_v[lane] : T(-1);
-      bi = lane < NW ? red_i[lane] : -1;
-#pragma unroll
-      for (int o = 16; o; o >>= 1) {
-        const T ov = __shfl_xor_sync(0xffffffffu, bv, o);
-        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-        if (better(ov, oi, bv, bi)) { bv = ov; bi = oi; }
-      }
-      if (lane == 0) {
-        s_best = bi;
-        cand[t & 1].val = bv;          // published locally; the other CTAs pull it after the barrier
-        cand[t & 1].idx = bi;
-      }
-    }
-    __syncthreads();
-    if (own && col == s_best) {
-      T* st = stage + (t & 1) * m;
-#pragma unroll
-      for (int j = 0; j < V; ++j) {
-        const int i = gl + tpc * j;
-        if (i >= t && i < m) st[i] = y[j];
-      }
-    }
-    cluster.sync();                                                 // 2.
-    // 3. winner, pivot column, reflection (warp 0)
-    if (wid == 0) {
-      T v = T(-1);
-      int ix = -1;
-      if (lane < CS) {
-        const Cand<T>* rc = cluster.map_shared_rank(cand + (t & 1), (unsigned)lane);
-        v = rc->val;
-        ix = rc->idx;
-      }
-#pragma unroll
-      for (int o = 16; o; o >>= 1) {
-        const T ov = __shfl_xor_sync(0xffffffffu, v, o);
-        const int oi = __shfl_xor_sync(0xffffffffu, ix, o);
-        if (better(ov, oi, v, ix)) { v = ov; ix = oi; }
-      }
-      if (ix < 0) {
-        if (lane == 0) {
-          s_stop = 1;
-          if (rank == 0) {
-            for (int q = t; q < K; ++q) J[q] = -1;
-            set_status(status, IDL_EDATA);
-          }
-        }
-      } else {
-        const int w = ix / nc;
-        if (lane == 0 && t > 0) vs[t - 1] = T(0);                    // rows above t stay zero
-        const T* rm = cluster.map_shared_rank(stage + (t & 1) * m, (unsigned)w);
-        T xs = T(0), x0 = T(0);
-        for (int i = t + lane; i < m; i += 32) {
-          const T x = rm[i];
-          vs[i] = x;
-          xs += x * x;
-          if (i == t) x0 = x;
-        }
-        xs = warp_sum(xs);
-        x0 = __shfl_sync(0xffffffffu, x0, 0);
-        const T nrm = sqrt(xs);
-        const T alpha = (x0 >= T(0)) ? -nrm : nrm;
-        const T beta = (nrm > T(0)) ? T(1) / (nrm * (nrm + fabs(x0))) : T(0);
-        if (lane == 0) {
-          vs[t] = x0 - alpha;
-          s_alpha = alpha;
-          s_beta = beta;
-          s_p = ix;
-          if (rank == 0) {
-            J[t] = ix;
-            if (rnorm) rnorm[t] = (double)fabs(alpha);
-            if (t == 0) diag[3] = (double)fabs(alpha);
-            if (t == K - 1) diag[4] = (double)fabs(alpha);
-          }
-        }
-      }
-    }
-    __syncthreads();                                                // 4.
-    if (s_stop) break;
-    const int p = s_p;
-    const T beta = s_beta;
-    const bool act = own && nrm2 >= T(0);
-    const bool piv = act && col == p;
-    const bool upd = act && !piv;
-    if (piv) { nrm2 = T(-1); tp = t; alpha_p = s_alpha; }
-    // vs is zero outside rows [t, m): no per-row predicates in the dot product and the update
-    T d0 = T(0), d1 = T(0);
-#pragma unroll
-    for (int j = 0; j < V; j += 2) {
-      d0 = fma(vs[gl + tpc * j], y[j], d0);
-      if (j + 1 < V) d1 = fma(vs[gl + tpc * (j + 1)], y[j + 1], d1);
-    }
-    T d = group_sum(d0 + d1, tpc) * beta;
-    if (!upd) d = T(0);
-    __syncwarp();   // re-read v below instead of keeping all of it in registers
-    // trailing norm over rows > t: rows gl + tpc*j with j >= jt
-    const int jt = (t - gl) >= 0 ? (t - gl) / tpc + 1 : 0;
-    T s0 = T(0), s1 = T(0);
-#pragma unroll
-    for (int j = 0; j < V; ++j) {
-      y[j] = fma(-d, vs[gl + tpc * j], y[j]);
-      const T q = (j >= jt) ? y[j] * y[j] : T(0);
-      if (j & 1) s1 += q; else s0 += q;
-    }
-    const T s2 = group_sum(s0 + s1, tpc);
-    if (upd) nrm2 = s2;
-  }
-  cluster.sync();                 // no CTA reads another's staging slot after this point
-  double r22 = 0.0;
-#pragma unroll
-  for (int j = 0; j < V; ++j) {
-    const int i = gl + tpc * j;
-    if (own && i < m) {
-      T out = y[j];
-      if (tp >= 0) out = (i < tp) ? y[j] : (i == tp ? alpha_p : T(0));
-      Yout[(int64_t)col * ld + i] = out;
-      if (tp < 0 && i >= K) r22 += (double)y[j] * (double)y[j];
-    }
-  }
-  r22 = warp_sum(r22);
-  if (lane == 0 && r22 != 0.0) atomicAdd(&diag[0], r22);
-}
-
-template <typename T, int V, int TPC>
-__host__ __device__ constexpr size_t reg_cpqr_smem(int m) {
-  return (size_t)(((int64_t)sizeof(T) * (2 * m + V * TPC) + 15) / 16 * 16) + sizeof(Cand<T>) * 2;
+  cpqr_reg_body<T, V, TPC>(Yin, Yout, m, R, ld, K, nc, J, rnorm, diag, status, smem_raw);
 }
 
 template <typename T, int V, int TPC>
@@ -567,100 +348,22 @@ __global__ void rest_kernel(const int32_t* __restrict__ J, int K, int R, int32_t
   for (int q = threadIdx.x; q < K; q += blockDim.x) sJ[q] = J[q];
   __syncthreads();
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
-  if (r >= R) return;
-  int less = 0;
-  bool piv = false;
-  for (int q = 0; q < K; ++q) {
-    const int j = sJ[q];
-    if (j < 0 || j >= R) continue;               // invalid pivots (flagged upstream) are ignored
-    less += j < r;
-    piv |= j == r;
-  }
-  const int pos = r - less;
-  if (!piv && pos >= 0 && pos < R - K) rest[pos] = r;
+  if (r < R) rest_elem(r, sJ, K, R, rest);
 }
 
-constexpr int kSolveMaxK = 128;
-
-// inv(R11) in FP64, R11 = rows 0..K-1 of the pivot columns in pivot order
-// (upper triangular).  One warp per column j of the inverse: column-oriented
-// back substitution of R11 x = e_j (x_i = b_i / u_ii, then b_k -= u_ki x_i for
-// k < i, lanes over k).  Output Rinv: K x K row-major, zero below the diagonal.
 template <typename T>
 __global__ void __launch_bounds__(256) rinv_kernel(const T* __restrict__ Y, int ld, int K, int R,
                                                    const int32_t* __restrict__ J, double* __restrict__ Rinv) {
-  extern __shared__ __align__(16) double U[];                         // K x (K+1)
-  const int KP = K + 1;
-  for (int e = threadIdx.x; e < K * K; e += blockDim.x) {
-    const int j = e / K, i = e - j * K;                              // column j (pivot j), row i
-    const int jj = J[j];
-    U[i * KP + j] = (i <= j && jj >= 0 && jj < R) ? (double)Y[(int64_t)jj * ld + i] : 0.0;
-  }
-  __syncthreads();
-  const int lane = threadIdx.x & 31;
-  const int nw = blockDim.x >> 5;
-  for (int j = blockIdx.x * nw + (threadIdx.x >> 5); j < K; j += gridDim.x * nw) {
-    double b[kSolveMaxK / 32];                                        // b_k for k = lane + 32 q
-#pragma unroll
-    for (int q = 0; q < kSolveMaxK / 32; ++q) b[q] = (lane + 32 * q == j) ? 1.0 : 0.0;
-    for (int i = j; i >= 0; --i) {
-      // owner lane of row i holds b_i
-      const int q = i >> 5;
-      double bi = 0.0;
-#pragma unroll
-      for (int qq = 0; qq < kSolveMaxK / 32; ++qq)
-        if (qq == q) bi = b[qq];
-      bi = __shfl_sync(0xffffffffu, bi, i & 31);
-      const double xi = bi / U[i * KP + i];
-#pragma unroll
-      for (int qq = 0; qq < kSolveMaxK / 32; ++qq) {
-        const int k = lane + 32 * qq;
-        if (k == i) b[qq] = xi;
-        else if (k < i) b[qq] -= U[k * KP + i] * xi;
-      }
-    }
-#pragma unroll
-    for (int q = 0; q < kSolveMaxK / 32; ++q) {
-      const int k = lane + 32 * q;
-      if (k < K) Rinv[(int64_t)k * K + j] = (k <= j) ? b[q] : 0.0;
-    }
-  }
+  extern __shared__ __align__(16) double U[];
+  rinv_block<T>(Y, ld, K, R, J, Rinv, blockIdx.x, gridDim.x, U);
 }
 
-// T[:, c] = inv(R11) R12[:, c] for the non-skeleton columns c, FP64.  A block owns
-// 64 columns; inv(R11) and the block's R12 rows sit in shared memory; every
-// thread forms whole dot products (no sequential dependence between outputs).
-constexpr int kTNB = 64;
 template <typename T>
 __global__ void __launch_bounds__(256) tgemm_kernel(const T* __restrict__ Y, int ld, int K, int R,
                                                     const double* __restrict__ Rinv, const int32_t* __restrict__ rest,
                                                     int nrest, double* __restrict__ Tout) {
   extern __shared__ __align__(16) double sh[];
-  double* Ri = sh;                         // K x K
-  double* B = sh + K * K;                  // K x (kTNB + 1)
-  const int BP = kTNB + 1;
-  for (int e = threadIdx.x; e < K * K; e += blockDim.x) Ri[e] = Rinv[e];
-  const int cb = blockIdx.x * kTNB;
-  for (int e = threadIdx.x; e < K * kTNB; e += blockDim.x) {
-    const int cc = e / K, i = e - cc * K;
-    const int c = cb + cc;
-    const int r = (c < nrest) ? rest[c] : -1;
-    B[i * BP + cc] = (r >= 0 && r < R) ? (double)Y[(int64_t)r * ld + i] : 0.0;
-  }
-  __syncthreads();
-  // thread -> (column cc = tid % 64, rows i = tid / 64 + 4 q)
-  const int cc = threadIdx.x & (kTNB - 1);
-  const int c = cb + cc;
-  for (int i = threadIdx.x >> 6; i < K; i += blockDim.x >> 6) {
-    double acc0 = 0.0, acc1 = 0.0;
-    int k = i;
-    for (; k + 1 < K; k += 2) {
-      acc0 = fma(Ri[i * K + k], B[k * BP + cc], acc0);
-      acc1 = fma(Ri[i * K + k + 1], B[(k + 1) * BP + cc], acc1);
-    }
-    if (k < K) acc0 = fma(Ri[i * K + k], B[k * BP + cc], acc0);
-    if (c < nrest) Tout[(int64_t)i * nrest + c] = acc0 + acc1;
-  }
+  tgemm_block<T>(Y, ld, K, R, Rinv, rest, nrest, Tout, blockIdx.x, sh);
 }
 
 int launch_t_solve(idl_ctx* ctx, const void* Y2, int64_t m, int64_t R, int64_t ld, int dtype, int64_t K,
@@ -766,21 +469,7 @@ int launch_residual(idl_ctx* ctx, const void* Y2orig, const void* Y2fact, int64_
 // ----------------------------------------------------------------------------
 __global__ void lambda_hat_kernel(const double* __restrict__ lam, const int32_t* __restrict__ J,
                                   const double* __restrict__ Tm, int nrest, double* __restrict__ out) {
-  __shared__ double part[32];
-  const int k = blockIdx.x;
-  double s = 0.0;
-  for (int c = threadIdx.x; c < nrest; c += blockDim.x) s += Tm[(int64_t)k * nrest + c];
-  s = warp_sum(s);
-  if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = s;
-  __syncthreads();
-  if (threadIdx.x < 32) {
-    s = threadIdx.x < (blockDim.x >> 5) ? part[threadIdx.x] : 0.0;
-    s = warp_sum(s);
-    if (threadIdx.x == 0) {
-      const int j = J[k];
-      out[k] = (j >= 0 && j < nrest + (int)gridDim.x) ? lam[j] * (1.0 + s) : 0.0;
-    }
-  }
+  lambda_hat_block(lam, J, Tm, nrest, (int)gridDim.x, out, blockIdx.x);
 }
 
 int launch_lambda_hat(idl_ctx* ctx, const double* lambda, const int32_t* J, const double* T, int64_t K, int64_t R,

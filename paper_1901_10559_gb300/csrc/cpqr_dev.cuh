@@ -1,0 +1,241 @@
+// cpqr_dev.cuh -- device bodies of the pivoted QR stage, shared by the
+// single-problem kernels (cpqr.cu) and the batched ones (batch.cu).
+#pragma once
+
+#include <cooperative_groups.h>
+
+#include "common.cuh"
+
+namespace idl {
+
+namespace cg = cooperative_groups;
+
+template <typename T> struct Cand { T val; int idx; int pad; };
+
+template <typename T>
+__device__ __forceinline__ bool better(T va, int ia, T vb, int ib) {
+  return va > vb || (va == vb && ia < ib && ia >= 0) || (ib < 0 && ia >= 0);
+}
+
+__device__ __forceinline__ float group_sum(float v, int tpc) {
+  for (int o = tpc >> 1; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ double group_sum(double v, int tpc) {
+  for (int o = tpc >> 1; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// ----------------------------------------------------------------------------
+// Register-resident variant (used whenever a cluster shape fits).  Each group
+// of TPC lanes keeps one column in registers (rows gl, gl + TPC, ...).  Per
+// pivot step:
+//   1. block argmax of the remaining norms (warp shuffles, one block barrier);
+//      warp 0 publishes the CTA's candidate in its own shared memory and,
+//      after a second block barrier, the owning group copies that column's
+//      trailing part into a double-buffered staging slot;
+//   2. one hardware cluster barrier;
+//   3. warp 0 of every CTA pulls the CS candidates (one DSMEM load per lane),
+//      reduces them (same result everywhere), pulls the winner's staged
+//      column and forms the Householder reflection (v in shared memory);
+//   4. one block barrier; every group applies the reflection to its column in
+//      registers and recomputes the trailing norm exactly.
+// Measured on GB300: cluster barrier ~580 cycles, DSMEM pull of a column
+// ~450, block barrier ~130; remote stores before the barrier (a push model)
+// made its release wait ~2000 cycles, so candidates are pulled instead.
+// ----------------------------------------------------------------------------
+// Threads per CTA each (type, values per lane, lanes per column) variant is
+// compiled for: sized so the column registers fit without spilling.
+template <typename T, int V, int TPC> struct RegCpqr {
+  static constexpr int kWords = V * (int)(sizeof(T) / 4);
+  static constexpr int kMaxThreads = kWords <= 16 ? 1024 : (kWords <= 32 ? (TPC == 1 ? 896 : 768)
+                                                                   : (TPC == 1 ? 640 : 512));
+};
+
+// Body of one cluster working on one problem (Yin/Yout m x R column-major, ld);
+// smem_raw: the dynamic shared memory (reg_cpqr_smem bytes).
+template <typename T, int V, int TPC>
+__device__ __forceinline__ void cpqr_reg_body(const T* __restrict__ Yin, T* __restrict__ Yout, int m, int R, int ld,
+                                              int K, int nc, int32_t* __restrict__ J, double* __restrict__ rnorm,
+                                              double* __restrict__ diag, int* status, unsigned char* smem_raw) {
+  constexpr int tpc = TPC;
+  cg::cluster_group cluster = cg::this_cluster();
+  const int CS = (int)cluster.num_blocks();
+  const int rank = (int)cluster.block_rank();
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, NW = blockDim.x >> 5;
+  const int g = tid / tpc, gl = tid - g * tpc;
+  const int c0 = rank * nc;
+  const int ncl = max(0, min(nc, R - c0));
+  const bool own = g < ncl;
+  const int col = c0 + g;
+
+  T* stage = (T*)smem_raw;                                          // [2][m] staged candidate column
+  T* vs = stage + 2 * m;                                            // V*TPC: v, zero outside rows [t, m)
+  Cand<T>* cand = (Cand<T>*)(smem_raw + round_up((int64_t)sizeof(T) * (2 * m + V * TPC), 16));   // [2]
+  __shared__ T red_v[32];
+  __shared__ int red_i[32];
+  __shared__ T s_beta, s_alpha;
+  __shared__ int s_p, s_stop, s_best;
+  if (tid == 0) s_stop = 0;
+  for (int i = tid; i < V * TPC; i += blockDim.x) vs[i] = T(0);
+
+  T y[V];
+#pragma unroll
+  for (int j = 0; j < V; ++j) {
+    const int i = gl + tpc * j;
+    y[j] = (own && i < m) ? Yin[(int64_t)col * ld + i] : T(0);
+  }
+  T nn = T(0);
+#pragma unroll
+  for (int j = 0; j < V; ++j) nn += y[j] * y[j];
+  nn = group_sum(nn, tpc);
+  {
+    double f = (own && gl == 0) ? (double)nn : 0.0;
+    f = warp_sum(f);
+    if (lane == 0 && f != 0.0) atomicAdd(&diag[1], f);
+  }
+  T nrm2 = own ? nn : T(-1);          // < 0: retired or no column
+  int tp = -1;
+  T alpha_p = T(0);
+  for (int t = 0; t < K; ++t) {
+    // 1. block candidate
+    T bv = (gl == 0 && nrm2 >= T(0)) ? nrm2 : T(-1);
+    int bi = (gl == 0 && nrm2 >= T(0)) ? col : -1;
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+      const T ov = __shfl_xor_sync(0xffffffffu, bv, o);
+      const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+      if (better(ov, oi, bv, bi)) { bv = ov; bi = oi; }
+    }
+    if (lane == 0) { red_v[wid] = bv; red_i[wid] = bi; }
+    __syncthreads();
+    if (wid == 0) {
+      bv = lane < NW ? red_v[lane] : T(-1);
+      bi = lane < NW ? red_i[lane] : -1;
+#pragma unroll
+      for (int o = 16; o; o >>= 1) {
+        const T ov = __shfl_xor_sync(0xffffffffu, bv, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        if (better(ov, oi, bv, bi)) { bv = ov; bi = oi; }
+      }
+      if (lane == 0) {
+        s_best = bi;
+        cand[t & 1].val = bv;          // published locally; the other CTAs pull it after the barrier
+        cand[t & 1].idx = bi;
+      }
+    }
+    __syncthreads();
+    if (own && col == s_best) {
+      T* st = stage + (t & 1) * m;
+#pragma unroll
+      for (int j = 0; j < V; ++j) {
+        const int i = gl + tpc * j;
+        if (i >= t && i < m) st[i] = y[j];
+      }
+    }
+    cluster.sync();                                                 // 2.
+    // 3. winner, pivot column, reflection (warp 0)
+    if (wid == 0) {
+      T v = T(-1);
+      int ix = -1;
+      if (lane < CS) {
+        const Cand<T>* rc = cluster.map_shared_rank(cand + (t & 1), (unsigned)lane);
+        v = rc->val;
+        ix = rc->idx;
+      }
+#pragma unroll
+      for (int o = 16; o; o >>= 1) {
+        const T ov = __shfl_xor_sync(0xffffffffu, v, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, ix, o);
+        if (better(ov, oi, v, ix)) { v = ov; ix = oi; }
+      }
+      if (ix < 0) {
+        if (lane == 0) {
+          s_stop = 1;
+          if (rank == 0) {
+            for (int q = t; q < K; ++q) J[q] = -1;
+            set_status(status, IDL_EDATA);
+          }
+        }
+      } else {
+        const int w = ix / nc;
+        if (lane == 0 && t > 0) vs[t - 1] = T(0);                    // rows above t stay zero
+        const T* rm = cluster.map_shared_rank(stage + (t & 1) * m, (unsigned)w);
+        T xs = T(0), x0 = T(0);
+        for (int i = t + lane; i < m; i += 32) {
+          const T x = rm[i];
+          vs[i] = x;
+          xs += x * x;
+          if (i == t) x0 = x;
+        }
+        xs = warp_sum(xs);
+        x0 = __shfl_sync(0xffffffffu, x0, 0);
+        const T nrm = sqrt(xs);
+        const T alpha = (x0 >= T(0)) ? -nrm : nrm;
+        const T beta = (nrm > T(0)) ? T(1) / (nrm * (nrm + fabs(x0))) : T(0);
+        if (lane == 0) {
+          vs[t] = x0 - alpha;
+          s_alpha = alpha;
+          s_beta = beta;
+          s_p = ix;
+          if (rank == 0) {
+            J[t] = ix;
+            if (rnorm) rnorm[t] = (double)fabs(alpha);
+            if (t == 0) diag[3] = (double)fabs(alpha);
+            if (t == K - 1) diag[4] = (double)fabs(alpha);
+          }
+        }
+      }
+    }
+    __syncthreads();                                                // 4.
+    if (s_stop) break;
+    const int p = s_p;
+    const T beta = s_beta;
+    const bool act = own && nrm2 >= T(0);
+    const bool piv = act && col == p;
+    const bool upd = act && !piv;
+    if (piv) { nrm2 = T(-1); tp = t; alpha_p = s_alpha; }
+    // vs is zero outside rows [t, m): no per-row predicates in the dot product and the update
+    T d0 = T(0), d1 = T(0);
+#pragma unroll
+    for (int j = 0; j < V; j += 2) {
+      d0 = fma(vs[gl + tpc * j], y[j], d0);
+      if (j + 1 < V) d1 = fma(vs[gl + tpc * (j + 1)], y[j + 1], d1);
+    }
+    T d = group_sum(d0 + d1, tpc) * beta;
+    if (!upd) d = T(0);
+    __syncwarp();   // re-read v below instead of keeping all of it in registers
+    // trailing norm over rows > t: rows gl + tpc*j with j >= jt
+    const int jt = (t - gl) >= 0 ? (t - gl) / tpc + 1 : 0;
+    T s0 = T(0), s1 = T(0);
+#pragma unroll
+    for (int j = 0; j < V; ++j) {
+      y[j] = fma(-d, vs[gl + tpc * j], y[j]);
+      const T q = (j >= jt) ? y[j] * y[j] : T(0);
+      if (j & 1) s1 += q; else s0 += q;
+    }
+    const T s2 = group_sum(s0 + s1, tpc);
+    if (upd) nrm2 = s2;
+  }
+  cluster.sync();                 // no CTA reads another's staging slot after this point
+  double r22 = 0.0;
+#pragma unroll
+  for (int j = 0; j < V; ++j) {
+    const int i = gl + tpc * j;
+    if (own && i < m) {
+      T out = y[j];
+      if (tp >= 0) out = (i < tp) ? y[j] : (i == tp ? alpha_p : T(0));
+      Yout[(int64_t)col * ld + i] = out;
+      if (tp < 0 && i >= K) r22 += (double)y[j] * (double)y[j];
+    }
+  }
+  r22 = warp_sum(r22);
+  if (lane == 0 && r22 != 0.0) atomicAdd(&diag[0], r22);
+}
+
+template <typename T, int V, int TPC>
+__host__ __device__ constexpr size_t reg_cpqr_smem(int m) {
+  return (size_t)(((int64_t)sizeof(T) * (2 * m + V * TPC) + 15) / 16 * 16) + sizeof(Cand<T>) * 2;
+}
+
+}  // namespace idl

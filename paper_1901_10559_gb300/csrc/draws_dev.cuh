@@ -1,0 +1,201 @@
+// draws_dev.cuh -- device bodies of the draws and of the bucket-offset build,
+// shared by the single-problem kernels (draws.cu) and the batched ones (batch.cu).
+#pragma once
+
+#include "common.cuh"
+
+namespace idl {
+
+struct FeistelKeys { uint64_t k[kFeistelRounds]; };
+
+__device__ __forceinline__ uint64_t feistel(uint64_t x, int half, uint64_t mask, const FeistelKeys& K) {
+  uint64_t l = x >> half, r = x & mask;
+#pragma unroll
+  for (int j = 0; j < kFeistelRounds; ++j) {
+    uint64_t f = mix64(K.k[j] ^ r) & mask;
+    uint64_t nl = r;
+    r = l ^ f;
+    l = nl;
+  }
+  return (l << half) | r;
+}
+
+// Arguments of the CountSketch draw of one problem (host-computed).
+struct CsDrawArgs {
+  uint64_t bucket_base, sign_base, mask;
+  FeistelKeys keys;
+  int half;
+};
+
+inline int feistel_width_host(int64_t I) {
+  int w = 1;
+  while (w < 62 && ((int64_t)1 << w) < I) ++w;
+  if (w & 1) ++w;
+  return w < 2 ? 2 : w;
+}
+
+inline CsDrawArgs make_cs_draw_args(uint64_t seed, int64_t I) {
+  CsDrawArgs a;
+  const uint64_t pb = stream_base(seed, kTagPerm);
+  for (int r = 0; r < kFeistelRounds; ++r) a.keys.k[r] = stream_at(pb, (uint64_t)r);
+  const int w = feistel_width_host(I);
+  a.half = w / 2;
+  a.mask = (1ull << a.half) - 1;
+  a.bucket_base = stream_base(seed, kTagBucket);
+  a.sign_base = stream_base(seed, kTagSign);
+  return a;
+}
+
+// h[i], s[i] of a CountSketch (plain or modified, Remark 2)
+__device__ __forceinline__ void cs_draw_elem(int64_t i, const CsDrawArgs& a, int64_t I, int64_t L, int modified,
+                                             int32_t* __restrict__ h, int8_t* __restrict__ s, int* status) {
+  const uint32_t x = bounded(stream_at(a.bucket_base, (uint64_t)i), (uint64_t)L);
+  uint32_t hv = x;
+  if (modified) {
+    uint64_t y = feistel((uint64_t)i, a.half, a.mask, a.keys);
+    // Cycle walking ends: i lies on a finite cycle of the bijection on [0, 2^w)
+    // and i < I.  The cap only guards against corrupted arguments.
+    int walks = 0;
+    while (y >= (uint64_t)I && walks < (1 << 22)) { y = feistel(y, a.half, a.mask, a.keys); ++walks; }
+    if (y >= (uint64_t)I) { set_status(status, IDL_ETIMEOUT); y = 0; }
+    if (y < (uint64_t)L) hv = (uint32_t)y;
+  }
+  h[i] = (int32_t)hv;
+  s[i] = (stream_at(a.sign_base, (uint64_t)i) >> 63) ? (int8_t)-1 : (int8_t)1;
+}
+
+// Box-Muller pair p (flat indices 2p, 2p+1) of Omega; cos(2 pi u2) as cospi(2 u2)
+__device__ __forceinline__ void gauss_pair(int64_t p, uint64_t base, int64_t n, double* __restrict__ Om) {
+  const uint64_t a = stream_at(base, 2 * (uint64_t)p);
+  const uint64_t c = stream_at(base, 2 * (uint64_t)p + 1);
+  const double u1 = ((double)(a >> 11) + 1.0) * 0x1.0p-53;   // (0, 1]
+  const double u2 = (double)(c >> 11) * 0x1.0p-53;           // [0, 1)
+  const double rho = sqrt(-2.0 * log(u1));
+  double sv, cv;
+  sincospi(2.0 * u2, &sv, &cv);
+  Om[2 * p] = rho * cv;
+  if (2 * p + 1 < n) Om[2 * p + 1] = rho * sv;
+}
+
+// TensorSketch map of one mode entry
+__device__ __forceinline__ void mode_elem(int64_t i, uint64_t hb, uint64_t sb, int64_t L, int32_t* __restrict__ h,
+                                          int8_t* __restrict__ s) {
+  h[i] = (int32_t)bounded(stream_at(hb, (uint64_t)i), (uint64_t)L);
+  s[i] = (stream_at(sb, (uint64_t)i) >> 63) ? (int8_t)-1 : (int8_t)1;
+}
+
+// ---------------------------------------------------------------------------
+// Bucket offsets: histogram, exclusive scan, atomic scatter, per-bucket rank sort
+// ---------------------------------------------------------------------------
+constexpr int kHistSmem = 12288;     // buckets histogrammed in shared memory first
+constexpr int kWarpSortCap = 1024;   // rows per bucket sorted by one warp
+constexpr int kBlockSortCap = 12288; // rows per bucket sorted by one block
+
+// block `blk` of `nblk` (grid-stride over rows); sh: >= L ints of shared memory when L <= kHistSmem
+__device__ __forceinline__ void bucket_hist_body(const int32_t* __restrict__ h, int64_t I, int64_t L,
+                                                 int32_t* __restrict__ cnt, int* status, int64_t blk, int64_t nblk,
+                                                 int32_t* sh) {
+  const bool local = L <= kHistSmem;
+  if (local) {
+    for (int64_t b = threadIdx.x; b < L; b += blockDim.x) sh[b] = 0;
+    __syncthreads();
+  }
+  for (int64_t i = blk * blockDim.x + threadIdx.x; i < I; i += nblk * blockDim.x) {
+    const int b = h[i];
+    if (b < 0 || (int64_t)b >= L) { set_status(status, IDL_EDATA); continue; }   // caller-supplied h out of range
+    if (local) atomicAdd(&sh[b], 1); else atomicAdd(&cnt[b], 1);
+  }
+  if (local) {
+    __syncthreads();
+    for (int64_t b = threadIdx.x; b < L; b += blockDim.x)
+      if (sh[b]) atomicAdd(&cnt[b], sh[b]);
+  }
+}
+
+// one block: exclusive scan of cnt[0..L) into ptr[0..L] and the scatter cursor
+// (cnt and cursor may alias: each thread reads cnt[b] before it writes cursor[b])
+__device__ __forceinline__ void bucket_scan_body(const int32_t* cnt, int64_t L, int32_t* __restrict__ ptr,
+                                                 int32_t* cursor) {
+  __shared__ int32_t warp_tot[32];
+  __shared__ int32_t carry;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int64_t base = 0; base < L; base += blockDim.x) {
+    int64_t b = base + threadIdx.x;
+    int32_t v = b < L ? cnt[b] : 0;
+    int32_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      int32_t y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) warp_tot[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+      int32_t t = lane < nw ? warp_tot[lane] : 0;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        int32_t y = __shfl_up_sync(0xffffffffu, t, o);
+        if (lane >= o) t += y;
+      }
+      if (lane < nw) warp_tot[lane] = t;  // inclusive warp prefix
+    }
+    __syncthreads();
+    int32_t excl = carry + (wid ? warp_tot[wid - 1] : 0) + x - v;
+    if (b < L) { ptr[b] = excl; cursor[b] = excl; }
+    __syncthreads();
+    if (threadIdx.x == blockDim.x - 1) carry = excl + v;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) ptr[L] = carry;
+}
+
+__device__ __forceinline__ void bucket_scatter_elem(int64_t i, const int32_t* __restrict__ h, int64_t L,
+                                                    int32_t* __restrict__ cursor, int32_t* __restrict__ row_list) {
+  const int b = h[i];
+  if (b < 0 || (int64_t)b >= L) return;        // flagged by the histogram pass
+  const int pos = atomicAdd(&cursor[b], 1);
+  row_list[pos] = (int32_t)i;
+}
+
+// one warp, bucket b: rank sort of its rows (distinct, so rank = #smaller); buckets
+// above kWarpSortCap go to the `big` list for a block.  seg: kWarpSortCap ints.
+__device__ __forceinline__ void bucket_sort_warp_body(const int32_t* __restrict__ ptr, int64_t b,
+                                                      int32_t* __restrict__ row_list, int32_t* __restrict__ big,
+                                                      int32_t* __restrict__ nbig, int32_t* seg) {
+  const int lane = threadIdx.x & 31;
+  const int a0 = ptr[b], n = ptr[b + 1] - a0;
+  if (n <= 1) return;
+  if (n > kWarpSortCap) {
+    if (lane == 0) big[atomicAdd(nbig, 1)] = (int32_t)b;
+    return;
+  }
+  for (int j = lane; j < n; j += 32) seg[j] = row_list[a0 + j];
+  __syncwarp();
+  for (int j = lane; j < n; j += 32) {
+    const int x = seg[j];
+    int rank = 0;
+    for (int t = 0; t < n; ++t) rank += seg[t] < x;
+    row_list[a0 + rank] = x;
+  }
+}
+
+// one block: rank sort of the rows of bucket b (up to kBlockSortCap; larger ones
+// stay in arrival order).  seg: kBlockSortCap ints.
+__device__ __forceinline__ void bucket_sort_block_body(const int32_t* __restrict__ ptr, int32_t b,
+                                                       int32_t* __restrict__ row_list, int32_t* seg) {
+  const int a0 = ptr[b], n = ptr[b + 1] - a0;
+  if (n > kBlockSortCap) return;
+  __syncthreads();
+  for (int j = threadIdx.x; j < n; j += blockDim.x) seg[j] = row_list[a0 + j];
+  __syncthreads();
+  for (int j = threadIdx.x; j < n; j += blockDim.x) {
+    const int x = seg[j];
+    int rank = 0;
+    for (int t = 0; t < n; ++t) rank += seg[t] < x;
+    row_list[a0 + rank] = x;
+  }
+}
+
+}  // namespace idl

@@ -31,365 +31,30 @@
 #include <algorithm>
 
 #include "common.cuh"
+#include "gemm_dev.cuh"
 #include "internal.h"
 
 namespace idl {
 
-namespace tc {
-
-constexpr int kThreads = 256;
-constexpr int kBM = 128;        // rows of D (columns r of Y1) per CTA
-constexpr int kBK = 64;         // K per stage (one 128-byte swizzle atom of bf16)
-constexpr int kStages = 2;
-constexpr uint64_t kTimeoutNs = 1000000000ull;
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ uint64_t global_timer() {
-  uint64_t t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
-  uint32_t done;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-      "selp.u32 %0, 1, 0, p;\n\t}"
-      : "=r"(done)
-      : "r"(smem_u32(bar)), "r"(parity)
-      : "memory");
-  return done != 0;
-}
-
-// Bounded wait: true when the phase of the given parity completed, false after ~1 s.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
-  if (mbar_try_wait(bar, parity)) return true;
-  const uint64_t t0 = global_timer();
-  while (true) {
-    if (mbar_try_wait(bar, parity)) return true;
-    if (global_timer() - t0 > kTimeoutNs) return false;
-  }
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
-}
-
-__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
-  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                   smem_u32(dst)),
-               "l"(src), "r"(bytes), "r"(smem_u32(bar))
-               : "memory");
-}
-
-__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
-__device__ __forceinline__ void fence_barrier_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
-__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-
-__device__ __forceinline__ void tmem_alloc(uint32_t* slot, uint32_t ncols) {
-  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(slot)), "r"(ncols)
-               : "memory");
-  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-}
-__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
-  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
-}
-
-__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
-                                         uint32_t accum) {
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "setp.ne.b32 p, %4, 0;\n\t"
-      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
-      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accum)
-      : "memory");
-}
-
-__device__ __forceinline__ void mma_commit(uint64_t* bar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
-               : "memory");
-}
-
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
-  uint32_t r[16];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
-        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int q = 0; q < 16; ++q) v[q] = __uint_as_float(r[q]);
-}
-
-// K-major operand, 128-byte swizzle: 8-row atoms of 1024 B, rows 128 B apart.
-__device__ __forceinline__ uint64_t sw128_desc(const void* base) {
-  const uint32_t a = smem_u32(base);
-  return (uint64_t)((a >> 4) & 0x3FFF) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) | ((uint64_t)1 << 46) |
-         ((uint64_t)2 << 61);
-}
-
-// instruction descriptor: D FP32, A and B bf16, both K-major, M = 128, N = n
-__host__ __device__ constexpr uint32_t idesc_bf16(int n) {
-  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(kBM >> 4) << 24);
-}
-
-// byte offset of the 16-byte chunk (row, kc) in a K-major 128-byte-swizzled tile
-__host__ __device__ __forceinline__ uint32_t sw128_off(int row, int kc) {
-  return (uint32_t)((row >> 3) * 1024 + (row & 7) * 128 + ((kc ^ (row & 7)) << 4));
-}
-
-// split x into NP bf16 terms.  NP <= 2: each term the round-to-nearest of what
-// the previous ones left (NP = 1 is the bf16 rounding the BF16 mode defines).
-// NP = 3: the top 8 mantissa bits of what is left, by truncation -- three terms
-// then hold all 24 bits of x exactly, and each step is one AND and one FSUB.
-template <int NP>
-__device__ __forceinline__ void split_bf16(float x, __nv_bfloat16* out) {
-  float r = x;
-  if constexpr (NP == 3) {
-#pragma unroll
-    for (int p = 0; p < NP; ++p) {
-      const uint32_t hb = __float_as_uint(r) & 0xFFFF0000u;
-      out[p] = __ushort_as_bfloat16((unsigned short)(hb >> 16));
-      r = r - __uint_as_float(hb);
-    }
-  } else {
-#pragma unroll
-    for (int p = 0; p < NP; ++p) {
-      const __nv_bfloat16 b = __float2bfloat16_rn(r);
-      out[p] = b;
-      r = r - __bfloat162float(b);
-    }
-  }
-}
-
-}  // namespace tc
-
-// Omega (m2 x m1, FP64) -> bf16 planes of Omega^T in the swizzled K-major tile layout:
-// [k block][plane][NT rows][64] with rows n = 0..NT-1 (zero beyond m2 / m1).
 template <int NP>
 __global__ void omega_planes_kernel(const double* __restrict__ Om, int m2, int64_t m1, int NT, int nkb,
                                     __nv_bfloat16* __restrict__ out) {
   const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;     // (kb, n, kc)
-  const int64_t total = (int64_t)nkb * NT * 8;
-  if (e >= total) return;
-  const int kc = (int)(e & 7);
-  const int n = (int)((e >> 3) % NT);
-  const int kb = (int)(e / (8 * NT));
-  __nv_bfloat16 pl[NP][8];
-#pragma unroll
-  for (int q = 0; q < 8; ++q) {
-    const int64_t k = (int64_t)kb * tc::kBK + kc * 8 + q;
-    const float x = (n < m2 && k < m1) ? (float)Om[(int64_t)n * m1 + k] : 0.f;
-    __nv_bfloat16 t[NP];
-    tc::split_bf16<NP>(x, t);
-#pragma unroll
-    for (int p = 0; p < NP; ++p) pl[p][q] = t[p];
-  }
-  unsigned char* tile = (unsigned char*)out + (size_t)kb * NP * NT * 128;
-#pragma unroll
-  for (int p = 0; p < NP; ++p)
-    *(uint4*)(tile + (size_t)p * NT * 128 + tc::sw128_off(n, kc)) = *(const uint4*)pl[p];
+  if (e < (int64_t)nkb * NT * 8) omega_planes_elem<NP>(e, Om, m2, m1, NT, out);
 }
-
-// Products (plane of A, plane of B) per precision mode, smallest terms first.
-__host__ __device__ constexpr int n_products(int np) { return np == 1 ? 1 : (np == 2 ? 3 : 6); }
-__host__ __device__ constexpr int prod_a(int np, int q) {
-  return np == 1 ? 0 : (np == 2 ? (q == 0 ? 1 : 0) : (q == 0 ? 2 : q == 1 ? 1 : q == 2 ? 0 : q == 3 ? 1 : 0));
-}
-__host__ __device__ constexpr int prod_b(int np, int q) {
-  return np == 1 ? 0 : (np == 2 ? (q == 1 ? 1 : 0) : (q == 0 ? 0 : q == 1 ? 1 : q == 2 ? 2 : q == 3 ? 0 : q == 4 ? 1 : 0));
-}
-
-// Warp-specialised: warps 0-7 convert (load FP32 Y1 one K block ahead in
-// registers, split into bf16 planes, store them swizzled, arrive on a_ready);
-// warp 8 feeds Omega^T planes through a 3-slot ring of bulk copies and one of
-// its lanes issues the MMAs.  Stages are handed over with mbarriers only.
-constexpr int kConvThreads = 256;
-constexpr int kTcThreads = kConvThreads + 32;
-constexpr int kBSlots = 3;
 
 template <int NP>
 __global__ void __launch_bounds__(kTcThreads, 1)
 gauss_tc_kernel(const float* __restrict__ Y1, int64_t ldy1, int64_t R, int64_t m1, const __nv_bfloat16* __restrict__ Bpl,
                 int NT, int NTc, int kb_per_cta, int nkb, float* __restrict__ part, int* status) {
-  // NT: rows of the Omega^T planes (= columns of part); this CTA computes columns
-  // [blockIdx.z * NTc, +NTc) of D for K blocks [blockIdx.y * kb_per_cta, ...).
-  using namespace tc;
   extern __shared__ unsigned char smem_raw[];
-  unsigned char* sm = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  const int a_plane = kBM * kBK * 2;                   // 16 KB
-  const int b_plane = NTc * kBK * 2;
-  const int n0 = blockIdx.z * NTc;
-  unsigned char* A = sm;                               // [stage][plane] a_plane
-  unsigned char* B = A + kStages * NP * a_plane;       // [slot][plane] b_plane
-  uint64_t* bars = (uint64_t*)(B + kBSlots * NP * b_plane);
-  uint64_t* a_ready = bars;                            // [kStages] 256 converter arrivals
-  uint64_t* mma_done = bars + 2;                       // [kStages] tcgen05.commit
-  uint64_t* b_full = bars + 4;                         // [kBSlots] bulk-copy bytes
-  uint64_t* b_free = bars + 7;                         // [kBSlots] tcgen05.commit
-  uint32_t* tmem_slot = (uint32_t*)(bars + 10);
-  __shared__ int s_flag;
-
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int64_t r0 = (int64_t)blockIdx.x * kBM;
   const int kb0 = blockIdx.y * kb_per_cta;
   const int nk = min(nkb, kb0 + kb_per_cta) - kb0;
-  // two accumulators (columns [0, NTc) and [NTc, 2 NTc)) taken in turn, so consecutive
-  // MMAs do not depend on each other's result
-  uint32_t tcols = 32;
-  while ((int)tcols < 2 * NTc) tcols <<= 1;
-
-  if (tid == 0) {
-    for (int q = 0; q < kStages; ++q) { mbar_init(&a_ready[q], kConvThreads); mbar_init(&mma_done[q], 1); }
-    for (int q = 0; q < kBSlots; ++q) { mbar_init(&b_full[q], 1); mbar_init(&b_free[q], 1); }
-    fence_barrier_init();
-    s_flag = 0;
-  }
-  if (warp == 0) tmem_alloc(tmem_slot, tcols);
-  tc_fence_before();
-  __syncthreads();
-  tc_fence_after();
-  const uint32_t tmem = *tmem_slot;
-  const uint32_t b_bytes = (uint32_t)(NP * b_plane);
-  // the NP planes' row chunks [n0, n0 + NTc) of K block kb into B slot sl
-  auto fetch_b = [&](int kb, int sl) {
-    mbar_expect_tx(&b_full[sl], b_bytes);
-#pragma unroll
-    for (int p = 0; p < NP; ++p)
-      bulk_g2s(B + (size_t)(sl * NP + p) * b_plane, Bpl + ((size_t)kb * NP * NT + (size_t)p * NT + n0) * kBK,
-               (uint32_t)b_plane, &b_full[sl]);
-  };
-
-  if (warp < 8) {
-    // ---------------- converters ----------------
-    const int m = tid & (kBM - 1);
-    const int kq = tid >> 7;                           // 0 or 1: k-chunks kq, kq+2, kq+4, kq+6
-    const bool col_ok = r0 + m < R;
-    // two register buffers: the loads of K block i+2 are in flight while block i is converted
-    float va[4][8], vb[4][8];
-    auto load_block = [&](float (&v)[4][8], int kb) {
-#pragma unroll
-      for (int c = 0; c < 4; ++c) {
-        const int kc = kq + 2 * c;
-#pragma unroll
-        for (int e = 0; e < 8; ++e) {
-          const int64_t b = (int64_t)kb * kBK + kc * 8 + e;
-          v[c][e] = (col_ok && b < m1) ? __ldcs(Y1 + b * ldy1 + r0 + m) : 0.f;
-        }
-      }
-    };
-    // convert block i from v into A stage i&1; false when the kernel is giving up
-    auto convert = [&](float (&v)[4][8], int i) -> bool {
-      const int s = i & 1;
-      if (i >= 2 && !mbar_wait(&mma_done[s], ((i - 2) >> 1) & 1)) { s_flag = 1; return false; }   // stage s free
-      if (*(volatile int*)&s_flag) return false;
-      unsigned char* As = A + (size_t)s * NP * a_plane;
-#pragma unroll
-      for (int c = 0; c < 4; ++c) {
-        const int kc = kq + 2 * c;
-        __nv_bfloat16 pl[NP][8];
-#pragma unroll
-        for (int e = 0; e < 8; ++e) {
-          __nv_bfloat16 t[NP];
-          split_bf16<NP>(v[c][e], t);
-#pragma unroll
-          for (int p = 0; p < NP; ++p) pl[p][e] = t[p];
-        }
-#pragma unroll
-        for (int p = 0; p < NP; ++p) *(uint4*)(As + (size_t)p * a_plane + sw128_off(m, kc)) = *(const uint4*)pl[p];
-      }
-      fence_async_smem();
-      asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&a_ready[s])) : "memory");
-      return true;
-    };
-    if (nk > 0) load_block(va, kb0);
-    if (nk > 1) load_block(vb, kb0 + 1);
-    for (int i = 0; i < nk; i += 2) {
-      if (!convert(va, i)) break;
-      if (i + 2 < nk) load_block(va, kb0 + i + 2);
-      if (i + 1 >= nk) break;
-      if (!convert(vb, i + 1)) break;
-      if (i + 3 < nk) load_block(vb, kb0 + i + 3);
-    }
-  } else if (lane == 0) {
-    // ---------------- producer of Omega^T planes + MMA issue ----------------
-    int last_commit = -1, b_issued = 0, b_done = 0;
-    for (int q = 0; q < kBSlots && q < nk; ++q) { fetch_b(kb0 + q, q); b_issued = q + 1; }
-    const uint32_t idesc = idesc_bf16(NTc);
-    for (int i = 0; i < nk && !*(volatile int*)&s_flag; ++i) {
-      const int s = i & 1, sb = i % kBSlots;
-      if (!mbar_wait(&a_ready[s], (i >> 1) & 1)) { s_flag = 1; break; }
-      if (!mbar_wait(&b_full[sb], (i / kBSlots) & 1)) { s_flag = 1; break; }
-      b_done = i + 1;
-      tc_fence_after();
-      const unsigned char* As = A + (size_t)s * NP * a_plane;
-      const unsigned char* Bs = B + (size_t)sb * NP * b_plane;
-#pragma unroll
-      for (int ks = 0; ks < kBK / 16; ++ks) {
-#pragma unroll
-        for (int q = 0; q < n_products(NP); ++q) {
-          const int u = (ks * n_products(NP) + q) & 1;           // accumulator of this MMA
-          const uint64_t ad = sw128_desc(As + (size_t)prod_a(NP, q) * a_plane) + (uint64_t)(ks * 2);
-          const uint64_t bd = sw128_desc(Bs + (size_t)prod_b(NP, q) * b_plane) + (uint64_t)(ks * 2);
-          const bool first = i == 0 && ks * n_products(NP) + q < 2;
-          mma_bf16(tmem + (uint32_t)(u * NTc), ad, bd, idesc, first ? 0u : 1u);
-        }
-      }
-      mma_commit(&mma_done[s]);
-      mma_commit(&b_free[sb]);
-      last_commit = i;
-      // refill the B slot of block i-1 with block i+2 once block i-1's MMAs are done
-      if (i >= 1 && i + 2 < nk) {
-        const int so = (i - 1) % kBSlots;
-        if (!mbar_wait(&b_free[so], ((i - 1) / kBSlots) & 1)) { s_flag = 1; break; }
-        fetch_b(kb0 + i + 2, so);
-        b_issued = i + 3;
-      }
-    }
-    // the accumulator is final once the last MMAs complete (bounded wait)
-    if (last_commit >= 0 && !mbar_wait(&mma_done[last_commit & 1], (last_commit >> 1) & 1)) s_flag = 2;
-    if (last_commit < nk - 1 && !s_flag) s_flag = 1;
-    // after an early exit, wait (bounded) for Omega^T copies still in flight
-    for (int j = b_done; j < b_issued; ++j) (void)mbar_wait(&b_full[j % kBSlots], (j / kBSlots) & 1);
-  }
-  tc_fence_before();
-  __syncthreads();
-  tc_fence_after();
-  if (s_flag == 0 && nk > 0 && warp < 8) {
-    // epilogue: warp w reads TMEM lanes 32*(w%4).. (rows of D); warps 0-3 and 4-7 split the columns
-    const int lane_base = (warp & 3) * 32;
-    const int64_t r = r0 + lane_base + lane;
-    float* prow = part + ((int64_t)blockIdx.y * R + r) * NT + n0;
-    const int uses = 4 * n_products(NP) * nk;        // MMAs issued; the second accumulator is used if > 1
-    for (int q = warp >> 2; q < NTc / 16; q += 2) {
-      float vals[16];
-      tmem_ld16(tmem + ((uint32_t)lane_base << 16) + (uint32_t)(q * 16), vals);
-      if (uses > 1) {
-        float v2[16];
-        tmem_ld16(tmem + ((uint32_t)lane_base << 16) + (uint32_t)(NTc + q * 16), v2);
-#pragma unroll
-        for (int j = 0; j < 16; ++j) vals[j] += v2[j];
-      }
-      if (r < R) {
-#pragma unroll
-        for (int j = 0; j < 16; j += 4)
-          *(float4*)(prow + q * 16 + j) = make_float4(vals[j], vals[j + 1], vals[j + 2], vals[j + 3]);
-      }
-    }
-  }
-  tc_fence_before();
-  __syncthreads();
-  if (tid == 0 && s_flag) set_status(status, IDL_ETIMEOUT);
-  if (warp == 0) tmem_dealloc(tmem, tcols);
+  gauss_tc_block<NP>(Y1, ldy1, R, m1, Bpl, NT, NTc, kb0, nk, blockIdx.x, blockIdx.z,
+                     part + (int64_t)blockIdx.y * R * NT, status, smem_raw);
 }
+
+using namespace tc;
 
 template <int NP>
 static int tc_impl(idl_ctx* ctx, const double* Omega, int64_t m2, int64_t m1, const float* Y1, int64_t R, int64_t ldy1,
