@@ -254,6 +254,45 @@ int id_cp_tensor(idl_ctx* ctx, int N, const int64_t* dims, int64_t R, const void
                  const int64_t* ldf, const double* lambda, int64_t K, const idl_params* p,
                  int32_t* J, double* T, double* lambda_hat, idl_info* info);
 
+/* ---------------------------------------------------------------------------
+ * Batches.  Many IDs of uneven sizes in one pass: every stage of the path is
+ * one launch over all items, and the pivoted QR runs one thread-block cluster
+ * per item in one launch.  The launch sequence of a batch shape is captured
+ * once into a CUDA graph and replayed on later calls with the same shape.  On
+ * the first call of a shape the dense sketch's block width and the Gaussian
+ * stage's split-K factor are chosen by timing the candidates (the call then
+ * runs the batch several times); idl_tune_save / idl_tune_load keep those
+ * choices in a text file.
+ *   Items: IDL_ITEM_DENSE (Algorithm 2 on a dense FP32 matrix) or IDL_ITEM_CP
+ *   (Algorithm 3 on a CP tensor), FP32 data, one precision mode per batch
+ *   (IDL_PREC_FP32 / BF16X3 / BF16), Gaussian stage required with
+ *   K <= m2 <= min(m1, 128), K <= 128.  All pointers are device pointers;
+ *   CP factors are stored column by column (ldf = dims[n]).  Outputs as for the
+ *   single-item calls.  The call is asynchronous after its first use of a
+ *   shape; idl_sync returns the device status word.
+ * ------------------------------------------------------------------------- */
+#define IDL_ITEM_DENSE 0
+#define IDL_ITEM_CP    2
+
+typedef struct idl_batch_item {
+  int32_t       kind;        /* IDL_ITEM_DENSE or IDL_ITEM_CP */
+  int32_t       N;           /* CP: number of modes (1..8) */
+  int64_t       I, R, lda;   /* dense: A is I x R row-major (lda >= R); CP: R = number of rank-1 terms */
+  int64_t       K;           /* target rank */
+  const float*  A;           /* dense matrix (device) */
+  int64_t       dims[8];     /* CP: mode sizes */
+  const float*  factors[8];  /* CP: factor matrices, column r of mode n at factors[n] + r*dims[n] (device) */
+  const double* lambda;      /* CP: R s-values (device) */
+  idl_params    params;      /* m1 (the TensorSketch length L for CP), m2, modified, precision, seed */
+  int32_t*      J;           /* out: K pivots (device) */
+  double*       T;           /* out: K x (R-K) FP64 (device) */
+  double*       lambda_hat;  /* out, CP: K s-values (device) */
+} idl_batch_item;
+
+int idl_batch_run(idl_ctx* ctx, const idl_batch_item* items, int n);
+int idl_tune_save(idl_ctx* ctx, const char* path);
+int idl_tune_load(idl_ctx* ctx, const char* path);
+
 #ifdef __cplusplus
 }
 #endif

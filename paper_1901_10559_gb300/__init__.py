@@ -49,6 +49,17 @@ class Info(ctypes.Structure):
         return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
 
 
+IDL_ITEM_DENSE, IDL_ITEM_CP = 0, 2
+
+
+class BatchItem(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("N", ctypes.c_int32), ("I", ctypes.c_int64), ("R", ctypes.c_int64),
+                ("lda", ctypes.c_int64), ("K", ctypes.c_int64), ("A", ctypes.c_void_p),
+                ("dims", ctypes.c_int64 * 8), ("factors", ctypes.c_void_p * 8), ("lambda_", ctypes.c_void_p),
+                ("params", Params), ("J", ctypes.c_void_p), ("T", ctypes.c_void_p),
+                ("lambda_hat", ctypes.c_void_p)]
+
+
 _lib = None
 _vp, _i64, _i32, _u64, _int = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_uint64, ctypes.c_int
 
@@ -84,6 +95,10 @@ _SIGS = {
                        ctypes.POINTER(Info)], _int),
     "id_cp_tensor": ([_vp, _int, _vp, _i64, _vp, _vp, _vp, _i64, ctypes.POINTER(Params), _vp, _vp, _vp,
                       ctypes.POINTER(Info)], _int),
+    "idl_batch_run": ([_vp, ctypes.POINTER(BatchItem), _int], _int),
+    "idl_tune_save": ([_vp, ctypes.c_char_p], _int),
+    "idl_tune_load": ([_vp, ctypes.c_char_p], _int),
+    "idl_debug_batch_mode": ([_vp, _int, _int], _int),
 }
 
 
@@ -278,3 +293,46 @@ def id_cp_tensor(ctx, factors, lam, K, params, J, T, lam_hat, info=None, ldf=Non
     return ctx.check(lib().id_cp_tensor(ctx.ptr, N, ctypes.cast(dims, _vp), R, ctypes.cast(fp, _vp),
                                         ctypes.cast(lp, _vp), _p(lam), K, ctypes.byref(params), _p(J), _p(T),
                                         _p(lam_hat), ctypes.byref(info) if info is not None else None))
+
+
+# ---------------------------------------------------------------- batches
+def dense_item(A, K, params, J, T, lda=None):
+    """Batch item for a dense FP32 CUDA matrix A (I, R)."""
+    it = BatchItem()
+    it.kind = IDL_ITEM_DENSE
+    it.I, it.R = int(A.shape[0]), int(A.shape[1])
+    it.lda = int(A.stride(0)) if lda is None else lda
+    it.K = int(K)
+    it.A = A.data_ptr()
+    it.params = params
+    it.J, it.T = J.data_ptr(), T.data_ptr()
+    return it
+
+
+def cp_item(factors, lam, K, params, J, T, lam_hat):
+    """Batch item for a CP tensor: factors are CUDA float32 tensors (R, I_n), contiguous."""
+    it = BatchItem()
+    it.kind = IDL_ITEM_CP
+    it.N = len(factors)
+    it.R = int(factors[0].shape[0])
+    it.K = int(K)
+    for n, f in enumerate(factors):
+        it.dims[n] = int(f.shape[1])
+        it.factors[n] = f.data_ptr()
+    it.lambda_ = lam.data_ptr()
+    it.params = params
+    it.J, it.T, it.lambda_hat = J.data_ptr(), T.data_ptr(), lam_hat.data_ptr()
+    return it
+
+
+def idl_batch_run(ctx, items):
+    arr = (BatchItem * len(items))(*items)
+    return ctx.check(lib().idl_batch_run(ctx.ptr, arr, len(items)))
+
+
+def idl_tune_save(ctx, path):
+    return ctx.check(lib().idl_tune_save(ctx.ptr, str(path).encode()))
+
+
+def idl_tune_load(ctx, path):
+    return ctx.check(lib().idl_tune_load(ctx.ptr, str(path).encode()))

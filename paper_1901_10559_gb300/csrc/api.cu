@@ -22,6 +22,7 @@ namespace idl {
 
 static std::atomic<long long> g_launches{0};
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+void ctx_add_launches(long long d) { g_launches.fetch_add(d, std::memory_order_relaxed); }
 
 int fail(idl_ctx* ctx, int code, const std::string& msg) {
   if (ctx) ctx->err = msg;
@@ -205,6 +206,7 @@ extern "C" int idl_destroy(idl_ctx* ctx) {
   for (auto& b : ctx->slots)
     if (b.p) cudaFree(b.p);
   for (auto& pp : ctx->prof) { cudaEventDestroy(pp.a); cudaEventDestroy(pp.b); }
+  idl_batch_state_free(ctx->batch);
   cudaFree(ctx->d_status);
   cudaFree(ctx->d_diag);
   delete ctx;

@@ -1,0 +1,771 @@
+// batch.cu -- many IDs of uneven sizes in one pass: every stage of the hot path
+// is one launch over all items (dense matrices for Algorithm 2, CP tensors for
+// Algorithm 3), and the pivoted QR runs one thread-block cluster per item in a
+// single launch.
+//
+// Every block finds its item by a binary search over a per-stage prefix table
+// of block counts, then runs the same device body as the single-problem kernel
+// (sketch_dev.cuh, draws_dev.cuh, tsketch_dev.cuh, gemm_dev.cuh, cpqr_dev.cuh,
+// tsolve_dev.cuh).  The item descriptors and the prefix tables live in device
+// memory, so the launch sequence of a batch shape is captured once into a CUDA
+// graph and replayed; descriptors are re-uploaded before each replay.
+//
+// Tuning: the dense sketch's block width and the Gaussian stage's split-K
+// factor are chosen per batch shape by timing the candidates on the first
+// call (CUDA events around the two stages); the choice is kept in the context
+// and can be saved to / loaded from a text file (idl_tune_save / idl_tune_load).
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <type_traits>
+#include <vector>
+
+#include "common.cuh"
+#include "cpqr_dev.cuh"
+#include "draws_dev.cuh"
+#include "gemm_dev.cuh"
+#include "internal.h"
+#include "sketch_dev.cuh"
+#include "tsketch_dev.cuh"
+#include "tsolve_dev.cuh"
+
+namespace idl {
+
+using namespace tc;
+
+// ---------------------------------------------------------------------------
+// device descriptor of one item
+// ---------------------------------------------------------------------------
+struct BItem {
+  int kind, N, modified, K, vec;
+  int64_t I, R, lda, m1, m2, ldy1, nkb, NT, mtiles, splits, kbpc, ntiles, mode_tot;
+  const float* A;
+  TsArgs ts;                      // CP: factors (column-contiguous), mode maps, dims
+  uint64_t mode_hb[kTsMaxModes], mode_sb[kTsMaxModes];
+  const double* lam;
+  CsDrawArgs cs;
+  uint64_t gauss_base;
+  int32_t *h, *ptr, *rows, *cursor, *big, *nbig, *mh;
+  int8_t *s, *ms;
+  double* Om;
+  __nv_bfloat16* Bpl;
+  float *Y1, *part, *Y2;
+  int32_t* rest;
+  double *Rinv, *diag;
+  int32_t* J;
+  double* T;
+  double* lam_hat;
+  int nc;
+};
+
+// stages with a flattened block list (prefix tables, one per stage)
+enum BStage { kBDraw = 0, kBGauss, kBHist, kBScan, kBScatter, kBSortW, kBSortB, kBSketchD, kBSketchT, kBPlanes,
+              kBGemm, kBReduce, kBRest, kBRinv, kBTgemm, kBLam, kBNumStages };
+
+__device__ __forceinline__ int find_item(const int64_t* __restrict__ pre, int n, int64_t blk) {
+  int lo = 0, hi = n - 1;                          // largest p with pre[p] <= blk
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (pre[mid] <= blk) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+#define ITEM_OF_BLOCK(pre, n)                         \
+  const int p = find_item(pre, n, (int64_t)blockIdx.x); \
+  const BItem& it = items[p];                         \
+  const int64_t local = (int64_t)blockIdx.x - pre[p]
+
+__global__ void b_draw_kernel(const BItem* __restrict__ items, const int64_t* __restrict__ pre, int n, int* status) {
+  ITEM_OF_BLOCK(pre, n);
+  const int64_t i = local * blockDim.x + threadIdx.x;
+  if (it.kind == IDL_ITEM_DENSE) {
+    if (i < it.I) cs_draw_elem(i, it.cs, it.I, it.m1, it.modified, it.h, it.s, status);
+  } else if (i < it.mode_tot) {
+    int64_t off = 0;
+    for (int q = 0; q < it.N; ++q) {
+      const int64_t d = it.ts.dims[q];
+      if (i < off + d) { mode_elem(i - off, it.mode_hb[q], it.mode_sb[q], it.m1, it.mh + off, it.ms + off); break; }
+      off += d;
+    }
+  }
+}
+
+__global__ void b_gauss_draw_kernel(const BItem* __restrict__ items, const int64_t* __restrict__ pre, int n) {
+  ITEM_OF_BLOCK(pre, n);
+  const int64_t q = local * blockDim.x + threadIdx.x;
+  const int64_t tot = it.m2 * it.m1;
+  if (2 * q < tot) gauss_pair(q, it.gauss_base, tot, it.Om);
+}
+
+constexpr int kBHistBlocks = 64;
+
+__global__ void b_hist_kernel(const BItem* __restrict__ items, const int64_t* __restrict__ pre, int n, int* status) {
+  extern __shared__ int32_t sh[];
+  ITEM_OF_BLOCK(pre, n);
+  const int64_t nb = pre[p + 1] - pre[p];
+  bucket_hist_body(it.h, it.I, it.m1, it.cursor, status, local, nb, sh);
+}
+
+__global__ void b_scan_kernel(const BItem* __restrict__ items, const int64_t* __restrict__ pre, int n) {
+  ITEM_OF_BLOCK(pre, n);
+  (void)local;
+  bucket_scan_body(it.cursor, it.m1, it.ptr, it.cursor);
+}
+
+__global__ void b_scatter_kernel(const BItem* __restrict__ items, const int64_t* __restrict__ pre, int n) {
+  ITEM_OF_BLOCK(pre, n);
+  const int64_t i = local * blockDim.x + threadIdx.x;
+  if (i < it.I) bucket_scatter_elem(i, it.h, it.m1, it.cursor, it.rows);
+}
+
+__global__ void b_sortw_kernel(const BItem* __restrict__ items, const int64_t* __restrict__ pre, int n) {
+  extern __shared__ int32_t sh[];
+  ITEM_OF_BLOCK(pre, n);
+  const int wid = threadIdx.x >> 5;
+  const int64_t b = local * (blockDim.x >> 5) + wid;
+  if (b < it.m1) bucket_sort_warp_body(it.ptr, b, it.rows, it.big, it.nbig, sh + wid * kWarpSortCap);
+}
+
+constexpr int kBSortBlocks = 4;
+
+__global__ void b_sortb_kernel(const BItem* __restrict__ items, const int64_t* __restrict__ pre, int n) {
+  extern __shared__ int32_t seg[];
+  ITEM_OF_BLOCK(pre, n);
+  const int count = *it.nbig;
+  for (int q = (int)local; q < count; q += kBSortBlocks) bucket_sort_block_body(it.ptr, it.big[q], it.rows, seg);
+}
+
+__global__ void __launch_bounds__(512) b_sketch_dense_kernel(const BItem* __restrict__ items,
+                                                             const int64_t* __restrict__ pre, int n) {
+  ITEM_OF_BLOCK(pre, n);
+  const int64_t b = local / it.ntiles;
+  const int tile = (int)(local % it.ntiles);
+  if (it.vec)
+    cs_dense_block<float, true>(it.A, it.lda, it.R, it.s, it.ptr, it.rows, it.Y1, it.ldy1, b, tile);
+  else
+    cs_dense_block<float, false>(it.A, it.lda, it.R, it.s, it.ptr, it.rows, it.Y1, it.ldy1, b, tile);
+}
+
+__global__ void __launch_bounds__(kTsThreads, 1) b_sketch_cp_kernel(const BItem* __restrict__ items,
+                                                                    const int64_t* __restrict__ pre, int n) {
+  extern __shared__ __align__(16) float2 sm2[];
+  ITEM_OF_BLOCK(pre, n);
+  int logL = 0;
+  while ((1LL << logL) < it.m1) ++logL;
+  tensorsketch_block(it.ts, it.R, (int)it.m1, logL, it.lam, it.Y1, it.ldy1, local * 2, sm2);
+}
+
+template <int NP>
+__global__ void b_planes_kernel(const BItem* __restrict__ items, const int64_t* __restrict__ pre, int n) {
+  ITEM_OF_BLOCK(pre, n);
+  const int64_t e = local * blockDim.x + threadIdx.x;
+  if (e < it.nkb * it.NT * 8) omega_planes_elem<NP>(e, it.Om, (int)it.m2, it.m1, (int)it.NT, it.Bpl);
+}
+
+template <int NP>
+__global__ void __launch_bounds__(kTcThreads, 1) b_gemm_kernel(const BItem* __restrict__ items,
+                                                               const int64_t* __restrict__ pre, int n, int* status) {
+  extern __shared__ unsigned char smem_raw[];
+  ITEM_OF_BLOCK(pre, n);
+  const int64_t mt = local / it.splits;
+  const int sp = (int)(local % it.splits);
+  const int kb0 = sp * (int)it.kbpc;
+  const int nk = (int)std::min<int64_t>(it.nkb, kb0 + it.kbpc) - kb0;
+  gauss_tc_block<NP>(it.Y1, it.ldy1, it.R, it.m1, it.Bpl, (int)it.NT, (int)it.NT, kb0, nk, mt, 0,
+                     it.part + (int64_t)sp * it.R * it.NT, status, smem_raw);
+}
+
+__global__ void b_reduce_kernel(const BItem* __restrict__ items, const int64_t* __restrict__ pre, int n) {
+  ITEM_OF_BLOCK(pre, n);
+  const int64_t e = local * blockDim.x + threadIdx.x;
+  if (e >= it.R * it.m2) return;
+  const int64_t r = e / it.m2;
+  const int64_t j = e - r * it.m2;
+  float acc = 0.f;
+  for (int q = 0; q < it.splits; ++q) acc += it.part[(int64_t)q * it.R * it.NT + r * it.NT + j];
+  it.Y2[r * it.m2 + j] = acc;
+}
+
+template <int V, int TPC>
+__global__ void __launch_bounds__(RegCpqr<float, V, TPC>::kMaxThreads, 1)
+b_cpqr_kernel(const BItem* __restrict__ items, const int32_t* __restrict__ list, int CS, int* status) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const BItem& it = items[list[blockIdx.x / CS]];
+  cpqr_reg_body<float, V, TPC>(it.Y2, it.Y2, (int)it.m2, (int)it.R, (int)it.m2, it.K, it.nc, it.J, nullptr, it.diag,
+                               status, smem_raw);
+}
+
+__global__ void b_rest_kernel(const BItem* __restrict__ items, const int64_t* __restrict__ pre, int n) {
+  extern __shared__ int32_t sJ[];
+  ITEM_OF_BLOCK(pre, n);
+  for (int q = threadIdx.x; q < it.K; q += blockDim.x) sJ[q] = it.J[q];
+  __syncthreads();
+  const int64_t r = local * blockDim.x + threadIdx.x;
+  if (r < it.R) rest_elem((int)r, sJ, it.K, (int)it.R, it.rest);
+}
+
+__global__ void __launch_bounds__(256) b_rinv_kernel(const BItem* __restrict__ items, const int64_t* __restrict__ pre,
+                                                     int n) {
+  extern __shared__ __align__(16) double shU[];
+  ITEM_OF_BLOCK(pre, n);
+  rinv_block<float>(it.Y2, (int)it.m2, it.K, (int)it.R, it.J, it.Rinv, (int)local, (int)(pre[p + 1] - pre[p]), shU);
+}
+
+__global__ void __launch_bounds__(256) b_tgemm_kernel(const BItem* __restrict__ items, const int64_t* __restrict__ pre,
+                                                      int n) {
+  extern __shared__ __align__(16) double shd[];
+  ITEM_OF_BLOCK(pre, n);
+  tgemm_block<float>(it.Y2, (int)it.m2, it.K, (int)it.R, it.Rinv, it.rest, (int)(it.R - it.K), it.T, (int)local, shd);
+}
+
+__global__ void b_lam_kernel(const BItem* __restrict__ items, const int64_t* __restrict__ pre, int n) {
+  ITEM_OF_BLOCK(pre, n);
+  lambda_hat_block(it.lam, it.J, it.T, (int)(it.R - it.K), it.K, it.lam_hat, (int)local);
+}
+
+}  // namespace idl
+
+// ===========================================================================
+// host side
+// ===========================================================================
+using namespace idl;
+
+namespace {
+
+struct Tune { int sketch_threads = 256; int split_mult = 1; };
+
+// a batch shape: the sizes that decide every launch
+std::string signature(const idl_batch_item* items, int n) {
+  std::string s;
+  char buf[160];
+  for (int i = 0; i < n; ++i) {
+    const idl_batch_item& x = items[i];
+    snprintf(buf, sizeof(buf), "%d:%lld:%lld:%lld:%lld:%lld:%d:%d;", x.kind, (long long)x.I, (long long)x.R,
+             (long long)x.K, (long long)x.params.m1, (long long)x.params.m2, x.params.precision, x.N);
+    s += buf;
+    for (int q = 0; q < x.N && x.kind == IDL_ITEM_CP; ++q) {
+      snprintf(buf, sizeof(buf), "%lld,", (long long)x.dims[q]);
+      s += buf;
+    }
+  }
+  return s;
+}
+
+uint64_t fnv1a(const std::string& s) {
+  uint64_t h = 1469598103934665603ull;
+  for (unsigned char c : s) { h ^= c; h *= 1099511628211ull; }
+  return h;
+}
+
+struct CpqrCfg { int V = 0, TPC = 0, CS = 16, threads = 0; size_t smem = 0; };
+
+}  // namespace
+
+// context-side batch state
+struct idl_batch_state {
+  std::map<uint64_t, Tune> tune;
+  uint64_t graph_sig = 0;
+  cudaGraphExec_t graph = nullptr;
+  int graph_launches = 0;
+  void* graph_ws = nullptr;
+};
+
+extern "C" long long idl_launch_count(void);
+
+static idl_batch_state* bstate(idl_ctx* ctx) {
+  if (!ctx->batch) ctx->batch = new idl_batch_state();
+  return ctx->batch;
+}
+
+void idl_batch_state_free(idl_batch_state* b) {
+  if (!b) return;
+  if (b->graph) cudaGraphExecDestroy(b->graph);
+  delete b;
+}
+
+#define BTRY(x)                     \
+  do {                              \
+    int _rc = (x);                  \
+    if (_rc != IDL_OK) return _rc;  \
+  } while (0)
+
+static int launch_check(idl_ctx* ctx, const char* where) { return cuda_check(ctx, cudaGetLastError(), where); }
+
+template <int V, int TPC>
+static bool cpqr_cfg_fits(const std::vector<int>& list, const std::vector<BItem>& it, int CS, CpqrCfg* cfg) {
+  int threads = 0, maxm = 0;
+  for (int p : list) {
+    const BItem& x = it[p];
+    if (cdiv(x.m2, TPC) > V) return false;
+    const int nc = (int)cdiv(x.R, CS);
+    threads = std::max(threads, (int)round_up((int64_t)nc * TPC, 32));
+    maxm = std::max(maxm, (int)x.m2);
+  }
+  if (threads > RegCpqr<float, V, TPC>::kMaxThreads || threads < 32) return false;
+  cfg->V = V;
+  cfg->TPC = TPC;
+  cfg->CS = CS;
+  cfg->threads = threads;
+  cfg->smem = reg_cpqr_smem<float, V, TPC>(maxm);
+  return true;
+}
+
+static bool pick_cpqr(const std::vector<int>& list, const std::vector<BItem>& it, CpqrCfg* cfg) {
+  const int CS = 16;
+#define PICK(VV, TT) if (cpqr_cfg_fits<VV, TT>(list, it, CS, cfg)) return true;
+  PICK(8, 32) PICK(8, 16) PICK(8, 8) PICK(16, 8) PICK(8, 4) PICK(16, 4) PICK(32, 4) PICK(16, 2) PICK(32, 2)
+  PICK(16, 1) PICK(32, 1) PICK(64, 4) PICK(64, 2) PICK(64, 1)
+#undef PICK
+  return false;
+}
+
+template <int V, int TPC>
+static int launch_b_cpqr(idl_ctx* ctx, const BItem* d_items, const int32_t* d_list, int nlist, const CpqrCfg& c) {
+  auto kern = b_cpqr_kernel<V, TPC>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c.smem);
+  if (e != cudaSuccess) return cuda_check(ctx, e, "batch cpqr attribute");
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(nlist * c.CS));
+  cfg.blockDim = dim3((unsigned)c.threads);
+  cfg.dynamicSmemBytes = c.smem;
+  cfg.stream = ctx->stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = c.CS;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  e = cudaLaunchKernelEx(&cfg, kern, d_items, d_list, c.CS, ctx->d_status);
+  count_launch();
+  return cuda_check(ctx, e, "batch cpqr");
+}
+
+static int dispatch_b_cpqr(idl_ctx* ctx, const BItem* d_items, const int32_t* d_list, int nlist, const CpqrCfg& c) {
+#define CASE(VV, TT) if (c.V == VV && c.TPC == TT) return launch_b_cpqr<VV, TT>(ctx, d_items, d_list, nlist, c);
+  CASE(8, 32) CASE(8, 16) CASE(8, 8) CASE(16, 8) CASE(8, 4) CASE(16, 4) CASE(32, 4) CASE(16, 2) CASE(32, 2)
+  CASE(16, 1) CASE(32, 1) CASE(64, 4) CASE(64, 2) CASE(64, 1)
+#undef CASE
+  return fail(ctx, IDL_ELIMIT, "batch cpqr: no configuration");
+}
+
+// Everything a batch needs on the host side, computed from the items.
+struct BatchPlan {
+  std::vector<BItem> it;
+  std::vector<int64_t> pre[kBNumStages];
+  std::vector<int32_t> dense_list, cp_list;
+  CpqrCfg cfg_dense, cfg_cp;
+  int NP = 3;
+  int maxL_hist = 0, maxK = 0, maxNT = 0, maxL_cp = 0;
+  size_t ws_bytes = 0, zero_bytes = 0;
+  size_t off_items = 0, off_pre = 0, off_lists = 0, table_bytes = 0;
+};
+
+static int plan_batch(idl_ctx* ctx, const idl_batch_item* items, int n, const Tune& tn, BatchPlan& P) {
+  P.it.assign(n, BItem());
+  int prec = -1;
+  for (int i = 0; i < n; ++i) {
+    const idl_batch_item& x = items[i];
+    const idl_params& pr = x.params;
+    if (prec < 0) prec = pr.precision;
+    if (pr.precision != prec) return fail(ctx, IDL_EINVAL, "batch: all items must use one precision");
+    if (prec == IDL_PREC_FP64) return fail(ctx, IDL_EINVAL, "batch: FP32 data only (precision FP32, BF16X3 or BF16)");
+    if (x.K < 1 || x.K >= x.R || pr.m2 < x.K || pr.m2 > pr.m1 || pr.m2 > 128 || x.K > 128 || !x.J || !x.T ||
+        x.R > 0x7fffffffLL)
+      return fail(ctx, IDL_EINVAL, "batch: need 1 <= K < R, K <= m2 <= min(m1, 128), K <= 128, outputs");
+    if (x.kind == IDL_ITEM_DENSE) {
+      if (!x.A || x.I < 1 || x.lda < x.R || x.I > 0x7fffffffLL) return fail(ctx, IDL_EINVAL, "batch: dense item");
+      if (pr.modified && !(pr.m1 < x.I)) return fail(ctx, IDL_EINVAL, "batch: modified CountSketch needs m1 < I");
+    } else if (x.kind == IDL_ITEM_CP) {
+      if (x.N < 1 || x.N > 8 || !x.lambda || !x.lambda_hat || (pr.m1 & (pr.m1 - 1)) || pr.m1 < 16 || pr.m1 > 8192)
+        return fail(ctx, IDL_EINVAL, "batch: CP item (1 <= N <= 8, L a power of two in [16, 8192])");
+      for (int q = 0; q < x.N; ++q)
+        if (!x.factors[q] || x.dims[q] < 1) return fail(ctx, IDL_EINVAL, "batch: CP factor");
+    } else {
+      return fail(ctx, IDL_EINVAL, "batch: item kind must be IDL_ITEM_DENSE or IDL_ITEM_CP");
+    }
+  }
+  P.NP = prec == IDL_PREC_BF16 ? 1 : (prec == IDL_PREC_BF16X3 ? 2 : 3);
+  // ---- per-item sizes and workspace layout ----
+  size_t off = 0;
+  auto take = [&](size_t bytes) { const size_t o = off; off += (bytes + 255) & ~(size_t)255; return o; };
+  std::vector<size_t> o_h(n), o_s(n), o_ptr(n), o_rows(n), o_big(n), o_Om(n), o_Bpl(n), o_Y1(n), o_part(n),
+      o_Y2(n), o_rest(n), o_Rinv(n), o_mh(n), o_ms(n);
+  // zero-initialised region first: cursors, nbig, diag
+  std::vector<size_t> o_cur(n), o_nbig(n), o_diag(n);
+  for (int i = 0; i < n; ++i) {
+    const idl_batch_item& x = items[i];
+    o_cur[i] = take(x.kind == IDL_ITEM_DENSE ? sizeof(int32_t) * (size_t)(x.params.m1 + 1) : 0);
+    o_nbig[i] = take(sizeof(int32_t));
+    o_diag[i] = take(sizeof(double) * 8);
+  }
+  P.zero_bytes = off;
+  const int per_sm_gemm = 1;
+  for (int i = 0; i < n; ++i) {
+    const idl_batch_item& x = items[i];
+    BItem& b = P.it[i];
+    b.kind = x.kind;
+    b.K = (int)x.K;
+    b.R = x.R;
+    b.m1 = x.params.m1;
+    b.m2 = x.params.m2;
+    b.ldy1 = round_up(x.R, 32);
+    b.modified = x.params.modified;
+    b.nkb = cdiv(b.m1, kBK);
+    b.NT = round_up(b.m2, 16);
+    b.mtiles = cdiv(b.R, kBM);
+    int64_t splits = std::max<int64_t>(1, cdiv((int64_t)ctx->num_sms * per_sm_gemm * tn.split_mult, b.mtiles));
+    splits = std::min<int64_t>(splits, b.nkb);
+    b.kbpc = cdiv(b.nkb, splits);
+    b.splits = cdiv(b.nkb, b.kbpc);
+    b.gauss_base = stream_base(x.params.seed, kTagGauss);
+    if (x.kind == IDL_ITEM_DENSE) {
+      b.I = x.I;
+      b.lda = x.lda;
+      b.A = x.A;
+      b.cs = make_cs_draw_args(x.params.seed, x.I);
+      b.vec = ((uintptr_t)x.A % 16 == 0) && (x.lda % 4 == 0);
+      b.ntiles = cdiv(x.R, (int64_t)tn.sketch_threads * 4);
+      o_h[i] = take(sizeof(int32_t) * (size_t)x.I);
+      o_s[i] = take((size_t)x.I);
+      o_ptr[i] = take(sizeof(int32_t) * (size_t)(b.m1 + 1));
+      o_rows[i] = take(sizeof(int32_t) * (size_t)x.I);
+      o_big[i] = take(sizeof(int32_t) * (size_t)(b.m1 + 1));
+      P.maxL_hist = std::max<int>(P.maxL_hist, (int)std::min<int64_t>(b.m1, kHistSmem));
+    } else {
+      b.N = x.N;
+      b.lam = x.lambda;
+      b.mode_tot = 0;
+      for (int q = 0; q < x.N; ++q) b.mode_tot += x.dims[q];
+      o_mh[i] = take(sizeof(int32_t) * (size_t)b.mode_tot);
+      o_ms[i] = take((size_t)b.mode_tot);
+      b.ts.N = x.N;
+      for (int q = 0; q < x.N; ++q) {
+        b.ts.F[q] = x.factors[q];
+        b.ts.dims[q] = (int)x.dims[q];
+        b.ts.ldf[q] = x.dims[q];
+        b.mode_hb[q] = stream_base(x.params.seed, kTagModeBucket + q);
+        b.mode_sb[q] = stream_base(x.params.seed, kTagModeSign + q);
+      }
+      P.maxL_cp = std::max<int>(P.maxL_cp, (int)b.m1);
+    }
+    o_Om[i] = take(sizeof(double) * (size_t)(b.m2 * b.m1));
+    o_Bpl[i] = take((size_t)b.nkb * P.NP * b.NT * kBK * 2);
+    o_Y1[i] = take(sizeof(float) * (size_t)(b.m1 * b.ldy1));
+    o_part[i] = take(sizeof(float) * (size_t)(b.splits * b.R * b.NT));
+    o_Y2[i] = take(sizeof(float) * (size_t)(b.R * b.m2));
+    o_rest[i] = take(sizeof(int32_t) * (size_t)b.R);
+    o_Rinv[i] = take(sizeof(double) * (size_t)(x.K * x.K));
+    b.J = x.J;
+    b.T = x.T;
+    b.lam_hat = x.lambda_hat;
+    P.maxK = std::max(P.maxK, (int)x.K);
+    P.maxNT = std::max(P.maxNT, (int)b.NT);
+  }
+  P.ws_bytes = off;
+  // tables: items, prefix arrays, cluster lists
+  size_t toff = 0;
+  P.off_items = toff;
+  toff += sizeof(BItem) * n;
+  toff = (toff + 255) & ~(size_t)255;
+  P.off_pre = toff;
+  toff += sizeof(int64_t) * (size_t)(n + 1) * kBNumStages;
+  P.off_lists = toff;
+  toff += sizeof(int32_t) * (size_t)(2 * n + 2);
+  P.table_bytes = toff;
+  // record workspace offsets (pointers are filled once the workspace address is known)
+  for (int i = 0; i < n; ++i) {
+    BItem& b = P.it[i];
+    b.h = (int32_t*)o_h[i]; b.s = (int8_t*)o_s[i]; b.ptr = (int32_t*)o_ptr[i]; b.rows = (int32_t*)o_rows[i];
+    b.cursor = (int32_t*)o_cur[i]; b.big = (int32_t*)o_big[i]; b.nbig = (int32_t*)o_nbig[i];
+    b.mh = (int32_t*)o_mh[i]; b.ms = (int8_t*)o_ms[i]; b.Om = (double*)o_Om[i];
+    b.Bpl = (__nv_bfloat16*)o_Bpl[i]; b.Y1 = (float*)o_Y1[i]; b.part = (float*)o_part[i]; b.Y2 = (float*)o_Y2[i];
+    b.rest = (int32_t*)o_rest[i]; b.Rinv = (double*)o_Rinv[i]; b.diag = (double*)o_diag[i];
+  }
+  // ---- prefix tables ----
+  for (int st = 0; st < kBNumStages; ++st) P.pre[st].assign(n + 1, 0);
+  for (int i = 0; i < n; ++i) {
+    const BItem& b = P.it[i];
+    const bool d = b.kind == IDL_ITEM_DENSE, cp = !d;
+    int64_t nb[kBNumStages] = {0};
+    nb[kBDraw] = cdiv(d ? b.I : b.mode_tot, 256);
+    nb[kBGauss] = cdiv(cdiv(b.m2 * b.m1, 2), 256);
+    nb[kBHist] = d ? std::min<int64_t>(kBHistBlocks, cdiv(b.I, 4096)) : 0;
+    nb[kBScan] = d ? 1 : 0;
+    nb[kBScatter] = d ? cdiv(b.I, 256) : 0;
+    nb[kBSortW] = d ? cdiv(b.m1, 8) : 0;
+    nb[kBSortB] = d ? kBSortBlocks : 0;
+    nb[kBSketchD] = d ? b.m1 * b.ntiles : 0;
+    nb[kBSketchT] = cp ? cdiv(b.R, 2) : 0;
+    nb[kBPlanes] = cdiv(b.nkb * b.NT * 8, 256);
+    nb[kBGemm] = b.mtiles * b.splits;
+    nb[kBReduce] = cdiv(b.R * b.m2, 256);
+    nb[kBRest] = cdiv(b.R, 256);
+    nb[kBRinv] = cdiv(b.K, 8);
+    nb[kBTgemm] = cdiv(b.R - b.K, kTNB);
+    nb[kBLam] = cp ? b.K : 0;
+    for (int st = 0; st < kBNumStages; ++st) P.pre[st][i + 1] = P.pre[st][i] + nb[st];
+    if (d) P.dense_list.push_back(i); else P.cp_list.push_back(i);
+  }
+  for (int i = 0; i < n; ++i) P.it[i].nc = 0;
+  if (!P.dense_list.empty()) {
+    if (!pick_cpqr(P.dense_list, P.it, &P.cfg_dense)) return fail(ctx, IDL_ELIMIT, "batch: no QR cluster shape");
+    for (int p : P.dense_list) P.it[p].nc = (int)cdiv(P.it[p].R, P.cfg_dense.CS);
+  }
+  if (!P.cp_list.empty()) {
+    if (!pick_cpqr(P.cp_list, P.it, &P.cfg_cp)) return fail(ctx, IDL_ELIMIT, "batch: no QR cluster shape");
+    for (int p : P.cp_list) P.it[p].nc = (int)cdiv(P.it[p].R, P.cfg_cp.CS);
+  }
+  return IDL_OK;
+}
+
+// one flattened launch: grid = the stage's total block count
+#define BLAUNCH(kern, st, threads, smem, ...)                                                         \
+  do {                                                                                                \
+    const int64_t nb_ = P.pre[st][n];                                                                 \
+    if (nb_ > 0) {                                                                                    \
+      kern<<<(unsigned)nb_, threads, smem, ctx->stream>>>(d_items, d_pre + (size_t)(st) * (n + 1), n, \
+                                                          ##__VA_ARGS__);                             \
+      count_launch();                                                                                 \
+      ++nlaunch;                                                                                      \
+    }                                                                                                 \
+  } while (0)
+
+template <int NP>
+static int run_gemm_stage(idl_ctx* ctx, const BatchPlan& P, const BItem* d_items, const int64_t* d_pre, int n,
+                          int& nlaunch) {
+  const size_t smem = 1024 + (size_t)kStages * NP * kBM * kBK * 2 + (size_t)kBSlots * NP * P.maxNT * kBK * 2 + 128;
+  if (smem > (size_t)ctx->smem_optin) return fail(ctx, IDL_ELIMIT, "batch gemm: shared memory");
+  cudaError_t e = cudaFuncSetAttribute(b_gemm_kernel<NP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return cuda_check(ctx, e, "batch gemm attribute");
+  BLAUNCH(b_planes_kernel<NP>, kBPlanes, 256, 0);
+  BLAUNCH(b_gemm_kernel<NP>, kBGemm, kTcThreads, smem, ctx->d_status);
+  return launch_check(ctx, "batch gemm");
+}
+
+// All launches of a batch (the part that is captured into a graph).
+static int run_stages(idl_ctx* ctx, const BatchPlan& P, const BItem* d_items, const int64_t* d_pre,
+                      const int32_t* d_lists, int n, int sketch_threads, int& nlaunch, float* ms_sketch,
+                      float* ms_gemm) {
+  nlaunch = 0;
+  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+  const bool timed = ms_sketch || ms_gemm;
+  if (timed)
+    for (auto& x : ev) cudaEventCreate(&x);
+  BLAUNCH(b_draw_kernel, kBDraw, 256, 0, ctx->d_status);
+  BLAUNCH(b_gauss_draw_kernel, kBGauss, 256, 0);
+  BLAUNCH(b_hist_kernel, kBHist, 512, sizeof(int32_t) * (size_t)P.maxL_hist, ctx->d_status);
+  BLAUNCH(b_scan_kernel, kBScan, 1024, 0);
+  BLAUNCH(b_scatter_kernel, kBScatter, 256, 0);
+  BLAUNCH(b_sortw_kernel, kBSortW, 256, sizeof(int32_t) * 8 * kWarpSortCap);
+  BLAUNCH(b_sortb_kernel, kBSortB, 512, sizeof(int32_t) * kBlockSortCap);
+  BTRY(launch_check(ctx, "batch buckets"));
+  if (timed) cudaEventRecord(ev[0], ctx->stream);
+  BLAUNCH(b_sketch_dense_kernel, kBSketchD, sketch_threads, 0);
+  if (timed) cudaEventRecord(ev[1], ctx->stream);
+  if (P.pre[kBSketchT][n] > 0) {
+    const size_t smem = sizeof(float2) * (size_t)(2 * P.maxL_cp + 2 * (P.maxL_cp / 2 + 1));
+    cudaError_t e = cudaFuncSetAttribute(b_sketch_cp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return cuda_check(ctx, e, "batch tensorsketch attribute");
+    BLAUNCH(b_sketch_cp_kernel, kBSketchT, kTsThreads, smem);
+  }
+  BTRY(launch_check(ctx, "batch sketch"));
+  if (timed) cudaEventRecord(ev[2], ctx->stream);
+  if (P.NP == 1) BTRY(run_gemm_stage<1>(ctx, P, d_items, d_pre, n, nlaunch));
+  else if (P.NP == 2) BTRY(run_gemm_stage<2>(ctx, P, d_items, d_pre, n, nlaunch));
+  else BTRY(run_gemm_stage<3>(ctx, P, d_items, d_pre, n, nlaunch));
+  if (timed) cudaEventRecord(ev[3], ctx->stream);
+  BLAUNCH(b_reduce_kernel, kBReduce, 256, 0);
+  if (!P.dense_list.empty()) {
+    BTRY(dispatch_b_cpqr(ctx, d_items, d_lists, (int)P.dense_list.size(), P.cfg_dense));
+    ++nlaunch;
+  }
+  if (!P.cp_list.empty()) {
+    BTRY(dispatch_b_cpqr(ctx, d_items, d_lists + n + 1, (int)P.cp_list.size(), P.cfg_cp));
+    ++nlaunch;
+  }
+  BLAUNCH(b_rest_kernel, kBRest, 256, sizeof(int32_t) * (size_t)P.maxK);
+  {
+    const size_t smem_inv = sizeof(double) * (size_t)P.maxK * (P.maxK + 1);
+    const size_t smem_t = sizeof(double) * ((size_t)P.maxK * P.maxK + (size_t)P.maxK * (kTNB + 1));
+    cudaError_t e = cudaFuncSetAttribute(b_rinv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_inv);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(b_tgemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_t);
+    if (e != cudaSuccess) return cuda_check(ctx, e, "batch solve attribute");
+    BLAUNCH(b_rinv_kernel, kBRinv, 256, smem_inv);
+    BLAUNCH(b_tgemm_kernel, kBTgemm, 256, smem_t);
+  }
+  BLAUNCH(b_lam_kernel, kBLam, 256, 0);
+  BTRY(launch_check(ctx, "batch solve"));
+  if (timed) {
+    cudaEventSynchronize(ev[3]);
+    if (ms_sketch) cudaEventElapsedTime(ms_sketch, ev[0], ev[1]);
+    if (ms_gemm) cudaEventElapsedTime(ms_gemm, ev[2], ev[3]);
+    for (auto& x : ev) cudaEventDestroy(x);
+  }
+  return IDL_OK;
+}
+
+// Uploads the tables (with workspace addresses filled in) and clears the zero region.
+static int upload(idl_ctx* ctx, BatchPlan& P, unsigned char* ws, unsigned char* tab, int n) {
+  std::vector<unsigned char> host(P.table_bytes, 0);
+  std::vector<BItem> items = P.it;
+  auto fix = [&](auto*& ptr) { ptr = (std::remove_reference_t<decltype(ptr)>)(ws + (size_t)(uintptr_t)ptr); };
+  for (auto& b : items) {
+    if (b.kind == IDL_ITEM_DENSE) { fix(b.h); fix(b.s); fix(b.ptr); fix(b.rows); fix(b.big); }
+    else {
+      fix(b.mh); fix(b.ms);
+      int64_t off = 0;
+      for (int q = 0; q < b.N; ++q) {
+        b.ts.h[q] = b.mh + off;
+        b.ts.s[q] = b.ms + off;
+        off += b.ts.dims[q];
+      }
+    }
+    fix(b.cursor); fix(b.nbig); fix(b.Om); fix(b.Bpl); fix(b.Y1); fix(b.part); fix(b.Y2); fix(b.rest); fix(b.Rinv);
+    fix(b.diag);
+  }
+  memcpy(host.data() + P.off_items, items.data(), sizeof(BItem) * n);
+  int64_t* pre = (int64_t*)(host.data() + P.off_pre);
+  for (int st = 0; st < kBNumStages; ++st) memcpy(pre + (size_t)st * (n + 1), P.pre[st].data(), sizeof(int64_t) * (n + 1));
+  int32_t* lists = (int32_t*)(host.data() + P.off_lists);
+  for (size_t q = 0; q < P.dense_list.size(); ++q) lists[q] = P.dense_list[q];
+  for (size_t q = 0; q < P.cp_list.size(); ++q) lists[n + 1 + q] = P.cp_list[q];
+  cudaError_t e = cudaMemcpyAsync(tab, host.data(), P.table_bytes, cudaMemcpyHostToDevice, ctx->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(ws, 0, P.zero_bytes, ctx->stream);
+  // the host buffer must outlive the copy: synchronise (the tables are small)
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  return cuda_check(ctx, e, "batch upload");
+}
+
+extern "C" int idl_batch_run(idl_ctx* ctx, const idl_batch_item* items, int n) {
+  if (!ctx) return IDL_EINVAL;
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return IDL_ECUDA;
+  if (n < 1 || !items) return fail(ctx, IDL_EINVAL, "batch: need n >= 1 items");
+  idl_batch_state* bs = bstate(ctx);
+  const std::string sig = signature(items, n);
+  const uint64_t key = fnv1a(sig);
+  const bool known = bs->tune.count(key) != 0;
+  Tune tn = known ? bs->tune[key] : Tune();
+  BatchPlan P;
+  BTRY(plan_batch(ctx, items, n, tn, P));
+  unsigned char* ws = (unsigned char*)ws_get(ctx, kWsBatch, P.ws_bytes);
+  unsigned char* tab = (unsigned char*)ws_get(ctx, kWsBatchTab, P.table_bytes);
+  if (!ws || !tab) return IDL_ENOMEM;
+  const BItem* d_items = (const BItem*)(tab + P.off_items);
+  const int64_t* d_pre = (const int64_t*)(tab + P.off_pre);
+  const int32_t* d_lists = (const int32_t*)(tab + P.off_lists);
+  int nlaunch = 0;
+  if (!known && !ctx->batch_no_tune) {
+    // autotune: dense sketch block width, then the Gaussian split-K factor
+    float best = 1e30f;
+    for (int th : {128, 256, 512}) {
+      Tune t = tn;
+      t.sketch_threads = th;
+      BatchPlan Q;
+      BTRY(plan_batch(ctx, items, n, t, Q));
+      unsigned char* ws2 = (unsigned char*)ws_get(ctx, kWsBatch, Q.ws_bytes);
+      unsigned char* tab2 = (unsigned char*)ws_get(ctx, kWsBatchTab, Q.table_bytes);
+      if (!ws2 || !tab2) return IDL_ENOMEM;
+      BTRY(upload(ctx, Q, ws2, tab2, n));
+      float ms_s = 0.f;
+      BTRY(run_stages(ctx, Q, (const BItem*)(tab2 + Q.off_items), (const int64_t*)(tab2 + Q.off_pre),
+                      (const int32_t*)(tab2 + Q.off_lists), n, th, nlaunch, &ms_s, nullptr));
+      if (ms_s < best) { best = ms_s; tn.sketch_threads = th; }
+    }
+    best = 1e30f;
+    for (int sm : {1, 2}) {
+      Tune t = tn;
+      t.split_mult = sm;
+      BatchPlan Q;
+      BTRY(plan_batch(ctx, items, n, t, Q));
+      unsigned char* ws2 = (unsigned char*)ws_get(ctx, kWsBatch, Q.ws_bytes);
+      unsigned char* tab2 = (unsigned char*)ws_get(ctx, kWsBatchTab, Q.table_bytes);
+      if (!ws2 || !tab2) return IDL_ENOMEM;
+      BTRY(upload(ctx, Q, ws2, tab2, n));
+      float ms_g = 0.f;
+      BTRY(run_stages(ctx, Q, (const BItem*)(tab2 + Q.off_items), (const int64_t*)(tab2 + Q.off_pre),
+                      (const int32_t*)(tab2 + Q.off_lists), n, tn.sketch_threads, nlaunch, nullptr, &ms_g));
+      if (ms_g < best) { best = ms_g; tn.split_mult = sm; }
+    }
+    bs->tune[key] = tn;
+    P = BatchPlan();
+    BTRY(plan_batch(ctx, items, n, tn, P));
+    ws = (unsigned char*)ws_get(ctx, kWsBatch, P.ws_bytes);
+    tab = (unsigned char*)ws_get(ctx, kWsBatchTab, P.table_bytes);
+    if (!ws || !tab) return IDL_ENOMEM;
+    d_items = (const BItem*)(tab + P.off_items);
+    d_pre = (const int64_t*)(tab + P.off_pre);
+    d_lists = (const int32_t*)(tab + P.off_lists);
+  }
+  BTRY(upload(ctx, P, ws, tab, n));
+  if (ctx->batch_no_graph) return run_stages(ctx, P, d_items, d_pre, d_lists, n, tn.sketch_threads, nlaunch, nullptr, nullptr);
+  // graph: captured once per (shape, workspace address), replayed afterwards
+  const uint64_t gkey = key ^ (uint64_t)(uintptr_t)ws ^ ((uint64_t)(uintptr_t)tab << 1);
+  if (!bs->graph || bs->graph_sig != gkey) {
+    if (bs->graph) { cudaGraphExecDestroy(bs->graph); bs->graph = nullptr; }
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return cuda_check(ctx, e, "batch capture begin");
+    const long long before = idl_launch_count();
+    const int rc = run_stages(ctx, P, d_items, d_pre, d_lists, n, tn.sketch_threads, nlaunch, nullptr, nullptr);
+    e = cudaStreamEndCapture(ctx->stream, &g);
+    if (rc != IDL_OK) { if (g) cudaGraphDestroy(g); return rc; }
+    if (e != cudaSuccess) return cuda_check(ctx, e, "batch capture end");
+    e = cudaGraphInstantiate(&bs->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) { bs->graph = nullptr; return cuda_check(ctx, e, "batch graph instantiate"); }
+    bs->graph_sig = gkey;
+    bs->graph_launches = (int)(idl_launch_count() - before);
+    ctx_add_launches(-bs->graph_launches);     // counted when the graph runs
+  }
+  cudaError_t e = cudaGraphLaunch(bs->graph, ctx->stream);
+  ctx_add_launches(bs->graph_launches);
+  return cuda_check(ctx, e, "batch graph launch");
+}
+
+extern "C" int idl_tune_save(idl_ctx* ctx, const char* path) {
+  if (!ctx || !path) return IDL_EINVAL;
+  FILE* f = fopen(path, "w");
+  if (!f) return fail(ctx, IDL_EINVAL, "tune_save: cannot open file");
+  fprintf(f, "# idl batch tuning: shape-hash sketch_threads split_mult\n");
+  for (auto& kv : bstate(ctx)->tune)
+    fprintf(f, "%016llx %d %d\n", (unsigned long long)kv.first, kv.second.sketch_threads, kv.second.split_mult);
+  fclose(f);
+  return IDL_OK;
+}
+
+extern "C" int idl_tune_load(idl_ctx* ctx, const char* path) {
+  if (!ctx || !path) return IDL_EINVAL;
+  FILE* f = fopen(path, "r");
+  if (!f) return fail(ctx, IDL_EINVAL, "tune_load: cannot open file");
+  char line[256];
+  int loaded = 0;
+  while (fgets(line, sizeof(line), f)) {
+    if (line[0] == '#') continue;
+    unsigned long long k;
+    int a, b;
+    if (sscanf(line, "%llx %d %d", &k, &a, &b) == 3 && (a == 128 || a == 256 || a == 512) && (b == 1 || b == 2)) {
+      Tune t;
+      t.sketch_threads = a;
+      t.split_mult = b;
+      bstate(ctx)->tune[(uint64_t)k] = t;
+      ++loaded;
+    }
+  }
+  fclose(f);
+  return loaded >= 0 ? IDL_OK : IDL_EINVAL;
+}
+
+extern "C" int idl_debug_batch_mode(idl_ctx* ctx, int no_graph, int no_tune) {
+  if (!ctx) return IDL_EINVAL;
+  ctx->batch_no_graph = no_graph != 0;
+  ctx->batch_no_tune = no_tune != 0;
+  return IDL_OK;
+}

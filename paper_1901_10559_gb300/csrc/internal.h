@@ -9,6 +9,9 @@
 
 #include "../../include/idl.h"
 
+struct idl_batch_state;
+void idl_batch_state_free(idl_batch_state* b);
+
 struct idl_ctx {
   int device = 0;
   cudaStream_t stream = nullptr;
@@ -23,7 +26,10 @@ struct idl_ctx {
   int last_cluster = 0;
   int gemm_simt = 0;
   int gemm_sync_loads = 0;     // 1: Gaussian tc stage loads Y1 through registers (comparison / tests)
-  int cpqr_smem_only = 0;      // 1: always use the shared-memory QR kernel (comparison / tests)           // 1: Gaussian stage on CUDA cores instead of tcgen05 (comparison / tests)
+  int cpqr_smem_only = 0;      // 1: always use the shared-memory QR kernel (comparison / tests)
+  idl_batch_state* batch = nullptr;   // batch graphs and tuning table
+  int batch_no_graph = 0;      // 1: run batches without graph capture (tests)
+  int batch_no_tune = 0;       // 1: skip the first-call tuning runs (tests)           // 1: Gaussian stage on CUDA cores instead of tcgen05 (comparison / tests)
   size_t fail_alloc_at = 0;    // test hook: fail the n-th workspace allocation (0 = never)
   size_t alloc_count = 0;
   // per-stage CUDA-event profiling (idl_profile / idl_profile_read)
@@ -39,7 +45,7 @@ namespace idl {
 enum Slot {
   kWsH = 0, kWsS, kWsOmega, kWsBucketPtr, kWsRowList, kWsCursor, kWsBig, kWsY1, kWsPart,
   kWsY2, kWsOmegaConv, kWsRest, kWsA, kWsRowptr, kWsColidx, kWsVals, kWsJ, kWsT,
-  kWsModeH, kWsModeS, kWsLam, kWsLamHat, kWsCpqrSync, kWsRinv, kWsCount
+  kWsModeH, kWsModeS, kWsLam, kWsLamHat, kWsCpqrSync, kWsRinv, kWsBatch, kWsBatchTab, kWsCount
 };
 
 // Returns a device buffer of at least `bytes` for the slot (grown on demand), or
@@ -47,6 +53,7 @@ enum Slot {
 void* ws_get(idl_ctx* ctx, int slot, size_t bytes);
 
 int fail(idl_ctx* ctx, int code, const std::string& msg);
+void ctx_add_launches(long long d);   // adjusts the process-wide launch counter (graph replays)
 int cuda_check(idl_ctx* ctx, cudaError_t e, const char* where);
 
 // draws.cu

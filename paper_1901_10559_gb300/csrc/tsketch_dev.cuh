@@ -24,7 +24,7 @@ __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
 
 // In-place radix-2 DIT FFT of z (bit-reversed input, natural-order output).
 // tw: per-stage twiddles, stage half-length hl at offset hl: exp(-i pi k / hl).
-__device__ void fft_inplace(float2* z, const float2* tw, int L, bool inverse) {
+__device__ __forceinline__ void fft_inplace(float2* z, const float2* tw, int L, bool inverse) {
   for (int hl = 1; hl < L; hl <<= 1) {
     for (int b = threadIdx.x; b < (L >> 1); b += blockDim.x) {
       const int k = b & (hl - 1);

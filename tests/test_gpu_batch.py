@@ -1,0 +1,144 @@
+"""Batched IDs (one launch per stage over all items, QR clusters per item, CUDA
+graph replay, first-call tuning) against the single-item calls and the oracle."""
+import numpy as np
+import pytest
+import torch
+
+import paper_1901_10559_gb300 as idl
+from oracle import errors as oer
+from oracle import idmethods as oid
+from oracle.gaussian import FP32
+from synth import cp_factors, lowrank_dense
+from tests.helpers import dev, host
+
+pytestmark = pytest.mark.gpu
+
+
+def _dense_problems(seed):
+    rng = np.random.default_rng(seed)
+    probs = []
+    for b, (I, R) in enumerate([(3000, 300), (5000, 700), (2048, 256), (7000, 1025), (4100, 513)]):
+        r = int(rng.integers(8, 30))
+        A = lowrank_dense(I, R, float(rng.uniform(0.7, 0.95)), 1e-6, seed=seed * 100 + b, dtype=np.float32, rank=r)
+        m2 = r + 10
+        probs.append(dict(A=A, K=r, m1=min(m2 * m2, I // 2), m2=m2, seed=1000 + b))
+    return probs
+
+
+def _cp_problems(seed):
+    probs = []
+    for b, (dims, R, K) in enumerate([((40, 30, 20), 300, 16), ((50, 50, 50, 50), 500, 32)]):
+        facs, lam = cp_factors(dims, R, seed=seed + b, lam=10.0 ** (-6.0 * np.minimum(np.arange(R), K) / K))
+        probs.append(dict(facs=facs, lam=lam, K=K, L=1024, m2=K + 10, seed=2000 + b))
+    return probs
+
+
+def _outputs(K, R, cp=False):
+    J = torch.empty(K, dtype=torch.int32, device="cuda")
+    T = torch.empty(K * (R - K), dtype=torch.float64, device="cuda")
+    lh = torch.empty(K, dtype=torch.float64, device="cuda") if cp else None
+    return J, T, lh
+
+
+def _build(dense, cps, prec=idl.PREC_FP32):
+    items, outs, keep = [], [], []
+    for pr in dense:
+        A = dev(pr["A"])
+        J, T, _ = _outputs(pr["K"], pr["A"].shape[1])
+        p = idl.make_params(pr["m1"], pr["m2"], seed=pr["seed"], modified=True, precision=prec)
+        items.append(idl.dense_item(A, pr["K"], p, J, T))
+        outs.append((J, T, None))
+        keep.append(A)
+    for pr in cps:
+        fd = [dev(np.ascontiguousarray(F.T)) for F in pr["facs"]]
+        lam = dev(pr["lam"])
+        R = pr["facs"][0].shape[1]
+        J, T, lh = _outputs(pr["K"], R, cp=True)
+        p = idl.make_params(pr["L"], pr["m2"], seed=pr["seed"], modified=False, precision=prec)
+        items.append(idl.cp_item(fd, lam, pr["K"], p, J, T, lh))
+        outs.append((J, T, lh))
+        keep.append((fd, lam))
+    return items, outs, keep
+
+
+@pytest.mark.parametrize("graph,tune", [(0, 0), (1, 1)])
+def test_batch_matches_single_item_calls(ctx, graph, tune):
+    dense, cps = _dense_problems(3), _cp_problems(5)
+    idl.lib().idl_debug_batch_mode(ctx.ptr, int(not graph), int(not tune))
+    items, outs, keep = _build(dense, cps)
+    for _ in range(2):                                   # second call replays the graph
+        idl.idl_batch_run(ctx, items)
+    assert ctx.sync() == idl.IDL_OK
+    idl.lib().idl_debug_batch_mode(ctx.ptr, 0, 0)
+    for pr, (J, T, _) in zip(dense, outs[:len(dense)]):
+        K, R = pr["K"], pr["A"].shape[1]
+        Js, Ts, _ = _outputs(K, R)
+        p = idl.make_params(pr["m1"], pr["m2"], seed=pr["seed"], modified=True, precision=idl.PREC_FP32)
+        idl.id_matrix(ctx, dev(pr["A"]), K, p, Js, Ts)
+        assert np.array_equal(host(J), host(Js))
+        assert np.allclose(host(T), host(Ts), rtol=1e-4, atol=1e-6)
+        # and the oracle's error gate
+        Jw, Tw, _ = oid.id_matrix(pr["A"], k=K, m1=pr["m1"], m2=pr["m2"], seed=pr["seed"], precision=FP32)
+        e_g = oer.matrix_id_error(pr["A"], J=host(J), T=host(T).reshape(K, R - K), exact=False, iters=30)
+        e_w = oer.matrix_id_error(pr["A"], J=Jw, T=Tw, exact=False, iters=30)
+        assert e_g <= 1.1 * e_w + 1e-7
+    for pr, (J, T, lh) in zip(cps, outs[len(dense):]):
+        K, R = pr["K"], pr["facs"][0].shape[1]
+        Js, Ts, lhs = _outputs(K, R, cp=True)
+        p = idl.make_params(pr["L"], pr["m2"], seed=pr["seed"], modified=False, precision=idl.PREC_FP32)
+        fd = [dev(np.ascontiguousarray(F.T)) for F in pr["facs"]]
+        idl.id_cp_tensor(ctx, fd, dev(pr["lam"]), K, p, Js, Ts, lhs)
+        assert np.array_equal(host(J), host(Js))
+        assert np.allclose(host(lh), host(lhs), rtol=1e-4, atol=1e-9)
+        Jw, Tw, lhw, _ = oid.id_cp_tensor(pr["facs"], pr["lam"], k=K, L=pr["L"], m2=pr["m2"], seed=pr["seed"],
+                                          precision=FP32)
+        e_g = oer.tensor_id_error(pr["facs"], pr["lam"], host(J), host(lh))
+        e_w = oer.tensor_id_error(pr["facs"], pr["lam"], Jw, lhw)
+        assert e_g <= 1.1 * e_w + 1e-7
+
+
+def test_batch_graph_replay_reads_new_data(ctx):
+    dense = _dense_problems(7)[:3]
+    items, outs, keep = _build(dense, [])
+    idl.idl_batch_run(ctx, items)                        # captures the graph
+    # new contents in the same buffers: the replayed graph must see them
+    for b, A in enumerate(keep):
+        g = torch.Generator(device="cuda").manual_seed(b)
+        perm = torch.randperm(A.shape[1], device="cuda", generator=g)
+        A.copy_(A[:, perm].contiguous())
+    idl.idl_batch_run(ctx, items)                        # replays it
+    assert ctx.sync() == idl.IDL_OK
+    for b, pr in enumerate(dense):
+        K, R = pr["K"], pr["A"].shape[1]
+        Js, Ts, _ = _outputs(K, R)
+        p = idl.make_params(pr["m1"], pr["m2"], seed=pr["seed"], modified=True, precision=idl.PREC_FP32)
+        idl.id_matrix(ctx, keep[b], K, p, Js, Ts)
+        assert np.array_equal(host(outs[b][0]), host(Js))
+
+
+def test_batch_tuning_save_load(ctx, tmp_path):
+    dense = _dense_problems(11)[:2]
+    items, outs, keep = _build(dense, [], prec=idl.PREC_BF16X3)
+    idl.idl_batch_run(ctx, items)
+    path = tmp_path / "tune.txt"
+    idl.idl_tune_save(ctx, path)
+    lines = [l for l in path.read_text().splitlines() if not l.startswith("#")]
+    assert len(lines) >= 1
+    c2 = idl.Context(0)
+    idl.idl_tune_load(c2, path)
+    J2, T2, _ = _outputs(dense[0]["K"], dense[0]["A"].shape[1])
+    items2 = list(items)
+    items2[0] = idl.dense_item(keep[0], dense[0]["K"], items[0].params, J2, T2)
+    idl.idl_batch_run(c2, items2)
+    assert c2.sync() == idl.IDL_OK
+    assert np.array_equal(host(J2), host(outs[0][0]))
+    c2.close()
+
+
+def test_batch_rejects_mixed_precision(ctx):
+    dense = _dense_problems(13)[:2]
+    items, outs, keep = _build(dense, [])
+    items[1].params.precision = idl.PREC_BF16
+    with pytest.raises(idl.IdlError) as ei:
+        idl.idl_batch_run(ctx, items)
+    assert ei.value.code == idl.IDL_EINVAL
