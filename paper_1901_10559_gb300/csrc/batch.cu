@@ -273,7 +273,8 @@ struct idl_batch_state {
   uint64_t graph_sig = 0;
   cudaGraphExec_t graph = nullptr;
   int graph_launches = 0;
-  void* graph_ws = nullptr;
+  cudaStream_t gstream = nullptr;    // private stream: capture and replay (the legacy stream cannot be captured)
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
 };
 
 extern "C" long long idl_launch_count(void);
@@ -286,6 +287,9 @@ static idl_batch_state* bstate(idl_ctx* ctx) {
 void idl_batch_state_free(idl_batch_state* b) {
   if (!b) return;
   if (b->graph) cudaGraphExecDestroy(b->graph);
+  if (b->gstream) cudaStreamDestroy(b->gstream);
+  if (b->ev_in) cudaEventDestroy(b->ev_in);
+  if (b->ev_out) cudaEventDestroy(b->ev_out);
   delete b;
 }
 
@@ -706,16 +710,26 @@ extern "C" int idl_batch_run(idl_ctx* ctx, const idl_batch_item* items, int n) {
   }
   BTRY(upload(ctx, P, ws, tab, n));
   if (ctx->batch_no_graph) return run_stages(ctx, P, d_items, d_pre, d_lists, n, tn.sketch_threads, nlaunch, nullptr, nullptr);
-  // graph: captured once per (shape, workspace address), replayed afterwards
+  // graph: captured once per (shape, workspace address) on a private stream, replayed afterwards;
+  // events order it after the caller's stream and the caller's stream after it
+  if (!bs->gstream) {
+    cudaError_t e = cudaStreamCreateWithFlags(&bs->gstream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&bs->ev_in, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&bs->ev_out, cudaEventDisableTiming);
+    if (e != cudaSuccess) return cuda_check(ctx, e, "batch stream");
+  }
   const uint64_t gkey = key ^ (uint64_t)(uintptr_t)ws ^ ((uint64_t)(uintptr_t)tab << 1);
+  cudaStream_t user = ctx->stream;
   if (!bs->graph || bs->graph_sig != gkey) {
     if (bs->graph) { cudaGraphExecDestroy(bs->graph); bs->graph = nullptr; }
     cudaGraph_t g = nullptr;
-    cudaError_t e = cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal);
-    if (e != cudaSuccess) return cuda_check(ctx, e, "batch capture begin");
+    ctx->stream = bs->gstream;
+    cudaError_t e = cudaStreamBeginCapture(bs->gstream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) { ctx->stream = user; return cuda_check(ctx, e, "batch capture begin"); }
     const long long before = idl_launch_count();
     const int rc = run_stages(ctx, P, d_items, d_pre, d_lists, n, tn.sketch_threads, nlaunch, nullptr, nullptr);
-    e = cudaStreamEndCapture(ctx->stream, &g);
+    e = cudaStreamEndCapture(bs->gstream, &g);
+    ctx->stream = user;
     if (rc != IDL_OK) { if (g) cudaGraphDestroy(g); return rc; }
     if (e != cudaSuccess) return cuda_check(ctx, e, "batch capture end");
     e = cudaGraphInstantiate(&bs->graph, g, 0);
@@ -725,7 +739,11 @@ extern "C" int idl_batch_run(idl_ctx* ctx, const idl_batch_item* items, int n) {
     bs->graph_launches = (int)(idl_launch_count() - before);
     ctx_add_launches(-bs->graph_launches);     // counted when the graph runs
   }
-  cudaError_t e = cudaGraphLaunch(bs->graph, ctx->stream);
+  cudaError_t e = cudaEventRecord(bs->ev_in, user);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(bs->gstream, bs->ev_in, 0);
+  if (e == cudaSuccess) e = cudaGraphLaunch(bs->graph, bs->gstream);
+  if (e == cudaSuccess) e = cudaEventRecord(bs->ev_out, bs->gstream);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(user, bs->ev_out, 0);
   ctx_add_launches(bs->graph_launches);
   return cuda_check(ctx, e, "batch graph launch");
 }
