@@ -99,6 +99,7 @@ _SIGS = {
     "idl_tune_save": ([_vp, ctypes.c_char_p], _int),
     "idl_tune_load": ([_vp, ctypes.c_char_p], _int),
     "idl_debug_batch_mode": ([_vp, _int, _int], _int),
+    "idl_debug_batch_timing": ([_vp, ctypes.POINTER(BatchItem), _int, ctypes.POINTER(ctypes.c_float)], _int),
 }
 
 
@@ -336,3 +337,11 @@ def idl_tune_save(ctx, path):
 
 def idl_tune_load(ctx, path):
     return ctx.check(lib().idl_tune_load(ctx.ptr, str(path).encode()))
+
+
+def batch_stage_ms(ctx, items):
+    """(dense sketch ms, Gaussian stage ms) of one un-graphed, event-timed run of the batch."""
+    arr = (BatchItem * len(items))(*items)
+    ms = (ctypes.c_float * 2)()
+    ctx.check(lib().idl_debug_batch_timing(ctx.ptr, arr, len(items), ms))
+    return float(ms[0]), float(ms[1])

@@ -781,6 +781,24 @@ extern "C" int idl_tune_load(idl_ctx* ctx, const char* path) {
   return loaded >= 0 ? IDL_OK : IDL_EINVAL;
 }
 
+// Runs the batch once without the graph, with CUDA events around the dense sketch
+// and the Gaussian stage (ms[0], ms[1]); used to attribute time to the kernels.
+extern "C" int idl_debug_batch_timing(idl_ctx* ctx, const idl_batch_item* items, int n, float* ms) {
+  if (!ctx || !items || n < 1 || !ms) return IDL_EINVAL;
+  idl_batch_state* bs = bstate(ctx);
+  const uint64_t key = fnv1a(signature(items, n));
+  Tune tn = bs->tune.count(key) ? bs->tune[key] : Tune();
+  BatchPlan P;
+  BTRY(plan_batch(ctx, items, n, tn, P));
+  unsigned char* ws = (unsigned char*)ws_get(ctx, kWsBatch, P.ws_bytes);
+  unsigned char* tab = (unsigned char*)ws_get(ctx, kWsBatchTab, P.table_bytes);
+  if (!ws || !tab) return IDL_ENOMEM;
+  BTRY(upload(ctx, P, ws, tab, n));
+  int nl = 0;
+  return run_stages(ctx, P, (const BItem*)(tab + P.off_items), (const int64_t*)(tab + P.off_pre),
+                    (const int32_t*)(tab + P.off_lists), n, tn.sketch_threads, nl, &ms[0], &ms[1]);
+}
+
 extern "C" int idl_debug_batch_mode(idl_ctx* ctx, int no_graph, int no_tune) {
   if (!ctx) return IDL_EINVAL;
   ctx->batch_no_graph = no_graph != 0;
