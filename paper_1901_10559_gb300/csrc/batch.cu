@@ -324,7 +324,7 @@ static bool pick_cpqr(const std::vector<int>& list, const std::vector<BItem>& it
   const int CS = 16;
 #define PICK(VV, TT) if (cpqr_cfg_fits<VV, TT>(list, it, CS, cfg)) return true;
   PICK(8, 32) PICK(8, 16) PICK(8, 8) PICK(16, 8) PICK(8, 4) PICK(16, 4) PICK(32, 4) PICK(16, 2) PICK(32, 2)
-  PICK(16, 1) PICK(32, 1) PICK(64, 4) PICK(64, 2) PICK(64, 1)
+  PICK(16, 1) PICK(32, 1) PICK(64, 4) PICK(64, 2) PICK(64, 1) PICK(96, 1) PICK(128, 1)
 #undef PICK
   return false;
 }
@@ -355,7 +355,7 @@ static int launch_b_cpqr(idl_ctx* ctx, const BItem* d_items, const int32_t* d_li
 static int dispatch_b_cpqr(idl_ctx* ctx, const BItem* d_items, const int32_t* d_list, int nlist, const CpqrCfg& c) {
 #define CASE(VV, TT) if (c.V == VV && c.TPC == TT) return launch_b_cpqr<VV, TT>(ctx, d_items, d_list, nlist, c);
   CASE(8, 32) CASE(8, 16) CASE(8, 8) CASE(16, 8) CASE(8, 4) CASE(16, 4) CASE(32, 4) CASE(16, 2) CASE(32, 2)
-  CASE(16, 1) CASE(32, 1) CASE(64, 4) CASE(64, 2) CASE(64, 1)
+  CASE(16, 1) CASE(32, 1) CASE(64, 4) CASE(64, 2) CASE(64, 1) CASE(96, 1) CASE(128, 1)
 #undef CASE
   return fail(ctx, IDL_ELIMIT, "batch cpqr: no configuration");
 }

@@ -278,7 +278,7 @@ static int reg_cpqr(idl_ctx* ctx, const T* Yin, T* Yout, int64_t m, int64_t R, i
     // most lanes per column first (shortest serial chain per step)
     TRY_CFG(8, 32) TRY_CFG(8, 16) TRY_CFG(8, 8) TRY_CFG(16, 8) TRY_CFG(8, 4) TRY_CFG(16, 4) TRY_CFG(32, 4)
     TRY_CFG(16, 2) TRY_CFG(32, 2) TRY_CFG(16, 1) TRY_CFG(32, 1)
-    if constexpr (sizeof(T) == 4) { TRY_CFG(64, 4) TRY_CFG(64, 2) TRY_CFG(64, 1) }
+    if constexpr (sizeof(T) == 4) { TRY_CFG(64, 4) TRY_CFG(64, 2) TRY_CFG(64, 1) TRY_CFG(96, 1) TRY_CFG(128, 1) }
 #undef TRY_CFG
   }
   return IDL_OK;

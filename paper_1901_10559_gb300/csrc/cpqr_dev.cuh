@@ -48,8 +48,8 @@ __device__ __forceinline__ double group_sum(double v, int tpc) {
 // compiled for: sized so the column registers fit without spilling.
 template <typename T, int V, int TPC> struct RegCpqr {
   static constexpr int kWords = V * (int)(sizeof(T) / 4);
-  static constexpr int kMaxThreads = kWords <= 16 ? 1024 : (kWords <= 32 ? (TPC == 1 ? 896 : 768)
-                                                                   : (TPC == 1 ? 640 : 512));
+  static constexpr int kMaxThreads = kWords <= 16 ? 1024 : kWords <= 32 ? (TPC == 1 ? 896 : 768)
+                                   : kWords <= 64 ? (TPC == 1 ? 640 : 512) : kWords <= 96 ? 448 : 384;
 };
 
 // Body of one cluster working on one problem (Yin/Yout m x R column-major, ld);
