@@ -20,7 +20,9 @@ matrix and tensor interpolative decomposition using CountSketch"):
                      s-value update lambda_hat)
   errors.py       -- ID error evaluation (spectral norm, Gram identity
                      Eq. MTM-formula for CP tensors)
-  mlp.py          -- the column-scoring MLP's forward / backward in float64
+  proposal.py     -- the learned column proposal for the QR stage: column
+                     features, the scoring MLP (forward, backward, Adam),
+                     top-C candidates and the certificate
 
 Parity status: every function is pinned by tests in ``tests/test_oracle_*``
 (closed forms, invariants, brute force, independent library routines).  The
