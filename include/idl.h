@@ -61,7 +61,7 @@ typedef struct idl_params {
   int32_t  precision; /* IDL_PREC_*; with IDL_F64 data only IDL_PREC_FP64 is accepted */
   uint64_t seed;      /* seed of the counter-based draws (h, s, the permutation, Omega) */
   int32_t  residual;  /* 0: none; 1: ||R22||_F / ||Y2||_F in FP64 (default); 2: explicit FP64 ||Y2_rest - Y2_J T||_F / ||Y2||_F */
-  int32_t  reserved0;
+  int32_t  learned;   /* QR stage column proposal: IDL_PROPOSAL_NONE (default), _MLP or _NORM (FP32 data, m <= 128) */
   int64_t  reserved[4];
 } idl_params;
 
@@ -73,7 +73,7 @@ typedef struct idl_info {
   int32_t  status;     /* device status word (IDL_OK, IDL_ERANK, IDL_EDATA, IDL_ETIMEOUT) */
   int32_t  precision;  /* precision actually used */
   int32_t  cluster;    /* CTAs in the QR stage's thread-block cluster */
-  int32_t  reserved;
+  int32_t  proposal;   /* 0: plain QR; 1: proposal certified; 2: proposal rejected, plain QR ran */
 } idl_info;
 
 /* ---------------------------------------------------------------------------
@@ -271,6 +271,83 @@ int id_cp_tensor(idl_ctx* ctx, int N, const int64_t* dims, int64_t R, const void
  *   single-item calls.  The call is asynchronous after its first use of a
  *   shape; idl_sync returns the device status word.
  * ------------------------------------------------------------------------- */
+/* ---------------------------------------------------------------------------
+ * Learned column proposal for the QR stage (not in the paper; an acceleration
+ * of Algorithm 1's pivot search that never changes its result).
+ *   With idl_params.learned = IDL_PROPOSAL_MLP the QR stage scores every
+ *   column of the sketch Y2 (m x R) with a 3-layer MLP (width 128, bfloat16
+ *   operands, FP32 accumulation) on 8 features per column: log and square root
+ *   of the relative squared norm, three ridge leverage scores
+ *   y^T (Y2 Y2^T + lambda I)^{-1} y with lambda = {1e-1, 1e-2, 1e-3} tr(Y2 Y2^T)/m,
+ *   max |y_i| / ||y||, K/R and m/R.  The C = min(2K, R) best columns (ties:
+ *   smaller index) go through the pivoted QR in one CTA; its reflectors are
+ *   applied to every other column, and the certificate checks that no outside
+ *   column's remaining norm reaches a step's pivot norm (squared norms within a
+ *   relative margin of 1e-4).  If it holds, J and the factored sketch equal
+ *   those of the plain QR; otherwise the plain QR runs (idl_info.proposal = 2).
+ *   IDL_PROPOSAL_NORM is the ablation that scores columns by their norm.
+ *   Needs FP32 data, m <= 128, K <= 128 (IDL_ELIMIT otherwise), and weights
+ *   (idl_mlp_init, idl_mlp_set_weights or idl_load_weights) for _MLP.
+ *
+ * Parameters: IDL_MLP_NPARAM floats, flat: W1 (128 x 8 row-major), b1 (128),
+ *   W2 (128 x 128 row-major), b2 (128), w3 (128), b3 (1); the context keeps
+ *   them in FP32 (master copy for training) and rounds W1, W2, w3, the
+ *   features and the first hidden layer to bfloat16 when it multiplies.
+ * idl_mlp_set_weights / idl_mlp_get_weights: host or device pointer; setting
+ *   resets the optimizer state.  idl_mlp_init: He-style random weights.
+ * idl_save_weights / idl_load_weights: binary file "IDLMLP01", uint32 version
+ *   1, 8, 128, IDL_MLP_NPARAM, the parameters (float32 little endian), uint64
+ *   FNV-1a hash of the parameter bytes; a wrong layout or hash is IDL_EINVAL.
+ * idl_proposal_features: F (R x 8 row-major FP32, device) of Y (m x R
+ *   column-major, ldy >= m, FP32, device); m <= 128.
+ * idl_mlp_scores: s[i] = MLP(F[i, :]) for n examples (device pointers).
+ * idl_mlp_grad: mean loss over n examples with labels y in {0, 1}
+ *   (pos_weight * y * softplus(-s) + (1 - y) * softplus(s)) and its gradient
+ *   (IDL_MLP_NPARAM floats) with respect to the FP32 weights, treating the
+ *   bfloat16 rounding as the identity; device pointers, no update.
+ * idl_proposal_labels: training examples of one sketch: F as above and
+ *   y[c] = 1 for the K pivots of the plain QR of Y (run on a copy), else 0.
+ * idl_train_proposal: Adam (Kingma & Ba 2015) on the context's weights over
+ *   n device-resident examples, minibatches of tp->batch in a seeded permuted
+ *   order per epoch; epoch_loss (host, tp->epochs floats, optional) receives
+ *   each epoch's mean minibatch loss.  Initialises the weights if none are set.
+ * ------------------------------------------------------------------------- */
+#define IDL_PROPOSAL_NONE 0
+#define IDL_PROPOSAL_MLP  1
+#define IDL_PROPOSAL_NORM 2
+#define IDL_MLP_NPARAM 17793
+
+typedef struct idl_train_params {
+  int32_t  epochs;
+  int32_t  batch;       /* examples per Adam step */
+  float    lr;
+  float    beta1, beta2, eps;   /* 0 = defaults 0.9, 0.999, 1e-8 */
+  float    pos_weight;  /* weight of the positive (pivot) examples; 0 = 1 */
+  int32_t  reserved0;
+  uint64_t seed;        /* epoch orders (and the initial weights if none are set) */
+} idl_train_params;
+
+int idl_mlp_init(idl_ctx* ctx, uint64_t seed);
+int idl_mlp_set_weights(idl_ctx* ctx, const float* theta);
+int idl_mlp_get_weights(idl_ctx* ctx, float* theta);
+int idl_save_weights(idl_ctx* ctx, const char* path);
+int idl_load_weights(idl_ctx* ctx, const char* path);
+int idl_proposal_features(idl_ctx* ctx, const float* Y, int64_t m, int64_t R, int64_t ldy, int64_t K, float* F);
+int idl_mlp_scores(idl_ctx* ctx, const float* F, int64_t n, float* s);
+int idl_mlp_grad(idl_ctx* ctx, const float* F, const float* y, int64_t n, float pos_weight, float* grad,
+                 float* loss);
+int idl_proposal_labels(idl_ctx* ctx, const float* Y, int64_t m, int64_t R, int64_t ldy, int64_t K,
+                        float* F, float* y);
+int idl_train_proposal(idl_ctx* ctx, const float* F, const float* y, int64_t n, const idl_train_params* tp,
+                       float* epoch_loss);
+/* The QR stage through the proposal on a given sketch: Y2 (m x R column-major,
+ * ldy2 >= m, FP32, device, read only) -> Yf (same shape, the factored sketch
+ * as idl_cpqr leaves it), J (K int32, device).  mode: IDL_PROPOSAL_MLP or
+ * IDL_PROPOSAL_NORM.  proposal (host, optional): 1 certified, 2 rejected
+ * (the plain QR ran); passing it synchronises the stream. */
+int idl_cpqr_proposal(idl_ctx* ctx, const float* Y2, float* Yf, int64_t m, int64_t R, int64_t ldy2,
+                      int64_t K, int mode, int32_t* J, int* proposal);
+
 #define IDL_ITEM_DENSE 0
 #define IDL_ITEM_CP    2
 
@@ -283,13 +360,17 @@ typedef struct idl_batch_item {
   int64_t       dims[8];     /* CP: mode sizes */
   const float*  factors[8];  /* CP: factor matrices, column r of mode n at factors[n] + r*dims[n] (device) */
   const double* lambda;      /* CP: R s-values (device) */
-  idl_params    params;      /* m1 (the TensorSketch length L for CP), m2, modified, precision, seed */
+  idl_params    params;      /* m1 (the TensorSketch length L for CP), m2, modified, precision, seed, learned */
   int32_t*      J;           /* out: K pivots (device) */
   double*       T;           /* out: K x (R-K) FP64 (device) */
   double*       lambda_hat;  /* out, CP: K s-values (device) */
 } idl_batch_item;
 
 int idl_batch_run(idl_ctx* ctx, const idl_batch_item* items, int n);
+/* Items of the last idl_batch_run whose column proposal (params.learned) was
+ * rejected by its certificate, so that the plain QR ran; synchronises the
+ * stream.  Returns the count (>= 0) or minus an error code. */
+int idl_batch_fallbacks(idl_ctx* ctx);
 int idl_tune_save(idl_ctx* ctx, const char* path);
 int idl_tune_load(idl_ctx* ctx, const char* path);
 

@@ -37,16 +37,26 @@ class IdlError(RuntimeError):
 class Params(ctypes.Structure):
     _fields_ = [("m1", ctypes.c_int64), ("m2", ctypes.c_int64), ("modified", ctypes.c_int32),
                 ("precision", ctypes.c_int32), ("seed", ctypes.c_uint64), ("residual", ctypes.c_int32),
-                ("reserved0", ctypes.c_int32), ("reserved", ctypes.c_int64 * 4)]
+                ("learned", ctypes.c_int32), ("reserved", ctypes.c_int64 * 4)]
 
 
 class Info(ctypes.Structure):
     _fields_ = [("residual", ctypes.c_double), ("rkk_ratio", ctypes.c_double), ("y2_norm", ctypes.c_double),
                 ("status", ctypes.c_int32), ("precision", ctypes.c_int32), ("cluster", ctypes.c_int32),
-                ("reserved", ctypes.c_int32)]
+                ("proposal", ctypes.c_int32)]
 
     def as_dict(self):
-        return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+PROPOSAL_NONE, PROPOSAL_MLP, PROPOSAL_NORM = 0, 1, 2
+MLP_NPARAM = 17793
+
+
+class TrainParams(ctypes.Structure):
+    _fields_ = [("epochs", ctypes.c_int32), ("batch", ctypes.c_int32), ("lr", ctypes.c_float),
+                ("beta1", ctypes.c_float), ("beta2", ctypes.c_float), ("eps", ctypes.c_float),
+                ("pos_weight", ctypes.c_float), ("reserved0", ctypes.c_int32), ("seed", ctypes.c_uint64)]
 
 
 IDL_ITEM_DENSE, IDL_ITEM_CP = 0, 2
@@ -100,6 +110,18 @@ _SIGS = {
     "idl_tune_load": ([_vp, ctypes.c_char_p], _int),
     "idl_debug_batch_mode": ([_vp, _int, _int], _int),
     "idl_debug_batch_timing": ([_vp, ctypes.POINTER(BatchItem), _int, ctypes.POINTER(ctypes.c_float)], _int),
+    "idl_batch_fallbacks": ([_vp], _int),
+    "idl_mlp_init": ([_vp, _u64], _int),
+    "idl_mlp_set_weights": ([_vp, _vp], _int),
+    "idl_mlp_get_weights": ([_vp, _vp], _int),
+    "idl_save_weights": ([_vp, ctypes.c_char_p], _int),
+    "idl_load_weights": ([_vp, ctypes.c_char_p], _int),
+    "idl_proposal_features": ([_vp, _vp, _i64, _i64, _i64, _i64, _vp], _int),
+    "idl_mlp_scores": ([_vp, _vp, _i64, _vp], _int),
+    "idl_mlp_grad": ([_vp, _vp, _vp, _i64, ctypes.c_float, _vp, _vp], _int),
+    "idl_proposal_labels": ([_vp, _vp, _i64, _i64, _i64, _i64, _vp, _vp], _int),
+    "idl_train_proposal": ([_vp, _vp, _vp, _i64, ctypes.POINTER(TrainParams), _vp], _int),
+    "idl_cpqr_proposal": ([_vp, _vp, _vp, _i64, _i64, _i64, _i64, _int, _vp, ctypes.POINTER(ctypes.c_int)], _int),
 }
 
 
@@ -189,10 +211,11 @@ def launch_count() -> int:
     return int(lib().idl_launch_count())
 
 
-def make_params(m1, m2, seed, modified=True, precision=PREC_FP32, residual=1):
+def make_params(m1, m2, seed, modified=True, precision=PREC_FP32, residual=1, learned=PROPOSAL_NONE):
     p = Params()
     p.m1, p.m2, p.modified, p.precision, p.seed, p.residual = int(m1), int(m2), int(modified), int(precision), \
         int(seed), int(residual)
+    p.learned = int(learned)
     return p
 
 
@@ -345,3 +368,67 @@ def batch_stage_ms(ctx, items):
     ms = (ctypes.c_float * 2)()
     ctx.check(lib().idl_debug_batch_timing(ctx.ptr, arr, len(items), ms))
     return float(ms[0]), float(ms[1])
+
+
+# ---------------------------------------------------------------- learned column proposal
+def idl_mlp_init(ctx, seed):
+    ctx.check(lib().idl_mlp_init(ctx.ptr, int(seed)))
+
+
+def idl_mlp_set_weights(ctx, theta):
+    """theta: IDL_MLP_NPARAM float32 values (numpy host array or CUDA tensor)."""
+    ctx.check(lib().idl_mlp_set_weights(ctx.ptr, _p(theta)))
+
+
+def idl_mlp_get_weights(ctx, theta):
+    ctx.check(lib().idl_mlp_get_weights(ctx.ptr, _p(theta)))
+
+
+def idl_save_weights(ctx, path):
+    ctx.check(lib().idl_save_weights(ctx.ptr, os.fsencode(path)))
+
+
+def idl_load_weights(ctx, path):
+    ctx.check(lib().idl_load_weights(ctx.ptr, os.fsencode(path)))
+
+
+def idl_proposal_features(ctx, Y, m, R, ldy, K, F):
+    ctx.check(lib().idl_proposal_features(ctx.ptr, _p(Y), m, R, ldy, K, _p(F)))
+
+
+def idl_mlp_scores(ctx, F, n, s):
+    ctx.check(lib().idl_mlp_scores(ctx.ptr, _p(F), n, _p(s)))
+
+
+def idl_mlp_grad(ctx, F, y, n, pos_weight, grad, loss):
+    ctx.check(lib().idl_mlp_grad(ctx.ptr, _p(F), _p(y), n, float(pos_weight), _p(grad), _p(loss)))
+
+
+def idl_proposal_labels(ctx, Y, m, R, ldy, K, F, y):
+    ctx.check(lib().idl_proposal_labels(ctx.ptr, _p(Y), m, R, ldy, K, _p(F), _p(y)))
+
+
+def idl_train_proposal(ctx, F, y, n, epochs, batch, lr, pos_weight=1.0, seed=0, beta1=0.9, beta2=0.999, eps=1e-8):
+    """Returns the per-epoch mean loss (list of floats)."""
+    tp = TrainParams()
+    tp.epochs, tp.batch, tp.lr, tp.pos_weight, tp.seed = int(epochs), int(batch), float(lr), float(pos_weight), \
+        int(seed)
+    tp.beta1, tp.beta2, tp.eps = float(beta1), float(beta2), float(eps)
+    out = (ctypes.c_float * int(epochs))()
+    ctx.check(lib().idl_train_proposal(ctx.ptr, _p(F), _p(y), n, ctypes.byref(tp), ctypes.cast(out, _vp)))
+    return list(out)
+
+
+def idl_batch_fallbacks(ctx):
+    """Items of the last idl_batch_run whose proposal certificate failed (synchronises)."""
+    rc = lib().idl_batch_fallbacks(ctx.ptr)
+    if rc < 0:
+        raise IdlError(-rc, lib().idl_last_error(ctx.ptr).decode())
+    return rc
+
+
+def idl_cpqr_proposal(ctx, Y2, Yf, m, R, ldy2, K, mode, J):
+    """Returns 1 (certified) or 2 (rejected: the plain QR ran)."""
+    out = ctypes.c_int(0)
+    ctx.check(lib().idl_cpqr_proposal(ctx.ptr, _p(Y2), _p(Yf), m, R, ldy2, K, int(mode), _p(J), ctypes.byref(out)))
+    return out.value

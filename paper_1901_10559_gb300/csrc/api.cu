@@ -137,23 +137,25 @@ static const void* stage_in(idl_ctx* ctx, const void* p, size_t bytes, int slot,
 }
 
 static int clear_diag(idl_ctx* ctx) {
-  return cuda_check(ctx, cudaMemsetAsync(ctx->d_diag, 0, sizeof(double) * 8, ctx->stream), "diag clear");
+  return cuda_check(ctx, cudaMemsetAsync(ctx->d_diag, 0, sizeof(double) * 16, ctx->stream), "diag clear");
 }
 
 static int finish_info(idl_ctx* ctx, const idl_params* p, int precision, idl_info* info, int64_t K, int64_t R) {
   (void)K; (void)R;
   if (!info) return IDL_OK;
   double d[8];
-  int st = 0;
+  int stw[2] = {0, 0};
   cudaError_t e = cudaMemcpyAsync(d, ctx->d_diag, sizeof(d), cudaMemcpyDeviceToHost, ctx->stream);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(&st, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(stw, ctx->d_status, sizeof(stw), cudaMemcpyDeviceToHost, ctx->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
   TRY(cuda_check(ctx, e, "info readback"));
+  int st = stw[0];
   memset(info, 0, sizeof(*info));
+  info->proposal = p->learned ? (stw[1] ? 2 : 1) : 0;
   info->y2_norm = std::sqrt(d[1]);
   info->rkk_ratio = d[3] > 0 ? d[4] / d[3] : 0.0;
   info->precision = precision;
-  info->cluster = ctx->last_cluster;
+  info->cluster = info->proposal == 1 ? 1 : ctx->last_cluster;
   const int mode = p->residual;
   if (mode == 1) info->residual = d[1] > 0 ? std::sqrt(d[0] / d[1]) : 0.0;
   else if (mode == 2) info->residual = d[1] > 0 ? std::sqrt(d[2] / d[1]) : 0.0;
@@ -189,12 +191,12 @@ extern "C" int idl_create(idl_ctx** out, int device) {
   c->num_sms = prop.multiProcessorCount;
   c->smem_optin = (int)prop.sharedMemPerBlockOptin;
   if (cudaMalloc(&c->d_status, sizeof(int) * 4) != cudaSuccess ||
-      cudaMalloc(&c->d_diag, sizeof(double) * 8) != cudaSuccess) {
+      cudaMalloc(&c->d_diag, sizeof(double) * 16) != cudaSuccess) {
     delete c;
     return IDL_ENOMEM;
   }
   cudaMemset(c->d_status, 0, sizeof(int) * 4);
-  cudaMemset(c->d_diag, 0, sizeof(double) * 8);
+  cudaMemset(c->d_diag, 0, sizeof(double) * 16);
   *out = c;
   return IDL_OK;
 }
@@ -207,6 +209,7 @@ extern "C" int idl_destroy(idl_ctx* ctx) {
     if (b.p) cudaFree(b.p);
   for (auto& pp : ctx->prof) { cudaEventDestroy(pp.a); cudaEventDestroy(pp.b); }
   idl_batch_state_free(ctx->batch);
+  if (ctx->mlp) cudaFree(ctx->mlp);
   cudaFree(ctx->d_status);
   cudaFree(ctx->d_diag);
   delete ctx;
@@ -408,6 +411,11 @@ static int check_params(idl_ctx* ctx, const idl_params* p, int dtype, int64_t I,
   if (tensor && (p->m1 & (p->m1 - 1))) return fail(ctx, IDL_EINVAL, "TensorSketch length must be a power of two");
   if (p->residual < 0 || p->residual > 2) return fail(ctx, IDL_EINVAL, "residual mode must be 0, 1 or 2");
   if (R > 0x7fffffffLL || I > 0x7fffffffLL) return fail(ctx, IDL_ELIMIT, "I and R must fit in int32");
+  if (p->learned < IDL_PROPOSAL_NONE || p->learned > IDL_PROPOSAL_NORM)
+    return fail(ctx, IDL_EINVAL, "unknown proposal mode");
+  if (p->learned && dtype != IDL_F32) return fail(ctx, IDL_EINVAL, "the column proposal needs FP32 data");
+  if (p->learned && ((p->m2 > 0 ? p->m2 : p->m1) > 128 || K > 128))
+    return fail(ctx, IDL_ELIMIT, "the column proposal needs m <= 128 and K <= 128");
   return IDL_OK;
 }
 
@@ -428,7 +436,11 @@ static int finish_pipeline(idl_ctx* ctx, const idl_params* p, int dtype, void* Y
     STAGE(kStGauss, launch_transpose_to_colmajor(ctx, Y1, m, R, ldy1, dtype, Y2, ld2));
   }
   void* Yf = Y2;
-  if (keep_orig) {
+  if (p->learned) {
+    // the proposal reads the sketch and writes the factored copy; the fallback re-reads the sketch
+    Yf = ws_get(ctx, kWsYf, (size_t)es * (size_t)(R * ld2));
+    if (!Yf) return IDL_ENOMEM;
+  } else if (keep_orig) {
     Yf = (char*)Y2 + (size_t)es * (size_t)(R * ld2);
     TRY(cuda_check(ctx, cudaMemcpyAsync(Yf, Y2, (size_t)es * R * ld2, cudaMemcpyDeviceToDevice, ctx->stream), "copy"));
   }
@@ -439,7 +451,10 @@ static int finish_pipeline(idl_ctx* ctx, const idl_params* p, int dtype, void* Y
   if (!tdev) { Td = (double*)ws_get(ctx, kWsT, sizeof(double) * (size_t)(K * (R - K))); if (!Td) return IDL_ENOMEM; }
   WS(rest, int32_t, kWsRest, R);
   TRY(clear_diag(ctx));
-  STAGE(kStQR, launch_cpqr(ctx, Yf, m, R, ld2, dtype, K, Jd, nullptr));
+  if (p->learned)
+    STAGE(kStQR, launch_proposal_qr(ctx, (const float*)Y2, (float*)Yf, m, R, ld2, K, p->learned, Jd));
+  else
+    STAGE(kStQR, launch_cpqr(ctx, Yf, m, R, ld2, dtype, K, Jd, nullptr));
   STAGE(kStSolve, launch_t_solve(ctx, Yf, m, R, ld2, dtype, K, Jd, Td, rest));
   if (keep_orig) STAGE(kStCheck, launch_residual(ctx, Y2, Yf, m, R, ld2, dtype, K, Jd, Td, rest));
   if (!jdev)

@@ -10,6 +10,11 @@
 // memory, so the launch sequence of a batch shape is captured once into a CUDA
 // graph and replayed; descriptors are re-uploaded before each replay.
 //
+// Column proposal (idl_params.learned): items that ask for it get the
+// proposal stages (features, MLP or norm scores, selection, one-CTA candidate
+// QR, certificate) before the cluster QR launch, in which their clusters only
+// run when the certificate failed (a per-item gate read at block start).
+//
 // Tuning: the dense sketch's block width and the Gaussian stage's split-K
 // factor are chosen per batch shape by timing the candidates on the first
 // call (CUDA events around the two stages); the choice is kept in the context
@@ -30,6 +35,7 @@
 #include "draws_dev.cuh"
 #include "gemm_dev.cuh"
 #include "internal.h"
+#include "proposal_dev.cuh"
 #include "sketch_dev.cuh"
 #include "tsketch_dev.cuh"
 #include "tsolve_dev.cuh"
@@ -61,11 +67,20 @@ struct BItem {
   double* T;
   double* lam_hat;
   int nc;
+  // column proposal
+  int learned, C, nsplit;
+  float* Yf;                       // factored sketch (== Y2 without a proposal)
+  float *Gp, *nmaxp, *scal, *Linv, *F, *sc, *V, *beta;
+  int32_t *cand, *outl;
+  double* rn;
+  int* flag;                       // certificate failed
+  const int* gate;                 // == flag for proposal items, nullptr otherwise
 };
 
 // stages with a flattened block list (prefix tables, one per stage)
 enum BStage { kBDraw = 0, kBGauss, kBHist, kBScan, kBScatter, kBSortW, kBSortB, kBSketchD, kBSketchT, kBPlanes,
-              kBGemm, kBReduce, kBRest, kBRinv, kBTgemm, kBLam, kBNumStages };
+              kBGemm, kBReduce, kBPGram, kBPChol, kBPFeat, kBPMlp, kBPNorm, kBPSel, kBPApply, kBRest, kBRinv,
+              kBTgemm, kBLam, kBNumStages };
 
 __device__ __forceinline__ int find_item(const int64_t* __restrict__ pre, int n, int64_t blk) {
   int lo = 0, hi = n - 1;                          // largest p with pre[p] <= blk
@@ -197,8 +212,71 @@ __global__ void __launch_bounds__(RegCpqr<float, V, TPC>::kMaxThreads, 1)
 b_cpqr_kernel(const BItem* __restrict__ items, const int32_t* __restrict__ list, int CS, int* status) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const BItem& it = items[list[blockIdx.x / CS]];
-  cpqr_reg_body<float, V, TPC>(it.Y2, it.Y2, (int)it.m2, (int)it.R, (int)it.m2, it.K, it.nc, it.J, nullptr, it.diag,
+  if (proposal_certified(it.gate, it.diag)) return;     // the whole cluster belongs to this item
+  cpqr_reg_body<float, V, TPC>(it.Y2, it.Yf, (int)it.m2, (int)it.R, (int)it.m2, it.K, it.nc, it.J, nullptr, it.diag,
                                status, smem_raw);
+}
+
+// ---- column proposal stages ----
+__global__ void __launch_bounds__(prop::kThreads) b_pgram_kernel(const BItem* __restrict__ items,
+                                                                 const int64_t* __restrict__ pre, int n) {
+  extern __shared__ __align__(16) float smf[];
+  ITEM_OF_BLOCK(pre, n);
+  prop::gram_partial_block(it.Y2, (int)it.m2, (int)it.m2, (int)it.R, (int)local, it.Gp, it.nmaxp, smf);
+}
+
+__global__ void __launch_bounds__(prop::kThreads) b_pchol_kernel(const BItem* __restrict__ items,
+                                                                 const int64_t* __restrict__ pre, int n) {
+  extern __shared__ __align__(16) float smf[];
+  ITEM_OF_BLOCK(pre, n);
+  prop::chol_inv_block(it.Gp, it.nsplit, it.nmaxp, (int)it.m2, (int)local, it.Linv, it.scal, smf);
+}
+
+__global__ void __launch_bounds__(prop::kThreads) b_pfeat_kernel(const BItem* __restrict__ items,
+                                                                 const int64_t* __restrict__ pre, int n) {
+  extern __shared__ __align__(16) float smf[];
+  ITEM_OF_BLOCK(pre, n);
+  prop::features_block(it.Y2, (int)it.m2, (int)it.m2, (int)it.R, it.K, it.Linv, it.scal, (int)local, it.F, smf);
+}
+
+__global__ void __launch_bounds__(prop::kThreads, 1) b_pmlp_kernel(const BItem* __restrict__ items,
+                                                                   const int64_t* __restrict__ pre, int n,
+                                                                   const float* __restrict__ theta) {
+  extern __shared__ __align__(16) float smf[];
+  ITEM_OF_BLOCK(pre, n);
+  prop::mlp_forward_tile(theta, it.F, it.R, local * prop::kTile, it.sc, smf);
+}
+
+__global__ void __launch_bounds__(prop::kThreads) b_pnorm_kernel(const BItem* __restrict__ items,
+                                                                 const int64_t* __restrict__ pre, int n) {
+  ITEM_OF_BLOCK(pre, n);
+  const int64_t c = local * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (c < it.R) prop::norm_scores_warp(it.Y2, (int)it.m2, (int)it.m2, (int)c, it.sc);
+}
+
+__global__ void __launch_bounds__(prop::kSelThreads) b_psel_kernel(const BItem* __restrict__ items,
+                                                                   const int64_t* __restrict__ pre, int n) {
+  ITEM_OF_BLOCK(pre, n);
+  (void)local;
+  prop::select_block(it.sc, (int)it.R, it.C, it.cand, it.outl);
+}
+
+__global__ void __launch_bounds__(prop::kApplyThreads) b_papply_kernel(const BItem* __restrict__ items,
+                                                                       const int64_t* __restrict__ pre, int n) {
+  extern __shared__ __align__(16) float smf[];
+  ITEM_OF_BLOCK(pre, n);
+  prop::apply_cert_block(it.Y2, it.Yf, (int)it.m2, (int)it.m2, it.K, it.outl, (int)(it.R - it.C), it.V, it.beta,
+                         it.rn, it.flag, it.diag + 8, (int)local, (int)(pre[p + 1] - pre[p]), smf);
+}
+
+// candidate QR: one CTA (a cluster of one) per proposal item
+template <int V, int TPC>
+__global__ void __launch_bounds__(RegCpqr<float, V, TPC>::kMaxThreads, 1)
+b_cand_kernel(const BItem* __restrict__ items, const int32_t* __restrict__ list, int* status) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const BItem& it = items[list[blockIdx.x]];
+  cpqr_reg_body<float, V, TPC>(it.Y2, it.Yf, (int)it.m2, it.C, (int)it.m2, it.K, it.C, it.J, it.rn, it.diag + 8,
+                               status, smem_raw, it.cand, it.V, it.beta);
 }
 
 __global__ void b_rest_kernel(const BItem* __restrict__ items, const int64_t* __restrict__ pre, int n) {
@@ -214,14 +292,14 @@ __global__ void __launch_bounds__(256) b_rinv_kernel(const BItem* __restrict__ i
                                                      int n) {
   extern __shared__ __align__(16) double shU[];
   ITEM_OF_BLOCK(pre, n);
-  rinv_block<float>(it.Y2, (int)it.m2, it.K, (int)it.R, it.J, it.Rinv, (int)local, (int)(pre[p + 1] - pre[p]), shU);
+  rinv_block<float>(it.Yf, (int)it.m2, it.K, (int)it.R, it.J, it.Rinv, (int)local, (int)(pre[p + 1] - pre[p]), shU);
 }
 
 __global__ void __launch_bounds__(256) b_tgemm_kernel(const BItem* __restrict__ items, const int64_t* __restrict__ pre,
                                                       int n) {
   extern __shared__ __align__(16) double shd[];
   ITEM_OF_BLOCK(pre, n);
-  tgemm_block<float>(it.Y2, (int)it.m2, it.K, (int)it.R, it.Rinv, it.rest, (int)(it.R - it.K), it.T, (int)local, shd);
+  tgemm_block<float>(it.Yf, (int)it.m2, it.K, (int)it.R, it.Rinv, it.rest, (int)(it.R - it.K), it.T, (int)local, shd);
 }
 
 __global__ void b_lam_kernel(const BItem* __restrict__ items, const int64_t* __restrict__ pre, int n) {
@@ -246,8 +324,9 @@ std::string signature(const idl_batch_item* items, int n) {
   char buf[160];
   for (int i = 0; i < n; ++i) {
     const idl_batch_item& x = items[i];
-    snprintf(buf, sizeof(buf), "%d:%lld:%lld:%lld:%lld:%lld:%d:%d;", x.kind, (long long)x.I, (long long)x.R,
-             (long long)x.K, (long long)x.params.m1, (long long)x.params.m2, x.params.precision, x.N);
+    snprintf(buf, sizeof(buf), "%d:%lld:%lld:%lld:%lld:%lld:%d:%d:%d;", x.kind, (long long)x.I, (long long)x.R,
+             (long long)x.K, (long long)x.params.m1, (long long)x.params.m2, x.params.precision, x.N,
+             x.params.learned);
     s += buf;
     for (int q = 0; q < x.N && x.kind == IDL_ITEM_CP; ++q) {
       snprintf(buf, sizeof(buf), "%lld,", (long long)x.dims[q]);
@@ -275,6 +354,8 @@ struct idl_batch_state {
   int graph_launches = 0;
   cudaStream_t gstream = nullptr;    // private stream: capture and replay (the legacy stream cannot be captured)
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  const int* d_flags = nullptr;      // certificate flags of the last batch (n ints, device)
+  int nflags = 0;
 };
 
 extern "C" long long idl_launch_count(void);
@@ -302,12 +383,13 @@ void idl_batch_state_free(idl_batch_state* b) {
 static int launch_check(idl_ctx* ctx, const char* where) { return cuda_check(ctx, cudaGetLastError(), where); }
 
 template <int V, int TPC>
-static bool cpqr_cfg_fits(const std::vector<int>& list, const std::vector<BItem>& it, int CS, CpqrCfg* cfg) {
+static bool cpqr_cfg_fits(const std::vector<int>& list, const std::vector<BItem>& it, int CS, CpqrCfg* cfg,
+                          bool cand = false) {
   int threads = 0, maxm = 0;
   for (int p : list) {
     const BItem& x = it[p];
     if (cdiv(x.m2, TPC) > V) return false;
-    const int nc = (int)cdiv(x.R, CS);
+    const int nc = cand ? x.C : (int)cdiv(x.R, CS);
     threads = std::max(threads, (int)round_up((int64_t)nc * TPC, 32));
     maxm = std::max(maxm, (int)x.m2);
   }
@@ -320,9 +402,9 @@ static bool cpqr_cfg_fits(const std::vector<int>& list, const std::vector<BItem>
   return true;
 }
 
-static bool pick_cpqr(const std::vector<int>& list, const std::vector<BItem>& it, CpqrCfg* cfg) {
-  const int CS = 16;
-#define PICK(VV, TT) if (cpqr_cfg_fits<VV, TT>(list, it, CS, cfg)) return true;
+static bool pick_cpqr(const std::vector<int>& list, const std::vector<BItem>& it, CpqrCfg* cfg, bool cand = false) {
+  const int CS = cand ? 1 : 16;
+#define PICK(VV, TT) if (cpqr_cfg_fits<VV, TT>(list, it, CS, cfg, cand)) return true;
   PICK(8, 32) PICK(8, 16) PICK(8, 8) PICK(16, 8) PICK(8, 4) PICK(16, 4) PICK(32, 4) PICK(16, 2) PICK(32, 2)
   PICK(16, 1) PICK(32, 1) PICK(64, 4) PICK(64, 2) PICK(64, 1) PICK(96, 1) PICK(128, 1)
 #undef PICK
@@ -352,6 +434,36 @@ static int launch_b_cpqr(idl_ctx* ctx, const BItem* d_items, const int32_t* d_li
   return cuda_check(ctx, e, "batch cpqr");
 }
 
+template <int V, int TPC>
+static int launch_b_cand(idl_ctx* ctx, const BItem* d_items, const int32_t* d_list, int nlist, const CpqrCfg& c) {
+  auto kern = b_cand_kernel<V, TPC>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c.smem);
+  if (e != cudaSuccess) return cuda_check(ctx, e, "batch candidate QR attribute");
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)nlist);
+  cfg.blockDim = dim3((unsigned)c.threads);
+  cfg.dynamicSmemBytes = c.smem;
+  cfg.stream = ctx->stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = 1;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  e = cudaLaunchKernelEx(&cfg, kern, d_items, d_list, ctx->d_status);
+  count_launch();
+  return cuda_check(ctx, e, "batch candidate QR");
+}
+
+static int dispatch_b_cand(idl_ctx* ctx, const BItem* d_items, const int32_t* d_list, int nlist, const CpqrCfg& c) {
+#define CASE(VV, TT) if (c.V == VV && c.TPC == TT) return launch_b_cand<VV, TT>(ctx, d_items, d_list, nlist, c);
+  CASE(8, 32) CASE(8, 16) CASE(8, 8) CASE(16, 8) CASE(8, 4) CASE(16, 4) CASE(32, 4) CASE(16, 2) CASE(32, 2)
+  CASE(16, 1) CASE(32, 1) CASE(64, 4) CASE(64, 2) CASE(64, 1) CASE(96, 1) CASE(128, 1)
+#undef CASE
+  return fail(ctx, IDL_ELIMIT, "batch candidate QR: no configuration");
+}
+
 static int dispatch_b_cpqr(idl_ctx* ctx, const BItem* d_items, const int32_t* d_list, int nlist, const CpqrCfg& c) {
 #define CASE(VV, TT) if (c.V == VV && c.TPC == TT) return launch_b_cpqr<VV, TT>(ctx, d_items, d_list, nlist, c);
   CASE(8, 32) CASE(8, 16) CASE(8, 8) CASE(16, 8) CASE(8, 4) CASE(16, 4) CASE(32, 4) CASE(16, 2) CASE(32, 2)
@@ -364,11 +476,11 @@ static int dispatch_b_cpqr(idl_ctx* ctx, const BItem* d_items, const int32_t* d_
 struct BatchPlan {
   std::vector<BItem> it;
   std::vector<int64_t> pre[kBNumStages];
-  std::vector<int32_t> dense_list, cp_list;
-  CpqrCfg cfg_dense, cfg_cp;
+  std::vector<int32_t> dense_list, cp_list, prop_list;
+  CpqrCfg cfg_dense, cfg_cp, cfg_cand;
   int NP = 3;
-  int maxL_hist = 0, maxK = 0, maxNT = 0, maxL_cp = 0;
-  size_t ws_bytes = 0, zero_bytes = 0;
+  int maxL_hist = 0, maxK = 0, maxNT = 0, maxL_cp = 0, maxm_prop = 0, maxKm_prop = 0;
+  size_t ws_bytes = 0, zero_bytes = 0, off_flags = 0;
   size_t off_items = 0, off_pre = 0, off_lists = 0, table_bytes = 0;
 };
 
@@ -380,6 +492,10 @@ static int plan_batch(idl_ctx* ctx, const idl_batch_item* items, int n, const Tu
     const idl_params& pr = x.params;
     if (prec < 0) prec = pr.precision;
     if (pr.precision != prec) return fail(ctx, IDL_EINVAL, "batch: all items must use one precision");
+    if (pr.learned < IDL_PROPOSAL_NONE || pr.learned > IDL_PROPOSAL_NORM)
+      return fail(ctx, IDL_EINVAL, "batch: unknown proposal mode");
+    if (pr.learned == IDL_PROPOSAL_MLP && !ctx->mlp_ready)
+      return fail(ctx, IDL_EINVAL, "batch: no MLP weights (idl_mlp_init / idl_load_weights)");
     if (prec == IDL_PREC_FP64) return fail(ctx, IDL_EINVAL, "batch: FP32 data only (precision FP32, BF16X3 or BF16)");
     if (x.K < 1 || x.K >= x.R || pr.m2 < x.K || pr.m2 > pr.m1 || pr.m2 > 128 || x.K > 128 || !x.J || !x.T ||
         x.R > 0x7fffffffLL)
@@ -401,14 +517,15 @@ static int plan_batch(idl_ctx* ctx, const idl_batch_item* items, int n, const Tu
   size_t off = 0;
   auto take = [&](size_t bytes) { const size_t o = off; off += (bytes + 255) & ~(size_t)255; return o; };
   std::vector<size_t> o_h(n), o_s(n), o_ptr(n), o_rows(n), o_big(n), o_Om(n), o_Bpl(n), o_Y1(n), o_part(n),
-      o_Y2(n), o_rest(n), o_Rinv(n), o_mh(n), o_ms(n);
-  // zero-initialised region first: cursors, nbig, diag
+      o_Y2(n), o_rest(n), o_Rinv(n), o_mh(n), o_ms(n), o_Yf(n), o_Gp(n), o_F(n), o_V(n), o_cand(n), o_rn(n);
+  // zero-initialised region first: certificate flags, cursors, nbig, diag
+  P.off_flags = take(sizeof(int) * (size_t)n);
   std::vector<size_t> o_cur(n), o_nbig(n), o_diag(n);
   for (int i = 0; i < n; ++i) {
     const idl_batch_item& x = items[i];
     o_cur[i] = take(x.kind == IDL_ITEM_DENSE ? sizeof(int32_t) * (size_t)(x.params.m1 + 1) : 0);
     o_nbig[i] = take(sizeof(int32_t));
-    o_diag[i] = take(sizeof(double) * 8);
+    o_diag[i] = take(sizeof(double) * 16);
   }
   P.zero_bytes = off;
   const int per_sm_gemm = 1;
@@ -467,6 +584,20 @@ static int plan_batch(idl_ctx* ctx, const idl_batch_item* items, int n, const Tu
     o_Y2[i] = take(sizeof(float) * (size_t)(b.R * b.m2));
     o_rest[i] = take(sizeof(int32_t) * (size_t)b.R);
     o_Rinv[i] = take(sizeof(double) * (size_t)(x.K * x.K));
+    b.learned = x.params.learned;
+    b.C = (int)std::min<int64_t>(2 * x.K, x.R);
+    b.nsplit = (int)cdiv(x.R, prop::kGramCols);
+    if (b.learned) {
+      const int64_t m = b.m2;
+      o_Yf[i] = take(sizeof(float) * (size_t)(b.R * m));
+      o_Gp[i] = take(sizeof(float) * (size_t)(b.nsplit * m * m + b.nsplit + 4 + 3 * m * m));
+      o_F[i] = take(sizeof(float) * (size_t)(b.R * prop::kNF + b.R));
+      o_V[i] = take(sizeof(float) * (size_t)(x.K * m + x.K));
+      o_cand[i] = take(sizeof(int32_t) * (size_t)b.R);
+      o_rn[i] = take(sizeof(double) * (size_t)x.K);
+      P.maxm_prop = std::max<int>(P.maxm_prop, (int)m);
+      P.maxKm_prop = std::max<int>(P.maxKm_prop, (int)(x.K * m + 2 * x.K));
+    }
     b.J = x.J;
     b.T = x.T;
     b.lam_hat = x.lambda_hat;
@@ -482,7 +613,7 @@ static int plan_batch(idl_ctx* ctx, const idl_batch_item* items, int n, const Tu
   P.off_pre = toff;
   toff += sizeof(int64_t) * (size_t)(n + 1) * kBNumStages;
   P.off_lists = toff;
-  toff += sizeof(int32_t) * (size_t)(2 * n + 2);
+  toff += sizeof(int32_t) * (size_t)(3 * n + 3);
   P.table_bytes = toff;
   // record workspace offsets (pointers are filled once the workspace address is known)
   for (int i = 0; i < n; ++i) {
@@ -492,6 +623,24 @@ static int plan_batch(idl_ctx* ctx, const idl_batch_item* items, int n, const Tu
     b.mh = (int32_t*)o_mh[i]; b.ms = (int8_t*)o_ms[i]; b.Om = (double*)o_Om[i];
     b.Bpl = (__nv_bfloat16*)o_Bpl[i]; b.Y1 = (float*)o_Y1[i]; b.part = (float*)o_part[i]; b.Y2 = (float*)o_Y2[i];
     b.rest = (int32_t*)o_rest[i]; b.Rinv = (double*)o_Rinv[i]; b.diag = (double*)o_diag[i];
+    b.flag = (int*)(P.off_flags + sizeof(int) * (size_t)i);
+    if (b.learned) {
+      const int64_t m = b.m2;
+      b.Yf = (float*)o_Yf[i];
+      b.Gp = (float*)o_Gp[i];
+      b.nmaxp = (float*)(o_Gp[i] + sizeof(float) * (size_t)(b.nsplit * m * m));
+      b.scal = (float*)((size_t)b.nmaxp + sizeof(float) * (size_t)b.nsplit);
+      b.Linv = (float*)((size_t)b.scal + sizeof(float) * 4);
+      b.F = (float*)o_F[i];
+      b.sc = (float*)(o_F[i] + sizeof(float) * (size_t)(b.R * prop::kNF));
+      b.V = (float*)o_V[i];
+      b.beta = (float*)(o_V[i] + sizeof(float) * (size_t)(b.K * m));
+      b.cand = (int32_t*)o_cand[i];
+      b.outl = (int32_t*)(o_cand[i] + sizeof(int32_t) * (size_t)b.C);
+      b.rn = (double*)o_rn[i];
+    } else {
+      b.Yf = b.Y2;
+    }
   }
   // ---- prefix tables ----
   for (int st = 0; st < kBNumStages; ++st) P.pre[st].assign(n + 1, 0);
@@ -511,12 +660,26 @@ static int plan_batch(idl_ctx* ctx, const idl_batch_item* items, int n, const Tu
     nb[kBPlanes] = cdiv(b.nkb * b.NT * 8, 256);
     nb[kBGemm] = b.mtiles * b.splits;
     nb[kBReduce] = cdiv(b.R * b.m2, 256);
+    const bool mlp = b.learned == IDL_PROPOSAL_MLP, nrm = b.learned == IDL_PROPOSAL_NORM;
+    nb[kBPGram] = mlp ? b.nsplit : 0;
+    nb[kBPChol] = mlp ? 3 : 0;
+    nb[kBPFeat] = mlp ? cdiv(b.R, prop::kFeatCols) : 0;
+    nb[kBPMlp] = mlp ? cdiv(b.R, prop::kTile) : 0;
+    nb[kBPNorm] = nrm ? cdiv(b.R, prop::kThreads / 32) : 0;
+    nb[kBPSel] = b.learned ? 1 : 0;
+    nb[kBPApply] = (b.learned && b.R > b.C) ? std::min<int64_t>(cdiv(b.R - b.C, prop::kApplyThreads / 32), 64) : 0;
     nb[kBRest] = cdiv(b.R, 256);
     nb[kBRinv] = cdiv(b.K, 8);
     nb[kBTgemm] = cdiv(b.R - b.K, kTNB);
     nb[kBLam] = cp ? b.K : 0;
     for (int st = 0; st < kBNumStages; ++st) P.pre[st][i + 1] = P.pre[st][i] + nb[st];
     if (d) P.dense_list.push_back(i); else P.cp_list.push_back(i);
+    if (b.learned) P.prop_list.push_back(i);
+  }
+  if (!P.prop_list.empty()) {
+    if (P.maxm_prop > prop::kMaxM || P.maxK > 128) return fail(ctx, IDL_ELIMIT, "batch: proposal needs m2, K <= 128");
+    if (!pick_cpqr(P.prop_list, P.it, &P.cfg_cand, true))
+      return fail(ctx, IDL_ELIMIT, "batch: no candidate QR shape");
   }
   for (int i = 0; i < n; ++i) P.it[i].nc = 0;
   if (!P.dense_list.empty()) {
@@ -554,6 +717,34 @@ static int run_gemm_stage(idl_ctx* ctx, const BatchPlan& P, const BItem* d_items
   return launch_check(ctx, "batch gemm");
 }
 
+// Proposal stages: scores, selection, candidate QR, certificate (the gated
+// cluster QR follows in run_stages).
+static int run_proposal(idl_ctx* ctx, const BatchPlan& P, const BItem* d_items, const int64_t* d_pre,
+                        const int32_t* d_plist, int n, int& nlaunch) {
+  const int m = P.maxm_prop;
+  const size_t sm_gram = sizeof(float) * 32 * round_up(m, 4);
+  const size_t sm_chol = sizeof(float) * (2 * (size_t)m * (m + 1) + m);
+  const size_t sm_feat = sizeof(float) * prop::features_smem_floats(m);
+  const size_t sm_mlp = sizeof(float) * prop::mlp_fwd_smem_floats();
+  const size_t sm_app = sizeof(float) * (size_t)P.maxKm_prop;
+  cudaError_t e = cudaFuncSetAttribute(b_pchol_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_chol);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(b_pfeat_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_feat);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(b_pmlp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_mlp);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(b_papply_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_app);
+  if (e != cudaSuccess) return cuda_check(ctx, e, "batch proposal attribute");
+  BLAUNCH(b_pgram_kernel, kBPGram, prop::kThreads, sm_gram);
+  BLAUNCH(b_pchol_kernel, kBPChol, prop::kThreads, sm_chol);
+  BLAUNCH(b_pfeat_kernel, kBPFeat, prop::kThreads, sm_feat);
+  BLAUNCH(b_pmlp_kernel, kBPMlp, prop::kThreads, sm_mlp, ctx->mlp);
+  BLAUNCH(b_pnorm_kernel, kBPNorm, prop::kThreads, 0);
+  BLAUNCH(b_psel_kernel, kBPSel, prop::kSelThreads, 0);
+  BTRY(launch_check(ctx, "batch proposal scores"));
+  BTRY(dispatch_b_cand(ctx, d_items, d_plist, (int)P.prop_list.size(), P.cfg_cand));
+  ++nlaunch;
+  BLAUNCH(b_papply_kernel, kBPApply, prop::kApplyThreads, sm_app);
+  return launch_check(ctx, "batch proposal");
+}
+
 // All launches of a batch (the part that is captured into a graph).
 static int run_stages(idl_ctx* ctx, const BatchPlan& P, const BItem* d_items, const int64_t* d_pre,
                       const int32_t* d_lists, int n, int sketch_threads, int& nlaunch, float* ms_sketch,
@@ -587,6 +778,7 @@ static int run_stages(idl_ctx* ctx, const BatchPlan& P, const BItem* d_items, co
   else BTRY(run_gemm_stage<3>(ctx, P, d_items, d_pre, n, nlaunch));
   if (timed) cudaEventRecord(ev[3], ctx->stream);
   BLAUNCH(b_reduce_kernel, kBReduce, 256, 0);
+  if (!P.prop_list.empty()) BTRY(run_proposal(ctx, P, d_items, d_pre, d_lists + 2 * (n + 1), n, nlaunch));
   if (!P.dense_list.empty()) {
     BTRY(dispatch_b_cpqr(ctx, d_items, d_lists, (int)P.dense_list.size(), P.cfg_dense));
     ++nlaunch;
@@ -633,7 +825,14 @@ static int upload(idl_ctx* ctx, BatchPlan& P, unsigned char* ws, unsigned char* 
       }
     }
     fix(b.cursor); fix(b.nbig); fix(b.Om); fix(b.Bpl); fix(b.Y1); fix(b.part); fix(b.Y2); fix(b.rest); fix(b.Rinv);
-    fix(b.diag);
+    fix(b.diag); fix(b.flag); fix(b.Yf);
+    if (b.learned) {
+      fix(b.Gp); fix(b.nmaxp); fix(b.scal); fix(b.Linv); fix(b.F); fix(b.sc); fix(b.V); fix(b.beta); fix(b.cand);
+      fix(b.outl); fix(b.rn);
+      b.gate = b.flag;
+    } else {
+      b.gate = nullptr;
+    }
   }
   memcpy(host.data() + P.off_items, items.data(), sizeof(BItem) * n);
   int64_t* pre = (int64_t*)(host.data() + P.off_pre);
@@ -641,6 +840,7 @@ static int upload(idl_ctx* ctx, BatchPlan& P, unsigned char* ws, unsigned char* 
   int32_t* lists = (int32_t*)(host.data() + P.off_lists);
   for (size_t q = 0; q < P.dense_list.size(); ++q) lists[q] = P.dense_list[q];
   for (size_t q = 0; q < P.cp_list.size(); ++q) lists[n + 1 + q] = P.cp_list[q];
+  for (size_t q = 0; q < P.prop_list.size(); ++q) lists[2 * (n + 1) + q] = P.prop_list[q];
   cudaError_t e = cudaMemcpyAsync(tab, host.data(), P.table_bytes, cudaMemcpyHostToDevice, ctx->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(ws, 0, P.zero_bytes, ctx->stream);
   // the host buffer must outlive the copy: synchronise (the tables are small)
@@ -709,6 +909,8 @@ extern "C" int idl_batch_run(idl_ctx* ctx, const idl_batch_item* items, int n) {
     d_lists = (const int32_t*)(tab + P.off_lists);
   }
   BTRY(upload(ctx, P, ws, tab, n));
+  bs->d_flags = (const int*)(ws + P.off_flags);
+  bs->nflags = n;
   if (ctx->batch_no_graph) return run_stages(ctx, P, d_items, d_pre, d_lists, n, tn.sketch_threads, nlaunch, nullptr, nullptr);
   // graph: captured once per (shape, workspace address) on a private stream, replayed afterwards;
   // events order it after the caller's stream and the caller's stream after it
@@ -797,6 +999,19 @@ extern "C" int idl_debug_batch_timing(idl_ctx* ctx, const idl_batch_item* items,
   int nl = 0;
   return run_stages(ctx, P, (const BItem*)(tab + P.off_items), (const int64_t*)(tab + P.off_pre),
                     (const int32_t*)(tab + P.off_lists), n, tn.sketch_threads, nl, &ms[0], &ms[1]);
+}
+
+extern "C" int idl_batch_fallbacks(idl_ctx* ctx) {
+  if (!ctx) return -IDL_EINVAL;
+  idl_batch_state* bs = bstate(ctx);
+  if (!bs->d_flags || bs->nflags < 1) return 0;
+  std::vector<int> h((size_t)bs->nflags);
+  cudaError_t e = cudaMemcpyAsync(h.data(), bs->d_flags, sizeof(int) * h.size(), cudaMemcpyDeviceToHost, ctx->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  if (e != cudaSuccess) return -cuda_check(ctx, e, "batch fallbacks");
+  int c = 0;
+  for (int v : h) c += v != 0;
+  return c;
 }
 
 extern "C" int idl_debug_batch_mode(idl_ctx* ctx, int no_graph, int no_tune) {

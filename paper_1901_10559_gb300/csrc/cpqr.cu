@@ -34,7 +34,8 @@ template <typename T>
 __global__ void __launch_bounds__(kCpqrThreads, 1)
 cpqr_cluster_kernel(const T* __restrict__ Yin, T* __restrict__ Yout, int m, int R, int ld, int K, int nc, int lds,
                     int tpc, int32_t* __restrict__ J, double* __restrict__ rnorm, double* __restrict__ diag,
-                    int* status) {
+                    int* status, const int* gate) {
+  if (proposal_certified(gate, diag)) return;
   cg::cluster_group cluster = cg::this_cluster();
   const int rank = (int)cluster.block_rank();
   const int c0 = rank * nc;
@@ -215,14 +216,16 @@ cpqr_cluster_kernel(const T* __restrict__ Yin, T* __restrict__ Yout, int m, int 
 template <typename T, int V, int TPC>
 __global__ void __launch_bounds__(RegCpqr<T, V, TPC>::kMaxThreads, 1)
 cpqr_reg_kernel(const T* __restrict__ Yin, T* __restrict__ Yout, int m, int R, int ld, int K, int nc,
-                int32_t* __restrict__ J, double* __restrict__ rnorm, double* __restrict__ diag, int* status) {
+                int32_t* __restrict__ J, double* __restrict__ rnorm, double* __restrict__ diag, int* status,
+                const int* gate, const int32_t* __restrict__ colmap, T* __restrict__ Vout, T* __restrict__ Bout) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  cpqr_reg_body<T, V, TPC>(Yin, Yout, m, R, ld, K, nc, J, rnorm, diag, status, smem_raw);
+  if (proposal_certified(gate, diag)) return;
+  cpqr_reg_body<T, V, TPC>(Yin, Yout, m, R, ld, K, nc, J, rnorm, diag, status, smem_raw, colmap, Vout, Bout);
 }
 
 template <typename T, int V, int TPC>
 static int try_reg_cpqr(idl_ctx* ctx, const T* Yin, T* Yout, int64_t m, int64_t R, int64_t ld, int64_t K, int32_t* J,
-                        double* rnorm, int CS, int nc, bool* launched) {
+                        double* rnorm, int CS, int nc, const QrExtra& x, bool* launched) {
   constexpr int tpc = TPC;
   *launched = false;
   const int threads = (int)round_up((int64_t)nc * tpc, 32);
@@ -248,9 +251,9 @@ static int try_reg_cpqr(idl_ctx* ctx, const T* Yin, T* Yout, int64_t m, int64_t 
   int nclusters = 0;
   e = cudaOccupancyMaxActiveClusters(&nclusters, kern, &cfg);
   if (e != cudaSuccess || nclusters < 1) { (void)cudaGetLastError(); return IDL_OK; }
-  ctx->last_cluster = CS;
-  e = cudaLaunchKernelEx(&cfg, kern, Yin, Yout, (int)m, (int)R, (int)ld, (int)K, nc, J, rnorm, ctx->d_diag,
-                         ctx->d_status);
+  if (!x.colmap) ctx->last_cluster = CS;
+  e = cudaLaunchKernelEx(&cfg, kern, Yin, Yout, (int)m, (int)R, (int)ld, (int)K, nc, J, rnorm,
+                         x.diag ? x.diag : ctx->d_diag, ctx->d_status, x.gate, x.colmap, (T*)x.Vout, (T*)x.Bout);
   idl::count_launch();
   *launched = true;
   return cuda_check(ctx, e, "cpqr reg launch");
@@ -259,22 +262,22 @@ static int try_reg_cpqr(idl_ctx* ctx, const T* Yin, T* Yout, int64_t m, int64_t 
 // Largest cluster, then the most lanes per column whose register budget fits.
 template <typename T, int V, int TPC>
 static bool reg_try(idl_ctx* ctx, const T* Yin, T* Yout, int64_t m, int64_t R, int64_t ld, int64_t K, int32_t* J,
-                    double* rnorm, int CS, int nc, int* rc) {
+                    double* rnorm, int CS, int nc, const QrExtra& x, int* rc) {
   bool launched = false;
   if (cdiv(m, TPC) > V) return false;
-  *rc = try_reg_cpqr<T, V, TPC>(ctx, Yin, Yout, m, R, ld, K, J, rnorm, CS, nc, &launched);
+  *rc = try_reg_cpqr<T, V, TPC>(ctx, Yin, Yout, m, R, ld, K, J, rnorm, CS, nc, x, &launched);
   return launched || *rc != IDL_OK;
 }
 
 template <typename T>
 static int reg_cpqr(idl_ctx* ctx, const T* Yin, T* Yout, int64_t m, int64_t R, int64_t ld, int64_t K, int32_t* J,
-                    double* rnorm, bool* launched) {
+                    double* rnorm, const QrExtra& x, bool* launched) {
   *launched = false;
-  if (ctx->cpqr_smem_only) return IDL_OK;
+  if (ctx->cpqr_smem_only && !x.colmap) return IDL_OK;
   int rc = IDL_OK;
-  for (int CS = 16; CS >= 1; CS >>= 1) {
+  for (int CS = x.max_cs; CS >= 1; CS >>= 1) {
     const int nc = (int)cdiv(R, CS);
-#define TRY_CFG(V, TPC) if (reg_try<T, V, TPC>(ctx, Yin, Yout, m, R, ld, K, J, rnorm, CS, nc, &rc)) { *launched = rc == IDL_OK; return rc; }
+#define TRY_CFG(V, TPC) if (reg_try<T, V, TPC>(ctx, Yin, Yout, m, R, ld, K, J, rnorm, CS, nc, x, &rc)) { *launched = rc == IDL_OK; return rc; }
     // most lanes per column first (shortest serial chain per step)
     TRY_CFG(8, 32) TRY_CFG(8, 16) TRY_CFG(8, 8) TRY_CFG(16, 8) TRY_CFG(8, 4) TRY_CFG(16, 4) TRY_CFG(32, 4)
     TRY_CFG(16, 2) TRY_CFG(32, 2) TRY_CFG(16, 1) TRY_CFG(32, 1)
@@ -286,13 +289,14 @@ static int reg_cpqr(idl_ctx* ctx, const T* Yin, T* Yout, int64_t m, int64_t R, i
 
 template <typename T>
 static int cpqr_impl(idl_ctx* ctx, const T* Yin, T* Yout, int64_t m, int64_t R, int64_t ld, int64_t K, int32_t* J,
-                     double* rnorm) {
+                     double* rnorm, const QrExtra& x) {
   if (m > 256 || m < 1) return fail(ctx, IDL_ELIMIT, "cpqr: m must be in [1, 256]");
   {
     bool launched = false;
-    const int rc = reg_cpqr<T>(ctx, Yin, Yout, m, R, ld, K, J, rnorm, &launched);
+    const int rc = reg_cpqr<T>(ctx, Yin, Yout, m, R, ld, K, J, rnorm, x, &launched);
     if (rc != IDL_OK || launched) return rc;
   }
+  if (x.colmap) return fail(ctx, IDL_ELIMIT, "cpqr: candidate set exceeds one CTA");
   auto kern = cpqr_cluster_kernel<T>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
   if (e != cudaSuccess) return cuda_check(ctx, e, "cpqr cluster attribute");
@@ -327,7 +331,7 @@ static int cpqr_impl(idl_ctx* ctx, const T* Yin, T* Yout, int64_t m, int64_t R, 
     if (e != cudaSuccess || nclusters < 1) { (void)cudaGetLastError(); continue; }
     ctx->last_cluster = CS;
     e = cudaLaunchKernelEx(&cfg, kern, Yin, Yout, (int)m, (int)R, (int)ld, (int)K, nc, lds, tpc, J, rnorm,
-                           ctx->d_diag, ctx->d_status);
+                           x.diag ? x.diag : ctx->d_diag, ctx->d_status, x.gate);
     idl::count_launch();
     return cuda_check(ctx, e, "cpqr launch");
   }
@@ -336,8 +340,14 @@ static int cpqr_impl(idl_ctx* ctx, const T* Yin, T* Yout, int64_t m, int64_t R, 
 
 int launch_cpqr(idl_ctx* ctx, void* Y2, int64_t m, int64_t R, int64_t ld, int dtype, int64_t K, int32_t* J,
                 double* rnorm) {
-  if (dtype == IDL_F32) return cpqr_impl<float>(ctx, (const float*)Y2, (float*)Y2, m, R, ld, K, J, rnorm);
-  return cpqr_impl<double>(ctx, (const double*)Y2, (double*)Y2, m, R, ld, K, J, rnorm);
+  const QrExtra x;
+  if (dtype == IDL_F32) return cpqr_impl<float>(ctx, (const float*)Y2, (float*)Y2, m, R, ld, K, J, rnorm, x);
+  return cpqr_impl<double>(ctx, (const double*)Y2, (double*)Y2, m, R, ld, K, J, rnorm, x);
+}
+
+int launch_cpqr_ex(idl_ctx* ctx, const float* Yin, float* Yout, int64_t m, int64_t R, int64_t ld, int64_t K,
+                   int32_t* J, double* rnorm, const QrExtra& x) {
+  return cpqr_impl<float>(ctx, Yin, Yout, m, R, ld, K, J, rnorm, x);
 }
 
 // ----------------------------------------------------------------------------

@@ -54,10 +54,16 @@ template <typename T, int V, int TPC> struct RegCpqr {
 
 // Body of one cluster working on one problem (Yin/Yout m x R column-major, ld);
 // smem_raw: the dynamic shared memory (reg_cpqr_smem bytes).
+// colmap (optional): the problem's column c is column colmap[c] of Yin/Yout
+// (ascending, so ties still go to the smaller original index); J reports
+// original indices.  Vout/Bout (optional): reflector t (zero above row t) at
+// Vout + t*m and its beta at Bout[t] -- the learned proposal's candidate QR.
 template <typename T, int V, int TPC>
 __device__ __forceinline__ void cpqr_reg_body(const T* __restrict__ Yin, T* __restrict__ Yout, int m, int R, int ld,
                                               int K, int nc, int32_t* __restrict__ J, double* __restrict__ rnorm,
-                                              double* __restrict__ diag, int* status, unsigned char* smem_raw) {
+                                              double* __restrict__ diag, int* status, unsigned char* smem_raw,
+                                              const int32_t* __restrict__ colmap = nullptr, T* __restrict__ Vout = nullptr,
+                                              T* __restrict__ Bout = nullptr) {
   constexpr int tpc = TPC;
   cg::cluster_group cluster = cg::this_cluster();
   const int CS = (int)cluster.num_blocks();
@@ -68,6 +74,7 @@ __device__ __forceinline__ void cpqr_reg_body(const T* __restrict__ Yin, T* __re
   const int ncl = max(0, min(nc, R - c0));
   const bool own = g < ncl;
   const int col = c0 + g;
+  const int64_t scol = own ? (colmap ? (int64_t)colmap[col] : (int64_t)col) : 0;   // column of Yin / Yout
 
   T* stage = (T*)smem_raw;                                          // [2][m] staged candidate column
   T* vs = stage + 2 * m;                                            // V*TPC: v, zero outside rows [t, m)
@@ -83,7 +90,7 @@ __device__ __forceinline__ void cpqr_reg_body(const T* __restrict__ Yin, T* __re
 #pragma unroll
   for (int j = 0; j < V; ++j) {
     const int i = gl + tpc * j;
-    y[j] = (own && i < m) ? Yin[(int64_t)col * ld + i] : T(0);
+    y[j] = (own && i < m) ? Yin[scol * ld + i] : T(0);
   }
   T nn = T(0);
 #pragma unroll
@@ -167,7 +174,10 @@ __device__ __forceinline__ void cpqr_reg_body(const T* __restrict__ Yin, T* __re
           vs[i] = x;
           xs += x * x;
           if (i == t) x0 = x;
+          if (Vout && rank == 0) Vout[(int64_t)t * m + i] = x;
         }
+        if (Vout && rank == 0)
+          for (int i = lane; i < t; i += 32) Vout[(int64_t)t * m + i] = T(0);
         xs = warp_sum(xs);
         x0 = __shfl_sync(0xffffffffu, x0, 0);
         const T nrm = sqrt(xs);
@@ -179,7 +189,8 @@ __device__ __forceinline__ void cpqr_reg_body(const T* __restrict__ Yin, T* __re
           s_beta = beta;
           s_p = ix;
           if (rank == 0) {
-            J[t] = ix;
+            J[t] = colmap ? colmap[ix] : ix;
+            if (Vout) { Vout[(int64_t)t * m + t] = x0 - alpha; Bout[t] = beta; }
             if (rnorm) rnorm[t] = (double)fabs(alpha);
             if (t == 0) diag[3] = (double)fabs(alpha);
             if (t == K - 1) diag[4] = (double)fabs(alpha);
@@ -225,12 +236,28 @@ __device__ __forceinline__ void cpqr_reg_body(const T* __restrict__ Yin, T* __re
     if (own && i < m) {
       T out = y[j];
       if (tp >= 0) out = (i < tp) ? y[j] : (i == tp ? alpha_p : T(0));
-      Yout[(int64_t)col * ld + i] = out;
+      Yout[scol * ld + i] = out;
       if (tp < 0 && i >= K) r22 += (double)y[j] * (double)y[j];
     }
   }
   r22 = warp_sum(r22);
   if (lane == 0 && r22 != 0.0) atomicAdd(&diag[0], r22);
+}
+
+// Fallback gate of the learned proposal.  With a gate, a QR launch is the
+// proposal's fallback and only runs when the certificate failed (*gate != 0);
+// otherwise block 0 moves the proposal's diagnostics (diag[8..12]) into
+// place and every block returns before any barrier.
+__device__ __forceinline__ bool proposal_certified(const int* gate, double* diag) {
+  if (!gate) return false;
+  if (*(volatile const int*)gate != 0) return false;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    diag[0] = diag[8];
+    diag[1] = diag[9];
+    diag[3] = diag[11];
+    diag[4] = diag[12];
+  }
+  return true;
 }
 
 template <typename T, int V, int TPC>

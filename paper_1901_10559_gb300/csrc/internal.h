@@ -30,6 +30,9 @@ struct idl_ctx {
   idl_batch_state* batch = nullptr;   // batch graphs and tuning table
   int batch_no_graph = 0;      // 1: run batches without graph capture (tests)
   int batch_no_tune = 0;       // 1: skip the first-call tuning runs (tests)           // 1: Gaussian stage on CUDA cores instead of tcgen05 (comparison / tests)
+  float* mlp = nullptr;        // proposal MLP: FP32 master weights | Adam first moments | second moments
+  bool mlp_ready = false;
+  long long mlp_step = 0;      // Adam steps taken since the weights were set
   size_t fail_alloc_at = 0;    // test hook: fail the n-th workspace allocation (0 = never)
   size_t alloc_count = 0;
   // per-stage CUDA-event profiling (idl_profile / idl_profile_read)
@@ -45,7 +48,8 @@ namespace idl {
 enum Slot {
   kWsH = 0, kWsS, kWsOmega, kWsBucketPtr, kWsRowList, kWsCursor, kWsBig, kWsY1, kWsPart,
   kWsY2, kWsOmegaConv, kWsRest, kWsA, kWsRowptr, kWsColidx, kWsVals, kWsJ, kWsT,
-  kWsModeH, kWsModeS, kWsLam, kWsLamHat, kWsCpqrSync, kWsRinv, kWsBatch, kWsBatchTab, kWsCount
+  kWsModeH, kWsModeS, kWsLam, kWsLamHat, kWsCpqrSync, kWsRinv, kWsBatch, kWsBatchTab, kWsYf, kWsProp,
+  kWsPropGram, kWsPropTrain, kWsPropCopy, kWsCount
 };
 
 // Returns a device buffer of at least `bytes` for the slot (grown on demand), or
@@ -85,6 +89,19 @@ int launch_gaussian_tc(idl_ctx* ctx, const double* Omega, int64_t m2, int64_t m1
                        int64_t ldy1, int precision, float* Y2, int64_t ldy2);
 
 // cpqr.cu
+// Extra roles of a QR launch (learned proposal): gate = fallback flag (run only
+// when *gate != 0); colmap/Vout/Bout = candidate QR on a column subset in one
+// CTA (max_cs = 1) with its reflectors recorded; diag = diagnostics base.
+struct QrExtra {
+  const int* gate = nullptr;
+  const int32_t* colmap = nullptr;
+  float* Vout = nullptr;
+  float* Bout = nullptr;
+  double* diag = nullptr;
+  int max_cs = 16;
+};
+int launch_cpqr_ex(idl_ctx* ctx, const float* Yin, float* Yout, int64_t m, int64_t R, int64_t ld, int64_t K,
+                   int32_t* J, double* rnorm, const QrExtra& x);
 int launch_cpqr(idl_ctx* ctx, void* Y2, int64_t m, int64_t R, int64_t ld, int dtype, int64_t K, int32_t* J,
                 double* rnorm);
 int launch_t_solve(idl_ctx* ctx, const void* Y2, int64_t m, int64_t R, int64_t ld, int dtype, int64_t K,
@@ -95,6 +112,12 @@ int launch_lambda_hat(idl_ctx* ctx, const double* lambda, const int32_t* J, cons
                       int64_t R, double* lambda_hat);
 int launch_transpose_to_colmajor(idl_ctx* ctx, const void* Y1, int64_t m, int64_t R, int64_t ldy1, int dtype,
                                  void* Y2, int64_t ldy2);
+
+// proposal.cu
+int launch_features(idl_ctx* ctx, const float* Y, int64_t m, int64_t R, int64_t ld, int64_t K, float* F);
+int launch_mlp_scores(idl_ctx* ctx, const float* F, int64_t n, float* s);
+int launch_proposal_qr(idl_ctx* ctx, const float* Y2, float* Yf, int64_t m, int64_t R, int64_t ld, int64_t K,
+                       int mode, int32_t* J);
 
 // tensorsketch.cu
 int launch_tensorsketch(idl_ctx* ctx, int N, const int64_t* dims, int64_t R, const void* const* factors,

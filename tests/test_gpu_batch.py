@@ -40,12 +40,13 @@ def _outputs(K, R, cp=False):
     return J, T, lh
 
 
-def _build(dense, cps, prec=idl.PREC_FP32):
+def _build(dense, cps, prec=idl.PREC_FP32, learned=(idl.PROPOSAL_NONE,)):
     items, outs, keep = [], [], []
-    for pr in dense:
+    for b, pr in enumerate(dense):
         A = dev(pr["A"])
         J, T, _ = _outputs(pr["K"], pr["A"].shape[1])
-        p = idl.make_params(pr["m1"], pr["m2"], seed=pr["seed"], modified=True, precision=prec)
+        p = idl.make_params(pr["m1"], pr["m2"], seed=pr["seed"], modified=True, precision=prec,
+                            learned=learned[b % len(learned)])
         items.append(idl.dense_item(A, pr["K"], p, J, T))
         outs.append((J, T, None))
         keep.append(A)
@@ -54,7 +55,8 @@ def _build(dense, cps, prec=idl.PREC_FP32):
         lam = dev(pr["lam"])
         R = pr["facs"][0].shape[1]
         J, T, lh = _outputs(pr["K"], R, cp=True)
-        p = idl.make_params(pr["L"], pr["m2"], seed=pr["seed"], modified=False, precision=prec)
+        p = idl.make_params(pr["L"], pr["m2"], seed=pr["seed"], modified=False, precision=prec,
+                            learned=learned[-1])
         items.append(idl.cp_item(fd, lam, pr["K"], p, J, T, lh))
         outs.append((J, T, lh))
         keep.append((fd, lam))
@@ -143,3 +145,34 @@ def test_batch_rejects_mixed_precision(ctx):
     with pytest.raises(idl.IdlError) as ei:
         idl.idl_batch_run(ctx, items)
     assert ei.value.code == idl.IDL_EINVAL
+
+
+@pytest.mark.parametrize("graph", [0, 1])
+def test_batch_with_proposal_matches_plain(ctx, graph):
+    """Items that take the column proposal (norm scores, MLP scores with random
+    weights) get the plain QR's pivots and T, certified or through the gated
+    fallback; the fallback count is reported."""
+    from oracle import proposal as opr
+    idl.idl_mlp_set_weights(ctx, opr.flatten(opr.init_params(3)).astype(np.float32))
+    dense, cps = _dense_problems(7), _cp_problems(9)
+    idl.lib().idl_debug_batch_mode(ctx.ptr, int(not graph), 1)
+    items0, outs0, keep0 = _build(dense, cps)
+    idl.idl_batch_run(ctx, items0)
+    assert ctx.sync() == idl.IDL_OK
+    modes = (idl.PROPOSAL_NORM, idl.PROPOSAL_NONE, idl.PROPOSAL_MLP)
+    items1, outs1, keep1 = _build(dense, cps, learned=modes)
+    for _ in range(2):
+        idl.idl_batch_run(ctx, items1)
+    assert ctx.sync() == idl.IDL_OK
+    nfb = idl.idl_batch_fallbacks(ctx)
+    idl.lib().idl_debug_batch_mode(ctx.ptr, 0, 0)
+    nprop = sum(1 for b in range(len(dense)) if modes[b % 3] != idl.PROPOSAL_NONE) + len(cps)
+    assert 0 <= nfb <= nprop
+    for (J0, T0, l0), (J1, T1, l1) in zip(outs0, outs1):
+        assert np.array_equal(host(J0), host(J1))
+        # same sketch, same pivots; the factor rows differ by FP32 rounding (another
+        # reduction layout), which T = R11^-1 R12 amplifies by cond(R11)
+        t0, t1 = host(T0), host(T1)
+        assert np.linalg.norm(t1 - t0) <= 1e-2 * np.linalg.norm(t0)
+        if l0 is not None:
+            assert np.allclose(host(l0), host(l1), rtol=1e-2, atol=1e-9)

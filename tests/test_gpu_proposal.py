@@ -1,0 +1,305 @@
+"""GPU parity of the learned column proposal (features, MLP forward/backward,
+Adam, labels, candidate QR + certificate + fallback, weight file) against the
+FP64 oracle, through the C ABI."""
+import os
+
+import numpy as np
+import pytest
+import torch
+
+import paper_1901_10559_gb300 as idl
+from oracle import cpqr as ocp
+from oracle import proposal as opr
+from synth import lowrank_dense
+from tests.helpers import colmajor_to_matrix, dev, host, rel_fro
+
+pytestmark = pytest.mark.gpu
+
+# Leverage features: Y Y^T and its Cholesky factor in FP32.  With lambda >=
+# 1e-3 tr(G)/m the shifted Gram matrix has condition number <= 1e3 m + 1, so
+# the FP32 values carry ~cond * 6e-8 relative error in the worst case
+# (m = 128: 8e-3); the gate is 1e-2 absolute on values in [0, 1).
+LEV_TOL = 1e-2
+# MLP: bf16 operands rounded identically on both sides; what remains is FP32
+# accumulation order over <= 128 terms.
+MLP_TOL = 1e-4
+# Against the unrounded FP64 model (bf16 operands on the device).
+BF16_TOL = 2e-2
+
+
+def _sketch(m, R, seed, decay=0.85, scale_cols=True, zero_col=None):
+    Y = lowrank_dense(m, R, decay=decay, noise=1e-3, seed=seed, dtype=np.float64)
+    if scale_cols:
+        Y = Y * np.random.default_rng(seed + 1).lognormal(0.0, 1.0, R)[None, :]
+    if zero_col is not None:
+        Y[:, zero_col] = 0.0
+    return Y.astype(np.float32)
+
+
+def _colmajor(Y):
+    """m x R float32 -> device column-major buffer (ld = m)."""
+    return dev(np.ascontiguousarray(Y.T))
+
+
+def _params(seed):
+    P = opr.init_params(seed)
+    return P, opr.flatten(P).astype(np.float32)
+
+
+# ------------------------------------------------------------------ features
+@pytest.mark.parametrize("m,R,K,seed", [(40, 700, 12, 1), (128, 300, 64, 2), (7, 129, 3, 3), (60, 1000, 50, 4)])
+def test_features_parity(ctx, m, R, K, seed):
+    Y = _sketch(m, R, seed, zero_col=5)
+    F = torch.empty(R * 8, dtype=torch.float32, device="cuda")
+    idl.idl_proposal_features(ctx, _colmajor(Y), m, R, m, K, F)
+    got = host(F).reshape(R, 8).astype(np.float64)
+    want = opr.features(Y.astype(np.float64), K)
+    assert np.abs(got[:, [0, 1, 5, 6, 7]] - want[:, [0, 1, 5, 6, 7]]).max() <= 1e-5
+    assert np.abs(got[:, 2:5] - want[:, 2:5]).max() <= LEV_TOL
+    assert ctx.sync() == idl.IDL_OK
+
+
+def test_features_zero_sketch(ctx):
+    Y = np.zeros((16, 50), np.float32)
+    F = torch.empty(50 * 8, dtype=torch.float32, device="cuda")
+    idl.idl_proposal_features(ctx, _colmajor(Y), 16, 50, 16, 4, F)
+    got = host(F).reshape(50, 8)
+    assert np.allclose(got, opr.features(Y.astype(np.float64), 4))
+
+
+# ------------------------------------------------------------------ MLP
+@pytest.mark.parametrize("n,seed", [(1, 5), (300, 6), (1024, 7)])
+def test_mlp_forward_parity(ctx, n, seed):
+    P, theta = _params(seed)
+    idl.idl_mlp_set_weights(ctx, theta)
+    F = np.random.default_rng(seed).standard_normal((n, 8)).astype(np.float32)
+    s = torch.empty(n, dtype=torch.float32, device="cuda")
+    idl.idl_mlp_scores(ctx, dev(F), n, s)
+    got = host(s).astype(np.float64)
+    want16, _ = opr.forward(P, F.astype(np.float64), bf16=True)
+    want64, _ = opr.forward(P, F.astype(np.float64))
+    scale = max(1.0, np.abs(want16).max())
+    assert np.abs(got - want16).max() <= MLP_TOL * scale
+    assert np.abs(got - want64).max() <= BF16_TOL * max(1.0, np.abs(want64).max())
+
+
+@pytest.mark.parametrize("n,pw,seed", [(128, 1.0, 8), (700, 5.0, 9)])
+def test_mlp_gradient_parity(ctx, n, pw, seed):
+    P, theta = _params(seed)
+    idl.idl_mlp_set_weights(ctx, theta)
+    rng = np.random.default_rng(seed)
+    F = rng.standard_normal((n, 8)).astype(np.float32)
+    y = (rng.uniform(size=n) < 0.2).astype(np.float32)
+    g = torch.empty(opr.NPARAM, dtype=torch.float32, device="cuda")
+    loss = torch.empty(1, dtype=torch.float32, device="cuda")
+    idl.idl_mlp_grad(ctx, dev(F), dev(y), n, pw, g, loss)
+    got = opr.unflatten(host(g).astype(np.float64))
+    want16 = opr.backward(P, F.astype(np.float64), y.astype(np.float64), pw, bf16=True)
+    want64 = opr.backward(P, F.astype(np.float64), y.astype(np.float64), pw)
+    for k in want16:
+        assert rel_fro(got[k], want16[k]) <= MLP_TOL * 10, k
+        assert rel_fro(got[k], want64[k]) <= BF16_TOL, k
+    l16 = opr.loss(P, F.astype(np.float64), y.astype(np.float64), pw, bf16=True)
+    assert abs(float(host(loss)[0]) - l16) <= 1e-5 * max(1.0, l16)
+
+
+def test_adam_steps_parity(ctx):
+    """Two full-batch Adam steps equal the oracle's update applied to the device
+    gradients (the gradients themselves are checked above)."""
+    P, theta = _params(10)
+    n = 256
+    rng = np.random.default_rng(11)
+    F = dev(rng.standard_normal((n, 8)).astype(np.float32))
+    y = dev((rng.uniform(size=n) < 0.3).astype(np.float32))
+    idl.idl_mlp_set_weights(ctx, theta)
+    th = theta.astype(np.float64)
+    m = np.zeros_like(th)
+    v = np.zeros_like(th)
+    g = torch.empty(opr.NPARAM, dtype=torch.float32, device="cuda")
+    loss = torch.empty(1, dtype=torch.float32, device="cuda")
+    lr = 1e-3
+    for t in (1, 2):
+        idl.idl_mlp_grad(ctx, F, y, n, 1.0, g, loss)
+        gd = host(g).astype(np.float64)
+        idl.idl_train_proposal(ctx, F, y, n, epochs=1, batch=n, lr=lr, seed=3)
+        th, m, v = opr.adam_step(th, gd, m, v, t, lr)
+    out = np.empty(opr.NPARAM, np.float32)
+    idl.idl_mlp_get_weights(ctx, out)
+    assert np.abs(out - th).max() <= 2e-6 + 1e-5 * lr
+
+
+def test_training_reduces_loss(ctx):
+    """Labels from a fixed rule on two features: a few epochs of Adam fit them."""
+    rng = np.random.default_rng(12)
+    n = 20000
+    F = rng.standard_normal((n, 8)).astype(np.float32)
+    y = ((F[:, 2] + 0.5 * F[:, 1]) > 1.0).astype(np.float32)
+    idl.idl_mlp_init(ctx, 5)
+    losses = idl.idl_train_proposal(ctx, dev(F), dev(y), n, epochs=20, batch=2048, lr=3e-3, seed=1)
+    assert losses[-1] < 0.5 * losses[0]
+    s = torch.empty(n, dtype=torch.float32, device="cuda")
+    idl.idl_mlp_scores(ctx, dev(F), n, s)
+    acc = np.mean((host(s) > 0) == (y > 0.5))
+    assert acc > 0.9
+
+
+def test_weight_file_roundtrip_and_checksum(ctx, tmp_path):
+    _, theta = _params(13)
+    idl.idl_mlp_set_weights(ctx, theta)
+    path = str(tmp_path / "w.bin")
+    idl.idl_save_weights(ctx, path)
+    idl.idl_mlp_init(ctx, 99)
+    idl.idl_load_weights(ctx, path)
+    out = np.empty(opr.NPARAM, np.float32)
+    idl.idl_mlp_get_weights(ctx, out)
+    assert np.array_equal(out, theta)
+    raw = bytearray(open(path, "rb").read())
+    raw[100] ^= 0x40
+    bad = str(tmp_path / "bad.bin")
+    open(bad, "wb").write(bytes(raw))
+    with pytest.raises(idl.IdlError) as e:
+        idl.idl_load_weights(ctx, bad)
+    assert e.value.code == idl.IDL_EINVAL
+    open(bad, "wb").write(b"IDLMLP01" + b"\0" * 16)
+    with pytest.raises(idl.IdlError):
+        idl.idl_load_weights(ctx, bad)
+
+
+def test_labels_are_plain_pivots(ctx):
+    m, R, K = 50, 600, 20
+    Y = _sketch(m, R, 14)
+    f = ocp.cpqr(Y.astype(np.float64), K)
+    assert np.all(f["gaps"] > 1e-3)
+    F = torch.empty(R * 8, dtype=torch.float32, device="cuda")
+    lab = torch.empty(R, dtype=torch.float32, device="cuda")
+    idl.idl_proposal_labels(ctx, _colmajor(Y), m, R, m, K, F, lab)
+    assert np.array_equal(np.nonzero(host(lab))[0], np.sort(f["perm"][:K]))
+
+
+# ------------------------------------------------------------------ proposal QR
+def _plain(ctx, Y, K):
+    m, R = Y.shape
+    Yd = _colmajor(Y)
+    J = torch.empty(K, dtype=torch.int32, device="cuda")
+    idl.idl_cpqr(ctx, Yd, m, R, m, idl.IDL_F32, K, J)
+    return host(J), colmajor_to_matrix(Yd, m, R, m)
+
+
+def _proposal(ctx, Y, K, mode):
+    m, R = Y.shape
+    Yd = _colmajor(Y)
+    Yf = torch.empty_like(Yd)
+    J = torch.empty(K, dtype=torch.int32, device="cuda")
+    st = idl.idl_cpqr_proposal(ctx, Yd, Yf, m, R, m, K, mode, J)
+    assert np.array_equal(host(Yd), np.ascontiguousarray(Y.T))      # the sketch is read only
+    return st, host(J), colmajor_to_matrix(Yf, m, R, m)
+
+
+def _oracle_margin(Y, cand, K):
+    """max over outside columns and steps of rho_o(t) / |r_tt| (oracle, FP64)."""
+    Y = Y.astype(np.float64)
+    f = ocp.cpqr(Y[:, cand], K)
+    J = cand[f["perm"][:K]]
+    out = np.setdiff1d(np.arange(Y.shape[1]), cand)
+    if out.size == 0:
+        return 0.0
+    Q, _ = np.linalg.qr(Y[:, J])
+    r2 = (Q.T @ Y[:, out]) ** 2
+    n = np.sum(Y[:, out] ** 2, axis=0)
+    rho2 = n[None, :] - np.vstack([np.zeros((1, out.size)), np.cumsum(r2, axis=0)[:-1]])
+    return float(np.max(np.sqrt(np.maximum(rho2, 0)) / f["norms"][:, None]))
+
+
+@pytest.mark.parametrize("m,R,K,seed", [(40, 800, 10, 20), (74, 5000, 64, 21), (60, 1000, 50, 22), (30, 50, 24, 23)])
+def test_norm_proposal_matches_plain(ctx, m, R, K, seed):
+    """Certified or not, the proposal path gives the plain QR's pivots and
+    factor rows; the device certificate agrees with the oracle's away from
+    the margin."""
+    Y = _sketch(m, R, seed)
+    Jp, Yp = _plain(ctx, Y, K)
+    st, J, Yf = _proposal(ctx, Y, K, idl.PROPOSAL_NORM)
+    assert st in (1, 2)
+    assert np.array_equal(J, Jp)
+    assert rel_fro(Yf[:K], Yp[:K]) <= 1e-4
+    assert abs(np.linalg.norm(Yf[K:]) - np.linalg.norm(Yp[K:])) <= 1e-3 * max(1.0, np.linalg.norm(Yp))
+    C = min(2 * K, R)
+    n32 = np.sum(Y.astype(np.float32) ** 2, axis=0)
+    cand = opr.candidates(n32.astype(np.float64), C)
+    r = _oracle_margin(Y, cand, K)
+    if r < 0.99:
+        assert st == 1
+    elif r > 1.01:
+        assert st == 2
+    assert ctx.sync() == idl.IDL_OK
+
+
+def test_proposal_rejects_a_hidden_pivot(ctx):
+    """Large-norm columns that are nearly collinear leave the later pivots to
+    small-norm columns: the norm proposal must be rejected, and the result is
+    still the plain QR's."""
+    rng = np.random.default_rng(30)
+    m, R, K = 32, 400, 8
+    Y = 0.1 * rng.standard_normal((m, R))
+    u = rng.standard_normal(m)
+    Y[:, :60] = 10.0 * u[:, None] + 1e-3 * rng.standard_normal((m, 60))      # 60 copies of one direction
+    Y = Y.astype(np.float32)
+    st, J, _ = _proposal(ctx, Y, K, idl.PROPOSAL_NORM)
+    Jp, _ = _plain(ctx, Y, K)
+    assert st == 2
+    assert np.array_equal(J, Jp)
+    cand = opr.candidates(np.sum(Y.astype(np.float64) ** 2, axis=0), 2 * K)
+    assert not opr.certificate(Y.astype(np.float64), cand, K)[0]
+
+
+def test_mlp_proposal_matches_plain_any_weights(ctx):
+    """Random weights give a poor proposal; the result is still the plain QR's."""
+    _, theta = _params(31)
+    idl.idl_mlp_set_weights(ctx, theta)
+    for seed, (m, R, K) in enumerate([(40, 700, 12), (74, 3000, 40)]):
+        Y = _sketch(m, R, 40 + seed)
+        Jp, Yp = _plain(ctx, Y, K)
+        st, J, Yf = _proposal(ctx, Y, K, idl.PROPOSAL_MLP)
+        assert st in (1, 2)
+        assert np.array_equal(J, Jp)
+        assert rel_fro(Yf[:K], Yp[:K]) <= 1e-4
+
+
+def test_id_matrix_with_proposal(ctx):
+    """End to end (Algorithm 2 + Gaussian stage + QR through the proposal):
+    same J and T as the plain path; info reports the proposal's outcome."""
+    A = lowrank_dense(4000, 2000, 0.8, 1e-4, 20190130, dtype=np.float32)
+    A = A * np.random.default_rng(1).lognormal(0.0, 1.0, 2000)[None, :].astype(np.float32)
+    Ad = dev(A)
+    K = 20
+    out = {}
+    for mode in (idl.PROPOSAL_NONE, idl.PROPOSAL_NORM):
+        p = idl.make_params(900, 30, 20190130, learned=mode, residual=2)
+        J = torch.empty(K, dtype=torch.int32, device="cuda")
+        T = torch.empty(K * (2000 - K), dtype=torch.float64, device="cuda")
+        info = idl.Info()
+        idl.id_matrix(ctx, Ad, K, p, J, T, info=info)
+        out[mode] = (host(J), host(T), info.as_dict())
+    assert out[idl.PROPOSAL_NONE][2]["proposal"] == 0
+    assert out[idl.PROPOSAL_NORM][2]["proposal"] in (1, 2)
+    assert np.array_equal(out[0][0], out[2][0])
+    assert np.allclose(out[0][1], out[2][1], rtol=1e-4, atol=1e-6)
+    assert abs(out[0][2]["residual"] - out[2][2]["residual"]) <= 1e-4 * max(1e-6, out[0][2]["residual"])
+
+
+def test_proposal_argument_errors(ctx):
+    Y = _colmajor(_sketch(20, 100, 50))
+    Yf = torch.empty_like(Y)
+    J = torch.empty(5, dtype=torch.int32, device="cuda")
+    with pytest.raises(idl.IdlError):
+        idl.idl_cpqr_proposal(ctx, Y, Y, 20, 100, 20, 5, idl.PROPOSAL_NORM, J)      # in place
+    with pytest.raises(idl.IdlError):
+        idl.idl_cpqr_proposal(ctx, Y, Yf, 20, 100, 20, 5, 7, J)                      # unknown mode
+    big = _colmajor(_sketch(130, 300, 51))
+    with pytest.raises(idl.IdlError) as e:
+        idl.idl_cpqr_proposal(ctx, big, torch.empty_like(big), 130, 300, 130, 5, idl.PROPOSAL_NORM, J)
+    assert e.value.code == idl.IDL_ELIMIT
+    A = dev(lowrank_dense(500, 100, 0.8, 0.0, 1, dtype=np.float64))
+    p = idl.make_params(200, 20, 1, precision=idl.PREC_FP64, learned=idl.PROPOSAL_NORM)
+    with pytest.raises(idl.IdlError) as e:
+        idl.id_matrix(ctx, A, 5, p, J, torch.empty(5 * 95, dtype=torch.float64, device="cuda"))
+    assert e.value.code == idl.IDL_EINVAL
