@@ -62,7 +62,9 @@ typedef struct idl_params {
   uint64_t seed;      /* seed of the counter-based draws (h, s, the permutation, Omega) */
   int32_t  residual;  /* 0: none; 1: ||R22||_F / ||Y2||_F in FP64 (default); 2: explicit FP64 ||Y2_rest - Y2_J T||_F / ||Y2||_F */
   int32_t  learned;   /* QR stage column proposal: IDL_PROPOSAL_NONE (default), _MLP or _NORM (FP32 data, m <= 128) */
-  int64_t  reserved[4];
+  int32_t  cand_factor; /* proposal candidates C = min(cand_factor * K, R); 0 = 2 (1..8) */
+  int32_t  reserved1;
+  int64_t  reserved[3];
 } idl_params;
 
 /* Diagnostics of one ID (filled when a non-NULL pointer is passed; the call then synchronises). */
@@ -280,7 +282,8 @@ int id_cp_tensor(idl_ctx* ctx, int N, const int64_t* dims, int64_t R, const void
  *   of the relative squared norm, three ridge leverage scores
  *   y^T (Y2 Y2^T + lambda I)^{-1} y with lambda = {1e-1, 1e-2, 1e-3} tr(Y2 Y2^T)/m,
  *   max |y_i| / ||y||, K/R and m/R.  The C = min(2K, R) best columns (ties:
- *   smaller index) go through the pivoted QR in one CTA; its reflectors are
+ *   smaller index; cand_factor = 4 or 8 widens the set) go through the
+ *   pivoted QR in one CTA; its reflectors are
  *   applied to every other column, and the certificate checks that no outside
  *   column's remaining norm reaches a step's pivot norm (squared norms within a
  *   relative margin of 1e-4).  If it holds, J and the factored sketch equal
@@ -343,10 +346,10 @@ int idl_train_proposal(idl_ctx* ctx, const float* F, const float* y, int64_t n, 
 /* The QR stage through the proposal on a given sketch: Y2 (m x R column-major,
  * ldy2 >= m, FP32, device, read only) -> Yf (same shape, the factored sketch
  * as idl_cpqr leaves it), J (K int32, device).  mode: IDL_PROPOSAL_MLP or
- * IDL_PROPOSAL_NORM.  proposal (host, optional): 1 certified, 2 rejected
+ * IDL_PROPOSAL_NORM; cand_factor as in idl_params.  proposal (host, optional): 1 certified, 2 rejected
  * (the plain QR ran); passing it synchronises the stream. */
 int idl_cpqr_proposal(idl_ctx* ctx, const float* Y2, float* Yf, int64_t m, int64_t R, int64_t ldy2,
-                      int64_t K, int mode, int32_t* J, int* proposal);
+                      int64_t K, int mode, int cand_factor, int32_t* J, int* proposal);
 
 #define IDL_ITEM_DENSE 0
 #define IDL_ITEM_CP    2

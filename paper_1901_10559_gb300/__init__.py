@@ -37,7 +37,8 @@ class IdlError(RuntimeError):
 class Params(ctypes.Structure):
     _fields_ = [("m1", ctypes.c_int64), ("m2", ctypes.c_int64), ("modified", ctypes.c_int32),
                 ("precision", ctypes.c_int32), ("seed", ctypes.c_uint64), ("residual", ctypes.c_int32),
-                ("learned", ctypes.c_int32), ("reserved", ctypes.c_int64 * 4)]
+                ("learned", ctypes.c_int32), ("cand_factor", ctypes.c_int32), ("reserved1", ctypes.c_int32),
+                ("reserved", ctypes.c_int64 * 3)]
 
 
 class Info(ctypes.Structure):
@@ -121,7 +122,8 @@ _SIGS = {
     "idl_mlp_grad": ([_vp, _vp, _vp, _i64, ctypes.c_float, _vp, _vp], _int),
     "idl_proposal_labels": ([_vp, _vp, _i64, _i64, _i64, _i64, _vp, _vp], _int),
     "idl_train_proposal": ([_vp, _vp, _vp, _i64, ctypes.POINTER(TrainParams), _vp], _int),
-    "idl_cpqr_proposal": ([_vp, _vp, _vp, _i64, _i64, _i64, _i64, _int, _vp, ctypes.POINTER(ctypes.c_int)], _int),
+    "idl_cpqr_proposal": ([_vp, _vp, _vp, _i64, _i64, _i64, _i64, _int, _int, _vp, ctypes.POINTER(ctypes.c_int)],
+                          _int),
 }
 
 
@@ -211,11 +213,12 @@ def launch_count() -> int:
     return int(lib().idl_launch_count())
 
 
-def make_params(m1, m2, seed, modified=True, precision=PREC_FP32, residual=1, learned=PROPOSAL_NONE):
+def make_params(m1, m2, seed, modified=True, precision=PREC_FP32, residual=1, learned=PROPOSAL_NONE,
+                cand_factor=0):
     p = Params()
     p.m1, p.m2, p.modified, p.precision, p.seed, p.residual = int(m1), int(m2), int(modified), int(precision), \
         int(seed), int(residual)
-    p.learned = int(learned)
+    p.learned, p.cand_factor = int(learned), int(cand_factor)
     return p
 
 
@@ -427,8 +430,9 @@ def idl_batch_fallbacks(ctx):
     return rc
 
 
-def idl_cpqr_proposal(ctx, Y2, Yf, m, R, ldy2, K, mode, J):
-    """Returns 1 (certified) or 2 (rejected: the plain QR ran)."""
+def idl_cpqr_proposal(ctx, Y2, Yf, m, R, ldy2, K, mode, J, cand_factor=2, sync=True):
+    """Returns 1 (certified) or 2 (rejected: the plain QR ran); None with sync=False."""
     out = ctypes.c_int(0)
-    ctx.check(lib().idl_cpqr_proposal(ctx.ptr, _p(Y2), _p(Yf), m, R, ldy2, K, int(mode), _p(J), ctypes.byref(out)))
-    return out.value
+    ctx.check(lib().idl_cpqr_proposal(ctx.ptr, _p(Y2), _p(Yf), m, R, ldy2, K, int(mode), int(cand_factor), _p(J),
+                                      ctypes.byref(out) if sync else None))
+    return out.value if sync else None

@@ -414,6 +414,7 @@ static int check_params(idl_ctx* ctx, const idl_params* p, int dtype, int64_t I,
   if (p->learned < IDL_PROPOSAL_NONE || p->learned > IDL_PROPOSAL_NORM)
     return fail(ctx, IDL_EINVAL, "unknown proposal mode");
   if (p->learned && dtype != IDL_F32) return fail(ctx, IDL_EINVAL, "the column proposal needs FP32 data");
+  if (p->cand_factor < 0 || p->cand_factor > 8) return fail(ctx, IDL_EINVAL, "cand_factor must be in 0..8");
   if (p->learned && ((p->m2 > 0 ? p->m2 : p->m1) > 128 || K > 128))
     return fail(ctx, IDL_ELIMIT, "the column proposal needs m <= 128 and K <= 128");
   return IDL_OK;
@@ -452,7 +453,7 @@ static int finish_pipeline(idl_ctx* ctx, const idl_params* p, int dtype, void* Y
   WS(rest, int32_t, kWsRest, R);
   TRY(clear_diag(ctx));
   if (p->learned)
-    STAGE(kStQR, launch_proposal_qr(ctx, (const float*)Y2, (float*)Yf, m, R, ld2, K, p->learned, Jd));
+    STAGE(kStQR, launch_proposal_qr(ctx, (const float*)Y2, (float*)Yf, m, R, ld2, K, p->learned, p->cand_factor, Jd));
   else
     STAGE(kStQR, launch_cpqr(ctx, Yf, m, R, ld2, dtype, K, Jd, nullptr));
   STAGE(kStSolve, launch_t_solve(ctx, Yf, m, R, ld2, dtype, K, Jd, Td, rest));

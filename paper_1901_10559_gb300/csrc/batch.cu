@@ -269,14 +269,14 @@ __global__ void __launch_bounds__(prop::kApplyThreads) b_papply_kernel(const BIt
                          it.rn, it.flag, it.diag + 8, (int)local, (int)(pre[p + 1] - pre[p]), smf);
 }
 
-// candidate QR: one CTA (a cluster of one) per proposal item
+// candidate QR: one CTA per proposal item
 template <int V, int TPC>
-__global__ void __launch_bounds__(RegCpqr<float, V, TPC>::kMaxThreads, 1)
+__global__ void __launch_bounds__(CtaCpqr<float, V, TPC>::kMaxThreads, 1)
 b_cand_kernel(const BItem* __restrict__ items, const int32_t* __restrict__ list, int* status) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const BItem& it = items[list[blockIdx.x]];
-  cpqr_reg_body<float, V, TPC>(it.Y2, it.Yf, (int)it.m2, it.C, (int)it.m2, it.K, it.C, it.J, it.rn, it.diag + 8,
-                               status, smem_raw, it.cand, it.V, it.beta);
+  cpqr_cta_body<float, V, TPC>(it.Y2, it.Yf, (int)it.m2, it.C, (int)it.m2, it.K, it.J, it.rn, it.diag + 8, status,
+                               smem_raw, it.cand, it.V, it.beta);
 }
 
 __global__ void b_rest_kernel(const BItem* __restrict__ items, const int64_t* __restrict__ pre, int n) {
@@ -326,7 +326,7 @@ std::string signature(const idl_batch_item* items, int n) {
     const idl_batch_item& x = items[i];
     snprintf(buf, sizeof(buf), "%d:%lld:%lld:%lld:%lld:%lld:%d:%d:%d;", x.kind, (long long)x.I, (long long)x.R,
              (long long)x.K, (long long)x.params.m1, (long long)x.params.m2, x.params.precision, x.N,
-             x.params.learned);
+             x.params.learned * 16 + x.params.cand_factor);
     s += buf;
     for (int q = 0; q < x.N && x.kind == IDL_ITEM_CP; ++q) {
       snprintf(buf, sizeof(buf), "%lld,", (long long)x.dims[q]);
@@ -393,7 +393,8 @@ static bool cpqr_cfg_fits(const std::vector<int>& list, const std::vector<BItem>
     threads = std::max(threads, (int)round_up((int64_t)nc * TPC, 32));
     maxm = std::max(maxm, (int)x.m2);
   }
-  if (threads > RegCpqr<float, V, TPC>::kMaxThreads || threads < 32) return false;
+  const int maxt = cand ? CtaCpqr<float, V, TPC>::kMaxThreads : RegCpqr<float, V, TPC>::kMaxThreads;
+  if (threads > maxt || threads < 32) return false;
   cfg->V = V;
   cfg->TPC = TPC;
   cfg->CS = CS;
@@ -436,24 +437,11 @@ static int launch_b_cpqr(idl_ctx* ctx, const BItem* d_items, const int32_t* d_li
 
 template <int V, int TPC>
 static int launch_b_cand(idl_ctx* ctx, const BItem* d_items, const int32_t* d_list, int nlist, const CpqrCfg& c) {
-  auto kern = b_cand_kernel<V, TPC>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c.smem);
-  if (e != cudaSuccess) return cuda_check(ctx, e, "batch candidate QR attribute");
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3((unsigned)nlist);
-  cfg.blockDim = dim3((unsigned)c.threads);
-  cfg.dynamicSmemBytes = c.smem;
-  cfg.stream = ctx->stream;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeClusterDimension;
-  attr[0].val.clusterDim.x = 1;
-  attr[0].val.clusterDim.y = 1;
-  attr[0].val.clusterDim.z = 1;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  e = cudaLaunchKernelEx(&cfg, kern, d_items, d_list, ctx->d_status);
+  (void)c.smem;
+  b_cand_kernel<V, TPC><<<(unsigned)nlist, (unsigned)c.threads, cta_cpqr_smem<float, V, TPC>(), ctx->stream>>>(
+      d_items, d_list, ctx->d_status);
   count_launch();
-  return cuda_check(ctx, e, "batch candidate QR");
+  return cuda_check(ctx, cudaGetLastError(), "batch candidate QR");
 }
 
 static int dispatch_b_cand(idl_ctx* ctx, const BItem* d_items, const int32_t* d_list, int nlist, const CpqrCfg& c) {
@@ -494,6 +482,7 @@ static int plan_batch(idl_ctx* ctx, const idl_batch_item* items, int n, const Tu
     if (pr.precision != prec) return fail(ctx, IDL_EINVAL, "batch: all items must use one precision");
     if (pr.learned < IDL_PROPOSAL_NONE || pr.learned > IDL_PROPOSAL_NORM)
       return fail(ctx, IDL_EINVAL, "batch: unknown proposal mode");
+    if (pr.cand_factor < 0 || pr.cand_factor > 8) return fail(ctx, IDL_EINVAL, "batch: cand_factor must be in 0..8");
     if (pr.learned == IDL_PROPOSAL_MLP && !ctx->mlp_ready)
       return fail(ctx, IDL_EINVAL, "batch: no MLP weights (idl_mlp_init / idl_load_weights)");
     if (prec == IDL_PREC_FP64) return fail(ctx, IDL_EINVAL, "batch: FP32 data only (precision FP32, BF16X3 or BF16)");
@@ -585,7 +574,7 @@ static int plan_batch(idl_ctx* ctx, const idl_batch_item* items, int n, const Tu
     o_rest[i] = take(sizeof(int32_t) * (size_t)b.R);
     o_Rinv[i] = take(sizeof(double) * (size_t)(x.K * x.K));
     b.learned = x.params.learned;
-    b.C = (int)std::min<int64_t>(2 * x.K, x.R);
+    b.C = (int)std::min<int64_t>((x.params.cand_factor > 0 ? x.params.cand_factor : 2) * x.K, x.R);
     b.nsplit = (int)cdiv(x.R, prop::kGramCols);
     if (b.learned) {
       const int64_t m = b.m2;

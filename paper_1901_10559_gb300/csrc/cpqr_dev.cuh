@@ -244,6 +244,167 @@ __device__ __forceinline__ void cpqr_reg_body(const T* __restrict__ Yin, T* __re
   if (lane == 0 && r22 != 0.0) atomicAdd(&diag[0], r22);
 }
 
+// ----------------------------------------------------------------------------
+// One-CTA variant for a column subset that fits one block (the learned
+// proposal's candidate QR).  Two block barriers per pivot step:
+//   A. every warp reduces its groups' remaining norms and publishes its best;
+//      barrier;
+//   B. every warp reduces the published candidates (same winner everywhere);
+//      the winner's own group forms the Householder reflection from its
+//      registers (group reductions, no staging) and writes v and beta to
+//      shared memory; barrier;
+//   C. every group applies the reflection to its column in registers and
+//      recomputes the trailing norm exactly.
+// Same arguments and outputs as cpqr_reg_body; colmap is required (column c
+// of the subset is column colmap[c] of Yin / Yout).
+// ----------------------------------------------------------------------------
+template <typename T, int V, int TPC>
+__device__ __forceinline__ void cpqr_cta_body(const T* __restrict__ Yin, T* __restrict__ Yout, int m, int C, int ld,
+                                              int K, int32_t* __restrict__ J, double* __restrict__ rnorm,
+                                              double* __restrict__ diag, int* status, unsigned char* smem_raw,
+                                              const int32_t* __restrict__ colmap, T* __restrict__ Vout,
+                                              T* __restrict__ Bout) {
+  constexpr int tpc = TPC;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, NW = blockDim.x >> 5;
+  const int g = tid / tpc, gl = tid - g * tpc;
+  const bool own = g < C;
+  const int64_t scol = own ? (int64_t)colmap[g] : 0;
+  T* vs = (T*)smem_raw;                                             // V*TPC: v, zero outside rows [t, m)
+  __shared__ T red_v[32];
+  __shared__ int red_i[32];
+  __shared__ T s_beta;
+  T y[V];
+#pragma unroll
+  for (int j = 0; j < V; ++j) {
+    const int i = gl + tpc * j;
+    y[j] = (own && i < m) ? Yin[scol * ld + i] : T(0);
+  }
+  T nn = T(0);
+#pragma unroll
+  for (int j = 0; j < V; ++j) nn += y[j] * y[j];
+  nn = group_sum(nn, tpc);
+  {
+    double f = (own && gl == 0) ? (double)nn : 0.0;
+    f = warp_sum(f);
+    if (lane == 0 && f != 0.0) atomicAdd(&diag[1], f);
+  }
+  T nrm2 = own ? nn : T(-1);
+  int tp = -1;
+  T alpha_p = T(0);
+  for (int t = 0; t < K; ++t) {
+    // A. warp candidates
+    T bv = (gl == 0 && nrm2 >= T(0)) ? nrm2 : T(-1);
+    int bi = (gl == 0 && nrm2 >= T(0)) ? g : -1;
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+      const T ov = __shfl_xor_sync(0xffffffffu, bv, o);
+      const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+      if (better(ov, oi, bv, bi)) { bv = ov; bi = oi; }
+    }
+    if (lane == 0) { red_v[wid] = bv; red_i[wid] = bi; }
+    __syncthreads();
+    // B. block winner (every warp), reflection by the winner's group
+    bv = lane < NW ? red_v[lane] : T(-1);
+    bi = lane < NW ? red_i[lane] : -1;
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+      const T ov = __shfl_xor_sync(0xffffffffu, bv, o);
+      const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+      if (better(ov, oi, bv, bi)) { bv = ov; bi = oi; }
+    }
+    const int p = bi;
+    if (p < 0) {                                                     // no finite remaining column
+      if (tid == 0) {
+        for (int q = t; q < K; ++q) J[q] = -1;
+        set_status(status, IDL_EDATA);
+      }
+      break;                                                         // uniform: every thread saw p < 0
+    }
+    const bool piv = own && g == p;
+    if ((p * tpc) >> 5 == wid) {
+      // the pivot's warp: trailing norm and x_t per group (all lanes shuffle;
+      // only the pivot's group uses the result)
+      T xs = T(0), x0 = T(0);
+#pragma unroll
+      for (int j = 0; j < V; ++j) {
+        const int i = gl + tpc * j;
+        if (i >= t) xs += y[j] * y[j];
+        if (i == t) x0 = y[j];
+      }
+      xs = group_sum(xs, tpc);
+      x0 = group_sum(x0, tpc);                                       // one lane of a group holds row t
+      if (piv) {
+      const T nrm = sqrt(xs);
+      const T alpha = (x0 >= T(0)) ? -nrm : nrm;
+      const T beta = (nrm > T(0)) ? T(1) / (nrm * (nrm + fabs(x0))) : T(0);
+#pragma unroll
+      for (int j = 0; j < V; ++j) {
+        const int i = gl + tpc * j;
+        const T v = (i < t || i >= m) ? T(0) : (i == t ? x0 - alpha : y[j]);
+        vs[i] = v;
+        if (i < m) Vout[(int64_t)t * m + i] = v;
+      }
+      if (gl == 0) {
+        s_beta = beta;
+        Bout[t] = beta;
+        J[t] = colmap[p];
+        if (rnorm) rnorm[t] = (double)fabs(alpha);
+        if (t == 0) diag[3] = (double)fabs(alpha);
+        if (t == K - 1) diag[4] = (double)fabs(alpha);
+      }
+      nrm2 = T(-1);
+      tp = t;
+      alpha_p = alpha;
+      }
+    }
+    __syncthreads();
+    // C. apply to the remaining columns
+    const T beta = s_beta;
+    const bool upd = own && nrm2 >= T(0);
+    T d0 = T(0), d1 = T(0);
+#pragma unroll
+    for (int j = 0; j < V; j += 2) {
+      d0 = fma(vs[gl + tpc * j], y[j], d0);
+      if (j + 1 < V) d1 = fma(vs[gl + tpc * (j + 1)], y[j + 1], d1);
+    }
+    T d = group_sum(d0 + d1, tpc) * beta;
+    if (!upd) d = T(0);
+    const int jt = (t - gl) >= 0 ? (t - gl) / tpc + 1 : 0;
+    T s0 = T(0), s1 = T(0);
+#pragma unroll
+    for (int j = 0; j < V; ++j) {
+      y[j] = fma(-d, vs[gl + tpc * j], y[j]);
+      const T q = (j >= jt) ? y[j] * y[j] : T(0);
+      if (j & 1) s1 += q; else s0 += q;
+    }
+    const T s2 = group_sum(s0 + s1, tpc);
+    if (upd) nrm2 = s2;
+  }
+  double r22 = 0.0;
+#pragma unroll
+  for (int j = 0; j < V; ++j) {
+    const int i = gl + tpc * j;
+    if (own && i < m) {
+      T out = y[j];
+      if (tp >= 0) out = (i < tp) ? y[j] : (i == tp ? alpha_p : T(0));
+      Yout[scol * ld + i] = out;
+      if (tp < 0 && i >= K) r22 += (double)y[j] * (double)y[j];
+    }
+  }
+  r22 = warp_sum(r22);
+  if (lane == 0 && r22 != 0.0) atomicAdd(&diag[0], r22);
+}
+
+template <typename T, int V, int TPC>
+__host__ __device__ constexpr size_t cta_cpqr_smem() { return sizeof(T) * (size_t)V * TPC; }
+
+// Threads per CTA of the one-CTA variant (no staging buffer, more registers
+// per thread than the cluster variant needs).
+template <typename T, int V, int TPC> struct CtaCpqr {
+  static constexpr int kWords = V * (int)(sizeof(T) / 4);
+  static constexpr int kMaxThreads = kWords <= 16 ? 1024 : kWords <= 32 ? 640 : kWords <= 64 ? 448 : 320;
+};
+
 // Fallback gate of the learned proposal.  With a gate, a QR launch is the
 // proposal's fallback and only runs when the certificate failed (*gate != 0);
 // otherwise block 0 moves the proposal's diagnostics (diag[8..12]) into

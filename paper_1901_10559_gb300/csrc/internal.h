@@ -117,7 +117,7 @@ int launch_transpose_to_colmajor(idl_ctx* ctx, const void* Y1, int64_t m, int64_
 int launch_features(idl_ctx* ctx, const float* Y, int64_t m, int64_t R, int64_t ld, int64_t K, float* F);
 int launch_mlp_scores(idl_ctx* ctx, const float* F, int64_t n, float* s);
 int launch_proposal_qr(idl_ctx* ctx, const float* Y2, float* Yf, int64_t m, int64_t R, int64_t ld, int64_t K,
-                       int mode, int32_t* J);
+                       int mode, int cand_factor, int32_t* J);
 
 // tensorsketch.cu
 int launch_tensorsketch(idl_ctx* ctx, int N, const int64_t* dims, int64_t R, const void* const* factors,

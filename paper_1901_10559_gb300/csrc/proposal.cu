@@ -12,6 +12,7 @@
 
 #include "common.cuh"
 #include "internal.h"
+#include "cpqr_dev.cuh"
 #include "proposal_dev.cuh"
 
 #define TRY(x)                     \
@@ -74,6 +75,17 @@ __global__ void __launch_bounds__(kApplyThreads) prop_apply_kernel(const float* 
                                                                    double* diag) {
   extern __shared__ __align__(16) float smf[];
   apply_cert_block(Y2, Yf, ld, m, K, outl, nout, V, beta, rn, cert_fail, diag, blockIdx.x, gridDim.x, smf);
+}
+
+// Candidate QR: the K-step pivoted QR of the C candidate columns in one CTA,
+// recording the reflectors (cpqr_cta_body).
+template <int V, int TPC>
+__global__ void __launch_bounds__(CtaCpqr<float, V, TPC>::kMaxThreads, 1)
+prop_cand_kernel(const float* __restrict__ Y2, float* __restrict__ Yf, int m, int C, int ld, int K,
+                 int32_t* __restrict__ J, double* __restrict__ rn, double* __restrict__ diag, int* status,
+                 const int32_t* __restrict__ cand, float* __restrict__ V_, float* __restrict__ beta) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cpqr_cta_body<float, V, TPC>(Y2, Yf, m, C, ld, K, J, rn, diag, status, smem_raw, cand, V_, beta);
 }
 
 // Gathers minibatch positions [p0, p0 + nb) of the epoch order into contiguous rows.
@@ -181,17 +193,42 @@ int launch_mlp_scores(idl_ctx* ctx, const float* F, int64_t n, float* s) {
   return cuda_check(ctx, cudaGetLastError(), "mlp scores");
 }
 
+template <int VV, int TT>
+static bool cand_try(idl_ctx* ctx, const float* Y2, float* Yf, int64_t m, int64_t C, int64_t ld, int64_t K, int32_t* J,
+                     double* rn, double* diag, const int32_t* cand, float* V, float* beta, int* rc) {
+  if (cdiv(m, TT) > VV) return false;
+  const int threads = (int)round_up(C * TT, 32);
+  if (threads > CtaCpqr<float, VV, TT>::kMaxThreads) return false;
+  prop_cand_kernel<VV, TT><<<1, threads, cta_cpqr_smem<float, VV, TT>(), ctx->stream>>>(
+      Y2, Yf, (int)m, (int)C, (int)ld, (int)K, J, rn, diag, ctx->d_status, cand, V, beta);
+  count_launch();
+  *rc = cuda_check(ctx, cudaGetLastError(), "candidate QR");
+  return true;
+}
+
+// Most lanes per column first (shortest serial chain per step).
+static int launch_cand_qr(idl_ctx* ctx, const float* Y2, float* Yf, int64_t m, int64_t C, int64_t ld, int64_t K,
+                          int32_t* J, double* rn, double* diag, const int32_t* cand, float* V, float* beta) {
+  int rc = IDL_OK;
+#define CAND(VV, TT) if (cand_try<VV, TT>(ctx, Y2, Yf, m, C, ld, K, J, rn, diag, cand, V, beta, &rc)) return rc;
+  CAND(8, 32) CAND(8, 16) CAND(8, 8) CAND(16, 8) CAND(8, 4) CAND(16, 4) CAND(32, 4) CAND(16, 2) CAND(32, 2)
+  CAND(16, 1) CAND(32, 1) CAND(64, 4) CAND(64, 2) CAND(64, 1) CAND(96, 1) CAND(128, 1)
+#undef CAND
+  return fail(ctx, IDL_ELIMIT, "proposal: the candidate set does not fit one CTA (lower cand_factor)");
+}
+
 // The QR stage through the proposal: Y2 (original sketch, read only) -> Yf
 // (factored, the layout idl_cpqr produces), J.  The certificate flag is
 // ctx->d_status[1]; the proposal's diagnostics go to d_diag[8..12] and the
 // gated fallback moves or recomputes d_diag[0..4].
 int launch_proposal_qr(idl_ctx* ctx, const float* Y2, float* Yf, int64_t m, int64_t R, int64_t ld, int64_t K,
-                       int mode, int32_t* J) {
+                       int mode, int cand_factor, int32_t* J) {
   if (m > kMaxM) return fail(ctx, IDL_ELIMIT, "proposal: needs m <= 128");
+  if (cand_factor < 0 || cand_factor > 8) return fail(ctx, IDL_EINVAL, "proposal: cand_factor must be in 0..8");
   if (K > 128) return fail(ctx, IDL_ELIMIT, "proposal: needs K <= 128");
   if (mode == IDL_PROPOSAL_MLP && !ctx->mlp_ready)
     return fail(ctx, IDL_EINVAL, "proposal: no MLP weights (idl_mlp_init / idl_load_weights)");
-  const int64_t C = std::min<int64_t>(2 * K, R);
+  const int64_t C = std::min<int64_t>((cand_factor ? cand_factor : 2) * K, R);
   const int64_t nout = R - C;
   // workspace: F (R x 8), scores (R), cand (C), outl (R - C), V (K x m), beta (K), rn (K doubles)
   const size_t bytes = sizeof(float) * (size_t)R * kNF + sizeof(float) * R + sizeof(int32_t) * (size_t)R +
@@ -216,13 +253,7 @@ int launch_proposal_qr(idl_ctx* ctx, const float* Y2, float* Yf, int64_t m, int6
         count_launch();
   }
   prop_select_kernel<<<1, kSelThreads, 0, ctx->stream>>>(sc, (int)R, (int)C, cand, outl), count_launch();
-  QrExtra xc;
-  xc.colmap = cand;
-  xc.Vout = V;
-  xc.Bout = beta;
-  xc.diag = pdiag;
-  xc.max_cs = 1;
-  TRY(launch_cpqr_ex(ctx, Y2, Yf, m, C, ld, K, J, rn, xc));
+  TRY(launch_cand_qr(ctx, Y2, Yf, m, C, ld, K, J, rn, pdiag, cand, V, beta));
   if (nout > 0) {
     const size_t sm = sizeof(float) * (size_t)(K * m + 2 * K);
     TRY(set_smem(ctx, (const void*)prop_apply_kernel, sm));
@@ -457,13 +488,13 @@ extern "C" int idl_proposal_labels(idl_ctx* ctx, const float* Y, int64_t m, int6
 // point of launch_proposal_qr).  proposal (host, optional): 1 certified,
 // 2 rejected (the plain QR ran); reading it synchronises the stream.
 extern "C" int idl_cpqr_proposal(idl_ctx* ctx, const float* Y2, float* Yf, int64_t m, int64_t R, int64_t ldy2,
-                                 int64_t K, int mode, int32_t* J, int* proposal) {
+                                 int64_t K, int mode, int cand_factor, int32_t* J, int* proposal) {
   TRY(ctx_ok(ctx));
   if (!Y2 || !Yf || !J || K < 1 || K >= R || K > m || ldy2 < m || R > 0x7fffffffLL || Y2 == Yf)
     return fail(ctx, IDL_EINVAL, "cpqr_proposal: bad arguments (Y2 and Yf must differ)");
   if (mode != IDL_PROPOSAL_MLP && mode != IDL_PROPOSAL_NORM) return fail(ctx, IDL_EINVAL, "cpqr_proposal: mode");
   TRY(cuda_check(ctx, cudaMemsetAsync(ctx->d_diag, 0, sizeof(double) * 16, ctx->stream), "diag clear"));
-  TRY(launch_proposal_qr(ctx, Y2, Yf, m, R, ldy2, K, mode, J));
+  TRY(launch_proposal_qr(ctx, Y2, Yf, m, R, ldy2, K, mode, cand_factor, J));
   if (proposal) {
     int f = 0;
     cudaError_t e = cudaMemcpyAsync(&f, ctx->d_status + 1, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream);

@@ -115,34 +115,45 @@ def collect(ctx, specs):
     return torch.cat(Fs).contiguous(), torch.cat(ys).contiguous()
 
 
-def evaluate(ctx, specs):
-    """Certified fraction and QR-stage device time: plain QR, MLP proposal, norm proposal."""
+def evaluate(ctx, specs, factors=(2, 4), reps=5):
+    """Per problem kind: certified fraction of the learned and the norm-heuristic
+    proposal for each candidate factor, whether J equals the plain QR's, and the
+    QR stage's device time (mean of ``reps`` back-to-back calls) of each path."""
     import torch
-    res = {"plain_ms": 0.0, "mlp_ms": 0.0, "norm_ms": 0.0, "mlp_certified": 0, "norm_certified": 0,
-           "problems": len(specs), "mlp_same_J": 0, "norm_same_J": 0}
+    res = {}
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     for sp in specs:
+        r = res.setdefault(sp["kind"], {"problems": 0, "plain_us": 0.0})
+        r["problems"] += 1
         Y2 = sketch(ctx, sp)
         m, R, K = sp["m2"], sp["R"], sp["K"]
-        Yp = Y2.clone()
+        copies = [Y2.clone() for _ in range(reps)]
         Jp = torch.empty(K, dtype=torch.int32, device="cuda")
         torch.cuda.synchronize()
         ev0.record()
-        idl.idl_cpqr(ctx, Yp, m, R, m, idl.IDL_F32, K, Jp)
+        for Yp in copies:
+            idl.idl_cpqr(ctx, Yp, m, R, m, idl.IDL_F32, K, Jp)
         ev1.record()
         torch.cuda.synchronize()
-        res["plain_ms"] += ev0.elapsed_time(ev1)
-        for mode, key in ((idl.PROPOSAL_MLP, "mlp"), (idl.PROPOSAL_NORM, "norm")):
-            Yf = torch.empty_like(Y2)
-            J = torch.empty(K, dtype=torch.int32, device="cuda")
-            ev0.record()
-            idl.lib().idl_cpqr_proposal(ctx.ptr, idl._p(Y2), idl._p(Yf), m, R, m, K, mode, idl._p(J), None)
-            ev1.record()
-            torch.cuda.synchronize()
-            res[key + "_ms"] += ev0.elapsed_time(ev1)
-            st = idl.idl_cpqr_proposal(ctx, Y2, Yf, m, R, m, K, mode, J)
-            res[key + "_certified"] += int(st == 1)
-            res[key + "_same_J"] += int(torch.equal(J, Jp))
+        r["plain_us"] += 1e3 * ev0.elapsed_time(ev1) / reps
+        Yf = torch.empty_like(Y2)
+        J = torch.empty(K, dtype=torch.int32, device="cuda")
+        for mode, name in ((idl.PROPOSAL_MLP, "mlp"), (idl.PROPOSAL_NORM, "norm")):
+            for c in factors:
+                key = "%s_c%d" % (name, c)
+                ev0.record()
+                for _ in range(reps):
+                    idl.idl_cpqr_proposal(ctx, Y2, Yf, m, R, m, K, mode, J, cand_factor=c, sync=False)
+                ev1.record()
+                torch.cuda.synchronize()
+                r[key + "_us"] = r.get(key + "_us", 0.0) + 1e3 * ev0.elapsed_time(ev1) / reps
+                st = idl.idl_cpqr_proposal(ctx, Y2, Yf, m, R, m, K, mode, J, cand_factor=c)
+                r[key + "_certified"] = r.get(key + "_certified", 0) + int(st == 1)
+                r[key + "_same_J"] = r.get(key + "_same_J", 0) + int(torch.equal(J, Jp))
+    for r in res.values():
+        for k in list(r):
+            if k.endswith("_us"):
+                r[k] /= r["problems"]
     return res
 
 
