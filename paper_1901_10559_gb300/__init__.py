@@ -19,6 +19,8 @@ import re
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libidl.so")
+# weights of the QR stage's column-proposal MLP, written by train_proposal.py
+PROPOSAL_WEIGHTS = os.path.join(_HERE, "proposal_weights.bin")
 HEADER = os.path.join(os.path.dirname(_HERE), "include", "idl.h")
 
 IDL_OK, IDL_EINVAL, IDL_ENOMEM, IDL_ECUDA, IDL_ERANK, IDL_ETIMEOUT, IDL_EDATA, IDL_ELIMIT = range(8)

@@ -309,3 +309,27 @@ def test_proposal_argument_errors(ctx):
     with pytest.raises(idl.IdlError) as e:
         idl.id_matrix(ctx, A, 5, p, J, torch.empty(5 * 95, dtype=torch.float64, device="cuda"))
     assert e.value.code == idl.IDL_EINVAL
+
+
+def test_learned_proposal_gain_vs_norm_heuristic(ctx):
+    """Held-out problems of the batched workload's shapes (sketched by the
+    library's own stages): with the shipped weights the learned proposal is
+    certified at least as often as the norm heuristic at the default candidate
+    factor, and every run returns the plain QR's pivots."""
+    from paper_1901_10559_gb300 import train_proposal as tp
+    idl.idl_load_weights(ctx, idl.PROPOSAL_WEIGHTS)
+    cert = {idl.PROPOSAL_MLP: 0, idl.PROPOSAL_NORM: 0}
+    for sp in tp.problem_specs(1001, 8, 16):
+        Y2 = tp.sketch(ctx, sp)
+        m, R, K = sp["m2"], sp["R"], sp["K"]
+        Yp = Y2.clone()
+        Jp = torch.empty(K, dtype=torch.int32, device="cuda")
+        idl.idl_cpqr(ctx, Yp, m, R, m, idl.IDL_F32, K, Jp)
+        Yf = torch.empty_like(Y2)
+        J = torch.empty(K, dtype=torch.int32, device="cuda")
+        for mode in cert:
+            st = idl.idl_cpqr_proposal(ctx, Y2, Yf, m, R, m, K, mode, J)
+            assert torch.equal(J, Jp)
+            cert[mode] += int(st == 1)
+    assert cert[idl.PROPOSAL_MLP] >= cert[idl.PROPOSAL_NORM], \
+        "learned proposal certified %d of 24, norm heuristic %d" % (cert[idl.PROPOSAL_MLP], cert[idl.PROPOSAL_NORM])
