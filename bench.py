@@ -224,14 +224,14 @@ def make_batch(seed, rank=0, n_dense=256, n_cp=64):
     return dense, cps
 
 
-def batch_items(idl, dense, cps, prec):
+def batch_items(idl, dense, cps, prec, learned=0):
     import torch
     items, outs = [], []
     for pr in dense:
         K, R = pr["K"], pr["A"].shape[1]
         J = torch.empty(K, dtype=torch.int32, device="cuda")
         T = torch.empty(K * (R - K), dtype=torch.float64, device="cuda")
-        p = idl.make_params(pr["m1"], pr["m2"], seed=pr["seed"], modified=True, precision=prec)
+        p = idl.make_params(pr["m1"], pr["m2"], seed=pr["seed"], modified=True, precision=prec, learned=learned)
         items.append(idl.dense_item(pr["A"], K, p, J, T))
         outs.append((J, T, None))
     for pr in cps:
@@ -239,7 +239,7 @@ def batch_items(idl, dense, cps, prec):
         J = torch.empty(K, dtype=torch.int32, device="cuda")
         T = torch.empty(K * (R - K), dtype=torch.float64, device="cuda")
         lh = torch.empty(K, dtype=torch.float64, device="cuda")
-        p = idl.make_params(pr["L"], pr["m2"], seed=pr["seed"], modified=False, precision=prec)
+        p = idl.make_params(pr["L"], pr["m2"], seed=pr["seed"], modified=False, precision=prec, learned=learned)
         items.append(idl.cp_item(pr["facs"], pr["lam"], K, p, J, T, lh))
         outs.append((J, T, lh))
     return items, outs
@@ -330,6 +330,26 @@ def run_ours(args, ws, rank, local):
             else:
                 idl.id_cp_tensor(ctx, d_f, d_lam, K, p, J, T, lh)
 
+    # the same step with the QR stage's learned column proposal (shipped MLP weights)
+    idl.idl_load_weights(ctx, idl.PROPOSAL_WEIGHTS)
+    p_l = idl.make_params(w["m1"], w["m2"], seed=seed, modified=(name != "cp"), precision=prec, residual=1,
+                          learned=idl.PROPOSAL_MLP)
+    if name == "batched":
+        items_l, bouts_l = batch_items(idl, dense, cps, prec, learned=idl.PROPOSAL_MLP)
+
+        def step_learned():
+            idl.idl_batch_run(ctx, items_l)
+    elif name in ("sparse", "sparse_small"):
+        def step_learned():
+            idl.id_matrix_csr(ctx, d_rp, d_ci, d_v, c.shape, K, p_l, J, T)
+    elif name in ("dense64", "mixed"):
+        def step_learned():
+            if w["dtype"] == "f32":
+                idl.id_matrix(ctx, d_A, K, p_l, J, T)
+    else:
+        def step_learned():
+            idl.id_cp_tensor(ctx, d_f, d_lam, K, p_l, J, T, lh)
+
     for _ in range(args.warmup):
         step(J, T, lh)
     torch.cuda.synchronize()
@@ -361,6 +381,44 @@ def run_ours(args, ws, rank, local):
     ms_per_step = ms / args.steps
     solves_per_step = (w["n_dense"] + w["n_cp"]) if name == "batched" else 1
     value = ws * args.steps * solves_per_step / (ms / 1e3)
+
+    # learned vs plain: the same workload with the column proposal in the QR stage (fallbacks count
+    # with their full time); untimed runs first (graph capture / tuning for a new batch shape)
+    lvp = None
+    if w["dtype"] == "f32":
+        for _ in range(max(3, args.warmup)):
+            step_learned()
+        torch.cuda.synchronize()
+        nl = max(1, min(args.steps, args.learned_steps))
+        e0.record()
+        for _ in range(nl):
+            step_learned()
+        e1.record()
+        torch.cuda.synchronize()
+        ms_l = e0.elapsed_time(e1)
+        if name == "batched":
+            nfb = idl.idl_batch_fallbacks(ctx)
+            cert = (len(items_l) - nfb) / len(items_l)
+        else:
+            info = idl.Info()
+            if name in ("sparse", "sparse_small"):
+                idl.id_matrix_csr(ctx, d_rp, d_ci, d_v, c.shape, K, p_l, J, T, info=info)
+            elif name == "mixed":
+                idl.id_matrix(ctx, d_A, K, p_l, J, T, info=info)
+            else:
+                idl.id_cp_tensor(ctx, d_f, d_lam, K, p_l, J, T, lh, info=info)
+            cert = 1.0 if info.proposal == 1 else 0.0
+        if dist:
+            t = torch.tensor([ms_l], dtype=torch.float64, device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms_l = float(t.item())
+        v_l = ws * nl * solves_per_step / (ms_l / 1e3)
+        lvp = {"proposal": "mlp (shipped weights), top-2K candidates, certificate, plain QR on rejection",
+               "value_learned": round(v_l, 3), "value_plain": round(value, 3), "ratio": round(v_l / value, 4),
+               "certified_fraction": round(cert, 4), "steps": nl, "unit": "solves/s"}
+        for _ in range(2):
+            step(J, T, lh)        # restore the plain path's outputs for the accuracy check below
+        torch.cuda.synchronize()
 
     # end to end through the C ABI with host buffers (pinned), copies inside the timed region
     e2e_steps = max(1, min(args.steps, args.e2e_steps))
@@ -458,6 +516,7 @@ def run_ours(args, ws, rank, local):
                 "d2h_bytes_per_step": int(d2h), "steps": e2e_steps},
         "gpu_launches": int(n1 - n0),
         "clocks": clk,
+        "learned_vs_plain": lvp,
     }
     if ws == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(name, inp, budget_s=args.cpu_budget)
@@ -576,6 +635,7 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="sparse")
     ap.add_argument("--e2e-steps", type=int, default=30)
+    ap.add_argument("--learned-steps", type=int, default=300)
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()

@@ -70,7 +70,7 @@ struct BItem {
   // column proposal
   int learned, C, nsplit;
   float* Yf;                       // factored sketch (== Y2 without a proposal)
-  float *Gp, *nmaxp, *scal, *Linv, *F, *sc, *V, *beta;
+  float *Gp, *nmaxp, *scal, *Linv, *G, *F, *sc, *V, *beta;
   int32_t *cand, *outl;
   double* rn;
   int* flag;                       // certificate failed
@@ -79,7 +79,7 @@ struct BItem {
 
 // stages with a flattened block list (prefix tables, one per stage)
 enum BStage { kBDraw = 0, kBGauss, kBHist, kBScan, kBScatter, kBSortW, kBSortB, kBSketchD, kBSketchT, kBPlanes,
-              kBGemm, kBReduce, kBPGram, kBPChol, kBPFeat, kBPMlp, kBPNorm, kBPSel, kBPApply, kBRest, kBRinv,
+              kBGemm, kBReduce, kBPGram, kBPGRed, kBPChol, kBPFeat, kBPMlp, kBPNorm, kBPSel, kBPApply, kBRest, kBRinv,
               kBTgemm, kBLam, kBNumStages };
 
 __device__ __forceinline__ int find_item(const int64_t* __restrict__ pre, int n, int64_t blk) {
@@ -225,11 +225,18 @@ __global__ void __launch_bounds__(prop::kThreads) b_pgram_kernel(const BItem* __
   prop::gram_partial_block(it.Y2, (int)it.m2, (int)it.m2, (int)it.R, (int)local, it.Gp, it.nmaxp, smf);
 }
 
+__global__ void __launch_bounds__(prop::kThreads) b_pgred_kernel(const BItem* __restrict__ items,
+                                                                 const int64_t* __restrict__ pre, int n) {
+  ITEM_OF_BLOCK(pre, n);
+  prop::gram_reduce_elem(it.Gp, it.nsplit, it.nmaxp, (int)it.m2, (int)(local * blockDim.x + threadIdx.x), it.G,
+                         it.scal);
+}
+
 __global__ void __launch_bounds__(prop::kThreads) b_pchol_kernel(const BItem* __restrict__ items,
                                                                  const int64_t* __restrict__ pre, int n) {
   extern __shared__ __align__(16) float smf[];
   ITEM_OF_BLOCK(pre, n);
-  prop::chol_inv_block(it.Gp, it.nsplit, it.nmaxp, (int)it.m2, (int)local, it.Linv, it.scal, smf);
+  prop::chol_inv_block(it.G, (int)it.m2, (int)local, it.Linv, it.scal, smf);
 }
 
 __global__ void __launch_bounds__(prop::kThreads) b_pfeat_kernel(const BItem* __restrict__ items,
@@ -579,7 +586,7 @@ static int plan_batch(idl_ctx* ctx, const idl_batch_item* items, int n, const Tu
     if (b.learned) {
       const int64_t m = b.m2;
       o_Yf[i] = take(sizeof(float) * (size_t)(b.R * m));
-      o_Gp[i] = take(sizeof(float) * (size_t)(b.nsplit * m * m + b.nsplit + 4 + 3 * m * m));
+      o_Gp[i] = take(sizeof(float) * (size_t)(b.nsplit * m * m + b.nsplit + 4 + 4 * m * m));
       o_F[i] = take(sizeof(float) * (size_t)(b.R * prop::kNF + b.R));
       o_V[i] = take(sizeof(float) * (size_t)(x.K * m + x.K));
       o_cand[i] = take(sizeof(int32_t) * (size_t)b.R);
@@ -620,6 +627,7 @@ static int plan_batch(idl_ctx* ctx, const idl_batch_item* items, int n, const Tu
       b.nmaxp = (float*)(o_Gp[i] + sizeof(float) * (size_t)(b.nsplit * m * m));
       b.scal = (float*)((size_t)b.nmaxp + sizeof(float) * (size_t)b.nsplit);
       b.Linv = (float*)((size_t)b.scal + sizeof(float) * 4);
+      b.G = (float*)((size_t)b.Linv + sizeof(float) * (size_t)(3 * m * m));
       b.F = (float*)o_F[i];
       b.sc = (float*)(o_F[i] + sizeof(float) * (size_t)(b.R * prop::kNF));
       b.V = (float*)o_V[i];
@@ -651,6 +659,7 @@ static int plan_batch(idl_ctx* ctx, const idl_batch_item* items, int n, const Tu
     nb[kBReduce] = cdiv(b.R * b.m2, 256);
     const bool mlp = b.learned == IDL_PROPOSAL_MLP, nrm = b.learned == IDL_PROPOSAL_NORM;
     nb[kBPGram] = mlp ? b.nsplit : 0;
+    nb[kBPGRed] = mlp ? cdiv(b.m2 * b.m2, prop::kThreads) : 0;
     nb[kBPChol] = mlp ? 3 : 0;
     nb[kBPFeat] = mlp ? cdiv(b.R, prop::kFeatCols) : 0;
     nb[kBPMlp] = mlp ? cdiv(b.R, prop::kTile) : 0;
@@ -722,6 +731,7 @@ static int run_proposal(idl_ctx* ctx, const BatchPlan& P, const BItem* d_items, 
   if (e == cudaSuccess) e = cudaFuncSetAttribute(b_papply_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_app);
   if (e != cudaSuccess) return cuda_check(ctx, e, "batch proposal attribute");
   BLAUNCH(b_pgram_kernel, kBPGram, prop::kThreads, sm_gram);
+  BLAUNCH(b_pgred_kernel, kBPGRed, prop::kThreads, 0);
   BLAUNCH(b_pchol_kernel, kBPChol, prop::kThreads, sm_chol);
   BLAUNCH(b_pfeat_kernel, kBPFeat, prop::kThreads, sm_feat);
   BLAUNCH(b_pmlp_kernel, kBPMlp, prop::kThreads, sm_mlp, ctx->mlp);
@@ -816,7 +826,7 @@ static int upload(idl_ctx* ctx, BatchPlan& P, unsigned char* ws, unsigned char* 
     fix(b.cursor); fix(b.nbig); fix(b.Om); fix(b.Bpl); fix(b.Y1); fix(b.part); fix(b.Y2); fix(b.rest); fix(b.Rinv);
     fix(b.diag); fix(b.flag); fix(b.Yf);
     if (b.learned) {
-      fix(b.Gp); fix(b.nmaxp); fix(b.scal); fix(b.Linv); fix(b.F); fix(b.sc); fix(b.V); fix(b.beta); fix(b.cand);
+      fix(b.Gp); fix(b.nmaxp); fix(b.scal); fix(b.Linv); fix(b.G); fix(b.F); fix(b.sc); fix(b.V); fix(b.beta); fix(b.cand);
       fix(b.outl); fix(b.rn);
       b.gate = b.flag;
     } else {

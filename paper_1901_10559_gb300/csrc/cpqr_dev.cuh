@@ -264,15 +264,17 @@ __device__ __forceinline__ void cpqr_cta_body(const T* __restrict__ Yin, T* __re
                                               double* __restrict__ diag, int* status, unsigned char* smem_raw,
                                               const int32_t* __restrict__ colmap, T* __restrict__ Vout,
                                               T* __restrict__ Bout) {
+  static_assert(sizeof(T) == 4, "the one-CTA variant orders FP32 norms by their bit patterns");
   constexpr int tpc = TPC;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, NW = blockDim.x >> 5;
   const int g = tid / tpc, gl = tid - g * tpc;
   const bool own = g < C;
   const int64_t scol = own ? (int64_t)colmap[g] : 0;
   T* vs = (T*)smem_raw;                                             // V*TPC: v, zero outside rows [t, m)
-  __shared__ T red_v[32];
-  __shared__ int red_i[32];
+  __shared__ unsigned red_k[32], red_i[32];
+  __shared__ int s_piv[128];                                        // pivots (subset indices), K <= 128
   __shared__ T s_beta;
+  for (int q = tid; q < K; q += blockDim.x) s_piv[q] = -1;
   T y[V];
 #pragma unroll
   for (int j = 0; j < V; ++j) {
@@ -292,32 +294,22 @@ __device__ __forceinline__ void cpqr_cta_body(const T* __restrict__ Yin, T* __re
   int tp = -1;
   T alpha_p = T(0);
   for (int t = 0; t < K; ++t) {
-    // A. warp candidates
-    T bv = (gl == 0 && nrm2 >= T(0)) ? nrm2 : T(-1);
-    int bi = (gl == 0 && nrm2 >= T(0)) ? g : -1;
-#pragma unroll
-    for (int o = 16; o; o >>= 1) {
-      const T ov = __shfl_xor_sync(0xffffffffu, bv, o);
-      const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-      if (better(ov, oi, bv, bi)) { bv = ov; bi = oi; }
-    }
-    if (lane == 0) { red_v[wid] = bv; red_i[wid] = bi; }
+    // A. warp candidates: the largest remaining norm (its FP32 bit pattern + 1;
+    // 0 marks a retired column or none), then the smallest index -- the same
+    // order as the cluster variant's comparison, by two warp reductions
+    const unsigned key = (gl == 0 && nrm2 >= T(0)) ? __float_as_uint((float)nrm2) + 1u : 0u;
+    const unsigned wk = __reduce_max_sync(0xffffffffu, key);
+    const unsigned wi = __reduce_min_sync(0xffffffffu, (key == wk && wk != 0u) ? (unsigned)g : 0xffffffffu);
+    if (lane == 0) { red_k[wid] = wk; red_i[wid] = wi; }
     __syncthreads();
     // B. block winner (every warp), reflection by the winner's group
-    bv = lane < NW ? red_v[lane] : T(-1);
-    bi = lane < NW ? red_i[lane] : -1;
-#pragma unroll
-    for (int o = 16; o; o >>= 1) {
-      const T ov = __shfl_xor_sync(0xffffffffu, bv, o);
-      const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-      if (better(ov, oi, bv, bi)) { bv = ov; bi = oi; }
-    }
-    const int p = bi;
+    const unsigned k2 = lane < NW ? red_k[lane] : 0u;
+    const unsigned bk = __reduce_max_sync(0xffffffffu, k2);
+    const unsigned i2 = (lane < NW && k2 == bk && bk != 0u) ? red_i[lane] : 0xffffffffu;
+    const unsigned bi = __reduce_min_sync(0xffffffffu, i2);
+    const int p = bk == 0u ? -1 : (int)bi;
     if (p < 0) {                                                     // no finite remaining column
-      if (tid == 0) {
-        for (int q = t; q < K; ++q) J[q] = -1;
-        set_status(status, IDL_EDATA);
-      }
+      if (tid == 0) set_status(status, IDL_EDATA);
       break;                                                         // uniform: every thread saw p < 0
     }
     const bool piv = own && g == p;
@@ -346,8 +338,8 @@ __device__ __forceinline__ void cpqr_cta_body(const T* __restrict__ Yin, T* __re
       }
       if (gl == 0) {
         s_beta = beta;
+        s_piv[t] = p;
         Bout[t] = beta;
-        J[t] = colmap[p];
         if (rnorm) rnorm[t] = (double)fabs(alpha);
         if (t == 0) diag[3] = (double)fabs(alpha);
         if (t == K - 1) diag[4] = (double)fabs(alpha);
@@ -393,6 +385,8 @@ __device__ __forceinline__ void cpqr_cta_body(const T* __restrict__ Yin, T* __re
   }
   r22 = warp_sum(r22);
   if (lane == 0 && r22 != 0.0) atomicAdd(&diag[0], r22);
+  __syncthreads();
+  for (int q = tid; q < K; q += blockDim.x) J[q] = s_piv[q] >= 0 ? colmap[s_piv[q]] : -1;
 }
 
 template <typename T, int V, int TPC>

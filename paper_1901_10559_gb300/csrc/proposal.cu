@@ -35,11 +35,16 @@ __global__ void __launch_bounds__(kThreads) prop_gram_kernel(const float* __rest
   gram_partial_block(Y, ld, m, R, blockIdx.x, Gp, nmaxp, smf);
 }
 
-__global__ void __launch_bounds__(kThreads) prop_chol_kernel(const float* __restrict__ Gp, int nsplit,
-                                                             const float* __restrict__ nmaxp, int m,
+__global__ void __launch_bounds__(kThreads) prop_gram_reduce_kernel(const float* __restrict__ Gp, int nsplit,
+                                                                    const float* __restrict__ nmaxp, int m,
+                                                                    float* __restrict__ G, float* __restrict__ scal) {
+  gram_reduce_elem(Gp, nsplit, nmaxp, m, blockIdx.x * blockDim.x + threadIdx.x, G, scal);
+}
+
+__global__ void __launch_bounds__(kThreads) prop_chol_kernel(const float* __restrict__ G, int m,
                                                              float* __restrict__ Linv, float* __restrict__ scal) {
   extern __shared__ __align__(16) float smf[];
-  chol_inv_block(Gp, nsplit, nmaxp, m, blockIdx.x, Linv, scal, smf);
+  chol_inv_block(G, m, blockIdx.x, Linv, scal, smf);
 }
 
 __global__ void __launch_bounds__(kThreads) prop_features_kernel(const float* __restrict__ Y, int ld, int m, int R,
@@ -167,18 +172,21 @@ static float* mlp_state(idl_ctx* ctx) {
 int launch_features(idl_ctx* ctx, const float* Y, int64_t m, int64_t R, int64_t ld, int64_t K, float* F) {
   if (m < 1 || m > kMaxM) return fail(ctx, IDL_ELIMIT, "proposal: needs 1 <= m <= 128");
   const int nsplit = (int)cdiv(R, kGramCols);
-  float* Gp = (float*)ws_get(ctx, kWsPropGram, sizeof(float) * ((size_t)nsplit * m * m + nsplit + 4 + 3 * m * m));
+  float* Gp = (float*)ws_get(ctx, kWsPropGram, sizeof(float) * ((size_t)nsplit * m * m + nsplit + 4 + 4 * m * m));
   if (!Gp) return IDL_ENOMEM;
   float* nmaxp = Gp + (size_t)nsplit * m * m;
   float* scal = nmaxp + nsplit;
   float* Linv = scal + 4;
+  float* G = Linv + 3 * m * m;
   const size_t sm_gram = sizeof(float) * 32 * round_up(m, 4);
   const size_t sm_chol = sizeof(float) * (2 * (size_t)m * (m + 1) + m);
   const size_t sm_feat = sizeof(float) * features_smem_floats((int)m);
   TRY(set_smem(ctx, (const void*)prop_chol_kernel, sm_chol));
   TRY(set_smem(ctx, (const void*)prop_features_kernel, sm_feat));
   prop_gram_kernel<<<nsplit, kThreads, sm_gram, ctx->stream>>>(Y, (int)ld, (int)m, (int)R, Gp, nmaxp), count_launch();
-  prop_chol_kernel<<<3, kThreads, sm_chol, ctx->stream>>>(Gp, nsplit, nmaxp, (int)m, Linv, scal), count_launch();
+  prop_gram_reduce_kernel<<<(unsigned)cdiv(m * m, kThreads), kThreads, 0, ctx->stream>>>(Gp, nsplit, nmaxp, (int)m, G,
+                                                                                       scal), count_launch();
+  prop_chol_kernel<<<3, kThreads, sm_chol, ctx->stream>>>(G, (int)m, Linv, scal), count_launch();
   prop_features_kernel<<<(unsigned)cdiv(R, kFeatCols), kThreads, sm_feat, ctx->stream>>>(Y, (int)ld, (int)m, (int)R,
                                                                                        (int)K, Linv, scal, F),
       count_launch();

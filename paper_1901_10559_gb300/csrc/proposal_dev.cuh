@@ -44,8 +44,8 @@ static_assert(kNParam == IDL_MLP_NPARAM, "parameter layout");
 
 constexpr int kMaxM = 128;         // sketch rows the proposal path handles
 constexpr int kThreads = 256;      // block size of every proposal kernel but the selection
-constexpr int kGramCols = 256;     // columns per Gram partial
-constexpr int kFeatCols = 128;     // columns per feature block
+constexpr int kGramCols = 64;      // columns per Gram partial
+constexpr int kFeatCols = 32;      // columns per feature block
 constexpr int kTile = 128;         // examples per MLP block
 constexpr int kLD = kTile + 1;     // odd leading dimension of the MLP's shared tiles
 constexpr int kSelThreads = 1024;
@@ -141,16 +141,32 @@ __device__ __forceinline__ void gram_partial_block(const float* __restrict__ Y, 
 }
 
 // ---------------------------------------------------------------------------
-// Cholesky factor of G + lambda_q I and its inverse (block q of three).
-// G = the sum of the nsplit partials in a fixed order (deterministic).
-// Writes Linv[q] (m x m row-major, lower triangular).  Block 0 also writes
-// scal[0] = max n_c, scal[1] = tr(G).  A zero (or non-finite) trace gives a
-// zero Linv, i.e. zero leverage features.
+// G = the sum of the nsplit Gram partials in a fixed order (deterministic), one
+// thread per entry; entry 0 also reduces the largest column norm into scal[0].
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void gram_reduce_elem(const float* __restrict__ Gp, int nsplit,
+                                                 const float* __restrict__ nmaxp, int m, int e, float* __restrict__ G,
+                                                 float* __restrict__ scal) {
+  if (e >= m * m) return;
+  float s = 0.f;
+  for (int p = 0; p < nsplit; ++p) s += Gp[(int64_t)p * m * m + e];
+  G[e] = s;
+  if (e == 0) {
+    float nm = 0.f;
+    for (int p = 0; p < nsplit; ++p) nm = fmaxf(nm, nmaxp[p]);
+    scal[0] = nm;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Cholesky factor of G + lambda_q I and its inverse (block q of three, 256
+// threads).  Reads the upper triangle of G (m x m row-major).  Writes Linv[q]
+// (m x m row-major, lower triangular); block 0 also writes scal[1] = tr(G).
+// A zero (or non-finite) trace gives a zero Linv, i.e. zero leverage features.
 // smem: 2 * m * (m + 1) + m floats.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void chol_inv_block(const float* __restrict__ Gp, int nsplit, const float* __restrict__ nmaxp,
-                                               int m, int q, float* __restrict__ Linv, float* __restrict__ scal,
-                                               float* smem) {
+__device__ __forceinline__ void chol_inv_block(const float* __restrict__ G, int m, int q, float* __restrict__ Linv,
+                                               float* __restrict__ scal, float* smem) {
   const int tid = threadIdx.x, nt = blockDim.x;
   const int ld = m + 1;
   float* M = smem;
@@ -160,10 +176,9 @@ __device__ __forceinline__ void chol_inv_block(const float* __restrict__ Gp, int
   for (int e = tid; e < m * m; e += nt) {
     const int i = e / m, j = e - i * m;
     if (i <= j) {
-      float s = 0.f;
-      for (int p = 0; p < nsplit; ++p) s += Gp[(int64_t)p * m * m + i * m + j];
-      M[i * ld + j] = s;
-      M[j * ld + i] = s;
+      const float v = G[e];
+      M[i * ld + j] = v;
+      M[j * ld + i] = v;
     }
   }
   __syncthreads();
@@ -171,12 +186,7 @@ __device__ __forceinline__ void chol_inv_block(const float* __restrict__ Gp, int
     float tr = 0.f;
     for (int i = 0; i < m; ++i) tr += M[i * ld + i];
     s_tr = tr;
-    if (q == 0) {
-      float nm = 0.f;
-      for (int p = 0; p < nsplit; ++p) nm = fmaxf(nm, nmaxp[p]);
-      scal[0] = nm;
-      scal[1] = tr;
-    }
+    if (q == 0) scal[1] = tr;
   }
   __syncthreads();
   const float tr = s_tr;
@@ -189,18 +199,14 @@ __device__ __forceinline__ void chol_inv_block(const float* __restrict__ Gp, int
   for (int i = tid; i < m; i += nt) M[i * ld + i] += lam;
   __syncthreads();
   // right-looking elimination on the lower triangle with the unscaled pivot
-  // column: M_ik -= M_ij M_kj / M_jj (j < k <= i); column j is not written in
-  // step j, so one barrier per step suffices
+  // column, M_ik -= M_ij M_kj / M_jj (j < k <= i), threads on a 16 x 16 grid of
+  // (i, k) residues; column j is not written in step j: one barrier per step
+  const int r0 = tid >> 4, c0 = tid & 15;
   for (int j = 0; j < m - 1; ++j) {
-    const float djj = fmaxf(M[j * ld + j], lam * 1e-6f);
-    const float rinv = 1.f / djj;
-    const int n = m - j - 1;
-    for (int e = tid; e < n * n; e += nt) {
-      const int a = e / n, b = e - a * n;
-      if (b <= a) {
-        const int i = j + 1 + a, k = j + 1 + b;
-        M[i * ld + k] = fmaf(-M[i * ld + j] * rinv, M[k * ld + j], M[i * ld + k]);
-      }
+    const float rinv = 1.f / fmaxf(M[j * ld + j], lam * 1e-6f);
+    for (int i = j + 1 + r0; i < m; i += 16) {
+      const float a = M[i * ld + j] * rinv;
+      for (int k = j + 1 + c0; k <= i; k += 16) M[i * ld + k] = fmaf(-a, M[k * ld + j], M[i * ld + k]);
     }
     __syncthreads();
   }
@@ -212,14 +218,20 @@ __device__ __forceinline__ void chol_inv_block(const float* __restrict__ Gp, int
   }
   for (int j = tid; j < m; j += nt) M[j * ld + j] = D[j];
   __syncthreads();
-  // X = L^{-1}: thread j forms column j by forward substitution; every thread
-  // walks the same rows so the reads of L are broadcasts
+  // X = L^{-1}: thread j forms column j by forward substitution (four partial sums)
   for (int j = tid; j < m; j += nt) {
-    for (int i = 0; i < m; ++i) {
-      if (i < j) { X[i * ld + j] = 0.f; continue; }
-      float acc = (i == j) ? 1.f : 0.f;
-      for (int k = j; k < i; ++k) acc = fmaf(-M[i * ld + k], X[k * ld + j], acc);
-      X[i * ld + j] = acc / M[i * ld + i];
+    for (int i = 0; i < j; ++i) X[i * ld + j] = 0.f;
+    for (int i = j; i < m; ++i) {
+      float a0 = (i == j) ? 1.f : 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+      int k = j;
+      for (; k + 3 < i; k += 4) {
+        a0 = fmaf(-M[i * ld + k], X[k * ld + j], a0);
+        a1 = fmaf(-M[i * ld + k + 1], X[(k + 1) * ld + j], a1);
+        a2 = fmaf(-M[i * ld + k + 2], X[(k + 2) * ld + j], a2);
+        a3 = fmaf(-M[i * ld + k + 3], X[(k + 3) * ld + j], a3);
+      }
+      for (; k < i; ++k) a0 = fmaf(-M[i * ld + k], X[k * ld + j], a0);
+      X[i * ld + j] = ((a0 + a1) + (a2 + a3)) / M[i * ld + i];
     }
   }
   __syncthreads();
@@ -230,11 +242,15 @@ __device__ __forceinline__ void chol_inv_block(const float* __restrict__ Gp, int
 }
 
 // ---------------------------------------------------------------------------
-// Features of columns [blk*128, blk*128 + 128): F row-major R x 8 (FP32).
-// smem: m * (m + 1) + kFeatCols * (m + 3) floats.
+// Features of columns [blk*32, blk*32 + 32): F row-major R x 8 (FP32).
+// The leverage scores ||L_q^{-1} y_c||^2 come from W = L_q^{-1} Y_blk, a
+// register-tiled product: thread (ti, tc) of a 32 x 8 grid owns rows ti + 32 u
+// and columns tc + 8 v; partial column sums of W^2 meet in shared memory.
+// Small column blocks keep many blocks in flight (the kernel is latency-bound
+// for the sketch sizes of the QR stage).  smem: features_smem_floats(m).
 // ---------------------------------------------------------------------------
 __host__ __device__ constexpr size_t features_smem_floats(int m) {
-  return (size_t)m * (m + 1) + (size_t)kFeatCols * (m + 3);
+  return (size_t)m * (m + 1) + (size_t)kFeatCols * (m + 1) + 32 * (size_t)kFeatCols + 3 * (size_t)kFeatCols;
 }
 
 __device__ __forceinline__ void features_block(const float* __restrict__ Y, int ld, int m, int R, int K,
@@ -243,15 +259,16 @@ __device__ __forceinline__ void features_block(const float* __restrict__ Y, int 
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
   const int lds = m + 1;
   float* Ls = smem;                                    // m x (m+1)
-  float* Yc = Ls + m * lds;                            // kFeatCols x m
-  float* Lev = Yc + kFeatCols * m;                     // kFeatCols x 3
+  float* Yc = Ls + m * lds;                            // kFeatCols x (m+1)
+  float* part = Yc + kFeatCols * lds;                  // 32 x kFeatCols
+  float* Lev = part + 32 * kFeatCols;                  // kFeatCols x 3
   const int c0 = blk * kFeatCols;
   const int nc = min(kFeatCols, R - c0);
-  for (int e = tid; e < nc * m; e += blockDim.x) {
+  for (int e = tid; e < kFeatCols * m; e += blockDim.x) {
     const int c = e / m, i = e - c * m;
-    Yc[e] = Y[(int64_t)(c0 + c) * ld + i];
+    Yc[c * lds + i] = c < nc ? Y[(int64_t)(c0 + c) * ld + i] : 0.f;
   }
-  const float nmax = scal[0];
+  const int ti = tid >> 3, tc = tid & 7;
   for (int q = 0; q < 3; ++q) {
     __syncthreads();
     for (int e = tid; e < m * m; e += blockDim.x) {
@@ -259,25 +276,43 @@ __device__ __forceinline__ void features_block(const float* __restrict__ Y, int 
       Ls[i * lds + j] = Linv[(int64_t)q * m * m + e];
     }
     __syncthreads();
-    for (int c = wid; c < nc; c += nw) {
-      const float* y = Yc + c * m;
-      float s = 0.f;
+    float acc[kMaxM / 32][4];
 #pragma unroll
-      for (int r = 0; r < kMaxM / 32; ++r) {
-        const int i = lane + 32 * r;
+    for (int u = 0; u < kMaxM / 32; ++u)
+#pragma unroll
+      for (int v = 0; v < 4; ++v) acc[u][v] = 0.f;
+    for (int k = 0; k < m; ++k) {
+      float b[4];
+#pragma unroll
+      for (int v = 0; v < 4; ++v) b[v] = Yc[(tc + 8 * v) * lds + k];
+#pragma unroll
+      for (int u = 0; u < kMaxM / 32; ++u) {
+        const int i = ti + 32 * u;
         if (i < m) {
-          float w = 0.f;
-          for (int k = 0; k <= i; ++k) w = fmaf(Ls[i * lds + k], y[k], w);
-          s = fmaf(w, w, s);
+          const float a = Ls[i * lds + k];
+#pragma unroll
+          for (int v = 0; v < 4; ++v) acc[u][v] = fmaf(a, b[v], acc[u][v]);
         }
       }
-      s = warp_sum(s);
-      if (lane == 0) Lev[c * 3 + q] = s;
+    }
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      float sq = 0.f;
+#pragma unroll
+      for (int u = 0; u < kMaxM / 32; ++u) sq = fmaf(acc[u][v], acc[u][v], sq);
+      part[ti * kFeatCols + tc + 8 * v] = sq;
+    }
+    __syncthreads();
+    for (int c = tid; c < kFeatCols; c += blockDim.x) {
+      float sq = 0.f;
+      for (int r = 0; r < 32; ++r) sq += part[r * kFeatCols + c];
+      Lev[c * 3 + q] = sq;
     }
   }
   __syncthreads();
+  const float nmax = scal[0];
   for (int c = wid; c < nc; c += nw) {
-    const float* y = Yc + c * m;
+    const float* y = Yc + c * lds;
     float n2 = 0.f, am = 0.f;
     for (int i = lane; i < m; i += 32) {
       n2 = fmaf(y[i], y[i], n2);
@@ -592,14 +627,29 @@ __device__ __forceinline__ void select_block(const float* __restrict__ scores, i
       if ((k & mask) == prefix) atomicAdd(&hist[(k >> shift) & 255], 1);
     }
     __syncthreads();
-    if (tid == 0) {
-      int cum = 0, sel = 0;
-      for (int b = 255; b >= 0; --b) {
-        if (cum + hist[b] >= need) { sel = b; break; }
-        cum += hist[b];
+    if (tid < 32) {
+      // lane l holds bins 255 - 8 l - q (q < 8), i.e. the bins in descending order
+      int cnt[8], sum = 0;
+#pragma unroll
+      for (int q = 0; q < 8; ++q) { cnt[q] = hist[255 - (tid * 8 + q)]; sum += cnt[q]; }
+      int incl = sum;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (tid >= o) incl += y;
       }
-      s_prefix = prefix | ((uint32_t)sel << shift);
-      s_need = need - cum;
+      const int excl = incl - sum;
+      const unsigned hit = __ballot_sync(0xffffffffu, excl < need && incl >= need);
+      if (tid == __ffs(hit) - 1) {
+        int cum = excl, sel = 0;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          if (cum + cnt[q] >= need) { sel = 255 - (tid * 8 + q); break; }
+          cum += cnt[q];
+        }
+        s_prefix = prefix | ((uint32_t)sel << shift);
+        s_need = need - cum;
+      }
     }
     __syncthreads();
     prefix = s_prefix;
