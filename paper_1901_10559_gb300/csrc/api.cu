@@ -210,6 +210,7 @@ extern "C" int idl_destroy(idl_ctx* ctx) {
   for (auto& pp : ctx->prof) { cudaEventDestroy(pp.a); cudaEventDestroy(pp.b); }
   idl_batch_state_free(ctx->batch);
   if (ctx->mlp) cudaFree(ctx->mlp);
+  if (ctx->ts_tw) cudaFree(ctx->ts_tw);
   cudaFree(ctx->d_status);
   cudaFree(ctx->d_diag);
   delete ctx;

@@ -167,13 +167,14 @@ __global__ void __launch_bounds__(512) b_sketch_dense_kernel(const BItem* __rest
     cs_dense_block<float, false>(it.A, it.lda, it.R, it.s, it.ptr, it.rows, it.Y1, it.ldy1, b, tile);
 }
 
-__global__ void __launch_bounds__(kTsThreads, 1) b_sketch_cp_kernel(const BItem* __restrict__ items,
-                                                                    const int64_t* __restrict__ pre, int n) {
+__global__ void __launch_bounds__(kTsMaxThreads, 1) b_sketch_cp_kernel(const BItem* __restrict__ items,
+                                                                    const int64_t* __restrict__ pre, int n,
+                                                                    const float2* __restrict__ tw) {
   extern __shared__ __align__(16) float2 sm2[];
   ITEM_OF_BLOCK(pre, n);
   int logL = 0;
   while ((1LL << logL) < it.m1) ++logL;
-  tensorsketch_block(it.ts, it.R, (int)it.m1, logL, it.lam, it.Y1, it.ldy1, local * 2, sm2);
+  tensorsketch_block(it.ts, it.R, (int)it.m1, logL, it.lam, it.Y1, it.ldy1, local * 2, tw, sm2);
 }
 
 template <int NP>
@@ -765,10 +766,10 @@ static int run_stages(idl_ctx* ctx, const BatchPlan& P, const BItem* d_items, co
   BLAUNCH(b_sketch_dense_kernel, kBSketchD, sketch_threads, 0);
   if (timed) cudaEventRecord(ev[1], ctx->stream);
   if (P.pre[kBSketchT][n] > 0) {
-    const size_t smem = sizeof(float2) * (size_t)(2 * P.maxL_cp + 2 * (P.maxL_cp / 2 + 1));
+    const size_t smem = ts_smem_bytes(P.maxL_cp);
     cudaError_t e = cudaFuncSetAttribute(b_sketch_cp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return cuda_check(ctx, e, "batch tensorsketch attribute");
-    BLAUNCH(b_sketch_cp_kernel, kBSketchT, kTsThreads, smem);
+    BLAUNCH(b_sketch_cp_kernel, kBSketchT, ts_threads(P.maxL_cp), smem, (const float2*)ctx->ts_tw);
   }
   BTRY(launch_check(ctx, "batch sketch"));
   if (timed) cudaEventRecord(ev[2], ctx->stream);
@@ -858,6 +859,7 @@ extern "C" int idl_batch_run(idl_ctx* ctx, const idl_batch_item* items, int n) {
   Tune tn = known ? bs->tune[key] : Tune();
   BatchPlan P;
   BTRY(plan_batch(ctx, items, n, tn, P));
+  if (!P.cp_list.empty() && !ts_twiddles(ctx)) return IDL_ENOMEM;    // built before any capture
   unsigned char* ws = (unsigned char*)ws_get(ctx, kWsBatch, P.ws_bytes);
   unsigned char* tab = (unsigned char*)ws_get(ctx, kWsBatchTab, P.table_bytes);
   if (!ws || !tab) return IDL_ENOMEM;
@@ -991,6 +993,7 @@ extern "C" int idl_debug_batch_timing(idl_ctx* ctx, const idl_batch_item* items,
   Tune tn = bs->tune.count(key) ? bs->tune[key] : Tune();
   BatchPlan P;
   BTRY(plan_batch(ctx, items, n, tn, P));
+  if (!P.cp_list.empty() && !ts_twiddles(ctx)) return IDL_ENOMEM;    // built before any capture
   unsigned char* ws = (unsigned char*)ws_get(ctx, kWsBatch, P.ws_bytes);
   unsigned char* tab = (unsigned char*)ws_get(ctx, kWsBatchTab, P.table_bytes);
   if (!ws || !tab) return IDL_ENOMEM;

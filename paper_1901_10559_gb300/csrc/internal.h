@@ -30,6 +30,7 @@ struct idl_ctx {
   idl_batch_state* batch = nullptr;   // batch graphs and tuning table
   int batch_no_graph = 0;      // 1: run batches without graph capture (tests)
   int batch_no_tune = 0;       // 1: skip the first-call tuning runs (tests)           // 1: Gaussian stage on CUDA cores instead of tcgen05 (comparison / tests)
+  void* ts_tw = nullptr;       // FFT twiddle table of the TensorSketch kernels (built on first use)
   float* mlp = nullptr;        // proposal MLP: FP32 master weights | Adam first moments | second moments
   bool mlp_ready = false;
   long long mlp_step = 0;      // Adam steps taken since the weights were set
@@ -120,6 +121,7 @@ int launch_proposal_qr(idl_ctx* ctx, const float* Y2, float* Yf, int64_t m, int6
                        int mode, int cand_factor, int32_t* J);
 
 // tensorsketch.cu
+const float2* ts_twiddles(idl_ctx* ctx);
 int launch_tensorsketch(idl_ctx* ctx, int N, const int64_t* dims, int64_t R, const void* const* factors,
                         const int64_t* ldf, const double* lambda, const int32_t* const* hs,
                         const int8_t* const* ss, int64_t L, float* Y, int64_t ldy);

@@ -3,18 +3,12 @@
 // (Sec. 1.3, Eq. TA-formula; Algorithm 3 line 5):
 //   Y[:, r] = lambda_r * IFFT( prod_n FFT( S^(n) a^(n)_r ) ).
 //
-// One block per pair of columns (r, r+1), everything in shared memory:
-//   * per mode n, the two columns' CountSketches are packed as the real and
-//     imaginary parts of one complex length-L vector z (scatter with shared
-//     atomics into bit-reversed positions), transformed by one in-place radix-2
-//     FFT, and separated by Hermitian symmetry:
-//        C_r[f] = (Z[f] + conj Z[-f]) / 2,   C_{r+1}[f] = (Z[f] - conj Z[-f]) / 2i;
-//   * the spectra are multiplied into P_r, P_{r+1} (f = 0..L/2; the rest is
-//     the conjugate mirror of a real signal's spectrum);
-//   * one inverse FFT of P_r + i P_{r+1} gives both real columns at once.
-// N modes cost N + 1 complex FFTs per pair of columns.  Twiddles are stored per
-// stage (stage with half-length h at offset h) so a stage reads them with
-// unit stride.  FP32 arithmetic.
+// One block per pair of columns (r, r+1): the two columns' CountSketches of
+// each mode are packed into one complex vector, transformed by a register-
+// blocked Stockham FFT (radix 16), separated by Hermitian symmetry and
+// multiplied into the running spectra; one inverse FFT gives both columns
+// (tsketch_dev.cuh).  N modes cost N + 1 complex FFTs per pair of columns.
+// FP32 arithmetic.
 #include <cuda_runtime.h>
 
 #include "common.cuh"
@@ -23,11 +17,33 @@
 
 namespace idl {
 
-__global__ void __launch_bounds__(kTsThreads, 1) tensorsketch_kernel(TsArgs a, int64_t R, int L, int logL,
+__global__ void __launch_bounds__(kTsMaxThreads, 1) tensorsketch_kernel(const __grid_constant__ TsArgs a, int64_t R, int L, int logL,
                                                                      const double* __restrict__ lambda,
-                                                                     float* __restrict__ Y, int64_t ldy) {
+                                                                     float* __restrict__ Y, int64_t ldy,
+                                                                     const float2* __restrict__ tw) {
   extern __shared__ __align__(16) float2 sm[];
-  tensorsketch_block(a, R, L, logL, lambda, Y, ldy, (int64_t)blockIdx.x * 2, sm);
+  tensorsketch_block(a, R, L, logL, lambda, Y, ldy, (int64_t)blockIdx.x * 2, tw, sm);
+}
+
+__global__ void ts_twiddle_kernel(float2* tw) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < kTsTwEntries) ts::twiddle_entry(e, tw);
+}
+
+// The FFT twiddle table of the context (built once, on the context's stream).
+const float2* ts_twiddles(idl_ctx* ctx) {
+  if (!ctx->ts_tw) {
+    void* p = nullptr;
+    if (cudaMalloc(&p, sizeof(float2) * kTsTwEntries) != cudaSuccess) {
+      (void)cudaGetLastError();
+      ctx->err = "twiddle table allocation failed";
+      return nullptr;
+    }
+    ts_twiddle_kernel<<<(unsigned)cdiv(kTsTwEntries, 256), 256, 0, ctx->stream>>>((float2*)p), idl::count_launch();
+    if (cudaGetLastError() != cudaSuccess) { cudaFree(p); ctx->err = "twiddle table build failed"; return nullptr; }
+    ctx->ts_tw = p;
+  }
+  return (const float2*)ctx->ts_tw;
 }
 
 int launch_tensorsketch(idl_ctx* ctx, int N, const int64_t* dims, int64_t R, const void* const* factors,
@@ -46,10 +62,13 @@ int launch_tensorsketch(idl_ctx* ctx, int N, const int64_t* dims, int64_t R, con
   }
   int logL = 0;
   while ((1LL << logL) < L) ++logL;
-  const size_t smem = sizeof(float2) * (size_t)(2 * L + 2 * (L / 2 + 1));
+  const size_t smem = ts_smem_bytes((int)L);
   cudaError_t e = cudaFuncSetAttribute(tensorsketch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return cuda_check(ctx, e, "tensorsketch attribute");
-  tensorsketch_kernel<<<(unsigned)cdiv(R, 2), kTsThreads, smem, ctx->stream>>>(a, R, (int)L, logL, lambda, Y, ldy), idl::count_launch();
+  const float2* tw = ts_twiddles(ctx);
+  if (!tw) return IDL_ENOMEM;
+  tensorsketch_kernel<<<(unsigned)cdiv(R, 2), ts_threads((int)L), smem, ctx->stream>>>(a, R, (int)L, logL, lambda, Y,
+                                                                                      ldy, tw), idl::count_launch();
   return cuda_check(ctx, cudaGetLastError(), "tensorsketch");
 }
 

@@ -222,7 +222,8 @@ def test_cpqr_exact_rank_and_ties(ctx):
 
 # ------------------------------------------------------------------ a5 TensorSketch + a9 lambda_hat
 @pytest.mark.parametrize("dims,R,L", [((1000, 1000, 1000), 100, 8192), ((6, 5, 4), 5, 16), ((200,) * 4, 51, 1024),
-                                      ((37, 41), 10, 64)])
+                                      ((37, 41), 10, 64), ((30, 20, 10), 7, 2048), ((9, 9), 4, 32),
+                                      ((50, 40), 9, 256)])
 def test_tensorsketch_parity(ctx, dims, R, L):
     facs, lam = cp_factors(dims, R, seed=len(dims) + R)
     hs, ss = odr.tensorsketch_maps(4, dims, L)
