@@ -26,6 +26,60 @@ __device__ __forceinline__ double group_sum(double v, int tpc) {
   return v;
 }
 
+// The Householder vector in shared memory is stored by thread slot: row
+// i = gl + TPC j (gl: lane within the column's group) at vslot(i) = gl V + j,
+// so that each thread's V values are contiguous and read as 16-byte vectors
+// (V is a multiple of 4 in every compiled variant).
+template <int V, int TPC>
+__device__ __forceinline__ int vslot(int i) { return (i % TPC) * V + i / TPC; }
+
+// sum_j v_j y_j over a thread's rows (four partial sums)
+template <typename T, int V>
+__device__ __forceinline__ T house_dot(const T* __restrict__ vrow, const T (&y)[V]) {
+  static_assert(V % 4 == 0, "V must be a multiple of 4");
+  T d0 = T(0), d1 = T(0), d2 = T(0), d3 = T(0);
+#pragma unroll
+  for (int j = 0; j < V; j += 4) {
+    if constexpr (sizeof(T) == 4) {
+      const float4 w = *reinterpret_cast<const float4*>(vrow + j);
+      d0 = fma(w.x, y[j], d0); d1 = fma(w.y, y[j + 1], d1); d2 = fma(w.z, y[j + 2], d2); d3 = fma(w.w, y[j + 3], d3);
+    } else {
+      const double2 a = *reinterpret_cast<const double2*>(vrow + j);
+      const double2 b = *reinterpret_cast<const double2*>(vrow + j + 2);
+      d0 = fma(a.x, y[j], d0); d1 = fma(a.y, y[j + 1], d1); d2 = fma(b.x, y[j + 2], d2); d3 = fma(b.y, y[j + 3], d3);
+    }
+  }
+  return (d0 + d1) + (d2 + d3);
+}
+
+// y -= d v over a thread's rows; returns the thread's part of the trailing
+// norm^2 over rows with slot index j >= jt (four partial sums)
+template <typename T, int V>
+__device__ __forceinline__ T house_update(const T* __restrict__ vrow, T (&y)[V], T d, int jt) {
+  T s0 = T(0), s1 = T(0), s2 = T(0), s3 = T(0);
+#pragma unroll
+  for (int j = 0; j < V; j += 4) {
+    T w0, w1, w2, w3;
+    if constexpr (sizeof(T) == 4) {
+      const float4 w = *reinterpret_cast<const float4*>(vrow + j);
+      w0 = w.x; w1 = w.y; w2 = w.z; w3 = w.w;
+    } else {
+      const double2 a = *reinterpret_cast<const double2*>(vrow + j);
+      const double2 b = *reinterpret_cast<const double2*>(vrow + j + 2);
+      w0 = a.x; w1 = a.y; w2 = b.x; w3 = b.y;
+    }
+    y[j] = fma(-d, w0, y[j]);
+    y[j + 1] = fma(-d, w1, y[j + 1]);
+    y[j + 2] = fma(-d, w2, y[j + 2]);
+    y[j + 3] = fma(-d, w3, y[j + 3]);
+    s0 += (j >= jt) ? y[j] * y[j] : T(0);
+    s1 += (j + 1 >= jt) ? y[j + 1] * y[j + 1] : T(0);
+    s2 += (j + 2 >= jt) ? y[j + 2] * y[j + 2] : T(0);
+    s3 += (j + 3 >= jt) ? y[j + 3] * y[j + 3] : T(0);
+  }
+  return (s0 + s1) + (s2 + s3);
+}
+
 // ----------------------------------------------------------------------------
 // Register-resident variant (used whenever a cluster shape fits).  Each group
 // of TPC lanes keeps one column in registers (rows gl, gl + TPC, ...).  Per
@@ -76,8 +130,9 @@ __device__ __forceinline__ void cpqr_reg_body(const T* __restrict__ Yin, T* __re
   const int col = c0 + g;
   const int64_t scol = own ? (colmap ? (int64_t)colmap[col] : (int64_t)col) : 0;   // column of Yin / Yout
 
-  T* stage = (T*)smem_raw;                                          // [2][m] staged candidate column
-  T* vs = stage + 2 * m;                                            // V*TPC: v, zero outside rows [t, m)
+  T* vs = (T*)smem_raw;                                             // V*TPC: v by thread slot, zero outside rows [t, m)
+                                                                    // (first: 16-byte aligned vector reads)
+  T* stage = vs + V * TPC;                                          // [2][m] staged candidate column
   Cand<T>* cand = (Cand<T>*)(smem_raw + round_up((int64_t)sizeof(T) * (2 * m + V * TPC), 16));   // [2]
   __shared__ T red_v[32];
   __shared__ int red_i[32];
@@ -166,12 +221,12 @@ __device__ __forceinline__ void cpqr_reg_body(const T* __restrict__ Yin, T* __re
         }
       } else {
         const int w = ix / nc;
-        if (lane == 0 && t > 0) vs[t - 1] = T(0);                    // rows above t stay zero
+        if (lane == 0 && t > 0) vs[vslot<V, TPC>(t - 1)] = T(0);     // rows above t stay zero
         const T* rm = cluster.map_shared_rank(stage + (t & 1) * m, (unsigned)w);
         T xs = T(0), x0 = T(0);
         for (int i = t + lane; i < m; i += 32) {
           const T x = rm[i];
-          vs[i] = x;
+          vs[vslot<V, TPC>(i)] = x;
           xs += x * x;
           if (i == t) x0 = x;
           if (Vout && rank == 0) Vout[(int64_t)t * m + i] = x;
@@ -184,7 +239,7 @@ __device__ __forceinline__ void cpqr_reg_body(const T* __restrict__ Yin, T* __re
         const T alpha = (x0 >= T(0)) ? -nrm : nrm;
         const T beta = (nrm > T(0)) ? T(1) / (nrm * (nrm + fabs(x0))) : T(0);
         if (lane == 0) {
-          vs[t] = x0 - alpha;
+          vs[vslot<V, TPC>(t)] = x0 - alpha;
           s_alpha = alpha;
           s_beta = beta;
           s_p = ix;
@@ -207,25 +262,13 @@ __device__ __forceinline__ void cpqr_reg_body(const T* __restrict__ Yin, T* __re
     const bool upd = act && !piv;
     if (piv) { nrm2 = T(-1); tp = t; alpha_p = s_alpha; }
     // vs is zero outside rows [t, m): no per-row predicates in the dot product and the update
-    T d0 = T(0), d1 = T(0);
-#pragma unroll
-    for (int j = 0; j < V; j += 2) {
-      d0 = fma(vs[gl + tpc * j], y[j], d0);
-      if (j + 1 < V) d1 = fma(vs[gl + tpc * (j + 1)], y[j + 1], d1);
-    }
-    T d = group_sum(d0 + d1, tpc) * beta;
+    const T* vrow = vs + gl * V;
+    T d = group_sum(house_dot<T, V>(vrow, y), tpc) * beta;
     if (!upd) d = T(0);
     __syncwarp();   // re-read v below instead of keeping all of it in registers
     // trailing norm over rows > t: rows gl + tpc*j with j >= jt
     const int jt = (t - gl) >= 0 ? (t - gl) / tpc + 1 : 0;
-    T s0 = T(0), s1 = T(0);
-#pragma unroll
-    for (int j = 0; j < V; ++j) {
-      y[j] = fma(-d, vs[gl + tpc * j], y[j]);
-      const T q = (j >= jt) ? y[j] * y[j] : T(0);
-      if (j & 1) s1 += q; else s0 += q;
-    }
-    const T s2 = group_sum(s0 + s1, tpc);
+    const T s2 = group_sum(house_update<T, V>(vrow, y, d, jt), tpc);
     if (upd) nrm2 = s2;
   }
   cluster.sync();                 // no CTA reads another's staging slot after this point
@@ -270,7 +313,7 @@ __device__ __forceinline__ void cpqr_cta_body(const T* __restrict__ Yin, T* __re
   const int g = tid / tpc, gl = tid - g * tpc;
   const bool own = g < C;
   const int64_t scol = own ? (int64_t)colmap[g] : 0;
-  T* vs = (T*)smem_raw;                                             // V*TPC: v, zero outside rows [t, m)
+  T* vs = (T*)smem_raw;                                             // V*TPC: v by thread slot, zero outside rows [t, m)
   __shared__ unsigned red_k[32], red_i[32];
   __shared__ int s_piv[128];                                        // pivots (subset indices), K <= 128
   __shared__ T s_beta;
@@ -333,7 +376,7 @@ __device__ __forceinline__ void cpqr_cta_body(const T* __restrict__ Yin, T* __re
       for (int j = 0; j < V; ++j) {
         const int i = gl + tpc * j;
         const T v = (i < t || i >= m) ? T(0) : (i == t ? x0 - alpha : y[j]);
-        vs[i] = v;
+        vs[gl * V + j] = v;
         if (i < m) Vout[(int64_t)t * m + i] = v;
       }
       if (gl == 0) {
@@ -353,23 +396,11 @@ __device__ __forceinline__ void cpqr_cta_body(const T* __restrict__ Yin, T* __re
     // C. apply to the remaining columns
     const T beta = s_beta;
     const bool upd = own && nrm2 >= T(0);
-    T d0 = T(0), d1 = T(0);
-#pragma unroll
-    for (int j = 0; j < V; j += 2) {
-      d0 = fma(vs[gl + tpc * j], y[j], d0);
-      if (j + 1 < V) d1 = fma(vs[gl + tpc * (j + 1)], y[j + 1], d1);
-    }
-    T d = group_sum(d0 + d1, tpc) * beta;
+    const T* vrow = vs + gl * V;
+    T d = group_sum(house_dot<T, V>(vrow, y), tpc) * beta;
     if (!upd) d = T(0);
     const int jt = (t - gl) >= 0 ? (t - gl) / tpc + 1 : 0;
-    T s0 = T(0), s1 = T(0);
-#pragma unroll
-    for (int j = 0; j < V; ++j) {
-      y[j] = fma(-d, vs[gl + tpc * j], y[j]);
-      const T q = (j >= jt) ? y[j] * y[j] : T(0);
-      if (j & 1) s1 += q; else s0 += q;
-    }
-    const T s2 = group_sum(s0 + s1, tpc);
+    const T s2 = group_sum(house_update<T, V>(vrow, y, d, jt), tpc);
     if (upd) nrm2 = s2;
   }
   double r22 = 0.0;

@@ -25,17 +25,21 @@ constexpr int kSolveMaxK = 128;
 // inv(R11) in FP64, R11 = rows 0..K-1 of the pivot columns in pivot order
 // (upper triangular).  One warp per column j of the inverse: column-oriented
 // back substitution of R11 x = e_j (x_i = b_i / u_ii, then b_k -= u_ki x_i for
-// k < i, lanes over k).  Output Rinv: K x K row-major, zero below the diagonal.
+// k < i, lanes over k), with the K reciprocals 1/u_ii formed once.  Launched
+// with one warp per block so that the columns spread over the SMs' FP64
+// units.  Output Rinv: K x K row-major, zero below the diagonal.
 template <typename T>
 __device__ __forceinline__ void rinv_block(const T* __restrict__ Y, int ld, int K, int R, const int32_t* __restrict__ J,
                                           double* __restrict__ Rinv, int blk, int nblk, double* U) {
-  // U: K x (K+1) doubles of shared memory
+  // U: K x (K+1) doubles of shared memory; its column K holds 1/u_ii
   const int KP = K + 1;
   for (int e = threadIdx.x; e < K * K; e += blockDim.x) {
     const int j = e / K, i = e - j * K;                              // column j (pivot j), row i
     const int jj = J[j];
     U[i * KP + j] = (i <= j && jj >= 0 && jj < R) ? (double)Y[(int64_t)jj * ld + i] : 0.0;
   }
+  __syncthreads();
+  for (int i = threadIdx.x; i < K; i += blockDim.x) U[i * KP + K] = 1.0 / U[i * KP + i];
   __syncthreads();
   const int lane = threadIdx.x & 31;
   const int nw = blockDim.x >> 5;
@@ -51,7 +55,7 @@ __device__ __forceinline__ void rinv_block(const T* __restrict__ Y, int ld, int 
       for (int qq = 0; qq < kSolveMaxK / 32; ++qq)
         if (qq == q) bi = b[qq];
       bi = __shfl_sync(0xffffffffu, bi, i & 31);
-      const double xi = bi / U[i * KP + i];
+      const double xi = bi * U[i * KP + K];
 #pragma unroll
       for (int qq = 0; qq < kSolveMaxK / 32; ++qq) {
         const int k = lane + 32 * qq;
@@ -71,6 +75,51 @@ __device__ __forceinline__ void rinv_block(const T* __restrict__ Y, int ld, int 
 // 64 columns; inv(R11) and the block's R12 rows sit in shared memory; every
 // thread forms whole dot products (no sequential dependence between outputs).
 constexpr int kTNB = 64;
+// FP32 sketches: R12 holds FP32 values, so T = inv(R11) R12 is accumulated
+// in double-float arithmetic on the FP32 pipes: inv(R11) = a_hi + a_lo
+// (two floats), a_hi b exactly by an FMA (p + e), a_lo b rounded, sums by
+// TwoSum (Knuth) into a (hi, lo) pair -- about 48 significant bits, far
+// below the FP32 sketch's own rounding, at a fraction of the FP64 pipes' cost.
+__device__ __forceinline__ void tgemm_block_df(const float* __restrict__ Y, int ld, int K, int R,
+                                              const double* __restrict__ Rinv, const int32_t* __restrict__ rest,
+                                              int nrest, double* __restrict__ Tout, int blk, float* sh) {
+  float* Ah = sh;                          // K x K
+  float* Al = Ah + K * K;                  // K x K
+  float* B = Al + K * K;                   // K x (kTNB + 1)
+  const int BP = kTNB + 1;
+  for (int e = threadIdx.x; e < K * K; e += blockDim.x) {
+    const double a = Rinv[e];
+    const float h = (float)a;
+    Ah[e] = h;
+    Al[e] = (float)(a - (double)h);
+  }
+  const int cb = blk * kTNB;
+  for (int e = threadIdx.x; e < K * kTNB; e += blockDim.x) {
+    const int cc = e / K, i = e - cc * K;
+    const int c = cb + cc;
+    const int r = (c < nrest) ? rest[c] : -1;
+    B[i * BP + cc] = (r >= 0 && r < R) ? Y[(int64_t)r * ld + i] : 0.f;
+  }
+  __syncthreads();
+  const int cc = threadIdx.x & (kTNB - 1);
+  const int c = cb + cc;
+  for (int i = threadIdx.x >> 6; i < K; i += blockDim.x >> 6) {
+    float sh_ = 0.f, sl = 0.f;
+    for (int k = i; k < K; ++k) {
+      const float ah = Ah[i * K + k], al = Al[i * K + k], b = B[k * BP + cc];
+      const float p = ah * b;
+      const float e = fmaf(ah, b, -p);                 // ah b = p + e exactly
+      const float q = fmaf(al, b, e);
+      const float t = sh_ + p;                         // TwoSum(sh_, p)
+      const float bp = t - sh_;
+      const float err = (sh_ - (t - bp)) + (p - bp);
+      sh_ = t;
+      sl += err + q;
+    }
+    if (c < nrest) Tout[(int64_t)i * nrest + c] = (double)sh_ + (double)sl;
+  }
+}
+
 template <typename T>
 __device__ __forceinline__ void tgemm_block(const T* __restrict__ Y, int ld, int K, int R,
                                            const double* __restrict__ Rinv, const int32_t* __restrict__ rest,

@@ -207,6 +207,37 @@ def test_cpqr_and_t_parity(ctx, dtype, m, R, K):
     assert ctx.sync() == idl.IDL_OK
 
 
+@pytest.mark.parametrize("dtype,K,R", [("f32", 50, 3000), ("f32", 128, 700), ("f64", 40, 500), ("f32", 3, 5)])
+def test_t_solve_from_factored_sketch(ctx, dtype, K, R):
+    """T = R11^{-1} R12 from a given factored sketch equals the FP64 back
+    substitution of the oracle on the same stored values: the FP32 path
+    accumulates in double-float arithmetic (about 48 bits), so the gate is
+    1e-11 relative to |R11^{-1}| |R12| (FP64 data: 1e-13)."""
+    rng = np.random.default_rng(K + R)
+    npdt = np.float32 if dtype == "f32" else np.float64
+    m = K + 7
+    J = rng.permutation(R)[:K].astype(np.int32)
+    U = np.triu(rng.standard_normal((K, K))) + np.diag(rng.uniform(2.0, 4.0, K) * rng.choice([-1, 1], K))
+    Y = rng.standard_normal((m, R))                                      # rows >= K of the rest: R22
+    Y[:, J] = 0.0
+    Y[:K, J] = U                                                         # pivot column t: rows 0..t of R11
+    Y = Y.astype(npdt)
+    rest = np.setdiff1d(np.arange(R), J)
+    R11 = Y[:K, J].astype(np.float64)
+    R12 = Y[:K, rest].astype(np.float64)
+    want = ocp.back_substitution(R11, R12)
+    Yd = dev(np.ascontiguousarray(Y.T))
+    T = torch.empty(K * (R - K), dtype=torch.float64, device="cuda")
+    rd = torch.empty(R - K, dtype=torch.int32, device="cuda")
+    dt = idl.IDL_F32 if dtype == "f32" else idl.IDL_F64
+    idl.idl_t_solve(ctx, Yd, m, R, m, dt, K, dev(J), T, rd)
+    got = host(T).reshape(K, R - K)
+    assert np.array_equal(host(rd), rest)
+    scale = np.abs(np.linalg.inv(R11)) @ np.abs(R12)
+    tol = 1e-11 if dtype == "f32" else 1e-13
+    assert np.all(np.abs(got - want) <= tol * np.maximum(scale, 1e-30))
+
+
 def test_cpqr_exact_rank_and_ties(ctx):
     # duplicated columns (exact ties): the smallest index wins, like the oracle
     base = np.random.default_rng(0).standard_normal((20, 8))
