@@ -296,7 +296,7 @@ __global__ void b_rest_kernel(const BItem* __restrict__ items, const int64_t* __
   if (r < it.R) rest_elem((int)r, sJ, it.K, (int)it.R, it.rest);
 }
 
-__global__ void __launch_bounds__(32) b_rinv_kernel(const BItem* __restrict__ items, const int64_t* __restrict__ pre,
+__global__ void __launch_bounds__(32 * kRinvWarps) b_rinv_kernel(const BItem* __restrict__ items, const int64_t* __restrict__ pre,
                                                      int n) {
   extern __shared__ __align__(16) double shU[];
   ITEM_OF_BLOCK(pre, n);
@@ -668,8 +668,8 @@ static int plan_batch(idl_ctx* ctx, const idl_batch_item* items, int n, const Tu
     nb[kBPSel] = b.learned ? 1 : 0;
     nb[kBPApply] = (b.learned && b.R > b.C) ? std::min<int64_t>(cdiv(b.R - b.C, prop::kApplyThreads / 32), 64) : 0;
     nb[kBRest] = cdiv(b.R, 256);
-    nb[kBRinv] = b.K;                                      // one warp per column
-    nb[kBTgemm] = cdiv(b.R - b.K, kTNB);
+    nb[kBRinv] = cdiv(b.K, kRinvWarps);                    // one warp per column
+    nb[kBTgemm] = cdiv(b.R - b.K, kTNBdf);
     nb[kBLam] = cp ? b.K : 0;
     for (int st = 0; st < kBNumStages; ++st) P.pre[st][i + 1] = P.pre[st][i] + nb[st];
     if (d) P.dense_list.push_back(i); else P.cp_list.push_back(i);
@@ -790,11 +790,11 @@ static int run_stages(idl_ctx* ctx, const BatchPlan& P, const BItem* d_items, co
   BLAUNCH(b_rest_kernel, kBRest, 256, sizeof(int32_t) * (size_t)P.maxK);
   {
     const size_t smem_inv = sizeof(double) * (size_t)P.maxK * (P.maxK + 1);
-    const size_t smem_t = sizeof(float) * (2 * (size_t)P.maxK * P.maxK + (size_t)P.maxK * (kTNB + 1));
+    const size_t smem_t = sizeof(float) * (2 * (size_t)P.maxK * P.maxK + (size_t)P.maxK * (kTNBdf + 1));
     cudaError_t e = cudaFuncSetAttribute(b_rinv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_inv);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(b_tgemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_t);
     if (e != cudaSuccess) return cuda_check(ctx, e, "batch solve attribute");
-    BLAUNCH(b_rinv_kernel, kBRinv, 32, smem_inv);
+    BLAUNCH(b_rinv_kernel, kBRinv, 32 * kRinvWarps, smem_inv);
     BLAUNCH(b_tgemm_kernel, kBTgemm, 256, smem_t);
   }
   BLAUNCH(b_lam_kernel, kBLam, 256, 0);

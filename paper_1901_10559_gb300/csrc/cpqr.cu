@@ -398,24 +398,24 @@ int launch_t_solve(idl_ctx* ctx, const void* Y2, int64_t m, int64_t R, int64_t l
       idl::count_launch();
   const size_t smem_inv = sizeof(double) * (size_t)K * (K + 1);
   const size_t smem_t = sizeof(double) * ((size_t)K * K + (size_t)K * (kTNB + 1));
-  const size_t smem_df = sizeof(float) * (2 * (size_t)K * K + (size_t)K * (kTNB + 1));
-  const unsigned inv_blocks = (unsigned)K;                 // one warp per column, one column per block
+  const size_t smem_df = sizeof(float) * (2 * (size_t)K * K + (size_t)K * (kTNBdf + 1));
+  const unsigned inv_blocks = (unsigned)cdiv(K, kRinvWarps);   // one warp per column
   cudaError_t e;
   if (dtype == IDL_F32) {
     e = cudaFuncSetAttribute(rinv_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_inv);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(tgemm_df_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_df);
     if (e == cudaSuccess) {
-      rinv_kernel<float><<<inv_blocks, 32, smem_inv, ctx->stream>>>((const float*)Y2, (int)ld, (int)K, (int)R, J, Rinv),
+      rinv_kernel<float><<<inv_blocks, 32 * kRinvWarps, smem_inv, ctx->stream>>>((const float*)Y2, (int)ld, (int)K, (int)R, J, Rinv),
           idl::count_launch();
       if (nrest > 0)
-        tgemm_df_kernel<<<(unsigned)cdiv(nrest, kTNB), 256, smem_df, ctx->stream>>>(
+        tgemm_df_kernel<<<(unsigned)cdiv(nrest, kTNBdf), 256, smem_df, ctx->stream>>>(
             (const float*)Y2, (int)ld, (int)K, (int)R, Rinv, rest, (int)nrest, T), idl::count_launch();
     }
   } else {
     e = cudaFuncSetAttribute(rinv_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_inv);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(tgemm_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_t);
     if (e == cudaSuccess) {
-      rinv_kernel<double><<<inv_blocks, 32, smem_inv, ctx->stream>>>((const double*)Y2, (int)ld, (int)K, (int)R, J,
+      rinv_kernel<double><<<inv_blocks, 32 * kRinvWarps, smem_inv, ctx->stream>>>((const double*)Y2, (int)ld, (int)K, (int)R, J,
                                                                       Rinv), idl::count_launch();
       if (nrest > 0)
         tgemm_kernel<double><<<(unsigned)cdiv(nrest, kTNB), 256, smem_t, ctx->stream>>>(

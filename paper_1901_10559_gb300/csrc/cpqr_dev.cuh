@@ -33,13 +33,16 @@ __device__ __forceinline__ double group_sum(double v, int tpc) {
 template <int V, int TPC>
 __device__ __forceinline__ int vslot(int i) { return (i % TPC) * V + i / TPC; }
 
-// sum_j v_j y_j over a thread's rows (four partial sums)
+// sum_j v_j y_j over a thread's rows (four partial sums).  Slots j < jskip
+// (a multiple of 4, the same for every lane) hold rows above the current
+// step, where v is zero: those chunks are skipped (warp-uniform branches).
 template <typename T, int V>
-__device__ __forceinline__ T house_dot(const T* __restrict__ vrow, const T (&y)[V]) {
+__device__ __forceinline__ T house_dot(const T* __restrict__ vrow, const T (&y)[V], int jskip) {
   static_assert(V % 4 == 0, "V must be a multiple of 4");
   T d0 = T(0), d1 = T(0), d2 = T(0), d3 = T(0);
 #pragma unroll
   for (int j = 0; j < V; j += 4) {
+    if (j < jskip) continue;
     if constexpr (sizeof(T) == 4) {
       const float4 w = *reinterpret_cast<const float4*>(vrow + j);
       d0 = fma(w.x, y[j], d0); d1 = fma(w.y, y[j + 1], d1); d2 = fma(w.z, y[j + 2], d2); d3 = fma(w.w, y[j + 3], d3);
@@ -53,12 +56,14 @@ __device__ __forceinline__ T house_dot(const T* __restrict__ vrow, const T (&y)[
 }
 
 // y -= d v over a thread's rows; returns the thread's part of the trailing
-// norm^2 over rows with slot index j >= jt (four partial sums)
+// norm^2 over rows with slot index j >= jt (four partial sums); chunks below
+// jskip are left alone (v is zero there and jt > jskip)
 template <typename T, int V>
-__device__ __forceinline__ T house_update(const T* __restrict__ vrow, T (&y)[V], T d, int jt) {
+__device__ __forceinline__ T house_update(const T* __restrict__ vrow, T (&y)[V], T d, int jt, int jskip) {
   T s0 = T(0), s1 = T(0), s2 = T(0), s3 = T(0);
 #pragma unroll
   for (int j = 0; j < V; j += 4) {
+    if (j < jskip) continue;
     T w0, w1, w2, w3;
     if constexpr (sizeof(T) == 4) {
       const float4 w = *reinterpret_cast<const float4*>(vrow + j);
@@ -79,6 +84,10 @@ __device__ __forceinline__ T house_update(const T* __restrict__ vrow, T (&y)[V],
   }
   return (s0 + s1) + (s2 + s3);
 }
+
+// first slot chunk (multiple of 4) that can hold rows >= t for some lane of a
+// TPC-lane group: rows gl + TPC j < t for all gl when TPC (j + 4) <= t
+__device__ __forceinline__ int skip_slots(int t, int tpc) { return (t / tpc) & ~3; }
 
 // ----------------------------------------------------------------------------
 // Register-resident variant (used whenever a cluster shape fits).  Each group
@@ -224,12 +233,22 @@ __device__ __forceinline__ void cpqr_reg_body(const T* __restrict__ Yin, T* __re
         if (lane == 0 && t > 0) vs[vslot<V, TPC>(t - 1)] = T(0);     // rows above t stay zero
         const T* rm = cluster.map_shared_rank(stage + (t & 1) * m, (unsigned)w);
         T xs = T(0), x0 = T(0);
-        for (int i = t + lane; i < m; i += 32) {
-          const T x = rm[i];
-          vs[vslot<V, TPC>(i)] = x;
-          xs += x * x;
-          if (i == t) x0 = x;
-          if (Vout && rank == 0) Vout[(int64_t)t * m + i] = x;
+        T xv[8];                                                     // m <= 256: every remote load issued first
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          const int i = t + lane + 32 * q;
+          xv[q] = i < m ? rm[i] : T(0);
+        }
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          const int i = t + lane + 32 * q;
+          if (i < m) {
+            const T x = xv[q];
+            vs[vslot<V, TPC>(i)] = x;
+            xs += x * x;
+            if (i == t) x0 = x;
+            if (Vout && rank == 0) Vout[(int64_t)t * m + i] = x;
+          }
         }
         if (Vout && rank == 0)
           for (int i = lane; i < t; i += 32) Vout[(int64_t)t * m + i] = T(0);
@@ -263,16 +282,17 @@ __device__ __forceinline__ void cpqr_reg_body(const T* __restrict__ Yin, T* __re
     if (piv) { nrm2 = T(-1); tp = t; alpha_p = s_alpha; }
     // vs is zero outside rows [t, m): no per-row predicates in the dot product and the update
     const T* vrow = vs + gl * V;
-    T d = group_sum(house_dot<T, V>(vrow, y), tpc) * beta;
+    const int jskip = skip_slots(t, tpc);
+    T d = group_sum(house_dot<T, V>(vrow, y, jskip), tpc) * beta;
     if (!upd) d = T(0);
     __syncwarp();   // re-read v below instead of keeping all of it in registers
     // trailing norm over rows > t: rows gl + tpc*j with j >= jt
     const int jt = (t - gl) >= 0 ? (t - gl) / tpc + 1 : 0;
-    const T s2 = group_sum(house_update<T, V>(vrow, y, d, jt), tpc);
+    const T s2 = group_sum(house_update<T, V>(vrow, y, d, jt, jskip), tpc);
     if (upd) nrm2 = s2;
   }
   cluster.sync();                 // no CTA reads another's staging slot after this point
-  double r22 = 0.0;
+  T r22t = T(0);                  // per-thread part in the working precision (FP64 pipes are scarce)
 #pragma unroll
   for (int j = 0; j < V; ++j) {
     const int i = gl + tpc * j;
@@ -280,10 +300,10 @@ __device__ __forceinline__ void cpqr_reg_body(const T* __restrict__ Yin, T* __re
       T out = y[j];
       if (tp >= 0) out = (i < tp) ? y[j] : (i == tp ? alpha_p : T(0));
       Yout[scol * ld + i] = out;
-      if (tp < 0 && i >= K) r22 += (double)y[j] * (double)y[j];
+      if (tp < 0 && i >= K) r22t = fma(y[j], y[j], r22t);
     }
   }
-  r22 = warp_sum(r22);
+  double r22 = warp_sum((double)r22t);
   if (lane == 0 && r22 != 0.0) atomicAdd(&diag[0], r22);
 }
 
@@ -397,13 +417,14 @@ __device__ __forceinline__ void cpqr_cta_body(const T* __restrict__ Yin, T* __re
     const T beta = s_beta;
     const bool upd = own && nrm2 >= T(0);
     const T* vrow = vs + gl * V;
-    T d = group_sum(house_dot<T, V>(vrow, y), tpc) * beta;
+    const int jskip = skip_slots(t, tpc);
+    T d = group_sum(house_dot<T, V>(vrow, y, jskip), tpc) * beta;
     if (!upd) d = T(0);
     const int jt = (t - gl) >= 0 ? (t - gl) / tpc + 1 : 0;
-    const T s2 = group_sum(house_update<T, V>(vrow, y, d, jt), tpc);
+    const T s2 = group_sum(house_update<T, V>(vrow, y, d, jt, jskip), tpc);
     if (upd) nrm2 = s2;
   }
-  double r22 = 0.0;
+  T r22t = T(0);
 #pragma unroll
   for (int j = 0; j < V; ++j) {
     const int i = gl + tpc * j;
@@ -411,10 +432,10 @@ __device__ __forceinline__ void cpqr_cta_body(const T* __restrict__ Yin, T* __re
       T out = y[j];
       if (tp >= 0) out = (i < tp) ? y[j] : (i == tp ? alpha_p : T(0));
       Yout[scol * ld + i] = out;
-      if (tp < 0 && i >= K) r22 += (double)y[j] * (double)y[j];
+      if (tp < 0 && i >= K) r22t = fma(y[j], y[j], r22t);
     }
   }
-  r22 = warp_sum(r22);
+  double r22 = warp_sum((double)r22t);
   if (lane == 0 && r22 != 0.0) atomicAdd(&diag[0], r22);
   __syncthreads();
   for (int q = tid; q < K; q += blockDim.x) J[q] = s_piv[q] >= 0 ? colmap[s_piv[q]] : -1;

@@ -100,8 +100,49 @@ __global__ void bucket_sort_block_kernel(const int32_t* __restrict__ ptr, int32_
   for (int q = blockIdx.x; q < count; q += gridDim.x) bucket_sort_block_body(ptr, big[q], row_list, seg);
 }
 
+__global__ void __launch_bounds__(256) stable_count_kernel(const int32_t* __restrict__ h, int64_t I, int L,
+                                                           int32_t* __restrict__ cnt, int* status) {
+  extern __shared__ int32_t shc[];
+  stable_count_block(h, I, L, blockIdx.x, cnt, status, shc);
+}
+
+__global__ void stable_prefix_kernel(int32_t* __restrict__ cnt, int64_t nblk, int L, int32_t* __restrict__ tot) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b < L) tot[b] = stable_prefix_bucket(cnt, nblk, L, b);
+}
+
+__global__ void __launch_bounds__(256) stable_scatter_kernel(const int32_t* __restrict__ h, int64_t I, int L,
+                                                             const int32_t* __restrict__ ptr,
+                                                             const int32_t* __restrict__ cnt,
+                                                             int32_t* __restrict__ row_list) {
+  extern __shared__ int32_t shc[];
+  stable_scatter_block(h, I, L, blockIdx.x, ptr, cnt, row_list, shc);
+}
+
+// Stable counting sort (see draws_dev.cuh): no per-bucket sort pass.
+static int stable_bucket_offsets(idl_ctx* ctx, const int32_t* h, int64_t I, int64_t L, int32_t* bucket_ptr,
+                                 int32_t* row_list) {
+  cudaStream_t st = ctx->stream;
+  const int W = stable_warps(L);
+  const int64_t nblk = cdiv(I, (int64_t)W * kStableSub);
+  int32_t* cnt = (int32_t*)ws_get(ctx, kWsCursor, sizeof(int32_t) * (size_t)(nblk * L + L + 1));
+  if (!cnt) return IDL_ENOMEM;
+  int32_t* tot = cnt + nblk * L;
+  const size_t sm = sizeof(int32_t) * (size_t)W * L;
+  cudaError_t e = cudaFuncSetAttribute(stable_count_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(stable_scatter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return cuda_check(ctx, e, "bucket attribute");
+  stable_count_kernel<<<(unsigned)nblk, 32 * W, sm, st>>>(h, I, (int)L, cnt, ctx->d_status), idl::count_launch();
+  stable_prefix_kernel<<<(unsigned)cdiv(L, 128), 128, 0, st>>>(cnt, nblk, (int)L, tot), idl::count_launch();
+  bucket_scan_kernel<<<1, 1024, 0, st>>>(tot, L, bucket_ptr, tot), idl::count_launch();
+  stable_scatter_kernel<<<(unsigned)nblk, 32 * W, sm, st>>>(h, I, (int)L, bucket_ptr, cnt, row_list),
+      idl::count_launch();
+  return cuda_check(ctx, cudaGetLastError(), "bucket offsets");
+}
+
 int launch_bucket_offsets(idl_ctx* ctx, const int32_t* h, int64_t I, int64_t L, int32_t* bucket_ptr,
                           int32_t* row_list) {
+  if (I > 0 && L <= kStableMaxL) return stable_bucket_offsets(ctx, h, I, L, bucket_ptr, row_list);
   cudaStream_t st = ctx->stream;
   int32_t* cursor = (int32_t*)ws_get(ctx, kWsCursor, sizeof(int32_t) * (size_t)(L + 1));
   int32_t* big = (int32_t*)ws_get(ctx, kWsBig, sizeof(int32_t) * (size_t)(L + 1));

@@ -198,4 +198,119 @@ __device__ __forceinline__ void bucket_sort_block_body(const int32_t* __restrict
   }
 }
 
+// ---------------------------------------------------------------------------
+// Stable counting sort by bucket (used when L <= kStableMaxL): row i goes to
+// its bucket in increasing i without any per-bucket sort.  A block of W warps
+// owns a chunk of W * kStableSub rows; warp w owns the chunk's w-th
+// sub-chunk of kStableSub consecutive rows.
+//   1. stable_count_block: per-warp histograms in shared memory (loads of a
+//      sub-chunk in flight together), then the per-bucket sum over the warps
+//      goes to cnt[blk][*];
+//   2. stable_prefix_bucket: per bucket b, cnt[blk][b] becomes the exclusive
+//      prefix over the blocks (one thread per bucket, loads batched) and the
+//      total; one block scans the totals into bucket_ptr (bucket_scan_body);
+//   3. stable_scatter_block: the per-warp histograms are formed again and
+//      turned into exclusive prefixes over the warps; warp w then walks its
+//      rows in order, 32 at a time, lanes with the same bucket found by
+//      __match_any_sync: row i of bucket b goes to ptr[b] + cnt[blk][b] +
+//      (rows of b in earlier warps of the block) + (earlier rows of b in the
+//      warp).
+// ---------------------------------------------------------------------------
+constexpr int kStableSub = 1024;                 // rows per warp
+constexpr int64_t kStableMaxL = 14336;          // at least three warps' counters fit
+constexpr int kStableSmemInts = 51200;          // W * L <= this (200 KB of shared memory)
+__host__ __device__ constexpr int stable_warps(int64_t L) {
+  return L <= 0 ? 1 : (int)(kStableSmemInts / L >= 8 ? 8 : (kStableSmemInts / L < 1 ? 1 : kStableSmemInts / L));
+}
+
+// per-warp histograms of the block's rows into hw[w * L + b]
+__device__ __forceinline__ void stable_warp_hist(const int32_t* __restrict__ h, int64_t I, int L, int64_t blk,
+                                                 int* status, int32_t* hw) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, W = blockDim.x >> 5;
+  for (int e = threadIdx.x; e < W * L; e += blockDim.x) hw[e] = 0;
+  __syncthreads();
+  const int64_t i0 = (blk * W + w) * (int64_t)kStableSub;
+  int32_t* cw = hw + w * L;
+#pragma unroll 8
+  for (int q = 0; q < kStableSub / 32; ++q) {
+    const int64_t i = i0 + q * 32 + lane;
+    if (i < I) {
+      const int b = h[i];
+      if (b < 0 || b >= L) set_status(status, IDL_EDATA);
+      else atomicAdd(&cw[b], 1);
+    }
+  }
+  __syncthreads();
+}
+
+__device__ __forceinline__ void stable_count_block(const int32_t* __restrict__ h, int64_t I, int L, int64_t blk,
+                                                   int32_t* __restrict__ cnt, int* status, int32_t* hw) {
+  stable_warp_hist(h, I, L, blk, status, hw);
+  const int W = blockDim.x >> 5;
+  int32_t* out = cnt + blk * (int64_t)L;
+  for (int b = threadIdx.x; b < L; b += blockDim.x) {
+    int32_t t = 0;
+    for (int w = 0; w < W; ++w) t += hw[w * L + b];
+    out[b] = t;
+  }
+}
+
+// bucket b: exclusive prefix over the nblk blocks in place; returns the total
+__device__ __forceinline__ int32_t stable_prefix_bucket(int32_t* __restrict__ cnt, int64_t nblk, int L, int b) {
+  int32_t run = 0;
+  int64_t c = 0;
+  for (; c + 8 <= nblk; c += 8) {
+    int32_t v[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) v[q] = cnt[(c + q) * L + b];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) { cnt[(c + q) * L + b] = run; run += v[q]; }
+  }
+  for (; c < nblk; ++c) {
+    const int32_t v = cnt[c * L + b];
+    cnt[c * L + b] = run;
+    run += v;
+  }
+  return run;
+}
+
+__device__ __forceinline__ void stable_scatter_block(const int32_t* __restrict__ h, int64_t I, int L, int64_t blk,
+                                                     const int32_t* __restrict__ ptr, const int32_t* __restrict__ cnt,
+                                                     int32_t* __restrict__ row_list, int32_t* hw) {
+  int* no_status = nullptr;
+  stable_warp_hist(h, I, L, blk, no_status, hw);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, W = blockDim.x >> 5;
+  // hw[w][b] <- next free slot of bucket b for warp w
+  const int32_t* pre = cnt + blk * (int64_t)L;
+  for (int b = threadIdx.x; b < L; b += blockDim.x) {
+    int32_t run = ptr[b] + pre[b];
+    for (int ww = 0; ww < W; ++ww) {
+      const int32_t v = hw[ww * L + b];
+      hw[ww * L + b] = run;
+      run += v;
+    }
+  }
+  __syncthreads();
+  int32_t* cw = hw + w * L;
+  const int64_t i0 = (blk * W + w) * (int64_t)kStableSub;
+  const unsigned lt = (1u << lane) - 1u;
+  int nb[2];
+  nb[0] = (i0 + lane < I) ? h[i0 + lane] : -1;
+  for (int q = 0; q < kStableSub / 32; ++q) {
+    const int64_t i = i0 + q * 32 + lane;
+    int b = nb[q & 1];
+    const int64_t inext = i + 32;
+    if (q + 1 < kStableSub / 32) nb[(q + 1) & 1] = inext < I ? h[inext] : -1;     // next row's bucket in flight
+    if (b >= L) b = -1;                                               // flagged by the counting pass
+    const unsigned peers = __match_any_sync(0xffffffffu, b);
+    const int slot = b >= 0 ? cw[b] : 0;
+    __syncwarp();
+    if (b >= 0) {
+      row_list[slot + __popc(peers & lt)] = (int32_t)i;
+      if ((peers & lt) == 0) cw[b] = slot + __popc(peers);             // the group's lowest lane advances it
+    }
+    __syncwarp();
+  }
+}
+
 }  // namespace idl

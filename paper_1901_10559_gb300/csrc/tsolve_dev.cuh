@@ -21,18 +21,21 @@ __device__ __forceinline__ void rest_elem(int r, const int32_t* sJ, int K, int R
 }
 
 constexpr int kSolveMaxK = 128;
+constexpr int kRinvWarps = 4;
 
 // inv(R11) in FP64, R11 = rows 0..K-1 of the pivot columns in pivot order
 // (upper triangular).  One warp per column j of the inverse: column-oriented
 // back substitution of R11 x = e_j (x_i = b_i / u_ii, then b_k -= u_ki x_i for
 // k < i, lanes over k), with the K reciprocals 1/u_ii formed once.  Launched
-// with one warp per block so that the columns spread over the SMs' FP64
-// units.  Output Rinv: K x K row-major, zero below the diagonal.
+// with kRinvWarps warps per block (columns spread over the SMs' FP64 units;
+// every thread of the block helps stage R11).  Output Rinv: K x K row-major,
+// zero below the diagonal.
 template <typename T>
 __device__ __forceinline__ void rinv_block(const T* __restrict__ Y, int ld, int K, int R, const int32_t* __restrict__ J,
                                           double* __restrict__ Rinv, int blk, int nblk, double* U) {
   // U: K x (K+1) doubles of shared memory; its column K holds 1/u_ii
   const int KP = K + 1;
+#pragma unroll 4
   for (int e = threadIdx.x; e < K * K; e += blockDim.x) {
     const int j = e / K, i = e - j * K;                              // column j (pivot j), row i
     const int jj = J[j];
@@ -80,30 +83,31 @@ constexpr int kTNB = 64;
 // (two floats), a_hi b exactly by an FMA (p + e), a_lo b rounded, sums by
 // TwoSum (Knuth) into a (hi, lo) pair -- about 48 significant bits, far
 // below the FP32 sketch's own rounding, at a fraction of the FP64 pipes' cost.
+constexpr int kTNBdf = 32;                 // columns per block of the double-float product
 __device__ __forceinline__ void tgemm_block_df(const float* __restrict__ Y, int ld, int K, int R,
                                               const double* __restrict__ Rinv, const int32_t* __restrict__ rest,
                                               int nrest, double* __restrict__ Tout, int blk, float* sh) {
   float* Ah = sh;                          // K x K
   float* Al = Ah + K * K;                  // K x K
-  float* B = Al + K * K;                   // K x (kTNB + 1)
-  const int BP = kTNB + 1;
+  float* B = Al + K * K;                   // K x (kTNBdf + 1)
+  const int BP = kTNBdf + 1;
   for (int e = threadIdx.x; e < K * K; e += blockDim.x) {
     const double a = Rinv[e];
     const float h = (float)a;
     Ah[e] = h;
     Al[e] = (float)(a - (double)h);
   }
-  const int cb = blk * kTNB;
-  for (int e = threadIdx.x; e < K * kTNB; e += blockDim.x) {
+  const int cb = blk * kTNBdf;
+  for (int e = threadIdx.x; e < K * kTNBdf; e += blockDim.x) {
     const int cc = e / K, i = e - cc * K;
     const int c = cb + cc;
     const int r = (c < nrest) ? rest[c] : -1;
     B[i * BP + cc] = (r >= 0 && r < R) ? Y[(int64_t)r * ld + i] : 0.f;
   }
   __syncthreads();
-  const int cc = threadIdx.x & (kTNB - 1);
+  const int cc = threadIdx.x & (kTNBdf - 1);
   const int c = cb + cc;
-  for (int i = threadIdx.x >> 6; i < K; i += blockDim.x >> 6) {
+  for (int i = threadIdx.x >> 5; i < K; i += blockDim.x >> 5) {
     float sh_ = 0.f, sl = 0.f;
     for (int k = i; k < K; ++k) {
       const float ah = Ah[i * K + k], al = Al[i * K + k], b = B[k * BP + cc];
