@@ -121,6 +121,12 @@ template <typename T, int V, int TPC> struct RegCpqr {
 // (ascending, so ties still go to the smaller original index); J reports
 // original indices.  Vout/Bout (optional): reflector t (zero above row t) at
 // Vout + t*m and its beta at Bout[t] -- the learned proposal's candidate QR.
+// Per pivot step: every warp publishes its best column, one block barrier;
+// every warp reduces those (the same winner everywhere), the winner's group
+// stages its column and thread 0 publishes the CTA's candidate; one cluster
+// barrier; warp 0 pulls every CTA's candidate, picks the winner, pulls its
+// staged column and forms the reflection; one block barrier; every group
+// updates its column.
 template <typename T, int V, int TPC>
 __device__ __forceinline__ void cpqr_reg_body(const T* __restrict__ Yin, T* __restrict__ Yout, int m, int R, int ld,
                                               int K, int nc, int32_t* __restrict__ J, double* __restrict__ rnorm,
@@ -138,23 +144,40 @@ __device__ __forceinline__ void cpqr_reg_body(const T* __restrict__ Yin, T* __re
   const bool own = g < ncl;
   const int col = c0 + g;
   const int64_t scol = own ? (colmap ? (int64_t)colmap[col] : (int64_t)col) : 0;   // column of Yin / Yout
+  const int mp = (m + 3) & ~3;
 
   T* vs = (T*)smem_raw;                                             // V*TPC: v by thread slot, zero outside rows [t, m)
-                                                                    // (first: 16-byte aligned vector reads)
-  T* stage = vs + V * TPC;                                          // [2][m] staged candidate column
-  Cand<T>* cand = (Cand<T>*)(smem_raw + round_up((int64_t)sizeof(T) * (2 * m + V * TPC), 16));   // [2]
+  T* stage = vs + V * TPC;                                          // [2][mp] this CTA's staged candidate column
+  Cand<T>* cand = (Cand<T>*)(smem_raw + round_up((int64_t)sizeof(T) * (V * TPC + 2 * mp), 16));   // [2]
   __shared__ T red_v[32];
   __shared__ int red_i[32];
   __shared__ T s_beta, s_alpha;
-  __shared__ int s_p, s_stop, s_best;
+  __shared__ int s_p, s_stop;
   if (tid == 0) s_stop = 0;
   for (int i = tid; i < V * TPC; i += blockDim.x) vs[i] = T(0);
 
+  // one thread per whole column with 16-byte aligned columns: vector loads and stores
+  bool vecio = false;
+  if constexpr (TPC == 1 && sizeof(T) == 4)
+    vecio = ((ld & 3) == 0) && ((((uintptr_t)Yin) & 15) == 0) && ((((uintptr_t)Yout) & 15) == 0);
   T y[V];
+  if (vecio) {
 #pragma unroll
-  for (int j = 0; j < V; ++j) {
-    const int i = gl + tpc * j;
-    y[j] = (own && i < m) ? Yin[scol * ld + i] : T(0);
+    for (int j = 0; j < V; j += 4) {
+      if (own && j + 4 <= m) {
+        const float4 q = *reinterpret_cast<const float4*>(Yin + scol * ld + j);
+        y[j] = q.x; y[j + 1] = q.y; y[j + 2] = q.z; y[j + 3] = q.w;
+      } else {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) y[j + u] = (own && j + u < m) ? Yin[scol * ld + j + u] : T(0);
+      }
+    }
+  } else {
+#pragma unroll
+    for (int j = 0; j < V; ++j) {
+      const int i = gl + tpc * j;
+      y[j] = (own && i < m) ? Yin[scol * ld + i] : T(0);
+    }
   }
   T nn = T(0);
 #pragma unroll
@@ -169,7 +192,7 @@ __device__ __forceinline__ void cpqr_reg_body(const T* __restrict__ Yin, T* __re
   int tp = -1;
   T alpha_p = T(0);
   for (int t = 0; t < K; ++t) {
-    // 1. block candidate
+    // A. warp candidates
     T bv = (gl == 0 && nrm2 >= T(0)) ? nrm2 : T(-1);
     int bi = (gl == 0 && nrm2 >= T(0)) ? col : -1;
 #pragma unroll
@@ -180,32 +203,35 @@ __device__ __forceinline__ void cpqr_reg_body(const T* __restrict__ Yin, T* __re
     }
     if (lane == 0) { red_v[wid] = bv; red_i[wid] = bi; }
     __syncthreads();
-    if (wid == 0) {
-      bv = lane < NW ? red_v[lane] : T(-1);
-      bi = lane < NW ? red_i[lane] : -1;
+    // B. the CTA's candidate, reduced by every warp (same result everywhere)
+    bv = lane < NW ? red_v[lane] : T(-1);
+    bi = lane < NW ? red_i[lane] : -1;
 #pragma unroll
-      for (int o = 16; o; o >>= 1) {
-        const T ov = __shfl_xor_sync(0xffffffffu, bv, o);
-        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-        if (better(ov, oi, bv, bi)) { bv = ov; bi = oi; }
-      }
-      if (lane == 0) {
-        s_best = bi;
-        cand[t & 1].val = bv;          // published locally; the other CTAs pull it after the barrier
-        cand[t & 1].idx = bi;
+    for (int o = 16; o; o >>= 1) {
+      const T ov = __shfl_xor_sync(0xffffffffu, bv, o);
+      const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+      if (better(ov, oi, bv, bi)) { bv = ov; bi = oi; }
+    }
+    if (own && col == bi) {
+      T* st = stage + (t & 1) * mp;
+      if (vecio) {
+#pragma unroll
+        for (int j = 0; j < V; j += 4)
+          if (j + 4 > t && j < mp) *reinterpret_cast<float4*>(st + j) = make_float4(y[j], y[j + 1], y[j + 2], y[j + 3]);
+      } else {
+#pragma unroll
+        for (int j = 0; j < V; ++j) {
+          const int i = gl + tpc * j;
+          if (i >= t && i < m) st[i] = y[j];
+        }
       }
     }
-    __syncthreads();
-    if (own && col == s_best) {
-      T* st = stage + (t & 1) * m;
-#pragma unroll
-      for (int j = 0; j < V; ++j) {
-        const int i = gl + tpc * j;
-        if (i >= t && i < m) st[i] = y[j];
-      }
+    if (tid == 0) {
+      cand[t & 1].val = bv;            // published locally; the other CTAs pull it after the barrier
+      cand[t & 1].idx = bi;
     }
-    cluster.sync();                                                 // 2.
-    // 3. winner, pivot column, reflection (warp 0)
+    cluster.sync();
+    // C. winner, pivot column, reflection (warp 0)
     if (wid == 0) {
       T v = T(-1);
       int ix = -1;
@@ -231,7 +257,7 @@ __device__ __forceinline__ void cpqr_reg_body(const T* __restrict__ Yin, T* __re
       } else {
         const int w = ix / nc;
         if (lane == 0 && t > 0) vs[vslot<V, TPC>(t - 1)] = T(0);     // rows above t stay zero
-        const T* rm = cluster.map_shared_rank(stage + (t & 1) * m, (unsigned)w);
+        const T* rm = cluster.map_shared_rank(stage + (t & 1) * mp, (unsigned)w);
         T xs = T(0), x0 = T(0);
         T xv[8];                                                     // m <= 256: every remote load issued first
 #pragma unroll
@@ -272,8 +298,9 @@ __device__ __forceinline__ void cpqr_reg_body(const T* __restrict__ Yin, T* __re
         }
       }
     }
-    __syncthreads();                                                // 4.
+    __syncthreads();
     if (s_stop) break;
+    // D. update
     const int p = s_p;
     const T beta = s_beta;
     const bool act = own && nrm2 >= T(0);
@@ -296,11 +323,25 @@ __device__ __forceinline__ void cpqr_reg_body(const T* __restrict__ Yin, T* __re
 #pragma unroll
   for (int j = 0; j < V; ++j) {
     const int i = gl + tpc * j;
-    if (own && i < m) {
-      T out = y[j];
-      if (tp >= 0) out = (i < tp) ? y[j] : (i == tp ? alpha_p : T(0));
-      Yout[scol * ld + i] = out;
-      if (tp < 0 && i >= K) r22t = fma(y[j], y[j], r22t);
+    if (tp >= 0) y[j] = (i < tp) ? y[j] : (i == tp ? alpha_p : T(0));
+    else if (own && i >= K && i < m) r22t = fma(y[j], y[j], r22t);
+  }
+  if (vecio) {
+#pragma unroll
+    for (int j = 0; j < V; j += 4) {
+      if (own && j + 4 <= m) {
+        *reinterpret_cast<float4*>(Yout + scol * ld + j) = make_float4(y[j], y[j + 1], y[j + 2], y[j + 3]);
+      } else {
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+          if (own && j + u < m) Yout[scol * ld + j + u] = y[j + u];
+      }
+    }
+  } else {
+#pragma unroll
+    for (int j = 0; j < V; ++j) {
+      const int i = gl + tpc * j;
+      if (own && i < m) Yout[scol * ld + i] = y[j];
     }
   }
   double r22 = warp_sum((double)r22t);
@@ -469,7 +510,7 @@ __device__ __forceinline__ bool proposal_certified(const int* gate, double* diag
 
 template <typename T, int V, int TPC>
 __host__ __device__ constexpr size_t reg_cpqr_smem(int m) {
-  return (size_t)(((int64_t)sizeof(T) * (2 * m + V * TPC) + 15) / 16 * 16) + sizeof(Cand<T>) * 2;
+  return (size_t)(((int64_t)sizeof(T) * (V * TPC + 2 * ((m + 3) & ~3)) + 15) / 16 * 16) + sizeof(Cand<T>) * 2;
 }
 
 }  // namespace idl
