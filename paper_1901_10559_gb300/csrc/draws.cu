@@ -107,8 +107,11 @@ __global__ void __launch_bounds__(256) stable_count_kernel(const int32_t* __rest
 }
 
 __global__ void stable_prefix_kernel(int32_t* __restrict__ cnt, int64_t nblk, int L, int32_t* __restrict__ tot) {
-  const int b = blockIdx.x * blockDim.x + threadIdx.x;
-  if (b < L) tot[b] = stable_prefix_bucket(cnt, nblk, L, b);
+  const int b = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);           // one warp per bucket
+  if (b < L) {
+    const int32_t t = stable_prefix_bucket(cnt, nblk, L, b);
+    if ((threadIdx.x & 31) == 0) tot[b] = t;
+  }
 }
 
 __global__ void __launch_bounds__(256) stable_scatter_kernel(const int32_t* __restrict__ h, int64_t I, int L,
@@ -133,7 +136,7 @@ static int stable_bucket_offsets(idl_ctx* ctx, const int32_t* h, int64_t I, int6
   if (e == cudaSuccess) e = cudaFuncSetAttribute(stable_scatter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return cuda_check(ctx, e, "bucket attribute");
   stable_count_kernel<<<(unsigned)nblk, 32 * W, sm, st>>>(h, I, (int)L, cnt, ctx->d_status), idl::count_launch();
-  stable_prefix_kernel<<<(unsigned)cdiv(L, 128), 128, 0, st>>>(cnt, nblk, (int)L, tot), idl::count_launch();
+  stable_prefix_kernel<<<(unsigned)cdiv(L, 8), 256, 0, st>>>(cnt, nblk, (int)L, tot), idl::count_launch();
   bucket_scan_kernel<<<1, 1024, 0, st>>>(tot, L, bucket_ptr, tot), idl::count_launch();
   stable_scatter_kernel<<<(unsigned)nblk, 32 * W, sm, st>>>(h, I, (int)L, bucket_ptr, cnt, row_list),
       idl::count_launch();

@@ -207,8 +207,9 @@ __device__ __forceinline__ void bucket_sort_block_body(const int32_t* __restrict
 //      sub-chunk in flight together), then the per-bucket sum over the warps
 //      goes to cnt[blk][*];
 //   2. stable_prefix_bucket: per bucket b, cnt[blk][b] becomes the exclusive
-//      prefix over the blocks (one thread per bucket, loads batched) and the
-//      total; one block scans the totals into bucket_ptr (bucket_scan_body);
+//      prefix over the blocks (one warp per bucket, lanes over blocks, warp
+//      scans) and the total; one block scans the totals into bucket_ptr
+//      (bucket_scan_body);
 //   3. stable_scatter_block: the per-warp histograms are formed again and
 //      turned into exclusive prefixes over the warps; warp w then walks its
 //      rows in order, 32 at a time, lanes with the same bucket found by
@@ -255,21 +256,22 @@ __device__ __forceinline__ void stable_count_block(const int32_t* __restrict__ h
   }
 }
 
-// bucket b: exclusive prefix over the nblk blocks in place; returns the total
+// bucket b (one warp): exclusive prefix over the nblk blocks in place, 32
+// blocks per round (lane = block); returns the total (every lane)
 __device__ __forceinline__ int32_t stable_prefix_bucket(int32_t* __restrict__ cnt, int64_t nblk, int L, int b) {
+  const int lane = threadIdx.x & 31;
   int32_t run = 0;
-  int64_t c = 0;
-  for (; c + 8 <= nblk; c += 8) {
-    int32_t v[8];
+  for (int64_t c0 = 0; c0 < nblk; c0 += 32) {
+    const int64_t c = c0 + lane;
+    const int32_t v = c < nblk ? cnt[c * L + b] : 0;
+    int32_t x = v;
 #pragma unroll
-    for (int q = 0; q < 8; ++q) v[q] = cnt[(c + q) * L + b];
-#pragma unroll
-    for (int q = 0; q < 8; ++q) { cnt[(c + q) * L + b] = run; run += v[q]; }
-  }
-  for (; c < nblk; ++c) {
-    const int32_t v = cnt[c * L + b];
-    cnt[c * L + b] = run;
-    run += v;
+    for (int o = 1; o < 32; o <<= 1) {
+      const int32_t y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (c < nblk) cnt[c * L + b] = run + x - v;
+    run += __shfl_sync(0xffffffffu, x, 31);
   }
   return run;
 }
