@@ -78,12 +78,19 @@ static int tc_impl(idl_ctx* ctx, const double* Omega, int64_t m2, int64_t m1, co
   if (smem > (size_t)ctx->smem_optin) return fail(ctx, IDL_ELIMIT, "gaussian tc: shared memory");
   const int NT = nz * NTc;                            // plane rows (zero beyond m2)
   const size_t b_plane_full = (size_t)NT * kBK * 2;
-  // CTAs per SM by shared memory; aim for about one wave of CTAs over the SMs
+  // split K so that (waves of CTAs) x (K blocks per CTA) is smallest: a CTA's time is
+  // proportional to its K blocks, and a partly filled last wave costs a whole one;
+  // each split adds a partial result to write and reduce (about half a K block)
   const int per_sm = std::max(1, (int)(ctx->smem_optin / smem));
-  int splits = (int)std::max<int64_t>(1, cdiv((int64_t)ctx->num_sms * per_sm, (int64_t)mtiles * nz));
-  splits = std::min(splits, nkb);
-  const int kbpc = (int)cdiv(nkb, splits);
-  splits = (int)cdiv(nkb, kbpc);
+  const int64_t slots = (int64_t)ctx->num_sms * per_sm;
+  int splits = 1, kbpc = nkb;
+  double best = 1e300;
+  for (int sp = 1; sp <= std::min(nkb, 32); ++sp) {
+    const int kb = (int)cdiv(nkb, sp);
+    const int se = (int)cdiv(nkb, kb);
+    const double cost = (double)cdiv((int64_t)mtiles * nz * se, slots) * kb + 0.5 * se;
+    if (cost < best - 1e-9) { best = cost; splits = se; kbpc = kb; }
+  }
   __nv_bfloat16* Bpl = (__nv_bfloat16*)ws_get(ctx, kWsOmegaConv, (size_t)nkb * NP * b_plane_full);
   float* part = (float*)ws_get(ctx, kWsPart, sizeof(float) * (size_t)splits * R * NT);
   if (!Bpl || !part) return IDL_ENOMEM;
