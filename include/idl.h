@@ -197,6 +197,14 @@ int idl_tensorsketch(idl_ctx* ctx, int N, const int64_t* dims, int64_t R,
                      const int32_t* const* hs, const int8_t* const* ss, int64_t L,
                      float* Y, int64_t ldy);
 
+/* The same with Y column-major: column r at Y + r*ldy, ldy >= L.  id_cp_tensor
+ * sketches in this layout when its Gaussian stage runs on the tensor cores
+ * (each column is written contiguously by the block that transforms it). */
+int idl_tensorsketch_colmajor(idl_ctx* ctx, int N, const int64_t* dims, int64_t R,
+                              const void* const* factors, const int64_t* ldf, const double* lambda,
+                              const int32_t* const* hs, const int8_t* const* ss, int64_t L,
+                              float* Y, int64_t ldy);
+
 /* ---------------------------------------------------------------------------
  * Gaussian stage Y2 = Omega Y1 (Sec. 1.2.1): Omega m2 x m1 row-major FP64
  * (device), Y1 m1 x R row-major (ldy1 >= R) of dtype, Y2 column-major
@@ -206,6 +214,12 @@ int idl_tensorsketch(idl_ctx* ctx, int N, const int64_t* dims, int64_t R,
 int idl_gaussian_stage(idl_ctx* ctx, const double* Omega, int64_t m2, int64_t m1,
                        const void* Y1, int64_t R, int64_t ldy1, int dtype, int precision,
                        void* Y2, int64_t ldy2);
+
+/* The same for FP32 Y1 stored column-major (column r at Y1 + r*ldy1, ldy1 >= m1),
+ * on the tensor cores: precision IDL_PREC_FP32, IDL_PREC_BF16X3 or IDL_PREC_BF16. */
+int idl_gaussian_stage_colmajor(idl_ctx* ctx, const double* Omega, int64_t m2, int64_t m1,
+                                const float* Y1, int64_t R, int64_t ldy1, int precision,
+                                float* Y2, int64_t ldy2);
 
 /* ---------------------------------------------------------------------------
  * Rank-K column-pivoted Householder QR of Y2 (Algorithm 1 line 3; Golub & Van

@@ -99,6 +99,8 @@ _SIGS = {
     "idl_countsketch_csr": ([_vp, _vp, _vp, _vp, _i64, _i64, _i64, _int, _vp, _vp, _vp, _vp, _i64, _vp, _i64], _int),
     "idl_tensorsketch": ([_vp, _int, _vp, _i64, _vp, _vp, _vp, _vp, _vp, _i64, _vp, _i64], _int),
     "idl_gaussian_stage": ([_vp, _vp, _i64, _i64, _vp, _i64, _i64, _int, _int, _vp, _i64], _int),
+    "idl_tensorsketch_colmajor": ([_vp, _int, _vp, _i64, _vp, _vp, _vp, _vp, _vp, _i64, _vp, _i64], _int),
+    "idl_gaussian_stage_colmajor": ([_vp, _vp, _i64, _i64, _vp, _i64, _i64, _int, _vp, _i64], _int),
     "idl_cpqr": ([_vp, _vp, _i64, _i64, _i64, _int, _i64, _vp, _vp], _int),
     "idl_t_solve": ([_vp, _vp, _i64, _i64, _i64, _int, _i64, _vp, _vp, _vp], _int),
     "idl_lambda_hat": ([_vp, _vp, _vp, _vp, _i64, _i64, _vp], _int),
@@ -262,7 +264,9 @@ def _arr(ctype, vals):
     return (ctype * len(vals))(*vals)
 
 
-def idl_tensorsketch(ctx, factors, ldf, lam, hs, ss, L, Y, ldy):
+def idl_tensorsketch(ctx, factors, ldf, lam, hs, ss, L, Y, ldy, colmajor=False):
+    """Y row-major (L x R, ldy >= R), or column-major (column r at Y + r*ldy,
+    ldy >= L) with colmajor=True."""
     N = len(factors)
     dims = _arr(ctypes.c_int64, [int(f.shape[1]) for f in factors])   # factors given as (R, I_n) tensors
     R = int(factors[0].shape[0])
@@ -270,14 +274,19 @@ def idl_tensorsketch(ctx, factors, ldf, lam, hs, ss, L, Y, ldy):
     lp = _arr(ctypes.c_int64, [int(x) for x in ldf])
     hp = _arr(_vp, [h.data_ptr() for h in hs])
     sp = _arr(_vp, [s.data_ptr() for s in ss])
-    return ctx.check(lib().idl_tensorsketch(ctx.ptr, N, ctypes.cast(dims, _vp), R, ctypes.cast(fp, _vp),
-                                            ctypes.cast(lp, _vp), _p(lam), ctypes.cast(hp, _vp),
-                                            ctypes.cast(sp, _vp), L, _p(Y), ldy))
+    fn = lib().idl_tensorsketch_colmajor if colmajor else lib().idl_tensorsketch
+    return ctx.check(fn(ctx.ptr, N, ctypes.cast(dims, _vp), R, ctypes.cast(fp, _vp), ctypes.cast(lp, _vp), _p(lam),
+                        ctypes.cast(hp, _vp), ctypes.cast(sp, _vp), L, _p(Y), ldy))
 
 
 def idl_gaussian_stage(ctx, Omega, m2, m1, Y1, R, ldy1, dtype, precision, Y2, ldy2):
     return ctx.check(lib().idl_gaussian_stage(ctx.ptr, _p(Omega), m2, m1, _p(Y1), R, ldy1, dtype, precision,
                                               _p(Y2), ldy2))
+
+
+def idl_gaussian_stage_colmajor(ctx, Omega, m2, m1, Y1, R, ldy1, precision, Y2, ldy2):
+    return ctx.check(lib().idl_gaussian_stage_colmajor(ctx.ptr, _p(Omega), m2, m1, _p(Y1), R, ldy1, precision,
+                                                       _p(Y2), ldy2))
 
 
 def idl_cpqr(ctx, Y2, m, R, ldy2, dtype, K, J, rnorm=None):

@@ -346,16 +346,29 @@ extern "C" int idl_countsketch_csr(idl_ctx* ctx, const int64_t* rowptr, const in
   return launch_countsketch_csr(ctx, rowptr, colidx, vals, I, R, nnz, dtype, s, bucket_ptr, row_list, L, Y1, ldy);
 }
 
-extern "C" int idl_tensorsketch(idl_ctx* ctx, int N, const int64_t* dims, int64_t R, const void* const* factors,
-                                const int64_t* ldf, const double* lambda, const int32_t* const* hs,
-                                const int8_t* const* ss, int64_t L, float* Y, int64_t ldy) {
+static int tensorsketch_entry(idl_ctx* ctx, int N, const int64_t* dims, int64_t R, const void* const* factors,
+                              const int64_t* ldf, const double* lambda, const int32_t* const* hs,
+                              const int8_t* const* ss, int64_t L, float* Y, int64_t ldy, bool cm) {
   TRY(check_ctx(ctx));
-  if (N < 1 || N > 8 || !dims || !factors || !ldf || !hs || !ss || !lambda || !Y || R < 1 || ldy < R)
+  if (N < 1 || N > 8 || !dims || !factors || !ldf || !hs || !ss || !lambda || !Y || R < 1 || ldy < (cm ? L : R))
     return fail(ctx, IDL_EINVAL, "tensorsketch: bad arguments");
   for (int n = 0; n < N; ++n)
     if (dims[n] < 1 || ldf[n] < dims[n] || !factors[n] || !hs[n] || !ss[n])
       return fail(ctx, IDL_EINVAL, "tensorsketch: bad mode arguments");
-  return launch_tensorsketch(ctx, N, dims, R, factors, ldf, lambda, hs, ss, L, Y, ldy);
+  return launch_tensorsketch(ctx, N, dims, R, factors, ldf, lambda, hs, ss, L, Y, ldy, cm);
+}
+
+extern "C" int idl_tensorsketch(idl_ctx* ctx, int N, const int64_t* dims, int64_t R, const void* const* factors,
+                                const int64_t* ldf, const double* lambda, const int32_t* const* hs,
+                                const int8_t* const* ss, int64_t L, float* Y, int64_t ldy) {
+  return tensorsketch_entry(ctx, N, dims, R, factors, ldf, lambda, hs, ss, L, Y, ldy, false);
+}
+
+extern "C" int idl_tensorsketch_colmajor(idl_ctx* ctx, int N, const int64_t* dims, int64_t R,
+                                         const void* const* factors, const int64_t* ldf, const double* lambda,
+                                         const int32_t* const* hs, const int8_t* const* ss, int64_t L, float* Y,
+                                         int64_t ldy) {
+  return tensorsketch_entry(ctx, N, dims, R, factors, ldf, lambda, hs, ss, L, Y, ldy, true);
 }
 
 extern "C" int idl_gaussian_stage(idl_ctx* ctx, const double* Omega, int64_t m2, int64_t m1, const void* Y1, int64_t R,
@@ -365,6 +378,15 @@ extern "C" int idl_gaussian_stage(idl_ctx* ctx, const double* Omega, int64_t m2,
       !Y1 || !Y2 || precision < 0 || precision > 3 || (dtype == IDL_F64 && precision != IDL_PREC_FP64))
     return fail(ctx, IDL_EINVAL, "gaussian_stage: bad arguments");
   return launch_gaussian(ctx, Omega, m2, m1, Y1, R, ldy1, dtype, precision, Y2, ldy2);
+}
+
+extern "C" int idl_gaussian_stage_colmajor(idl_ctx* ctx, const double* Omega, int64_t m2, int64_t m1, const float* Y1,
+                                           int64_t R, int64_t ldy1, int precision, float* Y2, int64_t ldy2) {
+  TRY(check_ctx(ctx));
+  if (m2 < 1 || m1 < 1 || R < 1 || ldy1 < m1 || ldy2 < m2 || !Omega || !Y1 || !Y2 ||
+      (precision != IDL_PREC_FP32 && precision != IDL_PREC_BF16X3 && precision != IDL_PREC_BF16))
+    return fail(ctx, IDL_EINVAL, "gaussian_stage_colmajor: bad arguments");
+  return launch_gaussian_tc(ctx, Omega, m2, m1, Y1, R, ldy1, true, precision, Y2, ldy2);
 }
 
 extern "C" int idl_cpqr(idl_ctx* ctx, void* Y2, int64_t m, int64_t R, int64_t ldy2, int dtype, int64_t K, int32_t* J,
@@ -421,9 +443,10 @@ static int check_params(idl_ctx* ctx, const idl_params* p, int dtype, int64_t I,
   return IDL_OK;
 }
 
-// Sketch Y1 (m1 x R, row-major, ld = ldy1) -> J, T, via the Gaussian stage and the QR stage.
+// Sketch Y1 (m1 x R, row-major, ld = ldy1; column-major when y1_cm, which needs the
+// tensor-core Gaussian stage) -> J, T, via the Gaussian stage and the QR stage.
 static int finish_pipeline(idl_ctx* ctx, const idl_params* p, int dtype, void* Y1, int64_t ldy1, int64_t R,
-                           int64_t K, int32_t* J, double* T, idl_info* info) {
+                           int64_t K, int32_t* J, double* T, idl_info* info, bool y1_cm = false) {
   const int es = dtype_size(dtype);
   const int64_t m = p->m2 > 0 ? p->m2 : p->m1;
   const int64_t ld2 = m;
@@ -433,7 +456,11 @@ static int finish_pipeline(idl_ctx* ctx, const idl_params* p, int dtype, void* Y
   if (p->m2 > 0) {
     WS(Om, double, kWsOmega, p->m2 * p->m1);
     STAGE(kStDraw, cuda_check(ctx, launch_draw_gaussian(ctx->stream, p->seed, p->m2, p->m1, Om), "draw gaussian"));
-    STAGE(kStGauss, launch_gaussian(ctx, Om, p->m2, p->m1, Y1, R, ldy1, dtype, p->precision, Y2, ld2));
+    if (y1_cm)
+      STAGE(kStGauss, launch_gaussian_tc(ctx, Om, p->m2, p->m1, (const float*)Y1, R, ldy1, true, p->precision,
+                                         (float*)Y2, ld2));
+    else
+      STAGE(kStGauss, launch_gaussian(ctx, Om, p->m2, p->m1, Y1, R, ldy1, dtype, p->precision, Y2, ld2));
   } else {
     STAGE(kStGauss, launch_transpose_to_colmajor(ctx, Y1, m, R, ldy1, dtype, Y2, ld2));
   }
@@ -554,17 +581,21 @@ extern "C" int id_cp_tensor(idl_ctx* ctx, int N, const int64_t* dims, int64_t R,
     ss[n] = sbuf + off;
     off += dims[n];
   }
-  const int64_t ldy1 = round_up(R, 32);
-  float* Y1 = (float*)ws_get(ctx, kWsY1, sizeof(float) * (size_t)(L * ldy1));
+  // with a Gaussian stage on the tensor cores the sketch is written column-major (each
+  // column contiguous for the FFT block that produces it and for the converter thread
+  // that reads it); otherwise row-major
+  const bool cm = p->m2 > 0 && !ctx->gemm_simt;
+  const int64_t ldy1 = cm ? L : round_up(R, 32);
+  float* Y1 = (float*)ws_get(ctx, kWsY1, sizeof(float) * (size_t)(cm ? R * L : L * ldy1));
   if (!Y1) return IDL_ENOMEM;
-  STAGE(kStSketch, launch_tensorsketch(ctx, N, dims, R, factors, ldf, lam, hs, ss, L, Y1, ldy1));
+  STAGE(kStSketch, launch_tensorsketch(ctx, N, dims, R, factors, ldf, lam, hs, ss, L, Y1, ldy1, cm));
   // J and T on the device for lambda_hat; staged back if the caller passed host pointers
   const bool jdev = is_device_ptr(J), tdev = is_device_ptr(T), ldev = is_device_ptr(lambda_hat);
   int32_t* Jd = J;
   double* Td = T;
   if (!jdev) { Jd = (int32_t*)ws_get(ctx, kWsJ, sizeof(int32_t) * (size_t)K); if (!Jd) return IDL_ENOMEM; }
   if (!tdev) { Td = (double*)ws_get(ctx, kWsT, sizeof(double) * (size_t)(K * (R - K))); if (!Td) return IDL_ENOMEM; }
-  TRY(finish_pipeline(ctx, p, IDL_F32, Y1, ldy1, R, K, Jd, Td, nullptr));
+  TRY(finish_pipeline(ctx, p, IDL_F32, Y1, ldy1, R, K, Jd, Td, nullptr, cm));
   double* lhd = lambda_hat;
   if (!ldev) { lhd = (double*)ws_get(ctx, kWsLamHat, sizeof(double) * (size_t)K); if (!lhd) return IDL_ENOMEM; }
   STAGE(kStCheck, launch_lambda_hat(ctx, lam, Jd, Td, K, R, lhd));

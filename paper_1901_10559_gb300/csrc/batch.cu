@@ -174,7 +174,8 @@ __global__ void __launch_bounds__(kTsMaxThreads, 1) b_sketch_cp_kernel(const BIt
   ITEM_OF_BLOCK(pre, n);
   int logL = 0;
   while ((1LL << logL) < it.m1) ++logL;
-  tensorsketch_block(it.ts, it.R, (int)it.m1, logL, it.lam, it.Y1, it.ldy1, local * 2, tw, sm2);
+  // column-major: column r at Y1 + r * m1 (the Gaussian stage reads each column's K values contiguously)
+  tensorsketch_block(it.ts, it.R, (int)it.m1, logL, it.lam, it.Y1, it.m1, true, local * 2, tw, sm2);
 }
 
 template <int NP>
@@ -193,8 +194,12 @@ __global__ void __launch_bounds__(kTcThreads, 1) b_gemm_kernel(const BItem* __re
   const int sp = (int)(local % it.splits);
   const int kb0 = sp * (int)it.kbpc;
   const int nk = (int)std::min<int64_t>(it.nkb, kb0 + it.kbpc) - kb0;
-  gauss_tc_block<NP>(it.Y1, it.ldy1, it.R, it.m1, it.Bpl, (int)it.NT, (int)it.NT, kb0, nk, mt, 0,
-                     it.part + (int64_t)sp * it.R * it.NT, status, smem_raw);
+  if (it.kind == IDL_ITEM_CP)
+    gauss_tc_block<NP, true>(it.Y1, it.m1, it.R, it.m1, it.Bpl, (int)it.NT, (int)it.NT, kb0, nk, mt, 0,
+                             it.part + (int64_t)sp * it.R * it.NT, status, smem_raw);
+  else
+    gauss_tc_block<NP, false>(it.Y1, it.ldy1, it.R, it.m1, it.Bpl, (int)it.NT, (int)it.NT, kb0, nk, mt, 0,
+                              it.part + (int64_t)sp * it.R * it.NT, status, smem_raw);
 }
 
 __global__ void b_reduce_kernel(const BItem* __restrict__ items, const int64_t* __restrict__ pre, int n) {

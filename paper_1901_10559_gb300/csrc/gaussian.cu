@@ -150,7 +150,7 @@ int launch_gaussian(idl_ctx* ctx, const double* Omega, int64_t m2, int64_t m1, c
   if (dtype == IDL_F64)
     return simt_impl<double>(ctx, Omega, m2, m1, (const double*)Y1, R, ldy1, (double*)Y2, ldy2, 0);
   if (!ctx->gemm_simt)
-    return launch_gaussian_tc(ctx, Omega, m2, m1, (const float*)Y1, R, ldy1, precision, (float*)Y2, ldy2);
+    return launch_gaussian_tc(ctx, Omega, m2, m1, (const float*)Y1, R, ldy1, false, precision, (float*)Y2, ldy2);
   // CUDA-core path (kept for comparison): FP32 FMA, or bf16-rounded operands for IDL_PREC_BF16
   float* om32 = (float*)ws_get(ctx, kWsOmegaConv, sizeof(float) * (size_t)(m2 * m1));
   if (!om32) return IDL_ENOMEM;

@@ -5,7 +5,8 @@
 // rounded up to 16, K = m1 (split over CTAs, partial sums reduced in a fixed
 // order by gauss_reduce_kernel).  Both operands are K-major bf16 in shared
 // memory with the 128-byte swizzle:
-//   * A (Y1^T): every thread loads FP32 Y1 (coalesced along r), splits each
+//   * A (Y1^T): every thread loads FP32 Y1 (row-major Y1: coalesced along r;
+//     column-major Y1: 32 consecutive K values per thread), splits each
 //     value into bf16 planes x = hi + mid + lo (each the bf16 rounding of the
 //     remainder) and stores the planes already transposed into the K-major
 //     swizzled layout -- the conversion and the transpose cost no extra HBM
@@ -43,14 +44,14 @@ __global__ void omega_planes_kernel(const double* __restrict__ Om, int m2, int64
   if (e < (int64_t)nkb * NT * 8) omega_planes_elem<NP>(e, Om, m2, m1, NT, out);
 }
 
-template <int NP>
+template <int NP, bool CM>
 __global__ void __launch_bounds__(kTcThreads, 1)
 gauss_tc_kernel(const float* __restrict__ Y1, int64_t ldy1, int64_t R, int64_t m1, const __nv_bfloat16* __restrict__ Bpl,
                 int NT, int NTc, int kb_per_cta, int nkb, float* __restrict__ part, int* status) {
   extern __shared__ unsigned char smem_raw[];
   const int kb0 = blockIdx.y * kb_per_cta;
   const int nk = min(nkb, kb0 + kb_per_cta) - kb0;
-  gauss_tc_block<NP>(Y1, ldy1, R, m1, Bpl, NT, NTc, kb0, nk, blockIdx.x, blockIdx.z,
+  gauss_tc_block<NP, CM>(Y1, ldy1, R, m1, Bpl, NT, NTc, kb0, nk, blockIdx.x, blockIdx.z,
                      part + (int64_t)blockIdx.y * R * NT, status, smem_raw);
 }
 
@@ -58,7 +59,7 @@ using namespace tc;
 
 template <int NP>
 static int tc_impl(idl_ctx* ctx, const double* Omega, int64_t m2, int64_t m1, const float* Y1, int64_t R, int64_t ldy1,
-                   float* Y2, int64_t ldy2) {
+                   bool y1_cm, float* Y2, int64_t ldy2) {
   using namespace tc;
   const int nkb = (int)cdiv(m1, kBK);
   const int mtiles = (int)cdiv(R, kBM);
@@ -99,7 +100,7 @@ static int tc_impl(idl_ctx* ctx, const double* Omega, int64_t m2, int64_t m1, co
     omega_planes_kernel<NP><<<(unsigned)cdiv(n, 256), 256, 0, ctx->stream>>>(Omega, (int)m2, m1, NT, nkb, Bpl),
         count_launch();
   }
-  auto k = gauss_tc_kernel<NP>;
+  auto k = y1_cm ? gauss_tc_kernel<NP, true> : gauss_tc_kernel<NP, false>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return cuda_check(ctx, e, "gaussian tc attribute");
   dim3 grid((unsigned)mtiles, (unsigned)splits, (unsigned)nz);
@@ -111,12 +112,12 @@ static int tc_impl(idl_ctx* ctx, const double* Omega, int64_t m2, int64_t m1, co
 }
 
 int launch_gaussian_tc(idl_ctx* ctx, const double* Omega, int64_t m2, int64_t m1, const float* Y1, int64_t R,
-                       int64_t ldy1, int precision, float* Y2, int64_t ldy2) {
+                       int64_t ldy1, bool y1_cm, int precision, float* Y2, int64_t ldy2) {
   if (m2 > 256) return fail(ctx, IDL_ELIMIT, "gaussian tc: m2 > 256");
   switch (precision) {
-    case IDL_PREC_BF16: return tc_impl<1>(ctx, Omega, m2, m1, Y1, R, ldy1, Y2, ldy2);
-    case IDL_PREC_BF16X3: return tc_impl<2>(ctx, Omega, m2, m1, Y1, R, ldy1, Y2, ldy2);
-    default: return tc_impl<3>(ctx, Omega, m2, m1, Y1, R, ldy1, Y2, ldy2);
+    case IDL_PREC_BF16: return tc_impl<1>(ctx, Omega, m2, m1, Y1, R, ldy1, y1_cm, Y2, ldy2);
+    case IDL_PREC_BF16X3: return tc_impl<2>(ctx, Omega, m2, m1, Y1, R, ldy1, y1_cm, Y2, ldy2);
+    default: return tc_impl<3>(ctx, Omega, m2, m1, Y1, R, ldy1, y1_cm, Y2, ldy2);
   }
 }
 

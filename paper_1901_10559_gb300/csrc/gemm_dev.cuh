@@ -189,7 +189,10 @@ constexpr int kBSlots = 3;
 // One CTA: rows [mt*128, +128) of D, columns [z*NTc, +NTc), K blocks [kb0, kb0 + nk);
 // partial result rows go to part_base[r * NT + column].  smem_raw: the dynamic
 // shared memory (1 KB alignment slack included by the launcher).
-template <int NP>
+// CM = false: Y1 row-major (Y1[b * ldy1 + r]); CM = true: column-major
+// (Y1[r * ldy1 + b]), each converter thread then reads 32 consecutive K values
+// of its row of D (one 128-byte line when ldy1 is a multiple of 32).
+template <int NP, bool CM = false>
 __device__ __forceinline__ void gauss_tc_block(const float* __restrict__ Y1, int64_t ldy1, int64_t R, int64_t m1,
                                                const __nv_bfloat16* __restrict__ Bpl, int NT, int NTc, int kb0, int nk,
                                                int64_t mt, int z, float* __restrict__ part_base, int* status,
@@ -240,18 +243,31 @@ __device__ __forceinline__ void gauss_tc_block(const float* __restrict__ Y1, int
   if (warp < 8) {
     // ---------------- converters ----------------
     const int m = tid & (kBM - 1);
-    const int kq = tid >> 7;                           // 0 or 1: k-chunks kq, kq+2, kq+4, kq+6
+    // 8-value k-chunks of this thread: kq, kq+2, kq+4, kq+6 (row-major Y1: a warp reads
+    // 32 consecutive columns of one row) or 4kq .. 4kq+3 (column-major Y1)
+    const int kq = tid >> 7;
+    auto kchunk = [&](int c) { return CM ? kq * 4 + c : kq + 2 * c; };
     const bool col_ok = r0 + m < R;
+    const float* ycol = CM && col_ok ? Y1 + (r0 + m) * ldy1 : Y1;
+    const bool cm_vec = CM && (ldy1 & 3) == 0 && (((uintptr_t)Y1) & 15) == 0;
     // two register buffers: the loads of K block i+2 are in flight while block i is converted
     float va[4][8], vb[4][8];
     auto load_block = [&](float (&v)[4][8], int kb) {
 #pragma unroll
       for (int c = 0; c < 4; ++c) {
-        const int kc = kq + 2 * c;
+        const int kc = kchunk(c);
+        const int64_t b0 = (int64_t)kb * kBK + kc * 8;
+        if (CM && cm_vec && col_ok && b0 + 8 <= m1) {
+          const float4 x = __ldcs((const float4*)(ycol + b0));
+          const float4 y = __ldcs((const float4*)(ycol + b0 + 4));
+          v[c][0] = x.x; v[c][1] = x.y; v[c][2] = x.z; v[c][3] = x.w;
+          v[c][4] = y.x; v[c][5] = y.y; v[c][6] = y.z; v[c][7] = y.w;
+        } else {
 #pragma unroll
-        for (int e = 0; e < 8; ++e) {
-          const int64_t b = (int64_t)kb * kBK + kc * 8 + e;
-          v[c][e] = (col_ok && b < m1) ? __ldcs(Y1 + b * ldy1 + r0 + m) : 0.f;
+          for (int e = 0; e < 8; ++e) {
+            const int64_t b = b0 + e;
+            v[c][e] = (col_ok && b < m1) ? __ldcs(CM ? ycol + b : Y1 + b * ldy1 + r0 + m) : 0.f;
+          }
         }
       }
     };
@@ -263,7 +279,7 @@ __device__ __forceinline__ void gauss_tc_block(const float* __restrict__ Y1, int
       unsigned char* As = A + (size_t)s * NP * a_plane;
 #pragma unroll
       for (int c = 0; c < 4; ++c) {
-        const int kc = kq + 2 * c;
+        const int kc = kchunk(c);
         __nv_bfloat16 pl[NP][8];
 #pragma unroll
         for (int e = 0; e < 8; ++e) {

@@ -86,8 +86,9 @@ int launch_gaussian(idl_ctx* ctx, const double* Omega, int64_t m2, int64_t m1, c
 int launch_gaussian_reduce(idl_ctx* ctx, const float* part, int splits, int64_t R, int MP, int64_t m2, float* Y2,
                            int64_t ldy2);
 // gaussian_tc.cu
+// y1_cm: Y1 column-major (column r at Y1 + r * ldy1) instead of row-major
 int launch_gaussian_tc(idl_ctx* ctx, const double* Omega, int64_t m2, int64_t m1, const float* Y1, int64_t R,
-                       int64_t ldy1, int precision, float* Y2, int64_t ldy2);
+                       int64_t ldy1, bool y1_cm, int precision, float* Y2, int64_t ldy2);
 
 // cpqr.cu
 // Extra roles of a QR launch (learned proposal): gate = fallback flag (run only
@@ -124,6 +125,6 @@ int launch_proposal_qr(idl_ctx* ctx, const float* Y2, float* Yf, int64_t m, int6
 const float2* ts_twiddles(idl_ctx* ctx);
 int launch_tensorsketch(idl_ctx* ctx, int N, const int64_t* dims, int64_t R, const void* const* factors,
                         const int64_t* ldf, const double* lambda, const int32_t* const* hs,
-                        const int8_t* const* ss, int64_t L, float* Y, int64_t ldy);
+                        const int8_t* const* ss, int64_t L, float* Y, int64_t ldy, bool colmajor);
 
 }  // namespace idl

@@ -19,10 +19,10 @@ namespace idl {
 
 __global__ void __launch_bounds__(kTsMaxThreads, 1) tensorsketch_kernel(const __grid_constant__ TsArgs a, int64_t R, int L, int logL,
                                                                      const double* __restrict__ lambda,
-                                                                     float* __restrict__ Y, int64_t ldy,
+                                                                     float* __restrict__ Y, int64_t ldy, bool cm,
                                                                      const float2* __restrict__ tw) {
   extern __shared__ __align__(16) float2 sm[];
-  tensorsketch_block(a, R, L, logL, lambda, Y, ldy, (int64_t)blockIdx.x * 2, tw, sm);
+  tensorsketch_block(a, R, L, logL, lambda, Y, ldy, cm, (int64_t)blockIdx.x * 2, tw, sm);
 }
 
 __global__ void ts_twiddle_kernel(float2* tw) {
@@ -48,7 +48,7 @@ const float2* ts_twiddles(idl_ctx* ctx) {
 
 int launch_tensorsketch(idl_ctx* ctx, int N, const int64_t* dims, int64_t R, const void* const* factors,
                         const int64_t* ldf, const double* lambda, const int32_t* const* hs, const int8_t* const* ss,
-                        int64_t L, float* Y, int64_t ldy) {
+                        int64_t L, float* Y, int64_t ldy, bool colmajor) {
   if (N < 1 || N > kTsMaxModes) return fail(ctx, IDL_EINVAL, "tensorsketch: need 1 <= N <= 8");
   if (L < 16 || L > 8192 || (L & (L - 1))) return fail(ctx, IDL_ELIMIT, "tensorsketch: L must be a power of two in [16, 8192]");
   TsArgs a = {};
@@ -68,7 +68,8 @@ int launch_tensorsketch(idl_ctx* ctx, int N, const int64_t* dims, int64_t R, con
   const float2* tw = ts_twiddles(ctx);
   if (!tw) return IDL_ENOMEM;
   tensorsketch_kernel<<<(unsigned)cdiv(R, 2), ts_threads((int)L), smem, ctx->stream>>>(a, R, (int)L, logL, lambda, Y,
-                                                                                      ldy, tw), idl::count_launch();
+                                                                                      ldy, colmajor, tw),
+      idl::count_launch();
   return cuda_check(ctx, cudaGetLastError(), "tensorsketch");
 }
 

@@ -213,9 +213,11 @@ __device__ __forceinline__ void twiddle_entry(int e, float2* tw) {
 }  // namespace ts
 
 // One block: columns r0 and r0 + 1.  sm: ts_smem_bytes(L) of shared memory.
+// cm = false: Y row-major (Y[l * ldy + r]); cm = true: column-major (Y[r * ldy + l]).
 __device__ __forceinline__ void tensorsketch_block(const TsArgs& a, int64_t R, int L, int logL,
                                                    const double* __restrict__ lambda, float* __restrict__ Y,
-                                                   int64_t ldy, int64_t r0, const float2* __restrict__ tw, float2* z) {
+                                                   int64_t ldy, bool cm, int64_t r0, const float2* __restrict__ tw,
+                                                   float2* z) {
   using ts::pad;
   const int t = threadIdx.x, nt = blockDim.x;
   const int T = L / kTsVals;
@@ -268,6 +270,17 @@ __device__ __forceinline__ void tensorsketch_block(const TsArgs& a, int64_t R, i
   // x = conj(FFT(conj W)) / L: column r0 = Re, column r0 + 1 = Im
   const float s0 = (float)(lambda[r0] / (double)L);
   const float s1 = two ? (float)(lambda[r0 + 1] / (double)L) : 0.f;
+  if (cm) {
+    // each column is contiguous: consecutive threads store consecutive l
+    float* y0 = Y + r0 * ldy;
+    float* y1 = y0 + ldy;
+    for (int l = t; l < L; l += nt) {
+      const float2 v = z[pad(l)];
+      y0[l] = v.x * s0;
+      if (two) y1[l] = -v.y * s1;
+    }
+    return;
+  }
   const bool vec = two && ((ldy & 1) == 0) && ((((uintptr_t)(Y + r0)) & 7) == 0);
   for (int l = t; l < L; l += nt) {
     const float2 v = z[pad(l)];

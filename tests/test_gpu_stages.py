@@ -272,6 +272,36 @@ def test_tensorsketch_parity(ctx, dims, R, L):
         assert rel_fro(got[:, r], want[:, r]) <= FP32_TOL, r
 
 
+@pytest.mark.parametrize("dims,R,L,extra", [((1000, 1000, 1000), 101, 8192, 0), ((6, 5, 4), 5, 16, 3),
+                                            ((200,) * 4, 51, 1024, 32), ((37, 41), 10, 64, 1)])
+def test_tensorsketch_colmajor_parity(ctx, dims, R, L, extra):
+    """Column-major output (column r at Y + r*ldy): the oracle's sketch column by
+    column, and the row-major call's values (up to the order of the shared-memory
+    atomic adds that sum colliding entries of a mode's CountSketch)."""
+    facs, lam = cp_factors(dims, R, seed=len(dims) + R + 1)
+    hs, ss = odr.tensorsketch_maps(6, dims, L)
+    want = ots.tensorsketch(facs, lam, hs, ss, L)
+    fd = [dev(np.ascontiguousarray(F.T)) for F in facs]
+    hd = [torch.empty(d, dtype=torch.int32, device="cuda") for d in dims]
+    sd = [torch.empty(d, dtype=torch.int8, device="cuda") for d in dims]
+    for n, d in enumerate(dims):
+        idl.idl_draw_mode(ctx, 6, n, d, L, hd[n], sd[n])
+    ldy = L + extra
+    Yc = torch.full((R, ldy), float("nan"), dtype=torch.float32, device="cuda")
+    idl.idl_tensorsketch(ctx, fd, list(dims), dev(lam), hd, sd, L, Yc, ldy, colmajor=True)
+    Yr = torch.empty((L, R), dtype=torch.float32, device="cuda")
+    idl.idl_tensorsketch(ctx, fd, list(dims), dev(lam), hd, sd, L, Yr, R)
+    got = host(Yc)[:, :L].T
+    rows = host(Yr)
+    for r in range(R):
+        assert rel_fro(got[:, r], rows[:, r]) <= FP32_TOL, r
+    for r in range(R):
+        assert rel_fro(got[:, r], want[:, r]) <= FP32_TOL, r
+    if extra:
+        assert np.all(np.isnan(host(Yc)[:, L:]))      # the padding is not written
+    assert ctx.sync() == idl.IDL_OK
+
+
 def test_lambda_hat_parity(ctx):
     rng = np.random.default_rng(3)
     K, R = 7, 40
@@ -306,6 +336,37 @@ def test_gaussian_tc_shapes_and_simt_agreement(ctx, m2, m1, R):
         assert rel_fro(outs[0], want) <= tol, (prec, rel_fro(outs[0], want))
         if prec == idl.PREC_FP32:
             assert rel_fro(outs[0], outs[1]) <= 2 * FP32_TOL
+    assert ctx.sync() == idl.IDL_OK
+
+
+@pytest.mark.parametrize("m2,m1,R,extra", [(60, 8192, 1000, 0), (17, 63, 130, 1), (33, 100, 5, 4),
+                                            (120, 1000, 257, 3), (16, 65, 1, 0), (74, 4096, 300, 0)])
+def test_gaussian_tc_colmajor_input(ctx, m2, m1, R, extra):
+    """Y1 column-major (ragged K tails, unaligned ldy1 -> scalar loads, aligned ->
+    vector loads): the same planes enter the same MMAs in the same K order, so
+    the result is bit-identical to the row-major call, and within the oracle's
+    tolerance of Omega Y1."""
+    rng = np.random.default_rng(m2 + 3 * m1 + R)
+    Y1 = rng.standard_normal((m1, R)).astype(np.float32)
+    Om = torch.empty(m2 * m1, dtype=torch.float64, device="cuda")
+    idl.idl_draw_gaussian(ctx, 8, m2, m1, Om)
+    Omw = odr.gaussian_matrix(8, m2, m1)
+    ldc = m1 + extra
+    Yc = np.zeros((R, ldc), np.float32)
+    Yc[:, :m1] = Y1.T
+    Ycd, Yrd = dev(Yc), dev(Y1)
+    for prec, tol in [(idl.PREC_FP32, FP32_TOL), (idl.PREC_BF16X3, 2e-5), (idl.PREC_BF16, 1e-5)]:
+        Y2c = torch.full((R * m2,), float("nan"), dtype=torch.float32, device="cuda")
+        Y2r = torch.full((R * m2,), float("nan"), dtype=torch.float32, device="cuda")
+        idl.idl_gaussian_stage_colmajor(ctx, Om, m2, m1, Ycd, R, ldc, prec, Y2c, m2)
+        idl.idl_gaussian_stage(ctx, Om, m2, m1, Yrd, R, R, idl.IDL_F32, prec, Y2r, m2)
+        assert torch.equal(Y2c, Y2r), prec
+        want = ogs.gaussian_stage(Omw, Y1, prec)
+        assert rel_fro(colmajor_to_matrix(Y2c, m2, R, m2), want) <= tol, prec
+    with pytest.raises(idl.IdlError):
+        idl.idl_gaussian_stage_colmajor(ctx, Om, m2, m1, Ycd, R, m1 - 1, idl.PREC_FP32, Y2c, m2)
+    with pytest.raises(idl.IdlError):
+        idl.idl_gaussian_stage_colmajor(ctx, Om, m2, m1, Ycd, R, ldc, idl.PREC_FP64, Y2c, m2)
     assert ctx.sync() == idl.IDL_OK
 
 
