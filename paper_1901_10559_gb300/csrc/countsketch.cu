@@ -11,13 +11,13 @@
 //   so the summation order is fixed) with streaming (evict-first) loads, four
 //   rows in flight per thread.
 // CSR:   block = bucket; the bucket's output row lives in shared memory.  Rows
-//   are taken in batches of blockDim.  Short rows' nonzeros are flattened (a
-//   block scan of their lengths and a row-id table), so loads stay coalesced
-//   and lanes full, with four nonzeros in flight per thread; rows of >= 256
-//   nonzeros are streamed by the whole block with 16-byte colidx/vals loads,
-//   two in flight per thread.  Nonzeros are added with shared-memory atomics.
-//   Rows too wide for shared memory use the same kernel with global atomics
-//   on the (pre-zeroed) output row.
+//   are taken in batches of blockDim and read as 16-byte-aligned element quads
+//   (masked to the row), the quads of all rows of a batch flattened into one
+//   stream (a block scan of the rows' quad counts; quad -> row by a table for
+//   short rows, by a binary search over the few long ones), four quads in
+//   flight per thread.  Nonzeros are added with shared-memory atomics.  Rows
+//   too wide for shared memory use the same kernel with global atomics on the
+//   (pre-zeroed) output row.
 #include <cuda_runtime.h>
 
 #include "common.cuh"
@@ -68,43 +68,37 @@ int launch_countsketch_dense(idl_ctx* ctx, const void* A, int64_t I, int64_t R, 
 // ----------------------------------------------------------------------------
 // CSR
 // ----------------------------------------------------------------------------
-constexpr int kCsrThreads = 512;
-
-// Block-wide exclusive scan of one int per thread; returns the exclusive prefix,
-// writes the block total to *total.  scratch: >= 32 ints of shared memory.
-__device__ __forceinline__ int block_excl_scan(int v, int* scratch, int* total) {
+// Block-wide exclusive scans of two ints per thread in one pass; returns the
+// exclusive prefixes, writes the block totals to *total.  scratch: >= 64 ints
+// of shared memory.
+__device__ __forceinline__ int2 block_excl_scan2(int2 v, int* scratch, int2* total) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  int x = v;
+  int2 x = v;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
-    int y = __shfl_up_sync(0xffffffffu, x, o);
-    if (lane >= o) x += y;
+    const int y0 = __shfl_up_sync(0xffffffffu, x.x, o), y1 = __shfl_up_sync(0xffffffffu, x.y, o);
+    if (lane >= o) { x.x += y0; x.y += y1; }
   }
-  if (lane == 31) scratch[wid] = x;
+  if (lane == 31) { scratch[wid] = x.x; scratch[32 + wid] = x.y; }
   __syncthreads();
   if (wid == 0) {
-    int t = lane < nw ? scratch[lane] : 0;
+    int t0 = lane < nw ? scratch[lane] : 0, t1 = lane < nw ? scratch[32 + lane] : 0;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-      int y = __shfl_up_sync(0xffffffffu, t, o);
-      if (lane >= o) t += y;
+      const int y0 = __shfl_up_sync(0xffffffffu, t0, o), y1 = __shfl_up_sync(0xffffffffu, t1, o);
+      if (lane >= o) { t0 += y0; t1 += y1; }
     }
-    if (lane < nw) scratch[lane] = t;
+    if (lane < nw) { scratch[lane] = t0; scratch[32 + lane] = t1; }
   }
   __syncthreads();
-  const int excl = (wid ? scratch[wid - 1] : 0) + x - v;
-  *total = scratch[nw - 1];
+  const int2 excl = make_int2((wid ? scratch[wid - 1] : 0) + x.x - v.x, (wid ? scratch[32 + wid - 1] : 0) + x.y - v.y);
+  *total = make_int2(scratch[nw - 1], scratch[32 + nw - 1]);
   __syncthreads();
   return excl;
 }
 
-constexpr int kLongRow = 256;     // rows at least this long are streamed by the whole block, vectorised
-constexpr int kRowIdCap = 8192;   // short-row nonzeros expanded to a row-id table per batch
-constexpr int kShortUnroll = 4;   // short-row nonzeros in flight per thread
-
-template <typename T> struct CsrVec;
-template <> struct CsrVec<float> { using V = float4; using C = int4; static constexpr int W = 4; };
-template <> struct CsrVec<double> { using V = double2; using C = int2; static constexpr int W = 2; };
+constexpr int kLongRow = 256;     // rows at least this long: quads found by a search over the long rows
+constexpr int kQuadUnroll = 4;    // quads in flight per thread (FP32; FP64: 2)
 
 template <typename T>
 __device__ __forceinline__ void csr_add(T* out, int64_t R, int c, T v, bool neg, int* status) {
@@ -112,7 +106,7 @@ __device__ __forceinline__ void csr_add(T* out, int64_t R, int c, T v, bool neg,
   atomicAdd(out + c, neg ? -v : v);
 }
 
-// largest t in [0, n) with start[t] <= p  (rows of zero length share a start with the next row)
+// largest t in [0, n) with start[t] <= p  (rows without quads share a start with the next row)
 __device__ __forceinline__ int row_of(const int* start, int n, int p) {
   int lo = 0, hi = n - 1;
   while (lo < hi) {
@@ -122,41 +116,84 @@ __device__ __forceinline__ int row_of(const int* start, int n, int p) {
   return lo;
 }
 
+template <int NT>
 struct CsrSmem {
-  int64_t bbeg[kCsrThreads];
-  int bstart[kCsrThreads + 1];
-  int blen[kCsrThreads];
-  int bneg[kCsrThreads];
-  int longs[kCsrThreads];
-  int scratch[32];
+  static constexpr int kRowIdCap = 8 * NT;    // short-row quads expanded to a row-id table per batch
+  int64_t bbeg[NT];
+  int blen[NT];
+  int sqstart[NT];          // first quad of each short row (long rows: the next short row's)
+  int longs[NT];            // batch row of the i-th long row
+  int lqstart[NT];          // first quad of the i-th long row in the long-row part of the stream
+  int scratch[64];
   uint16_t rowid[kRowIdCap];
+  uint8_t bneg[NT];
 };
 
-template <typename T, bool SMEM>
-__global__ void __launch_bounds__(kCsrThreads) cs_csr_kernel(const int64_t* __restrict__ rowptr,
-                                                              const int32_t* __restrict__ colidx,
-                                                              const T* __restrict__ vals, int64_t R, int64_t nnz,
-                                                              const int8_t* __restrict__ s,
-                                                              const int32_t* __restrict__ ptr,
-                                                              const int32_t* __restrict__ rows, T* __restrict__ Y,
-                                                              int64_t ldy, int* status, int vec_ok) {
-  using V = typename CsrVec<T>::V;
-  using C = typename CsrVec<T>::C;
-  constexpr int W = CsrVec<T>::W;
+// Elements q .. q+3 of colidx / vals into c, v (only [lo, hi) loaded when the quad
+// cannot be read with 16-byte loads).
+template <typename T>
+__device__ __forceinline__ void load_quad(const int32_t* __restrict__ colidx, const T* __restrict__ vals, int64_t q,
+                                          int lo, int hi, bool vec, int (&c)[4], T (&v)[4]) {
+  if (vec) {
+    const int4 ci = __ldcs(reinterpret_cast<const int4*>(colidx + q));
+    c[0] = ci.x; c[1] = ci.y; c[2] = ci.z; c[3] = ci.w;
+    if constexpr (sizeof(T) == 4) {
+      const float4 vi = __ldcs(reinterpret_cast<const float4*>(vals + q));
+      v[0] = vi.x; v[1] = vi.y; v[2] = vi.z; v[3] = vi.w;
+    } else {
+      const double2 v0 = __ldcs(reinterpret_cast<const double2*>(vals + q));
+      const double2 v1 = __ldcs(reinterpret_cast<const double2*>(vals + q + 2));
+      v[0] = v0.x; v[1] = v0.y; v[2] = v1.x; v[3] = v1.y;
+    }
+  } else {
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const bool in = j >= lo && j < hi;
+      c[j] = in ? __ldcs(colidx + q + j) : 0;
+      v[j] = in ? __ldcs(vals + q + j) : T(0);
+    }
+  }
+}
+
+// One block per bucket b: Y[b, :] = sum over the bucket's rows r of s[r] * A[r, :].
+// The rows are taken in batches of NT (one row per thread).  Every row is read as
+// the element quads that cover it (quad k of a row starting at element beg:
+// elements 4*floor(beg/4) + 4k .. + 3, masked to the row), with 16-byte loads of
+// colidx and vals when both arrays are 16-byte aligned and the quad ends inside
+// them.  The quads of a batch form one stream -- short rows first (quad -> row by
+// a table), then long rows (by a binary search over the few long rows) -- and
+// thread t takes quads t, t + NT, t + 2 NT, ..., U of them into registers at a
+// time, then adds their elements with shared-memory atomics into the output row
+// (SMEM), or with global atomics into the pre-zeroed output row (rows too wide
+// for shared memory).
+// Measured on the sparse workload (1e6 x 1e4, 1.1e8 nonzeros, 3600 buckets):
+// without the atomics the loop streams colidx / vals at ~6 TB/s; the atomics
+// (about 4 lanes per clock per SM) do not overlap with the loads -- a cp.async
+// ring of three quads per thread, double-buffered registers and bank-rotated
+// lanes were each slower, as were 256-thread blocks (four buckets per SM).
+template <typename T, bool SMEM, int NT>
+__global__ void __launch_bounds__(NT, 1024 / NT) cs_csr_kernel(const int64_t* __restrict__ rowptr,
+                                                                const int32_t* __restrict__ colidx,
+                                                                const T* __restrict__ vals, int64_t R, int64_t nnz,
+                                                                const int8_t* __restrict__ s,
+                                                                const int32_t* __restrict__ ptr,
+                                                                const int32_t* __restrict__ rows, T* __restrict__ Y,
+                                                                int64_t ldy, int* status, int vec_ok) {
+  using Sm = CsrSmem<NT>;
+  constexpr int U = sizeof(T) == 4 ? kQuadUnroll : 2;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  CsrSmem& sm = *reinterpret_cast<CsrSmem*>(smem_raw);
-  T* acc = (T*)(smem_raw + round_up((int64_t)sizeof(CsrSmem), 16));
+  Sm& sm = *reinterpret_cast<Sm*>(smem_raw);
+  T* acc = (T*)(smem_raw + round_up((int64_t)sizeof(Sm), 16));
   const int tid = threadIdx.x;
   const int64_t b = blockIdx.x;
   T* yrow = Y + b * ldy;
   T* out = SMEM ? acc : yrow;
-  if (SMEM) {
-    for (int64_t c = tid; c < R; c += blockDim.x) acc[c] = T(0);
-  }
-  __syncthreads();
   const int a0 = ptr[b], a1 = ptr[b + 1];
-  for (int base = a0; base < a1; base += kCsrThreads) {
-    const int n = min(kCsrThreads, a1 - base);
+  if (SMEM) {
+    for (int64_t c = tid; c < R; c += NT) acc[c] = T(0);
+  }
+  for (int base = a0; base < a1; base += NT) {
+    const int n = min(NT, a1 - base);
     int len = 0, neg = 0;
     int64_t beg = 0;
     if (tid < n) {
@@ -168,107 +205,106 @@ __global__ void __launch_bounds__(kCsrThreads) cs_csr_kernel(const int64_t* __re
       neg = s[r] < 0;
     }
     const int is_long = len >= kLongRow;
-    int total, nlong;
-    const int excl = block_excl_scan(is_long ? 0 : len, sm.scratch, &total);
-    const int lpos = block_excl_scan(is_long, sm.scratch, &nlong);
-    if (tid < n) { sm.bbeg[tid] = beg; sm.bstart[tid] = excl; sm.blen[tid] = len; sm.bneg[tid] = neg; }
-    if (is_long) sm.longs[lpos] = tid;
-    if (tid == 0) sm.bstart[n] = total;
-    const bool expand = total <= kRowIdCap;
-    if (expand && tid < n && !is_long)
-      for (int j = 0; j < len; ++j) sm.rowid[excl + j] = (uint16_t)tid;
+    const int nq = len > 0 ? (int)(((beg + len + 3) >> 2) - (beg >> 2)) : 0;
+    int2 tot;
+    const int2 ex = block_excl_scan2(make_int2(is_long ? 0 : nq, is_long ? nq : 0), sm.scratch, &tot);
+    const int squads = tot.x, nquads = tot.x + tot.y;
+    // rank of each long row among the batch's long rows
+    const unsigned bal = __ballot_sync(0xffffffffu, is_long);
+    if ((tid & 31) == 0) sm.scratch[tid >> 5] = __popc(bal);
+    if (tid < n) { sm.bbeg[tid] = beg; sm.blen[tid] = len; sm.bneg[tid] = neg; }
+    sm.sqstart[tid] = ex.x;
     __syncthreads();
-    // short rows: flattened nonzeros, kShortUnroll independent loads per thread
-    for (int p0 = tid; p0 < total; p0 += kCsrThreads * kShortUnroll) {
-      int cc[kShortUnroll], ng[kShortUnroll];
-      T vv[kShortUnroll];
+    int nlong = 0, lpos = __popc(bal & ((1u << (tid & 31)) - 1));
 #pragma unroll
-      for (int u = 0; u < kShortUnroll; ++u) {
-        const int p = p0 + u * kCsrThreads;
-        cc[u] = -1;
-        if (p < total) {
-          const int t = expand ? (int)sm.rowid[p] : row_of(sm.bstart, n, p);
-          const int64_t q = sm.bbeg[t] + (p - sm.bstart[t]);
-          cc[u] = __ldcs(colidx + q);
-          vv[u] = __ldcs(vals + q);
-          ng[u] = sm.bneg[t];
-        }
-      }
-#pragma unroll
-      for (int u = 0; u < kShortUnroll; ++u)
-        if (p0 + u * kCsrThreads < total) csr_add(out, R, cc[u], vv[u], ng[u] != 0, status);
+    for (int w = 0; w < NT / 32; ++w) {
+      const int c = sm.scratch[w];
+      if (w < (tid >> 5)) lpos += c;
+      nlong += c;
     }
-    // long rows: the whole block streams each one with 16-byte loads
-    for (int li = 0; li < nlong; ++li) {
-      const int t = sm.longs[li];
-      const int64_t q0 = sm.bbeg[t];
-      const int L = sm.blen[t];
-      const bool ngt = sm.bneg[t] != 0;
-      const int head = vec_ok ? min(L, (int)((W - (q0 % W)) % W)) : L;
-      if (tid < head) csr_add(out, R, __ldcs(colidx + q0 + tid), __ldcs(vals + q0 + tid), ngt, status);
-      const int64_t qb = q0 + head;
-      const int nvec = (L - head) / W;
-      const C* cv = reinterpret_cast<const C*>(colidx + qb);
-      const V* vv = reinterpret_cast<const V*>(vals + qb);
-      for (int vi = tid; vi < nvec; vi += 2 * kCsrThreads) {
-        const bool two = vi + kCsrThreads < nvec;
-        const C c0 = __ldcs(cv + vi);
-        const V v0 = __ldcs(vv + vi);
-        C c1;
-        V v1;
-        if (two) { c1 = __ldcs(cv + vi + kCsrThreads); v1 = __ldcs(vv + vi + kCsrThreads); }
-        if constexpr (W == 4) {
-          csr_add(out, R, c0.x, v0.x, ngt, status); csr_add(out, R, c0.y, v0.y, ngt, status);
-          csr_add(out, R, c0.z, v0.z, ngt, status); csr_add(out, R, c0.w, v0.w, ngt, status);
-          if (two) {
-            csr_add(out, R, c1.x, v1.x, ngt, status); csr_add(out, R, c1.y, v1.y, ngt, status);
-            csr_add(out, R, c1.z, v1.z, ngt, status); csr_add(out, R, c1.w, v1.w, ngt, status);
-          }
-        } else {
-          csr_add(out, R, c0.x, v0.x, ngt, status); csr_add(out, R, c0.y, v0.y, ngt, status);
-          if (two) { csr_add(out, R, c1.x, v1.x, ngt, status); csr_add(out, R, c1.y, v1.y, ngt, status); }
+    if (is_long) { sm.longs[lpos] = tid; sm.lqstart[lpos] = squads + ex.y; }
+    const bool expand = squads <= Sm::kRowIdCap;
+    if (expand && !is_long)
+      for (int j = 0; j < nq; ++j) sm.rowid[ex.x + j] = (uint16_t)tid;
+    __syncthreads();
+    // quad p of the stream: first element q, valid elements [lo, hi), row sign
+    auto locate = [&](int p, int64_t& q, int& lo, int& hi, bool& ng) {
+      int t, k;
+      if (p < squads) {
+        t = expand ? (int)sm.rowid[p] : row_of(sm.sqstart, n, p);
+        k = p - sm.sqstart[t];
+      } else {
+        const int li = row_of(sm.lqstart, nlong, p);
+        t = sm.longs[li];
+        k = p - sm.lqstart[li];
+      }
+      const int64_t b0 = sm.bbeg[t], b1 = b0 + sm.blen[t];
+      q = ((b0 >> 2) + k) << 2;
+      lo = b0 > q ? (int)(b0 - q) : 0;
+      hi = b1 - q < 4 ? (int)(b1 - q) : 4;
+      ng = sm.bneg[t] != 0;
+    };
+    for (int p0 = tid; p0 < nquads; p0 += NT * U) {
+      int cq[U][4], lo[U], hi[U];
+      T vq[U][4];
+      bool ngq[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int p = p0 + u * NT;
+        lo[u] = 4;
+        hi[u] = 0;
+        ngq[u] = false;
+        if (p < nquads) {
+          int64_t q;
+          locate(p, q, lo[u], hi[u], ngq[u]);
+          load_quad(colidx, vals, q, lo[u], hi[u], vec_ok && q + 4 <= nnz, cq[u], vq[u]);
         }
       }
-      const int rem = (L - head) - nvec * W;
-      if (tid < rem) {
-        const int64_t q = qb + (int64_t)nvec * W + tid;
-        csr_add(out, R, __ldcs(colidx + q), __ldcs(vals + q), ngt, status);
-      }
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+          if (j >= lo[u] && j < hi[u]) csr_add(out, R, cq[u][j], vq[u][j], ngq[u], status);
     }
     __syncthreads();
   }
   if (SMEM) {
-    for (int64_t c = tid; c < R; c += blockDim.x) yrow[c] = acc[c];
+    for (int64_t c = tid; c < R; c += NT) yrow[c] = acc[c];
   }
 }
 
-static size_t csr_smem_header() { return (size_t)round_up((int64_t)sizeof(CsrSmem), 16); }
+template <typename T, int NT>
+static int csr_launch(idl_ctx* ctx, const int64_t* rowptr, const int32_t* colidx, const T* vals, int64_t R,
+                      int64_t nnz, const int8_t* s, const int32_t* ptr, const int32_t* rows, int64_t L, T* Y,
+                      int64_t ldy, int vec_ok) {
+  const size_t head = (size_t)round_up((int64_t)sizeof(CsrSmem<NT>), 16);
+  const size_t want = head + sizeof(T) * (size_t)R;
+  if (want <= (size_t)ctx->smem_optin) {
+    auto k = cs_csr_kernel<T, true, NT>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)want);
+    if (e != cudaSuccess) return cuda_check(ctx, e, "csr smem attribute");
+    k<<<(unsigned)L, NT, want, ctx->stream>>>(rowptr, colidx, vals, R, nnz, s, ptr, rows, Y, ldy, ctx->d_status,
+                                              vec_ok), idl::count_launch();
+  } else {
+    cudaError_t e = cudaMemset2DAsync(Y, ldy * sizeof(T), 0, R * sizeof(T), L, ctx->stream);
+    if (e != cudaSuccess) return cuda_check(ctx, e, "csr zero");
+    auto k = cs_csr_kernel<T, false, NT>;
+    e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)head);
+    if (e != cudaSuccess) return cuda_check(ctx, e, "csr smem attribute");
+    k<<<(unsigned)L, NT, head, ctx->stream>>>(rowptr, colidx, vals, R, nnz, s, ptr, rows, Y, ldy, ctx->d_status,
+                                              vec_ok), idl::count_launch();
+  }
+  return cuda_check(ctx, cudaGetLastError(), "countsketch csr");
+}
 
 template <typename T>
 static int csr_impl(idl_ctx* ctx, const int64_t* rowptr, const int32_t* colidx, const T* vals, int64_t R, int64_t nnz,
                     const int8_t* s, const int32_t* ptr, const int32_t* rows, int64_t L, T* Y, int64_t ldy) {
-  const size_t head = csr_smem_header();
-  const size_t want = head + sizeof(T) * (size_t)R;
   if (L > 0x7fffffffLL) return fail(ctx, IDL_ELIMIT, "countsketch csr: too many buckets");
-  // a batch of kCsrThreads rows is flattened with int offsets: bound the row width
+  // a batch's quads are counted in int: bound the row width
   if (R > 4000000) return fail(ctx, IDL_ELIMIT, "countsketch csr: R > 4e6");
   const int vec_ok = ((uintptr_t)colidx % 16 == 0) && ((uintptr_t)vals % 16 == 0);
-  if (want <= (size_t)ctx->smem_optin) {
-    auto k = cs_csr_kernel<T, true>;
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)want);
-    if (e != cudaSuccess) return cuda_check(ctx, e, "csr smem attribute");
-    k<<<(unsigned)L, kCsrThreads, want, ctx->stream>>>(rowptr, colidx, vals, R, nnz, s, ptr, rows, Y, ldy,
-                                                       ctx->d_status, vec_ok), idl::count_launch();
-  } else {
-    cudaError_t e = cudaMemset2DAsync(Y, ldy * sizeof(T), 0, R * sizeof(T), L, ctx->stream);
-    if (e != cudaSuccess) return cuda_check(ctx, e, "csr zero");
-    auto k = cs_csr_kernel<T, false>;
-    e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)head);
-    if (e != cudaSuccess) return cuda_check(ctx, e, "csr smem attribute");
-    k<<<(unsigned)L, kCsrThreads, head, ctx->stream>>>(rowptr, colidx, vals, R, nnz, s, ptr, rows, Y, ldy,
-                                                       ctx->d_status, vec_ok), idl::count_launch();
-  }
-  return cuda_check(ctx, cudaGetLastError(), "countsketch csr");
+  return csr_launch<T, 512>(ctx, rowptr, colidx, vals, R, nnz, s, ptr, rows, L, Y, ldy, vec_ok);
 }
 
 int launch_countsketch_csr(idl_ctx* ctx, const int64_t* rowptr, const int32_t* colidx, const void* vals, int64_t I,

@@ -24,12 +24,12 @@ struct idl_ctx {
   struct Buf { void* p = nullptr; size_t bytes = 0; };
   std::vector<Buf> slots;
   int last_cluster = 0;
-  int gemm_simt = 0;
+  int gemm_simt = 0;           // 1: Gaussian stage on CUDA cores instead of tcgen05 (comparison / tests)
   int gemm_sync_loads = 0;     // 1: Gaussian tc stage loads Y1 through registers (comparison / tests)
   int cpqr_smem_only = 0;      // 1: always use the shared-memory QR kernel (comparison / tests)
   idl_batch_state* batch = nullptr;   // batch graphs and tuning table
   int batch_no_graph = 0;      // 1: run batches without graph capture (tests)
-  int batch_no_tune = 0;       // 1: skip the first-call tuning runs (tests)           // 1: Gaussian stage on CUDA cores instead of tcgen05 (comparison / tests)
+  int batch_no_tune = 0;       // 1: skip the first-call tuning runs (tests)
   void* ts_tw = nullptr;       // FFT twiddle table of the TensorSketch kernels (built on first use)
   float* mlp = nullptr;        // proposal MLP: FP32 master weights | Adam first moments | second moments
   bool mlp_ready = false;

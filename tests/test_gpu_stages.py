@@ -128,6 +128,76 @@ def test_countsketch_csr_parity(ctx, dtype, I, R, L, density):
     assert ctx.sync() == idl.IDL_OK
 
 
+@pytest.mark.parametrize("dtype,offset,R,L", [("f32", 0, 3000, 40), ("f32", 1, 3000, 40), ("f64", 0, 2500, 33),
+                                              ("f64", 1, 2500, 33), ("f32", 3, 20000, 7),
+                                              ("f32", 1, 60000, 5)])
+def test_countsketch_csr_long_rows(ctx, dtype, offset, R, L):
+    """Rows of 256 .. R nonzeros (read as masked 16-byte quads) mixed with short
+    and empty rows; the last row is long and nnz is not a multiple of 4; with
+    offset > 0 colidx and vals start off a 16-byte boundary (scalar loads)."""
+    rng = np.random.default_rng(R + offset)
+    npdt = np.float32 if dtype == "f32" else np.float64
+    I = 400
+    lens = np.where(rng.random(I) < 0.15, rng.integers(256, R + 1, I), rng.integers(0, 20, I))
+    lens[-1] = R - 1 if (R - 1) % 4 else R - 2
+    cols = np.concatenate([rng.permutation(R)[:n] for n in lens]).astype(np.int32)
+    if cols.size % 4 == 0:
+        lens[-1] -= 1
+        cols = cols[:-1]
+    vals = rng.standard_normal(cols.size).astype(npdt)
+    rowptr = np.concatenate([[0], np.cumsum(lens)]).astype(np.int64)
+    nnz = int(rowptr[-1])
+    assert nnz % 4 != 0
+    cbuf = torch.zeros(nnz + offset, dtype=torch.int32, device="cuda")
+    vbuf = torch.zeros(nnz + offset, dtype=torch.float32 if dtype == "f32" else torch.float64, device="cuda")
+    cbuf[offset:] = dev(cols)
+    vbuf[offset:] = dev(vals)
+    h, s, ptr, rows = _draw(ctx, 31, I, L, True)
+    Y = torch.empty((L, R), dtype=vbuf.dtype, device="cuda")
+    idl.idl_countsketch_csr(ctx, dev(rowptr), cbuf[offset:], vbuf[offset:], I, R, nnz,
+                            idl.IDL_F32 if dtype == "f32" else idl.IDL_F64, h, s, ptr, rows, L, Y, R)
+    hw, sw = odr.countsketch_maps(31, I, L, True)
+    want = ocs.countsketch_csr(rowptr, cols, vals, R, hw, sw, L)
+    tol = FP32_TOL if dtype == "f32" else FP64_TOL
+    assert rel_fro(host(Y), want) <= tol
+    assert ctx.sync() == idl.IDL_OK
+
+
+@pytest.mark.parametrize("dtype,R", [("f32", 3000), ("f64", 1000), ("f32", 10000)])
+def test_countsketch_csr_full_rows(ctx, dtype, R):
+    """Rows with nnz == R (every quad of them read with 16-byte loads): stored in
+    column order, permuted, or with a repeated column, mixed with short rows."""
+    rng = np.random.default_rng(R)
+    npdt = np.float32 if dtype == "f32" else np.float64
+    I, L = 300, 37
+    kind = rng.choice(4, size=I, p=[0.75, 0.15, 0.05, 0.05])    # short, sorted, permuted, repeated column
+    cols_l = []
+    for k in kind:
+        if k == 0:
+            cols_l.append(np.sort(rng.permutation(R)[:rng.integers(0, 30)]))
+        elif k == 1:
+            cols_l.append(np.arange(R))
+        elif k == 2:
+            cols_l.append(rng.permutation(R))
+        else:
+            c = np.arange(R)
+            c[rng.integers(1, R)] = c[0]
+            cols_l.append(c)
+    lens = np.array([len(c) for c in cols_l])
+    cols = np.concatenate(cols_l).astype(np.int32)
+    vals = rng.standard_normal(cols.size).astype(npdt)
+    rowptr = np.concatenate([[0], np.cumsum(lens)]).astype(np.int64)
+    h, s, ptr, rows = _draw(ctx, 41, I, L, True)
+    hw, sw = odr.countsketch_maps(41, I, L, True)
+    want = ocs.countsketch_csr(rowptr, cols, vals, R, hw, sw, L)
+    tol = FP32_TOL if dtype == "f32" else FP64_TOL
+    Y = torch.empty((L, R), dtype=torch.float32 if dtype == "f32" else torch.float64, device="cuda")
+    idl.idl_countsketch_csr(ctx, dev(rowptr), dev(cols), dev(vals), I, R, cols.size,
+                            idl.IDL_F32 if dtype == "f32" else idl.IDL_F64, h, s, ptr, rows, L, Y, R)
+    assert rel_fro(host(Y), want) <= tol
+    assert ctx.sync() == idl.IDL_OK
+
+
 def test_countsketch_csr_flags_bad_column(ctx):
     c = random_csr(1000, 50, 0.1, seed=1)
     cols = c.colidx.copy()
