@@ -278,7 +278,13 @@ static int reg_cpqr(idl_ctx* ctx, const T* Yin, T* Yout, int64_t m, int64_t R, i
   for (int CS = x.max_cs; CS >= 1; CS >>= 1) {
     const int nc = (int)cdiv(R, CS);
 #define TRY_CFG(V, TPC) if (reg_try<T, V, TPC>(ctx, Yin, Yout, m, R, ld, K, J, rnorm, CS, nc, x, &rc)) { *launched = rc == IDL_OK; return rc; }
-    // most lanes per column first (shortest serial chain per step)
+    // FP64: fewest lanes per column first.  GB300's FP64 pipe retires about two
+    // lanes per clock per SM, so the per-step group reductions (log2 TPC adds on
+    // all TPC lanes of a column) dominate when a column is spread over many lanes
+    // (measured, 30 x 2000 sketch, 20 pivots: 431 us with 8 lanes per column,
+    // 180 us with one lane and 32 values (some spilled), 156 us with two lanes).
+    if constexpr (sizeof(T) == 8) { TRY_CFG(16, 1) TRY_CFG(16, 2) TRY_CFG(32, 1) TRY_CFG(32, 2) TRY_CFG(32, 4) }
+    // FP32: most lanes per column first (shortest serial chain per step)
     TRY_CFG(8, 32) TRY_CFG(8, 16) TRY_CFG(8, 8) TRY_CFG(16, 8) TRY_CFG(8, 4) TRY_CFG(16, 4) TRY_CFG(32, 4)
     TRY_CFG(16, 2) TRY_CFG(32, 2) TRY_CFG(16, 1) TRY_CFG(32, 1)
     if constexpr (sizeof(T) == 4) { TRY_CFG(64, 4) TRY_CFG(64, 2) TRY_CFG(64, 1) TRY_CFG(96, 1) TRY_CFG(128, 1) }

@@ -17,6 +17,28 @@ __device__ __forceinline__ bool better(T va, int ia, T vb, int ib) {
   return va > vb || (va == vb && ia < ib && ia >= 0) || (ib < 0 && ia >= 0);
 }
 
+// Pivot search key of a remaining squared norm.  FP32: the value itself.  FP64:
+// the bit pattern as a signed integer (non-negative doubles order like their
+// bits), so the block / cluster argmax runs on the integer pipes -- GB300's
+// FP64 pipe retires about two lanes per clock per SM.  Retired columns and NaN
+// norms get -1 (never chosen).
+template <typename T> struct PivKey;
+template <> struct PivKey<float> {
+  using K = float;
+  static __device__ __forceinline__ K of(float v, bool ok) { return ok && v >= 0.f ? v : -1.f; }
+  static __device__ __forceinline__ float store(K k) { return k; }
+  static __device__ __forceinline__ K load(float v) { return v; }
+};
+template <> struct PivKey<double> {
+  using K = long long;
+  static __device__ __forceinline__ K of(double v, bool ok) {
+    const long long b = __double_as_longlong(v);
+    return ok && b >= 0 && (b & 0x7fffffffffffffffLL) <= 0x7ff0000000000000LL ? b : -1LL;
+  }
+  static __device__ __forceinline__ double store(K k) { return __longlong_as_double(k); }
+  static __device__ __forceinline__ K load(double v) { return __double_as_longlong(v); }
+};
+
 __device__ __forceinline__ float group_sum(float v, int tpc) {
   for (int o = tpc >> 1; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
@@ -35,14 +57,15 @@ __device__ __forceinline__ int vslot(int i) { return (i % TPC) * V + i / TPC; }
 
 // sum_j v_j y_j over a thread's rows (four partial sums).  Slots j < jskip
 // (a multiple of 4, the same for every lane) hold rows above the current
-// step, where v is zero: those chunks are skipped (warp-uniform branches).
+// step, where v is zero, and slots j >= jend (a multiple of 4) rows past m for
+// every lane: those chunks are skipped (warp-uniform branches).
 template <typename T, int V>
-__device__ __forceinline__ T house_dot(const T* __restrict__ vrow, const T (&y)[V], int jskip) {
+__device__ __forceinline__ T house_dot(const T* __restrict__ vrow, const T (&y)[V], int jskip, int jend) {
   static_assert(V % 4 == 0, "V must be a multiple of 4");
   T d0 = T(0), d1 = T(0), d2 = T(0), d3 = T(0);
 #pragma unroll
   for (int j = 0; j < V; j += 4) {
-    if (j < jskip) continue;
+    if (j < jskip || j >= jend) continue;
     if constexpr (sizeof(T) == 4) {
       const float4 w = *reinterpret_cast<const float4*>(vrow + j);
       d0 = fma(w.x, y[j], d0); d1 = fma(w.y, y[j + 1], d1); d2 = fma(w.z, y[j + 2], d2); d3 = fma(w.w, y[j + 3], d3);
@@ -57,13 +80,14 @@ __device__ __forceinline__ T house_dot(const T* __restrict__ vrow, const T (&y)[
 
 // y -= d v over a thread's rows; returns the thread's part of the trailing
 // norm^2 over rows with slot index j >= jt (four partial sums); chunks below
-// jskip are left alone (v is zero there and jt > jskip)
+// jskip or from jend on are left alone (v is zero there, jt > jskip, and the
+// rows past m stay zero)
 template <typename T, int V>
-__device__ __forceinline__ T house_update(const T* __restrict__ vrow, T (&y)[V], T d, int jt, int jskip) {
+__device__ __forceinline__ T house_update(const T* __restrict__ vrow, T (&y)[V], T d, int jt, int jskip, int jend) {
   T s0 = T(0), s1 = T(0), s2 = T(0), s3 = T(0);
 #pragma unroll
   for (int j = 0; j < V; j += 4) {
-    if (j < jskip) continue;
+    if (j < jskip || j >= jend) continue;
     T w0, w1, w2, w3;
     if constexpr (sizeof(T) == 4) {
       const float4 w = *reinterpret_cast<const float4*>(vrow + j);
@@ -88,6 +112,8 @@ __device__ __forceinline__ T house_update(const T* __restrict__ vrow, T (&y)[V],
 // first slot chunk (multiple of 4) that can hold rows >= t for some lane of a
 // TPC-lane group: rows gl + TPC j < t for all gl when TPC (j + 4) <= t
 __device__ __forceinline__ int skip_slots(int t, int tpc) { return (t / tpc) & ~3; }
+// end of the slot chunks that hold some row < m for some lane
+__device__ __forceinline__ int end_slots(int m, int tpc) { return ((m + tpc - 1) / tpc + 3) & ~3; }
 
 // ----------------------------------------------------------------------------
 // Register-resident variant (used whenever a cluster shape fits).  Each group
@@ -145,11 +171,14 @@ __device__ __forceinline__ void cpqr_reg_body(const T* __restrict__ Yin, T* __re
   const int col = c0 + g;
   const int64_t scol = own ? (colmap ? (int64_t)colmap[col] : (int64_t)col) : 0;   // column of Yin / Yout
   const int mp = (m + 3) & ~3;
+  const int jend = end_slots(m, tpc);
 
   T* vs = (T*)smem_raw;                                             // V*TPC: v by thread slot, zero outside rows [t, m)
   T* stage = vs + V * TPC;                                          // [2][mp] this CTA's staged candidate column
   Cand<T>* cand = (Cand<T>*)(smem_raw + round_up((int64_t)sizeof(T) * (V * TPC + 2 * mp), 16));   // [2]
-  __shared__ T red_v[32];
+  using PK = PivKey<T>;
+  using KT = typename PK::K;
+  __shared__ KT red_v[32];
   __shared__ int red_i[32];
   __shared__ T s_beta, s_alpha;
   __shared__ int s_p, s_stop;
@@ -189,26 +218,27 @@ __device__ __forceinline__ void cpqr_reg_body(const T* __restrict__ Yin, T* __re
     if (lane == 0 && f != 0.0) atomicAdd(&diag[1], f);
   }
   T nrm2 = own ? nn : T(-1);          // < 0: retired or no column
+  bool alive = own;                   // the column is still a pivot candidate
   int tp = -1;
   T alpha_p = T(0);
   for (int t = 0; t < K; ++t) {
     // A. warp candidates
-    T bv = (gl == 0 && nrm2 >= T(0)) ? nrm2 : T(-1);
-    int bi = (gl == 0 && nrm2 >= T(0)) ? col : -1;
+    KT bv = PK::of(nrm2, gl == 0 && alive);
+    int bi = bv >= KT(0) ? col : -1;
 #pragma unroll
     for (int o = 16; o; o >>= 1) {
-      const T ov = __shfl_xor_sync(0xffffffffu, bv, o);
+      const KT ov = __shfl_xor_sync(0xffffffffu, bv, o);
       const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
       if (better(ov, oi, bv, bi)) { bv = ov; bi = oi; }
     }
     if (lane == 0) { red_v[wid] = bv; red_i[wid] = bi; }
     __syncthreads();
     // B. the CTA's candidate, reduced by every warp (same result everywhere)
-    bv = lane < NW ? red_v[lane] : T(-1);
+    bv = lane < NW ? red_v[lane] : KT(-1);
     bi = lane < NW ? red_i[lane] : -1;
 #pragma unroll
     for (int o = 16; o; o >>= 1) {
-      const T ov = __shfl_xor_sync(0xffffffffu, bv, o);
+      const KT ov = __shfl_xor_sync(0xffffffffu, bv, o);
       const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
       if (better(ov, oi, bv, bi)) { bv = ov; bi = oi; }
     }
@@ -227,22 +257,22 @@ __device__ __forceinline__ void cpqr_reg_body(const T* __restrict__ Yin, T* __re
       }
     }
     if (tid == 0) {
-      cand[t & 1].val = bv;            // published locally; the other CTAs pull it after the barrier
+      cand[t & 1].val = PK::store(bv);   // published locally; the other CTAs pull it after the barrier
       cand[t & 1].idx = bi;
     }
     cluster.sync();
     // C. winner, pivot column, reflection (warp 0)
     if (wid == 0) {
-      T v = T(-1);
+      KT v = KT(-1);
       int ix = -1;
       if (lane < CS) {
         const Cand<T>* rc = cluster.map_shared_rank(cand + (t & 1), (unsigned)lane);
-        v = rc->val;
+        v = PK::load(rc->val);
         ix = rc->idx;
       }
 #pragma unroll
       for (int o = 16; o; o >>= 1) {
-        const T ov = __shfl_xor_sync(0xffffffffu, v, o);
+        const KT ov = __shfl_xor_sync(0xffffffffu, v, o);
         const int oi = __shfl_xor_sync(0xffffffffu, ix, o);
         if (better(ov, oi, v, ix)) { v = ov; ix = oi; }
       }
@@ -303,19 +333,19 @@ __device__ __forceinline__ void cpqr_reg_body(const T* __restrict__ Yin, T* __re
     // D. update
     const int p = s_p;
     const T beta = s_beta;
-    const bool act = own && nrm2 >= T(0);
+    const bool act = alive;
     const bool piv = act && col == p;
     const bool upd = act && !piv;
-    if (piv) { nrm2 = T(-1); tp = t; alpha_p = s_alpha; }
+    if (piv) { nrm2 = T(-1); alive = false; tp = t; alpha_p = s_alpha; }
     // vs is zero outside rows [t, m): no per-row predicates in the dot product and the update
     const T* vrow = vs + gl * V;
     const int jskip = skip_slots(t, tpc);
-    T d = group_sum(house_dot<T, V>(vrow, y, jskip), tpc) * beta;
+    T d = group_sum(house_dot<T, V>(vrow, y, jskip, jend), tpc) * beta;
     if (!upd) d = T(0);
     __syncwarp();   // re-read v below instead of keeping all of it in registers
     // trailing norm over rows > t: rows gl + tpc*j with j >= jt
     const int jt = (t - gl) >= 0 ? (t - gl) / tpc + 1 : 0;
-    const T s2 = group_sum(house_update<T, V>(vrow, y, d, jt, jskip), tpc);
+    const T s2 = group_sum(house_update<T, V>(vrow, y, d, jt, jskip, jend), tpc);
     if (upd) nrm2 = s2;
   }
   cluster.sync();                 // no CTA reads another's staging slot after this point
@@ -459,10 +489,10 @@ __device__ __forceinline__ void cpqr_cta_body(const T* __restrict__ Yin, T* __re
     const bool upd = own && nrm2 >= T(0);
     const T* vrow = vs + gl * V;
     const int jskip = skip_slots(t, tpc);
-    T d = group_sum(house_dot<T, V>(vrow, y, jskip), tpc) * beta;
+    T d = group_sum(house_dot<T, V>(vrow, y, jskip, V), tpc) * beta;
     if (!upd) d = T(0);
     const int jt = (t - gl) >= 0 ? (t - gl) / tpc + 1 : 0;
-    const T s2 = group_sum(house_update<T, V>(vrow, y, d, jt, jskip), tpc);
+    const T s2 = group_sum(house_update<T, V>(vrow, y, d, jt, jskip, V), tpc);
     if (upd) nrm2 = s2;
   }
   T r22t = T(0);
