@@ -301,18 +301,20 @@ __global__ void b_rest_kernel(const BItem* __restrict__ items, const int64_t* __
   if (r < it.R) rest_elem((int)r, sJ, it.K, (int)it.R, it.rest);
 }
 
-__global__ void __launch_bounds__(32 * kRinvWarps) b_rinv_kernel(const BItem* __restrict__ items, const int64_t* __restrict__ pre,
+__global__ void __launch_bounds__(32 * kRinvWarpsDf) b_rinv_kernel(const BItem* __restrict__ items, const int64_t* __restrict__ pre,
                                                      int n) {
   extern __shared__ __align__(16) double shU[];
   ITEM_OF_BLOCK(pre, n);
-  rinv_block<float>(it.Yf, (int)it.m2, it.K, (int)it.R, it.J, it.Rinv, (int)local, (int)(pre[p + 1] - pre[p]), shU);
+  rinv_block_df(it.Yf, (int)it.m2, it.K, (int)it.R, it.J, (float*)(it.Rinv + it.K * it.K), (int)local,
+                (int)(pre[p + 1] - pre[p]), (float*)shU);
 }
 
 __global__ void __launch_bounds__(256) b_tgemm_kernel(const BItem* __restrict__ items, const int64_t* __restrict__ pre,
                                                       int n) {
   extern __shared__ __align__(16) float shf[];
   ITEM_OF_BLOCK(pre, n);
-  tgemm_block_df(it.Yf, (int)it.m2, it.K, (int)it.R, it.Rinv, it.rest, (int)(it.R - it.K), it.T, (int)local, shf);
+  tgemm_block_df(it.Yf, (int)it.m2, it.K, (int)it.R, (const float*)(it.Rinv + it.K * it.K), it.rest, (int)(it.R - it.K),
+                 it.T, (int)local, shf);
 }
 
 __global__ void b_lam_kernel(const BItem* __restrict__ items, const int64_t* __restrict__ pre, int n) {
@@ -585,7 +587,7 @@ static int plan_batch(idl_ctx* ctx, const idl_batch_item* items, int n, const Tu
     o_part[i] = take(sizeof(float) * (size_t)(b.splits * b.R * b.NT));
     o_Y2[i] = take(sizeof(float) * (size_t)(b.R * b.m2));
     o_rest[i] = take(sizeof(int32_t) * (size_t)b.R);
-    o_Rinv[i] = take(sizeof(double) * (size_t)(x.K * x.K));
+    o_Rinv[i] = take(2 * sizeof(double) * (size_t)(x.K * x.K));     // FP64 inverse, then its FP32 pairs
     b.learned = x.params.learned;
     b.C = (int)std::min<int64_t>((x.params.cand_factor > 0 ? x.params.cand_factor : 2) * x.K, x.R);
     b.nsplit = (int)cdiv(x.R, prop::kGramCols);
@@ -673,7 +675,7 @@ static int plan_batch(idl_ctx* ctx, const idl_batch_item* items, int n, const Tu
     nb[kBPSel] = b.learned ? 1 : 0;
     nb[kBPApply] = (b.learned && b.R > b.C) ? std::min<int64_t>(cdiv(b.R - b.C, prop::kApplyThreads / 32), 64) : 0;
     nb[kBRest] = cdiv(b.R, 256);
-    nb[kBRinv] = cdiv(b.K, kRinvWarps);                    // one warp per column
+    nb[kBRinv] = cdiv(b.K, kRinvWarpsDf);                  // one warp per column
     nb[kBTgemm] = cdiv(b.R - b.K, kTNBdf);
     nb[kBLam] = cp ? b.K : 0;
     for (int st = 0; st < kBNumStages; ++st) P.pre[st][i + 1] = P.pre[st][i] + nb[st];
@@ -795,11 +797,11 @@ static int run_stages(idl_ctx* ctx, const BatchPlan& P, const BItem* d_items, co
   BLAUNCH(b_rest_kernel, kBRest, 256, sizeof(int32_t) * (size_t)P.maxK);
   {
     const size_t smem_inv = sizeof(double) * (size_t)P.maxK * (P.maxK + 1);
-    const size_t smem_t = sizeof(float) * (2 * (size_t)P.maxK * P.maxK + (size_t)P.maxK * (kTNBdf + 1));
+    const size_t smem_t = sizeof(float) * (size_t)tgemm_df_floats(P.maxK);
     cudaError_t e = cudaFuncSetAttribute(b_rinv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_inv);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(b_tgemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_t);
     if (e != cudaSuccess) return cuda_check(ctx, e, "batch solve attribute");
-    BLAUNCH(b_rinv_kernel, kBRinv, 32 * kRinvWarps, smem_inv);
+    BLAUNCH(b_rinv_kernel, kBRinv, 32 * kRinvWarpsDf, smem_inv);
     BLAUNCH(b_tgemm_kernel, kBTgemm, 256, smem_t);
   }
   BLAUNCH(b_lam_kernel, kBLam, 256, 0);

@@ -369,16 +369,18 @@ __global__ void rest_kernel(const int32_t* __restrict__ J, int K, int R, int32_t
 
 template <typename T>
 __global__ void __launch_bounds__(256) rinv_kernel(const T* __restrict__ Y, int ld, int K, int R,
-                                                   const int32_t* __restrict__ J, double* __restrict__ Rinv) {
+                                                   const int32_t* __restrict__ J, double* __restrict__ Rinv,
+                                                   float* __restrict__ Rsplit) {
   extern __shared__ __align__(16) double U[];
-  rinv_block<T>(Y, ld, K, R, J, Rinv, blockIdx.x, gridDim.x, U);
+  if constexpr (sizeof(T) == 4) rinv_block_df(Y, ld, K, R, J, Rsplit, blockIdx.x, gridDim.x, (float*)U);
+  else rinv_block<T>(Y, ld, K, R, J, Rinv, blockIdx.x, gridDim.x, U, Rsplit);
 }
 
 __global__ void __launch_bounds__(256) tgemm_df_kernel(const float* __restrict__ Y, int ld, int K, int R,
-                                                      const double* __restrict__ Rinv, const int32_t* __restrict__ rest,
+                                                      const float* __restrict__ Rsplit, const int32_t* __restrict__ rest,
                                                       int nrest, double* __restrict__ Tout) {
   extern __shared__ __align__(16) float shf[];
-  tgemm_block_df(Y, ld, K, R, Rinv, rest, nrest, Tout, blockIdx.x, shf);
+  tgemm_block_df(Y, ld, K, R, Rsplit, rest, nrest, Tout, blockIdx.x, shf);
 }
 
 template <typename T>
@@ -398,31 +400,36 @@ int launch_t_solve(idl_ctx* ctx, const void* Y2, int64_t m, int64_t R, int64_t l
     rest = (int32_t*)ws_get(ctx, kWsRest, sizeof(int32_t) * (size_t)(R > 0 ? R : 1));
     if (!rest) return IDL_ENOMEM;
   }
-  double* Rinv = (double*)ws_get(ctx, kWsRinv, sizeof(double) * (size_t)(K * K));
+  // inv(R11): FP64 (FP64 data) or FP32 pairs (FP32 data)
+  double* Rinv = (double*)ws_get(ctx, kWsRinv, 2 * sizeof(double) * (size_t)(K * K));
   if (!Rinv) return IDL_ENOMEM;
+  float* Rsplit = (float*)(Rinv + K * K);
   rest_kernel<<<(unsigned)cdiv(R, 256), 256, sizeof(int32_t) * (size_t)K, ctx->stream>>>(J, (int)K, (int)R, rest),
       idl::count_launch();
   const size_t smem_inv = sizeof(double) * (size_t)K * (K + 1);
-  const size_t smem_t = sizeof(double) * ((size_t)K * K + (size_t)K * (kTNB + 1));
-  const size_t smem_df = sizeof(float) * (2 * (size_t)K * K + (size_t)K * (kTNBdf + 1));
+  const size_t smem_t = sizeof(double) * ((size_t)K * K + (size_t)K * (kTNB + 1)) + sizeof(int) * kTNB;
+  const size_t smem_df = sizeof(float) * (size_t)tgemm_df_floats((int)K);
   const unsigned inv_blocks = (unsigned)cdiv(K, kRinvWarps);   // one warp per column
+  const unsigned inv_blocks_df = (unsigned)cdiv(K, kRinvWarpsDf);
   cudaError_t e;
   if (dtype == IDL_F32) {
     e = cudaFuncSetAttribute(rinv_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_inv);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(tgemm_df_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_df);
     if (e == cudaSuccess) {
-      rinv_kernel<float><<<inv_blocks, 32 * kRinvWarps, smem_inv, ctx->stream>>>((const float*)Y2, (int)ld, (int)K, (int)R, J, Rinv),
+      rinv_kernel<float><<<inv_blocks_df, 32 * kRinvWarpsDf, smem_inv, ctx->stream>>>((const float*)Y2, (int)ld, (int)K,
+                                                                                (int)R, J, Rinv, Rsplit),
           idl::count_launch();
       if (nrest > 0)
         tgemm_df_kernel<<<(unsigned)cdiv(nrest, kTNBdf), 256, smem_df, ctx->stream>>>(
-            (const float*)Y2, (int)ld, (int)K, (int)R, Rinv, rest, (int)nrest, T), idl::count_launch();
+            (const float*)Y2, (int)ld, (int)K, (int)R, Rsplit, rest, (int)nrest, T), idl::count_launch();
     }
   } else {
     e = cudaFuncSetAttribute(rinv_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_inv);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(tgemm_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_t);
     if (e == cudaSuccess) {
-      rinv_kernel<double><<<inv_blocks, 32 * kRinvWarps, smem_inv, ctx->stream>>>((const double*)Y2, (int)ld, (int)K, (int)R, J,
-                                                                      Rinv), idl::count_launch();
+      rinv_kernel<double><<<inv_blocks, 32 * kRinvWarps, smem_inv, ctx->stream>>>((const double*)Y2, (int)ld, (int)K,
+                                                                                 (int)R, J, Rinv, nullptr),
+          idl::count_launch();
       if (nrest > 0)
         tgemm_kernel<double><<<(unsigned)cdiv(nrest, kTNB), 256, smem_t, ctx->stream>>>(
             (const double*)Y2, (int)ld, (int)K, (int)R, Rinv, rest, (int)nrest, T), idl::count_launch();
