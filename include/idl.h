@@ -249,6 +249,19 @@ int idl_lambda_hat(idl_ctx* ctx, const double* lambda, const int32_t* J, const d
                    int64_t K, int64_t R, double* lambda_hat);
 
 /* ---------------------------------------------------------------------------
+ * CUDA-graph replay of the pipeline calls (id_matrix, id_matrix_csr,
+ * id_cp_tensor).  With on != 0, a call whose arguments (every pointer, size and
+ * the params struct) equal an earlier call's is captured once and then replayed
+ * as one CUDA graph: the same kernels on the same buffers, the draws from the
+ * same seed, with the dependent-launch gaps of the single kernels removed.  Only
+ * calls whose arrays are all device pointers, with info == NULL and without
+ * stage profiling, are replayed; the others run as usual.  Contents of the
+ * buffers may change between calls.  Replays are ordered on the context's
+ * stream like eager calls.  Default off; off also frees the cached graphs.
+ * ------------------------------------------------------------------------- */
+int idl_set_graphs(idl_ctx* ctx, int on);
+
+/* ---------------------------------------------------------------------------
  * Pipelines.  J: K int32, T: K x (R-K) FP64 row-major (see idl_t_solve),
  * lambda_hat: K FP64.  info may be NULL (then the call does not synchronise
  * unless host pointers are involved).

@@ -89,6 +89,7 @@ _SIGS = {
     "idl_debug_fail_alloc": ([_vp, _int], _int),
     "idl_debug_release_workspace": ([_vp], _int),
     "idl_debug_gemm_path": ([_vp, _int], _int),
+    "idl_set_graphs": ([_vp, _int], _int),
     "idl_debug_cpqr_path": ([_vp, _int], _int),
     "idl_draw_countsketch": ([_vp, _u64, _i64, _i64, _int, _vp, _vp], _int),
     "idl_draw_gaussian": ([_vp, _u64, _i64, _i64, _vp], _int),
@@ -287,6 +288,11 @@ def idl_gaussian_stage(ctx, Omega, m2, m1, Y1, R, ldy1, dtype, precision, Y2, ld
 def idl_gaussian_stage_colmajor(ctx, Omega, m2, m1, Y1, R, ldy1, precision, Y2, ldy2):
     return ctx.check(lib().idl_gaussian_stage_colmajor(ctx.ptr, _p(Omega), m2, m1, _p(Y1), R, ldy1, precision,
                                                        _p(Y2), ldy2))
+
+
+def idl_set_graphs(ctx, on=True):
+    """Replay repeated pipeline calls (same arguments) as CUDA graphs."""
+    return ctx.check(lib().idl_set_graphs(ctx.ptr, 1 if on else 0))
 
 
 def idl_cpqr(ctx, Y2, m, R, ldy2, dtype, K, J, rnorm=None):

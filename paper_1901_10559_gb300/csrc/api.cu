@@ -8,7 +8,12 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <initializer_list>
 #include <limits>
+#include <map>
+#include <mutex>
+#include <tuple>
+#include <utility>
 #include <string>
 
 #include <atomic>
@@ -27,6 +32,50 @@ void ctx_add_launches(long long d) { g_launches.fetch_add(d, std::memory_order_r
 int fail(idl_ctx* ctx, int code, const std::string& msg) {
   if (ctx) ctx->err = msg;
   return code;
+}
+
+namespace {
+std::mutex g_attr_mu;
+std::map<std::pair<int, const void*>, int> g_smem_set;                      // (device, kernel) -> bytes allowed
+std::map<std::pair<int, const void*>, bool> g_cluster_np;
+std::map<std::tuple<int, const void*, int, int, size_t>, int> g_cluster_occ;  // (device, kernel, CS, threads, smem)
+}  // namespace
+
+cudaError_t ensure_smem(idl_ctx* ctx, const void* kern, size_t bytes) {
+  std::lock_guard<std::mutex> lk(g_attr_mu);
+  const auto key = std::make_pair(ctx->device, kern);
+  auto it = g_smem_set.find(key);
+  if (it != g_smem_set.end() && (size_t)it->second >= bytes) return cudaSuccess;
+  const cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e == cudaSuccess) g_smem_set[key] = (int)bytes;
+  return e;
+}
+
+cudaError_t ensure_cluster_nonportable(idl_ctx* ctx, const void* kern) {
+  std::lock_guard<std::mutex> lk(g_attr_mu);
+  const auto key = std::make_pair(ctx->device, kern);
+  if (g_cluster_np.count(key)) return cudaSuccess;
+  const cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  if (e == cudaSuccess) g_cluster_np[key] = true;
+  return e;
+}
+
+cudaError_t cluster_occupancy(idl_ctx* ctx, const void* kern, const cudaLaunchConfig_t& cfg, int* nclusters) {
+  int cs = 1;
+  for (unsigned a = 0; a < cfg.numAttrs; ++a)
+    if (cfg.attrs[a].id == cudaLaunchAttributeClusterDimension) cs = (int)cfg.attrs[a].val.clusterDim.x;
+  const auto key = std::make_tuple(ctx->device, kern, cs, (int)cfg.blockDim.x, (size_t)cfg.dynamicSmemBytes);
+  {
+    std::lock_guard<std::mutex> lk(g_attr_mu);
+    auto it = g_cluster_occ.find(key);
+    if (it != g_cluster_occ.end()) { *nclusters = it->second; return cudaSuccess; }
+  }
+  const cudaError_t e = cudaOccupancyMaxActiveClusters(nclusters, kern, &cfg);
+  if (e == cudaSuccess) {
+    std::lock_guard<std::mutex> lk(g_attr_mu);
+    g_cluster_occ[key] = *nclusters;
+  }
+  return e;
 }
 
 int cuda_check(idl_ctx* ctx, cudaError_t e, const char* where) {
@@ -51,6 +100,7 @@ void* ws_get(idl_ctx* ctx, int slot, size_t bytes) {
     b.p = nullptr;
     b.bytes = 0;
   }
+  ++ctx->ws_gen;                          // captured graphs hold the old addresses
   size_t want = bytes + bytes / 8;        // grow with headroom
   want = (want + 255) & ~(size_t)255;
   if (cudaMalloc(&b.p, want) != cudaSuccess) {
@@ -211,6 +261,14 @@ extern "C" int idl_destroy(idl_ctx* ctx) {
   idl_batch_state_free(ctx->batch);
   if (ctx->mlp) cudaFree(ctx->mlp);
   if (ctx->ts_tw) cudaFree(ctx->ts_tw);
+  if (ctx->side) { cudaStreamSynchronize(ctx->side); cudaStreamDestroy(ctx->side); }
+  for (auto& g : ctx->pgraphs)
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+  if (ctx->gstream) { cudaStreamSynchronize(ctx->gstream); cudaStreamDestroy(ctx->gstream); }
+  if (ctx->gev_in) cudaEventDestroy(ctx->gev_in);
+  if (ctx->gev_out) cudaEventDestroy(ctx->gev_out);
+  if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
+  if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
   cudaFree(ctx->d_status);
   cudaFree(ctx->d_diag);
   delete ctx;
@@ -443,10 +501,36 @@ static int check_params(idl_ctx* ctx, const idl_params* p, int dtype, int64_t I,
   return IDL_OK;
 }
 
+// The Gaussian matrix of the pipeline (m2 > 0): drawn on the context's side
+// stream, forked from the main stream here -- after everything already queued,
+// which may still read the Omega workspace -- so that the draw (FP64 Box-Muller,
+// tens of microseconds) overlaps the sketch; finish_pipeline joins it before
+// the Gaussian stage.  *Om = nullptr when m2 = 0.
+static int fork_omega(idl_ctx* ctx, const idl_params* p, double** Om) {
+  *Om = nullptr;
+  if (p->m2 <= 0) return IDL_OK;
+  double* o = (double*)ws_get(ctx, kWsOmega, sizeof(double) * (size_t)(p->m2 * p->m1));
+  if (!o) return IDL_ENOMEM;
+  if (!ctx->side) {
+    cudaError_t e = cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming);
+    if (e != cudaSuccess) return cuda_check(ctx, e, "side stream");
+  }
+  TRY(cuda_check(ctx, cudaEventRecord(ctx->ev_fork, ctx->stream), "fork"));
+  TRY(cuda_check(ctx, cudaStreamWaitEvent(ctx->side, ctx->ev_fork, 0), "fork wait"));
+  TRY(cuda_check(ctx, launch_draw_gaussian(ctx->side, p->seed, p->m2, p->m1, o), "draw gaussian"));
+  TRY(cuda_check(ctx, cudaEventRecord(ctx->ev_join, ctx->side), "join"));
+  *Om = o;
+  return IDL_OK;
+}
+
 // Sketch Y1 (m1 x R, row-major, ld = ldy1; column-major when y1_cm, which needs the
 // tensor-core Gaussian stage) -> J, T, via the Gaussian stage and the QR stage.
+// Om: the Gaussian matrix from fork_omega (joined here), or nullptr to draw it now.
 static int finish_pipeline(idl_ctx* ctx, const idl_params* p, int dtype, void* Y1, int64_t ldy1, int64_t R,
-                           int64_t K, int32_t* J, double* T, idl_info* info, bool y1_cm = false) {
+                           int64_t K, int32_t* J, double* T, idl_info* info, bool y1_cm = false,
+                           const double* Om = nullptr) {
   const int es = dtype_size(dtype);
   const int64_t m = p->m2 > 0 ? p->m2 : p->m1;
   const int64_t ld2 = m;
@@ -454,8 +538,14 @@ static int finish_pipeline(idl_ctx* ctx, const idl_params* p, int dtype, void* Y
   void* Y2 = ws_get(ctx, kWsY2, (size_t)es * (size_t)(R * ld2) * (keep_orig ? 2 : 1));
   if (!Y2) return IDL_ENOMEM;
   if (p->m2 > 0) {
-    WS(Om, double, kWsOmega, p->m2 * p->m1);
-    STAGE(kStDraw, cuda_check(ctx, launch_draw_gaussian(ctx->stream, p->seed, p->m2, p->m1, Om), "draw gaussian"));
+    if (Om) {
+      TRY(cuda_check(ctx, cudaStreamWaitEvent(ctx->stream, ctx->ev_join, 0), "join wait"));
+    } else {
+      double* o = (double*)ws_get(ctx, kWsOmega, sizeof(double) * (size_t)(p->m2 * p->m1));
+      if (!o) return IDL_ENOMEM;
+      STAGE(kStDraw, cuda_check(ctx, launch_draw_gaussian(ctx->stream, p->seed, p->m2, p->m1, o), "draw gaussian"));
+      Om = o;
+    }
     if (y1_cm)
       STAGE(kStGauss, launch_gaussian_tc(ctx, Om, p->m2, p->m1, (const float*)Y1, R, ldy1, true, p->precision,
                                          (float*)Y2, ld2));
@@ -496,13 +586,15 @@ static int finish_pipeline(idl_ctx* ctx, const idl_params* p, int dtype, void* Y
   return IDL_OK;
 }
 
-extern "C" int id_matrix(idl_ctx* ctx, const void* A, int64_t I, int64_t R, int64_t lda, int dtype, int64_t K,
+static int id_matrix_impl(idl_ctx* ctx, const void* A, int64_t I, int64_t R, int64_t lda, int dtype, int64_t K,
                          const idl_params* p, int32_t* J, double* T, idl_info* info) {
   TRY(check_ctx(ctx));
   TRY(check_params(ctx, p, dtype, I, R, K, false));
   if (I < 1 || lda < R || !A || !J || !T) return fail(ctx, IDL_EINVAL, "id_matrix: bad arguments");
   const int es = dtype_size(dtype);
   const int64_t m1 = p->m1;
+  double* Om;
+  TRY(fork_omega(ctx, p, &Om));
   int rc;
   const void* Ad = stage_in(ctx, A, (size_t)es * (size_t)((I - 1) * lda + R), kWsA, &rc);
   TRY(rc);
@@ -517,10 +609,10 @@ extern "C" int id_matrix(idl_ctx* ctx, const void* A, int64_t I, int64_t R, int6
                                                          ctx->d_status), "draw countsketch"));
   STAGE(kStBucket, launch_bucket_offsets(ctx, h, I, m1, ptr, rows));
   STAGE(kStSketch, launch_countsketch_dense(ctx, Ad, I, R, lda, dtype, s, ptr, rows, m1, Y1, ldy1));
-  return finish_pipeline(ctx, p, dtype, Y1, ldy1, R, K, J, T, info);
+  return finish_pipeline(ctx, p, dtype, Y1, ldy1, R, K, J, T, info, false, Om);
 }
 
-extern "C" int id_matrix_csr(idl_ctx* ctx, const int64_t* rowptr, const int32_t* colidx, const void* vals, int64_t I,
+static int id_matrix_csr_impl(idl_ctx* ctx, const int64_t* rowptr, const int32_t* colidx, const void* vals, int64_t I,
                              int64_t R, int64_t nnz, int dtype, int64_t K, const idl_params* p, int32_t* J, double* T,
                              idl_info* info) {
   TRY(check_ctx(ctx));
@@ -529,6 +621,8 @@ extern "C" int id_matrix_csr(idl_ctx* ctx, const int64_t* rowptr, const int32_t*
     return fail(ctx, IDL_EINVAL, "id_matrix_csr: bad arguments");
   const int es = dtype_size(dtype);
   const int64_t m1 = p->m1;
+  double* Om;
+  TRY(fork_omega(ctx, p, &Om));
   int rc;
   const int64_t* rp = (const int64_t*)stage_in(ctx, rowptr, sizeof(int64_t) * (size_t)(I + 1), kWsRowptr, &rc);
   TRY(rc);
@@ -548,10 +642,10 @@ extern "C" int id_matrix_csr(idl_ctx* ctx, const int64_t* rowptr, const int32_t*
                                                          ctx->d_status), "draw countsketch"));
   STAGE(kStBucket, launch_bucket_offsets(ctx, h, I, m1, ptr, rows));
   STAGE(kStSketch, launch_countsketch_csr(ctx, rp, ci, vv, I, R, nnz, dtype, s, ptr, rows, m1, Y1, ldy1));
-  return finish_pipeline(ctx, p, dtype, Y1, ldy1, R, K, J, T, info);
+  return finish_pipeline(ctx, p, dtype, Y1, ldy1, R, K, J, T, info, false, Om);
 }
 
-extern "C" int id_cp_tensor(idl_ctx* ctx, int N, const int64_t* dims, int64_t R, const void* const* factors,
+static int id_cp_tensor_impl(idl_ctx* ctx, int N, const int64_t* dims, int64_t R, const void* const* factors,
                             const int64_t* ldf, const double* lambda, int64_t K, const idl_params* p, int32_t* J,
                             double* T, double* lambda_hat, idl_info* info) {
   TRY(check_ctx(ctx));
@@ -566,6 +660,8 @@ extern "C" int id_cp_tensor(idl_ctx* ctx, int N, const int64_t* dims, int64_t R,
     maxdim = std::max(maxdim, dims[n]);
     tot += dims[n];
   }
+  double* Om;
+  TRY(fork_omega(ctx, p, &Om));
   int rc;
   const double* lam = (const double*)stage_in(ctx, lambda, sizeof(double) * (size_t)R, kWsLam, &rc);
   TRY(rc);
@@ -595,7 +691,7 @@ extern "C" int id_cp_tensor(idl_ctx* ctx, int N, const int64_t* dims, int64_t R,
   double* Td = T;
   if (!jdev) { Jd = (int32_t*)ws_get(ctx, kWsJ, sizeof(int32_t) * (size_t)K); if (!Jd) return IDL_ENOMEM; }
   if (!tdev) { Td = (double*)ws_get(ctx, kWsT, sizeof(double) * (size_t)(K * (R - K))); if (!Td) return IDL_ENOMEM; }
-  TRY(finish_pipeline(ctx, p, IDL_F32, Y1, ldy1, R, K, Jd, Td, nullptr, cm));
+  TRY(finish_pipeline(ctx, p, IDL_F32, Y1, ldy1, R, K, Jd, Td, nullptr, cm, Om));
   double* lhd = lambda_hat;
   if (!ldev) { lhd = (double*)ws_get(ctx, kWsLamHat, sizeof(double) * (size_t)K); if (!lhd) return IDL_ENOMEM; }
   STAGE(kStCheck, launch_lambda_hat(ctx, lam, Jd, Td, K, R, lhd));
@@ -607,5 +703,156 @@ extern "C" int id_cp_tensor(idl_ctx* ctx, int N, const int64_t* dims, int64_t R,
                    "lambda_hat"));
   if (info) return finish_info(ctx, p, p->precision, info, K, R);
   if (!jdev || !tdev || !ldev) TRY(cuda_check(ctx, cudaStreamSynchronize(ctx->stream), "sync"));
+  return IDL_OK;
+}
+
+// ---------------------------------------------------------------------------
+// CUDA-graph replay of the pipelines (idl_set_graphs).  The first call with a
+// given set of arguments runs eagerly (it sizes the workspace); the second is
+// captured on a private stream and the graph launched; later calls replay it,
+// ordered after the caller's stream and the caller's stream after it by events.
+// A workspace reallocation (any call) makes the cached graphs stale.
+// ---------------------------------------------------------------------------
+namespace {
+struct KeyHash {
+  uint64_t h = 1469598103934665603ull;                 // FNV-1a, 64-bit
+  void add(const void* p, size_t n) {
+    const unsigned char* c = (const unsigned char*)p;
+    for (size_t i = 0; i < n; ++i) { h ^= c[i]; h *= 1099511628211ull; }
+  }
+  template <typename X> void v(const X& x) { add(&x, sizeof(X)); }
+};
+constexpr size_t kMaxPipeGraphs = 8;
+}  // namespace
+
+static int launch_pipe_graph(idl_ctx* ctx, const PipeGraph& g) {
+  cudaError_t e = cudaEventRecord(ctx->gev_in, ctx->stream);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->gstream, ctx->gev_in, 0);
+  if (e == cudaSuccess) e = cudaGraphLaunch(g.exec, ctx->gstream);
+  if (e == cudaSuccess) e = cudaEventRecord(ctx->gev_out, ctx->gstream);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->stream, ctx->gev_out, 0);
+  ctx_add_launches(g.launches);
+  return cuda_check(ctx, e, "pipeline graph launch");
+}
+
+template <typename F>
+static int graphed(idl_ctx* ctx, uint64_t key, F&& body) {
+  PipeGraph* g = nullptr;
+  for (auto& x : ctx->pgraphs)
+    if (x.key == key) { g = &x; break; }
+  if (g && g->exec && g->gen == ctx->ws_gen) return launch_pipe_graph(ctx, *g);
+  if (!g || g->nocap || g->gen != ctx->ws_gen) {
+    const int rc = body();                               // eager
+    if (rc != IDL_OK) return rc;
+    if (!g) {
+      if (ctx->pgraphs.size() >= kMaxPipeGraphs) {
+        if (ctx->pgraphs.front().exec) cudaGraphExecDestroy(ctx->pgraphs.front().exec);
+        ctx->pgraphs.erase(ctx->pgraphs.begin());
+      }
+      ctx->pgraphs.push_back(PipeGraph{});
+      g = &ctx->pgraphs.back();
+      g->key = key;
+    }
+    if (g->exec) { cudaGraphExecDestroy(g->exec); g->exec = nullptr; }
+    g->gen = ctx->ws_gen;                                // the workspace as this call left it
+    return IDL_OK;
+  }
+  if (!ctx->gstream) {
+    cudaError_t e = cudaStreamCreateWithFlags(&ctx->gstream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->gev_in, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->gev_out, cudaEventDisableTiming);
+    if (e != cudaSuccess) return cuda_check(ctx, e, "graph stream");
+  }
+  cudaStream_t user = ctx->stream;
+  ctx->stream = ctx->gstream;
+  cudaGraph_t graph = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(ctx->gstream, cudaStreamCaptureModeThreadLocal);
+  int rc = IDL_OK;
+  const long long before = idl_launch_count();
+  const uint64_t gen0 = ctx->ws_gen;
+  if (e == cudaSuccess) {
+    rc = body();
+    e = cudaStreamEndCapture(ctx->gstream, &graph);
+  }
+  ctx->stream = user;
+  const long long nl = idl_launch_count() - before;
+  ctx_add_launches(-nl);                                 // counted when the graph runs
+  if (e == cudaSuccess && rc == IDL_OK && ctx->ws_gen == gen0 && graph) {
+    e = cudaGraphInstantiate(&g->exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e == cudaSuccess) {
+      g->launches = nl;
+      return launch_pipe_graph(ctx, *g);
+    }
+    g->exec = nullptr;
+  } else if (graph) {
+    cudaGraphDestroy(graph);
+  }
+  // nothing of the captured call ran: run it eagerly, and do not capture these arguments again
+  (void)cudaGetLastError();
+  ctx->err.clear();
+  g->nocap = true;
+  return body();
+}
+
+static bool graph_ok(idl_ctx* ctx, idl_info* info, std::initializer_list<const void*> ptrs) {
+  if (!ctx || !ctx->graphs || info || ctx->prof_on) return false;
+  for (const void* q : ptrs)
+    if (q && !is_device_ptr(q)) return false;
+  return true;
+}
+
+static void key_ctx(KeyHash& k, idl_ctx* ctx, const idl_params* p) {
+  k.v(ctx->gemm_simt);
+  k.v(ctx->gemm_sync_loads);
+  k.v(ctx->cpqr_smem_only);
+  if (p) k.v(*p);
+}
+
+extern "C" int id_matrix(idl_ctx* ctx, const void* A, int64_t I, int64_t R, int64_t lda, int dtype, int64_t K,
+                         const idl_params* p, int32_t* J, double* T, idl_info* info) {
+  auto body = [&] { return id_matrix_impl(ctx, A, I, R, lda, dtype, K, p, J, T, info); };
+  if (!p || !graph_ok(ctx, info, {A, J, T})) return body();
+  KeyHash k;
+  k.v(1);
+  k.v(A); k.v(I); k.v(R); k.v(lda); k.v(dtype); k.v(K); k.v(J); k.v(T);
+  key_ctx(k, ctx, p);
+  return graphed(ctx, k.h, body);
+}
+
+extern "C" int id_matrix_csr(idl_ctx* ctx, const int64_t* rowptr, const int32_t* colidx, const void* vals, int64_t I,
+                             int64_t R, int64_t nnz, int dtype, int64_t K, const idl_params* p, int32_t* J, double* T,
+                             idl_info* info) {
+  auto body = [&] { return id_matrix_csr_impl(ctx, rowptr, colidx, vals, I, R, nnz, dtype, K, p, J, T, info); };
+  if (!p || !graph_ok(ctx, info, {rowptr, colidx, vals, J, T})) return body();
+  KeyHash k;
+  k.v(2);
+  k.v(rowptr); k.v(colidx); k.v(vals); k.v(I); k.v(R); k.v(nnz); k.v(dtype); k.v(K); k.v(J); k.v(T);
+  key_ctx(k, ctx, p);
+  return graphed(ctx, k.h, body);
+}
+
+extern "C" int id_cp_tensor(idl_ctx* ctx, int N, const int64_t* dims, int64_t R, const void* const* factors,
+                            const int64_t* ldf, const double* lambda, int64_t K, const idl_params* p, int32_t* J,
+                            double* T, double* lambda_hat, idl_info* info) {
+  auto body = [&] { return id_cp_tensor_impl(ctx, N, dims, R, factors, ldf, lambda, K, p, J, T, lambda_hat, info); };
+  if (!p || N < 1 || N > 8 || !dims || !factors || !ldf || !graph_ok(ctx, info, {lambda, J, T, lambda_hat}))
+    return body();
+  KeyHash k;
+  k.v(3);
+  k.v(N); k.v(R); k.v(lambda); k.v(K); k.v(J); k.v(T); k.v(lambda_hat);
+  for (int n = 0; n < N; ++n) { k.v(dims[n]); k.v(factors[n]); k.v(ldf[n]); }
+  key_ctx(k, ctx, p);
+  return graphed(ctx, k.h, body);
+}
+
+extern "C" int idl_set_graphs(idl_ctx* ctx, int on) {
+  if (!ctx) return IDL_EINVAL;
+  ctx->graphs = on != 0;
+  if (!on) {
+    for (auto& g : ctx->pgraphs)
+      if (g.exec) cudaGraphExecDestroy(g.exec);
+    ctx->pgraphs.clear();
+  }
   return IDL_OK;
 }

@@ -430,8 +430,8 @@ static bool pick_cpqr(const std::vector<int>& list, const std::vector<BItem>& it
 template <int V, int TPC>
 static int launch_b_cpqr(idl_ctx* ctx, const BItem* d_items, const int32_t* d_list, int nlist, const CpqrCfg& c) {
   auto kern = b_cpqr_kernel<V, TPC>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c.smem);
+  cudaError_t e = ensure_cluster_nonportable(ctx, (const void*)kern);
+  if (e == cudaSuccess) e = ensure_smem(ctx, (const void*)kern, c.smem);
   if (e != cudaSuccess) return cuda_check(ctx, e, "batch cpqr attribute");
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)(nlist * c.CS));
@@ -716,7 +716,7 @@ static int run_gemm_stage(idl_ctx* ctx, const BatchPlan& P, const BItem* d_items
                           int& nlaunch) {
   const size_t smem = 1024 + (size_t)kStages * NP * kBM * kBK * 2 + (size_t)kBSlots * NP * P.maxNT * kBK * 2 + 128;
   if (smem > (size_t)ctx->smem_optin) return fail(ctx, IDL_ELIMIT, "batch gemm: shared memory");
-  cudaError_t e = cudaFuncSetAttribute(b_gemm_kernel<NP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = ensure_smem(ctx, (const void*)b_gemm_kernel<NP>, smem);
   if (e != cudaSuccess) return cuda_check(ctx, e, "batch gemm attribute");
   BLAUNCH(b_planes_kernel<NP>, kBPlanes, 256, 0);
   BLAUNCH(b_gemm_kernel<NP>, kBGemm, kTcThreads, smem, ctx->d_status);
@@ -733,10 +733,10 @@ static int run_proposal(idl_ctx* ctx, const BatchPlan& P, const BItem* d_items, 
   const size_t sm_feat = sizeof(float) * prop::features_smem_floats(m);
   const size_t sm_mlp = sizeof(float) * prop::mlp_fwd_smem_floats();
   const size_t sm_app = sizeof(float) * (size_t)P.maxKm_prop;
-  cudaError_t e = cudaFuncSetAttribute(b_pchol_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_chol);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(b_pfeat_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_feat);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(b_pmlp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_mlp);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(b_papply_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_app);
+  cudaError_t e = ensure_smem(ctx, (const void*)b_pchol_kernel, sm_chol);
+  if (e == cudaSuccess) e = ensure_smem(ctx, (const void*)b_pfeat_kernel, sm_feat);
+  if (e == cudaSuccess) e = ensure_smem(ctx, (const void*)b_pmlp_kernel, sm_mlp);
+  if (e == cudaSuccess) e = ensure_smem(ctx, (const void*)b_papply_kernel, sm_app);
   if (e != cudaSuccess) return cuda_check(ctx, e, "batch proposal attribute");
   BLAUNCH(b_pgram_kernel, kBPGram, prop::kThreads, sm_gram);
   BLAUNCH(b_pgred_kernel, kBPGRed, prop::kThreads, 0);
@@ -774,7 +774,7 @@ static int run_stages(idl_ctx* ctx, const BatchPlan& P, const BItem* d_items, co
   if (timed) cudaEventRecord(ev[1], ctx->stream);
   if (P.pre[kBSketchT][n] > 0) {
     const size_t smem = ts_smem_bytes(P.maxL_cp);
-    cudaError_t e = cudaFuncSetAttribute(b_sketch_cp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = ensure_smem(ctx, (const void*)b_sketch_cp_kernel, smem);
     if (e != cudaSuccess) return cuda_check(ctx, e, "batch tensorsketch attribute");
     BLAUNCH(b_sketch_cp_kernel, kBSketchT, ts_threads(P.maxL_cp), smem, (const float2*)ctx->ts_tw);
   }
@@ -798,8 +798,8 @@ static int run_stages(idl_ctx* ctx, const BatchPlan& P, const BItem* d_items, co
   {
     const size_t smem_inv = sizeof(double) * (size_t)P.maxK * (P.maxK + 1);
     const size_t smem_t = sizeof(float) * (size_t)tgemm_df_floats(P.maxK);
-    cudaError_t e = cudaFuncSetAttribute(b_rinv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_inv);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(b_tgemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_t);
+    cudaError_t e = ensure_smem(ctx, (const void*)b_rinv_kernel, smem_inv);
+    if (e == cudaSuccess) e = ensure_smem(ctx, (const void*)b_tgemm_kernel, smem_t);
     if (e != cudaSuccess) return cuda_check(ctx, e, "batch solve attribute");
     BLAUNCH(b_rinv_kernel, kBRinv, 32 * kRinvWarpsDf, smem_inv);
     BLAUNCH(b_tgemm_kernel, kBTgemm, 256, smem_t);

@@ -281,7 +281,7 @@ static int csr_launch(idl_ctx* ctx, const int64_t* rowptr, const int32_t* colidx
   const size_t want = head + sizeof(T) * (size_t)R;
   if (want <= (size_t)ctx->smem_optin) {
     auto k = cs_csr_kernel<T, true, NT>;
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)want);
+    cudaError_t e = ensure_smem(ctx, (const void*)k, want);
     if (e != cudaSuccess) return cuda_check(ctx, e, "csr smem attribute");
     k<<<(unsigned)L, NT, want, ctx->stream>>>(rowptr, colidx, vals, R, nnz, s, ptr, rows, Y, ldy, ctx->d_status,
                                               vec_ok), idl::count_launch();
@@ -289,7 +289,7 @@ static int csr_launch(idl_ctx* ctx, const int64_t* rowptr, const int32_t* colidx
     cudaError_t e = cudaMemset2DAsync(Y, ldy * sizeof(T), 0, R * sizeof(T), L, ctx->stream);
     if (e != cudaSuccess) return cuda_check(ctx, e, "csr zero");
     auto k = cs_csr_kernel<T, false, NT>;
-    e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)head);
+    e = ensure_smem(ctx, (const void*)k, head);
     if (e != cudaSuccess) return cuda_check(ctx, e, "csr smem attribute");
     k<<<(unsigned)L, NT, head, ctx->stream>>>(rowptr, colidx, vals, R, nnz, s, ptr, rows, Y, ldy, ctx->d_status,
                                               vec_ok), idl::count_launch();

@@ -233,8 +233,8 @@ static int try_reg_cpqr(idl_ctx* ctx, const T* Yin, T* Yout, int64_t m, int64_t 
   const size_t smem = reg_cpqr_smem<T, V, TPC>((int)m);
   if (smem > (size_t)ctx->smem_optin) return IDL_OK;
   auto kern = cpqr_reg_kernel<T, V, TPC>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = ensure_cluster_nonportable(ctx, (const void*)kern);
+  if (e == cudaSuccess) e = ensure_smem(ctx, (const void*)kern, smem);
   if (e != cudaSuccess) return cuda_check(ctx, e, "cpqr reg attribute");
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(CS);
@@ -249,7 +249,7 @@ static int try_reg_cpqr(idl_ctx* ctx, const T* Yin, T* Yout, int64_t m, int64_t 
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   int nclusters = 0;
-  e = cudaOccupancyMaxActiveClusters(&nclusters, kern, &cfg);
+  e = cluster_occupancy(ctx, (const void*)kern, cfg, &nclusters);
   if (e != cudaSuccess || nclusters < 1) { (void)cudaGetLastError(); return IDL_OK; }
   if (!x.colmap) ctx->last_cluster = CS;
   e = cudaLaunchKernelEx(&cfg, kern, Yin, Yout, (int)m, (int)R, (int)ld, (int)K, nc, J, rnorm,
@@ -304,7 +304,7 @@ static int cpqr_impl(idl_ctx* ctx, const T* Yin, T* Yout, int64_t m, int64_t R, 
   }
   if (x.colmap) return fail(ctx, IDL_ELIMIT, "cpqr: candidate set exceeds one CTA");
   auto kern = cpqr_cluster_kernel<T>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  cudaError_t e = ensure_cluster_nonportable(ctx, (const void*)kern);
   if (e != cudaSuccess) return cuda_check(ctx, e, "cpqr cluster attribute");
   for (int CS = 16; CS >= 1; CS >>= 1) {
     const int nc = (int)cdiv(R, CS);
@@ -318,7 +318,7 @@ static int cpqr_impl(idl_ctx* ctx, const T* Yin, T* Yout, int64_t m, int64_t R, 
       if (CS == 16) return fail(ctx, IDL_ELIMIT, "cpqr: sketch exceeds the cluster's shared memory");
       continue;
     }
-    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    e = ensure_smem(ctx, (const void*)kern, smem);
     if (e != cudaSuccess) return cuda_check(ctx, e, "cpqr smem attribute");
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(CS);
@@ -333,7 +333,7 @@ static int cpqr_impl(idl_ctx* ctx, const T* Yin, T* Yout, int64_t m, int64_t R, 
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     int nclusters = 0;
-    e = cudaOccupancyMaxActiveClusters(&nclusters, kern, &cfg);
+    e = cluster_occupancy(ctx, (const void*)kern, cfg, &nclusters);
     if (e != cudaSuccess || nclusters < 1) { (void)cudaGetLastError(); continue; }
     ctx->last_cluster = CS;
     e = cudaLaunchKernelEx(&cfg, kern, Yin, Yout, (int)m, (int)R, (int)ld, (int)K, nc, lds, tpc, J, rnorm,
@@ -413,8 +413,8 @@ int launch_t_solve(idl_ctx* ctx, const void* Y2, int64_t m, int64_t R, int64_t l
   const unsigned inv_blocks_df = (unsigned)cdiv(K, kRinvWarpsDf);
   cudaError_t e;
   if (dtype == IDL_F32) {
-    e = cudaFuncSetAttribute(rinv_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_inv);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(tgemm_df_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_df);
+    e = ensure_smem(ctx, (const void*)rinv_kernel<float>, smem_inv);
+    if (e == cudaSuccess) e = ensure_smem(ctx, (const void*)tgemm_df_kernel, smem_df);
     if (e == cudaSuccess) {
       rinv_kernel<float><<<inv_blocks_df, 32 * kRinvWarpsDf, smem_inv, ctx->stream>>>((const float*)Y2, (int)ld, (int)K,
                                                                                 (int)R, J, Rinv, Rsplit),
@@ -424,8 +424,8 @@ int launch_t_solve(idl_ctx* ctx, const void* Y2, int64_t m, int64_t R, int64_t l
             (const float*)Y2, (int)ld, (int)K, (int)R, Rsplit, rest, (int)nrest, T), idl::count_launch();
     }
   } else {
-    e = cudaFuncSetAttribute(rinv_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_inv);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(tgemm_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_t);
+    e = ensure_smem(ctx, (const void*)rinv_kernel<double>, smem_inv);
+    if (e == cudaSuccess) e = ensure_smem(ctx, (const void*)tgemm_kernel<double>, smem_t);
     if (e == cudaSuccess) {
       rinv_kernel<double><<<inv_blocks, 32 * kRinvWarps, smem_inv, ctx->stream>>>((const double*)Y2, (int)ld, (int)K,
                                                                                  (int)R, J, Rinv, nullptr),
@@ -481,12 +481,12 @@ int launch_residual(idl_ctx* ctx, const void* Y2orig, const void* Y2fact, int64_
   const int blocks = (int)std::min<int64_t>(cdiv(nrest, 8), 4 * ctx->num_sms);
   cudaError_t e;
   if (dtype == IDL_F32) {
-    e = cudaFuncSetAttribute(residual_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    e = ensure_smem(ctx, (const void*)residual_kernel<float>, smem);
     if (e == cudaSuccess)
       residual_kernel<float><<<blocks, 256, smem, ctx->stream>>>((const float*)Y2orig, (int)m, (int)ld, (int)K, (int)R, J, T,
                                                                  rest, (int)nrest, ctx->d_diag), idl::count_launch();
   } else {
-    e = cudaFuncSetAttribute(residual_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    e = ensure_smem(ctx, (const void*)residual_kernel<double>, smem);
     if (e == cudaSuccess)
       residual_kernel<double><<<blocks, 256, smem, ctx->stream>>>((const double*)Y2orig, (int)m, (int)ld, (int)K, (int)R, J,
                                                                   T, rest, (int)nrest, ctx->d_diag), idl::count_launch();

@@ -132,8 +132,8 @@ static int stable_bucket_offsets(idl_ctx* ctx, const int32_t* h, int64_t I, int6
   if (!cnt) return IDL_ENOMEM;
   int32_t* tot = cnt + nblk * L;
   const size_t sm = sizeof(int32_t) * (size_t)W * L;
-  cudaError_t e = cudaFuncSetAttribute(stable_count_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(stable_scatter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  cudaError_t e = ensure_smem(ctx, (const void*)stable_count_kernel, sm);
+  if (e == cudaSuccess) e = ensure_smem(ctx, (const void*)stable_scatter_kernel, sm);
   if (e != cudaSuccess) return cuda_check(ctx, e, "bucket attribute");
   stable_count_kernel<<<(unsigned)nblk, 32 * W, sm, st>>>(h, I, (int)L, cnt, ctx->d_status), idl::count_launch();
   stable_prefix_kernel<<<(unsigned)cdiv(L, 8), 256, 0, st>>>(cnt, nblk, (int)L, tot), idl::count_launch();

@@ -101,7 +101,7 @@ static int tc_impl(idl_ctx* ctx, const double* Omega, int64_t m2, int64_t m1, co
         count_launch();
   }
   auto k = y1_cm ? gauss_tc_kernel<NP, true> : gauss_tc_kernel<NP, false>;
-  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = ensure_smem(ctx, (const void*)k, smem);
   if (e != cudaSuccess) return cuda_check(ctx, e, "gaussian tc attribute");
   dim3 grid((unsigned)mtiles, (unsigned)splits, (unsigned)nz);
   k<<<grid, kTcThreads, smem, ctx->stream>>>(Y1, ldy1, R, m1, Bpl, NT, NTc, kbpc, nkb, part, ctx->d_status),

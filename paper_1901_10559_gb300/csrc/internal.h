@@ -12,9 +12,25 @@
 struct idl_batch_state;
 void idl_batch_state_free(idl_batch_state* b);
 
+// A single-problem pipeline captured as a CUDA graph (idl_set_graphs).
+struct PipeGraph {
+  uint64_t key = 0;                // hash of the call's arguments
+  uint64_t gen = 0;                // workspace generation the graph's addresses belong to
+  cudaGraphExec_t exec = nullptr;
+  long long launches = 0;          // kernels in the graph (the launch counter adds them per replay)
+  bool nocap = false;              // capture failed once: run these calls eagerly
+};
+
 struct idl_ctx {
   int device = 0;
   cudaStream_t stream = nullptr;
+  cudaStream_t side = nullptr;     // the Gaussian draw runs here, overlapping the sketch (created on first use)
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  int graphs = 0;                  // idl_set_graphs: replay repeated pipeline calls as CUDA graphs
+  uint64_t ws_gen = 1;             // bumped whenever a workspace slot is (re)allocated
+  std::vector<PipeGraph> pgraphs;  // most recent last
+  cudaStream_t gstream = nullptr;  // capture / replay stream (the legacy stream cannot be captured)
+  cudaEvent_t gev_in = nullptr, gev_out = nullptr;
   int num_sms = 0;
   int smem_optin = 0;          // max dynamic shared memory per block (bytes)
   int* d_status = nullptr;     // device status word
@@ -60,6 +76,14 @@ void* ws_get(idl_ctx* ctx, int slot, size_t bytes);
 int fail(idl_ctx* ctx, int code, const std::string& msg);
 void ctx_add_launches(long long d);   // adjusts the process-wide launch counter (graph replays)
 int cuda_check(idl_ctx* ctx, cudaError_t e, const char* where);
+// cudaFuncSetAttribute(MaxDynamicSharedMemorySize) only when kern needs more than
+// was already allowed on this device (the attribute is per process and device;
+// the driver call costs microseconds per launch).  Process-wide caches, locked.
+cudaError_t ensure_smem(idl_ctx* ctx, const void* kern, size_t bytes);
+// cudaFuncAttributeNonPortableClusterSizeAllowed, once per kernel
+cudaError_t ensure_cluster_nonportable(idl_ctx* ctx, const void* kern);
+// cudaOccupancyMaxActiveClusters, cached per (kernel, cluster size, threads, shared memory)
+cudaError_t cluster_occupancy(idl_ctx* ctx, const void* kern, const cudaLaunchConfig_t& cfg, int* nclusters);
 
 // draws.cu
 cudaError_t launch_draw_countsketch(cudaStream_t st, uint64_t seed, int64_t I, int64_t L, int modified,

@@ -152,7 +152,7 @@ __global__ void prop_labels_kernel(const int32_t* __restrict__ J, int K, int R, 
 // ---------------------------------------------------------------------------
 static int set_smem(idl_ctx* ctx, const void* kern, size_t bytes) {
   if (bytes > (size_t)ctx->smem_optin) return fail(ctx, IDL_ELIMIT, "proposal: shared memory");
-  return cuda_check(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes),
+  return cuda_check(ctx, ensure_smem(ctx, (const void*)kern, bytes),
                     "proposal smem attribute");
 }
 

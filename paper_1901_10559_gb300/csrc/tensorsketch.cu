@@ -63,7 +63,7 @@ int launch_tensorsketch(idl_ctx* ctx, int N, const int64_t* dims, int64_t R, con
   int logL = 0;
   while ((1LL << logL) < L) ++logL;
   const size_t smem = ts_smem_bytes((int)L);
-  cudaError_t e = cudaFuncSetAttribute(tensorsketch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = ensure_smem(ctx, (const void*)tensorsketch_kernel, smem);
   if (e != cudaSuccess) return cuda_check(ctx, e, "tensorsketch attribute");
   const float2* tw = ts_twiddles(ctx);
   if (!tw) return IDL_ENOMEM;

@@ -260,3 +260,76 @@ def test_injected_allocation_failure_is_reported(ctx):
     lib.idl_debug_fail_alloc(ctx.ptr, 0)
     idl.id_matrix(ctx, A, 5, idl.make_params(40, 10, 1, precision=idl.PREC_FP32), J, T)   # recovers
     assert ctx.sync() == idl.IDL_OK
+
+
+# ------------------------------------------------------------------ CUDA-graph replay
+def test_graph_replay_matches_eager(ctx):
+    """idl_set_graphs: the first call runs eagerly, the second is captured, later
+    ones replay; every call reads the buffers' current contents (A is changed
+    in place between calls, by powers of two), runs as many kernels as an eager
+    call, and gives the eager call's J and T.  A call with other
+    arguments in between (which regrows the workspace) invalidates the graph."""
+    K, I, R, m1, m2 = 12, 3000, 400, 200, 30
+    rng = np.random.default_rng(11)
+    A0 = lowrank_dense(I, R, 0.7, 1e-9, seed=21).astype(np.float32)
+    A = dev(A0)
+    p = idl.make_params(m1, m2, seed=4, modified=True, precision=idl.PREC_FP32)
+    J0, T0 = _outputs(K, R)
+    idl.id_matrix(ctx, A, K, p, J0, T0)                     # eager reference
+    Je, Te = host(J0).copy(), host(T0).copy()
+    n_eager = None
+    try:
+        idl.idl_set_graphs(ctx, True)
+        J, T = _outputs(K, R)
+        for call in range(4):
+            if call == 2:   # another problem that needs a larger workspace: the graph goes stale
+                Ab = dev(lowrank_dense(2 * I, 2 * R, 0.7, 1e-9, seed=22).astype(np.float32))
+                Jb, Tb = _outputs(K, 2 * R)
+                idl.id_matrix(ctx, Ab, K, idl.make_params(2 * m1, m2, seed=5), Jb, Tb)
+            scale = float(2.0 ** rng.integers(-3, 4))         # exact in FP32: J and T unchanged
+            A.copy_(dev(A0 * np.float32(scale)))
+            before = idl.lib().idl_launch_count()
+            idl.id_matrix(ctx, A, K, p, J, T)
+            torch.cuda.synchronize()
+            n = idl.lib().idl_launch_count() - before
+            if n_eager is None:
+                n_eager = n
+            assert n == n_eager, (call, n, n_eager)
+            assert np.array_equal(host(J), Je), call          # J is scale invariant
+            assert np.allclose(host(T), Te, rtol=1e-4, atol=1e-6), call
+        assert ctx.sync() == idl.IDL_OK
+    finally:
+        idl.idl_set_graphs(ctx, False)
+
+
+def test_graph_replay_cp_and_csr(ctx):
+    """The CSR and CP pipelines replayed as graphs give the eager results."""
+    K = 10
+    c = random_csr(4000, 300, 0.02, seed=3)
+    vals = (c.vals * (1.0 + 4.0 * c.colidx / 300.0)).astype(np.float32)   # column norms well apart
+    p = idl.make_params(150, 25, seed=6, modified=True, precision=idl.PREC_FP32)
+    rp, ci, vv = dev(c.rowptr), dev(c.colidx), dev(vals)
+    dims, R = (60, 50, 40), 120
+    facs, lam = cp_factors(dims, R, seed=8)
+    fd = [dev(np.ascontiguousarray(F.T)) for F in facs]
+    dl = dev(lam)
+    pc = idl.make_params(1024, 25, seed=7, modified=False, precision=idl.PREC_FP32)
+    outs = {}
+    for graphs in (False, True):
+        idl.idl_set_graphs(ctx, graphs)
+        try:
+            for rep in range(3):
+                J, T = _outputs(K, 300)
+                idl.id_matrix_csr(ctx, rp, ci, vv, c.shape, K, p, J, T)
+                Jc, Tc = _outputs(K, R)
+                lh = torch.empty(K, dtype=torch.float64, device="cuda")
+                idl.id_cp_tensor(ctx, fd, dl, K, pc, Jc, Tc, lh)
+                outs[(graphs, rep)] = (host(J), host(T), host(Jc), host(Tc), host(lh))
+        finally:
+            idl.idl_set_graphs(ctx, False)
+    ref = outs[(False, 0)]
+    for key, o in outs.items():
+        assert np.array_equal(o[0], ref[0]) and np.array_equal(o[2], ref[2]), key
+        for a, b in ((o[1], ref[1]), (o[3], ref[3]), (o[4], ref[4])):
+            assert np.allclose(a, b, rtol=1e-4, atol=1e-6), key
+    assert ctx.sync() == idl.IDL_OK
