@@ -262,6 +262,11 @@ __device__ __forceinline__ void gauss_tc_block(const float* __restrict__ Y1, int
           const float4 y = __ldcs((const float4*)(ycol + b0 + 4));
           v[c][0] = x.x; v[c][1] = x.y; v[c][2] = x.z; v[c][3] = x.w;
           v[c][4] = y.x; v[c][5] = y.y; v[c][6] = y.z; v[c][7] = y.w;
+        } else if (!CM && col_ok && b0 + 8 <= m1) {
+          // whole chunk inside Y1: one row pointer, stride ldy1, no per-value predicate
+          const float* q = Y1 + b0 * ldy1 + r0 + m;
+#pragma unroll
+          for (int e = 0; e < 8; ++e) v[c][e] = __ldcs(q + e * ldy1);
         } else {
 #pragma unroll
           for (int e = 0; e < 8; ++e) {
@@ -280,16 +285,38 @@ __device__ __forceinline__ void gauss_tc_block(const float* __restrict__ Y1, int
 #pragma unroll
       for (int c = 0; c < 4; ++c) {
         const int kc = kchunk(c);
-        __nv_bfloat16 pl[NP][8];
+        if constexpr (NP == 3) {
+          // truncation split (split_bf16<3>) of two values at a time: a plane's bf16 pair
+          // is the top halves of the two remainders, one byte permute
+          uint32_t w[NP][4];
 #pragma unroll
-        for (int e = 0; e < 8; ++e) {
-          __nv_bfloat16 t[NP];
-          split_bf16<NP>(v[c][e], t);
+          for (int j = 0; j < 4; ++j) {
+            float x0 = v[c][2 * j], x1 = v[c][2 * j + 1];
 #pragma unroll
-          for (int p = 0; p < NP; ++p) pl[p][e] = t[p];
+            for (int p = 0; p < NP; ++p) {
+              const uint32_t u0 = __float_as_uint(x0), u1 = __float_as_uint(x1);
+              w[p][j] = __byte_perm(u0, u1, 0x7632);
+              if (p + 1 < NP) {
+                x0 -= __uint_as_float(u0 & 0xFFFF0000u);
+                x1 -= __uint_as_float(u1 & 0xFFFF0000u);
+              }
+            }
+          }
+#pragma unroll
+          for (int p = 0; p < NP; ++p)
+            *(uint4*)(As + (size_t)p * a_plane + sw128_off(m, kc)) = make_uint4(w[p][0], w[p][1], w[p][2], w[p][3]);
+        } else {
+          __nv_bfloat16 pl[NP][8];
+#pragma unroll
+          for (int e = 0; e < 8; ++e) {
+            __nv_bfloat16 t[NP];
+            split_bf16<NP>(v[c][e], t);
+#pragma unroll
+            for (int p = 0; p < NP; ++p) pl[p][e] = t[p];
+          }
+#pragma unroll
+          for (int p = 0; p < NP; ++p) *(uint4*)(As + (size_t)p * a_plane + sw128_off(m, kc)) = *(const uint4*)pl[p];
         }
-#pragma unroll
-        for (int p = 0; p < NP; ++p) *(uint4*)(As + (size_t)p * a_plane + sw128_off(m, kc)) = *(const uint4*)pl[p];
       }
       fence_async_smem();
       asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&a_ready[s])) : "memory");
