@@ -101,10 +101,17 @@ __device__ __forceinline__ T house_update(const T* __restrict__ vrow, T (&y)[V],
     y[j + 1] = fma(-d, w1, y[j + 1]);
     y[j + 2] = fma(-d, w2, y[j + 2]);
     y[j + 3] = fma(-d, w3, y[j + 3]);
-    s0 += (j >= jt) ? y[j] * y[j] : T(0);
-    s1 += (j + 1 >= jt) ? y[j + 1] * y[j + 1] : T(0);
-    s2 += (j + 2 >= jt) ? y[j + 2] * y[j + 2] : T(0);
-    s3 += (j + 3 >= jt) ? y[j + 3] * y[j + 3] : T(0);
+    if (j >= jt) {                     // the whole chunk is trailing: one FMA per row
+      s0 = fma(y[j], y[j], s0);
+      s1 = fma(y[j + 1], y[j + 1], s1);
+      s2 = fma(y[j + 2], y[j + 2], s2);
+      s3 = fma(y[j + 3], y[j + 3], s3);
+    } else {                           // the chunk holding row t (or above it): masked
+      s0 += (j >= jt) ? y[j] * y[j] : T(0);
+      s1 += (j + 1 >= jt) ? y[j + 1] * y[j + 1] : T(0);
+      s2 += (j + 2 >= jt) ? y[j + 2] * y[j + 2] : T(0);
+      s3 += (j + 3 >= jt) ? y[j + 3] * y[j + 3] : T(0);
+    }
   }
   return (s0 + s1) + (s2 + s3);
 }
