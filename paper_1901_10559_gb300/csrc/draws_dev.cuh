@@ -232,14 +232,19 @@ __device__ __forceinline__ void stable_warp_hist(const int32_t* __restrict__ h, 
   __syncthreads();
   const int64_t i0 = (blk * W + w) * (int64_t)kStableSub;
   int32_t* cw = hw + w * L;
-#pragma unroll 8
+  // all of the lane's buckets first (one memory round trip), then the counts
+  int hv[kStableSub / 32];
+#pragma unroll
   for (int q = 0; q < kStableSub / 32; ++q) {
     const int64_t i = i0 + q * 32 + lane;
-    if (i < I) {
-      const int b = h[i];
-      if (b < 0 || b >= L) set_status(status, IDL_EDATA);
-      else atomicAdd(&cw[b], 1);
-    }
+    hv[q] = i < I ? __ldg(h + i) : 0;
+  }
+#pragma unroll
+  for (int q = 0; q < kStableSub / 32; ++q) {
+    if (i0 + q * 32 + lane >= I) break;
+    const int b = hv[q];
+    if (b < 0 || b >= L) set_status(status, IDL_EDATA);
+    else atomicAdd(&cw[b], 1);
   }
   __syncthreads();
 }
@@ -282,27 +287,42 @@ __device__ __forceinline__ void stable_scatter_block(const int32_t* __restrict__
   int* no_status = nullptr;
   stable_warp_hist(h, I, L, blk, no_status, hw);
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, W = blockDim.x >> 5;
-  // hw[w][b] <- next free slot of bucket b for warp w
+  // hw[w][b] <- next free slot of bucket b for warp w; the bucket bases first, 8 loads
+  // of each array in flight per thread, then the shared-memory prefix over the warps
   const int32_t* pre = cnt + blk * (int64_t)L;
-  for (int b = threadIdx.x; b < L; b += blockDim.x) {
-    int32_t run = ptr[b] + pre[b];
-    for (int ww = 0; ww < W; ++ww) {
-      const int32_t v = hw[ww * L + b];
-      hw[ww * L + b] = run;
-      run += v;
+  for (int b0 = threadIdx.x; b0 < L; b0 += 8 * blockDim.x) {
+    int32_t base[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int b = b0 + u * blockDim.x;
+      base[u] = b < L ? __ldg(ptr + b) + __ldg(pre + b) : 0;
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int b = b0 + u * blockDim.x;
+      if (b >= L) break;
+      int32_t run = base[u];
+      for (int ww = 0; ww < W; ++ww) {
+        const int32_t v = hw[ww * L + b];
+        hw[ww * L + b] = run;
+        run += v;
+      }
     }
   }
   __syncthreads();
   int32_t* cw = hw + w * L;
   const int64_t i0 = (blk * W + w) * (int64_t)kStableSub;
   const unsigned lt = (1u << lane) - 1u;
-  int nb[2];
-  nb[0] = (i0 + lane < I) ? h[i0 + lane] : -1;
+  int hv[kStableSub / 32];                                            // the lane's buckets, loaded at once
+#pragma unroll
   for (int q = 0; q < kStableSub / 32; ++q) {
     const int64_t i = i0 + q * 32 + lane;
-    int b = nb[q & 1];
-    const int64_t inext = i + 32;
-    if (q + 1 < kStableSub / 32) nb[(q + 1) & 1] = inext < I ? h[inext] : -1;     // next row's bucket in flight
+    hv[q] = i < I ? __ldg(h + i) : -1;
+  }
+#pragma unroll
+  for (int q = 0; q < kStableSub / 32; ++q) {
+    const int64_t i = i0 + q * 32 + lane;
+    int b = hv[q];
     if (b >= L) b = -1;                                               // flagged by the counting pass
     const unsigned peers = __match_any_sync(0xffffffffu, b);
     const int slot = b >= 0 ? cw[b] : 0;
