@@ -328,7 +328,6 @@ extern "C" int idl_debug_fail_alloc(idl_ctx* ctx, int nth) {
 extern "C" int idl_debug_gemm_path(idl_ctx* ctx, int simt) {
   if (!ctx) return IDL_EINVAL;
   ctx->gemm_simt = simt == 1;
-  ctx->gemm_sync_loads = simt == 2;
   return IDL_OK;
 }
 extern "C" int idl_debug_cpqr_path(idl_ctx* ctx, int smem_only) {
@@ -804,7 +803,6 @@ static bool graph_ok(idl_ctx* ctx, idl_info* info, std::initializer_list<const v
 
 static void key_ctx(KeyHash& k, idl_ctx* ctx, const idl_params* p) {
   k.v(ctx->gemm_simt);
-  k.v(ctx->gemm_sync_loads);
   k.v(ctx->cpqr_smem_only);
   if (p) k.v(*p);
 }

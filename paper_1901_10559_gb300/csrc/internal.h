@@ -41,7 +41,6 @@ struct idl_ctx {
   std::vector<Buf> slots;
   int last_cluster = 0;
   int gemm_simt = 0;           // 1: Gaussian stage on CUDA cores instead of tcgen05 (comparison / tests)
-  int gemm_sync_loads = 0;     // 1: Gaussian tc stage loads Y1 through registers (comparison / tests)
   int cpqr_smem_only = 0;      // 1: always use the shared-memory QR kernel (comparison / tests)
   idl_batch_state* batch = nullptr;   // batch graphs and tuning table
   int batch_no_graph = 0;      // 1: run batches without graph capture (tests)
