@@ -64,6 +64,26 @@ WORKLOADS = {
 
 
 # ----------------------------------------------------------------------------- helpers
+def max_over_ranks(x: float, dist, device: str) -> float:
+    """The maximum of x over all ranks (x itself without a process group)."""
+    if not dist:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def rank_seed(w: dict, rank: int) -> int:
+    """Each rank solves its own instance: independent draws per rank."""
+    return w["seed"] + 1000 * rank
+
+
+def job_value(ws: int, steps: int, solves_per_step: int, seconds: float) -> float:
+    """Whole-job throughput: the solves of all ranks over the slowest rank's time."""
+    return ws * steps * solves_per_step / seconds
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -265,7 +285,7 @@ def run_ours(args, ws, rank, local):
     idl.idl_set_graphs(ctx, True)
     prec = {"FP64": idl.PREC_FP64, "FP32": idl.PREC_FP32, "BF16X3": idl.PREC_BF16X3, "BF16": idl.PREC_BF16}[
         w["precision"]]
-    seed = w["seed"] + 1000 * rank                    # independent draws per rank
+    seed = rank_seed(w, rank)                         # independent draws per rank
     p = idl.make_params(w["m1"], w["m2"], seed=seed, modified=(name != "cp"), precision=prec, residual=1)
     K = max(1, w["k"])
     R = max(2, w["R"])
@@ -380,15 +400,12 @@ def run_ours(args, ws, rank, local):
     torch.cuda.synchronize()
     prof = ctx.profile_read()
     ctx.profile(False)
+    ms = max_over_ranks(ms, dist, "cuda")
     if dist:
-        import torch.distributed as dist
-        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
         dist.barrier()
     ms_per_step = ms / args.steps
     solves_per_step = (w["n_dense"] + w["n_cp"]) if name == "batched" else 1
-    value = ws * args.steps * solves_per_step / (ms / 1e3)
+    value = job_value(ws, args.steps, solves_per_step, ms / 1e3)
 
     # learned vs plain: the same workload with the column proposal in the QR stage (fallbacks count
     # with their full time); untimed runs first (graph capture / tuning for a new batch shape)
@@ -416,11 +433,8 @@ def run_ours(args, ws, rank, local):
             else:
                 idl.id_cp_tensor(ctx, d_f, d_lam, K, p_l, J, T, lh, info=info)
             cert = 1.0 if info.proposal == 1 else 0.0
-        if dist:
-            t = torch.tensor([ms_l], dtype=torch.float64, device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms_l = float(t.item())
-        v_l = ws * nl * solves_per_step / (ms_l / 1e3)
+        ms_l = max_over_ranks(ms_l, dist, "cuda")
+        v_l = job_value(ws, nl, solves_per_step, ms_l / 1e3)
         lvp = {"proposal": "mlp (shipped weights), top-2K candidates, certificate, plain QR on rejection",
                "value_learned": round(v_l, 3), "value_plain": round(value, 3), "ratio": round(v_l / value, 4),
                "certified_fraction": round(cert, 4), "steps": nl, "unit": "solves/s"}
@@ -445,11 +459,8 @@ def run_ours(args, ws, rank, local):
             torch.cuda.synchronize()
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
-    if dist:
-        t = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e_val = ws * e2e_steps * solves_per_step / e2e_s
+    e2e_s = max_over_ranks(e2e_s, dist, "cuda")
+    e2e_val = job_value(ws, e2e_steps, solves_per_step, e2e_s)
     d2h = 4 * K + 8 * K * (R - K) + (8 * K if name == "cp" else 0)
     if name == "batched":
         d2h = sum(o[0].numel() * 4 + o[1].numel() * 8 for o in bouts)
