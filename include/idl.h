@@ -37,7 +37,11 @@ extern "C" {
 #define IDL_ENOMEM    2  /* device workspace allocation failed */
 #define IDL_ECUDA     3  /* CUDA runtime error (message in idl_last_error) */
 #define IDL_ERANK     4  /* |r_KK| <= 64 eps |r_11|: sketch numerically rank deficient; J written, T undefined */
-#define IDL_ETIMEOUT  5  /* a bounded device wait expired */
+#define IDL_ETIMEOUT  5  /* a bounded device wait expired.  Once idl_sync (or an idl_info readback)
+                            has reported it, the context is poisoned: every later call on it returns
+                            IDL_ETIMEOUT, because tensor-core work or copies that the timed-out kernel
+                            left in flight may still write the context's memory.  Destroy the context
+                            and create a new one. */
 #define IDL_EDATA     6  /* malformed input found on the device (CSR index out of range); bad entries skipped */
 #define IDL_ELIMIT    7  /* problem exceeds an on-chip capacity of this build (see the entry point) */
 
@@ -271,8 +275,8 @@ int idl_set_graphs(idl_ctx* ctx, int on);
  *   m2 > 0, m2 <= m1, m1 < I when modified.
  * id_matrix_csr: CSR A as in idl_countsketch_csr.
  * id_cp_tensor (Algorithm 3 with a Gaussian stage): CP tensor with N factor
- *   matrices (see idl_tensorsketch; host pointers not accepted for factors),
- *   s-values lambda, params.m1 = the TensorSketch length L (power of two).
+ *   matrices (see idl_tensorsketch; device or host arrays), s-values lambda,
+ *   params.m1 = the TensorSketch length L (power of two).
  * ------------------------------------------------------------------------- */
 int id_matrix(idl_ctx* ctx, const void* A, int64_t I, int64_t R, int64_t lda, int dtype, int64_t K,
               const idl_params* p, int32_t* J, double* T, idl_info* info);

@@ -115,6 +115,7 @@ _SIGS = {
     "idl_tune_save": ([_vp, ctypes.c_char_p], _int),
     "idl_tune_load": ([_vp, ctypes.c_char_p], _int),
     "idl_debug_batch_mode": ([_vp, _int, _int], _int),
+    "idl_debug_wait_probe": ([_vp, _int, ctypes.c_ulonglong], _int),
     "idl_debug_batch_timing": ([_vp, ctypes.POINTER(BatchItem), _int, ctypes.POINTER(ctypes.c_float)], _int),
     "idl_batch_fallbacks": ([_vp], _int),
     "idl_mlp_init": ([_vp, _u64], _int),
@@ -341,7 +342,8 @@ def id_cp_tensor(ctx, factors, lam, K, params, J, T, lam_hat, info=None, ldf=Non
 
 # ---------------------------------------------------------------- batches
 def dense_item(A, K, params, J, T, lda=None):
-    """Batch item for a dense FP32 CUDA matrix A (I, R)."""
+    """Batch item for a dense FP32 matrix A (I, R): a CUDA tensor, or a host (pinned)
+    tensor with host J, T."""
     it = BatchItem()
     it.kind = IDL_ITEM_DENSE
     it.I, it.R = int(A.shape[0]), int(A.shape[1])
@@ -354,7 +356,8 @@ def dense_item(A, K, params, J, T, lda=None):
 
 
 def cp_item(factors, lam, K, params, J, T, lam_hat):
-    """Batch item for a CP tensor: factors are CUDA float32 tensors (R, I_n), contiguous."""
+    """Batch item for a CP tensor: factors are float32 tensors (R, I_n), contiguous, on
+    the device or (with every other array of the batch) in host memory."""
     it = BatchItem()
     it.kind = IDL_ITEM_CP
     it.N = len(factors)
@@ -369,9 +372,17 @@ def cp_item(factors, lam, K, params, J, T, lam_hat):
     return it
 
 
+def batch_array(items):
+    """A ctypes array of batch items (build it once and pass it to idl_batch_run on
+    every call to save the per-call conversion)."""
+    return (BatchItem * len(items))(*items)
+
+
 def idl_batch_run(ctx, items):
-    arr = (BatchItem * len(items))(*items)
-    return ctx.check(lib().idl_batch_run(ctx.ptr, arr, len(items)))
+    """items: a list of BatchItem or a batch_array.  All arrays of the batch are device
+    memory, or all host memory (then the call copies them and synchronises)."""
+    arr = items if isinstance(items, ctypes.Array) else batch_array(items)
+    return ctx.check(lib().idl_batch_run(ctx.ptr, arr, len(arr)))
 
 
 def idl_tune_save(ctx, path):
@@ -382,12 +393,16 @@ def idl_tune_load(ctx, path):
     return ctx.check(lib().idl_tune_load(ctx.ptr, str(path).encode()))
 
 
+BATCH_STAGES = ("draws_buckets", "sketch_cp", "sketch_dense", "gaussian", "proposal", "cpqr", "tsolve")
+
+
 def batch_stage_ms(ctx, items):
-    """(dense sketch ms, Gaussian stage ms) of one un-graphed, event-timed run of the batch."""
+    """Milliseconds per stage group of one un-graphed, event-timed run of the batch
+    (a dict keyed by BATCH_STAGES)."""
     arr = (BatchItem * len(items))(*items)
-    ms = (ctypes.c_float * 2)()
+    ms = (ctypes.c_float * len(BATCH_STAGES))()
     ctx.check(lib().idl_debug_batch_timing(ctx.ptr, arr, len(items), ms))
-    return float(ms[0]), float(ms[1])
+    return {k: float(ms[i]) for i, k in enumerate(BATCH_STAGES)}
 
 
 # ---------------------------------------------------------------- learned column proposal

@@ -156,7 +156,8 @@ static void prof_end(idl_ctx* ctx, int idx) {
     if (_rc != IDL_OK) return _rc;          \
   } while (0)
 
-static bool is_device_ptr(const void* p) {
+namespace idl {
+bool is_device_ptr(const void* p) {
   if (!p) return false;
   cudaPointerAttributes a;
   if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
@@ -165,14 +166,21 @@ static bool is_device_ptr(const void* p) {
   }
   return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
+}  // namespace idl
 
 static int dtype_size(int dtype) { return dtype == IDL_F64 ? 8 : 4; }
 
-static int check_ctx(idl_ctx* ctx) {
+namespace idl {
+int ctx_usable(idl_ctx* ctx) {
   if (!ctx) return IDL_EINVAL;
-  cudaError_t e = cudaSetDevice(ctx->device);
-  return cuda_check(ctx, e, "cudaSetDevice");
+  if (ctx->poisoned)
+    return fail(ctx, IDL_ETIMEOUT, "a bounded device wait expired on this context earlier; destroy it and create "
+                                   "a new one (work that the timed-out kernel left in flight may still write its memory)");
+  return cuda_check(ctx, cudaSetDevice(ctx->device), "cudaSetDevice");
 }
+}  // namespace idl
+
+static int check_ctx(idl_ctx* ctx) { return ctx_usable(ctx); }
 
 // Copies a host array into a workspace slot (or returns the device pointer as is).
 static const void* stage_in(idl_ctx* ctx, const void* p, size_t bytes, int slot, int* rc) {
@@ -211,6 +219,7 @@ static int finish_info(idl_ctx* ctx, const idl_params* p, int precision, idl_inf
   else if (mode == 2) info->residual = d[1] > 0 ? std::sqrt(d[2] / d[1]) : 0.0;
   else info->residual = std::numeric_limits<double>::quiet_NaN();
   const double eps = precision == IDL_PREC_FP64 ? 2.220446049250313e-16 : 1.1920928955078125e-07;
+  if (st == IDL_ETIMEOUT) ctx->poisoned = true;
   if (st == IDL_OK && !(d[4] > 64.0 * eps * d[3])) st = IDL_ERANK;
   info->status = st;
   int zero = 0;
@@ -261,6 +270,7 @@ extern "C" int idl_destroy(idl_ctx* ctx) {
   idl_batch_state_free(ctx->batch);
   if (ctx->mlp) cudaFree(ctx->mlp);
   if (ctx->ts_tw) cudaFree(ctx->ts_tw);
+  if (ctx->ts8_tw) cudaFree(ctx->ts8_tw);
   if (ctx->side) { cudaStreamSynchronize(ctx->side); cudaStreamDestroy(ctx->side); }
   for (auto& g : ctx->pgraphs)
     if (g.exec) cudaGraphExecDestroy(g.exec);
@@ -287,6 +297,7 @@ extern "C" int idl_sync(idl_ctx* ctx) {
   cudaError_t e = cudaMemcpyAsync(&st, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
   TRY(cuda_check(ctx, e, "idl_sync"));
+  if (st == IDL_ETIMEOUT) ctx->poisoned = true;
   if (st != IDL_OK) {
     cudaMemsetAsync(ctx->d_status, 0, sizeof(int), ctx->stream);
     cudaStreamSynchronize(ctx->stream);
@@ -653,15 +664,35 @@ static int id_cp_tensor_impl(idl_ctx* ctx, int N, const int64_t* dims, int64_t R
     return fail(ctx, IDL_EINVAL, "id_cp_tensor: bad arguments");
   const int64_t L = p->m1;
   int64_t maxdim = 0, tot = 0;
+  size_t host_bytes = 0;
   for (int n = 0; n < N; ++n) {
-    if (dims[n] < 1 || ldf[n] < dims[n] || !factors[n] || !is_device_ptr(factors[n]))
-      return fail(ctx, IDL_EINVAL, "id_cp_tensor: factors must be device pointers with ldf >= dims");
+    if (dims[n] < 1 || ldf[n] < dims[n] || !factors[n])
+      return fail(ctx, IDL_EINVAL, "id_cp_tensor: factors must be non-null with ldf >= dims");
+    if (!is_device_ptr(factors[n])) host_bytes += (sizeof(float) * (size_t)((R - 1) * ldf[n] + dims[n]) + 255) & ~(size_t)255;
     maxdim = std::max(maxdim, dims[n]);
     tot += dims[n];
   }
   double* Om;
   TRY(fork_omega(ctx, p, &Om));
   int rc;
+  // host factors: copied into one workspace buffer (each at a 256-byte offset)
+  const void* fdev[8];
+  {
+    unsigned char* stg = host_bytes ? (unsigned char*)ws_get(ctx, kWsFactors, host_bytes) : nullptr;
+    if (host_bytes && !stg) return IDL_ENOMEM;
+    size_t off = 0;
+    for (int n = 0; n < N; ++n) {
+      fdev[n] = factors[n];
+      if (is_device_ptr(factors[n])) continue;
+      const size_t b = sizeof(float) * (size_t)((R - 1) * ldf[n] + dims[n]);
+      const int pi = prof_begin(ctx, kStCopy);
+      TRY(cuda_check(ctx, cudaMemcpyAsync(stg + off, factors[n], b, cudaMemcpyHostToDevice, ctx->stream), "copy in"));
+      prof_end(ctx, pi);
+      fdev[n] = stg + off;
+      off += (b + 255) & ~(size_t)255;
+    }
+  }
+  factors = fdev;
   const double* lam = (const double*)stage_in(ctx, lambda, sizeof(double) * (size_t)R, kWsLam, &rc);
   TRY(rc);
   WS(hbuf, int32_t, kWsModeH, tot);
@@ -713,11 +744,15 @@ static int id_cp_tensor_impl(idl_ctx* ctx, int N, const int64_t* dims, int64_t R
 // A workspace reallocation (any call) makes the cached graphs stale.
 // ---------------------------------------------------------------------------
 namespace {
+// The arguments of a pipeline call: an FNV-1a hash for the lookup and the raw
+// bytes, compared in full before a cached graph is replayed.
 struct KeyHash {
   uint64_t h = 1469598103934665603ull;                 // FNV-1a, 64-bit
+  std::string raw;
   void add(const void* p, size_t n) {
     const unsigned char* c = (const unsigned char*)p;
     for (size_t i = 0; i < n; ++i) { h ^= c[i]; h *= 1099511628211ull; }
+    raw.append((const char*)p, n);
   }
   template <typename X> void v(const X& x) { add(&x, sizeof(X)); }
 };
@@ -735,10 +770,11 @@ static int launch_pipe_graph(idl_ctx* ctx, const PipeGraph& g) {
 }
 
 template <typename F>
-static int graphed(idl_ctx* ctx, uint64_t key, F&& body) {
+static int graphed(idl_ctx* ctx, const KeyHash& k, F&& body) {
+  const uint64_t key = k.h;
   PipeGraph* g = nullptr;
   for (auto& x : ctx->pgraphs)
-    if (x.key == key) { g = &x; break; }
+    if (x.key == key && x.raw == k.raw) { g = &x; break; }
   if (g && g->exec && g->gen == ctx->ws_gen) return launch_pipe_graph(ctx, *g);
   if (!g || g->nocap || g->gen != ctx->ws_gen) {
     const int rc = body();                               // eager
@@ -751,6 +787,7 @@ static int graphed(idl_ctx* ctx, uint64_t key, F&& body) {
       ctx->pgraphs.push_back(PipeGraph{});
       g = &ctx->pgraphs.back();
       g->key = key;
+      g->raw = k.raw;
     }
     if (g->exec) { cudaGraphExecDestroy(g->exec); g->exec = nullptr; }
     g->gen = ctx->ws_gen;                                // the workspace as this call left it
@@ -815,7 +852,7 @@ extern "C" int id_matrix(idl_ctx* ctx, const void* A, int64_t I, int64_t R, int6
   k.v(1);
   k.v(A); k.v(I); k.v(R); k.v(lda); k.v(dtype); k.v(K); k.v(J); k.v(T);
   key_ctx(k, ctx, p);
-  return graphed(ctx, k.h, body);
+  return graphed(ctx, k, body);
 }
 
 extern "C" int id_matrix_csr(idl_ctx* ctx, const int64_t* rowptr, const int32_t* colidx, const void* vals, int64_t I,
@@ -827,7 +864,7 @@ extern "C" int id_matrix_csr(idl_ctx* ctx, const int64_t* rowptr, const int32_t*
   k.v(2);
   k.v(rowptr); k.v(colidx); k.v(vals); k.v(I); k.v(R); k.v(nnz); k.v(dtype); k.v(K); k.v(J); k.v(T);
   key_ctx(k, ctx, p);
-  return graphed(ctx, k.h, body);
+  return graphed(ctx, k, body);
 }
 
 extern "C" int id_cp_tensor(idl_ctx* ctx, int N, const int64_t* dims, int64_t R, const void* const* factors,
@@ -841,7 +878,7 @@ extern "C" int id_cp_tensor(idl_ctx* ctx, int N, const int64_t* dims, int64_t R,
   k.v(N); k.v(R); k.v(lambda); k.v(K); k.v(J); k.v(T); k.v(lambda_hat);
   for (int n = 0; n < N; ++n) { k.v(dims[n]); k.v(factors[n]); k.v(ldf[n]); }
   key_ctx(k, ctx, p);
-  return graphed(ctx, k.h, body);
+  return graphed(ctx, k, body);
 }
 
 extern "C" int idl_set_graphs(idl_ctx* ctx, int on) {

@@ -38,6 +38,7 @@
 #include "proposal_dev.cuh"
 #include "sketch_dev.cuh"
 #include "tsketch_dev.cuh"
+#include "tsketch8k_dev.cuh"
 #include "tsolve_dev.cuh"
 
 namespace idl {
@@ -78,9 +79,13 @@ struct BItem {
 };
 
 // stages with a flattened block list (prefix tables, one per stage)
-enum BStage { kBDraw = 0, kBGauss, kBHist, kBScan, kBScatter, kBSortW, kBSortB, kBSketchD, kBSketchT, kBPlanes,
+enum BStage { kBDraw = 0, kBGauss, kBHist, kBScan, kBScatter, kBSortW, kBSortB, kBSketchD, kBSketchT, kBSketchT8,
+              kBPlanes,
               kBGemm, kBReduce, kBPGram, kBPGRed, kBPChol, kBPFeat, kBPMlp, kBPNorm, kBPSel, kBPApply, kBRest, kBRinv,
               kBTgemm, kBLam, kBNumStages };
+
+// stage groups timed by idl_debug_batch_timing
+enum BTimed { kBTDrawBuckets = 0, kBTSketchCP, kBTSketchDense, kBTGauss, kBTProposal, kBTQR, kBTSolve, kBTimedStages };
 
 __device__ __forceinline__ int find_item(const int64_t* __restrict__ pre, int n, int64_t blk) {
   int lo = 0, hi = n - 1;                          // largest p with pre[p] <= blk
@@ -153,12 +158,18 @@ __global__ void b_sortb_kernel(const BItem* __restrict__ items, const int64_t* _
   extern __shared__ int32_t seg[];
   ITEM_OF_BLOCK(pre, n);
   const int count = *it.nbig;
-  for (int q = (int)local; q < count; q += kBSortBlocks) bucket_sort_block_body(it.ptr, it.big[q], it.rows, seg);
+  for (int q = (int)local; q < count; q += kBSortBlocks)
+    bucket_sort_block_body(it.ptr, it.big[q], it.rows, seg, it.h, it.I);
 }
 
+// blk0: first block of this launch in the stage's flattened block list (a launch may
+// cover only the items whose matrices have arrived)
 __global__ void __launch_bounds__(512) b_sketch_dense_kernel(const BItem* __restrict__ items,
-                                                             const int64_t* __restrict__ pre, int n) {
-  ITEM_OF_BLOCK(pre, n);
+                                                             const int64_t* __restrict__ pre, int n, int64_t blk0) {
+  const int64_t gblk = (int64_t)blockIdx.x + blk0;
+  const int p = find_item(pre, n, gblk);
+  const BItem& it = items[p];
+  const int64_t local = gblk - pre[p];
   const int64_t b = local / it.ntiles;
   const int tile = (int)(local % it.ntiles);
   if (it.vec)
@@ -176,6 +187,26 @@ __global__ void __launch_bounds__(kTsMaxThreads, 1) b_sketch_cp_kernel(const BIt
   while ((1LL << logL) < it.m1) ++logL;
   // column-major: column r at Y1 + r * m1 (the Gaussian stage reads each column's K values contiguously)
   tensorsketch_block(it.ts, it.R, (int)it.m1, logL, it.lam, it.Y1, it.m1, true, local * 2, tw, sm2);
+}
+
+// CP items with L = 8192: persistent blocks (one per SM) over the column pairs of all
+// such items; pre counts pairs, not blocks
+__global__ void __launch_bounds__(ts8::kT, 1) b_sketch_cp8k_kernel(const BItem* __restrict__ items,
+                                                                   const int64_t* __restrict__ pre, int n,
+                                                                   const float2* __restrict__ tab) {
+  extern __shared__ __align__(16) float2 sm8[];
+  float2 *z, *tw1, *tw2;
+  ts8::block_setup(sm8, tab, &z, &tw1, &tw2);
+  const int64_t total = pre[n];
+  ts8::Pre pf;
+  for (int64_t g = blockIdx.x; g < total; g += gridDim.x) {
+    const int p = find_item(pre, n, g);
+    const BItem& it = items[p];
+    const int64_t r0 = 2 * (g - pre[p]);
+    ts8::load_mode(it.ts, 0, r0, r0 + 1 < it.R, pf);
+    // column-major: column r at Y1 + r * m1 (the Gaussian stage reads each column's K values contiguously)
+    ts8::pair_body(it.ts, it.R, r0, it.lam, it.Y1, it.m1, true, pf, z, tw1, tw2);
+  }
 }
 
 template <int NP>
@@ -371,6 +402,8 @@ struct idl_batch_state {
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
   const int* d_flags = nullptr;      // certificate flags of the last batch (n ints, device)
   int nflags = 0;
+  cudaStream_t cstream = nullptr;    // host-staged batches: the copies run here
+  std::vector<cudaEvent_t> cev;      // their events (reused)
 };
 
 extern "C" long long idl_launch_count(void);
@@ -386,6 +419,8 @@ void idl_batch_state_free(idl_batch_state* b) {
   if (b->gstream) cudaStreamDestroy(b->gstream);
   if (b->ev_in) cudaEventDestroy(b->ev_in);
   if (b->ev_out) cudaEventDestroy(b->ev_out);
+  if (b->cstream) { cudaStreamSynchronize(b->cstream); cudaStreamDestroy(b->cstream); }
+  for (cudaEvent_t e : b->cev) cudaEventDestroy(e);
   delete b;
 }
 
@@ -393,6 +428,12 @@ void idl_batch_state_free(idl_batch_state* b) {
   do {                              \
     int _rc = (x);                  \
     if (_rc != IDL_OK) return _rc;  \
+  } while (0)
+
+#define TRYC(expr, where)                                   \
+  do {                                                      \
+    cudaError_t _e = (expr);                                \
+    if (_e != cudaSuccess) return cuda_check(ctx, _e, where); \
   } while (0)
 
 static int launch_check(idl_ctx* ctx, const char* where) { return cuda_check(ctx, cudaGetLastError(), where); }
@@ -661,7 +702,8 @@ static int plan_batch(idl_ctx* ctx, const idl_batch_item* items, int n, const Tu
     nb[kBSortW] = d ? cdiv(b.m1, 8) : 0;
     nb[kBSortB] = d ? kBSortBlocks : 0;
     nb[kBSketchD] = d ? b.m1 * b.ntiles : 0;
-    nb[kBSketchT] = cp ? cdiv(b.R, 2) : 0;
+    nb[kBSketchT] = cp && b.m1 != ts8::kL ? cdiv(b.R, 2) : 0;
+    nb[kBSketchT8] = cp && b.m1 == ts8::kL ? cdiv(b.R, 2) : 0;    // column pairs
     nb[kBPlanes] = cdiv(b.nkb * b.NT * 8, 256);
     nb[kBGemm] = b.mtiles * b.splits;
     nb[kBReduce] = cdiv(b.R * b.m2, 256);
@@ -752,15 +794,27 @@ static int run_proposal(idl_ctx* ctx, const BatchPlan& P, const BItem* d_items, 
   return launch_check(ctx, "batch proposal");
 }
 
-// All launches of a batch (the part that is captured into a graph).
+// Host-staged inputs (idl_batch_run with host arrays): events recorded on the copy
+// stream once the CP items' factors are on the device, and once each group of dense
+// items is; dense[g].first = end of group g in the dense-sketch block list.
+struct HostFeed {
+  cudaEvent_t ev_cp = nullptr;
+  std::vector<std::pair<int64_t, cudaEvent_t>> dense;
+};
+
+// All launches of a batch (the part that is captured into a graph).  ms (optional,
+// kBTimedStages floats): CUDA-event times of the stage groups (see BTimed).  feed
+// (optional): the sketches wait for the staged inputs they read, group by group.
 static int run_stages(idl_ctx* ctx, const BatchPlan& P, const BItem* d_items, const int64_t* d_pre,
-                      const int32_t* d_lists, int n, int sketch_threads, int& nlaunch, float* ms_sketch,
-                      float* ms_gemm) {
+                      const int32_t* d_lists, int n, int sketch_threads, int& nlaunch, float* ms,
+                      const HostFeed* feed = nullptr) {
   nlaunch = 0;
-  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
-  const bool timed = ms_sketch || ms_gemm;
+  cudaEvent_t ev[kBTimedStages + 1] = {};
+  const bool timed = ms != nullptr;
   if (timed)
     for (auto& x : ev) cudaEventCreate(&x);
+  auto mark = [&](int i) { if (timed) cudaEventRecord(ev[i], ctx->stream); };
+  mark(0);
   BLAUNCH(b_draw_kernel, kBDraw, 256, 0, ctx->d_status);
   BLAUNCH(b_gauss_draw_kernel, kBGauss, 256, 0);
   BLAUNCH(b_hist_kernel, kBHist, 512, sizeof(int32_t) * (size_t)P.maxL_hist, ctx->d_status);
@@ -769,23 +823,55 @@ static int run_stages(idl_ctx* ctx, const BatchPlan& P, const BItem* d_items, co
   BLAUNCH(b_sortw_kernel, kBSortW, 256, sizeof(int32_t) * 8 * kWarpSortCap);
   BLAUNCH(b_sortb_kernel, kBSortB, 512, sizeof(int32_t) * kBlockSortCap);
   BTRY(launch_check(ctx, "batch buckets"));
-  if (timed) cudaEventRecord(ev[0], ctx->stream);
-  BLAUNCH(b_sketch_dense_kernel, kBSketchD, sketch_threads, 0);
-  if (timed) cudaEventRecord(ev[1], ctx->stream);
+  mark(1);
+  // the TensorSketch first: with host-staged inputs it runs while the dense matrices
+  // are still being copied
+  if (feed && feed->ev_cp) TRYC(cudaStreamWaitEvent(ctx->stream, feed->ev_cp, 0), "batch feed wait");
   if (P.pre[kBSketchT][n] > 0) {
     const size_t smem = ts_smem_bytes(P.maxL_cp);
     cudaError_t e = ensure_smem(ctx, (const void*)b_sketch_cp_kernel, smem);
     if (e != cudaSuccess) return cuda_check(ctx, e, "batch tensorsketch attribute");
     BLAUNCH(b_sketch_cp_kernel, kBSketchT, ts_threads(P.maxL_cp), smem, (const float2*)ctx->ts_tw);
   }
+  if (P.pre[kBSketchT8][n] > 0) {
+    cudaError_t e = ensure_smem(ctx, (const void*)b_sketch_cp8k_kernel, ts8::kSmemBytes);
+    if (e != cudaSuccess) return cuda_check(ctx, e, "batch tensorsketch attribute");
+    const int64_t grid = std::min<int64_t>(P.pre[kBSketchT8][n], ctx->num_sms);
+    b_sketch_cp8k_kernel<<<(unsigned)grid, ts8::kT, ts8::kSmemBytes, ctx->stream>>>(
+        d_items, d_pre + (size_t)kBSketchT8 * (n + 1), n, (const float2*)ctx->ts8_tw);
+    count_launch();
+    ++nlaunch;
+  }
+  mark(2);
+  {
+    const int64_t nbd = P.pre[kBSketchD][n];
+    const int64_t* pre_d = d_pre + (size_t)kBSketchD * (n + 1);
+    if (feed && !feed->dense.empty()) {
+      int64_t b0 = 0;
+      for (const auto& g : feed->dense) {
+        TRYC(cudaStreamWaitEvent(ctx->stream, g.second, 0), "batch feed wait");
+        if (g.first > b0) {
+          b_sketch_dense_kernel<<<(unsigned)(g.first - b0), sketch_threads, 0, ctx->stream>>>(d_items, pre_d, n, b0);
+          count_launch();
+          ++nlaunch;
+        }
+        b0 = g.first;
+      }
+    } else if (nbd > 0) {
+      b_sketch_dense_kernel<<<(unsigned)nbd, sketch_threads, 0, ctx->stream>>>(d_items, pre_d, n, 0);
+      count_launch();
+      ++nlaunch;
+    }
+  }
   BTRY(launch_check(ctx, "batch sketch"));
-  if (timed) cudaEventRecord(ev[2], ctx->stream);
+  mark(3);
   if (P.NP == 1) BTRY(run_gemm_stage<1>(ctx, P, d_items, d_pre, n, nlaunch));
   else if (P.NP == 2) BTRY(run_gemm_stage<2>(ctx, P, d_items, d_pre, n, nlaunch));
   else BTRY(run_gemm_stage<3>(ctx, P, d_items, d_pre, n, nlaunch));
-  if (timed) cudaEventRecord(ev[3], ctx->stream);
   BLAUNCH(b_reduce_kernel, kBReduce, 256, 0);
+  mark(4);
   if (!P.prop_list.empty()) BTRY(run_proposal(ctx, P, d_items, d_pre, d_lists + 2 * (n + 1), n, nlaunch));
+  mark(5);
   if (!P.dense_list.empty()) {
     BTRY(dispatch_b_cpqr(ctx, d_items, d_lists, (int)P.dense_list.size(), P.cfg_dense));
     ++nlaunch;
@@ -794,6 +880,7 @@ static int run_stages(idl_ctx* ctx, const BatchPlan& P, const BItem* d_items, co
     BTRY(dispatch_b_cpqr(ctx, d_items, d_lists + n + 1, (int)P.cp_list.size(), P.cfg_cp));
     ++nlaunch;
   }
+  mark(6);
   BLAUNCH(b_rest_kernel, kBRest, 256, sizeof(int32_t) * (size_t)P.maxK);
   {
     const size_t smem_inv = sizeof(double) * (size_t)P.maxK * (P.maxK + 1);
@@ -806,10 +893,10 @@ static int run_stages(idl_ctx* ctx, const BatchPlan& P, const BItem* d_items, co
   }
   BLAUNCH(b_lam_kernel, kBLam, 256, 0);
   BTRY(launch_check(ctx, "batch solve"));
+  mark(7);
   if (timed) {
-    cudaEventSynchronize(ev[3]);
-    if (ms_sketch) cudaEventElapsedTime(ms_sketch, ev[0], ev[1]);
-    if (ms_gemm) cudaEventElapsedTime(ms_gemm, ev[2], ev[3]);
+    cudaEventSynchronize(ev[kBTimedStages]);
+    for (int i = 0; i < kBTimedStages; ++i) cudaEventElapsedTime(&ms[i], ev[i], ev[i + 1]);
     for (auto& x : ev) cudaEventDestroy(x);
   }
   return IDL_OK;
@@ -855,18 +942,152 @@ static int upload(idl_ctx* ctx, BatchPlan& P, unsigned char* ws, unsigned char* 
   return cuda_check(ctx, e, "batch upload");
 }
 
+// ---------------------------------------------------------------------------
+// Host arrays.  The batch's inputs are copied into one device staging buffer on
+// the context's copy stream -- the CP items' factors and s-values first, then the
+// dense matrices in groups -- while the kernels run on the context's stream and
+// wait only for what they read (HostFeed); the outputs are copied back at the end.
+// ---------------------------------------------------------------------------
+struct HostStage {
+  struct Copy { size_t off; const void* host; size_t bytes; };
+  std::vector<Copy> in_cp, in_dense, out;
+  std::vector<int> dense_item;       // item index of each in_dense entry
+  size_t bytes = 0;
+  unsigned char* base = nullptr;
+};
+
+static int stage_layout(idl_ctx* ctx, const idl_batch_item* items, int n, std::vector<idl_batch_item>& dv,
+                        HostStage& hs) {
+  dv.assign(items, items + n);
+  size_t off = 0;
+  auto take = [&](size_t bytes) { const size_t o = off; off += (bytes + 255) & ~(size_t)255; return o; };
+  for (int i = 0; i < n; ++i) {
+    const idl_batch_item& x = items[i];
+    if (x.K < 1 || x.K >= x.R || x.R > 0x7fffffffLL) return fail(ctx, IDL_EINVAL, "batch: need 1 <= K < R");
+    if (x.kind == IDL_ITEM_DENSE) {
+      if (!x.A || x.I < 1 || x.lda < x.R) return fail(ctx, IDL_EINVAL, "batch: dense item");
+      const size_t b = sizeof(float) * (size_t)((x.I - 1) * x.lda + x.R);
+      hs.in_dense.push_back({take(b), x.A, b});
+      hs.dense_item.push_back(i);
+      dv[i].A = (const float*)(uintptr_t)hs.in_dense.back().off;
+    } else if (x.kind == IDL_ITEM_CP) {
+      if (x.N < 1 || x.N > 8 || !x.lambda) return fail(ctx, IDL_EINVAL, "batch: CP item");
+      for (int q = 0; q < x.N; ++q) {
+        if (!x.factors[q] || x.dims[q] < 1) return fail(ctx, IDL_EINVAL, "batch: CP factor");
+        const size_t b = sizeof(float) * (size_t)(x.dims[q] * x.R);
+        hs.in_cp.push_back({take(b), x.factors[q], b});
+        dv[i].factors[q] = (const float*)(uintptr_t)hs.in_cp.back().off;
+      }
+      const size_t b = sizeof(double) * (size_t)x.R;
+      hs.in_cp.push_back({take(b), x.lambda, b});
+      dv[i].lambda = (const double*)(uintptr_t)hs.in_cp.back().off;
+    } else {
+      return fail(ctx, IDL_EINVAL, "batch: item kind must be IDL_ITEM_DENSE or IDL_ITEM_CP");
+    }
+    if (!x.J || !x.T || (x.kind == IDL_ITEM_CP && !x.lambda_hat)) return fail(ctx, IDL_EINVAL, "batch: outputs");
+    hs.out.push_back({take(sizeof(int32_t) * (size_t)x.K), x.J, sizeof(int32_t) * (size_t)x.K});
+    dv[i].J = (int32_t*)(uintptr_t)hs.out.back().off;
+    hs.out.push_back({take(sizeof(double) * (size_t)(x.K * (x.R - x.K))), x.T, sizeof(double) * (size_t)(x.K * (x.R - x.K))});
+    dv[i].T = (double*)(uintptr_t)hs.out.back().off;
+    if (x.kind == IDL_ITEM_CP) {
+      hs.out.push_back({take(sizeof(double) * (size_t)x.K), x.lambda_hat, sizeof(double) * (size_t)x.K});
+      dv[i].lambda_hat = (double*)(uintptr_t)hs.out.back().off;
+    }
+  }
+  hs.bytes = off;
+  hs.base = (unsigned char*)ws_get(ctx, kWsBatchIn, off);
+  if (!hs.base) return IDL_ENOMEM;
+  auto fix = [&](auto& ptr) {
+    using P = std::remove_reference_t<decltype(ptr)>;
+    ptr = (P)(hs.base + (size_t)(uintptr_t)ptr);
+  };
+  for (int i = 0; i < n; ++i) {
+    if (dv[i].kind == IDL_ITEM_DENSE) fix(dv[i].A);
+    else {
+      for (int q = 0; q < dv[i].N; ++q) fix(dv[i].factors[q]);
+      fix(dv[i].lambda);
+      fix(dv[i].lambda_hat);
+    }
+    fix(dv[i].J);
+    fix(dv[i].T);
+  }
+  return IDL_OK;
+}
+
+static cudaEvent_t stage_event(idl_batch_state* bs, size_t i) {
+  while (bs->cev.size() <= i) {
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return nullptr;
+    bs->cev.push_back(e);
+  }
+  return bs->cev[i];
+}
+
+// Issues the input copies on the copy stream (after the context stream's queued
+// work, which may still read the staging buffer) and fills feed; groups: dense
+// groups wanted.
+static int stage_inputs(idl_ctx* ctx, idl_batch_state* bs, const HostStage& hs, const BatchPlan& P, int n,
+                        int groups, HostFeed* feed) {
+  if (!bs->cstream) TRYC(cudaStreamCreateWithFlags(&bs->cstream, cudaStreamNonBlocking), "batch copy stream");
+  cudaEvent_t ev0 = stage_event(bs, 0);
+  if (!ev0) return fail(ctx, IDL_ECUDA, "batch: event creation failed");
+  TRYC(cudaEventRecord(ev0, ctx->stream), "batch stage order");
+  TRYC(cudaStreamWaitEvent(bs->cstream, ev0, 0), "batch stage order");
+  for (const auto& c : hs.in_cp)
+    TRYC(cudaMemcpyAsync(hs.base + c.off, c.host, c.bytes, cudaMemcpyDefault, bs->cstream), "batch copy in");
+  size_t ne = 1;
+  feed->ev_cp = stage_event(bs, ne++);
+  if (!feed->ev_cp) return fail(ctx, IDL_ECUDA, "batch: event creation failed");
+  TRYC(cudaEventRecord(feed->ev_cp, bs->cstream), "batch copy event");
+  size_t tot = 0;
+  for (const auto& c : hs.in_dense) tot += c.bytes;
+  const size_t per = tot / (size_t)std::max(1, groups) + 1;
+  size_t acc = 0;
+  for (size_t q = 0; q < hs.in_dense.size(); ++q) {
+    const auto& c = hs.in_dense[q];
+    TRYC(cudaMemcpyAsync(hs.base + c.off, c.host, c.bytes, cudaMemcpyDefault, bs->cstream), "batch copy in");
+    acc += c.bytes;
+    const bool last = q + 1 == hs.in_dense.size();
+    if (acc >= per || last) {
+      // the group ends with item dense_item[q]: its dense-sketch blocks end at pre[item + 1]
+      cudaEvent_t e = stage_event(bs, ne++);
+      if (!e) return fail(ctx, IDL_ECUDA, "batch: event creation failed");
+      TRYC(cudaEventRecord(e, bs->cstream), "batch copy event");
+      const int64_t end = last ? P.pre[kBSketchD][n] : P.pre[kBSketchD][hs.dense_item[q] + 1];
+      feed->dense.push_back({end, e});
+      acc = 0;
+    }
+  }
+  return IDL_OK;
+}
+
+static int stage_outputs(idl_ctx* ctx, const HostStage& hs) {
+  for (const auto& c : hs.out)
+    TRYC(cudaMemcpyAsync((void*)c.host, hs.base + c.off, c.bytes, cudaMemcpyDefault, ctx->stream), "batch copy out");
+  TRYC(cudaStreamSynchronize(ctx->stream), "batch sync");
+  return IDL_OK;
+}
+
 extern "C" int idl_batch_run(idl_ctx* ctx, const idl_batch_item* items, int n) {
-  if (!ctx) return IDL_EINVAL;
-  if (cudaSetDevice(ctx->device) != cudaSuccess) return IDL_ECUDA;
+  BTRY(ctx_usable(ctx));
   if (n < 1 || !items) return fail(ctx, IDL_EINVAL, "batch: need n >= 1 items");
   idl_batch_state* bs = bstate(ctx);
+  // host arrays: decided by the first item's input; the whole batch is then staged
+  const void* first = items[0].kind == IDL_ITEM_DENSE ? (const void*)items[0].A : (const void*)items[0].factors[0];
+  const bool host = first && !is_device_ptr(first);
+  std::vector<idl_batch_item> staged;
+  HostStage hs;
+  if (host) {
+    BTRY(stage_layout(ctx, items, n, staged, hs));
+    items = staged.data();
+  }
   const std::string sig = signature(items, n);
   const uint64_t key = fnv1a(sig);
   const bool known = bs->tune.count(key) != 0;
   Tune tn = known ? bs->tune[key] : Tune();
   BatchPlan P;
   BTRY(plan_batch(ctx, items, n, tn, P));
-  if (!P.cp_list.empty() && !ts_twiddles(ctx)) return IDL_ENOMEM;    // built before any capture
+  if (!P.cp_list.empty() && (!ts_twiddles(ctx) || !ts8_twiddles(ctx))) return IDL_ENOMEM;   // built before any capture
   unsigned char* ws = (unsigned char*)ws_get(ctx, kWsBatch, P.ws_bytes);
   unsigned char* tab = (unsigned char*)ws_get(ctx, kWsBatchTab, P.table_bytes);
   if (!ws || !tab) return IDL_ENOMEM;
@@ -875,6 +1096,12 @@ extern "C" int idl_batch_run(idl_ctx* ctx, const idl_batch_item* items, int n) {
   const int32_t* d_lists = (const int32_t*)(tab + P.off_lists);
   int nlaunch = 0;
   if (!known && !ctx->batch_no_tune) {
+    if (host) {       // the tuning runs read the inputs: stage them all first
+      HostFeed f0;
+      BTRY(stage_inputs(ctx, bs, hs, P, n, 1, &f0));
+      for (const auto& g : f0.dense) TRYC(cudaStreamWaitEvent(ctx->stream, g.second, 0), "batch stage wait");
+      TRYC(cudaStreamWaitEvent(ctx->stream, f0.ev_cp, 0), "batch stage wait");
+    }
     // autotune: dense sketch block width, then the Gaussian split-K factor
     float best = 1e30f;
     for (int th : {128, 256, 512}) {
@@ -886,10 +1113,10 @@ extern "C" int idl_batch_run(idl_ctx* ctx, const idl_batch_item* items, int n) {
       unsigned char* tab2 = (unsigned char*)ws_get(ctx, kWsBatchTab, Q.table_bytes);
       if (!ws2 || !tab2) return IDL_ENOMEM;
       BTRY(upload(ctx, Q, ws2, tab2, n));
-      float ms_s = 0.f;
+      float ms[kBTimedStages] = {};
       BTRY(run_stages(ctx, Q, (const BItem*)(tab2 + Q.off_items), (const int64_t*)(tab2 + Q.off_pre),
-                      (const int32_t*)(tab2 + Q.off_lists), n, th, nlaunch, &ms_s, nullptr));
-      if (ms_s < best) { best = ms_s; tn.sketch_threads = th; }
+                      (const int32_t*)(tab2 + Q.off_lists), n, th, nlaunch, ms));
+      if (ms[kBTSketchDense] < best) { best = ms[kBTSketchDense]; tn.sketch_threads = th; }
     }
     best = 1e30f;
     for (int sm : {1, 2}) {
@@ -901,10 +1128,10 @@ extern "C" int idl_batch_run(idl_ctx* ctx, const idl_batch_item* items, int n) {
       unsigned char* tab2 = (unsigned char*)ws_get(ctx, kWsBatchTab, Q.table_bytes);
       if (!ws2 || !tab2) return IDL_ENOMEM;
       BTRY(upload(ctx, Q, ws2, tab2, n));
-      float ms_g = 0.f;
+      float ms[kBTimedStages] = {};
       BTRY(run_stages(ctx, Q, (const BItem*)(tab2 + Q.off_items), (const int64_t*)(tab2 + Q.off_pre),
-                      (const int32_t*)(tab2 + Q.off_lists), n, tn.sketch_threads, nlaunch, nullptr, &ms_g));
-      if (ms_g < best) { best = ms_g; tn.split_mult = sm; }
+                      (const int32_t*)(tab2 + Q.off_lists), n, tn.sketch_threads, nlaunch, ms));
+      if (ms[kBTGauss] < best) { best = ms[kBTGauss]; tn.split_mult = sm; }
     }
     bs->tune[key] = tn;
     P = BatchPlan();
@@ -919,7 +1146,13 @@ extern "C" int idl_batch_run(idl_ctx* ctx, const idl_batch_item* items, int n) {
   BTRY(upload(ctx, P, ws, tab, n));
   bs->d_flags = (const int*)(ws + P.off_flags);
   bs->nflags = n;
-  if (ctx->batch_no_graph) return run_stages(ctx, P, d_items, d_pre, d_lists, n, tn.sketch_threads, nlaunch, nullptr, nullptr);
+  if (host) {         // eager launches that wait for their inputs group by group
+    HostFeed feed;
+    BTRY(stage_inputs(ctx, bs, hs, P, n, 8, &feed));
+    BTRY(run_stages(ctx, P, d_items, d_pre, d_lists, n, tn.sketch_threads, nlaunch, nullptr, &feed));
+    return stage_outputs(ctx, hs);
+  }
+  if (ctx->batch_no_graph) return run_stages(ctx, P, d_items, d_pre, d_lists, n, tn.sketch_threads, nlaunch, nullptr);
   // graph: captured once per (shape, workspace address) on a private stream, replayed afterwards;
   // events order it after the caller's stream and the caller's stream after it
   if (!bs->gstream) {
@@ -937,7 +1170,7 @@ extern "C" int idl_batch_run(idl_ctx* ctx, const idl_batch_item* items, int n) {
     cudaError_t e = cudaStreamBeginCapture(bs->gstream, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) { ctx->stream = user; return cuda_check(ctx, e, "batch capture begin"); }
     const long long before = idl_launch_count();
-    const int rc = run_stages(ctx, P, d_items, d_pre, d_lists, n, tn.sketch_threads, nlaunch, nullptr, nullptr);
+    const int rc = run_stages(ctx, P, d_items, d_pre, d_lists, n, tn.sketch_threads, nlaunch, nullptr);
     e = cudaStreamEndCapture(bs->gstream, &g);
     ctx->stream = user;
     if (rc != IDL_OK) { if (g) cudaGraphDestroy(g); return rc; }
@@ -991,23 +1224,26 @@ extern "C" int idl_tune_load(idl_ctx* ctx, const char* path) {
   return loaded >= 0 ? IDL_OK : IDL_EINVAL;
 }
 
-// Runs the batch once without the graph, with CUDA events around the dense sketch
-// and the Gaussian stage (ms[0], ms[1]); used to attribute time to the kernels.
+// Runs the batch once without the graph, with CUDA events around the stage groups:
+// ms[0] draws and bucket offsets, [1] dense sketch, [2] CP TensorSketch, [3] Gaussian
+// stage, [4] column proposal, [5] pivoted QR, [6] T solve and lambda_hat.  Used to
+// attribute time to the kernels.
 extern "C" int idl_debug_batch_timing(idl_ctx* ctx, const idl_batch_item* items, int n, float* ms) {
-  if (!ctx || !items || n < 1 || !ms) return IDL_EINVAL;
+  BTRY(ctx_usable(ctx));
+  if (!items || n < 1 || !ms) return IDL_EINVAL;
   idl_batch_state* bs = bstate(ctx);
   const uint64_t key = fnv1a(signature(items, n));
   Tune tn = bs->tune.count(key) ? bs->tune[key] : Tune();
   BatchPlan P;
   BTRY(plan_batch(ctx, items, n, tn, P));
-  if (!P.cp_list.empty() && !ts_twiddles(ctx)) return IDL_ENOMEM;    // built before any capture
+  if (!P.cp_list.empty() && (!ts_twiddles(ctx) || !ts8_twiddles(ctx))) return IDL_ENOMEM;   // built before any capture
   unsigned char* ws = (unsigned char*)ws_get(ctx, kWsBatch, P.ws_bytes);
   unsigned char* tab = (unsigned char*)ws_get(ctx, kWsBatchTab, P.table_bytes);
   if (!ws || !tab) return IDL_ENOMEM;
   BTRY(upload(ctx, P, ws, tab, n));
   int nl = 0;
   return run_stages(ctx, P, (const BItem*)(tab + P.off_items), (const int64_t*)(tab + P.off_pre),
-                    (const int32_t*)(tab + P.off_lists), n, tn.sketch_threads, nl, &ms[0], &ms[1]);
+                    (const int32_t*)(tab + P.off_lists), n, tn.sketch_threads, nl, ms);
 }
 
 extern "C" int idl_batch_fallbacks(idl_ctx* ctx) {

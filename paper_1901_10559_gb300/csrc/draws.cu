@@ -94,10 +94,11 @@ __global__ void bucket_sort_warp_kernel(const int32_t* __restrict__ ptr, int64_t
 }
 
 __global__ void bucket_sort_block_kernel(const int32_t* __restrict__ ptr, int32_t* __restrict__ row_list,
-                                         const int32_t* __restrict__ big, const int32_t* __restrict__ nbig) {
+                                         const int32_t* __restrict__ big, const int32_t* __restrict__ nbig,
+                                         const int32_t* __restrict__ h, int64_t I) {
   extern __shared__ int32_t seg[];
   const int count = *nbig;
-  for (int q = blockIdx.x; q < count; q += gridDim.x) bucket_sort_block_body(ptr, big[q], row_list, seg);
+  for (int q = blockIdx.x; q < count; q += gridDim.x) bucket_sort_block_body(ptr, big[q], row_list, seg, h, I);
 }
 
 __global__ void __launch_bounds__(256) stable_count_kernel(const int32_t* __restrict__ h, int64_t I, int L,
@@ -168,7 +169,8 @@ int launch_bucket_offsets(idl_ctx* ctx, const int32_t* h, int64_t I, int64_t L, 
     int warps = 8;
     bucket_sort_warp_kernel<<<(unsigned)cdiv(L, warps), warps * 32, sizeof(int32_t) * warps * kWarpSortCap, st>>>(
         bucket_ptr, L, row_list, big, nbig), idl::count_launch();
-    bucket_sort_block_kernel<<<64, 512, sizeof(int32_t) * kBlockSortCap, st>>>(bucket_ptr, row_list, big, nbig), idl::count_launch();
+    bucket_sort_block_kernel<<<64, 512, sizeof(int32_t) * kBlockSortCap, st>>>(bucket_ptr, row_list, big, nbig, h, I),
+        idl::count_launch();
   }
   return cuda_check(ctx, cudaGetLastError(), "bucket offsets");
 }

@@ -181,12 +181,65 @@ __device__ __forceinline__ void bucket_sort_warp_body(const int32_t* __restrict_
   }
 }
 
-// one block: rank sort of the rows of bucket b (up to kBlockSortCap; larger ones
-// stay in arrival order).  seg: kBlockSortCap ints.
+// one block: the rows of bucket b written in increasing order by one pass over all
+// of h (for buckets above kBlockSortCap rows).  Each thread takes 16 consecutive
+// rows of a chunk, a block-wide prefix of the per-thread match counts places them.
+// sh: >= 32 ints of shared memory.
+__device__ __forceinline__ void bucket_rescan_block_body(const int32_t* __restrict__ h, int64_t I,
+                                                         const int32_t* __restrict__ ptr, int32_t b,
+                                                         int32_t* __restrict__ row_list, int32_t* sh) {
+  constexpr int E = 16;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  int32_t base = ptr[b];
+  const int64_t chunk = (int64_t)blockDim.x * E;
+  for (int64_t c0 = 0; c0 < I; c0 += chunk) {
+    const int64_t i0 = c0 + (int64_t)threadIdx.x * E;
+    int hv[E];
+#pragma unroll
+    for (int u = 0; u < E; ++u) hv[u] = i0 + u < I ? __ldg(h + i0 + u) : -1;
+    unsigned m = 0;
+#pragma unroll
+    for (int u = 0; u < E; ++u) m |= (hv[u] == b ? 1u : 0u) << u;
+    const int cnt = __popc(m);
+    int x = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) sh[w] = x;
+    __syncthreads();
+    if (w == 0) {
+      int t = lane < nw ? sh[lane] : 0;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, t, o);
+        if (lane >= o) t += y;
+      }
+      if (lane < nw) sh[lane] = t;                       // inclusive prefix over the warps
+    }
+    __syncthreads();
+    int pos = base + (w ? sh[w - 1] : 0) + x - cnt;
+    const int32_t total = sh[nw - 1];
+#pragma unroll
+    for (int u = 0; u < E; ++u)
+      if ((m >> u) & 1u) row_list[pos++] = (int32_t)(i0 + u);
+    __syncthreads();                                     // sh is reused by the next chunk
+    base += total;
+  }
+}
+
+// one block: rank sort of the rows of bucket b (up to kBlockSortCap; larger ones are
+// rewritten in increasing order by a pass over h).  seg: kBlockSortCap ints.
 __device__ __forceinline__ void bucket_sort_block_body(const int32_t* __restrict__ ptr, int32_t b,
-                                                       int32_t* __restrict__ row_list, int32_t* seg) {
+                                                       int32_t* __restrict__ row_list, int32_t* seg,
+                                                       const int32_t* __restrict__ h, int64_t I) {
   const int a0 = ptr[b], n = ptr[b + 1] - a0;
-  if (n > kBlockSortCap) return;
+  if (n > kBlockSortCap) {
+    __syncthreads();
+    bucket_rescan_block_body(h, I, ptr, b, row_list, seg);
+    return;
+  }
   __syncthreads();
   for (int j = threadIdx.x; j < n; j += blockDim.x) seg[j] = row_list[a0 + j];
   __syncthreads();

@@ -122,3 +122,36 @@ int launch_gaussian_tc(idl_ctx* ctx, const double* Omega, int64_t m2, int64_t m1
 }
 
 }  // namespace idl
+
+// ---------------------------------------------------------------------------
+// Failure detection without a fault: one warp waits, through the same bounded
+// mbarrier wait as the Gaussian stage, for a phase that completes only when the
+// caller asks for the arrival (arrive != 0).  Without it the wait gives up after
+// limit_ns and the kernel records IDL_ETIMEOUT in the status word and returns.
+// ---------------------------------------------------------------------------
+namespace idl {
+
+__global__ void wait_probe_kernel(int arrive, uint64_t limit_ns, int* status) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) {
+    tc::mbar_init(&bar, 1);
+    tc::fence_barrier_init();
+  }
+  __syncwarp();
+  if (threadIdx.x == 0 && arrive) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc::smem_u32(&bar)) : "memory");
+  __syncwarp();
+  const bool done = tc::mbar_wait(&bar, 0, limit_ns);
+  if (!done && threadIdx.x == 0) set_status(status, IDL_ETIMEOUT);
+}
+
+}  // namespace idl
+
+// Test hook (not in the public header): runs the wait probe on the context's stream.
+extern "C" int idl_debug_wait_probe(idl_ctx* ctx, int arrive, unsigned long long limit_ns) {
+  using namespace idl;
+  const int rc = ctx_usable(ctx);
+  if (rc != IDL_OK) return rc;
+  if (limit_ns < 1000ull || limit_ns > tc::kTimeoutNs) return fail(ctx, IDL_EINVAL, "wait probe: limit in [1 us, 1 s]");
+  wait_probe_kernel<<<1, 32, 0, ctx->stream>>>(arrive, (uint64_t)limit_ns, ctx->d_status), count_launch();
+  return cuda_check(ctx, cudaGetLastError(), "wait probe");
+}

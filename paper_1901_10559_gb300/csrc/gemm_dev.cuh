@@ -40,13 +40,14 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   return done != 0;
 }
 
-// Bounded wait: true when the phase of the given parity completed, false after ~1 s.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+// Bounded wait: true when the phase of the given parity completed, false once
+// limit_ns (default 1 s) of %globaltimer time have passed.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint64_t limit_ns = kTimeoutNs) {
   if (mbar_try_wait(bar, parity)) return true;
   const uint64_t t0 = global_timer();
   while (true) {
     if (mbar_try_wait(bar, parity)) return true;
-    if (global_timer() - t0 > kTimeoutNs) return false;
+    if (global_timer() - t0 > limit_ns) return false;
   }
 }
 

@@ -15,6 +15,7 @@ void idl_batch_state_free(idl_batch_state* b);
 // A single-problem pipeline captured as a CUDA graph (idl_set_graphs).
 struct PipeGraph {
   uint64_t key = 0;                // hash of the call's arguments
+  std::string raw;                 // the arguments' bytes (compared in full before a replay)
   uint64_t gen = 0;                // workspace generation the graph's addresses belong to
   cudaGraphExec_t exec = nullptr;
   long long launches = 0;          // kernels in the graph (the launch counter adds them per replay)
@@ -46,9 +47,11 @@ struct idl_ctx {
   int batch_no_graph = 0;      // 1: run batches without graph capture (tests)
   int batch_no_tune = 0;       // 1: skip the first-call tuning runs (tests)
   void* ts_tw = nullptr;       // FFT twiddle table of the TensorSketch kernels (built on first use)
+  void* ts8_tw = nullptr;      // twiddle table of the L = 8192 TensorSketch kernels (built on first use)
   float* mlp = nullptr;        // proposal MLP: FP32 master weights | Adam first moments | second moments
   bool mlp_ready = false;
   long long mlp_step = 0;      // Adam steps taken since the weights were set
+  bool poisoned = false;       // a bounded device wait expired: every later call returns IDL_ETIMEOUT
   size_t fail_alloc_at = 0;    // test hook: fail the n-th workspace allocation (0 = never)
   size_t alloc_count = 0;
   // per-stage CUDA-event profiling (idl_profile / idl_profile_read)
@@ -65,7 +68,7 @@ enum Slot {
   kWsH = 0, kWsS, kWsOmega, kWsBucketPtr, kWsRowList, kWsCursor, kWsBig, kWsY1, kWsPart,
   kWsY2, kWsOmegaConv, kWsRest, kWsA, kWsRowptr, kWsColidx, kWsVals, kWsJ, kWsT,
   kWsModeH, kWsModeS, kWsLam, kWsLamHat, kWsCpqrSync, kWsRinv, kWsBatch, kWsBatchTab, kWsYf, kWsProp,
-  kWsPropGram, kWsPropTrain, kWsPropCopy, kWsCount
+  kWsPropGram, kWsPropTrain, kWsPropCopy, kWsBatchIn, kWsFactors, kWsCount
 };
 
 // Returns a device buffer of at least `bytes` for the slot (grown on demand), or
@@ -73,6 +76,10 @@ enum Slot {
 void* ws_get(idl_ctx* ctx, int slot, size_t bytes);
 
 int fail(idl_ctx* ctx, int code, const std::string& msg);
+// IDL_OK when ctx is non-null, not poisoned (see idl_ctx::poisoned) and its device is made current
+int ctx_usable(idl_ctx* ctx);
+// true for memory of a device (or managed memory); false for host memory and NULL
+bool is_device_ptr(const void* p);
 void ctx_add_launches(long long d);   // adjusts the process-wide launch counter (graph replays)
 int cuda_check(idl_ctx* ctx, cudaError_t e, const char* where);
 // cudaFuncSetAttribute(MaxDynamicSharedMemorySize) only when kern needs more than
@@ -146,6 +153,7 @@ int launch_proposal_qr(idl_ctx* ctx, const float* Y2, float* Yf, int64_t m, int6
 
 // tensorsketch.cu
 const float2* ts_twiddles(idl_ctx* ctx);
+const float2* ts8_twiddles(idl_ctx* ctx);
 int launch_tensorsketch(idl_ctx* ctx, int N, const int64_t* dims, int64_t R, const void* const* factors,
                         const int64_t* ldf, const double* lambda, const int32_t* const* hs,
                         const int8_t* const* ss, int64_t L, float* Y, int64_t ldy, bool colmajor);

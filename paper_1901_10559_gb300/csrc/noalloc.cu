@@ -31,7 +31,8 @@ __global__ void bucket_scatter_kernel(const int32_t* __restrict__ h, int64_t I, 
 __global__ void bucket_sort_warp_kernel(const int32_t* __restrict__ ptr, int64_t L, int32_t* __restrict__ row_list,
                                         int32_t* __restrict__ big, int32_t* __restrict__ nbig);
 __global__ void bucket_sort_block_kernel(const int32_t* __restrict__ ptr, int32_t* __restrict__ row_list,
-                                         const int32_t* __restrict__ big, const int32_t* __restrict__ nbig);
+                                         const int32_t* __restrict__ big, const int32_t* __restrict__ nbig,
+                                         const int32_t* __restrict__ h, int64_t I);
 
 namespace {
 
@@ -115,7 +116,7 @@ extern "C" int idl_bucket_offsets_noalloc(void* stream, const int32_t* h, int64_
   const int warps = 8;
   bucket_sort_warp_kernel<<<(unsigned)cdiv(L, warps), warps * 32, sizeof(int32_t) * warps * 1024, st>>>(
       bucket_ptr, L, row_list, big, nbig), count_launch();
-  bucket_sort_block_kernel<<<64, 512, sizeof(int32_t) * 12288, st>>>(bucket_ptr, row_list, big, nbig),
+  bucket_sort_block_kernel<<<64, 512, sizeof(int32_t) * 12288, st>>>(bucket_ptr, row_list, big, nbig, h, I),
       count_launch();
   if (cudaGetLastError() != cudaSuccess) return IDL_ECUDA;
   return IDL_OK;

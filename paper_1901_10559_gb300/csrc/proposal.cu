@@ -293,10 +293,7 @@ static bool dev_ptr(const void* p) {
   return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
-static int ctx_ok(idl_ctx* ctx) {
-  if (!ctx) return IDL_EINVAL;
-  return cudaSetDevice(ctx->device) == cudaSuccess ? IDL_OK : IDL_ECUDA;
-}
+static int ctx_ok(idl_ctx* ctx) { return ctx_usable(ctx); }
 
 extern "C" int idl_mlp_set_weights(idl_ctx* ctx, const float* theta) {
   TRY(ctx_ok(ctx));

@@ -207,3 +207,34 @@ def batch_matrix_specs(n: int, seed: int):
         d = float(rng.uniform(0.7, 0.95))
         out.append(dict(I=I, R=R, rank=r, decay=d, seed=int(seed * 1000 + b)))
     return out
+
+
+def batch_dense_item(spec: dict, seed: int, dtype=np.float32) -> np.ndarray:
+    """One dense matrix of the batched workload (numpy, host): A = U diag(sigma) V^T
+    + noise with U (I x r), V (R x r) N(0,1) scaled by 1/sqrt(I), 1/sqrt(R),
+    sigma_i = d^i (i = 1..r) and N(0,1) noise of scale 1e-6 d / sqrt(max(I, R)).
+    The GPU bench draws the same recipe with torch on the device."""
+    rng = _rng(seed)
+    I, R, r, d = spec["I"], spec["R"], spec["rank"], spec["decay"]
+    U = rng.standard_normal((I, r)) / np.sqrt(I)
+    V = rng.standard_normal((R, r)) / np.sqrt(R)
+    sig = d ** np.arange(1, r + 1, dtype=np.float64)
+    A = (U * sig[None, :]) @ V.T
+    A += (1e-6 * d / np.sqrt(max(I, R))) * rng.standard_normal((I, R))
+    return np.ascontiguousarray(A.astype(dtype))
+
+
+def batch_cp_lambda(R: int, K: int) -> np.ndarray:
+    """s-values of a CP item of the batched workload: 10^(-6 r / K) for r < K
+    (0-based), 1e-6 beyond (a paper-shaped decay to the target rank K)."""
+    r = np.arange(R, dtype=np.float64)
+    return np.where(r < K, 10.0 ** (-6.0 * r / K), 1e-6)
+
+
+def batch_cp_item(b: int, seed: int, dims=(200, 200, 200, 200), R: int = 5000):
+    """CP item b of the batched workload (numpy, host): N(0,1) unit-norm factor
+    columns, K cycling over (16, 32, 48, 64), s-values batch_cp_lambda(R, K).
+    Returns (factors (I_n x R each, float32), lam, K)."""
+    K = (16, 32, 48, 64)[b % 4]
+    facs, lam = cp_factors(dims, R, seed=seed, lam=batch_cp_lambda(R, K))
+    return facs, lam, K

@@ -27,9 +27,10 @@ def _dense_problems(seed):
 
 def _cp_problems(seed):
     probs = []
-    for b, (dims, R, K) in enumerate([((40, 30, 20), 300, 16), ((50, 50, 50, 50), 500, 32)]):
+    # one item per TensorSketch kernel: L = 1024 (per-pair blocks) and L = 8192 (persistent blocks)
+    for b, (dims, R, K, L) in enumerate([((40, 30, 20), 300, 16, 1024), ((50, 50, 50, 50), 501, 32, 8192)]):
         facs, lam = cp_factors(dims, R, seed=seed + b, lam=10.0 ** (-6.0 * np.minimum(np.arange(R), K) / K))
-        probs.append(dict(facs=facs, lam=lam, K=K, L=1024, m2=K + 10, seed=2000 + b))
+        probs.append(dict(facs=facs, lam=lam, K=K, L=L, m2=K + 10, seed=2000 + b))
     return probs
 
 
@@ -176,3 +177,38 @@ def test_batch_with_proposal_matches_plain(ctx, graph):
         assert np.linalg.norm(t1 - t0) <= 1e-2 * np.linalg.norm(t0)
         if l0 is not None:
             assert np.allclose(host(l0), host(l1), rtol=1e-2, atol=1e-9)
+
+
+def test_batch_host_arrays_match_device_arrays(ctx):
+    """The same batch with every array in pinned host memory: idl_batch_run stages the
+    inputs (the TensorSketch waits only for the CP factors, the dense sketch for each
+    group of matrices) and copies the outputs back; results equal the device call's."""
+    dense, cps = _dense_problems(17), _cp_problems(19)
+    items, outs, keep = _build(dense, cps)
+    idl.idl_batch_run(ctx, items)
+    assert ctx.sync() == idl.IDL_OK
+    hitems, houts = [], []
+    for it, pr in zip(items[:len(dense)], dense):
+        A = torch.from_numpy(pr["A"]).pin_memory()
+        K, R = pr["K"], pr["A"].shape[1]
+        J = torch.full((K,), -1, dtype=torch.int32).pin_memory()
+        T = torch.empty(K * (R - K), dtype=torch.float64).pin_memory()
+        hitems.append(idl.dense_item(A, K, it.params, J, T))
+        houts.append((J, T, None, A))
+    for it, pr in zip(items[len(dense):], cps):
+        fs = [torch.from_numpy(np.ascontiguousarray(F.T)).pin_memory() for F in pr["facs"]]
+        lam = torch.from_numpy(pr["lam"]).pin_memory()
+        K, R = pr["K"], pr["facs"][0].shape[1]
+        J = torch.full((K,), -1, dtype=torch.int32).pin_memory()
+        T = torch.empty(K * (R - K), dtype=torch.float64).pin_memory()
+        lh = torch.empty(K, dtype=torch.float64).pin_memory()
+        hitems.append(idl.cp_item(fs, lam, K, it.params, J, T, lh))
+        houts.append((J, T, lh, fs, lam))
+    for _ in range(2):                                   # the second call reuses the staging buffer
+        idl.idl_batch_run(ctx, hitems)
+        for (Jd, Td, ld), (Jh, Th, lh, *_) in zip(outs, houts):
+            assert np.array_equal(host(Jd), Jh.numpy())
+            assert np.array_equal(host(Td), Th.numpy())
+            if ld is not None:
+                assert np.array_equal(host(ld), lh.numpy())
+    assert ctx.sync() == idl.IDL_OK

@@ -227,6 +227,27 @@ def test_host_pointer_calls_match_device_calls(ctx):
     # so the last bits of T) may differ between calls; J and T agree to FP32 rounding
     assert np.array_equal(Jh2, host(Jd2))
     assert np.allclose(Th2, host(Td2), rtol=1e-4, atol=1e-6)
+    # CP tensor with host factors and s-values (pinned and pageable) and host outputs
+    facs, lam = cp_factors((300, 200, 100), 120, seed=12)
+    Kc = 10
+    pc = idl.make_params(8192, 20, seed=3, modified=False, precision=idl.PREC_FP32)
+    Jd3, Td3 = _outputs(Kc, 120)
+    lhd = torch.empty(Kc, dtype=torch.float64, device="cuda")
+    idl.id_cp_tensor(ctx, [dev(np.ascontiguousarray(F.T)) for F in facs], dev(lam), Kc, pc, Jd3, Td3, lhd)
+    for pin in (False, True):
+        fh = [torch.from_numpy(np.ascontiguousarray(F.T)) for F in facs]
+        lam_h = torch.from_numpy(lam)
+        if pin:
+            fh, lam_h = [f.pin_memory() for f in fh], lam_h.pin_memory()
+        Jh3 = np.full(Kc, -1, np.int32)
+        Th3 = np.empty(Kc * (120 - Kc), np.float64)
+        lhh = np.empty(Kc, np.float64)
+        idl.id_cp_tensor(ctx, fh, lam_h, Kc, pc, Jh3, Th3, lhh)
+        # colliding entries of a mode's CountSketch are summed by shared-memory atomics
+        # (order not fixed): J equal, T and lambda_hat to FP32 rounding
+        assert np.array_equal(Jh3, host(Jd3))
+        assert np.allclose(Th3, host(Td3), rtol=1e-4, atol=1e-6)
+        assert np.allclose(lhh, host(lhd), rtol=1e-4, atol=1e-9)
 
 
 def test_argument_errors(ctx):

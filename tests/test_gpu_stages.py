@@ -324,7 +324,8 @@ def test_cpqr_exact_rank_and_ties(ctx):
 # ------------------------------------------------------------------ a5 TensorSketch + a9 lambda_hat
 @pytest.mark.parametrize("dims,R,L", [((1000, 1000, 1000), 100, 8192), ((6, 5, 4), 5, 16), ((200,) * 4, 51, 1024),
                                       ((37, 41), 10, 64), ((30, 20, 10), 7, 2048), ((9, 9), 4, 32),
-                                      ((50, 40), 9, 256)])
+                                      ((50, 40), 9, 256), ((200,) * 4, 331, 8192), ((1500, 7, 2100), 9, 8192),
+                                      ((300,), 1, 8192), ((8192, 3), 4, 8192)])
 def test_tensorsketch_parity(ctx, dims, R, L):
     facs, lam = cp_factors(dims, R, seed=len(dims) + R)
     hs, ss = odr.tensorsketch_maps(4, dims, L)
@@ -343,7 +344,8 @@ def test_tensorsketch_parity(ctx, dims, R, L):
 
 
 @pytest.mark.parametrize("dims,R,L,extra", [((1000, 1000, 1000), 101, 8192, 0), ((6, 5, 4), 5, 16, 3),
-                                            ((200,) * 4, 51, 1024, 32), ((37, 41), 10, 64, 1)])
+                                            ((200,) * 4, 51, 1024, 32), ((37, 41), 10, 64, 1),
+                                            ((200,) * 4, 307, 8192, 4)])
 def test_tensorsketch_colmajor_parity(ctx, dims, R, L, extra):
     """Column-major output (column r at Y + r*ldy): the oracle's sketch column by
     column, and the row-major call's values (up to the order of the shared-memory
