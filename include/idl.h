@@ -129,12 +129,18 @@ int idl_draw_countsketch(idl_ctx* ctx, uint64_t seed, int64_t I, int64_t L, int 
                          int32_t* h, int8_t* s);
 int idl_draw_gaussian(idl_ctx* ctx, uint64_t seed, int64_t m2, int64_t m1, double* Omega);
 int idl_draw_mode(idl_ctx* ctx, uint64_t seed, int n, int64_t In, int64_t L, int32_t* h, int8_t* s);
+/* idl_draw_gaussian_fp32: the Box-Muller pairs of idl_draw_gaussian from the same
+ * uniforms, in FP32 arithmetic (ln U1 as log1pf(-(1 - U1)) for U1 > 1/2, the
+ * angle reduced in integers), stored as FP64: within about 4e-7 (rho + |z|) of
+ * idl_draw_gaussian.  The pipelines with FP32 data and the batches draw Omega
+ * this way (GB300's FP64 pipes are narrow); FP64 data keeps idl_draw_gaussian. */
+int idl_draw_gaussian_fp32(idl_ctx* ctx, uint64_t seed, int64_t m2, int64_t m1, double* Omega);
 
 /* ---------------------------------------------------------------------------
  * Bucket offsets of Phi (Sec. 1.3): rows grouped by bucket, ascending within a
  * bucket.  bucket_ptr (L+1 int32) and row_list (I int32) are device outputs.
- * Buckets holding more than 12288 rows are left in arrival order (status IDL_OK;
- * the sketch is still exact, only its summation order is then not fixed).
+ * Every bucket lists its rows in increasing order, however many it holds (the
+ * output is the stable counting sort of h, bit for bit).
  * ------------------------------------------------------------------------- */
 int idl_bucket_offsets(idl_ctx* ctx, const int32_t* h, int64_t I, int64_t L,
                        int32_t* bucket_ptr, int32_t* row_list);
@@ -161,7 +167,8 @@ int idl_bucket_offsets(idl_ctx* ctx, const int32_t* h, int64_t I, int64_t L,
  *   All calls on a device share the one scratch array and each call clears
  *   the parts that must start at zero, so calls that overlap on the GPU (on
  *   different streams or from different threads) race: serialise them.
- *   Entries of h outside [0, L) are skipped; then bucket_ptr[L] < I.
+ *   Entries of h outside [0, L) are skipped; then bucket_ptr[L] < I: the caller
+ *   detects them by checking bucket_ptr[L] == I (no status word is kept).
  * ------------------------------------------------------------------------- */
 #define IDL_NOALLOC_MAX_BUCKETS 65536
 int idl_bucket_offsets_noalloc(void* stream, const int32_t* h, int64_t I, int64_t L,
@@ -288,21 +295,67 @@ int id_cp_tensor(idl_ctx* ctx, int N, const int64_t* dims, int64_t R, const void
                  int32_t* J, double* T, double* lambda_hat, idl_info* info);
 
 /* ---------------------------------------------------------------------------
+ * Gaussian ID, the comparison method of the paper (Sec. 1.2.1 and Sec. 1.2.2).
+ * The sketch size is L = params.m2 (K <= L <= 256; L <= 112 for FP64 data);
+ * params.m1 and params.modified are not used.  Outputs as for the pipelines
+ * above; device or host arrays.
+ * id_matrix_gaussian: Y = Omega A with Omega an L x I matrix of iid N(0,1)
+ *   entries (the counter-based Box-Muller draw of idl_draw_gaussian with tag 5,
+ *   row-major L x I), formed on the tensor cores in the precision mode of
+ *   params.precision (FP64 data: CUDA cores), then the pivoted QR and T of
+ *   Algorithm 1.  Dense A only (row-major, lda >= R).
+ * id_cp_tensor_gaussian: the Khatri-Rao structured Gaussian sketch of Eq.
+ *   G-matrix, y_lr = lambda_r prod_n <omega^(n)_:l, a^(n)_:r>, with Omega^(n)T
+ *   the L x I_n draw of tag 48 + n; one tensor-core product per mode and an
+ *   entrywise product; then Algorithm 1 and lambda_hat as in Algorithm 3.  FP32
+ *   factors stored column by column (ldf[n] >= dims[n]).
+ * ------------------------------------------------------------------------- */
+int id_matrix_gaussian(idl_ctx* ctx, const void* A, int64_t I, int64_t R, int64_t lda, int dtype, int64_t K,
+                       const idl_params* p, int32_t* J, double* T, idl_info* info);
+int id_cp_tensor_gaussian(idl_ctx* ctx, int N, const int64_t* dims, int64_t R, const void* const* factors,
+                          const int64_t* ldf, const double* lambda, int64_t K, const idl_params* p,
+                          int32_t* J, double* T, double* lambda_hat, idl_info* info);
+
+/* ---------------------------------------------------------------------------
+ * ID error estimate of Sec. 6 (the randomized spectral-norm estimate of Woolfe
+ * et al., Sec. 3.4): err = est ||A - A_J P||_2 / est ||A||_2, each estimate
+ * `iters` steps of the power method on E^T E (E = A - A_J P) and on A^T A from
+ * the counter-based Gaussian start vector of tag 6 (1 x R; seed for E, seed + 1
+ * for A), FP64 vectors and accumulation.  The power method never overestimates a
+ * spectral norm.  A dense (row-major, lda >= R) or CSR as for id_matrix_csr;
+ * J (K int32) and T (K x (R-K) FP64, the pipelines' layout) from any pipeline.
+ * Device or host arrays; err is a host double; the call synchronises.
+ * 1 <= iters <= 1000.
+ * ------------------------------------------------------------------------- */
+int idl_id_error(idl_ctx* ctx, const void* A, int64_t I, int64_t R, int64_t lda, int dtype, const int32_t* J,
+                 const double* T, int64_t K, int32_t iters, uint64_t seed, double* err);
+int idl_id_error_csr(idl_ctx* ctx, const int64_t* rowptr, const int32_t* colidx, const void* vals, int64_t I,
+                     int64_t R, int64_t nnz, int dtype, const int32_t* J, const double* T, int64_t K, int32_t iters,
+                     uint64_t seed, double* err);
+
+/* ---------------------------------------------------------------------------
  * Batches.  Many IDs of uneven sizes in one pass: every stage of the path is
  * one launch over all items, and the pivoted QR runs one thread-block cluster
  * per item in one launch.  The launch sequence of a batch shape is captured
  * once into a CUDA graph and replayed on later calls with the same shape.  On
- * the first call of a shape the dense sketch's block width and the Gaussian
- * stage's split-K factor are chosen by timing the candidates (the call then
- * runs the batch several times); idl_tune_save / idl_tune_load keep those
- * choices in a text file.
+ * the first call of a shape the dense sketch's block width, the Gaussian
+ * stage's split-K factor and the QR stage's cluster sizes (16, 8 or 4 CTAs per
+ * item, dense and CP items separately) are chosen by timing the candidates
+ * (the call then runs the batch several times); idl_tune_save / idl_tune_load
+ * keep those choices in a text file.
  *   Items: IDL_ITEM_DENSE (Algorithm 2 on a dense FP32 matrix) or IDL_ITEM_CP
  *   (Algorithm 3 on a CP tensor), FP32 data, one precision mode per batch
  *   (IDL_PREC_FP32 / BF16X3 / BF16), Gaussian stage required with
- *   K <= m2 <= min(m1, 128), K <= 128.  All pointers are device pointers;
- *   CP factors are stored column by column (ldf = dims[n]).  Outputs as for the
- *   single-item calls.  The call is asynchronous after its first use of a
- *   shape; idl_sync returns the device status word.
+ *   K <= m2 <= min(m1, 128), K <= 128.  CP factors are stored column by
+ *   column (ldf = dims[n]).  Outputs as for the single-item calls.
+ *   Either every array of the batch is device memory -- the call is then
+ *   asynchronous after its first use of a shape, and idl_sync returns the
+ *   device status word -- or every array is host memory (decided by the first
+ *   item's A or first factor; pinned memory copies fastest): the call then
+ *   copies the inputs into a device staging buffer on a copy stream of its own,
+ *   the CP items' factors first and the dense matrices in groups, while the
+ *   kernels run and wait only for the inputs they read; it copies J, T and
+ *   lambda_hat back and synchronises before it returns.
  * ------------------------------------------------------------------------- */
 /* ---------------------------------------------------------------------------
  * Learned column proposal for the QR stage (not in the paper; an acceleration

@@ -41,6 +41,9 @@ TAG_PERM = 3         # round keys of the permutation pi
 TAG_GAUSS = 4        # Omega
 TAG_MODE_BUCKET = 16  # + n : h_n of TensorSketch
 TAG_MODE_SIGN = 32    # + n : s_n of TensorSketch
+TAG_GAUSS_ID = 5      # the L x I Gaussian sketch of Gaussian matrix ID (Sec. 1.2.1)
+TAG_GAUSS_MODE = 48   # + n : the per-mode Gaussian matrices of Eq. G-matrix
+TAG_ERR_START = 6     # start vectors of the power-method error estimate (Sec. 6)
 FEISTEL_ROUNDS = 4
 
 _U64 = np.uint64
@@ -182,18 +185,19 @@ def tensorsketch_maps(seed: int, dims, L: int):
     return hs, ss
 
 
-def gaussian_matrix(seed: int, m2: int, m1: int) -> np.ndarray:
+def gaussian_matrix(seed: int, m2: int, m1: int, tag: int = TAG_GAUSS) -> np.ndarray:
     """Omega in R^{m2 x m1}, iid N(0,1) by the Box-Muller transform (Box &
     Muller 1958), row-major flat index q = j*m1 + b, pair p = q // 2:
-      U1 = ((u(seed, GAUSS, 2p) >> 11) + 1) * 2**-53   in (0, 1]
-      U2 =  (u(seed, GAUSS, 2p+1) >> 11)     * 2**-53   in [0, 1)
+      U1 = ((u(seed, tag, 2p) >> 11) + 1) * 2**-53   in (0, 1]
+      U2 =  (u(seed, tag, 2p+1) >> 11)     * 2**-53   in [0, 1)
       rho = sqrt(-2 ln U1);  z_q = rho cos(2 pi U2) for even q, rho sin(2 pi U2) for odd q.
-    Returned in float64."""
+    tag = GAUSS for the Gaussian stage; GAUSS_ID and GAUSS_MODE + n for the
+    Gaussian ID comparators.  Returned in float64."""
     n = m2 * m1
     q = np.arange(n)
     p = q // 2
-    a = stream(seed, TAG_GAUSS, 2 * p)
-    c = stream(seed, TAG_GAUSS, 2 * p + 1)
+    a = stream(seed, tag, 2 * p)
+    c = stream(seed, tag, 2 * p + 1)
     U1 = ((a >> _U64(11)).astype(np.float64) + 1.0) * 2.0 ** -53
     U2 = (c >> _U64(11)).astype(np.float64) * 2.0 ** -53
     rho = np.sqrt(-2.0 * np.log(U1))

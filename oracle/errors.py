@@ -6,7 +6,9 @@ Matrix: relative spectral-norm error ||A - A_J P||_2 / ||A||_2.  Exact (LAPACK
 SVD) for small A; otherwise 50 steps of the power method on E^T E from a seeded
 Gaussian start, which never overestimates ||E||_2 -- the same one-sided
 behaviour as the randomized estimate the paper uses (Sec. 6, after Woolfe et
-al. Sec. 3.4).
+al. Sec. 3.4).  The start vector is the counter-based Gaussian draw with tag
+ERR_START (1 x n, seed ``seed`` for E and ``seed + 1`` for A), so that the
+device estimator can start from the same vector.
 
 CP tensor: relative Frobenius error ||X_hat - X||_F / ||X||_F, exact, from the
 Gram identity M^T M = Hadamard product of A^(n)T A^(n) (Eq. MTM-formula):
@@ -18,12 +20,12 @@ from __future__ import annotations
 
 import numpy as np
 
+from . import draws
 from .cpqr import build_P
 
 
 def _power(matvec, rmatvec, n: int, iters: int, seed: int) -> float:
-    rng = np.random.Generator(np.random.PCG64(seed))
-    x = rng.standard_normal(n)
+    x = draws.gaussian_matrix(seed, 1, n, tag=draws.TAG_ERR_START)[0]
     x /= np.linalg.norm(x)
     est = 0.0
     for _ in range(iters):

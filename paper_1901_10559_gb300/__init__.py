@@ -93,6 +93,7 @@ _SIGS = {
     "idl_debug_cpqr_path": ([_vp, _int], _int),
     "idl_draw_countsketch": ([_vp, _u64, _i64, _i64, _int, _vp, _vp], _int),
     "idl_draw_gaussian": ([_vp, _u64, _i64, _i64, _vp], _int),
+    "idl_draw_gaussian_fp32": ([_vp, _u64, _i64, _i64, _vp], _int),
     "idl_draw_mode": ([_vp, _u64, _int, _i64, _i64, _vp, _vp], _int),
     "idl_bucket_offsets": ([_vp, _vp, _i64, _i64, _vp, _vp], _int),
     "idl_bucket_offsets_noalloc": ([_vp, _vp, _i64, _i64, _vp, _vp], _int),
@@ -111,6 +112,14 @@ _SIGS = {
                        ctypes.POINTER(Info)], _int),
     "id_cp_tensor": ([_vp, _int, _vp, _i64, _vp, _vp, _vp, _i64, ctypes.POINTER(Params), _vp, _vp, _vp,
                       ctypes.POINTER(Info)], _int),
+    "id_matrix_gaussian": ([_vp, _vp, _i64, _i64, _i64, _int, _i64, ctypes.POINTER(Params), _vp, _vp,
+                            ctypes.POINTER(Info)], _int),
+    "id_cp_tensor_gaussian": ([_vp, _int, _vp, _i64, _vp, _vp, _vp, _i64, ctypes.POINTER(Params), _vp, _vp, _vp,
+                               ctypes.POINTER(Info)], _int),
+    "idl_id_error": ([_vp, _vp, _i64, _i64, _i64, _int, _vp, _vp, _i64, ctypes.c_int32, ctypes.c_uint64,
+                      ctypes.POINTER(ctypes.c_double)], _int),
+    "idl_id_error_csr": ([_vp, _vp, _vp, _vp, _i64, _i64, _i64, _int, _vp, _vp, _i64, ctypes.c_int32,
+                          ctypes.c_uint64, ctypes.POINTER(ctypes.c_double)], _int),
     "idl_batch_run": ([_vp, ctypes.POINTER(BatchItem), _int], _int),
     "idl_tune_save": ([_vp, ctypes.c_char_p], _int),
     "idl_tune_load": ([_vp, ctypes.c_char_p], _int),
@@ -237,6 +246,10 @@ def idl_draw_gaussian(ctx, seed, m2, m1, Omega):
     return ctx.check(lib().idl_draw_gaussian(ctx.ptr, seed, m2, m1, _p(Omega)))
 
 
+def idl_draw_gaussian_fp32(ctx, seed, m2, m1, Omega):
+    return ctx.check(lib().idl_draw_gaussian_fp32(ctx.ptr, seed, m2, m1, _p(Omega)))
+
+
 def idl_draw_mode(ctx, seed, n, In, L, h, s):
     return ctx.check(lib().idl_draw_mode(ctx.ptr, seed, n, In, L, _p(h), _p(s)))
 
@@ -328,7 +341,8 @@ def id_matrix_csr(ctx, rowptr, colidx, vals, shape, K, params, J, T, info=None):
 
 
 def id_cp_tensor(ctx, factors, lam, K, params, J, T, lam_hat, info=None, ldf=None):
-    """factors: list of CUDA float32 tensors of shape (R, I_n) (A^(n) stored column by column)."""
+    """factors: list of float32 tensors of shape (R, I_n) (A^(n) stored column by column), on the
+    device or in host memory."""
     N = len(factors)
     R = int(factors[0].shape[0])
     dims = _arr(ctypes.c_int64, [int(f.shape[1]) for f in factors])
@@ -338,6 +352,47 @@ def id_cp_tensor(ctx, factors, lam, K, params, J, T, lam_hat, info=None, ldf=Non
     return ctx.check(lib().id_cp_tensor(ctx.ptr, N, ctypes.cast(dims, _vp), R, ctypes.cast(fp, _vp),
                                         ctypes.cast(lp, _vp), _p(lam), K, ctypes.byref(params), _p(J), _p(T),
                                         _p(lam_hat), ctypes.byref(info) if info is not None else None))
+
+
+def id_matrix_gaussian(ctx, A, K, params, J, T, info=None, lda=None):
+    """Gaussian matrix ID (the comparison method): params.m2 = L."""
+    I, R = int(A.shape[0]), int(A.shape[1])
+    dt = IDL_F64 if str(A.dtype).endswith("float64") else IDL_F32
+    lda = R if lda is None else lda
+    return ctx.check(lib().id_matrix_gaussian(ctx.ptr, _p(A), I, R, lda, dt, K, ctypes.byref(params), _p(J), _p(T),
+                                              ctypes.byref(info) if info is not None else None))
+
+
+def id_cp_tensor_gaussian(ctx, factors, lam, K, params, J, T, lam_hat, info=None, ldf=None):
+    """Gaussian (Khatri-Rao) tensor ID: factors as for id_cp_tensor, params.m2 = L."""
+    N = len(factors)
+    R = int(factors[0].shape[0])
+    dims = _arr(ctypes.c_int64, [int(f.shape[1]) for f in factors])
+    ldf = [int(f.stride(0)) for f in factors] if ldf is None else ldf
+    fp = _arr(_vp, [f.data_ptr() for f in factors])
+    lp = _arr(ctypes.c_int64, ldf)
+    return ctx.check(lib().id_cp_tensor_gaussian(ctx.ptr, N, ctypes.cast(dims, _vp), R, ctypes.cast(fp, _vp),
+                                                 ctypes.cast(lp, _vp), _p(lam), K, ctypes.byref(params), _p(J),
+                                                 _p(T), _p(lam_hat), ctypes.byref(info) if info is not None else None))
+
+
+def idl_id_error(ctx, A, J, T, K, iters=50, seed=1234, lda=None):
+    """||A - A_J P||_2 / ||A||_2 estimated on the device (power method, Sec. 6)."""
+    I, R = int(A.shape[0]), int(A.shape[1])
+    dt = IDL_F64 if str(A.dtype).endswith("float64") else IDL_F32
+    err = ctypes.c_double()
+    ctx.check(lib().idl_id_error(ctx.ptr, _p(A), I, R, R if lda is None else lda, dt, _p(J), _p(T), K, iters, seed,
+                                 ctypes.byref(err)))
+    return err.value
+
+
+def idl_id_error_csr(ctx, rowptr, colidx, vals, shape, J, T, K, iters=50, seed=1234):
+    I, R = int(shape[0]), int(shape[1])
+    dt = IDL_F64 if str(vals.dtype).endswith("float64") else IDL_F32
+    err = ctypes.c_double()
+    ctx.check(lib().idl_id_error_csr(ctx.ptr, _p(rowptr), _p(colidx), _p(vals), I, R, int(vals.shape[0]), dt, _p(J),
+                                     _p(T), K, iters, seed, ctypes.byref(err)))
+    return err.value
 
 
 # ---------------------------------------------------------------- batches

@@ -19,7 +19,7 @@ CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libidl.so")
 SOURCES = ["api.cu", "draws.cu", "countsketch.cu", "gaussian.cu", "gaussian_tc.cu", "cpqr.cu",
-           "tensorsketch.cu", "batch.cu", "proposal.cu", "noalloc.cu"]
+           "tensorsketch.cu", "batch.cu", "proposal.cu", "noalloc.cu", "errest.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-Xcompiler", "-Wno-unused-parameter"]

@@ -376,6 +376,12 @@ extern "C" int idl_draw_gaussian(idl_ctx* ctx, uint64_t seed, int64_t m2, int64_
   return cuda_check(ctx, launch_draw_gaussian(ctx->stream, seed, m2, m1, Omega), "draw_gaussian");
 }
 
+extern "C" int idl_draw_gaussian_fp32(idl_ctx* ctx, uint64_t seed, int64_t m2, int64_t m1, double* Omega) {
+  TRY(check_ctx(ctx));
+  if (m2 < 0 || m1 < 0 || (m2 * m1 > 0 && !Omega)) return fail(ctx, IDL_EINVAL, "draw_gaussian_fp32: bad arguments");
+  return cuda_check(ctx, launch_draw_gaussian_f32(ctx->stream, seed, m2, m1, Omega), "draw_gaussian_fp32");
+}
+
 extern "C" int idl_draw_mode(idl_ctx* ctx, uint64_t seed, int n, int64_t In, int64_t L, int32_t* h, int8_t* s) {
   TRY(check_ctx(ctx));
   if (n < 0 || In < 0 || L < 1 || L > 0x7fffffffLL || (In > 0 && (!h || !s)))
@@ -529,11 +535,16 @@ static int fork_omega(idl_ctx* ctx, const idl_params* p, double** Om) {
   }
   TRY(cuda_check(ctx, cudaEventRecord(ctx->ev_fork, ctx->stream), "fork"));
   TRY(cuda_check(ctx, cudaStreamWaitEvent(ctx->side, ctx->ev_fork, 0), "fork wait"));
-  TRY(cuda_check(ctx, launch_draw_gaussian(ctx->side, p->seed, p->m2, p->m1, o), "draw gaussian"));
+  TRY(cuda_check(ctx, p->precision == IDL_PREC_FP64 ? launch_draw_gaussian(ctx->side, p->seed, p->m2, p->m1, o)
+                                                     : launch_draw_gaussian_f32(ctx->side, p->seed, p->m2, p->m1, o),
+                 "draw gaussian"));
   TRY(cuda_check(ctx, cudaEventRecord(ctx->ev_join, ctx->side), "join"));
   *Om = o;
   return IDL_OK;
 }
+
+static int finish_from_y2(idl_ctx* ctx, const idl_params* p, int dtype, void* Y2, int64_t m, int64_t R, int64_t K,
+                          int32_t* J, double* T, idl_info* info);
 
 // Sketch Y1 (m1 x R, row-major, ld = ldy1; column-major when y1_cm, which needs the
 // tensor-core Gaussian stage) -> J, T, via the Gaussian stage and the QR stage.
@@ -553,7 +564,10 @@ static int finish_pipeline(idl_ctx* ctx, const idl_params* p, int dtype, void* Y
     } else {
       double* o = (double*)ws_get(ctx, kWsOmega, sizeof(double) * (size_t)(p->m2 * p->m1));
       if (!o) return IDL_ENOMEM;
-      STAGE(kStDraw, cuda_check(ctx, launch_draw_gaussian(ctx->stream, p->seed, p->m2, p->m1, o), "draw gaussian"));
+      STAGE(kStDraw, cuda_check(ctx, p->precision == IDL_PREC_FP64
+                                         ? launch_draw_gaussian(ctx->stream, p->seed, p->m2, p->m1, o)
+                                         : launch_draw_gaussian_f32(ctx->stream, p->seed, p->m2, p->m1, o),
+                                "draw gaussian"));
       Om = o;
     }
     if (y1_cm)
@@ -564,6 +578,17 @@ static int finish_pipeline(idl_ctx* ctx, const idl_params* p, int dtype, void* Y
   } else {
     STAGE(kStGauss, launch_transpose_to_colmajor(ctx, Y1, m, R, ldy1, dtype, Y2, ld2));
   }
+  return finish_from_y2(ctx, p, dtype, Y2, m, R, K, J, T, info);
+}
+
+// The QR stage onwards from a sketch Y2 (m x R column-major, ld m, in the kWsY2 slot with
+// room for a second copy when p->residual == 2): pivoted QR (or the column proposal),
+// T solve, residual, outputs (staged back to host pointers), diagnostics.
+static int finish_from_y2(idl_ctx* ctx, const idl_params* p, int dtype, void* Y2, int64_t m, int64_t R, int64_t K,
+                          int32_t* J, double* T, idl_info* info) {
+  const int es = dtype_size(dtype);
+  const int64_t ld2 = m;
+  const bool keep_orig = p->residual == 2;
   void* Yf = Y2;
   if (p->learned) {
     // the proposal reads the sketch and writes the factored copy; the fallback re-reads the sketch
@@ -655,6 +680,42 @@ static int id_matrix_csr_impl(idl_ctx* ctx, const int64_t* rowptr, const int32_t
   return finish_pipeline(ctx, p, dtype, Y1, ldy1, R, K, J, T, info, false, Om);
 }
 
+// Host factor matrices are copied into one workspace buffer (each at a 256-byte
+// offset, host_bytes in all); device ones are used in place.  fdev: N pointers.
+static int stage_factors(idl_ctx* ctx, int N, const int64_t* dims, int64_t R, const void* const* factors,
+                         const int64_t* ldf, size_t host_bytes, const void** fdev) {
+  unsigned char* stg = host_bytes ? (unsigned char*)ws_get(ctx, kWsFactors, host_bytes) : nullptr;
+  if (host_bytes && !stg) return IDL_ENOMEM;
+  size_t off = 0;
+  for (int n = 0; n < N; ++n) {
+    fdev[n] = factors[n];
+    if (is_device_ptr(factors[n])) continue;
+    const size_t b = sizeof(float) * (size_t)((R - 1) * ldf[n] + dims[n]);
+    const int pi = prof_begin(ctx, kStCopy);
+    TRY(cuda_check(ctx, cudaMemcpyAsync(stg + off, factors[n], b, cudaMemcpyHostToDevice, ctx->stream), "copy in"));
+    prof_end(ctx, pi);
+    fdev[n] = stg + off;
+    off += (b + 255) & ~(size_t)255;
+  }
+  return IDL_OK;
+}
+
+// Bytes of workspace the host factors need (0 when all are device pointers), and the
+// argument checks shared by the two CP entry points.
+static int cp_factor_args(idl_ctx* ctx, int N, const int64_t* dims, int64_t R, const void* const* factors,
+                          const int64_t* ldf, size_t* host_bytes, int64_t* tot) {
+  *host_bytes = 0;
+  *tot = 0;
+  for (int n = 0; n < N; ++n) {
+    if (dims[n] < 1 || ldf[n] < dims[n] || !factors[n])
+      return fail(ctx, IDL_EINVAL, "CP factors must be non-null with ldf >= dims");
+    if (!is_device_ptr(factors[n]))
+      *host_bytes += (sizeof(float) * (size_t)((R - 1) * ldf[n] + dims[n]) + 255) & ~(size_t)255;
+    *tot += dims[n];
+  }
+  return IDL_OK;
+}
+
 static int id_cp_tensor_impl(idl_ctx* ctx, int N, const int64_t* dims, int64_t R, const void* const* factors,
                             const int64_t* ldf, const double* lambda, int64_t K, const idl_params* p, int32_t* J,
                             double* T, double* lambda_hat, idl_info* info) {
@@ -675,23 +736,8 @@ static int id_cp_tensor_impl(idl_ctx* ctx, int N, const int64_t* dims, int64_t R
   double* Om;
   TRY(fork_omega(ctx, p, &Om));
   int rc;
-  // host factors: copied into one workspace buffer (each at a 256-byte offset)
   const void* fdev[8];
-  {
-    unsigned char* stg = host_bytes ? (unsigned char*)ws_get(ctx, kWsFactors, host_bytes) : nullptr;
-    if (host_bytes && !stg) return IDL_ENOMEM;
-    size_t off = 0;
-    for (int n = 0; n < N; ++n) {
-      fdev[n] = factors[n];
-      if (is_device_ptr(factors[n])) continue;
-      const size_t b = sizeof(float) * (size_t)((R - 1) * ldf[n] + dims[n]);
-      const int pi = prof_begin(ctx, kStCopy);
-      TRY(cuda_check(ctx, cudaMemcpyAsync(stg + off, factors[n], b, cudaMemcpyHostToDevice, ctx->stream), "copy in"));
-      prof_end(ctx, pi);
-      fdev[n] = stg + off;
-      off += (b + 255) & ~(size_t)255;
-    }
-  }
+  TRY(stage_factors(ctx, N, dims, R, factors, ldf, host_bytes, fdev));
   factors = fdev;
   const double* lam = (const double*)stage_in(ctx, lambda, sizeof(double) * (size_t)R, kWsLam, &rc);
   TRY(rc);
@@ -734,6 +780,147 @@ static int id_cp_tensor_impl(idl_ctx* ctx, int N, const int64_t* dims, int64_t R
   if (info) return finish_info(ctx, p, p->precision, info, K, R);
   if (!jdev || !tdev || !ldev) TRY(cuda_check(ctx, cudaStreamSynchronize(ctx->stream), "sync"));
   return IDL_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Gaussian ID, the comparison method (Sec. 1.2.1; Sec. 1.2.2 Eq. G-matrix):
+// the sketch is a Gaussian matrix applied to A itself (matrix) or the
+// Khatri-Rao structured Gaussian sketch of M (CP tensor); the QR stage and the
+// T solve are the CountSketch pipelines'.
+// ---------------------------------------------------------------------------
+static int check_gaussian_id(idl_ctx* ctx, const idl_params* p, int dtype, int64_t R, int64_t K) {
+  if (!p) return fail(ctx, IDL_EINVAL, "null params");
+  if (dtype != IDL_F32 && dtype != IDL_F64) return fail(ctx, IDL_EINVAL, "dtype must be IDL_F32 or IDL_F64");
+  if (p->precision < 0 || p->precision > 3) return fail(ctx, IDL_EINVAL, "unknown precision");
+  if ((dtype == IDL_F64) != (p->precision == IDL_PREC_FP64))
+    return fail(ctx, IDL_EINVAL, "FP64 data needs precision IDL_PREC_FP64 and FP32 data another mode");
+  if (K < 1 || K >= R) return fail(ctx, IDL_EINVAL, "need 1 <= K < R");
+  if (p->m2 < K) return fail(ctx, IDL_EINVAL, "need K <= L = params.m2");
+  if (p->m2 > (dtype == IDL_F64 ? 112 : 256)) return fail(ctx, IDL_ELIMIT, "Gaussian ID: L = params.m2 > 256 (112 in FP64)");
+  if (p->residual < 0 || p->residual > 2) return fail(ctx, IDL_EINVAL, "residual mode must be 0, 1 or 2");
+  if (p->learned < IDL_PROPOSAL_NONE || p->learned > IDL_PROPOSAL_NORM)
+    return fail(ctx, IDL_EINVAL, "unknown proposal mode");
+  if (p->learned && (dtype != IDL_F32 || p->m2 > 128 || K > 128))
+    return fail(ctx, IDL_ELIMIT, "the column proposal needs FP32 data, m <= 128 and K <= 128");
+  if (R > 0x7fffffffLL) return fail(ctx, IDL_ELIMIT, "R must fit in int32");
+  return IDL_OK;
+}
+
+extern "C" int id_matrix_gaussian(idl_ctx* ctx, const void* A, int64_t I, int64_t R, int64_t lda, int dtype,
+                                  int64_t K, const idl_params* p, int32_t* J, double* T, idl_info* info) {
+  TRY(check_ctx(ctx));
+  TRY(check_gaussian_id(ctx, p, dtype, R, K));
+  if (I < 1 || I > 0x7fffffffLL || lda < R || !A || !J || !T) return fail(ctx, IDL_EINVAL, "id_matrix_gaussian: bad arguments");
+  const int es = dtype_size(dtype);
+  const int64_t L = p->m2;
+  int rc;
+  const void* Ad = stage_in(ctx, A, (size_t)es * (size_t)((I - 1) * lda + R), kWsA, &rc);
+  TRY(rc);
+  double* Om = (double*)ws_get(ctx, kWsOmega, sizeof(double) * (size_t)(L * I));
+  if (!Om) return IDL_ENOMEM;
+  void* Y2 = ws_get(ctx, kWsY2, (size_t)es * (size_t)(R * L) * (p->residual == 2 ? 2 : 1));
+  if (!Y2) return IDL_ENOMEM;
+  STAGE(kStDraw, cuda_check(ctx, launch_draw_gaussian_tag(ctx->stream, p->seed, kTagGaussId, L, I, Om), "draw"));
+  STAGE(kStSketch, launch_gaussian(ctx, Om, L, I, Ad, R, lda, dtype, p->precision, Y2, L));
+  return finish_from_y2(ctx, p, dtype, Y2, L, R, K, J, T, info);
+}
+
+extern "C" int id_cp_tensor_gaussian(idl_ctx* ctx, int N, const int64_t* dims, int64_t R, const void* const* factors,
+                                     const int64_t* ldf, const double* lambda, int64_t K, const idl_params* p,
+                                     int32_t* J, double* T, double* lambda_hat, idl_info* info) {
+  TRY(check_ctx(ctx));
+  TRY(check_gaussian_id(ctx, p, IDL_F32, R, K));
+  if (N < 1 || N > 8 || !dims || !factors || !ldf || !lambda || !J || !T || !lambda_hat)
+    return fail(ctx, IDL_EINVAL, "id_cp_tensor_gaussian: bad arguments");
+  size_t host_bytes;
+  int64_t tot;
+  TRY(cp_factor_args(ctx, N, dims, R, factors, ldf, &host_bytes, &tot));
+  const int64_t L = p->m2;
+  int rc;
+  const void* fdev[8];
+  TRY(stage_factors(ctx, N, dims, R, factors, ldf, host_bytes, fdev));
+  const double* lam = (const double*)stage_in(ctx, lambda, sizeof(double) * (size_t)R, kWsLam, &rc);
+  TRY(rc);
+  double* Om = (double*)ws_get(ctx, kWsOmega, sizeof(double) * (size_t)(L * tot));
+  float* G = (float*)ws_get(ctx, kWsModeSketch, sizeof(float) * (size_t)(N * L * R));
+  float* Y2 = (float*)ws_get(ctx, kWsY2, sizeof(float) * (size_t)(R * L) * (p->residual == 2 ? 2 : 1));
+  if (!Om || !G || !Y2) return IDL_ENOMEM;
+  int64_t off = 0;
+  for (int n = 0; n < N; ++n) {     // Omega^(n)T (L x I_n, row-major), then G_n = Omega^(n)T A^(n)
+    STAGE(kStDraw, cuda_check(ctx, launch_draw_gaussian_tag(ctx->stream, p->seed, kTagGaussMode + n, L, dims[n],
+                                                            Om + off), "draw"));
+    STAGE(kStSketch, launch_gaussian_tc(ctx, Om + off, L, dims[n], (const float*)fdev[n], R, ldf[n], true,
+                                        p->precision, G + (size_t)n * L * R, L));
+    off += L * dims[n];
+  }
+  STAGE(kStSketch, launch_kr_product(ctx, G, N, L, R, lam, Y2));
+  const bool jdev = is_device_ptr(J), tdev = is_device_ptr(T), ldev = is_device_ptr(lambda_hat);
+  int32_t* Jd = J;
+  double* Td = T;
+  if (!jdev) { Jd = (int32_t*)ws_get(ctx, kWsJ, sizeof(int32_t) * (size_t)K); if (!Jd) return IDL_ENOMEM; }
+  if (!tdev) { Td = (double*)ws_get(ctx, kWsT, sizeof(double) * (size_t)(K * (R - K))); if (!Td) return IDL_ENOMEM; }
+  TRY(finish_from_y2(ctx, p, IDL_F32, Y2, L, R, K, Jd, Td, nullptr));
+  double* lhd = lambda_hat;
+  if (!ldev) { lhd = (double*)ws_get(ctx, kWsLamHat, sizeof(double) * (size_t)K); if (!lhd) return IDL_ENOMEM; }
+  STAGE(kStCheck, launch_lambda_hat(ctx, lam, Jd, Td, K, R, lhd));
+  if (!jdev) TRY(cuda_check(ctx, cudaMemcpyAsync(J, Jd, sizeof(int32_t) * K, cudaMemcpyDeviceToHost, ctx->stream), "J"));
+  if (!tdev)
+    TRY(cuda_check(ctx, cudaMemcpyAsync(T, Td, sizeof(double) * K * (R - K), cudaMemcpyDeviceToHost, ctx->stream), "T"));
+  if (!ldev)
+    TRY(cuda_check(ctx, cudaMemcpyAsync(lambda_hat, lhd, sizeof(double) * K, cudaMemcpyDeviceToHost, ctx->stream),
+                   "lambda_hat"));
+  if (info) return finish_info(ctx, p, p->precision, info, K, R);
+  if (!jdev || !tdev || !ldev) TRY(cuda_check(ctx, cudaStreamSynchronize(ctx->stream), "sync"));
+  return IDL_OK;
+}
+
+// ---------------------------------------------------------------------------
+// ID error estimate (Sec. 6): ||A - A_J P||_2 / ||A||_2 by the power method on the
+// device.  Host arrays are staged like the pipelines'; the call synchronises.
+// ---------------------------------------------------------------------------
+static int stage_jt(idl_ctx* ctx, const int32_t* J, const double* T, int64_t K, int64_t R, const int32_t** Jd,
+                    const double** Td) {
+  int rc;
+  *Jd = (const int32_t*)stage_in(ctx, J, sizeof(int32_t) * (size_t)K, kWsJ, &rc);
+  TRY(rc);
+  *Td = (const double*)stage_in(ctx, T, sizeof(double) * (size_t)(K * (R - K)), kWsT, &rc);
+  return rc;
+}
+
+extern "C" int idl_id_error(idl_ctx* ctx, const void* A, int64_t I, int64_t R, int64_t lda, int dtype,
+                            const int32_t* J, const double* T, int64_t K, int32_t iters, uint64_t seed, double* err) {
+  TRY(check_ctx(ctx));
+  if ((dtype != IDL_F32 && dtype != IDL_F64) || I < 1 || R < 2 || lda < R || K < 1 || K >= R || !A || !J || !T ||
+      !err || iters < 1 || iters > 1000 || R > 0x7fffffffLL)
+    return fail(ctx, IDL_EINVAL, "id_error: bad arguments");
+  int rc;
+  const void* Ad = stage_in(ctx, A, (size_t)dtype_size(dtype) * (size_t)((I - 1) * lda + R), kWsA, &rc);
+  TRY(rc);
+  const int32_t* Jd;
+  const double* Td;
+  TRY(stage_jt(ctx, J, T, K, R, &Jd, &Td));
+  return launch_id_error_dense(ctx, Ad, I, R, lda, dtype, Jd, Td, K, iters, seed, err);
+}
+
+extern "C" int idl_id_error_csr(idl_ctx* ctx, const int64_t* rowptr, const int32_t* colidx, const void* vals,
+                                int64_t I, int64_t R, int64_t nnz, int dtype, const int32_t* J, const double* T,
+                                int64_t K, int32_t iters, uint64_t seed, double* err) {
+  TRY(check_ctx(ctx));
+  if ((dtype != IDL_F32 && dtype != IDL_F64) || I < 1 || R < 2 || nnz < 0 || K < 1 || K >= R || !rowptr || !J ||
+      !T || !err || (nnz > 0 && (!colidx || !vals)) || iters < 1 || iters > 1000 || R > 0x7fffffffLL)
+    return fail(ctx, IDL_EINVAL, "id_error_csr: bad arguments");
+  int rc;
+  const int64_t* rp = (const int64_t*)stage_in(ctx, rowptr, sizeof(int64_t) * (size_t)(I + 1), kWsRowptr, &rc);
+  TRY(rc);
+  const int32_t* ci = nnz ? (const int32_t*)stage_in(ctx, colidx, sizeof(int32_t) * (size_t)nnz, kWsColidx, &rc)
+                          : colidx;
+  TRY(rc);
+  const void* vv = nnz ? stage_in(ctx, vals, (size_t)dtype_size(dtype) * (size_t)nnz, kWsVals, &rc) : vals;
+  TRY(rc);
+  const int32_t* Jd;
+  const double* Td;
+  TRY(stage_jt(ctx, J, T, K, R, &Jd, &Td));
+  return launch_id_error_csr(ctx, rp, ci, vv, I, R, dtype, Jd, Td, K, iters, seed, err);
 }
 
 // ---------------------------------------------------------------------------

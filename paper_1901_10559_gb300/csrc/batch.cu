@@ -15,14 +15,17 @@
 // QR, certificate) before the cluster QR launch, in which their clusters only
 // run when the certificate failed (a per-item gate read at block start).
 //
-// Tuning: the dense sketch's block width and the Gaussian stage's split-K
-// factor are chosen per batch shape by timing the candidates on the first
-// call (CUDA events around the two stages); the choice is kept in the context
-// and can be saved to / loaded from a text file (idl_tune_save / idl_tune_load).
+// Tuning: the dense sketch's block width, the Gaussian stage's split-K factor
+// and the thread-block cluster sizes of the dense and the CP items' pivoted QR
+// are chosen per batch shape by timing the candidates on the first call (CUDA
+// events around the stage groups, one knob at a time); the choice is kept in
+// the context and can be saved to / loaded from a text file (idl_tune_save /
+// idl_tune_load).
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <initializer_list>
 #include <cstdio>
 #include <cstring>
 #include <map>
@@ -120,7 +123,7 @@ __global__ void b_gauss_draw_kernel(const BItem* __restrict__ items, const int64
   ITEM_OF_BLOCK(pre, n);
   const int64_t q = local * blockDim.x + threadIdx.x;
   const int64_t tot = it.m2 * it.m1;
-  if (2 * q < tot) gauss_pair(q, it.gauss_base, tot, it.Om);
+  if (2 * q < tot) gauss_pair_f32(q, it.gauss_base, tot, it.Om);     // batches hold FP32 data
 }
 
 constexpr int kBHistBlocks = 64;
@@ -362,7 +365,9 @@ using namespace idl;
 
 namespace {
 
-struct Tune { int sketch_threads = 256; int split_mult = 1; };
+// Tuned per batch shape: the dense sketch's block width, the Gaussian stage's split-K
+// factor, and the thread-block cluster size of the pivoted QR of dense and of CP items.
+struct Tune { int sketch_threads = 256; int split_mult = 1; int qr_cs_dense = 16; int qr_cs_cp = 16; };
 
 // a batch shape: the sizes that decide every launch
 std::string signature(const idl_batch_item* items, int n) {
@@ -459,8 +464,9 @@ static bool cpqr_cfg_fits(const std::vector<int>& list, const std::vector<BItem>
   return true;
 }
 
-static bool pick_cpqr(const std::vector<int>& list, const std::vector<BItem>& it, CpqrCfg* cfg, bool cand = false) {
-  const int CS = cand ? 1 : 16;
+static bool pick_cpqr(const std::vector<int>& list, const std::vector<BItem>& it, CpqrCfg* cfg, bool cand = false,
+                      int cluster = 16) {
+  const int CS = cand ? 1 : cluster;
 #define PICK(VV, TT) if (cpqr_cfg_fits<VV, TT>(list, it, CS, cfg, cand)) return true;
   PICK(8, 32) PICK(8, 16) PICK(8, 8) PICK(16, 8) PICK(8, 4) PICK(16, 4) PICK(32, 4) PICK(16, 2) PICK(32, 2)
   PICK(16, 1) PICK(32, 1) PICK(64, 4) PICK(64, 2) PICK(64, 1) PICK(96, 1) PICK(128, 1)
@@ -731,11 +737,14 @@ static int plan_batch(idl_ctx* ctx, const idl_batch_item* items, int n, const Tu
   }
   for (int i = 0; i < n; ++i) P.it[i].nc = 0;
   if (!P.dense_list.empty()) {
-    if (!pick_cpqr(P.dense_list, P.it, &P.cfg_dense)) return fail(ctx, IDL_ELIMIT, "batch: no QR cluster shape");
+    if (!pick_cpqr(P.dense_list, P.it, &P.cfg_dense, false, tn.qr_cs_dense) &&
+        !pick_cpqr(P.dense_list, P.it, &P.cfg_dense, false, 16))
+      return fail(ctx, IDL_ELIMIT, "batch: no QR cluster shape");
     for (int p : P.dense_list) P.it[p].nc = (int)cdiv(P.it[p].R, P.cfg_dense.CS);
   }
   if (!P.cp_list.empty()) {
-    if (!pick_cpqr(P.cp_list, P.it, &P.cfg_cp)) return fail(ctx, IDL_ELIMIT, "batch: no QR cluster shape");
+    if (!pick_cpqr(P.cp_list, P.it, &P.cfg_cp, false, tn.qr_cs_cp) && !pick_cpqr(P.cp_list, P.it, &P.cfg_cp, false, 16))
+      return fail(ctx, IDL_ELIMIT, "batch: no QR cluster shape");
     for (int p : P.cp_list) P.it[p].nc = (int)cdiv(P.it[p].R, P.cfg_cp.CS);
   }
   return IDL_OK;
@@ -1102,11 +1111,9 @@ extern "C" int idl_batch_run(idl_ctx* ctx, const idl_batch_item* items, int n) {
       for (const auto& g : f0.dense) TRYC(cudaStreamWaitEvent(ctx->stream, g.second, 0), "batch stage wait");
       TRYC(cudaStreamWaitEvent(ctx->stream, f0.ev_cp, 0), "batch stage wait");
     }
-    // autotune: dense sketch block width, then the Gaussian split-K factor
-    float best = 1e30f;
-    for (int th : {128, 256, 512}) {
-      Tune t = tn;
-      t.sketch_threads = th;
+    // autotune, one knob at a time on whole-batch runs timed per stage group: the dense
+    // sketch's block width, the Gaussian split-K factor, the QR cluster sizes
+    auto trial = [&](const Tune& t, int stage, float* out) -> int {
       BatchPlan Q;
       BTRY(plan_batch(ctx, items, n, t, Q));
       unsigned char* ws2 = (unsigned char*)ws_get(ctx, kWsBatch, Q.ws_bytes);
@@ -1115,24 +1122,27 @@ extern "C" int idl_batch_run(idl_ctx* ctx, const idl_batch_item* items, int n) {
       BTRY(upload(ctx, Q, ws2, tab2, n));
       float ms[kBTimedStages] = {};
       BTRY(run_stages(ctx, Q, (const BItem*)(tab2 + Q.off_items), (const int64_t*)(tab2 + Q.off_pre),
-                      (const int32_t*)(tab2 + Q.off_lists), n, th, nlaunch, ms));
-      if (ms[kBTSketchDense] < best) { best = ms[kBTSketchDense]; tn.sketch_threads = th; }
-    }
-    best = 1e30f;
-    for (int sm : {1, 2}) {
-      Tune t = tn;
-      t.split_mult = sm;
-      BatchPlan Q;
-      BTRY(plan_batch(ctx, items, n, t, Q));
-      unsigned char* ws2 = (unsigned char*)ws_get(ctx, kWsBatch, Q.ws_bytes);
-      unsigned char* tab2 = (unsigned char*)ws_get(ctx, kWsBatchTab, Q.table_bytes);
-      if (!ws2 || !tab2) return IDL_ENOMEM;
-      BTRY(upload(ctx, Q, ws2, tab2, n));
-      float ms[kBTimedStages] = {};
-      BTRY(run_stages(ctx, Q, (const BItem*)(tab2 + Q.off_items), (const int64_t*)(tab2 + Q.off_pre),
-                      (const int32_t*)(tab2 + Q.off_lists), n, tn.sketch_threads, nlaunch, ms));
-      if (ms[kBTGauss] < best) { best = ms[kBTGauss]; tn.split_mult = sm; }
-    }
+                      (const int32_t*)(tab2 + Q.off_lists), n, t.sketch_threads, nlaunch, ms));
+      *out = ms[stage];
+      return IDL_OK;
+    };
+    auto tune_knob = [&](int Tune::*knob, std::initializer_list<int> values, int stage) -> int {
+      float best = 1e30f;
+      int pick = tn.*knob;
+      for (int v : values) {
+        Tune t = tn;
+        t.*knob = v;
+        float ms = 0.f;
+        BTRY(trial(t, stage, &ms));
+        if (ms < best) { best = ms; pick = v; }
+      }
+      tn.*knob = pick;
+      return IDL_OK;
+    };
+    BTRY(tune_knob(&Tune::sketch_threads, {128, 256, 512}, kBTSketchDense));
+    BTRY(tune_knob(&Tune::split_mult, {1, 2}, kBTGauss));
+    if (!P.dense_list.empty()) BTRY(tune_knob(&Tune::qr_cs_dense, {16, 8, 4}, kBTQR));
+    if (!P.cp_list.empty()) BTRY(tune_knob(&Tune::qr_cs_cp, {16, 8, 4}, kBTQR));
     bs->tune[key] = tn;
     P = BatchPlan();
     BTRY(plan_batch(ctx, items, n, tn, P));
@@ -1195,9 +1205,10 @@ extern "C" int idl_tune_save(idl_ctx* ctx, const char* path) {
   if (!ctx || !path) return IDL_EINVAL;
   FILE* f = fopen(path, "w");
   if (!f) return fail(ctx, IDL_EINVAL, "tune_save: cannot open file");
-  fprintf(f, "# idl batch tuning: shape-hash sketch_threads split_mult\n");
+  fprintf(f, "# idl batch tuning: shape-hash sketch_threads split_mult qr_cluster_dense qr_cluster_cp\n");
   for (auto& kv : bstate(ctx)->tune)
-    fprintf(f, "%016llx %d %d\n", (unsigned long long)kv.first, kv.second.sketch_threads, kv.second.split_mult);
+    fprintf(f, "%016llx %d %d %d %d\n", (unsigned long long)kv.first, kv.second.sketch_threads, kv.second.split_mult,
+            kv.second.qr_cs_dense, kv.second.qr_cs_cp);
   fclose(f);
   return IDL_OK;
 }
@@ -1211,11 +1222,15 @@ extern "C" int idl_tune_load(idl_ctx* ctx, const char* path) {
   while (fgets(line, sizeof(line), f)) {
     if (line[0] == '#') continue;
     unsigned long long k;
-    int a, b;
-    if (sscanf(line, "%llx %d %d", &k, &a, &b) == 3 && (a == 128 || a == 256 || a == 512) && (b == 1 || b == 2)) {
+    int a, b, c = 16, d = 16;
+    const int got = sscanf(line, "%llx %d %d %d %d", &k, &a, &b, &c, &d);
+    auto cs_ok = [](int x) { return x == 4 || x == 8 || x == 16; };
+    if (got >= 3 && (a == 128 || a == 256 || a == 512) && (b == 1 || b == 2) && cs_ok(c) && cs_ok(d)) {
       Tune t;
       t.sketch_threads = a;
       t.split_mult = b;
+      t.qr_cs_dense = c;
+      t.qr_cs_cp = d;
       bstate(ctx)->tune[(uint64_t)k] = t;
       ++loaded;
     }
@@ -1225,7 +1240,7 @@ extern "C" int idl_tune_load(idl_ctx* ctx, const char* path) {
 }
 
 // Runs the batch once without the graph, with CUDA events around the stage groups:
-// ms[0] draws and bucket offsets, [1] dense sketch, [2] CP TensorSketch, [3] Gaussian
+// ms[0] draws and bucket offsets, [1] CP TensorSketch, [2] dense sketch, [3] Gaussian
 // stage, [4] column proposal, [5] pivoted QR, [6] T solve and lambda_hat.  Used to
 // attribute time to the kernels.
 extern "C" int idl_debug_batch_timing(idl_ctx* ctx, const idl_batch_item* items, int n, float* ms) {

@@ -25,8 +25,8 @@ __device__ __forceinline__ void set_status(int* status, int code) {
 // ----------------------------------------------------------------------------
 constexpr uint64_t kGamma = 0x9E3779B97F4A7C15ull;
 constexpr uint64_t kTagMul = 0xD1B54A32D192ED03ull;
-enum : uint32_t { kTagBucket = 1, kTagSign = 2, kTagPerm = 3, kTagGauss = 4,
-                  kTagModeBucket = 16, kTagModeSign = 32 };
+enum : uint32_t { kTagBucket = 1, kTagSign = 2, kTagPerm = 3, kTagGauss = 4, kTagGaussId = 5, kTagErrStart = 6,
+                  kTagModeBucket = 16, kTagModeSign = 32, kTagGaussMode = 48 };
 constexpr int kFeistelRounds = 4;
 
 __host__ __device__ __forceinline__ uint64_t mix64(uint64_t z) {

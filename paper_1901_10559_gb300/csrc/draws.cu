@@ -43,11 +43,30 @@ __global__ void draw_gaussian_kernel(uint64_t base, int64_t n, double* __restric
   if (2 * p < n) gauss_pair(p, base, n, Om);
 }
 
-cudaError_t launch_draw_gaussian(cudaStream_t st, uint64_t seed, int64_t m2, int64_t m1, double* Omega) {
+cudaError_t launch_draw_gaussian_tag(cudaStream_t st, uint64_t seed, uint32_t tag, int64_t m2, int64_t m1,
+                                     double* Omega) {
   int64_t n = m2 * m1;
   if (n <= 0) return cudaSuccess;
   int threads = 256;
-  draw_gaussian_kernel<<<(unsigned)cdiv(cdiv(n, 2), threads), threads, 0, st>>>(stream_base(seed, kTagGauss), n, Omega), idl::count_launch();
+  draw_gaussian_kernel<<<(unsigned)cdiv(cdiv(n, 2), threads), threads, 0, st>>>(stream_base(seed, tag), n, Omega),
+      idl::count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_draw_gaussian(cudaStream_t st, uint64_t seed, int64_t m2, int64_t m1, double* Omega) {
+  return launch_draw_gaussian_tag(st, seed, kTagGauss, m2, m1, Omega);
+}
+
+__global__ void draw_gaussian_f32_kernel(uint64_t base, int64_t n, double* __restrict__ Om) {
+  const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (2 * p < n) gauss_pair_f32(p, base, n, Om);
+}
+
+cudaError_t launch_draw_gaussian_f32(cudaStream_t st, uint64_t seed, int64_t m2, int64_t m1, double* Omega) {
+  int64_t n = m2 * m1;
+  if (n <= 0) return cudaSuccess;
+  draw_gaussian_f32_kernel<<<(unsigned)cdiv(cdiv(n, 2), 256), 256, 0, st>>>(stream_base(seed, kTagGauss), n, Omega),
+      idl::count_launch();
   return cudaGetLastError();
 }
 

@@ -77,6 +77,32 @@ __device__ __forceinline__ void gauss_pair(int64_t p, uint64_t base, int64_t n, 
   if (2 * p + 1 < n) Om[2 * p + 1] = rho * sv;
 }
 
+// The same pair in FP32 arithmetic (the draw of the FP32 pipelines and batches:
+// GB300's FP64 pipes made the FP64 form several milliseconds per batch).  The
+// uniforms are the same 53-bit integers; ln U1 is log1pf(-(1 - U1)) when U1 > 1/2
+// (1 - U1 formed exactly in integers) and logf(U1) otherwise, and the angle
+// 2 pi U2 is reduced to pi t, t in [-1, 1), in integers before the conversion.
+// The result differs from the FP64 draw by a few units in the last place of
+// FP32 (about 4e-7 (rho + |z|)).
+__device__ __forceinline__ void gauss_pair_f32(int64_t p, uint64_t base, int64_t n, double* __restrict__ Om) {
+  const uint64_t ka = stream_at(base, 2 * (uint64_t)p) >> 11;       // U1 = (ka + 1) 2^-53
+  const uint64_t kc = stream_at(base, 2 * (uint64_t)p + 1) >> 11;   // U2 = kc 2^-53
+  float lg;
+  if (ka >= (1ull << 52)) {
+    const float v = __ull2float_rn((1ull << 53) - 1 - ka) * 0x1.0p-53f;   // 1 - U1
+    lg = log1pf(-v);
+  } else {
+    lg = logf(__ull2float_rn(ka + 1) * 0x1.0p-53f);
+  }
+  const float rho = sqrtf(-2.f * lg);
+  const int64_t kt = kc >= (1ull << 52) ? (int64_t)kc - (int64_t)(1ull << 53) : (int64_t)kc;   // 2 U2 (- 2)
+  const float t = __ll2float_rn(kt) * 0x1.0p-52f;
+  float sv, cv;
+  sincospif(t, &sv, &cv);
+  Om[2 * p] = (double)(rho * cv);
+  if (2 * p + 1 < n) Om[2 * p + 1] = (double)(rho * sv);
+}
+
 // TensorSketch map of one mode entry
 __device__ __forceinline__ void mode_elem(int64_t i, uint64_t hb, uint64_t sb, int64_t L, int32_t* __restrict__ h,
                                           int8_t* __restrict__ s) {

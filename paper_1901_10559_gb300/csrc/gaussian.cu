@@ -160,3 +160,29 @@ int launch_gaussian(idl_ctx* ctx, const double* Omega, int64_t m2, int64_t m1, c
 }
 
 }  // namespace idl
+
+// ---------------------------------------------------------------------------
+// Khatri-Rao Gaussian sketch of a CP tensor (Eq. G-matrix): the per-mode products
+// G_n = Omega^(n)T A^(n) (L x R, from the Gaussian stage) multiplied entrywise
+// and scaled by the s-values, y_lr = lambda_r prod_n G_n[l, r].
+// ---------------------------------------------------------------------------
+namespace idl {
+
+__global__ void kr_product_kernel(const float* __restrict__ G, int N, int64_t L, int64_t R,
+                                  const double* __restrict__ lambda, float* __restrict__ Y) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= L * R) return;
+  const int64_t r = e / L;
+  float v = (float)lambda[r];
+  for (int n = 0; n < N; ++n) v *= G[(int64_t)n * L * R + e];
+  Y[e] = v;
+}
+
+int launch_kr_product(idl_ctx* ctx, const float* G, int N, int64_t L, int64_t R, const double* lambda, float* Y) {
+  const int64_t n = L * R;
+  if (n <= 0) return IDL_OK;
+  kr_product_kernel<<<(unsigned)cdiv(n, 256), 256, 0, ctx->stream>>>(G, N, L, R, lambda, Y), count_launch();
+  return cuda_check(ctx, cudaGetLastError(), "khatri-rao product");
+}
+
+}  // namespace idl

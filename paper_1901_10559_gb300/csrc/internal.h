@@ -68,7 +68,7 @@ enum Slot {
   kWsH = 0, kWsS, kWsOmega, kWsBucketPtr, kWsRowList, kWsCursor, kWsBig, kWsY1, kWsPart,
   kWsY2, kWsOmegaConv, kWsRest, kWsA, kWsRowptr, kWsColidx, kWsVals, kWsJ, kWsT,
   kWsModeH, kWsModeS, kWsLam, kWsLamHat, kWsCpqrSync, kWsRinv, kWsBatch, kWsBatchTab, kWsYf, kWsProp,
-  kWsPropGram, kWsPropTrain, kWsPropCopy, kWsBatchIn, kWsFactors, kWsCount
+  kWsPropGram, kWsPropTrain, kWsPropCopy, kWsBatchIn, kWsFactors, kWsModeSketch, kWsErrVec, kWsCount
 };
 
 // Returns a device buffer of at least `bytes` for the slot (grown on demand), or
@@ -95,6 +95,11 @@ cudaError_t cluster_occupancy(idl_ctx* ctx, const void* kern, const cudaLaunchCo
 cudaError_t launch_draw_countsketch(cudaStream_t st, uint64_t seed, int64_t I, int64_t L, int modified,
                                     int32_t* h, int8_t* s, int* status);
 cudaError_t launch_draw_gaussian(cudaStream_t st, uint64_t seed, int64_t m2, int64_t m1, double* Omega);
+// the same Box-Muller pairs in FP32 arithmetic (FP32 pipelines and batches), stored as doubles
+cudaError_t launch_draw_gaussian_f32(cudaStream_t st, uint64_t seed, int64_t m2, int64_t m1, double* Omega);
+// the same draw from the stream of another tag (kTagGaussId, kTagGaussMode + n)
+cudaError_t launch_draw_gaussian_tag(cudaStream_t st, uint64_t seed, uint32_t tag, int64_t m2, int64_t m1,
+                                     double* Omega);
 cudaError_t launch_draw_mode(cudaStream_t st, uint64_t seed, int n, int64_t In, int64_t L, int32_t* h,
                              int8_t* s);
 int launch_bucket_offsets(idl_ctx* ctx, const int32_t* h, int64_t I, int64_t L, int32_t* bucket_ptr,
@@ -112,6 +117,10 @@ int launch_countsketch_csr(idl_ctx* ctx, const int64_t* rowptr, const int32_t* c
 // gaussian.cu
 int launch_gaussian(idl_ctx* ctx, const double* Omega, int64_t m2, int64_t m1, const void* Y1, int64_t R,
                     int64_t ldy1, int dtype, int precision, void* Y2, int64_t ldy2);
+
+// Y[l, r] = lambda_r prod_n G_n[l, r]: G holds N blocks of L x R column-major FP32 (ld L,
+// block stride L R), Y column-major (ld L)
+int launch_kr_product(idl_ctx* ctx, const float* G, int N, int64_t L, int64_t R, const double* lambda, float* Y);
 
 int launch_gaussian_reduce(idl_ctx* ctx, const float* part, int splits, int64_t R, int MP, int64_t m2, float* Y2,
                            int64_t ldy2);
@@ -144,6 +153,13 @@ int launch_lambda_hat(idl_ctx* ctx, const double* lambda, const int32_t* J, cons
                       int64_t R, double* lambda_hat);
 int launch_transpose_to_colmajor(idl_ctx* ctx, const void* Y1, int64_t m, int64_t R, int64_t ldy1, int dtype,
                                  void* Y2, int64_t ldy2);
+
+// errest.cu: ||A - A_J P||_2 / ||A||_2 by the power method (device pointers; synchronises)
+int launch_id_error_dense(idl_ctx* ctx, const void* A, int64_t I, int64_t R, int64_t lda, int dtype,
+                          const int32_t* J, const double* T, int64_t K, int iters, uint64_t seed, double* err);
+int launch_id_error_csr(idl_ctx* ctx, const int64_t* rowptr, const int32_t* colidx, const void* vals, int64_t I,
+                        int64_t R, int dtype, const int32_t* J, const double* T, int64_t K, int iters, uint64_t seed,
+                        double* err);
 
 // proposal.cu
 int launch_features(idl_ctx* ctx, const float* Y, int64_t m, int64_t R, int64_t ld, int64_t K, float* F);

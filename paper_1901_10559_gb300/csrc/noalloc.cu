@@ -37,7 +37,7 @@ __global__ void bucket_sort_block_kernel(const int32_t* __restrict__ ptr, int32_
 namespace {
 
 constexpr int64_t kMaxBuckets = IDL_NOALLOC_MAX_BUCKETS;
-// layout (int32 words): cursor[kMaxBuckets + 1] | big[kMaxBuckets + 1] | nbig | status | pad
+// layout (int32 words): cursor[kMaxBuckets + 1] | big[kMaxBuckets + 1] | nbig | pad
 constexpr int64_t kWords = 2 * (kMaxBuckets + 1) + 4;
 
 __device__ __align__(256) int32_t g_noalloc_scratch[kWords];
@@ -96,10 +96,9 @@ extern "C" int idl_bucket_offsets_noalloc(void* stream, const int32_t* h, int64_
   int32_t* cursor = d->base;
   int32_t* big = d->base + (kMaxBuckets + 1);
   int32_t* nbig = big + (kMaxBuckets + 1);
-  int* status = (int*)(nbig + 1);
   // the counters and the oversized-bucket count must start at zero on every call
   if (cudaMemsetAsync(cursor, 0, sizeof(int32_t) * (size_t)L, st) != cudaSuccess ||
-      cudaMemsetAsync(nbig, 0, 2 * sizeof(int32_t), st) != cudaSuccess) {
+      cudaMemsetAsync(nbig, 0, sizeof(int32_t), st) != cudaSuccess) {
     (void)cudaGetLastError();
     return IDL_ECUDA;
   }
@@ -109,7 +108,8 @@ extern "C" int idl_bucket_offsets_noalloc(void* stream, const int32_t* h, int64_
     if (blocks > 4 * d->num_sms) blocks = 4 * d->num_sms;
     if (blocks < 1) blocks = 1;
     const size_t sm = L <= 12288 ? sizeof(int32_t) * (size_t)L : 0;
-    bucket_hist_kernel<<<(unsigned)blocks, threads, sm, st>>>(h, I, L, cursor, status), count_launch();
+    // no status word: out-of-range entries of h show as bucket_ptr[L] < I
+    bucket_hist_kernel<<<(unsigned)blocks, threads, sm, st>>>(h, I, L, cursor, nullptr), count_launch();
   }
   bucket_scan_kernel<<<1, 1024, 0, st>>>(cursor, L, bucket_ptr, cursor), count_launch();
   if (I > 0) bucket_scatter_kernel<<<(unsigned)cdiv(I, 256), 256, 0, st>>>(h, I, L, cursor, row_list), count_launch();

@@ -46,6 +46,23 @@ def test_gaussian_draws(ctx):
         assert np.all(np.abs(g32 - w32) <= np.spacing(np.abs(w32)))
 
 
+def test_gaussian_draws_fp32_arithmetic(ctx):
+    """The FP32-arithmetic draw of the FP32 pipelines: every entry within
+    4e-7 (rho + |z|) of the FP64 definition, rho the pair's radius; the even sizes
+    and an odd count (a lone last entry) are covered."""
+    for m2, m1, seed in [(30, 900, 20190130), (7, 13, 1), (120, 14400, 4), (1, 1_000_001, 9)]:
+        Om = torch.empty(m2 * m1, dtype=torch.float64, device="cuda")
+        idl.idl_draw_gaussian_fp32(ctx, seed, m2, m1, Om)
+        want = odr.gaussian_matrix(seed, m2, m1).ravel()
+        got = host(Om)
+        n = want.size
+        first = 2 * (np.arange(n) // 2)                                # first entry of each entry's pair
+        second = np.where(first + 1 < n, want[np.minimum(first + 1, n - 1)], 0.0)
+        rho = np.hypot(want[first], second)
+        assert np.all(np.abs(got - want) <= 4e-7 * (rho + np.abs(want)) + 1e-30), np.abs(got - want).max()
+        assert np.all(got == got.astype(np.float32))                 # FP32 values
+
+
 def test_mode_draws(ctx):
     for n in range(4):
         h = torch.empty(1000, dtype=torch.int32, device="cuda")

@@ -10,6 +10,7 @@ import pytest
 import torch
 
 import paper_1901_10559_gb300 as idl
+from oracle import countsketch as ocs
 
 pytestmark = pytest.mark.gpu
 
@@ -43,6 +44,30 @@ def test_noalloc_matches_bucket_offsets_on_consecutive_calls(ctx):
         assert rc == idl.IDL_OK
         torch.cuda.synchronize()
         # integer work: bit-exact, the tolerance the other bucket tests use
+        assert np.array_equal(ptr.cpu().numpy(), want_ptr)
+        assert np.array_equal(rows.cpu().numpy(), want_rows)
+
+
+@pytest.mark.parametrize("I,L,skew", [(300_000, 8, False), (60_000, 20_000, True)])
+def test_noalloc_and_regular_offsets_equal_the_oracle_with_oversized_buckets(ctx, I, L, skew):
+    """Buckets of more than 12288 rows (I = 300000 over 8 buckets, and a skewed map
+    that puts 20000 rows into one of 20000 buckets) come out in increasing row order
+    from both entry points: bit-exact against the oracle's stable counting sort."""
+    if skew:
+        g = torch.Generator(device="cuda").manual_seed(3)
+        h = torch.randint(0, L, (I,), dtype=torch.int32, device="cuda", generator=g)
+        h[torch.randperm(I, device="cuda", generator=g)[:20_000]] = 7
+    else:
+        h = _maps(ctx, 21, I, L, False)
+    want_ptr, want_rows = ocs.bucket_offsets(h.cpu().numpy(), L)
+    got = _reference_offsets(ctx, h, I, L)
+    assert np.array_equal(got[0], want_ptr) and np.array_equal(got[1], want_rows)
+    stream = torch.cuda.current_stream()
+    for _ in range(2):
+        ptr = torch.full((L + 1,), -7, dtype=torch.int32, device="cuda")
+        rows = torch.full((I,), -7, dtype=torch.int32, device="cuda")
+        assert idl.idl_bucket_offsets_noalloc(stream, h, I, L, ptr, rows) == idl.IDL_OK
+        torch.cuda.synchronize()
         assert np.array_equal(ptr.cpu().numpy(), want_ptr)
         assert np.array_equal(rows.cpu().numpy(), want_rows)
 
