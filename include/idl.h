@@ -67,7 +67,9 @@ typedef struct idl_params {
   int32_t  residual;  /* 0: none; 1: ||R22||_F / ||Y2||_F in FP64 (default); 2: explicit FP64 ||Y2_rest - Y2_J T||_F / ||Y2||_F */
   int32_t  learned;   /* QR stage column proposal: IDL_PROPOSAL_NONE (default), _MLP or _NORM (FP32 data, m <= 128) */
   int32_t  cand_factor; /* proposal candidates C = min(cand_factor * K, R); 0 = 2 (1..8) */
-  int32_t  reserved1;
+  float    srrqr_f;   /* 0: the pivoted QR's J (default); f > 1: Gu-Eisenstat exchanges after it until no
+                         W_ij^2 + (gamma_j / omega_i)^2 exceeds f^2 (a strong rank-revealing QR, Fact 1 with
+                         f = 2: |T_ij| <= f); single-item pipelines, not with a column proposal or batches */
   int64_t  reserved[3];
 } idl_params;
 
@@ -247,6 +249,23 @@ int idl_cpqr(idl_ctx* ctx, void* Y2, int64_t m, int64_t R, int64_t ldy2, int dty
              int32_t* J, double* rnorm);
 
 /* ---------------------------------------------------------------------------
+ * The QR stage with the strong rank-revealing exchanges of Fact 1 (Gu &
+ * Eisenstat 1996): the pivoted QR of idl_cpqr, then, while some
+ * rho_ij = W_ij^2 + (gamma_j / omega_i)^2 exceeds f^2 (W = R11^{-1} R12,
+ * gamma_j the norm of R22's column j, 1 / omega_i the norm of row i of
+ * R11^{-1}), skeleton column J[i] is exchanged for the j-th non-skeleton
+ * column (largest rho; ties: smallest i, then j) and the sketch factored again
+ * with J as given pivots; each exchange multiplies |det R11| by sqrt(rho).
+ * Y2 (m x R column-major, ldy2 >= m, dtype, device) is read only; J (K int32)
+ * and T (K x (R-K) FP64, the layout of idl_t_solve) are device outputs for the
+ * final selection.  f > 1 (Fact 1 uses f = 2).  Synchronises once per exchange
+ * considered; at most 256 exchanges.  The pipelines do the same with
+ * idl_params.srrqr_f.
+ * ------------------------------------------------------------------------- */
+int idl_cpqr_srrqr(idl_ctx* ctx, const void* Y2, int64_t m, int64_t R, int64_t ldy2, int dtype, int64_t K, float f,
+                   int32_t* J, double* T);
+
+/* ---------------------------------------------------------------------------
  * T = R11^{-1} R12 in FP64 by back substitution (Algorithm 1 lines 5-6), from
  * the factored Y2 of idl_cpqr and its J.  T: K x (R-K) row-major FP64 (device);
  * column c of T belongs to the c-th non-skeleton column in ascending index.
@@ -293,6 +312,30 @@ int id_matrix_csr(idl_ctx* ctx, const int64_t* rowptr, const int32_t* colidx, co
 int id_cp_tensor(idl_ctx* ctx, int N, const int64_t* dims, int64_t R, const void* const* factors,
                  const int64_t* ldf, const double* lambda, int64_t K, const idl_params* p,
                  int32_t* J, double* T, double* lambda_hat, idl_info* info);
+
+/* ---------------------------------------------------------------------------
+ * Row blocks.  The sketch is linear in the rows of A (Sec. 1.3):
+ *   Omega S A = sum over row blocks B of Omega S[:, B] A[B, :],
+ * so a matrix split by rows over several GPUs (or streamed in pieces) is
+ * sketched block by block and the partial sketches are summed.
+ * idl_sketch_rows / idl_sketch_rows_csr: rows i0 .. i0+n-1 of an I-row matrix
+ *   (A here holds just those n rows; the CSR rowptr has n + 1 entries indexing
+ *   colidx / vals), sketched with the maps h, s, the permutation and Omega of
+ *   the whole I-row matrix (params as for id_matrix; K is not needed), into
+ *   the m x R column-major sketch Y2 (device memory, ldy2 >= m; m = params.m2,
+ *   or params.m1 when m2 = 0): Y2 = partial (accumulate = 0) or Y2 += partial.
+ *   A, rowptr, colidx, vals: device or host arrays.
+ * idl_id_from_sketch: Algorithm 1 on a complete sketch Y2 (m x R column-major,
+ *   device or host, ldy2 >= m, m <= 256): J, T (and info) as the pipelines
+ *   give them; params.residual, learned, cand_factor and srrqr_f apply.
+ * ------------------------------------------------------------------------- */
+int idl_sketch_rows(idl_ctx* ctx, const void* A, int64_t n, int64_t R, int64_t lda, int dtype, int64_t i0, int64_t I,
+                    const idl_params* p, void* Y2, int64_t ldy2, int accumulate);
+int idl_sketch_rows_csr(idl_ctx* ctx, const int64_t* rowptr, const int32_t* colidx, const void* vals, int64_t n,
+                        int64_t R, int64_t nnz, int dtype, int64_t i0, int64_t I, const idl_params* p, void* Y2,
+                        int64_t ldy2, int accumulate);
+int idl_id_from_sketch(idl_ctx* ctx, const void* Y2, int64_t m, int64_t R, int64_t ldy2, int dtype, int64_t K,
+                       const idl_params* p, int32_t* J, double* T, idl_info* info);
 
 /* ---------------------------------------------------------------------------
  * Gaussian ID, the comparison method of the paper (Sec. 1.2.1 and Sec. 1.2.2).

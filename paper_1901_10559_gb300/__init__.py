@@ -39,7 +39,7 @@ class IdlError(RuntimeError):
 class Params(ctypes.Structure):
     _fields_ = [("m1", ctypes.c_int64), ("m2", ctypes.c_int64), ("modified", ctypes.c_int32),
                 ("precision", ctypes.c_int32), ("seed", ctypes.c_uint64), ("residual", ctypes.c_int32),
-                ("learned", ctypes.c_int32), ("cand_factor", ctypes.c_int32), ("reserved1", ctypes.c_int32),
+                ("learned", ctypes.c_int32), ("cand_factor", ctypes.c_int32), ("srrqr_f", ctypes.c_float),
                 ("reserved", ctypes.c_int64 * 3)]
 
 
@@ -95,6 +95,7 @@ _SIGS = {
     "idl_draw_gaussian": ([_vp, _u64, _i64, _i64, _vp], _int),
     "idl_draw_gaussian_fp32": ([_vp, _u64, _i64, _i64, _vp], _int),
     "idl_draw_mode": ([_vp, _u64, _int, _i64, _i64, _vp, _vp], _int),
+    "idl_cpqr_srrqr": ([_vp, _vp, _i64, _i64, _i64, _int, _i64, ctypes.c_float, _vp, _vp], _int),
     "idl_bucket_offsets": ([_vp, _vp, _i64, _i64, _vp, _vp], _int),
     "idl_bucket_offsets_noalloc": ([_vp, _vp, _i64, _i64, _vp, _vp], _int),
     "idl_countsketch_dense": ([_vp, _vp, _i64, _i64, _i64, _int, _vp, _vp, _vp, _vp, _i64, _vp, _i64], _int),
@@ -120,6 +121,12 @@ _SIGS = {
                       ctypes.POINTER(ctypes.c_double)], _int),
     "idl_id_error_csr": ([_vp, _vp, _vp, _vp, _i64, _i64, _i64, _int, _vp, _vp, _i64, ctypes.c_int32,
                           ctypes.c_uint64, ctypes.POINTER(ctypes.c_double)], _int),
+    "idl_sketch_rows": ([_vp, _vp, _i64, _i64, _i64, _int, _i64, _i64, ctypes.POINTER(Params), _vp, _i64, _int],
+                        _int),
+    "idl_sketch_rows_csr": ([_vp, _vp, _vp, _vp, _i64, _i64, _i64, _int, _i64, _i64, ctypes.POINTER(Params), _vp,
+                             _i64, _int], _int),
+    "idl_id_from_sketch": ([_vp, _vp, _i64, _i64, _i64, _int, _i64, ctypes.POINTER(Params), _vp, _vp,
+                            ctypes.POINTER(Info)], _int),
     "idl_batch_run": ([_vp, ctypes.POINTER(BatchItem), _int], _int),
     "idl_tune_save": ([_vp, ctypes.c_char_p], _int),
     "idl_tune_load": ([_vp, ctypes.c_char_p], _int),
@@ -229,11 +236,11 @@ def launch_count() -> int:
 
 
 def make_params(m1, m2, seed, modified=True, precision=PREC_FP32, residual=1, learned=PROPOSAL_NONE,
-                cand_factor=0):
+                cand_factor=0, srrqr_f=0.0):
     p = Params()
     p.m1, p.m2, p.modified, p.precision, p.seed, p.residual = int(m1), int(m2), int(modified), int(precision), \
         int(seed), int(residual)
-    p.learned, p.cand_factor = int(learned), int(cand_factor)
+    p.learned, p.cand_factor, p.srrqr_f = int(learned), int(cand_factor), float(srrqr_f)
     return p
 
 
@@ -248,6 +255,10 @@ def idl_draw_gaussian(ctx, seed, m2, m1, Omega):
 
 def idl_draw_gaussian_fp32(ctx, seed, m2, m1, Omega):
     return ctx.check(lib().idl_draw_gaussian_fp32(ctx.ptr, seed, m2, m1, _p(Omega)))
+
+
+def idl_cpqr_srrqr(ctx, Y2, m, R, ldy2, dtype, K, f, J, T):
+    return ctx.check(lib().idl_cpqr_srrqr(ctx.ptr, _p(Y2), m, R, ldy2, dtype, K, f, _p(J), _p(T)))
 
 
 def idl_draw_mode(ctx, seed, n, In, L, h, s):
@@ -393,6 +404,34 @@ def idl_id_error_csr(ctx, rowptr, colidx, vals, shape, J, T, K, iters=50, seed=1
     ctx.check(lib().idl_id_error_csr(ctx.ptr, _p(rowptr), _p(colidx), _p(vals), I, R, int(vals.shape[0]), dt, _p(J),
                                      _p(T), K, iters, seed, ctypes.byref(err)))
     return err.value
+
+
+def _dt(x):
+    return IDL_F64 if str(x.dtype).endswith("float64") else IDL_F32
+
+
+def idl_sketch_rows(ctx, A_rows, i0, I, params, Y2, ldy2=None, accumulate=False, lda=None):
+    """Y2 (+)= the sketch of rows i0 .. i0 + n - 1 (A_rows, n x R) of an I-row matrix."""
+    n, R = int(A_rows.shape[0]), int(A_rows.shape[1])
+    m = params.m2 if params.m2 > 0 else params.m1
+    ctx.check(lib().idl_sketch_rows(ctx.ptr, _p(A_rows), n, R, R if lda is None else lda, _dt(A_rows), int(i0),
+                                    int(I), ctypes.byref(params), _p(Y2), m if ldy2 is None else ldy2,
+                                    int(bool(accumulate))))
+
+
+def idl_sketch_rows_csr(ctx, rowptr, colidx, vals, n, R, i0, I, params, Y2, ldy2=None, accumulate=False):
+    """The same for a CSR block of n rows (rowptr: n + 1 entries)."""
+    m = params.m2 if params.m2 > 0 else params.m1
+    ctx.check(lib().idl_sketch_rows_csr(ctx.ptr, _p(rowptr), _p(colidx), _p(vals), int(n), int(R),
+                                        int(vals.shape[0]), _dt(vals), int(i0), int(I), ctypes.byref(params), _p(Y2),
+                                        m if ldy2 is None else ldy2, int(bool(accumulate))))
+
+
+def idl_id_from_sketch(ctx, Y2, m, R, K, params, J, T, info=None, ldy2=None):
+    """Algorithm 1 on a complete m x R column-major sketch."""
+    return ctx.check(lib().idl_id_from_sketch(ctx.ptr, _p(Y2), int(m), int(R), m if ldy2 is None else ldy2, _dt(Y2),
+                                              int(K), ctypes.byref(params), _p(J), _p(T),
+                                              ctypes.byref(info) if info is not None else None))
 
 
 # ---------------------------------------------------------------- batches

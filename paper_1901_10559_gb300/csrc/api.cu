@@ -279,6 +279,8 @@ extern "C" int idl_destroy(idl_ctx* ctx) {
   if (ctx->gev_out) cudaEventDestroy(ctx->gev_out);
   if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
   if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
+  if (ctx->copy) { cudaStreamSynchronize(ctx->copy); cudaStreamDestroy(ctx->copy); }
+  for (cudaEvent_t e : ctx->cevs) cudaEventDestroy(e);
   cudaFree(ctx->d_status);
   cudaFree(ctx->d_diag);
   delete ctx;
@@ -472,6 +474,23 @@ extern "C" int idl_cpqr(idl_ctx* ctx, void* Y2, int64_t m, int64_t R, int64_t ld
   return launch_cpqr(ctx, Y2, m, R, ldy2, dtype, K, J, rnorm);
 }
 
+extern "C" int idl_cpqr_srrqr(idl_ctx* ctx, const void* Y2, int64_t m, int64_t R, int64_t ldy2, int dtype, int64_t K,
+                              float f, int32_t* J, double* T) {
+  TRY(check_ctx(ctx));
+  if ((dtype != IDL_F32 && dtype != IDL_F64) || m < 1 || R < 2 || ldy2 < m || K < 1 || K > m || K >= R || !Y2 || !J ||
+      !T || !(f > 1.f))
+    return fail(ctx, IDL_EINVAL, "cpqr_srrqr: bad arguments");
+  const int es = dtype_size(dtype);
+  void* Yf = ws_get(ctx, kWsYf, (size_t)es * (size_t)(R * ldy2));
+  int32_t* rest = (int32_t*)ws_get(ctx, kWsRest, sizeof(int32_t) * (size_t)R);
+  if (!Yf || !rest) return IDL_ENOMEM;
+  TRY(cuda_check(ctx, cudaMemcpyAsync(Yf, Y2, (size_t)es * (size_t)(R * ldy2), cudaMemcpyDeviceToDevice, ctx->stream),
+                 "copy"));
+  TRY(clear_diag(ctx));
+  TRY(launch_cpqr(ctx, Yf, m, R, ldy2, dtype, K, J, nullptr));
+  return launch_srrqr(ctx, Y2, Yf, m, R, ldy2, dtype, K, J, T, rest, f);
+}
+
 extern "C" int idl_t_solve(idl_ctx* ctx, const void* Y2, int64_t m, int64_t R, int64_t ldy2, int dtype, int64_t K,
                            const int32_t* J, double* T, int32_t* rest) {
   TRY(check_ctx(ctx));
@@ -514,6 +533,8 @@ static int check_params(idl_ctx* ctx, const idl_params* p, int dtype, int64_t I,
   if (p->cand_factor < 0 || p->cand_factor > 8) return fail(ctx, IDL_EINVAL, "cand_factor must be in 0..8");
   if (p->learned && ((p->m2 > 0 ? p->m2 : p->m1) > 128 || K > 128))
     return fail(ctx, IDL_ELIMIT, "the column proposal needs m <= 128 and K <= 128");
+  if (!(p->srrqr_f == 0.f || p->srrqr_f > 1.f)) return fail(ctx, IDL_EINVAL, "srrqr_f must be 0 or > 1");
+  if (p->srrqr_f > 0.f && p->learned) return fail(ctx, IDL_EINVAL, "srrqr_f and the column proposal exclude each other");
   return IDL_OK;
 }
 
@@ -546,6 +567,10 @@ static int fork_omega(idl_ctx* ctx, const idl_params* p, double** Om) {
 static int finish_from_y2(idl_ctx* ctx, const idl_params* p, int dtype, void* Y2, int64_t m, int64_t R, int64_t K,
                           int32_t* J, double* T, idl_info* info);
 
+// The QR stage factors a copy of the sketch (kept beside it in the kWsY2 slot) for the
+// explicit residual and for the strong rank-revealing exchanges.
+static bool keeps_sketch(const idl_params* p) { return p->residual == 2 || p->srrqr_f > 0.f; }
+
 // Sketch Y1 (m1 x R, row-major, ld = ldy1; column-major when y1_cm, which needs the
 // tensor-core Gaussian stage) -> J, T, via the Gaussian stage and the QR stage.
 // Om: the Gaussian matrix from fork_omega (joined here), or nullptr to draw it now.
@@ -555,8 +580,7 @@ static int finish_pipeline(idl_ctx* ctx, const idl_params* p, int dtype, void* Y
   const int es = dtype_size(dtype);
   const int64_t m = p->m2 > 0 ? p->m2 : p->m1;
   const int64_t ld2 = m;
-  const bool keep_orig = p->residual == 2;
-  void* Y2 = ws_get(ctx, kWsY2, (size_t)es * (size_t)(R * ld2) * (keep_orig ? 2 : 1));
+  void* Y2 = ws_get(ctx, kWsY2, (size_t)es * (size_t)(R * ld2) * (keeps_sketch(p) ? 2 : 1));
   if (!Y2) return IDL_ENOMEM;
   if (p->m2 > 0) {
     if (Om) {
@@ -588,7 +612,7 @@ static int finish_from_y2(idl_ctx* ctx, const idl_params* p, int dtype, void* Y2
                           int32_t* J, double* T, idl_info* info) {
   const int es = dtype_size(dtype);
   const int64_t ld2 = m;
-  const bool keep_orig = p->residual == 2;
+  const bool keep_orig = keeps_sketch(p);
   void* Yf = Y2;
   if (p->learned) {
     // the proposal reads the sketch and writes the factored copy; the fallback re-reads the sketch
@@ -609,8 +633,11 @@ static int finish_from_y2(idl_ctx* ctx, const idl_params* p, int dtype, void* Y2
     STAGE(kStQR, launch_proposal_qr(ctx, (const float*)Y2, (float*)Yf, m, R, ld2, K, p->learned, p->cand_factor, Jd));
   else
     STAGE(kStQR, launch_cpqr(ctx, Yf, m, R, ld2, dtype, K, Jd, nullptr));
-  STAGE(kStSolve, launch_t_solve(ctx, Yf, m, R, ld2, dtype, K, Jd, Td, rest));
-  if (keep_orig) STAGE(kStCheck, launch_residual(ctx, Y2, Yf, m, R, ld2, dtype, K, Jd, Td, rest));
+  if (p->srrqr_f > 0.f)       // exchanges after the pivoted QR; ends with the T solve of the final selection
+    STAGE(kStQR, launch_srrqr(ctx, Y2, Yf, m, R, ld2, dtype, K, Jd, Td, rest, p->srrqr_f));
+  else
+    STAGE(kStSolve, launch_t_solve(ctx, Yf, m, R, ld2, dtype, K, Jd, Td, rest));
+  if (p->residual == 2) STAGE(kStCheck, launch_residual(ctx, Y2, Yf, m, R, ld2, dtype, K, Jd, Td, rest));
   if (!jdev)
     TRY(cuda_check(ctx, cudaMemcpyAsync(J, Jd, sizeof(int32_t) * K, cudaMemcpyDeviceToHost, ctx->stream), "copy J"));
   if (!tdev)
@@ -647,6 +674,68 @@ static int id_matrix_impl(idl_ctx* ctx, const void* A, int64_t I, int64_t R, int
   return finish_pipeline(ctx, p, dtype, Y1, ldy1, R, K, J, T, info, false, Om);
 }
 
+// Host CSR arrays of a large matrix: the sketch is a sum over row blocks
+// (Y1 = sum_c S[:, rows_c] A[rows_c, :]), so the rows are cut into chunks of about
+// equal nonzeros, each chunk's column indices and values are copied on the context's
+// copy stream, and the chunk is sketched (bucket offsets of its rows, CSR sketch added
+// into Y1) as soon as its copy has arrived -- the copies of the next chunks overlap it.
+constexpr int64_t kCsrChunkMinNnz = 1 << 22;
+constexpr int kCsrChunks = 8;
+
+static cudaEvent_t ctx_event(idl_ctx* ctx, size_t i) {
+  while (ctx->cevs.size() <= i) {
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return nullptr;
+    ctx->cevs.push_back(e);
+  }
+  return ctx->cevs[i];
+}
+
+static int csr_chunked_sketch(idl_ctx* ctx, const int64_t* h_rowptr, const int32_t* h_colidx, const void* h_vals,
+                              int64_t I, int64_t R, int64_t nnz, int dtype, const int64_t* d_rowptr, const int32_t* h,
+                              const int8_t* s, int64_t m1, int32_t* ptr, int32_t* rows, void* Y1, int64_t ldy1) {
+  const int es = dtype_size(dtype);
+  int32_t* d_ci = (int32_t*)ws_get(ctx, kWsColidx, sizeof(int32_t) * (size_t)nnz);
+  unsigned char* d_v = (unsigned char*)ws_get(ctx, kWsVals, (size_t)es * (size_t)nnz);
+  if (!d_ci || !d_v) return IDL_ENOMEM;
+  if (!ctx->copy) TRY(cuda_check(ctx, cudaStreamCreateWithFlags(&ctx->copy, cudaStreamNonBlocking), "copy stream"));
+  cudaEvent_t e0 = ctx_event(ctx, 0);
+  if (!e0) return fail(ctx, IDL_ECUDA, "event creation failed");
+  // the copies start after the work queued before this call (which may still read these buffers)
+  TRY(cuda_check(ctx, cudaEventRecord(e0, ctx->stream), "copy order"));
+  TRY(cuda_check(ctx, cudaStreamWaitEvent(ctx->copy, e0, 0), "copy order"));
+  int64_t r0 = 0;
+  for (int c = 0; c < kCsrChunks && r0 < I; ++c) {
+    // last row of the chunk: the first row whose rowptr reaches the chunk's share of nonzeros
+    const int64_t target = nnz * (c + 1) / kCsrChunks;
+    int64_t lo = r0 + 1, hi = I;
+    while (lo < hi) {
+      const int64_t mid = (lo + hi) / 2;
+      if (h_rowptr[mid] >= target) hi = mid; else lo = mid + 1;
+    }
+    const int64_t r1 = c + 1 == kCsrChunks ? I : lo;
+    const int64_t z0 = std::min(std::max<int64_t>(h_rowptr[r0], 0), nnz);
+    const int64_t z1 = std::min(std::max<int64_t>(h_rowptr[r1], z0), nnz);
+    if (z1 > z0) {
+      TRY(cuda_check(ctx, cudaMemcpyAsync(d_ci + z0, h_colidx + z0, sizeof(int32_t) * (size_t)(z1 - z0),
+                                          cudaMemcpyHostToDevice, ctx->copy), "copy in"));
+      TRY(cuda_check(ctx, cudaMemcpyAsync(d_v + (size_t)es * z0, (const unsigned char*)h_vals + (size_t)es * z0,
+                                          (size_t)es * (size_t)(z1 - z0), cudaMemcpyHostToDevice, ctx->copy),
+                     "copy in"));
+    }
+    cudaEvent_t ec = ctx_event(ctx, (size_t)c + 1);
+    if (!ec) return fail(ctx, IDL_ECUDA, "event creation failed");
+    TRY(cuda_check(ctx, cudaEventRecord(ec, ctx->copy), "copy event"));
+    const int64_t n = r1 - r0;
+    STAGE(kStBucket, launch_bucket_offsets(ctx, h + r0, n, m1, ptr, rows));
+    TRY(cuda_check(ctx, cudaStreamWaitEvent(ctx->stream, ec, 0), "chunk wait"));
+    STAGE(kStSketch, launch_countsketch_csr(ctx, d_rowptr + r0, d_ci, d_v, n, R, nnz, dtype, s + r0, ptr, rows, m1,
+                                            Y1, ldy1, c > 0));
+    r0 = r1;
+  }
+  return IDL_OK;
+}
+
 static int id_matrix_csr_impl(idl_ctx* ctx, const int64_t* rowptr, const int32_t* colidx, const void* vals, int64_t I,
                              int64_t R, int64_t nnz, int dtype, int64_t K, const idl_params* p, int32_t* J, double* T,
                              idl_info* info) {
@@ -661,11 +750,16 @@ static int id_matrix_csr_impl(idl_ctx* ctx, const int64_t* rowptr, const int32_t
   int rc;
   const int64_t* rp = (const int64_t*)stage_in(ctx, rowptr, sizeof(int64_t) * (size_t)(I + 1), kWsRowptr, &rc);
   TRY(rc);
-  const int32_t* ci = nnz ? (const int32_t*)stage_in(ctx, colidx, sizeof(int32_t) * (size_t)nnz, kWsColidx, &rc)
-                          : colidx;
-  TRY(rc);
-  const void* vv = nnz ? stage_in(ctx, vals, (size_t)es * (size_t)nnz, kWsVals, &rc) : vals;
-  TRY(rc);
+  const bool chunked = nnz >= kCsrChunkMinNnz && !is_device_ptr(rowptr) && !is_device_ptr(colidx) &&
+                       !is_device_ptr(vals);
+  const int32_t* ci = colidx;
+  const void* vv = vals;
+  if (!chunked && nnz) {
+    ci = (const int32_t*)stage_in(ctx, colidx, sizeof(int32_t) * (size_t)nnz, kWsColidx, &rc);
+    TRY(rc);
+    vv = stage_in(ctx, vals, (size_t)es * (size_t)nnz, kWsVals, &rc);
+    TRY(rc);
+  }
   WS(h, int32_t, kWsH, I);
   WS(s, int8_t, kWsS, I);
   WS(ptr, int32_t, kWsBucketPtr, m1 + 1);
@@ -675,8 +769,12 @@ static int id_matrix_csr_impl(idl_ctx* ctx, const int64_t* rowptr, const int32_t
   if (!Y1) return IDL_ENOMEM;
   STAGE(kStDraw, cuda_check(ctx, launch_draw_countsketch(ctx->stream, p->seed, I, m1, p->modified, h, s,
                                                          ctx->d_status), "draw countsketch"));
-  STAGE(kStBucket, launch_bucket_offsets(ctx, h, I, m1, ptr, rows));
-  STAGE(kStSketch, launch_countsketch_csr(ctx, rp, ci, vv, I, R, nnz, dtype, s, ptr, rows, m1, Y1, ldy1));
+  if (chunked) {
+    TRY(csr_chunked_sketch(ctx, rowptr, colidx, vals, I, R, nnz, dtype, rp, h, s, m1, ptr, rows, Y1, ldy1));
+  } else {
+    STAGE(kStBucket, launch_bucket_offsets(ctx, h, I, m1, ptr, rows));
+    STAGE(kStSketch, launch_countsketch_csr(ctx, rp, ci, vv, I, R, nnz, dtype, s, ptr, rows, m1, Y1, ldy1));
+  }
   return finish_pipeline(ctx, p, dtype, Y1, ldy1, R, K, J, T, info, false, Om);
 }
 
@@ -783,6 +881,121 @@ static int id_cp_tensor_impl(idl_ctx* ctx, int N, const int64_t* dims, int64_t R
 }
 
 // ---------------------------------------------------------------------------
+// Row blocks (Sec. 1.3: S A = sum over row blocks of S[:, rows] A[rows, :]): the
+// sketch Omega S[:, i0 .. i0+n) A[i0 .. i0+n, :] of one block of an I-row matrix,
+// drawn with the whole matrix's maps, written or added into Y2; and the ID from a
+// complete sketch.  Ranks that each hold a block of rows sum their partial
+// sketches (one all-reduce of m x R) and run idl_id_from_sketch.
+// ---------------------------------------------------------------------------
+static int check_rows(idl_ctx* ctx, const idl_params* p, int dtype, int64_t n, int64_t i0, int64_t I, int64_t R,
+                      const void* Y2, int64_t ldy2) {
+  if (!p) return fail(ctx, IDL_EINVAL, "null params");
+  if (dtype != IDL_F32 && dtype != IDL_F64) return fail(ctx, IDL_EINVAL, "dtype must be IDL_F32 or IDL_F64");
+  if (p->precision < 0 || p->precision > 3 || (dtype == IDL_F64) != (p->precision == IDL_PREC_FP64))
+    return fail(ctx, IDL_EINVAL, "precision does not match the data type");
+  if (p->m1 < 1 || p->m1 > 0x7fffffffLL || p->m2 < 0 || p->m2 > p->m1) return fail(ctx, IDL_EINVAL, "need 0 <= m2 <= m1");
+  if (n < 1 || i0 < 0 || i0 + n > I || I > 0x7fffffffLL || R < 1 || R > 0x7fffffffLL || !Y2)
+    return fail(ctx, IDL_EINVAL, "sketch_rows: need 0 <= i0, i0 + n <= I");
+  if (p->modified && !(p->m1 < I)) return fail(ctx, IDL_EINVAL, "modified CountSketch needs m1 < I");
+  if (ldy2 < (p->m2 > 0 ? p->m2 : p->m1)) return fail(ctx, IDL_EINVAL, "sketch_rows: ldy2 < m");
+  if (!is_device_ptr(Y2)) return fail(ctx, IDL_EINVAL, "sketch_rows: Y2 must be device memory");
+  return IDL_OK;
+}
+
+// shared tail: draws of the block's rows, bucket offsets, the sketch (dense or CSR), the
+// Gaussian stage into a packed partial sketch, then Y2 (+)= it
+template <typename SK>
+static int sketch_rows_tail(idl_ctx* ctx, const idl_params* p, int dtype, int64_t n, int64_t i0, int64_t I, int64_t R,
+                            void* Y2, int64_t ldy2, int accumulate, SK&& sketch) {
+  const int es = dtype_size(dtype);
+  const int64_t m1 = p->m1, m = p->m2 > 0 ? p->m2 : m1;
+  WS(h, int32_t, kWsH, n);
+  WS(s, int8_t, kWsS, n);
+  WS(ptr, int32_t, kWsBucketPtr, m1 + 1);
+  WS(rows, int32_t, kWsRowList, n);
+  const int64_t ldy1 = round_up(R, 32);
+  void* Y1 = ws_get(ctx, kWsY1, (size_t)es * (size_t)(m1 * ldy1));
+  void* Yp = ws_get(ctx, kWsY2, (size_t)es * (size_t)(m * R));
+  if (!Y1 || !Yp) return IDL_ENOMEM;
+  STAGE(kStDraw, cuda_check(ctx, launch_draw_countsketch_range(ctx->stream, p->seed, I, i0, n, m1, p->modified, h, s,
+                                                               ctx->d_status), "draw countsketch"));
+  STAGE(kStBucket, launch_bucket_offsets(ctx, h, n, m1, ptr, rows));
+  STAGE(kStSketch, sketch(s, ptr, rows, Y1, ldy1));
+  if (p->m2 > 0) {
+    double* Om = (double*)ws_get(ctx, kWsOmega, sizeof(double) * (size_t)(p->m2 * m1));
+    if (!Om) return IDL_ENOMEM;
+    STAGE(kStDraw, cuda_check(ctx, p->precision == IDL_PREC_FP64
+                                       ? launch_draw_gaussian(ctx->stream, p->seed, p->m2, m1, Om)
+                                       : launch_draw_gaussian_f32(ctx->stream, p->seed, p->m2, m1, Om),
+                              "draw gaussian"));
+    STAGE(kStGauss, launch_gaussian(ctx, Om, p->m2, m1, Y1, R, ldy1, dtype, p->precision, Yp, m));
+  } else {
+    STAGE(kStGauss, launch_transpose_to_colmajor(ctx, Y1, m, R, ldy1, dtype, Yp, m));
+  }
+  return launch_add_sketch(ctx, Yp, m, R, dtype, Y2, ldy2, accumulate);
+}
+
+extern "C" int idl_sketch_rows(idl_ctx* ctx, const void* A, int64_t n, int64_t R, int64_t lda, int dtype, int64_t i0,
+                               int64_t I, const idl_params* p, void* Y2, int64_t ldy2, int accumulate) {
+  TRY(check_ctx(ctx));
+  TRY(check_rows(ctx, p, dtype, n, i0, I, R, Y2, ldy2));
+  if (!A || lda < R) return fail(ctx, IDL_EINVAL, "sketch_rows: bad A");
+  int rc;
+  const void* Ad = stage_in(ctx, A, (size_t)dtype_size(dtype) * (size_t)((n - 1) * lda + R), kWsA, &rc);
+  TRY(rc);
+  return sketch_rows_tail(ctx, p, dtype, n, i0, I, R, Y2, ldy2, accumulate,
+                          [&](const int8_t* s, const int32_t* ptr, const int32_t* rows, void* Y1, int64_t ldy1) {
+                            return launch_countsketch_dense(ctx, Ad, n, R, lda, dtype, s, ptr, rows, p->m1, Y1, ldy1);
+                          });
+}
+
+extern "C" int idl_sketch_rows_csr(idl_ctx* ctx, const int64_t* rowptr, const int32_t* colidx, const void* vals,
+                                   int64_t n, int64_t R, int64_t nnz, int dtype, int64_t i0, int64_t I,
+                                   const idl_params* p, void* Y2, int64_t ldy2, int accumulate) {
+  TRY(check_ctx(ctx));
+  TRY(check_rows(ctx, p, dtype, n, i0, I, R, Y2, ldy2));
+  if (!rowptr || nnz < 0 || (nnz > 0 && (!colidx || !vals))) return fail(ctx, IDL_EINVAL, "sketch_rows_csr: bad CSR");
+  int rc;
+  const int64_t* rp = (const int64_t*)stage_in(ctx, rowptr, sizeof(int64_t) * (size_t)(n + 1), kWsRowptr, &rc);
+  TRY(rc);
+  const int32_t* ci = colidx;
+  const void* vv = vals;
+  if (nnz) {
+    ci = (const int32_t*)stage_in(ctx, colidx, sizeof(int32_t) * (size_t)nnz, kWsColidx, &rc);
+    TRY(rc);
+    vv = stage_in(ctx, vals, (size_t)dtype_size(dtype) * (size_t)nnz, kWsVals, &rc);
+    TRY(rc);
+  }
+  return sketch_rows_tail(ctx, p, dtype, n, i0, I, R, Y2, ldy2, accumulate,
+                          [&](const int8_t* s, const int32_t* ptr, const int32_t* rows, void* Y1, int64_t ldy1) {
+                            return launch_countsketch_csr(ctx, rp, ci, vv, n, R, nnz, dtype, s, ptr, rows, p->m1, Y1,
+                                                          ldy1);
+                          });
+}
+
+extern "C" int idl_id_from_sketch(idl_ctx* ctx, const void* Y2, int64_t m, int64_t R, int64_t ldy2, int dtype,
+                                  int64_t K, const idl_params* p, int32_t* J, double* T, idl_info* info) {
+  TRY(check_ctx(ctx));
+  if (!p || !Y2 || !J || !T || (dtype != IDL_F32 && dtype != IDL_F64) || m < 1 || m > 256 || ldy2 < m || K < 1 ||
+      K > m || K >= R || R > 0x7fffffffLL)
+    return fail(ctx, IDL_EINVAL, "id_from_sketch: bad arguments (1 <= K <= m <= 256, K < R)");
+  if (p->residual < 0 || p->residual > 2 || !(p->srrqr_f == 0.f || p->srrqr_f > 1.f) ||
+      p->learned < IDL_PROPOSAL_NONE || p->learned > IDL_PROPOSAL_NORM || (p->learned && p->srrqr_f > 0.f))
+    return fail(ctx, IDL_EINVAL, "id_from_sketch: bad params");
+  if (p->learned && (dtype != IDL_F32 || m > 128 || K > 128))
+    return fail(ctx, IDL_ELIMIT, "the column proposal needs FP32 data, m <= 128 and K <= 128");
+  const int es = dtype_size(dtype);
+  void* Yw = ws_get(ctx, kWsY2, (size_t)es * (size_t)(R * m) * (keeps_sketch(p) ? 2 : 1));
+  if (!Yw) return IDL_ENOMEM;
+  int rc;
+  const void* Yd = stage_in(ctx, Y2, (size_t)es * (size_t)((R - 1) * ldy2 + m), kWsA, &rc);
+  TRY(rc);
+  TRY(cuda_check(ctx, cudaMemcpy2DAsync(Yw, (size_t)es * m, Yd, (size_t)es * ldy2, (size_t)es * m, R,
+                                        cudaMemcpyDeviceToDevice, ctx->stream), "copy sketch"));
+  return finish_from_y2(ctx, p, dtype, Yw, m, R, K, J, T, info);
+}
+
+// ---------------------------------------------------------------------------
 // Gaussian ID, the comparison method (Sec. 1.2.1; Sec. 1.2.2 Eq. G-matrix):
 // the sketch is a Gaussian matrix applied to A itself (matrix) or the
 // Khatri-Rao structured Gaussian sketch of M (CP tensor); the QR stage and the
@@ -803,6 +1016,8 @@ static int check_gaussian_id(idl_ctx* ctx, const idl_params* p, int dtype, int64
   if (p->learned && (dtype != IDL_F32 || p->m2 > 128 || K > 128))
     return fail(ctx, IDL_ELIMIT, "the column proposal needs FP32 data, m <= 128 and K <= 128");
   if (R > 0x7fffffffLL) return fail(ctx, IDL_ELIMIT, "R must fit in int32");
+  if (!(p->srrqr_f == 0.f || p->srrqr_f > 1.f)) return fail(ctx, IDL_EINVAL, "srrqr_f must be 0 or > 1");
+  if (p->srrqr_f > 0.f && p->learned) return fail(ctx, IDL_EINVAL, "srrqr_f and the column proposal exclude each other");
   return IDL_OK;
 }
 
@@ -818,7 +1033,7 @@ extern "C" int id_matrix_gaussian(idl_ctx* ctx, const void* A, int64_t I, int64_
   TRY(rc);
   double* Om = (double*)ws_get(ctx, kWsOmega, sizeof(double) * (size_t)(L * I));
   if (!Om) return IDL_ENOMEM;
-  void* Y2 = ws_get(ctx, kWsY2, (size_t)es * (size_t)(R * L) * (p->residual == 2 ? 2 : 1));
+  void* Y2 = ws_get(ctx, kWsY2, (size_t)es * (size_t)(R * L) * (keeps_sketch(p) ? 2 : 1));
   if (!Y2) return IDL_ENOMEM;
   STAGE(kStDraw, cuda_check(ctx, launch_draw_gaussian_tag(ctx->stream, p->seed, kTagGaussId, L, I, Om), "draw"));
   STAGE(kStSketch, launch_gaussian(ctx, Om, L, I, Ad, R, lda, dtype, p->precision, Y2, L));
@@ -843,7 +1058,7 @@ extern "C" int id_cp_tensor_gaussian(idl_ctx* ctx, int N, const int64_t* dims, i
   TRY(rc);
   double* Om = (double*)ws_get(ctx, kWsOmega, sizeof(double) * (size_t)(L * tot));
   float* G = (float*)ws_get(ctx, kWsModeSketch, sizeof(float) * (size_t)(N * L * R));
-  float* Y2 = (float*)ws_get(ctx, kWsY2, sizeof(float) * (size_t)(R * L) * (p->residual == 2 ? 2 : 1));
+  float* Y2 = (float*)ws_get(ctx, kWsY2, sizeof(float) * (size_t)(R * L) * (keeps_sketch(p) ? 2 : 1));
   if (!Om || !G || !Y2) return IDL_ENOMEM;
   int64_t off = 0;
   for (int n = 0; n < N; ++n) {     // Omega^(n)T (L x I_n, row-major), then G_n = Omega^(n)T A^(n)

@@ -545,6 +545,7 @@ static int plan_batch(idl_ctx* ctx, const idl_batch_item* items, int n, const Tu
     if (pr.learned < IDL_PROPOSAL_NONE || pr.learned > IDL_PROPOSAL_NORM)
       return fail(ctx, IDL_EINVAL, "batch: unknown proposal mode");
     if (pr.cand_factor < 0 || pr.cand_factor > 8) return fail(ctx, IDL_EINVAL, "batch: cand_factor must be in 0..8");
+    if (pr.srrqr_f != 0.f) return fail(ctx, IDL_EINVAL, "batch: srrqr_f is for the single-item pipelines");
     if (pr.learned == IDL_PROPOSAL_MLP && !ctx->mlp_ready)
       return fail(ctx, IDL_EINVAL, "batch: no MLP weights (idl_mlp_init / idl_load_weights)");
     if (prec == IDL_PREC_FP64) return fail(ctx, IDL_EINVAL, "batch: FP32 data only (precision FP32, BF16X3 or BF16)");

@@ -34,13 +34,13 @@ __global__ void __launch_bounds__(256) cs_dense_kernel(const T* __restrict__ A, 
                                                        const int8_t* __restrict__ s,
                                                        const int32_t* __restrict__ ptr,
                                                        const int32_t* __restrict__ rows, T* __restrict__ Y,
-                                                       int64_t ldy, int ntiles) {
-  cs_dense_block<T, VEC>(A, lda, R, s, ptr, rows, Y, ldy, blockIdx.x / ntiles, blockIdx.x % ntiles);
+                                                       int64_t ldy, int ntiles, bool accum) {
+  cs_dense_block<T, VEC>(A, lda, R, s, ptr, rows, Y, ldy, blockIdx.x / ntiles, blockIdx.x % ntiles, accum);
 }
 
 template <typename T>
 static int dense_impl(idl_ctx* ctx, const T* A, int64_t R, int64_t lda, const int8_t* s, const int32_t* ptr,
-                      const int32_t* rows, int64_t L, T* Y, int64_t ldy) {
+                      const int32_t* rows, int64_t L, T* Y, int64_t ldy, bool accum) {
   constexpr int W = 16 / sizeof(T);
   const int threads = 256;
   const int64_t tile_cols = (int64_t)threads * W;
@@ -50,19 +50,21 @@ static int dense_impl(idl_ctx* ctx, const T* A, int64_t R, int64_t lda, const in
   const bool vec = ((uintptr_t)A % 16 == 0) && ((uintptr_t)Y % 16 == 0) && ((lda * sizeof(T)) % 16 == 0) &&
                    ((ldy * sizeof(T)) % 16 == 0);
   if (vec)
-    cs_dense_kernel<T, true><<<(unsigned)blocks, threads, 0, ctx->stream>>>(A, lda, R, s, ptr, rows, Y, ldy, ntiles), idl::count_launch();
+    cs_dense_kernel<T, true><<<(unsigned)blocks, threads, 0, ctx->stream>>>(A, lda, R, s, ptr, rows, Y, ldy, ntiles, accum),
+        idl::count_launch();
   else
-    cs_dense_kernel<T, false><<<(unsigned)blocks, threads, 0, ctx->stream>>>(A, lda, R, s, ptr, rows, Y, ldy, ntiles), idl::count_launch();
+    cs_dense_kernel<T, false><<<(unsigned)blocks, threads, 0, ctx->stream>>>(A, lda, R, s, ptr, rows, Y, ldy, ntiles, accum),
+        idl::count_launch();
   return cuda_check(ctx, cudaGetLastError(), "countsketch dense");
 }
 
 int launch_countsketch_dense(idl_ctx* ctx, const void* A, int64_t I, int64_t R, int64_t lda, int dtype,
                              const int8_t* s, const int32_t* bucket_ptr, const int32_t* row_list, int64_t L,
-                             void* Y1, int64_t ldy) {
+                             void* Y1, int64_t ldy, bool accum) {
   (void)I;
   if (dtype == IDL_F32)
-    return dense_impl<float>(ctx, (const float*)A, R, lda, s, bucket_ptr, row_list, L, (float*)Y1, ldy);
-  return dense_impl<double>(ctx, (const double*)A, R, lda, s, bucket_ptr, row_list, L, (double*)Y1, ldy);
+    return dense_impl<float>(ctx, (const float*)A, R, lda, s, bucket_ptr, row_list, L, (float*)Y1, ldy, accum);
+  return dense_impl<double>(ctx, (const double*)A, R, lda, s, bucket_ptr, row_list, L, (double*)Y1, ldy, accum);
 }
 
 // ----------------------------------------------------------------------------
@@ -178,7 +180,7 @@ __global__ void __launch_bounds__(NT, 1024 / NT) cs_csr_kernel(const int64_t* __
                                                                 const int8_t* __restrict__ s,
                                                                 const int32_t* __restrict__ ptr,
                                                                 const int32_t* __restrict__ rows, T* __restrict__ Y,
-                                                                int64_t ldy, int* status, int vec_ok) {
+                                                                int64_t ldy, int* status, int vec_ok, int accum) {
   using Sm = CsrSmem<NT>;
   constexpr int U = sizeof(T) == 4 ? kQuadUnroll : 2;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -269,14 +271,15 @@ __global__ void __launch_bounds__(NT, 1024 / NT) cs_csr_kernel(const int64_t* __
     __syncthreads();
   }
   if (SMEM) {
-    for (int64_t c = tid; c < R; c += NT) yrow[c] = acc[c];
+    if (accum) for (int64_t c = tid; c < R; c += NT) yrow[c] += acc[c];
+    else for (int64_t c = tid; c < R; c += NT) yrow[c] = acc[c];
   }
 }
 
 template <typename T, int NT>
 static int csr_launch(idl_ctx* ctx, const int64_t* rowptr, const int32_t* colidx, const T* vals, int64_t R,
                       int64_t nnz, const int8_t* s, const int32_t* ptr, const int32_t* rows, int64_t L, T* Y,
-                      int64_t ldy, int vec_ok) {
+                      int64_t ldy, int vec_ok, int accum) {
   const size_t head = (size_t)round_up((int64_t)sizeof(CsrSmem<NT>), 16);
   const size_t want = head + sizeof(T) * (size_t)R;
   if (want <= (size_t)ctx->smem_optin) {
@@ -284,37 +287,38 @@ static int csr_launch(idl_ctx* ctx, const int64_t* rowptr, const int32_t* colidx
     cudaError_t e = ensure_smem(ctx, (const void*)k, want);
     if (e != cudaSuccess) return cuda_check(ctx, e, "csr smem attribute");
     k<<<(unsigned)L, NT, want, ctx->stream>>>(rowptr, colidx, vals, R, nnz, s, ptr, rows, Y, ldy, ctx->d_status,
-                                              vec_ok), idl::count_launch();
+                                              vec_ok, accum), idl::count_launch();
   } else {
-    cudaError_t e = cudaMemset2DAsync(Y, ldy * sizeof(T), 0, R * sizeof(T), L, ctx->stream);
+    cudaError_t e = accum ? cudaSuccess : cudaMemset2DAsync(Y, ldy * sizeof(T), 0, R * sizeof(T), L, ctx->stream);
     if (e != cudaSuccess) return cuda_check(ctx, e, "csr zero");
     auto k = cs_csr_kernel<T, false, NT>;
     e = ensure_smem(ctx, (const void*)k, head);
     if (e != cudaSuccess) return cuda_check(ctx, e, "csr smem attribute");
     k<<<(unsigned)L, NT, head, ctx->stream>>>(rowptr, colidx, vals, R, nnz, s, ptr, rows, Y, ldy, ctx->d_status,
-                                              vec_ok), idl::count_launch();
+                                              vec_ok, accum), idl::count_launch();
   }
   return cuda_check(ctx, cudaGetLastError(), "countsketch csr");
 }
 
 template <typename T>
 static int csr_impl(idl_ctx* ctx, const int64_t* rowptr, const int32_t* colidx, const T* vals, int64_t R, int64_t nnz,
-                    const int8_t* s, const int32_t* ptr, const int32_t* rows, int64_t L, T* Y, int64_t ldy) {
+                    const int8_t* s, const int32_t* ptr, const int32_t* rows, int64_t L, T* Y, int64_t ldy, int accum) {
   if (L > 0x7fffffffLL) return fail(ctx, IDL_ELIMIT, "countsketch csr: too many buckets");
   // a batch's quads are counted in int: bound the row width
   if (R > 4000000) return fail(ctx, IDL_ELIMIT, "countsketch csr: R > 4e6");
   const int vec_ok = ((uintptr_t)colidx % 16 == 0) && ((uintptr_t)vals % 16 == 0);
-  return csr_launch<T, 512>(ctx, rowptr, colidx, vals, R, nnz, s, ptr, rows, L, Y, ldy, vec_ok);
+  return csr_launch<T, 512>(ctx, rowptr, colidx, vals, R, nnz, s, ptr, rows, L, Y, ldy, vec_ok, accum);
 }
 
 int launch_countsketch_csr(idl_ctx* ctx, const int64_t* rowptr, const int32_t* colidx, const void* vals, int64_t I,
                            int64_t R, int64_t nnz, int dtype, const int8_t* s, const int32_t* bucket_ptr,
-                           const int32_t* row_list, int64_t L, void* Y1, int64_t ldy) {
+                           const int32_t* row_list, int64_t L, void* Y1, int64_t ldy, bool accum) {
   (void)I;
   if (dtype == IDL_F32)
-    return csr_impl<float>(ctx, rowptr, colidx, (const float*)vals, R, nnz, s, bucket_ptr, row_list, L, (float*)Y1, ldy);
+    return csr_impl<float>(ctx, rowptr, colidx, (const float*)vals, R, nnz, s, bucket_ptr, row_list, L, (float*)Y1, ldy,
+                           accum);
   return csr_impl<double>(ctx, rowptr, colidx, (const double*)vals, R, nnz, s, bucket_ptr, row_list, L, (double*)Y1,
-                          ldy);
+                          ldy, accum);
 }
 
 }  // namespace idl

@@ -19,6 +19,7 @@
 #include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cfloat>
 
 #include "common.cuh"
@@ -217,10 +218,11 @@ template <typename T, int V, int TPC>
 __global__ void __launch_bounds__(RegCpqr<T, V, TPC>::kMaxThreads, 1)
 cpqr_reg_kernel(const T* __restrict__ Yin, T* __restrict__ Yout, int m, int R, int ld, int K, int nc,
                 int32_t* __restrict__ J, double* __restrict__ rnorm, double* __restrict__ diag, int* status,
-                const int* gate, const int32_t* __restrict__ colmap, T* __restrict__ Vout, T* __restrict__ Bout) {
+                const int* gate, const int32_t* __restrict__ colmap, T* __restrict__ Vout, T* __restrict__ Bout,
+                const int32_t* force) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   if (proposal_certified(gate, diag)) return;
-  cpqr_reg_body<T, V, TPC>(Yin, Yout, m, R, ld, K, nc, J, rnorm, diag, status, smem_raw, colmap, Vout, Bout);
+  cpqr_reg_body<T, V, TPC>(Yin, Yout, m, R, ld, K, nc, J, rnorm, diag, status, smem_raw, colmap, Vout, Bout, force);
 }
 
 template <typename T, int V, int TPC>
@@ -253,7 +255,8 @@ static int try_reg_cpqr(idl_ctx* ctx, const T* Yin, T* Yout, int64_t m, int64_t 
   if (e != cudaSuccess || nclusters < 1) { (void)cudaGetLastError(); return IDL_OK; }
   if (!x.colmap) ctx->last_cluster = CS;
   e = cudaLaunchKernelEx(&cfg, kern, Yin, Yout, (int)m, (int)R, (int)ld, (int)K, nc, J, rnorm,
-                         x.diag ? x.diag : ctx->d_diag, ctx->d_status, x.gate, x.colmap, (T*)x.Vout, (T*)x.Bout);
+                         x.diag ? x.diag : ctx->d_diag, ctx->d_status, x.gate, x.colmap, (T*)x.Vout, (T*)x.Bout,
+                         x.force);
   idl::count_launch();
   *launched = true;
   return cuda_check(ctx, e, "cpqr reg launch");
@@ -303,6 +306,7 @@ static int cpqr_impl(idl_ctx* ctx, const T* Yin, T* Yout, int64_t m, int64_t R, 
     if (rc != IDL_OK || launched) return rc;
   }
   if (x.colmap) return fail(ctx, IDL_ELIMIT, "cpqr: candidate set exceeds one CTA");
+  if (x.force) return fail(ctx, IDL_ELIMIT, "cpqr: given pivots need the register-resident QR");
   auto kern = cpqr_cluster_kernel<T>;
   cudaError_t e = ensure_cluster_nonportable(ctx, (const void*)kern);
   if (e != cudaSuccess) return cuda_check(ctx, e, "cpqr cluster attribute");
@@ -538,6 +542,135 @@ int launch_transpose_to_colmajor(idl_ctx* ctx, const void* Y1, int64_t m, int64_
   else
     transpose_kernel<double><<<grid, block, 0, ctx->stream>>>((const double*)Y1, m, R, ldy1, (double*)Y2, ldy2), idl::count_launch();
   return cuda_check(ctx, cudaGetLastError(), "transpose");
+}
+
+}  // namespace idl
+
+// ----------------------------------------------------------------------------
+// Strong rank-revealing refinement (Fact 1; Gu & Eisenstat 1996): with the
+// factored sketch of the current selection J (R11 on J's columns, R12 and R22 on
+// the rest) and W = T = R11^{-1} R12 from the T solve, rho_ij = W_ij^2 +
+// gamma_j^2 ||e_i^T R11^{-1}||^2 (gamma_j = ||R22 e_j||); while the largest rho
+// exceeds f^2, J[i] is exchanged for rest[j] (ties: smallest i, then j) and the
+// sketch is factored again with J as given pivots.  Each exchange multiplies
+// |det R11| by sqrt(rho) > f.
+// ----------------------------------------------------------------------------
+namespace idl {
+
+constexpr int kSrrqrMaxSwaps = 256;
+
+// winv2[i] = ||e_i^T R11^{-1}||^2: row i of the inverse by forward substitution
+// (r R11 = e_i), one warp per row, FP64
+template <typename T>
+__global__ void srrqr_rinv_rows_kernel(const T* __restrict__ Yf, int64_t ld, int K, const int32_t* __restrict__ J,
+                                       double* __restrict__ rowbuf, double* __restrict__ winv2) {
+  const int i = blockIdx.x, lane = threadIdx.x;
+  double* r = rowbuf + (int64_t)i * K;                   // r[l], l >= i
+  double s2 = 0.0;
+  for (int j = i; j < K; ++j) {
+    const T* col = Yf + (int64_t)J[j] * ld;              // column j of R11: rows 0..j
+    double acc = 0.0;
+    for (int l = i + lane; l < j; l += 32) acc += r[l] * (double)col[l];
+    acc = warp_sum(acc);
+    const double v = ((j == i ? 1.0 : 0.0) - acc) / (double)col[j];
+    if (lane == 0) r[j] = v;
+    __syncwarp();
+    s2 += v * v;
+  }
+  if (lane == 0) winv2[i] = s2;
+}
+
+// gam2[c] = ||R22 e_c||^2 over rows K..m-1 of the non-skeleton column rest[c]
+template <typename T>
+__global__ void srrqr_gamma_kernel(const T* __restrict__ Yf, int64_t ld, int m, int K,
+                                   const int32_t* __restrict__ rest, int nr, double* __restrict__ gam2) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= nr) return;
+  const T* col = Yf + (int64_t)rest[c] * ld;
+  double s = 0.0;
+  for (int l = K; l < m; ++l) { const double y = (double)col[l]; s += y * y; }
+  gam2[c] = s;
+}
+
+// key = max over (i, c) of (FP32 bits of rho_ic) << 32 | (~(i nr + c)): the largest rho,
+// then the smallest flat index
+__global__ void srrqr_argmax_kernel(const double* __restrict__ T, const double* __restrict__ winv2,
+                                    const double* __restrict__ gam2, int K, int nr,
+                                    unsigned long long* __restrict__ key) {
+  unsigned long long best = 0ull;
+  const int64_t tot = (int64_t)K * nr;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e / nr), c = (int)(e - (int64_t)i * nr);
+    const double w = T[e];
+    const float rho = (float)(w * w + gam2[c] * winv2[i]);
+    const unsigned long long k = ((unsigned long long)__float_as_uint(rho) << 32) | (0xffffffffu - (unsigned)e);
+    best = k > best ? k : best;
+  }
+  for (int o = 16; o; o >>= 1) {
+    const unsigned long long v = __shfl_xor_sync(0xffffffffu, best, o);
+    best = v > best ? v : best;
+  }
+  if ((threadIdx.x & 31) == 0 && best) atomicMax(key, best);
+}
+
+// the exchange (flag = 1) or the end (flag = 0)
+__global__ void srrqr_swap_kernel(const unsigned long long* __restrict__ key, const int32_t* __restrict__ rest, int nr,
+                                  float f2, int32_t* __restrict__ J, int* __restrict__ flag) {
+  const unsigned long long k = *key;
+  const float rho = __uint_as_float((unsigned)(k >> 32));
+  const unsigned e = 0xffffffffu - (unsigned)(k & 0xffffffffull);
+  if (!(rho > f2) || k == 0ull) { *flag = 0; return; }
+  const unsigned i = e / (unsigned)nr, c = e - i * (unsigned)nr;
+  J[i] = rest[c];
+  *flag = 1;
+}
+
+int launch_srrqr(idl_ctx* ctx, const void* Yorig, void* Yf, int64_t m, int64_t R, int64_t ld, int dtype, int64_t K,
+                 int32_t* J, double* T, int32_t* rest, float f) {
+  const int nr = (int)(R - K);
+  unsigned char* ws = (unsigned char*)ws_get(ctx, kWsSrrqr,
+                                             sizeof(double) * (size_t)(K * K + K + nr) + 2 * sizeof(unsigned long long));
+  if (!ws) return IDL_ENOMEM;
+  double* rowbuf = (double*)ws;
+  double* winv2 = rowbuf + K * K;
+  double* gam2 = winv2 + K;
+  unsigned long long* key = (unsigned long long*)(gam2 + nr);
+  int* flag = (int*)(key + 1);
+  QrExtra x;
+  x.force = J;
+  for (int s = 0; s <= kSrrqrMaxSwaps; ++s) {
+    int rc = launch_t_solve(ctx, Yf, m, R, ld, dtype, K, J, T, rest);
+    if (rc != IDL_OK) return rc;
+    if (s == kSrrqrMaxSwaps) break;
+    cudaStream_t st = ctx->stream;
+    if (dtype == IDL_F32) {
+      srrqr_rinv_rows_kernel<float><<<(unsigned)K, 32, 0, st>>>((const float*)Yf, ld, (int)K, J, rowbuf, winv2);
+      srrqr_gamma_kernel<float><<<(unsigned)cdiv(nr, 256), 256, 0, st>>>((const float*)Yf, ld, (int)m, (int)K, rest,
+                                                                         nr, gam2);
+    } else {
+      srrqr_rinv_rows_kernel<double><<<(unsigned)K, 32, 0, st>>>((const double*)Yf, ld, (int)K, J, rowbuf, winv2);
+      srrqr_gamma_kernel<double><<<(unsigned)cdiv(nr, 256), 256, 0, st>>>((const double*)Yf, ld, (int)m, (int)K, rest,
+                                                                          nr, gam2);
+    }
+    idl::count_launch();
+    idl::count_launch();
+    cudaMemsetAsync(key, 0, sizeof(unsigned long long), st);
+    srrqr_argmax_kernel<<<(unsigned)std::min<int64_t>(cdiv((int64_t)K * nr, 256), 4LL * ctx->num_sms), 256, 0, st>>>(
+        T, winv2, gam2, (int)K, nr, key), idl::count_launch();
+    srrqr_swap_kernel<<<1, 1, 0, st>>>(key, rest, nr, f * f, J, flag), idl::count_launch();
+    int hflag = 0;
+    cudaError_t e = cudaMemcpyAsync(&hflag, flag, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_check(ctx, e, "srrqr");
+    if (!hflag) return IDL_OK;
+    // factor the sketch again with the exchanged selection as given pivots
+    e = cudaMemsetAsync(ctx->d_diag, 0, sizeof(double) * 16, st);
+    if (e != cudaSuccess) return cuda_check(ctx, e, "srrqr");
+    rc = dtype == IDL_F32 ? cpqr_impl<float>(ctx, (const float*)Yorig, (float*)Yf, m, R, ld, K, J, nullptr, x)
+                          : cpqr_impl<double>(ctx, (const double*)Yorig, (double*)Yf, m, R, ld, K, J, nullptr, x);
+    if (rc != IDL_OK) return rc;
+  }
+  return IDL_OK;
 }
 
 }  // namespace idl

@@ -154,6 +154,8 @@ template <typename T, int V, int TPC> struct RegCpqr {
 // (ascending, so ties still go to the smaller original index); J reports
 // original indices.  Vout/Bout (optional): reflector t (zero above row t) at
 // Vout + t*m and its beta at Bout[t] -- the learned proposal's candidate QR.
+// force (optional, no colmap): the pivot of step t is column force[t] (the QR
+// of a given column selection in a given order; force may alias J).
 // Per pivot step: every warp publishes its best column, one block barrier;
 // every warp reduces those (the same winner everywhere), the winner's group
 // stages its column and thread 0 publishes the CTA's candidate; one cluster
@@ -165,7 +167,7 @@ __device__ __forceinline__ void cpqr_reg_body(const T* __restrict__ Yin, T* __re
                                               int K, int nc, int32_t* __restrict__ J, double* __restrict__ rnorm,
                                               double* __restrict__ diag, int* status, unsigned char* smem_raw,
                                               const int32_t* __restrict__ colmap = nullptr, T* __restrict__ Vout = nullptr,
-                                              T* __restrict__ Bout = nullptr) {
+                                              T* __restrict__ Bout = nullptr, const int32_t* __restrict__ force = nullptr) {
   constexpr int tpc = TPC;
   cg::cluster_group cluster = cg::this_cluster();
   const int CS = (int)cluster.num_blocks();
@@ -229,8 +231,8 @@ __device__ __forceinline__ void cpqr_reg_body(const T* __restrict__ Yin, T* __re
   int tp = -1;
   T alpha_p = T(0);
   for (int t = 0; t < K; ++t) {
-    // A. warp candidates
-    KT bv = PK::of(nrm2, gl == 0 && alive);
+    // A. warp candidates (with forced pivots, step t's only candidate is column force[t])
+    KT bv = PK::of(nrm2, gl == 0 && alive && (!force || col == force[t]));
     int bi = bv >= KT(0) ? col : -1;
 #pragma unroll
     for (int o = 16; o; o >>= 1) {

@@ -36,6 +36,22 @@ cudaError_t launch_draw_countsketch(cudaStream_t st, uint64_t seed, int64_t I, i
   return cudaGetLastError();
 }
 
+// rows i0 .. i0 + n - 1 of an I-row CountSketch (the draws of the whole matrix)
+__global__ void draw_countsketch_range_kernel(CsDrawArgs a, int64_t I, int64_t i0, int64_t n, int64_t L, int modified,
+                                              int32_t* __restrict__ h, int8_t* __restrict__ s, int* status) {
+  const int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (r < n) cs_draw_value(i0 + r, a, I, L, modified, h + r, s + r, status);
+}
+
+cudaError_t launch_draw_countsketch_range(cudaStream_t st, uint64_t seed, int64_t I, int64_t i0, int64_t n, int64_t L,
+                                          int modified, int32_t* h, int8_t* s, int* status) {
+  if (n <= 0) return cudaSuccess;
+  const CsDrawArgs a = make_cs_draw_args(seed, I);
+  draw_countsketch_range_kernel<<<(unsigned)cdiv(n, 256), 256, 0, st>>>(a, I, i0, n, L, modified, h, s, status),
+      idl::count_launch();
+  return cudaGetLastError();
+}
+
 // One thread per Box-Muller pair (flat indices 2p, 2p+1): one log and one
 // sincospi per pair.
 __global__ void draw_gaussian_kernel(uint64_t base, int64_t n, double* __restrict__ Om) {

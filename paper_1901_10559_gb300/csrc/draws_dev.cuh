@@ -46,9 +46,9 @@ inline CsDrawArgs make_cs_draw_args(uint64_t seed, int64_t I) {
   return a;
 }
 
-// h[i], s[i] of a CountSketch (plain or modified, Remark 2)
-__device__ __forceinline__ void cs_draw_elem(int64_t i, const CsDrawArgs& a, int64_t I, int64_t L, int modified,
-                                             int32_t* __restrict__ h, int8_t* __restrict__ s, int* status) {
+// h(i), s(i) of a CountSketch (plain or modified, Remark 2) for row i of I
+__device__ __forceinline__ void cs_draw_value(int64_t i, const CsDrawArgs& a, int64_t I, int64_t L, int modified,
+                                              int32_t* hv_out, int8_t* s_out, int* status) {
   const uint32_t x = bounded(stream_at(a.bucket_base, (uint64_t)i), (uint64_t)L);
   uint32_t hv = x;
   if (modified) {
@@ -60,8 +60,14 @@ __device__ __forceinline__ void cs_draw_elem(int64_t i, const CsDrawArgs& a, int
     if (y >= (uint64_t)I) { set_status(status, IDL_ETIMEOUT); y = 0; }
     if (y < (uint64_t)L) hv = (uint32_t)y;
   }
-  h[i] = (int32_t)hv;
-  s[i] = (stream_at(a.sign_base, (uint64_t)i) >> 63) ? (int8_t)-1 : (int8_t)1;
+  *hv_out = (int32_t)hv;
+  *s_out = (stream_at(a.sign_base, (uint64_t)i) >> 63) ? (int8_t)-1 : (int8_t)1;
+}
+
+// h[i], s[i] of a CountSketch (plain or modified, Remark 2)
+__device__ __forceinline__ void cs_draw_elem(int64_t i, const CsDrawArgs& a, int64_t I, int64_t L, int modified,
+                                             int32_t* __restrict__ h, int8_t* __restrict__ s, int* status) {
+  cs_draw_value(i, a, I, L, modified, h + i, s + i, status);
 }
 
 // Box-Muller pair p (flat indices 2p, 2p+1) of Omega; cos(2 pi u2) as cospi(2 u2)

@@ -186,3 +186,33 @@ int launch_kr_product(idl_ctx* ctx, const float* G, int N, int64_t L, int64_t R,
 }
 
 }  // namespace idl
+
+// ---------------------------------------------------------------------------
+// Y2 (+)= Yp for column-major m x R sketches (ld of Y2: ldy2; Yp packed, ld m):
+// the partial sketches of row blocks add up to the sketch of all rows.
+// ---------------------------------------------------------------------------
+namespace idl {
+
+template <typename T>
+__global__ void add_sketch_kernel(const T* __restrict__ Yp, int64_t m, int64_t R, T* __restrict__ Y2, int64_t ldy2,
+                                  int accumulate) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= m * R) return;
+  const int64_t r = e / m, j = e - r * m;
+  T* y = Y2 + r * ldy2 + j;
+  *y = accumulate ? *y + Yp[e] : Yp[e];
+}
+
+int launch_add_sketch(idl_ctx* ctx, const void* Yp, int64_t m, int64_t R, int dtype, void* Y2, int64_t ldy2,
+                      int accumulate) {
+  const unsigned blocks = (unsigned)cdiv(m * R, 256);
+  if (m * R <= 0) return IDL_OK;
+  if (dtype == IDL_F32)
+    add_sketch_kernel<float><<<blocks, 256, 0, ctx->stream>>>((const float*)Yp, m, R, (float*)Y2, ldy2, accumulate);
+  else
+    add_sketch_kernel<double><<<blocks, 256, 0, ctx->stream>>>((const double*)Yp, m, R, (double*)Y2, ldy2, accumulate);
+  count_launch();
+  return cuda_check(ctx, cudaGetLastError(), "add sketch");
+}
+
+}  // namespace idl

@@ -27,6 +27,8 @@ struct idl_ctx {
   cudaStream_t stream = nullptr;
   cudaStream_t side = nullptr;     // the Gaussian draw runs here, overlapping the sketch (created on first use)
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  cudaStream_t copy = nullptr;     // host-array copies of the chunked CSR pipeline (created on first use)
+  std::vector<cudaEvent_t> cevs;   // their events
   int graphs = 0;                  // idl_set_graphs: replay repeated pipeline calls as CUDA graphs
   uint64_t ws_gen = 1;             // bumped whenever a workspace slot is (re)allocated
   std::vector<PipeGraph> pgraphs;  // most recent last
@@ -68,7 +70,7 @@ enum Slot {
   kWsH = 0, kWsS, kWsOmega, kWsBucketPtr, kWsRowList, kWsCursor, kWsBig, kWsY1, kWsPart,
   kWsY2, kWsOmegaConv, kWsRest, kWsA, kWsRowptr, kWsColidx, kWsVals, kWsJ, kWsT,
   kWsModeH, kWsModeS, kWsLam, kWsLamHat, kWsCpqrSync, kWsRinv, kWsBatch, kWsBatchTab, kWsYf, kWsProp,
-  kWsPropGram, kWsPropTrain, kWsPropCopy, kWsBatchIn, kWsFactors, kWsModeSketch, kWsErrVec, kWsCount
+  kWsPropGram, kWsPropTrain, kWsPropCopy, kWsBatchIn, kWsFactors, kWsModeSketch, kWsErrVec, kWsSrrqr, kWsCount
 };
 
 // Returns a device buffer of at least `bytes` for the slot (grown on demand), or
@@ -94,6 +96,9 @@ cudaError_t cluster_occupancy(idl_ctx* ctx, const void* kern, const cudaLaunchCo
 // draws.cu
 cudaError_t launch_draw_countsketch(cudaStream_t st, uint64_t seed, int64_t I, int64_t L, int modified,
                                     int32_t* h, int8_t* s, int* status);
+// h, s of rows i0 .. i0 + n - 1 of an I-row CountSketch, written to h[0 .. n), s[0 .. n)
+cudaError_t launch_draw_countsketch_range(cudaStream_t st, uint64_t seed, int64_t I, int64_t i0, int64_t n, int64_t L,
+                                          int modified, int32_t* h, int8_t* s, int* status);
 cudaError_t launch_draw_gaussian(cudaStream_t st, uint64_t seed, int64_t m2, int64_t m1, double* Omega);
 // the same Box-Muller pairs in FP32 arithmetic (FP32 pipelines and batches), stored as doubles
 cudaError_t launch_draw_gaussian_f32(cudaStream_t st, uint64_t seed, int64_t m2, int64_t m1, double* Omega);
@@ -106,13 +111,14 @@ int launch_bucket_offsets(idl_ctx* ctx, const int32_t* h, int64_t I, int64_t L, 
                           int32_t* row_list);
 
 // countsketch.cu
+// accum: add this block of rows' sketch to Y1 instead of writing it
 int launch_countsketch_dense(idl_ctx* ctx, const void* A, int64_t I, int64_t R, int64_t lda, int dtype,
                              const int8_t* s, const int32_t* bucket_ptr, const int32_t* row_list,
-                             int64_t L, void* Y1, int64_t ldy);
+                             int64_t L, void* Y1, int64_t ldy, bool accum = false);
 int launch_countsketch_csr(idl_ctx* ctx, const int64_t* rowptr, const int32_t* colidx, const void* vals,
                            int64_t I, int64_t R, int64_t nnz, int dtype, const int8_t* s,
                            const int32_t* bucket_ptr, const int32_t* row_list, int64_t L, void* Y1,
-                           int64_t ldy);
+                           int64_t ldy, bool accum = false);
 
 // gaussian.cu
 int launch_gaussian(idl_ctx* ctx, const double* Omega, int64_t m2, int64_t m1, const void* Y1, int64_t R,
@@ -121,6 +127,10 @@ int launch_gaussian(idl_ctx* ctx, const double* Omega, int64_t m2, int64_t m1, c
 // Y[l, r] = lambda_r prod_n G_n[l, r]: G holds N blocks of L x R column-major FP32 (ld L,
 // block stride L R), Y column-major (ld L)
 int launch_kr_product(idl_ctx* ctx, const float* G, int N, int64_t L, int64_t R, const double* lambda, float* Y);
+
+// Y2 (column-major, ld ldy2) = or += Yp (column-major m x R, ld m)
+int launch_add_sketch(idl_ctx* ctx, const void* Yp, int64_t m, int64_t R, int dtype, void* Y2, int64_t ldy2,
+                      int accumulate);
 
 int launch_gaussian_reduce(idl_ctx* ctx, const float* part, int splits, int64_t R, int MP, int64_t m2, float* Y2,
                            int64_t ldy2);
@@ -140,11 +150,18 @@ struct QrExtra {
   float* Bout = nullptr;
   double* diag = nullptr;
   int max_cs = 16;
+  const int32_t* force = nullptr;   // pivots given in order (register QR only; may alias J)
 };
 int launch_cpqr_ex(idl_ctx* ctx, const float* Yin, float* Yout, int64_t m, int64_t R, int64_t ld, int64_t K,
                    int32_t* J, double* rnorm, const QrExtra& x);
 int launch_cpqr(idl_ctx* ctx, void* Y2, int64_t m, int64_t R, int64_t ld, int dtype, int64_t K, int32_t* J,
                 double* rnorm);
+// Gu-Eisenstat swaps after the pivoted QR (Fact 1; params.srrqr_f = f > 1): Yorig the
+// sketch, Yf its factored form and J the pivots of the pivoted QR on entry; J, Yf, T and
+// rest are those of the strong rank-revealing selection on exit.  Synchronises once
+// per exchange considered.
+int launch_srrqr(idl_ctx* ctx, const void* Yorig, void* Yf, int64_t m, int64_t R, int64_t ld, int dtype, int64_t K,
+                 int32_t* J, double* T, int32_t* rest, float f);
 int launch_t_solve(idl_ctx* ctx, const void* Y2, int64_t m, int64_t R, int64_t ld, int dtype, int64_t K,
                    const int32_t* J, double* T, int32_t* rest);
 int launch_residual(idl_ctx* ctx, const void* Y2orig, const void* Y2fact, int64_t m, int64_t R, int64_t ld,

@@ -19,12 +19,13 @@ __device__ __forceinline__ void vadd(double2& a, const double2& v, bool neg) {
 }
 
 // One block of the dense CountSketch: bucket b, column tile `tile` (blockDim.x
-// vectors of 16 bytes): Y[b, cols] = sum over the bucket's rows i of s[i] A[i, cols].
+// vectors of 16 bytes): Y[b, cols] = sum over the bucket's rows i of s[i] A[i, cols]
+// (accum: added to Y's current values -- the sketch of a further block of rows).
 template <typename T, bool VEC>
 __device__ __forceinline__ void cs_dense_block(const T* __restrict__ A, int64_t lda, int64_t R,
                                                const int8_t* __restrict__ s, const int32_t* __restrict__ ptr,
                                                const int32_t* __restrict__ rows, T* __restrict__ Y, int64_t ldy,
-                                               int64_t b, int tile) {
+                                               int64_t b, int tile, bool accum = false) {
   using V = typename Vec4<T>::type;
   constexpr int W = 16 / sizeof(T);  // elements per vector
   const int64_t c0 = ((int64_t)tile * blockDim.x + threadIdx.x) * W;
@@ -50,6 +51,7 @@ __device__ __forceinline__ void cs_dense_block(const T* __restrict__ A, int64_t 
       const int r = rows[j];
       vadd(acc, ldcs_vec<T>(A + (int64_t)r * lda + c0), s[r] < 0);
     }
+    if (accum) vadd(acc, *(const V*)yrow, false);
     *(V*)yrow = acc;
   } else {
     const int w = (int)((R - c0) < W ? (R - c0) : W);
@@ -66,7 +68,7 @@ __device__ __forceinline__ void cs_dense_block(const T* __restrict__ A, int64_t 
     }
 #pragma unroll
     for (int q = 0; q < W; ++q)
-      if (q < w) yrow[q] = acc[q];
+      if (q < w) yrow[q] = accum ? yrow[q] + acc[q] : acc[q];
   }
 }
 

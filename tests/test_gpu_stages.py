@@ -12,7 +12,7 @@ from oracle import draws as odr
 from oracle import gaussian as ogs
 from oracle import tensorsketch as ots
 from synth import cp_factors, random_csr
-from tests.helpers import colmajor_to_matrix, dev, host, pivots_well_separated, rel_fro
+from tests.helpers import assert_sum_within_bound, colmajor_to_matrix, dev, host, pivots_well_separated, rel_fro
 
 pytestmark = pytest.mark.gpu
 
@@ -119,6 +119,10 @@ def test_countsketch_dense_parity(ctx, dtype, I, R, L, lda_pad):
     tol = FP32_TOL if dtype == "f32" else FP64_TOL
     assert rel_fro(got, want) <= tol
     assert np.all(np.isnan(host(Y)[:, R:]))                 # padding untouched
+    # entry by entry: within the rounding of a sum of the bucket's terms
+    absum = ocs.countsketch_dense(np.abs(Afull[:, :R]), hw, np.ones_like(sw), L)
+    u = 2.0 ** -24 if dtype == "f32" else 2.0 ** -52
+    assert_sum_within_bound(got, want, absum, int(np.bincount(hw, minlength=L).max()), u)
 
 
 # ------------------------------------------------------------------ a4 CSR CountSketch
@@ -142,6 +146,9 @@ def test_countsketch_csr_parity(ctx, dtype, I, R, L, density):
     want = ocs.countsketch_csr(rowptr, cols, vals, R, hw, sw, L)
     tol = FP32_TOL if dtype == "f32" else FP64_TOL
     assert rel_fro(host(Y), want) <= tol
+    absum = ocs.countsketch_csr(rowptr, cols, np.abs(vals), R, hw, np.ones_like(sw), L)
+    nterms = int(np.max(np.bincount(hw, weights=np.diff(rowptr), minlength=L)))   # nonzeros per bucket
+    assert_sum_within_bound(host(Y), want, absum, nterms, 2.0 ** -24 if dtype == "f32" else 2.0 ** -52)
     assert ctx.sync() == idl.IDL_OK
 
 
@@ -177,6 +184,9 @@ def test_countsketch_csr_long_rows(ctx, dtype, offset, R, L):
     want = ocs.countsketch_csr(rowptr, cols, vals, R, hw, sw, L)
     tol = FP32_TOL if dtype == "f32" else FP64_TOL
     assert rel_fro(host(Y), want) <= tol
+    absum = ocs.countsketch_csr(rowptr, cols, np.abs(vals), R, hw, np.ones_like(sw), L)
+    nterms = int(np.max(np.bincount(hw, weights=np.diff(rowptr), minlength=L)))
+    assert_sum_within_bound(host(Y), want, absum, nterms, 2.0 ** -24 if dtype == "f32" else 2.0 ** -52)
     assert ctx.sync() == idl.IDL_OK
 
 
