@@ -15,6 +15,11 @@ formed here in float64):
   BF16X3 : fl32(Omega)                times Y1      (same definition; the device
                                                      forms it from bf16 splits)
   BF16   : bf16(fl32(Omega))          times bf16(fl32(Y1))
+
+FP8 (e4m3) operands are not a mode of the library; ``round_e4m3`` and
+``fp8_operand`` state what such a mode would multiply (per-tensor scaling to the
+format's largest finite value, 448), so that its error can be measured against
+the FP64 oracle.
 """
 from __future__ import annotations
 
@@ -49,3 +54,25 @@ def gaussian_stage(Omega64: np.ndarray, Y1: np.ndarray, precision: int = FP64) -
     if precision == BF16:
         Y = round_bf16(Y.astype(np.float32)).astype(np.float64)
     return Om @ Y
+
+
+def round_e4m3(x) -> np.ndarray:
+    """Round to the nearest FP8 e4m3 value (1 sign, 4 exponent bits with bias 7, 3
+    mantissa bits; subnormals down to 2^-9; largest finite 448), ties to even,
+    saturating at 448; returned as float64."""
+    x = np.asarray(x, dtype=np.float64)
+    a = np.abs(x)
+    e = np.clip(np.floor(np.log2(np.maximum(a, 2.0 ** -9))), -6, 8)
+    q = 2.0 ** (e - 3)                       # spacing of the binade (subnormal spacing 2^-9)
+    r = np.minimum(np.round(a / q) * q, 448.0)
+    return np.sign(x) * r
+
+
+def fp8_operand(X) -> np.ndarray:
+    """X scaled so that its largest magnitude is 448, rounded to e4m3, scaled back."""
+    X = np.asarray(X, dtype=np.float64)
+    m = np.abs(X).max()
+    if m == 0:
+        return X.copy()
+    s = 448.0 / m
+    return round_e4m3(X * s) / s
