@@ -9,7 +9,8 @@
 // 8192 = 16 * 16 * 32 (index digits n = 512 n1 + 32 n2 + n'', frequency
 // f = k1 + 16 k2 + 256 k''):
 //   pass 1: thread t (= n' = 32 n2 + n'') takes the 16 values x[512 n1 + t],
-//           a 16-point DFT over n1, the twiddles exp(-2 pi i t k1 / 8192), and
+//           a 16-point DFT over n1, the twiddles exp(-2 pi i t k1 / 8192) (formed
+//           from the table's powers k1 = 1, 2, 4, 8 by products), and
 //           writes them back to the same 16 places (segment k1);
 //   pass 2: warp w (segment k1 = w), lane n'' takes x[512 w + 32 n2 + n''],
 //           a 16-point DFT over n2, the twiddles exp(-2 pi i n'' k2 / 512),
@@ -36,7 +37,7 @@
 //
 // Shared memory: the vector (one pad entry per 32, so every pass is free of
 // bank conflicts beyond the two wavefronts of a 64-bit warp access), the
-// pass-1 twiddles (15 x 512) and the pass-2 twiddles (15 x 32), built once per
+// pass-1 twiddles (4 x 512) and the pass-2 twiddles (4 x 32), built once per
 // context in FP64 (GB300's FP64 pipes are narrow: a per-block build cost more
 // than the transforms) and copied in by every block.
 #pragma once
@@ -52,8 +53,8 @@ namespace ts8 {
 constexpr int kL = 8192;
 constexpr int kT = 512;                 // threads per block
 constexpr int kZ = kL + kL / 32;        // padded vector
-constexpr int kTw1 = 15 * kT;
-constexpr int kTw2 = 15 * 32;
+constexpr int kTw1 = 4 * kT;               // w^1, w^2, w^4, w^8 of w = exp(-2 pi i t / 8192), per thread t
+constexpr int kTw2 = 4 * 32;               // the same of exp(-2 pi i l / 512), per lane l
 constexpr int kSeg = 528;               // padded segment of 512 values
 constexpr int kMaxPre = 2;              // factor entries per thread held in registers (I_n <= 1024)
 constexpr size_t kSmemBytes = sizeof(float2) * (size_t)(kZ + kTw1 + kTw2 + 2);
@@ -137,13 +138,28 @@ __device__ __forceinline__ void rot_odd_inv(float2* v, bool odd, std::integer_se
   ((v[M] = odd ? rot32<M, true>(v[M]) : v[M]), ...);
 }
 
+// The pass twiddles w^1 .. w^15 from the table's w, w^2, w^4, w^8 (w^3 = w^2 w, w^5 = w^4 w,
+// ..., w^15 = w^8 w^7: at most three products of rounded factors), multiplied into
+// v[1..15] (conjugated for the inverse passes).  Four shared-memory loads instead of
+// fifteen: the transform is bound by shared-memory bandwidth, not by the FMA pipe.
+template <bool CONJ>
+__device__ __forceinline__ void apply_twiddles(float2* v, const float2* tab, int stride, int idx) {
+  const float2 w1 = tab[idx], w2 = tab[stride + idx], w4 = tab[2 * stride + idx], w8 = tab[3 * stride + idx];
+  auto app = [&](int q, float2 w) { v[q] = CONJ ? cmulc(v[q], w) : cmul(v[q], w); };
+  const float2 w3 = cmul(w2, w1);
+  const float2 w5 = cmul(w4, w1), w6 = cmul(w4, w2), w7 = cmul(w4, w3);
+  app(1, w1); app(2, w2); app(3, w3); app(4, w4); app(5, w5); app(6, w6); app(7, w7); app(8, w8);
+  app(9, cmul(w8, w1)); app(10, cmul(w8, w2)); app(11, cmul(w8, w3)); app(12, cmul(w8, w4));
+  app(13, cmul(w8, w5)); app(14, cmul(w8, w6)); app(15, cmul(w8, w7));
+}
+
 // Entry e of the twiddle table of passes 1 and 2 (kTw1 + kTw2 entries, built once
-// per context in FP64 and rounded): e < kTw1: exp(-2 pi i t k1 / 8192) at
-// [(k1 - 1) 512 + t]; then exp(-2 pi i l k2 / 512) at [kTw1 + (k2 - 1) 32 + l].
+// per context in FP64 and rounded): e < kTw1: exp(-2 pi i t 2^j / 8192) at
+// [j 512 + t], j = 0..3; then exp(-2 pi i l 2^j / 512) at [kTw1 + j 32 + l].
 __device__ __forceinline__ float2 table_entry(int e) {
   int num, den;
-  if (e < kTw1) { const int k1 = e / kT + 1, t = e % kT; num = t * k1; den = kL; }
-  else { const int q = e - kTw1, k2 = q / 32 + 1, l = q % 32; num = l * k2; den = 512; }
+  if (e < kTw1) { const int j = e / kT, t = e % kT; num = t << j; den = kL; }
+  else { const int q = e - kTw1, j = q / 32, l = q % 32; num = l << j; den = 512; }
   double sv, cv;
   sincospi(-2.0 * (double)(num % den) / (double)den, &sv, &cv);
   return make_float2((float)cv, (float)sv);
@@ -205,8 +221,7 @@ __device__ __forceinline__ void fwd_pass1(float2* z, const float2* tw1) {
 #pragma unroll
   for (int q = 0; q < 16; ++q) v[q] = z[q * kSeg + base];
   dft16<false>(v);
-#pragma unroll
-  for (int q = 1; q < 16; ++q) v[q] = cmul(v[q], tw1[(q - 1) * kT + t]);
+  apply_twiddles<false>(v, tw1, kT, t);
 #pragma unroll
   for (int q = 0; q < 16; ++q) z[q * kSeg + base] = v[q];
 }
@@ -219,8 +234,7 @@ __device__ __forceinline__ void fwd_pass23(float2* z, const float2* tw2) {
 #pragma unroll
     for (int q = 0; q < 16; ++q) v[q] = z[b2 + q * 33];
     dft16<false>(v);
-#pragma unroll
-    for (int q = 1; q < 16; ++q) v[q] = cmul(v[q], tw2[(q - 1) * 32 + lane]);
+    apply_twiddles<false>(v, tw2, 32, lane);
 #pragma unroll
     for (int q = 0; q < 16; ++q) z[b2 + q * 33] = v[q];
   }
@@ -312,9 +326,9 @@ __device__ __forceinline__ void inv_pass32(float2* z, const float2* tw2) {
   {
     const int b2 = w * kSeg + lane;
     float2 v[16];
-    v[0] = z[b2];
 #pragma unroll
-    for (int q = 1; q < 16; ++q) v[q] = cmulc(z[b2 + q * 33], tw2[(q - 1) * 32 + lane]);
+    for (int q = 0; q < 16; ++q) v[q] = z[b2 + q * 33];
+    apply_twiddles<true>(v, tw2, 32, lane);
     dft16<true>(v);
 #pragma unroll
     for (int q = 0; q < 16; ++q) z[b2 + q * 33] = v[q];
@@ -324,13 +338,12 @@ __device__ __forceinline__ void inv_pass32(float2* z, const float2* tw2) {
 // inverse pass 1^H: natural-order results x[512 q + t] in v; clears the thread's places
 __device__ __forceinline__ void inv_pass1(float2* z, const float2* tw1, float2* v) {
   const int t = threadIdx.x, base = t + (t >> 5);
-  v[0] = z[base];
-  z[base] = make_float2(0.f, 0.f);
 #pragma unroll
-  for (int q = 1; q < 16; ++q) {
-    v[q] = cmulc(z[q * kSeg + base], tw1[(q - 1) * kT + t]);
+  for (int q = 0; q < 16; ++q) {
+    v[q] = z[q * kSeg + base];
     z[q * kSeg + base] = make_float2(0.f, 0.f);
   }
+  apply_twiddles<true>(v, tw1, kT, t);
   dft16<true>(v);
 }
 
