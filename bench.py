@@ -259,6 +259,12 @@ def make_batch(seed, rank=0, n_dense=256, n_cp=64):
     return dense, cps
 
 
+def precision_code(idl, name):
+    """IDL_PREC_* of a precision mode's name."""
+    return {"FP64": idl.PREC_FP64, "FP32": idl.PREC_FP32, "BF16X3": idl.PREC_BF16X3, "BF16": idl.PREC_BF16,
+            "TF32X3": idl.PREC_TF32X3}[name]
+
+
 def batch_items(idl, dense, cps, prec, learned=0):
     import torch
     items, outs = [], []
@@ -298,8 +304,7 @@ def run_ours(args, ws, rank, local):
     # repeated pipeline calls with the same arguments replay as CUDA graphs (the warm-up
     # steps run the eager call and the capture; the batch call has its own graph)
     idl.idl_set_graphs(ctx, True)
-    prec = {"FP64": idl.PREC_FP64, "FP32": idl.PREC_FP32, "BF16X3": idl.PREC_BF16X3, "BF16": idl.PREC_BF16}[
-        w["precision"]]
+    prec = precision_code(idl, w["precision"])
     seed = rank_seed(w, rank)                         # independent draws per rank
     p = idl.make_params(w["m1"], w["m2"], seed=seed, modified=(name != "cp"), precision=prec, residual=1)
     K = max(1, w["k"])
@@ -626,7 +631,7 @@ def run_batched(args, ws, rank, local):
     inp = make_inputs("batched", rank)
     dense, cps = inp["dense"], inp["cps"]
     ctx = idl.Context(local)
-    prec = idl.PREC_BF16X3
+    prec = precision_code(idl, w["precision"])
     items, bouts = batch_items(idl, dense, cps, prec)
     arr = idl.batch_array(items)
     n_items = len(items)
@@ -729,13 +734,13 @@ def run_batched(args, ws, rank, local):
         facs = [f.cpu().numpy().T.astype(np.float64) for f in pr["facs"]]
         errs.append(oer.tensor_id_error(facs, pr["lam"].cpu().numpy(), o[0].cpu().numpy(), o[2].cpu().numpy()))
 
-    vs_gauss = compare_gaussian_id(idl, ctx, dense, cps)
+    vs_gauss = compare_gaussian_id(idl, ctx, dense, cps, prec)
 
     out = {
         "metric": METRIC, "value": round(value, 3), "unit": "solves/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 4), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": w["desc"], "precision": "BF16X3 Gaussian stage, FP32 sketches, FP64 T",
+        "config": {"workload": w["desc"], "precision": f"{w['precision']} Gaussian stage, FP32 sketches, FP64 T",
                    "items_per_step": n_items,
                    "l2": "no flush: inputs larger than L2 (16 GB of dense matrices, 1 GB of CP factors per step)",
                    "parallelism": f"replicas x{ws}" if ws > 1 else "1 GPU",
@@ -762,7 +767,7 @@ def run_batched(args, ws, rank, local):
     return out
 
 
-def compare_gaussian_id(idl, ctx, dense, cps, reps=5):
+def compare_gaussian_id(idl, ctx, dense, cps, prec, reps=5):
     """The paper's comparison on GB300: the CountSketch / TensorSketch pipelines against
     Gaussian ID (Sec. 1.2.1; Khatri-Rao Gaussian sketch of Eq. G-matrix for CP tensors)
     on the same items, one call at a time, CUDA-event timed; both sketch to the
@@ -790,8 +795,8 @@ def compare_gaussian_id(idl, ctx, dense, cps, reps=5):
         K, R = pr["K"], pr["A"].shape[1]
         J = torch.empty(K, dtype=torch.int32, device="cuda")
         T = torch.empty(K * (R - K), dtype=torch.float64, device="cuda")
-        pc = idl.make_params(pr["m1"], pr["m2"], seed=pr["seed"], modified=True, precision=idl.PREC_BF16X3)
-        pg = idl.make_params(0, pr["m2"], seed=pr["seed"], modified=False, precision=idl.PREC_BF16X3)
+        pc = idl.make_params(pr["m1"], pr["m2"], seed=pr["seed"], modified=True, precision=prec)
+        pg = idl.make_params(0, pr["m2"], seed=pr["seed"], modified=False, precision=prec)
         t_cs += timed(lambda: idl.id_matrix(ctx, pr["A"], K, pc, J, T))
         err["countsketch"].append(oer.matrix_id_error(pr["A"].cpu().numpy(), J=J.cpu().numpy(),
                                                       T=T.cpu().numpy().reshape(K, R - K), exact=False, iters=20))
@@ -809,8 +814,8 @@ def compare_gaussian_id(idl, ctx, dense, cps, reps=5):
         J = torch.empty(K, dtype=torch.int32, device="cuda")
         T = torch.empty(K * (R - K), dtype=torch.float64, device="cuda")
         lh = torch.empty(K, dtype=torch.float64, device="cuda")
-        pc = idl.make_params(pr["L"], pr["m2"], seed=pr["seed"], modified=False, precision=idl.PREC_BF16X3)
-        pg = idl.make_params(0, pr["m2"], seed=pr["seed"], modified=False, precision=idl.PREC_BF16X3)
+        pc = idl.make_params(pr["L"], pr["m2"], seed=pr["seed"], modified=False, precision=prec)
+        pg = idl.make_params(0, pr["m2"], seed=pr["seed"], modified=False, precision=prec)
         facs = [f.cpu().numpy().T.astype(np.float64) for f in pr["facs"]]
         lam = pr["lam"].cpu().numpy()
         t_cs += timed(lambda: idl.id_cp_tensor(ctx, pr["facs"], pr["lam"], K, pc, J, T, lh))
@@ -1040,6 +1045,8 @@ def main():
     ap.add_argument("--learned-steps", type=int, default=300)
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--precision", choices=["FP32", "BF16X3", "BF16", "TF32X3"], default=None,
+                    help="Gaussian-stage mode of an FP32 workload (default: the workload's own)")
     args = ap.parse_args()
     batched = args.workload == "batched"
     if args.steps is None:
@@ -1048,6 +1055,10 @@ def main():
         args.warmup = 3 if args.impl == "reference" else (5 if batched else 20)
     if batched:
         args.e2e_steps = min(args.e2e_steps, 5)
+    if args.precision is not None:
+        if WORKLOADS[args.workload]["precision"] == "FP64":
+            ap.error("the FP64 workload has FP64 data: no other Gaussian-stage mode")
+        WORKLOADS[args.workload]["precision"] = args.precision
     ws, rank, local = dist_env()
     if args.impl == "reference":
         out = run_reference_batched(args, ws, rank) if batched else run_reference(args, ws, rank)

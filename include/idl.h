@@ -54,6 +54,11 @@ extern "C" {
 #define IDL_PREC_FP32   1  /* FP32-accurate: 3-way bf16 split of both operands, 6 tcgen05 products */
 #define IDL_PREC_BF16X3 2  /* 2-way bf16 split, 3 tcgen05 products (hi*hi + hi*lo + lo*hi)         */
 #define IDL_PREC_BF16   3  /* bf16 operands, FP32 accumulation, 1 tcgen05 product                   */
+#define IDL_PREC_TF32X3 4  /* 2-way TF32 split of both operands (hi = top 11 significand bits, lo =
+                              the top 11 of the rest, both by truncation), 3 tcgen05 kind::tf32
+                              products (hi*hi + hi*lo + lo*hi): ~2^-21 relative per product.
+                              Column-major FP32 Y1 is copied into shared memory as it is and only
+                              the residual is formed (the fast mode of the column-major pipelines) */
 
 typedef struct idl_ctx idl_ctx;
 
@@ -229,7 +234,7 @@ int idl_gaussian_stage(idl_ctx* ctx, const double* Omega, int64_t m2, int64_t m1
                        void* Y2, int64_t ldy2);
 
 /* The same for FP32 Y1 stored column-major (column r at Y1 + r*ldy1, ldy1 >= m1),
- * on the tensor cores: precision IDL_PREC_FP32, IDL_PREC_BF16X3 or IDL_PREC_BF16. */
+ * on the tensor cores: precision IDL_PREC_FP32, IDL_PREC_BF16X3, IDL_PREC_BF16 or IDL_PREC_TF32X3. */
 int idl_gaussian_stage_colmajor(idl_ctx* ctx, const double* Omega, int64_t m2, int64_t m1,
                                 const float* Y1, int64_t R, int64_t ldy1, int precision,
                                 float* Y2, int64_t ldy2);
@@ -337,6 +342,20 @@ int idl_sketch_rows_csr(idl_ctx* ctx, const int64_t* rowptr, const int32_t* coli
 int idl_id_from_sketch(idl_ctx* ctx, const void* Y2, int64_t m, int64_t R, int64_t ldy2, int dtype, int64_t K,
                        const idl_params* p, int32_t* J, double* T, idl_info* info);
 
+/* Column blocks of a CP tensor.  Column r of the tensor's sketch depends only on
+ * lambda_r, column r of every factor and the modes' maps h_n, s_n (drawn from
+ * seed, n, I_n and L; Sec. 1.3, Eq. TA-formula), so a tensor whose R columns are
+ * split over GPUs is sketched block by block and the blocks, gathered side by
+ * side in column order, are the whole tensor's sketch (then idl_id_from_sketch
+ * and idl_lambda_hat with the whole lambda).
+ * idl_sketch_cp: Y2 = Omega Y1 (m x R column-major, device memory, ldy2 >= m;
+ *   m = params.m2 <= 256, or L = params.m1 when m2 = 0) for the R columns given:
+ *   factors, ldf, lambda as for id_cp_tensor (device or host arrays); params.m1
+ *   = L a power of two, precision FP32, BF16X3, BF16 or TF32X3; K, residual, learned
+ *   and srrqr_f are not used.  Returns without synchronising. */
+int idl_sketch_cp(idl_ctx* ctx, int N, const int64_t* dims, int64_t R, const void* const* factors,
+                  const int64_t* ldf, const double* lambda, const idl_params* p, float* Y2, int64_t ldy2);
+
 /* ---------------------------------------------------------------------------
  * Gaussian ID, the comparison method of the paper (Sec. 1.2.1 and Sec. 1.2.2).
  * The sketch size is L = params.m2 (K <= L <= 256; L <= 112 for FP64 data);
@@ -388,7 +407,7 @@ int idl_id_error_csr(idl_ctx* ctx, const int64_t* rowptr, const int32_t* colidx,
  * keep those choices in a text file.
  *   Items: IDL_ITEM_DENSE (Algorithm 2 on a dense FP32 matrix) or IDL_ITEM_CP
  *   (Algorithm 3 on a CP tensor), FP32 data, one precision mode per batch
- *   (IDL_PREC_FP32 / BF16X3 / BF16), Gaussian stage required with
+ *   (IDL_PREC_FP32 / BF16X3 / BF16 / TF32X3), Gaussian stage required with
  *   K <= m2 <= min(m1, 128), K <= 128.  CP factors are stored column by
  *   column (ldf = dims[n]).  Outputs as for the single-item calls.
  *   Either every array of the batch is device memory -- the call is then

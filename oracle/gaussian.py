@@ -15,6 +15,9 @@ formed here in float64):
   BF16X3 : fl32(Omega)                times Y1      (same definition; the device
                                                      forms it from bf16 splits)
   BF16   : bf16(fl32(Omega))          times bf16(fl32(Y1))
+  TF32X3 : fl32(Omega)                times Y1      (same definition; the device
+                                                     forms it from two-term TF32
+                                                     splits, three products)
 
 FP8 (e4m3) operands are not a mode of the library; ``round_e4m3`` and
 ``fp8_operand`` state what such a mode would multiply (per-tensor scaling to the
@@ -25,7 +28,7 @@ from __future__ import annotations
 
 import numpy as np
 
-FP64, FP32, BF16X3, BF16 = 0, 1, 2, 3
+FP64, FP32, BF16X3, BF16, TF32X3 = 0, 1, 2, 3, 4
 
 
 def round_bf16(x) -> np.ndarray:

@@ -25,7 +25,7 @@ HEADER = os.path.join(os.path.dirname(_HERE), "include", "idl.h")
 
 IDL_OK, IDL_EINVAL, IDL_ENOMEM, IDL_ECUDA, IDL_ERANK, IDL_ETIMEOUT, IDL_EDATA, IDL_ELIMIT = range(8)
 IDL_F32, IDL_F64 = 0, 1
-PREC_FP64, PREC_FP32, PREC_BF16X3, PREC_BF16 = 0, 1, 2, 3
+PREC_FP64, PREC_FP32, PREC_BF16X3, PREC_BF16, PREC_TF32X3 = 0, 1, 2, 3, 4
 STAGES = ("draws", "buckets", "sketch", "gaussian", "cpqr", "tsolve", "check", "copy")
 STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ERANK", 5: "ETIMEOUT", 6: "EDATA", 7: "ELIMIT"}
 
@@ -127,6 +127,7 @@ _SIGS = {
                              _i64, _int], _int),
     "idl_id_from_sketch": ([_vp, _vp, _i64, _i64, _i64, _int, _i64, ctypes.POINTER(Params), _vp, _vp,
                             ctypes.POINTER(Info)], _int),
+    "idl_sketch_cp": ([_vp, _int, _vp, _i64, _vp, _vp, _vp, ctypes.POINTER(Params), _vp, _i64], _int),
     "idl_batch_run": ([_vp, ctypes.POINTER(BatchItem), _int], _int),
     "idl_tune_save": ([_vp, ctypes.c_char_p], _int),
     "idl_tune_load": ([_vp, ctypes.c_char_p], _int),
@@ -432,6 +433,20 @@ def idl_id_from_sketch(ctx, Y2, m, R, K, params, J, T, info=None, ldy2=None):
     return ctx.check(lib().idl_id_from_sketch(ctx.ptr, _p(Y2), int(m), int(R), m if ldy2 is None else ldy2, _dt(Y2),
                                               int(K), ctypes.byref(params), _p(J), _p(T),
                                               ctypes.byref(info) if info is not None else None))
+
+
+def idl_sketch_cp(ctx, factors, lam, params, Y2, ldy2=None):
+    """Y2 = the m x R column-major sketch of the CP tensor's R columns given (factors:
+    (R, I_n) tensors, lam: R float64), without the QR stage."""
+    N = len(factors)
+    R = int(factors[0].shape[0])
+    dims = _arr(ctypes.c_int64, [int(f.shape[1]) for f in factors])
+    fp = _arr(_vp, [f.data_ptr() for f in factors])
+    lp = _arr(ctypes.c_int64, [int(f.stride(0)) for f in factors])
+    m = params.m2 if params.m2 > 0 else params.m1
+    return ctx.check(lib().idl_sketch_cp(ctx.ptr, N, ctypes.cast(dims, _vp), R, ctypes.cast(fp, _vp),
+                                         ctypes.cast(lp, _vp), _p(lam), ctypes.byref(params), _p(Y2),
+                                         m if ldy2 is None else ldy2))
 
 
 # ---------------------------------------------------------------- batches

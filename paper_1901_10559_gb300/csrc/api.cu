@@ -451,7 +451,7 @@ extern "C" int idl_gaussian_stage(idl_ctx* ctx, const double* Omega, int64_t m2,
                                   int64_t ldy1, int dtype, int precision, void* Y2, int64_t ldy2) {
   TRY(check_ctx(ctx));
   if ((dtype != IDL_F32 && dtype != IDL_F64) || m2 < 1 || m1 < 1 || R < 1 || ldy1 < R || ldy2 < m2 || !Omega ||
-      !Y1 || !Y2 || precision < 0 || precision > 3 || (dtype == IDL_F64 && precision != IDL_PREC_FP64))
+      !Y1 || !Y2 || precision < 0 || precision > IDL_PREC_TF32X3 || (dtype == IDL_F64 && precision != IDL_PREC_FP64))
     return fail(ctx, IDL_EINVAL, "gaussian_stage: bad arguments");
   return launch_gaussian(ctx, Omega, m2, m1, Y1, R, ldy1, dtype, precision, Y2, ldy2);
 }
@@ -460,7 +460,8 @@ extern "C" int idl_gaussian_stage_colmajor(idl_ctx* ctx, const double* Omega, in
                                            int64_t R, int64_t ldy1, int precision, float* Y2, int64_t ldy2) {
   TRY(check_ctx(ctx));
   if (m2 < 1 || m1 < 1 || R < 1 || ldy1 < m1 || ldy2 < m2 || !Omega || !Y1 || !Y2 ||
-      (precision != IDL_PREC_FP32 && precision != IDL_PREC_BF16X3 && precision != IDL_PREC_BF16))
+      (precision != IDL_PREC_FP32 && precision != IDL_PREC_BF16X3 && precision != IDL_PREC_BF16 &&
+       precision != IDL_PREC_TF32X3))
     return fail(ctx, IDL_EINVAL, "gaussian_stage_colmajor: bad arguments");
   return launch_gaussian_tc(ctx, Omega, m2, m1, Y1, R, ldy1, true, precision, Y2, ldy2);
 }
@@ -513,7 +514,7 @@ extern "C" int idl_lambda_hat(idl_ctx* ctx, const double* lambda, const int32_t*
 static int check_params(idl_ctx* ctx, const idl_params* p, int dtype, int64_t I, int64_t R, int64_t K, bool tensor) {
   if (!p) return fail(ctx, IDL_EINVAL, "null params");
   if (dtype != IDL_F32 && dtype != IDL_F64) return fail(ctx, IDL_EINVAL, "dtype must be IDL_F32 or IDL_F64");
-  if (p->precision < 0 || p->precision > 3) return fail(ctx, IDL_EINVAL, "unknown precision");
+  if (p->precision < 0 || p->precision > IDL_PREC_TF32X3) return fail(ctx, IDL_EINVAL, "unknown precision");
   if (dtype == IDL_F64 && p->precision != IDL_PREC_FP64)
     return fail(ctx, IDL_EINVAL, "FP64 data needs precision IDL_PREC_FP64");
   if (dtype == IDL_F32 && p->precision == IDL_PREC_FP64)
@@ -881,6 +882,67 @@ static int id_cp_tensor_impl(idl_ctx* ctx, int N, const int64_t* dims, int64_t R
 }
 
 // ---------------------------------------------------------------------------
+// The sketch of a CP tensor without the QR stage: Y2 = Omega Y1 (m x R, column-major)
+// with Y1 the TensorSketch of the columns lambda_r a_r^(1) o ... o a_r^(N) (Sec. 1.3,
+// Eq. TA-formula).  Column r of the sketch depends on column r of the factors and on
+// the maps of the modes only (drawn from seed, mode index, I_n and L), so a tensor
+// whose R columns are split over ranks is sketched block by block and the blocks
+// are gathered side by side: the column-sharded CP tensor ID.
+// ---------------------------------------------------------------------------
+extern "C" int idl_sketch_cp(idl_ctx* ctx, int N, const int64_t* dims, int64_t R, const void* const* factors,
+                             const int64_t* ldf, const double* lambda, const idl_params* p, float* Y2,
+                             int64_t ldy2) {
+  TRY(check_ctx(ctx));
+  if (!p || N < 1 || N > 8 || !dims || !factors || !ldf || !lambda || !Y2 || R < 1 || R > 0x7fffffffLL)
+    return fail(ctx, IDL_EINVAL, "sketch_cp: bad arguments");
+  if (p->precision < 0 || p->precision > IDL_PREC_TF32X3 || p->precision == IDL_PREC_FP64)
+    return fail(ctx, IDL_EINVAL, "sketch_cp: FP32 data needs precision FP32, BF16X3, BF16 or TF32X3");
+  if (p->m1 < 1 || p->m1 > 0x7fffffffLL || (p->m1 & (p->m1 - 1)))
+    return fail(ctx, IDL_EINVAL, "TensorSketch length must be a power of two");
+  if (p->m2 < 0 || p->m2 > p->m1 || p->m2 > 256) return fail(ctx, IDL_EINVAL, "need 0 <= m2 <= min(m1, 256)");
+  const int64_t L = p->m1, m = p->m2 > 0 ? p->m2 : L;
+  if (ldy2 < m) return fail(ctx, IDL_EINVAL, "sketch_cp: ldy2 < m");
+  if (!is_device_ptr(Y2)) return fail(ctx, IDL_EINVAL, "sketch_cp: Y2 must be device memory");
+  size_t host_bytes;
+  int64_t tot;
+  TRY(cp_factor_args(ctx, N, dims, R, factors, ldf, &host_bytes, &tot));
+  double* Om;
+  TRY(fork_omega(ctx, p, &Om));
+  const void* fdev[8];
+  TRY(stage_factors(ctx, N, dims, R, factors, ldf, host_bytes, fdev));
+  int rc;
+  const double* lam = (const double*)stage_in(ctx, lambda, sizeof(double) * (size_t)R, kWsLam, &rc);
+  TRY(rc);
+  WS(hbuf, int32_t, kWsModeH, tot);
+  WS(sbuf, int8_t, kWsModeS, tot);
+  const int32_t* hs[8];
+  const int8_t* ss[8];
+  int64_t off = 0;
+  for (int n = 0; n < N; ++n) {
+    STAGE(kStDraw, cuda_check(ctx, launch_draw_mode(ctx->stream, p->seed, n, dims[n], L, hbuf + off, sbuf + off),
+                              "draw mode"));
+    hs[n] = hbuf + off;
+    ss[n] = sbuf + off;
+    off += dims[n];
+  }
+  const bool cm = p->m2 > 0 && !ctx->gemm_simt;
+  const int64_t ldy1 = cm ? L : round_up(R, 32);
+  float* Y1 = (float*)ws_get(ctx, kWsY1, sizeof(float) * (size_t)(cm ? R * L : L * ldy1));
+  if (!Y1) return IDL_ENOMEM;
+  STAGE(kStSketch, launch_tensorsketch(ctx, N, dims, R, fdev, ldf, lam, hs, ss, L, Y1, ldy1, cm));
+  if (p->m2 > 0) {
+    TRY(cuda_check(ctx, cudaStreamWaitEvent(ctx->stream, ctx->ev_join, 0), "join wait"));
+    if (cm)
+      STAGE(kStGauss, launch_gaussian_tc(ctx, Om, p->m2, L, Y1, R, ldy1, true, p->precision, Y2, ldy2));
+    else
+      STAGE(kStGauss, launch_gaussian(ctx, Om, p->m2, L, Y1, R, ldy1, IDL_F32, p->precision, Y2, ldy2));
+  } else {
+    STAGE(kStGauss, launch_transpose_to_colmajor(ctx, Y1, m, R, ldy1, IDL_F32, Y2, ldy2));
+  }
+  return IDL_OK;
+}
+
+// ---------------------------------------------------------------------------
 // Row blocks (Sec. 1.3: S A = sum over row blocks of S[:, rows] A[rows, :]): the
 // sketch Omega S[:, i0 .. i0+n) A[i0 .. i0+n, :] of one block of an I-row matrix,
 // drawn with the whole matrix's maps, written or added into Y2; and the ID from a
@@ -891,7 +953,7 @@ static int check_rows(idl_ctx* ctx, const idl_params* p, int dtype, int64_t n, i
                       const void* Y2, int64_t ldy2) {
   if (!p) return fail(ctx, IDL_EINVAL, "null params");
   if (dtype != IDL_F32 && dtype != IDL_F64) return fail(ctx, IDL_EINVAL, "dtype must be IDL_F32 or IDL_F64");
-  if (p->precision < 0 || p->precision > 3 || (dtype == IDL_F64) != (p->precision == IDL_PREC_FP64))
+  if (p->precision < 0 || p->precision > IDL_PREC_TF32X3 || (dtype == IDL_F64) != (p->precision == IDL_PREC_FP64))
     return fail(ctx, IDL_EINVAL, "precision does not match the data type");
   if (p->m1 < 1 || p->m1 > 0x7fffffffLL || p->m2 < 0 || p->m2 > p->m1) return fail(ctx, IDL_EINVAL, "need 0 <= m2 <= m1");
   if (n < 1 || i0 < 0 || i0 + n > I || I > 0x7fffffffLL || R < 1 || R > 0x7fffffffLL || !Y2)
@@ -1004,7 +1066,7 @@ extern "C" int idl_id_from_sketch(idl_ctx* ctx, const void* Y2, int64_t m, int64
 static int check_gaussian_id(idl_ctx* ctx, const idl_params* p, int dtype, int64_t R, int64_t K) {
   if (!p) return fail(ctx, IDL_EINVAL, "null params");
   if (dtype != IDL_F32 && dtype != IDL_F64) return fail(ctx, IDL_EINVAL, "dtype must be IDL_F32 or IDL_F64");
-  if (p->precision < 0 || p->precision > 3) return fail(ctx, IDL_EINVAL, "unknown precision");
+  if (p->precision < 0 || p->precision > IDL_PREC_TF32X3) return fail(ctx, IDL_EINVAL, "unknown precision");
   if ((dtype == IDL_F64) != (p->precision == IDL_PREC_FP64))
     return fail(ctx, IDL_EINVAL, "FP64 data needs precision IDL_PREC_FP64 and FP32 data another mode");
   if (K < 1 || K >= R) return fail(ctx, IDL_EINVAL, "need 1 <= K < R");

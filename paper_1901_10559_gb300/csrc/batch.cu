@@ -37,6 +37,7 @@
 #include "cpqr_dev.cuh"
 #include "draws_dev.cuh"
 #include "gemm_dev.cuh"
+#include "gemm_tf32_dev.cuh"
 #include "internal.h"
 #include "proposal_dev.cuh"
 #include "sketch_dev.cuh"
@@ -47,6 +48,8 @@
 namespace idl {
 
 using namespace tc;
+
+constexpr int kNPTf32 = 4;      // BatchPlan::NP of the TF32X3 mode (two TF32 planes)
 
 // ---------------------------------------------------------------------------
 // device descriptor of one item
@@ -234,6 +237,29 @@ __global__ void __launch_bounds__(kTcThreads, 1) b_gemm_kernel(const BItem* __re
   else
     gauss_tc_block<NP, false>(it.Y1, it.ldy1, it.R, it.m1, it.Bpl, (int)it.NT, (int)it.NT, kb0, nk, mt, 0,
                               it.part + (int64_t)sp * it.R * it.NT, status, smem_raw);
+}
+
+__global__ void b_planes_tf32_kernel(const BItem* __restrict__ items, const int64_t* __restrict__ pre, int n) {
+  ITEM_OF_BLOCK(pre, n);
+  const int64_t e = local * blockDim.x + threadIdx.x;
+  if (e < it.nkb * it.NT * 8) omega_tf32_elem(e, it.Om, (int)it.m2, it.m1, (int)it.NT, (float*)it.Bpl);
+}
+
+__global__ void __launch_bounds__(kTcThreads, 1) b_gemm_tf32_kernel(const BItem* __restrict__ items,
+                                                                    const int64_t* __restrict__ pre, int n,
+                                                                    int* status, int S) {
+  extern __shared__ unsigned char smem_raw[];
+  ITEM_OF_BLOCK(pre, n);
+  const int64_t mt = local / it.splits;
+  const int sp = (int)(local % it.splits);
+  const int kb0 = sp * (int)it.kbpc;
+  const int nk = (int)std::min<int64_t>(it.nkb, kb0 + it.kbpc) - kb0;
+  if (it.kind == IDL_ITEM_CP)
+    gauss_tf32_block<true>(it.Y1, it.m1, it.R, it.m1, (const float*)it.Bpl, (int)it.NT, (int)it.NT, kb0, nk, mt, 0, S,
+                           it.part + (int64_t)sp * it.R * it.NT, status, smem_raw);
+  else
+    gauss_tf32_block<false>(it.Y1, it.ldy1, it.R, it.m1, (const float*)it.Bpl, (int)it.NT, (int)it.NT, kb0, nk, mt,
+                            0, S, it.part + (int64_t)sp * it.R * it.NT, status, smem_raw);
 }
 
 __global__ void b_reduce_kernel(const BItem* __restrict__ items, const int64_t* __restrict__ pre, int n) {
@@ -548,7 +574,7 @@ static int plan_batch(idl_ctx* ctx, const idl_batch_item* items, int n, const Tu
     if (pr.srrqr_f != 0.f) return fail(ctx, IDL_EINVAL, "batch: srrqr_f is for the single-item pipelines");
     if (pr.learned == IDL_PROPOSAL_MLP && !ctx->mlp_ready)
       return fail(ctx, IDL_EINVAL, "batch: no MLP weights (idl_mlp_init / idl_load_weights)");
-    if (prec == IDL_PREC_FP64) return fail(ctx, IDL_EINVAL, "batch: FP32 data only (precision FP32, BF16X3 or BF16)");
+    if (prec == IDL_PREC_FP64) return fail(ctx, IDL_EINVAL, "batch: FP32 data only (precision FP32, BF16X3, BF16 or TF32X3)");
     if (x.K < 1 || x.K >= x.R || pr.m2 < x.K || pr.m2 > pr.m1 || pr.m2 > 128 || x.K > 128 || !x.J || !x.T ||
         x.R > 0x7fffffffLL)
       return fail(ctx, IDL_EINVAL, "batch: need 1 <= K < R, K <= m2 <= min(m1, 128), K <= 128, outputs");
@@ -564,7 +590,9 @@ static int plan_batch(idl_ctx* ctx, const idl_batch_item* items, int n, const Tu
       return fail(ctx, IDL_EINVAL, "batch: item kind must be IDL_ITEM_DENSE or IDL_ITEM_CP");
     }
   }
-  P.NP = prec == IDL_PREC_BF16 ? 1 : (prec == IDL_PREC_BF16X3 ? 2 : 3);
+  // operand planes of the Gaussian stage: 1..3 bf16 planes, or kNPTf32 for the two TF32 planes
+  P.NP = prec == IDL_PREC_BF16 ? 1 : (prec == IDL_PREC_BF16X3 ? 2 : (prec == IDL_PREC_TF32X3 ? kNPTf32 : 3));
+  const bool tf32 = P.NP == kNPTf32;
   // ---- per-item sizes and workspace layout ----
   size_t off = 0;
   auto take = [&](size_t bytes) { const size_t o = off; off += (bytes + 255) & ~(size_t)255; return o; };
@@ -591,7 +619,7 @@ static int plan_batch(idl_ctx* ctx, const idl_batch_item* items, int n, const Tu
     b.m2 = x.params.m2;
     b.ldy1 = round_up(x.R, 32);
     b.modified = x.params.modified;
-    b.nkb = cdiv(b.m1, kBK);
+    b.nkb = cdiv(b.m1, tf32 ? kBKt : kBK);
     b.NT = round_up(b.m2, 16);
     b.mtiles = cdiv(b.R, kBM);
     int64_t splits = std::max<int64_t>(1, cdiv((int64_t)ctx->num_sms * per_sm_gemm * tn.split_mult, b.mtiles));
@@ -630,7 +658,7 @@ static int plan_batch(idl_ctx* ctx, const idl_batch_item* items, int n, const Tu
       P.maxL_cp = std::max<int>(P.maxL_cp, (int)b.m1);
     }
     o_Om[i] = take(sizeof(double) * (size_t)(b.m2 * b.m1));
-    o_Bpl[i] = take((size_t)b.nkb * P.NP * b.NT * kBK * 2);
+    o_Bpl[i] = take(tf32 ? (size_t)b.nkb * 2 * b.NT * 128 : (size_t)b.nkb * P.NP * b.NT * kBK * 2);
     o_Y1[i] = take(sizeof(float) * (size_t)(b.m1 * b.ldy1));
     o_part[i] = take(sizeof(float) * (size_t)(b.splits * b.R * b.NT));
     o_Y2[i] = take(sizeof(float) * (size_t)(b.R * b.m2));
@@ -775,6 +803,19 @@ static int run_gemm_stage(idl_ctx* ctx, const BatchPlan& P, const BItem* d_items
   return launch_check(ctx, "batch gemm");
 }
 
+static int run_gemm_stage_tf32(idl_ctx* ctx, const BatchPlan& P, const BItem* d_items, const int64_t* d_pre, int n,
+                               int& nlaunch) {
+  int S = 3;
+  while (S < kTf32MaxStages && tf32_smem_bytes(S + 1, P.maxNT) <= (size_t)ctx->smem_optin) ++S;
+  const size_t smem = tf32_smem_bytes(S, P.maxNT);
+  if (smem > (size_t)ctx->smem_optin) return fail(ctx, IDL_ELIMIT, "batch gemm: shared memory");
+  cudaError_t e = ensure_smem(ctx, (const void*)b_gemm_tf32_kernel, smem);
+  if (e != cudaSuccess) return cuda_check(ctx, e, "batch gemm attribute");
+  BLAUNCH(b_planes_tf32_kernel, kBPlanes, 256, 0);
+  BLAUNCH(b_gemm_tf32_kernel, kBGemm, kTcThreads, smem, ctx->d_status, S);
+  return launch_check(ctx, "batch gemm");
+}
+
 // Proposal stages: scores, selection, candidate QR, certificate (the gated
 // cluster QR follows in run_stages).
 static int run_proposal(idl_ctx* ctx, const BatchPlan& P, const BItem* d_items, const int64_t* d_pre,
@@ -875,7 +916,8 @@ static int run_stages(idl_ctx* ctx, const BatchPlan& P, const BItem* d_items, co
   }
   BTRY(launch_check(ctx, "batch sketch"));
   mark(3);
-  if (P.NP == 1) BTRY(run_gemm_stage<1>(ctx, P, d_items, d_pre, n, nlaunch));
+  if (P.NP == kNPTf32) BTRY(run_gemm_stage_tf32(ctx, P, d_items, d_pre, n, nlaunch));
+  else if (P.NP == 1) BTRY(run_gemm_stage<1>(ctx, P, d_items, d_pre, n, nlaunch));
   else if (P.NP == 2) BTRY(run_gemm_stage<2>(ctx, P, d_items, d_pre, n, nlaunch));
   else BTRY(run_gemm_stage<3>(ctx, P, d_items, d_pre, n, nlaunch));
   BLAUNCH(b_reduce_kernel, kBReduce, 256, 0);

@@ -33,6 +33,7 @@
 
 #include "common.cuh"
 #include "gemm_dev.cuh"
+#include "gemm_tf32_dev.cuh"
 #include "internal.h"
 
 namespace idl {
@@ -55,7 +56,77 @@ gauss_tc_kernel(const float* __restrict__ Y1, int64_t ldy1, int64_t R, int64_t m
                      part + (int64_t)blockIdx.y * R * NT, status, smem_raw);
 }
 
+__global__ void omega_tf32_kernel(const double* __restrict__ Om, int m2, int64_t m1, int NT, int nkb,
+                                  float* __restrict__ out) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;     // (kb, n, kc)
+  if (e < (int64_t)nkb * NT * 8) omega_tf32_elem(e, Om, m2, m1, NT, out);
+}
+
+template <bool CM>
+__global__ void __launch_bounds__(kTcThreads, 1)
+gauss_tf32_kernel(const float* __restrict__ Y1, int64_t ldy1, int64_t R, int64_t m1, const float* __restrict__ Bpl,
+                  int NT, int NTc, int kb_per_cta, int nkb, int S, float* __restrict__ part, int* status) {
+  extern __shared__ unsigned char smem_raw[];
+  const int kb0 = blockIdx.y * kb_per_cta;
+  const int nk = min(nkb, kb0 + kb_per_cta) - kb0;
+  gauss_tf32_block<CM>(Y1, ldy1, R, m1, Bpl, NT, NTc, kb0, nk, blockIdx.x, blockIdx.z, S,
+                       part + (int64_t)blockIdx.y * R * NT, status, smem_raw);
+}
+
 using namespace tc;
+
+// Split K over CTAs so that (waves of CTAs) x (K blocks per CTA) is smallest: a CTA's
+// time is proportional to its K blocks and a partly filled last wave costs a whole one;
+// each split adds a partial result to write and reduce (about half a K block).
+static void choose_splits(int64_t ctas_per_split, int nkb, int64_t slots, int* splits, int* kbpc) {
+  *splits = 1;
+  *kbpc = nkb;
+  double best = 1e300;
+  for (int sp = 1; sp <= std::min(nkb, 32); ++sp) {
+    const int kb = (int)cdiv(nkb, sp);
+    const int se = (int)cdiv(nkb, kb);
+    const double cost = (double)cdiv(ctas_per_split * se, slots) * kb + 0.5 * se;
+    if (cost < best - 1e-9) { best = cost; *splits = se; *kbpc = kb; }
+  }
+}
+
+// TF32X3: K blocks of 32, stages as many as fit (3..6) after the Omega^T ring
+static int tf32_impl(idl_ctx* ctx, const double* Omega, int64_t m2, int64_t m1, const float* Y1, int64_t R,
+                     int64_t ldy1, bool y1_cm, float* Y2, int64_t ldy2) {
+  const int nkb = (int)cdiv(m1, kBKt);
+  const int mtiles = (int)cdiv(R, kBM);
+  const int NT0 = (int)round_up(m2, 16);
+  int nz = 1, NTc = NT0;
+  while ((tf32_smem_bytes(3, NTc) > (size_t)ctx->smem_optin || 2 * NTc > 512) && NTc > 16) {
+    ++nz;
+    NTc = (int)round_up(cdiv(NT0, nz), 16);
+  }
+  int S = 3;
+  while (S < kTf32MaxStages && tf32_smem_bytes(S + 1, NTc) <= (size_t)ctx->smem_optin) ++S;
+  const size_t smem = tf32_smem_bytes(S, NTc);
+  if (smem > (size_t)ctx->smem_optin) return fail(ctx, IDL_ELIMIT, "gaussian tf32: shared memory");
+  const int NT = nz * NTc;
+  const int per_sm = std::max(1, (int)(ctx->smem_optin / smem));
+  int splits, kbpc;
+  choose_splits((int64_t)mtiles * nz, nkb, (int64_t)ctx->num_sms * per_sm, &splits, &kbpc);
+  float* Bpl = (float*)ws_get(ctx, kWsOmegaConv, (size_t)nkb * 2 * NT * 128);
+  float* part = (float*)ws_get(ctx, kWsPart, sizeof(float) * (size_t)splits * R * NT);
+  if (!Bpl || !part) return IDL_ENOMEM;
+  {
+    const int64_t n = (int64_t)nkb * NT * 8;
+    omega_tf32_kernel<<<(unsigned)cdiv(n, 256), 256, 0, ctx->stream>>>(Omega, (int)m2, m1, NT, nkb, Bpl),
+        count_launch();
+  }
+  auto k = y1_cm ? gauss_tf32_kernel<true> : gauss_tf32_kernel<false>;
+  cudaError_t e = ensure_smem(ctx, (const void*)k, smem);
+  if (e != cudaSuccess) return cuda_check(ctx, e, "gaussian tf32 attribute");
+  dim3 grid((unsigned)mtiles, (unsigned)splits, (unsigned)nz);
+  k<<<grid, kTcThreads, smem, ctx->stream>>>(Y1, ldy1, R, m1, Bpl, NT, NTc, kbpc, nkb, S, part, ctx->d_status),
+      count_launch();
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_check(ctx, e, "gaussian tf32");
+  return launch_gaussian_reduce(ctx, part, splits, R, NT, m2, Y2, ldy2);
+}
 
 template <int NP>
 static int tc_impl(idl_ctx* ctx, const double* Omega, int64_t m2, int64_t m1, const float* Y1, int64_t R, int64_t ldy1,
@@ -83,15 +154,8 @@ static int tc_impl(idl_ctx* ctx, const double* Omega, int64_t m2, int64_t m1, co
   // proportional to its K blocks, and a partly filled last wave costs a whole one;
   // each split adds a partial result to write and reduce (about half a K block)
   const int per_sm = std::max(1, (int)(ctx->smem_optin / smem));
-  const int64_t slots = (int64_t)ctx->num_sms * per_sm;
-  int splits = 1, kbpc = nkb;
-  double best = 1e300;
-  for (int sp = 1; sp <= std::min(nkb, 32); ++sp) {
-    const int kb = (int)cdiv(nkb, sp);
-    const int se = (int)cdiv(nkb, kb);
-    const double cost = (double)cdiv((int64_t)mtiles * nz * se, slots) * kb + 0.5 * se;
-    if (cost < best - 1e-9) { best = cost; splits = se; kbpc = kb; }
-  }
+  int splits, kbpc;
+  choose_splits((int64_t)mtiles * nz, nkb, (int64_t)ctx->num_sms * per_sm, &splits, &kbpc);
   __nv_bfloat16* Bpl = (__nv_bfloat16*)ws_get(ctx, kWsOmegaConv, (size_t)nkb * NP * b_plane_full);
   float* part = (float*)ws_get(ctx, kWsPart, sizeof(float) * (size_t)splits * R * NT);
   if (!Bpl || !part) return IDL_ENOMEM;
@@ -117,6 +181,7 @@ int launch_gaussian_tc(idl_ctx* ctx, const double* Omega, int64_t m2, int64_t m1
   switch (precision) {
     case IDL_PREC_BF16: return tc_impl<1>(ctx, Omega, m2, m1, Y1, R, ldy1, y1_cm, Y2, ldy2);
     case IDL_PREC_BF16X3: return tc_impl<2>(ctx, Omega, m2, m1, Y1, R, ldy1, y1_cm, Y2, ldy2);
+    case IDL_PREC_TF32X3: return tf32_impl(ctx, Omega, m2, m1, Y1, R, ldy1, y1_cm, Y2, ldy2);
     default: return tc_impl<3>(ctx, Omega, m2, m1, Y1, R, ldy1, y1_cm, Y2, ldy2);
   }
 }

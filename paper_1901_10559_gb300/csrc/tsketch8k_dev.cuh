@@ -143,8 +143,8 @@ __device__ __forceinline__ void rot_odd_inv(float2* v, bool odd, std::integer_se
 // v[1..15] (conjugated for the inverse passes).  Four shared-memory loads instead of
 // fifteen: the transform is bound by shared-memory bandwidth, not by the FMA pipe.
 template <bool CONJ>
-__device__ __forceinline__ void apply_twiddles(float2* v, const float2* tab, int stride, int idx) {
-  const float2 w1 = tab[idx], w2 = tab[stride + idx], w4 = tab[2 * stride + idx], w8 = tab[3 * stride + idx];
+__device__ __forceinline__ void apply_twiddles(float2* v, const float2* w) {
+  const float2 w1 = w[0], w2 = w[1], w4 = w[2], w8 = w[3];
   auto app = [&](int q, float2 w) { v[q] = CONJ ? cmulc(v[q], w) : cmul(v[q], w); };
   const float2 w3 = cmul(w2, w1);
   const float2 w5 = cmul(w4, w1), w6 = cmul(w4, w2), w7 = cmul(w4, w3);
@@ -215,13 +215,13 @@ __device__ __forceinline__ void scatter_mode(const TsArgs& a, int n, int64_t r0,
 }
 
 // forward passes; z holds the mode's vector, natural order in, digit-reversed out
-__device__ __forceinline__ void fwd_pass1(float2* z, const float2* tw1) {
+__device__ __forceinline__ void fwd_pass1(float2* z, const float2* tw1) {  // tw1: this thread's 4 powers
   const int t = threadIdx.x, base = t + (t >> 5);
   float2 v[16];
 #pragma unroll
   for (int q = 0; q < 16; ++q) v[q] = z[q * kSeg + base];
   dft16<false>(v);
-  apply_twiddles<false>(v, tw1, kT, t);
+  apply_twiddles<false>(v, tw1);
 #pragma unroll
   for (int q = 0; q < 16; ++q) z[q * kSeg + base] = v[q];
 }
@@ -234,7 +234,7 @@ __device__ __forceinline__ void fwd_pass23(float2* z, const float2* tw2) {
 #pragma unroll
     for (int q = 0; q < 16; ++q) v[q] = z[b2 + q * 33];
     dft16<false>(v);
-    apply_twiddles<false>(v, tw2, 32, lane);
+    apply_twiddles<false>(v, tw2);
 #pragma unroll
     for (int q = 0; q < 16; ++q) z[b2 + q * 33] = v[q];
   }
@@ -328,7 +328,7 @@ __device__ __forceinline__ void inv_pass32(float2* z, const float2* tw2) {
     float2 v[16];
 #pragma unroll
     for (int q = 0; q < 16; ++q) v[q] = z[b2 + q * 33];
-    apply_twiddles<true>(v, tw2, 32, lane);
+    apply_twiddles<true>(v, tw2);
     dft16<true>(v);
 #pragma unroll
     for (int q = 0; q < 16; ++q) z[b2 + q * 33] = v[q];
@@ -343,7 +343,7 @@ __device__ __forceinline__ void inv_pass1(float2* z, const float2* tw1, float2* 
     v[q] = z[q * kSeg + base];
     z[q * kSeg + base] = make_float2(0.f, 0.f);
   }
-  apply_twiddles<true>(v, tw1, kT, t);
+  apply_twiddles<true>(v, tw1);
   dft16<true>(v);
 }
 
@@ -354,6 +354,13 @@ __device__ __forceinline__ void pair_body(const TsArgs& a, int64_t R, int64_t r0
                                           float* __restrict__ Y, int64_t ldy, bool cm, Pre& pre, float2* z,
                                           const float2* tw1, const float2* tw2) {
   const bool two = r0 + 1 < R;
+  // this thread's twiddle powers, held in registers for the pair's 2N + 2 passes
+  float2 w1[4], w2[4];
+  {
+    const int t = threadIdx.x, lane = t & 31;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) { w1[j] = tw1[j * kT + t]; w2[j] = tw2[j * 32 + lane]; }
+  }
   float2 P0[8], P1[8];
 #pragma unroll
   for (int j = 0; j < 8; ++j) { P0[j] = make_float2(1.f, 0.f); P1[j] = make_float2(1.f, 0.f); }
@@ -363,19 +370,19 @@ __device__ __forceinline__ void pair_body(const TsArgs& a, int64_t R, int64_t r0
     scatter_mode(a, n, r0, two, pre, z);
     if (n + 1 < a.N) load_mode(a, n + 1, r0, two, pre);     // in flight during this mode's transform
     __syncthreads();
-    fwd_pass1(z, tw1);
+    fwd_pass1(z, w1);
     __syncthreads();
-    fwd_pass23(z, tw2);
+    fwd_pass23(z, w2);
     __syncthreads();
     hadamard(z, P0, P1, ext);
     __syncthreads();
   }
   build_w(z, P0, P1, ext);
   __syncthreads();
-  inv_pass32(z, tw2);
+  inv_pass32(z, w2);
   __syncthreads();
   float2 v[16];
-  inv_pass1(z, tw1, v);
+  inv_pass1(z, w1, v);
   const float s0 = (float)(lambda[r0] / (double)kL);
   const float s1 = two ? (float)(lambda[r0 + 1] / (double)kL) : 0.f;
   const int t = threadIdx.x;

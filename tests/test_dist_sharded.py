@@ -1,4 +1,5 @@
-"""Row-sharded matrix ID (paper_1901_10559_gb300.sharded) with two gloo ranks on CPU.
+"""Sharded IDs (paper_1901_10559_gb300.sharded) with two gloo ranks on CPU: a
+matrix split by rows (all-reduce) and a CP tensor split by columns (all-gather).
 
 Each rank holds a contiguous block of rows; its partial sketch is
 Omega S[:, B] A[B, :] with the maps of the whole matrix; one all-reduce sums the
@@ -114,3 +115,86 @@ def test_row_blocks_partition_and_csr_slices():
     assert rp[0] == 0 and rp.shape[0] == 21
     assert np.array_equal(ci, c.colidx[c.rowptr[10]:c.rowptr[30]])
     assert np.array_equal(rp, c.rowptr[10:31] - c.rowptr[10])
+
+
+DIMS, RC, KC, LC, M2C = (30, 40, 25), 301, 10, 256, 24
+
+
+def _cp_worker(rank, ws, port, q):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    sys.path.insert(0, ROOT)
+    import torch
+    import torch.distributed as dist
+
+    from oracle import cpqr as ocp
+    from oracle import draws as odr
+    from oracle import gaussian as ogs
+    from oracle import idmethods as oid
+    from oracle import tensorsketch as ots
+    from paper_1901_10559_gb300 import sharded
+    from synth import cp_factors
+
+    dist.init_process_group("gloo", rank=rank, world_size=ws)
+    try:
+        factors, lam = cp_factors(DIMS, RC, seed=4, dtype=np.float64)
+        c0, c1 = sharded.column_blocks(RC, ws)[rank]
+        mine = [torch.from_numpy(np.ascontiguousarray(F[:, c0:c1].T)) for F in factors]   # (columns, I_n)
+        hs, ss = odr.tensorsketch_maps(SEED, DIMS, LC)
+        Om = odr.gaussian_matrix(SEED, M2C, LC)
+
+        def sketch_cols(f_, lam_, params_, Y2_):
+            Fs = [t.numpy().T for t in f_]
+            Y = ots.tensorsketch(Fs, lam_, hs, ss, LC)
+            Y2_[:Y.shape[1] * M2C] = torch.from_numpy(np.ascontiguousarray((Om @ Y).T).ravel()).to(Y2_.dtype)
+
+        def id_from_sketch(Y2_, m_, R_, K_, params_, J_, T_):
+            Jw, Tw, _ = ocp.matrix_id(Y2_.double().numpy().reshape(R_, m_).T, K_)
+            J_[:] = Jw
+            T_[:] = Tw.ravel()
+
+        def lambda_hat(lam_, J_, T_, K_, R_, out_):
+            out_[:] = oid.lambda_hat(lam_, J_, T_.reshape(K_, R_ - K_))
+
+        params = type("P", (), {"m1": LC, "m2": M2C})()
+        J = np.empty(KC, np.int64)
+        T = np.empty(KC * (RC - KC))
+        lh = np.empty(KC)
+        Y2 = sharded.sharded_cp_id(mine, lam[c0:c1], lam, RC, KC, params, J, T, lh, sketch_cols=sketch_cols,
+                                   id_from_sketch=id_from_sketch, lambda_hat=lambda_hat)
+        q.put((rank, (c0, c1), Y2.double().numpy().copy(), J.copy(), T.copy(), lh.copy()))
+        dist.barrier()
+    finally:
+        dist.destroy_process_group()
+
+
+def test_two_ranks_gather_cp_column_blocks_to_the_whole_tensor_id():
+    """Column blocks of a CP tensor sketched apart and gathered give the whole
+    tensor's sketch (FP32 pieces: 2^-24 relative per entry), and Algorithm 3 on
+    it gives the oracle's J, T and lambda_hat for the whole tensor."""
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_cp_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    out = {}
+    for _ in range(2):
+        rank, *rest = q.get(timeout=120)
+        out[rank] = rest
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    sys.path.insert(0, ROOT)
+    from oracle import idmethods as oid
+    from synth import cp_factors
+    factors, lam = cp_factors(DIMS, RC, seed=4, dtype=np.float64)
+    Jw, Tw, lw, info = oid.id_cp_tensor(factors, lam, k=KC, L=LC, m2=M2C, seed=SEED)
+    want = info["Y2"]
+    assert out[0][0] == (0, RC // 2) and out[1][0] == (RC // 2, RC)
+    for rank in (0, 1):
+        _, Y2, J, T, lh = out[rank]
+        got = Y2.reshape(RC, M2C).T
+        assert np.abs(got - want).max() <= 2.0 ** -23 * np.abs(want).max()
+        assert np.array_equal(J, Jw)
+        assert np.abs(T - Tw.ravel()).max() <= 1e-4 * max(1.0, np.abs(Tw).max())
+        assert np.allclose(lh, lw, rtol=1e-4, atol=0)

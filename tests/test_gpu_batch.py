@@ -64,11 +64,11 @@ def _build(dense, cps, prec=idl.PREC_FP32, learned=(idl.PROPOSAL_NONE,)):
     return items, outs, keep
 
 
-@pytest.mark.parametrize("graph,tune", [(0, 0), (1, 1)])
-def test_batch_matches_single_item_calls(ctx, graph, tune):
+@pytest.mark.parametrize("graph,tune,prec", [(0, 0, idl.PREC_FP32), (1, 1, idl.PREC_FP32), (1, 0, idl.PREC_TF32X3)])
+def test_batch_matches_single_item_calls(ctx, graph, tune, prec):
     dense, cps = _dense_problems(3), _cp_problems(5)
     idl.lib().idl_debug_batch_mode(ctx.ptr, int(not graph), int(not tune))
-    items, outs, keep = _build(dense, cps)
+    items, outs, keep = _build(dense, cps, prec=prec)
     for _ in range(2):                                   # second call replays the graph
         idl.idl_batch_run(ctx, items)
     assert ctx.sync() == idl.IDL_OK
@@ -76,7 +76,7 @@ def test_batch_matches_single_item_calls(ctx, graph, tune):
     for pr, (J, T, _) in zip(dense, outs[:len(dense)]):
         K, R = pr["K"], pr["A"].shape[1]
         Js, Ts, _ = _outputs(K, R)
-        p = idl.make_params(pr["m1"], pr["m2"], seed=pr["seed"], modified=True, precision=idl.PREC_FP32)
+        p = idl.make_params(pr["m1"], pr["m2"], seed=pr["seed"], modified=True, precision=prec)
         idl.id_matrix(ctx, dev(pr["A"]), K, p, Js, Ts)
         assert np.array_equal(host(J), host(Js))
         # T agrees to FP32 rounding of the sketch amplified by cond(R11); the batch may split
@@ -89,7 +89,7 @@ def test_batch_matches_single_item_calls(ctx, graph, tune):
     for pr, (J, T, lh) in zip(cps, outs[len(dense):]):
         K, R = pr["K"], pr["facs"][0].shape[1]
         Js, Ts, lhs = _outputs(K, R, cp=True)
-        p = idl.make_params(pr["L"], pr["m2"], seed=pr["seed"], modified=False, precision=idl.PREC_FP32)
+        p = idl.make_params(pr["L"], pr["m2"], seed=pr["seed"], modified=False, precision=prec)
         fd = [dev(np.ascontiguousarray(F.T)) for F in pr["facs"]]
         idl.id_cp_tensor(ctx, fd, dev(pr["lam"]), K, p, Js, Ts, lhs)
         assert np.array_equal(host(J), host(Js))

@@ -148,7 +148,7 @@ def test_cfg2_mixed_precision(ctx):
     I, R, K, m1, m2 = 32768, 4096, 100, 14400, 120
     A = gaussian_lowrank_dense(I, R, 100, 1e-4, seed=20190132)
     errs = {}
-    for prec in (idl.PREC_FP32, idl.PREC_BF16X3, idl.PREC_BF16):
+    for prec in (idl.PREC_FP32, idl.PREC_BF16X3, idl.PREC_BF16, idl.PREC_TF32X3):
         p = idl.make_params(m1, m2, seed=8, modified=True, precision=prec)
         J, T = _outputs(K, R)
         info = idl.Info()
@@ -157,9 +157,10 @@ def test_cfg2_mixed_precision(ctx):
     Jw, Tw, iw = oid.id_matrix(A, k=K, m1=m1, m2=m2, seed=8, modified=True, precision=FP64)
     e_or = oer.matrix_id_error(A, J=Jw, T=Tw, exact=False, iters=15)
     print(f"cfg2-shaped ID error: oracle FP64 {e_or:.3e}, FP32 {errs[idl.PREC_FP32]:.3e}, "
-          f"BF16X3 {errs[idl.PREC_BF16X3]:.3e}, BF16 {errs[idl.PREC_BF16]:.3e}")
+          f"BF16X3 {errs[idl.PREC_BF16X3]:.3e}, BF16 {errs[idl.PREC_BF16]:.3e}, TF32X3 {errs[idl.PREC_TF32X3]:.3e}")
     assert errs[idl.PREC_FP32] <= RATIO * e_or
     assert errs[idl.PREC_BF16X3] <= RATIO * e_or
+    assert errs[idl.PREC_TF32X3] <= RATIO * e_or
     # plain bf16 operands (8-bit mantissa) put ~2^-9 relative noise on every sketch
     # entry, far above this matrix's 1e-4 noise floor: its error is stated, not gated
     # at 1.1x (it misses the 1e-3 level; BF16X3 is the mixed-precision mode that meets it)
@@ -189,11 +190,12 @@ def test_cfg2_full_size_mixed_precision(ctx):
     assert errs[idl.PREC_BF16X3] <= RATIO * e_or
 
 
-def test_cfg3_cp_tensor(ctx):
+@pytest.mark.parametrize("prec", [idl.PREC_FP32, idl.PREC_TF32X3])
+def test_cfg3_cp_tensor(ctx, prec):
     dims, R, K, L, m2 = (1000, 1000, 1000), 1000, 50, 8192, 60
     facs, lam = cp_factors(dims, R, seed=20190133)
     fd = [dev(np.ascontiguousarray(F.T)) for F in facs]
-    p = idl.make_params(L, m2, seed=9, modified=False, precision=idl.PREC_FP32)
+    p = idl.make_params(L, m2, seed=9, modified=False, precision=prec)
     J, T = _outputs(K, R)
     lh = torch.empty(K, dtype=torch.float64, device="cuda")
     info = idl.Info()
@@ -425,4 +427,55 @@ def test_row_blocks_sum_to_the_whole_sketch(ctx, kind):
     idl.idl_id_from_sketch(ctx, Y2, m2, R, K, p, J2, T2)
     assert np.array_equal(host(J2), host(J1))
     assert np.allclose(host(T2), host(T1), rtol=1e-3, atol=1e-6)
+    assert ctx.sync() == idl.IDL_OK
+
+
+@pytest.mark.parametrize("L,m2", [(8192, 40), (1024, 40), (256, 0)])
+def test_cp_column_blocks_gather_to_the_whole_sketch(ctx, L, m2):
+    """Column r of a CP tensor's sketch depends on column r of the factors and the
+    modes' maps only (Sec. 1.3, Eq. TA-formula): column blocks sketched apart by
+    idl_sketch_cp and placed side by side equal the oracle's sketch of the whole
+    tensor, and Algorithm 1 + the s-value update on the gathered sketch give
+    id_cp_tensor's J and lambda_hat."""
+    from paper_1901_10559_gb300 import sharded
+    dims, R, K = (70, 50, 40), 333, 12
+    facs, lam = cp_factors(dims, R, seed=31)
+    p = idl.make_params(L, m2, seed=17, modified=False, precision=idl.PREC_FP32)
+    m = m2 if m2 > 0 else L
+    Y2 = torch.full((m * R,), float("nan"), dtype=torch.float32, device="cuda")
+    for c0, c1 in sharded.column_blocks(R, 3):
+        fd = [dev(np.ascontiguousarray(F[:, c0:c1].T)) for F in facs]
+        idl.idl_sketch_cp(ctx, fd, dev(lam[c0:c1]), p, Y2[c0 * m:c1 * m])
+    Jw, Tw, lhw, iw = oid.id_cp_tensor(facs, lam, k=K, L=L, m2=m2, seed=17, precision=FP32)
+    got = host(Y2).reshape(R, m).T
+    assert rel_fro(got, iw["Y2"]) <= 1e-5
+    J1, T1 = _outputs(K, R)
+    lh1 = torch.empty(K, dtype=torch.float64, device="cuda")
+    idl.id_cp_tensor(ctx, [dev(np.ascontiguousarray(F.T)) for F in facs], dev(lam), K, p, J1, T1, lh1)
+    J2, T2 = _outputs(K, R)
+    lh2 = torch.empty(K, dtype=torch.float64, device="cuda")
+    idl.idl_id_from_sketch(ctx, Y2, m, R, K, p, J2, T2)
+    idl.idl_lambda_hat(ctx, dev(lam), J2, T2, K, R, lh2)
+    if pivots_well_separated(iw["gaps"]):
+        assert np.array_equal(host(J2), Jw) and np.array_equal(host(J1), Jw)
+        assert np.allclose(host(lh2), host(lh1), rtol=1e-3, atol=1e-6)
+    e_w = oer.tensor_id_error(facs, lam, Jw, lhw)
+    assert oer.tensor_id_error(facs, lam, host(J2), host(lh2)) <= RATIO * e_w
+    assert ctx.sync() == idl.IDL_OK
+
+
+def test_sketch_cp_argument_errors(ctx):
+    facs, lam = cp_factors((20, 20), 30, seed=1)
+    fd = [dev(np.ascontiguousarray(F.T)) for F in facs]
+    Y2 = torch.empty(40 * 30, dtype=torch.float32, device="cuda")
+    for kw, code in [(dict(m1=100, m2=20), idl.IDL_EINVAL),                        # L not a power of two
+                     (dict(m1=256, m2=20, precision=idl.PREC_FP64), idl.IDL_EINVAL)]:
+        p = idl.make_params(kw["m1"], kw["m2"], seed=1, modified=False, precision=kw.get("precision", idl.PREC_FP32))
+        with pytest.raises(idl.IdlError) as e:
+            idl.idl_sketch_cp(ctx, fd, dev(lam), p, Y2)
+        assert e.value.code == code
+    p = idl.make_params(256, 20, seed=1, modified=False, precision=idl.PREC_FP32)
+    with pytest.raises(idl.IdlError) as e:
+        idl.idl_sketch_cp(ctx, fd, dev(lam), p, torch.empty(20 * 30, dtype=torch.float32))   # host Y2
+    assert e.value.code == idl.IDL_EINVAL
     assert ctx.sync() == idl.IDL_OK

@@ -152,6 +152,33 @@ def test_countsketch_csr_parity(ctx, dtype, I, R, L, density):
     assert ctx.sync() == idl.IDL_OK
 
 
+@pytest.mark.parametrize("I,R,L,modified,frac_long", [(20000, 3000, 300, True, 0.0), (50, 400, 200, False, 0.0),
+                                                       (3000, 10000, 61, True, 0.02), (700, 20000, 9, True, 0.1),
+                                                       (1, 5, 3, False, 0.0)])
+def test_countsketch_csr_edge_shapes(ctx, I, R, L, modified, frac_long):
+    """The CSR CountSketch against the oracle entry by entry within the rounding of
+    each bucket's sum: empty buckets (plain maps with L > I), rows of thousands of
+    nonzeros beside short ones, unaligned row starts, a single row."""
+    rng = np.random.default_rng(I + R + L)
+    lens = np.where(rng.random(I) < frac_long, rng.integers(min(4000, R), R + 1, I), rng.integers(0, 40, I))
+    lens = np.minimum(lens, R)
+    cols = np.concatenate([np.sort(rng.permutation(R)[:n]) for n in lens]).astype(np.int32)
+    vals = rng.standard_normal(cols.size).astype(np.float32)
+    rowptr = np.concatenate([[0], np.cumsum(lens)]).astype(np.int64)
+    nnz = int(rowptr[-1])
+    h, s, ptr, rows = _draw(ctx, 41, I, L, modified)
+    hw, sw = odr.countsketch_maps(41, I, L, modified)
+    want = ocs.countsketch_csr(rowptr, cols, vals, R, hw, sw, L)
+    absum = ocs.countsketch_csr(rowptr, cols, np.abs(vals), R, hw, np.ones_like(sw), L)
+    nterms = int(np.max(np.bincount(hw, weights=np.diff(rowptr), minlength=L)))
+    Y = torch.full((L, R), float("nan"), dtype=torch.float32, device="cuda")
+    idl.idl_countsketch_csr(ctx, dev(rowptr), dev(cols), dev(vals), I, R, nnz, idl.IDL_F32, h, s, ptr, rows, L, Y, R)
+    g = host(Y)
+    assert np.all(np.isfinite(g))
+    assert_sum_within_bound(g, want, absum, nterms, 2.0 ** -24)
+    assert ctx.sync() == idl.IDL_OK
+
+
 @pytest.mark.parametrize("dtype,offset,R,L", [("f32", 0, 3000, 40), ("f32", 1, 3000, 40), ("f64", 0, 2500, 33),
                                               ("f64", 1, 2500, 33), ("f32", 3, 20000, 7),
                                               ("f32", 1, 60000, 5)])
@@ -248,7 +275,8 @@ def test_countsketch_csr_flags_bad_column(ctx):
 # ------------------------------------------------------------------ a6 Gaussian stage
 @pytest.mark.parametrize("prec,m2,m1,R", [(idl.PREC_FP64, 30, 900, 2000), (idl.PREC_FP32, 60, 3600, 1000),
                                           (idl.PREC_BF16X3, 60, 3600, 1000), (idl.PREC_BF16, 120, 1440, 520),
-                                          (idl.PREC_FP32, 17, 100, 45)])
+                                          (idl.PREC_FP32, 17, 100, 45), (idl.PREC_TF32X3, 60, 3600, 1000),
+                                          (idl.PREC_TF32X3, 17, 100, 45), (idl.PREC_TF32X3, 256, 777, 300)])
 def test_gaussian_stage_parity(ctx, prec, m2, m1, R):
     rng = np.random.default_rng(m1)
     f64 = prec == idl.PREC_FP64
@@ -264,7 +292,8 @@ def test_gaussian_stage_parity(ctx, prec, m2, m1, R):
     idl.idl_gaussian_stage(ctx, Om, m2, m1, dev(Y1p), R, ldy1, idl.IDL_F64 if f64 else idl.IDL_F32, prec, Y2, ldy2)
     want = ogs.gaussian_stage(odr.gaussian_matrix(3, m2, m1), Y1, prec)
     got = colmajor_to_matrix(Y2, m2, R, ldy2)
-    tol = {idl.PREC_FP64: 1e-12, idl.PREC_FP32: FP32_TOL, idl.PREC_BF16X3: 2e-5, idl.PREC_BF16: 1e-5}[prec]
+    tol = {idl.PREC_FP64: 1e-12, idl.PREC_FP32: FP32_TOL, idl.PREC_BF16X3: 2e-5, idl.PREC_BF16: 1e-5,
+           idl.PREC_TF32X3: FP32_TOL}[prec]
     assert rel_fro(got, want) <= tol
 
 
@@ -422,7 +451,8 @@ def test_gaussian_tc_shapes_and_simt_agreement(ctx, m2, m1, R):
     Om = torch.empty(m2 * m1, dtype=torch.float64, device="cuda")
     idl.idl_draw_gaussian(ctx, 5, m2, m1, Om)
     Omw = odr.gaussian_matrix(5, m2, m1)
-    for prec, tol in [(idl.PREC_FP32, FP32_TOL), (idl.PREC_BF16X3, 2e-5), (idl.PREC_BF16, 1e-5)]:
+    for prec, tol in [(idl.PREC_FP32, FP32_TOL), (idl.PREC_BF16X3, 2e-5), (idl.PREC_BF16, 1e-5),
+                      (idl.PREC_TF32X3, FP32_TOL)]:
         outs = []
         for simt in (0, 1):             # tcgen05, CUDA cores
             idl.lib().idl_debug_gemm_path(ctx.ptr, simt)
@@ -454,7 +484,8 @@ def test_gaussian_tc_colmajor_input(ctx, m2, m1, R, extra):
     Yc = np.zeros((R, ldc), np.float32)
     Yc[:, :m1] = Y1.T
     Ycd, Yrd = dev(Yc), dev(Y1)
-    for prec, tol in [(idl.PREC_FP32, FP32_TOL), (idl.PREC_BF16X3, 2e-5), (idl.PREC_BF16, 1e-5)]:
+    for prec, tol in [(idl.PREC_FP32, FP32_TOL), (idl.PREC_BF16X3, 2e-5), (idl.PREC_BF16, 1e-5),
+                      (idl.PREC_TF32X3, FP32_TOL)]:
         Y2c = torch.full((R * m2,), float("nan"), dtype=torch.float32, device="cuda")
         Y2r = torch.full((R * m2,), float("nan"), dtype=torch.float32, device="cuda")
         idl.idl_gaussian_stage_colmajor(ctx, Om, m2, m1, Ycd, R, ldc, prec, Y2c, m2)
