@@ -22,7 +22,7 @@
 // Warp-specialised pipeline (measured: with one block-wide barrier per K block
 // and the MMA issue on a converter thread, ncu showed ~25% barrier stalls and
 // the tensor pipe active 16% of the time): eight converter warps and one
-// MMA/producer warp hand over two stages of A planes and a 3-slot ring of
+// MMA/producer warp hand over two stages of A planes and a 2- or 3-slot ring of
 // Omega^T planes through mbarriers only.  Every mbarrier wait is bounded (1 s); on a timeout the kernel
 // records IDL_ETIMEOUT, waits (bounded) for the MMAs it issued, frees TMEM
 // and returns.
@@ -46,14 +46,14 @@ __global__ void omega_planes_kernel(const double* __restrict__ Om, int m2, int64
 }
 
 template <int NP, bool CM>
-__global__ void __launch_bounds__(kTcThreads, 1)
+__global__ void __launch_bounds__(kTcThreads, CM ? 1 : 2)
 gauss_tc_kernel(const float* __restrict__ Y1, int64_t ldy1, int64_t R, int64_t m1, const __nv_bfloat16* __restrict__ Bpl,
-                int NT, int NTc, int kb_per_cta, int nkb, float* __restrict__ part, int* status) {
+                int NT, int NTc, int kb_per_cta, int nkb, float* __restrict__ part, int* status, int bslots) {
   extern __shared__ unsigned char smem_raw[];
   const int kb0 = blockIdx.y * kb_per_cta;
   const int nk = min(nkb, kb0 + kb_per_cta) - kb0;
   gauss_tc_block<NP, CM>(Y1, ldy1, R, m1, Bpl, NT, NTc, kb0, nk, blockIdx.x, blockIdx.z,
-                     part + (int64_t)blockIdx.y * R * NT, status, smem_raw);
+                         part + (int64_t)blockIdx.y * R * NT, status, smem_raw, bslots);
 }
 
 __global__ void omega_tf32_kernel(const double* __restrict__ Om, int m2, int64_t m1, int NT, int nkb,
@@ -135,27 +135,40 @@ static int tc_impl(idl_ctx* ctx, const double* Omega, int64_t m2, int64_t m1, co
   const int nkb = (int)cdiv(m1, kBK);
   const int mtiles = (int)cdiv(R, kBM);
   const size_t a_plane = (size_t)kBM * kBK * 2;
-  // N chunks: the widest chunk (multiple of 16, <= 256) whose two stages fit in shared memory
+  // N chunks: the widest chunk (multiple of 16, <= 256) whose stages fit in shared memory,
+  // for an Omega^T ring of bs slots; two accumulators of NTc columns fit in TMEM (2 NTc <= 512)
   const int NT0 = (int)round_up(m2, 16);
-  int nz = 1, NTc = NT0;
-  auto smem_for = [&](int ntc) {
-    return 1024 + (size_t)kStages * NP * a_plane + (size_t)kBSlots * NP * ntc * kBK * 2 + 128;
+  auto smem_for = [&](int bs, int ntc) {
+    return 1024 + (size_t)kStages * NP * a_plane + (size_t)bs * NP * ntc * kBK * 2 + 128;
   };
-  // two accumulators of NTc columns must fit in TMEM's 512 columns: NTc <= 256 already; keep 2*NTc <= 512
-  while ((smem_for(NTc) > (size_t)ctx->smem_optin || 2 * NTc > 512) && NTc > 16) {
-    ++nz;
-    NTc = (int)round_up(cdiv(NT0, nz), 16);
-  }
-  const size_t smem = smem_for(NTc);
+  struct Plan { int bs, nz, NTc, per_sm; };
+  auto plan = [&](int bs) {
+    Plan q{bs, 1, NT0, 1};
+    while ((smem_for(bs, q.NTc) > (size_t)ctx->smem_optin || 2 * q.NTc > 512) && q.NTc > 16) {
+      ++q.nz;
+      q.NTc = (int)round_up(cdiv(NT0, q.nz), 16);
+    }
+    q.per_sm = std::max(1, (int)(ctx->smem_optin / smem_for(bs, q.NTc)));
+    return q;
+  };
+  // Fewer N chunks first (each chunk re-reads and re-splits Y1); then two slots for
+  // row-major Y1 and three for column-major.  Measured: a two-slot ring that avoids N
+  // chunks took the dense 14400 x 4096 FP32 shape 162 -> 107 us; on the sparse
+  // 3600 x 10000 shape two slots beat three (BF16X3 62 vs 72 us, FP32 78 vs 82 us);
+  // column-major Y1 was slower with two slots and two CTAs per SM (CP-item shape 75 -> 88 us).
+  const Plan p3 = plan(kBSlots), p2 = plan(2);
+  Plan pl = p3;
+  if (p2.nz < p3.nz || (!y1_cm && p2.nz == p3.nz)) pl = p2;
+  const int bslots = pl.bs, nz = pl.nz, NTc = pl.NTc;
+  const size_t smem = smem_for(bslots, NTc);
   if (smem > (size_t)ctx->smem_optin) return fail(ctx, IDL_ELIMIT, "gaussian tc: shared memory");
   const int NT = nz * NTc;                            // plane rows (zero beyond m2)
   const size_t b_plane_full = (size_t)NT * kBK * 2;
   // split K so that (waves of CTAs) x (K blocks per CTA) is smallest: a CTA's time is
   // proportional to its K blocks, and a partly filled last wave costs a whole one;
   // each split adds a partial result to write and reduce (about half a K block)
-  const int per_sm = std::max(1, (int)(ctx->smem_optin / smem));
   int splits, kbpc;
-  choose_splits((int64_t)mtiles * nz, nkb, (int64_t)ctx->num_sms * per_sm, &splits, &kbpc);
+  choose_splits((int64_t)mtiles * nz, nkb, (int64_t)ctx->num_sms * pl.per_sm, &splits, &kbpc);
   __nv_bfloat16* Bpl = (__nv_bfloat16*)ws_get(ctx, kWsOmegaConv, (size_t)nkb * NP * b_plane_full);
   float* part = (float*)ws_get(ctx, kWsPart, sizeof(float) * (size_t)splits * R * NT);
   if (!Bpl || !part) return IDL_ENOMEM;
@@ -168,7 +181,7 @@ static int tc_impl(idl_ctx* ctx, const double* Omega, int64_t m2, int64_t m1, co
   cudaError_t e = ensure_smem(ctx, (const void*)k, smem);
   if (e != cudaSuccess) return cuda_check(ctx, e, "gaussian tc attribute");
   dim3 grid((unsigned)mtiles, (unsigned)splits, (unsigned)nz);
-  k<<<grid, kTcThreads, smem, ctx->stream>>>(Y1, ldy1, R, m1, Bpl, NT, NTc, kbpc, nkb, part, ctx->d_status),
+  k<<<grid, kTcThreads, smem, ctx->stream>>>(Y1, ldy1, R, m1, Bpl, NT, NTc, kbpc, nkb, part, ctx->d_status, bslots),
       count_launch();
   e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_check(ctx, e, "gaussian tc");

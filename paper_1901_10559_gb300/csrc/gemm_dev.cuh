@@ -181,11 +181,13 @@ __host__ __device__ constexpr int prod_b(int np, int q) {
 
 // Warp-specialised: warps 0-7 convert (load FP32 Y1 one K block ahead in
 // registers, split into bf16 planes, store them swizzled, arrive on a_ready);
-// warp 8 feeds Omega^T planes through a 3-slot ring of bulk copies and one of
+// warp 8 feeds Omega^T planes through a ring of bulk copies (BS = 2 or 3 slots) and one of
 // its lanes issues the MMAs.  Stages are handed over with mbarriers only.
 constexpr int kConvThreads = 256;
 constexpr int kTcThreads = kConvThreads + 32;
-constexpr int kBSlots = 3;
+constexpr int kBSlots = 3;     // Omega^T ring slots (at most; the launcher may pass 2)
+// The single-problem launcher passes two slots for row-major Y1 (and wherever two slots
+// avoid splitting N); the batch and column-major Y1 use three.
 
 // One CTA: rows [mt*128, +128) of D, columns [z*NTc, +NTc), K blocks [kb0, kb0 + nk);
 // partial result rows go to part_base[r * NT + column].  smem_raw: the dynamic
@@ -197,7 +199,7 @@ template <int NP, bool CM = false>
 __device__ __forceinline__ void gauss_tc_block(const float* __restrict__ Y1, int64_t ldy1, int64_t R, int64_t m1,
                                                const __nv_bfloat16* __restrict__ Bpl, int NT, int NTc, int kb0, int nk,
                                                int64_t mt, int z, float* __restrict__ part_base, int* status,
-                                               unsigned char* smem_raw) {
+                                               unsigned char* smem_raw, int BS = kBSlots) {
   using namespace tc;
   unsigned char* sm = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   const int a_plane = kBM * kBK * 2;                   // 16 KB
@@ -205,11 +207,11 @@ __device__ __forceinline__ void gauss_tc_block(const float* __restrict__ Y1, int
   const int n0 = z * NTc;
   unsigned char* A = sm;                               // [stage][plane] a_plane
   unsigned char* B = A + kStages * NP * a_plane;       // [slot][plane] b_plane
-  uint64_t* bars = (uint64_t*)(B + kBSlots * NP * b_plane);
+  uint64_t* bars = (uint64_t*)(B + BS * NP * b_plane);
   uint64_t* a_ready = bars;                            // [kStages] 256 converter arrivals
   uint64_t* mma_done = bars + 2;                       // [kStages] tcgen05.commit
-  uint64_t* b_full = bars + 4;                         // [kBSlots] bulk-copy bytes
-  uint64_t* b_free = bars + 7;                         // [kBSlots] tcgen05.commit
+  uint64_t* b_full = bars + 4;                         // [BS] bulk-copy bytes
+  uint64_t* b_free = bars + 7;                         // [BS] tcgen05.commit
   uint32_t* tmem_slot = (uint32_t*)(bars + 10);
   __shared__ int s_flag;
 
@@ -222,7 +224,7 @@ __device__ __forceinline__ void gauss_tc_block(const float* __restrict__ Y1, int
 
   if (tid == 0) {
     for (int q = 0; q < kStages; ++q) { mbar_init(&a_ready[q], kConvThreads); mbar_init(&mma_done[q], 1); }
-    for (int q = 0; q < kBSlots; ++q) { mbar_init(&b_full[q], 1); mbar_init(&b_free[q], 1); }
+    for (int q = 0; q < BS; ++q) { mbar_init(&b_full[q], 1); mbar_init(&b_free[q], 1); }
     fence_barrier_init();
     s_flag = 0;
   }
@@ -335,12 +337,12 @@ __device__ __forceinline__ void gauss_tc_block(const float* __restrict__ Y1, int
   } else if (lane == 0) {
     // ---------------- producer of Omega^T planes + MMA issue ----------------
     int last_commit = -1, b_issued = 0, b_done = 0;
-    for (int q = 0; q < kBSlots && q < nk; ++q) { fetch_b(kb0 + q, q); b_issued = q + 1; }
+    for (int q = 0; q < BS && q < nk; ++q) { fetch_b(kb0 + q, q); b_issued = q + 1; }
     const uint32_t idesc = idesc_bf16(NTc);
     for (int i = 0; i < nk && !*(volatile int*)&s_flag; ++i) {
-      const int s = i & 1, sb = i % kBSlots;
+      const int s = i & 1, sb = i % BS;
       if (!mbar_wait(&a_ready[s], (i >> 1) & 1)) { s_flag = 1; break; }
-      if (!mbar_wait(&b_full[sb], (i / kBSlots) & 1)) { s_flag = 1; break; }
+      if (!mbar_wait(&b_full[sb], (i / BS) & 1)) { s_flag = 1; break; }
       b_done = i + 1;
       tc_fence_after();
       const unsigned char* As = A + (size_t)s * NP * a_plane;
@@ -359,19 +361,19 @@ __device__ __forceinline__ void gauss_tc_block(const float* __restrict__ Y1, int
       mma_commit(&mma_done[s]);
       mma_commit(&b_free[sb]);
       last_commit = i;
-      // refill the B slot of block i-1 with block i+2 once block i-1's MMAs are done
-      if (i >= 1 && i + 2 < nk) {
-        const int so = (i - 1) % kBSlots;
-        if (!mbar_wait(&b_free[so], ((i - 1) / kBSlots) & 1)) { s_flag = 1; break; }
-        fetch_b(kb0 + i + 2, so);
-        b_issued = i + 3;
+      // refill the B slot of block i-1 with block i-1+BS once block i-1's MMAs are done
+      if (i >= 1 && i - 1 + BS < nk) {
+        const int so = (i - 1) % BS;
+        if (!mbar_wait(&b_free[so], ((i - 1) / BS) & 1)) { s_flag = 1; break; }
+        fetch_b(kb0 + i - 1 + BS, so);
+        b_issued = i + BS;
       }
     }
     // the accumulator is final once the last MMAs complete (bounded wait)
     if (last_commit >= 0 && !mbar_wait(&mma_done[last_commit & 1], (last_commit >> 1) & 1)) s_flag = 2;
     if (last_commit < nk - 1 && !s_flag) s_flag = 1;
     // after an early exit, wait (bounded) for Omega^T copies still in flight
-    for (int j = b_done; j < b_issued; ++j) (void)mbar_wait(&b_full[j % kBSlots], (j / kBSlots) & 1);
+    for (int j = b_done; j < b_issued; ++j) (void)mbar_wait(&b_full[j % BS], (j / BS) & 1);
   }
   tc_fence_before();
   __syncthreads();

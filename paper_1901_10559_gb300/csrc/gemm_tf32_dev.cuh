@@ -22,7 +22,7 @@
 //     stored transposed into the same layout.
 // B (Omega^T): both TF32 planes built once per call in global memory in the
 // shared-memory layout, fetched per K block by one cp.async.bulk into a
-// 3-slot ring.  Warp 8's lane 0 issues the MMAs; handovers use mbarriers only,
+// kBSlots-slot ring.  Warp 8's lane 0 issues the MMAs; handovers use mbarriers only,
 // every wait bounded as in the bf16 body.
 #pragma once
 
@@ -90,7 +90,7 @@ __device__ __forceinline__ void omega_tf32_elem(int64_t e, const double* __restr
 
 // Shared memory of one CTA (the launcher adds 1 KB of alignment slack)
 __host__ __device__ constexpr size_t tf32_smem_bytes(int stages, int ntc) {
-  return 1024 + (size_t)stages * 2 * tc::kBM * 128 + (size_t)3 * 2 * ntc * 128 + 8 * (2 * stages + 6) + 16;
+  return 1024 + (size_t)stages * 2 * tc::kBM * 128 + (size_t)kBSlots * 2 * ntc * 128 + 8 * (2 * stages + 6) + 16;
 }
 
 // One CTA: rows [mt*128, +128) of D, columns [z*NTc, +NTc), K blocks [kb0, kb0 + nk);
@@ -276,11 +276,11 @@ __device__ __forceinline__ void gauss_tf32_block(const float* __restrict__ Y1, i
       mma_commit(&mma_done[s]);
       mma_commit(&b_free[sb]);
       last_commit = i;
-      if (i >= 1 && i + 2 < nk) {
+      if (i >= 1 && i - 1 + kBSlots < nk) {
         const int so = (i - 1) % kBSlots;
         if (!mbar_wait(&b_free[so], (uint32_t)(((i - 1) / kBSlots) & 1))) { s_flag = 1; break; }
-        fetch_b(kb0 + i + 2, so);
-        b_issued = i + 3;
+        fetch_b(kb0 + i - 1 + kBSlots, so);
+        b_issued = i + kBSlots;
       }
     }
     if (last_commit >= 0 && !mbar_wait(&mma_done[last_commit % S], (uint32_t)((last_commit / S) & 1))) s_flag = 2;

@@ -472,9 +472,10 @@ def test_gaussian_tc_shapes_and_simt_agreement(ctx, m2, m1, R):
                                             (120, 1000, 257, 3), (16, 65, 1, 0), (74, 4096, 300, 0)])
 def test_gaussian_tc_colmajor_input(ctx, m2, m1, R, extra):
     """Y1 column-major (ragged K tails, unaligned ldy1 -> scalar loads, aligned ->
-    vector loads): the same planes enter the same MMAs in the same K order, so
-    the result is bit-identical to the row-major call, and within the oracle's
-    tolerance of Omega Y1."""
+    vector loads): the same planes enter the same MMAs, so the result equals the
+    row-major call's up to the order of the split-K partial sums (the two layouts
+    may run a different number of CTAs per SM and so split K differently), and
+    is within the oracle's tolerance of Omega Y1."""
     rng = np.random.default_rng(m2 + 3 * m1 + R)
     Y1 = rng.standard_normal((m1, R)).astype(np.float32)
     Om = torch.empty(m2 * m1, dtype=torch.float64, device="cuda")
@@ -490,7 +491,7 @@ def test_gaussian_tc_colmajor_input(ctx, m2, m1, R, extra):
         Y2r = torch.full((R * m2,), float("nan"), dtype=torch.float32, device="cuda")
         idl.idl_gaussian_stage_colmajor(ctx, Om, m2, m1, Ycd, R, ldc, prec, Y2c, m2)
         idl.idl_gaussian_stage(ctx, Om, m2, m1, Yrd, R, R, idl.IDL_F32, prec, Y2r, m2)
-        assert torch.equal(Y2c, Y2r), prec
+        assert rel_fro(host(Y2c), host(Y2r)) <= 1e-6, prec
         want = ogs.gaussian_stage(Omw, Y1, prec)
         assert rel_fro(colmajor_to_matrix(Y2c, m2, R, m2), want) <= tol, prec
     with pytest.raises(idl.IdlError):
