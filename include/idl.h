@@ -415,9 +415,12 @@ int idl_id_error_csr(idl_ctx* ctx, const int64_t* rowptr, const int32_t* colidx,
  *   device status word -- or every array is host memory (decided by the first
  *   item's A or first factor; pinned memory copies fastest): the call then
  *   copies the inputs into a device staging buffer on a copy stream of its own,
- *   the CP items' factors first and the dense matrices in groups, while the
- *   kernels run and wait only for the inputs they read; it copies J, T and
- *   lambda_hat back and synchronises before it returns.
+ *   the CP items' factors first and the dense matrices in eight groups of about
+ *   equal bytes, and runs each group (the CP items, then each dense group)
+ *   through every stage as soon as its own inputs have landed -- the results
+ *   are those of the device-array call; it copies J, T and lambda_hat back and
+ *   synchronises before it returns.  idl_batch_fallbacks then counts over all
+ *   groups.
  * ------------------------------------------------------------------------- */
 /* ---------------------------------------------------------------------------
  * Learned column proposal for the QR stage (not in the paper; an acceleration

@@ -433,6 +433,9 @@ struct idl_batch_state {
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
   const int* d_flags = nullptr;      // certificate flags of the last batch (n ints, device)
   int nflags = 0;
+  std::vector<std::pair<const int*, int>> flag_sets;   // host-array batches: one per item group
+  unsigned char* pin = nullptr;      // pinned staging of the item groups' tables (host-array batches)
+  size_t pin_bytes = 0;
   cudaStream_t cstream = nullptr;    // host-staged batches: the copies run here
   std::vector<cudaEvent_t> cev;      // their events (reused)
 };
@@ -446,6 +449,7 @@ static idl_batch_state* bstate(idl_ctx* ctx) {
 
 void idl_batch_state_free(idl_batch_state* b) {
   if (!b) return;
+  if (b->pin) cudaFreeHost(b->pin);
   if (b->graph) cudaGraphExecDestroy(b->graph);
   if (b->gstream) cudaStreamDestroy(b->gstream);
   if (b->ev_in) cudaEventDestroy(b->ev_in);
@@ -560,7 +564,10 @@ struct BatchPlan {
   size_t off_items = 0, off_pre = 0, off_lists = 0, table_bytes = 0;
 };
 
-static int plan_batch(idl_ctx* ctx, const idl_batch_item* items, int n, const Tune& tn, BatchPlan& P) {
+// like (optional): a plan of a batch that contains these items; its QR kernel shapes are
+// kept, so that every item is factored by the same kernel as in that batch
+static int plan_batch(idl_ctx* ctx, const idl_batch_item* items, int n, const Tune& tn, BatchPlan& P,
+                      const BatchPlan* like = nullptr) {
   P.it.assign(n, BItem());
   int prec = -1;
   for (int i = 0; i < n; ++i) {
@@ -761,18 +768,22 @@ static int plan_batch(idl_ctx* ctx, const idl_batch_item* items, int n, const Tu
   }
   if (!P.prop_list.empty()) {
     if (P.maxm_prop > prop::kMaxM || P.maxK > 128) return fail(ctx, IDL_ELIMIT, "batch: proposal needs m2, K <= 128");
-    if (!pick_cpqr(P.prop_list, P.it, &P.cfg_cand, true))
+    if (like && !like->prop_list.empty()) P.cfg_cand = like->cfg_cand;
+    else if (!pick_cpqr(P.prop_list, P.it, &P.cfg_cand, true))
       return fail(ctx, IDL_ELIMIT, "batch: no candidate QR shape");
   }
   for (int i = 0; i < n; ++i) P.it[i].nc = 0;
   if (!P.dense_list.empty()) {
-    if (!pick_cpqr(P.dense_list, P.it, &P.cfg_dense, false, tn.qr_cs_dense) &&
-        !pick_cpqr(P.dense_list, P.it, &P.cfg_dense, false, 16))
+    if (like && !like->dense_list.empty()) P.cfg_dense = like->cfg_dense;
+    else if (!pick_cpqr(P.dense_list, P.it, &P.cfg_dense, false, tn.qr_cs_dense) &&
+             !pick_cpqr(P.dense_list, P.it, &P.cfg_dense, false, 16))
       return fail(ctx, IDL_ELIMIT, "batch: no QR cluster shape");
     for (int p : P.dense_list) P.it[p].nc = (int)cdiv(P.it[p].R, P.cfg_dense.CS);
   }
   if (!P.cp_list.empty()) {
-    if (!pick_cpqr(P.cp_list, P.it, &P.cfg_cp, false, tn.qr_cs_cp) && !pick_cpqr(P.cp_list, P.it, &P.cfg_cp, false, 16))
+    if (like && !like->cp_list.empty()) P.cfg_cp = like->cfg_cp;
+    else if (!pick_cpqr(P.cp_list, P.it, &P.cfg_cp, false, tn.qr_cs_cp) &&
+             !pick_cpqr(P.cp_list, P.it, &P.cfg_cp, false, 16))
       return fail(ctx, IDL_ELIMIT, "batch: no QR cluster shape");
     for (int p : P.cp_list) P.it[p].nc = (int)cdiv(P.it[p].R, P.cfg_cp.CS);
   }
@@ -845,20 +856,10 @@ static int run_proposal(idl_ctx* ctx, const BatchPlan& P, const BItem* d_items, 
   return launch_check(ctx, "batch proposal");
 }
 
-// Host-staged inputs (idl_batch_run with host arrays): events recorded on the copy
-// stream once the CP items' factors are on the device, and once each group of dense
-// items is; dense[g].first = end of group g in the dense-sketch block list.
-struct HostFeed {
-  cudaEvent_t ev_cp = nullptr;
-  std::vector<std::pair<int64_t, cudaEvent_t>> dense;
-};
-
 // All launches of a batch (the part that is captured into a graph).  ms (optional,
-// kBTimedStages floats): CUDA-event times of the stage groups (see BTimed).  feed
-// (optional): the sketches wait for the staged inputs they read, group by group.
+// kBTimedStages floats): CUDA-event times of the stage groups (see BTimed).
 static int run_stages(idl_ctx* ctx, const BatchPlan& P, const BItem* d_items, const int64_t* d_pre,
-                      const int32_t* d_lists, int n, int sketch_threads, int& nlaunch, float* ms,
-                      const HostFeed* feed = nullptr) {
+                      const int32_t* d_lists, int n, int sketch_threads, int& nlaunch, float* ms) {
   nlaunch = 0;
   cudaEvent_t ev[kBTimedStages + 1] = {};
   const bool timed = ms != nullptr;
@@ -875,9 +876,6 @@ static int run_stages(idl_ctx* ctx, const BatchPlan& P, const BItem* d_items, co
   BLAUNCH(b_sortb_kernel, kBSortB, 512, sizeof(int32_t) * kBlockSortCap);
   BTRY(launch_check(ctx, "batch buckets"));
   mark(1);
-  // the TensorSketch first: with host-staged inputs it runs while the dense matrices
-  // are still being copied
-  if (feed && feed->ev_cp) TRYC(cudaStreamWaitEvent(ctx->stream, feed->ev_cp, 0), "batch feed wait");
   if (P.pre[kBSketchT][n] > 0) {
     const size_t smem = ts_smem_bytes(P.maxL_cp);
     cudaError_t e = ensure_smem(ctx, (const void*)b_sketch_cp_kernel, smem);
@@ -897,18 +895,7 @@ static int run_stages(idl_ctx* ctx, const BatchPlan& P, const BItem* d_items, co
   {
     const int64_t nbd = P.pre[kBSketchD][n];
     const int64_t* pre_d = d_pre + (size_t)kBSketchD * (n + 1);
-    if (feed && !feed->dense.empty()) {
-      int64_t b0 = 0;
-      for (const auto& g : feed->dense) {
-        TRYC(cudaStreamWaitEvent(ctx->stream, g.second, 0), "batch feed wait");
-        if (g.first > b0) {
-          b_sketch_dense_kernel<<<(unsigned)(g.first - b0), sketch_threads, 0, ctx->stream>>>(d_items, pre_d, n, b0);
-          count_launch();
-          ++nlaunch;
-        }
-        b0 = g.first;
-      }
-    } else if (nbd > 0) {
+    if (nbd > 0) {
       b_sketch_dense_kernel<<<(unsigned)nbd, sketch_threads, 0, ctx->stream>>>(d_items, pre_d, n, 0);
       count_launch();
       ++nlaunch;
@@ -955,7 +942,11 @@ static int run_stages(idl_ctx* ctx, const BatchPlan& P, const BItem* d_items, co
 }
 
 // Uploads the tables (with workspace addresses filled in) and clears the zero region.
-static int upload(idl_ctx* ctx, BatchPlan& P, unsigned char* ws, unsigned char* tab, int n) {
+// pinned (optional): a pinned host region of P.table_bytes the tables pass through, so
+// that the copy is queued without waiting for the stream (a pageable source may make
+// the driver synchronise with the stream first)
+static int upload(idl_ctx* ctx, BatchPlan& P, unsigned char* ws, unsigned char* tab, int n, bool sync = true,
+                  unsigned char* pinned = nullptr) {
   std::vector<unsigned char> host(P.table_bytes, 0);
   std::vector<BItem> items = P.it;
   auto fix = [&](auto*& ptr) { ptr = (std::remove_reference_t<decltype(ptr)>)(ws + (size_t)(uintptr_t)ptr); };
@@ -987,18 +978,21 @@ static int upload(idl_ctx* ctx, BatchPlan& P, unsigned char* ws, unsigned char* 
   for (size_t q = 0; q < P.dense_list.size(); ++q) lists[q] = P.dense_list[q];
   for (size_t q = 0; q < P.cp_list.size(); ++q) lists[n + 1 + q] = P.cp_list[q];
   for (size_t q = 0; q < P.prop_list.size(); ++q) lists[2 * (n + 1) + q] = P.prop_list[q];
-  cudaError_t e = cudaMemcpyAsync(tab, host.data(), P.table_bytes, cudaMemcpyHostToDevice, ctx->stream);
+  if (pinned) memcpy(pinned, host.data(), P.table_bytes);
+  cudaError_t e = cudaMemcpyAsync(tab, pinned ? pinned : host.data(), P.table_bytes, cudaMemcpyHostToDevice,
+                                  ctx->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(ws, 0, P.zero_bytes, ctx->stream);
-  // the host buffer must outlive the copy: synchronise (the tables are small)
-  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  // a pageable host-to-device copy returns once its source is staged; the synchronisation
+  // (sync = true) keeps the tuning runs' timing free of queued work
+  if (e == cudaSuccess && sync) e = cudaStreamSynchronize(ctx->stream);
   return cuda_check(ctx, e, "batch upload");
 }
 
 // ---------------------------------------------------------------------------
 // Host arrays.  The batch's inputs are copied into one device staging buffer on
 // the context's copy stream -- the CP items' factors and s-values first, then the
-// dense matrices in groups -- while the kernels run on the context's stream and
-// wait only for what they read (HostFeed); the outputs are copied back at the end.
+// dense matrices in groups -- while the item groups run on the context's stream,
+// each after its own inputs (run_host_groups); the outputs are copied back at the end.
 // ---------------------------------------------------------------------------
 struct HostStage {
   struct Copy { size_t off; const void* host; size_t bytes; };
@@ -1075,41 +1069,20 @@ static cudaEvent_t stage_event(idl_batch_state* bs, size_t i) {
   return bs->cev[i];
 }
 
-// Issues the input copies on the copy stream (after the context stream's queued
-// work, which may still read the staging buffer) and fills feed; groups: dense
-// groups wanted.
-static int stage_inputs(idl_ctx* ctx, idl_batch_state* bs, const HostStage& hs, const BatchPlan& P, int n,
-                        int groups, HostFeed* feed) {
+// All inputs of a host-array batch copied in on the copy stream; the context's stream
+// waits for them (the first call's tuning runs read every input).
+static int stage_all_inputs(idl_ctx* ctx, idl_batch_state* bs, const HostStage& hs) {
   if (!bs->cstream) TRYC(cudaStreamCreateWithFlags(&bs->cstream, cudaStreamNonBlocking), "batch copy stream");
-  cudaEvent_t ev0 = stage_event(bs, 0);
-  if (!ev0) return fail(ctx, IDL_ECUDA, "batch: event creation failed");
+  cudaEvent_t ev0 = stage_event(bs, 0), ev1 = stage_event(bs, 1);
+  if (!ev0 || !ev1) return fail(ctx, IDL_ECUDA, "batch: event creation failed");
   TRYC(cudaEventRecord(ev0, ctx->stream), "batch stage order");
   TRYC(cudaStreamWaitEvent(bs->cstream, ev0, 0), "batch stage order");
   for (const auto& c : hs.in_cp)
     TRYC(cudaMemcpyAsync(hs.base + c.off, c.host, c.bytes, cudaMemcpyDefault, bs->cstream), "batch copy in");
-  size_t ne = 1;
-  feed->ev_cp = stage_event(bs, ne++);
-  if (!feed->ev_cp) return fail(ctx, IDL_ECUDA, "batch: event creation failed");
-  TRYC(cudaEventRecord(feed->ev_cp, bs->cstream), "batch copy event");
-  size_t tot = 0;
-  for (const auto& c : hs.in_dense) tot += c.bytes;
-  const size_t per = tot / (size_t)std::max(1, groups) + 1;
-  size_t acc = 0;
-  for (size_t q = 0; q < hs.in_dense.size(); ++q) {
-    const auto& c = hs.in_dense[q];
+  for (const auto& c : hs.in_dense)
     TRYC(cudaMemcpyAsync(hs.base + c.off, c.host, c.bytes, cudaMemcpyDefault, bs->cstream), "batch copy in");
-    acc += c.bytes;
-    const bool last = q + 1 == hs.in_dense.size();
-    if (acc >= per || last) {
-      // the group ends with item dense_item[q]: its dense-sketch blocks end at pre[item + 1]
-      cudaEvent_t e = stage_event(bs, ne++);
-      if (!e) return fail(ctx, IDL_ECUDA, "batch: event creation failed");
-      TRYC(cudaEventRecord(e, bs->cstream), "batch copy event");
-      const int64_t end = last ? P.pre[kBSketchD][n] : P.pre[kBSketchD][hs.dense_item[q] + 1];
-      feed->dense.push_back({end, e});
-      acc = 0;
-    }
-  }
+  TRYC(cudaEventRecord(ev1, bs->cstream), "batch copy event");
+  TRYC(cudaStreamWaitEvent(ctx->stream, ev1, 0), "batch stage wait");
   return IDL_OK;
 }
 
@@ -1117,6 +1090,115 @@ static int stage_outputs(idl_ctx* ctx, const HostStage& hs) {
   for (const auto& c : hs.out)
     TRYC(cudaMemcpyAsync((void*)c.host, hs.base + c.off, c.bytes, cudaMemcpyDefault, ctx->stream), "batch copy out");
   TRYC(cudaStreamSynchronize(ctx->stream), "batch sync");
+  return IDL_OK;
+}
+
+// Host arrays: the CP items, then the dense items in groups of about equal bytes (eight),
+// each group copied in on the copy stream and run through every stage as soon as its
+// own copies have landed, so the Gaussian stage, QR and T of all groups but the last
+// overlap the later groups' copies.  Each group has its own plan, tables and workspace
+// region (the regions add up to the whole batch's), so nothing is reused while queued.
+// Results equal the single-plan run's: the group plans keep the whole batch's tuning and
+// QR kernel shapes, and every other choice depends on the item alone.
+static int run_host_groups(idl_ctx* ctx, idl_batch_state* bs, const HostStage& hs, const idl_batch_item* items,
+                           int n, const Tune& tn, const BatchPlan& whole) {
+  std::vector<std::vector<int>> groups;
+  {
+    std::vector<int> cp;
+    for (int i = 0; i < n; ++i)
+      if (items[i].kind == IDL_ITEM_CP) cp.push_back(i);
+    if (!cp.empty()) groups.push_back(cp);
+  }
+  const size_t first_dense = groups.size();
+  size_t tot = 0;
+  for (const auto& c : hs.in_dense) tot += c.bytes;
+  const size_t per = tot / 8 + 1;
+  {
+    std::vector<int> cur;
+    size_t acc = 0;
+    for (size_t q = 0; q < hs.in_dense.size(); ++q) {
+      cur.push_back(hs.dense_item[q]);
+      acc += hs.in_dense[q].bytes;
+      if (acc >= per || q + 1 == hs.in_dense.size()) { groups.push_back(cur); cur.clear(); acc = 0; }
+    }
+  }
+  // one plan per group, placed side by side in the workspace and the table buffer
+  const size_t G = groups.size();
+  std::vector<std::vector<idl_batch_item>> subs(G);
+  std::vector<BatchPlan> plans(G);
+  std::vector<size_t> ws_off(G), tab_off(G);
+  size_t ws_tot = 0, tab_tot = 0;
+  for (size_t g = 0; g < G; ++g) {
+    for (int i : groups[g]) subs[g].push_back(items[i]);
+    BTRY(plan_batch(ctx, subs[g].data(), (int)subs[g].size(), tn, plans[g], &whole));
+    ws_off[g] = ws_tot;
+    tab_off[g] = tab_tot;
+    ws_tot += (plans[g].ws_bytes + 255) & ~(size_t)255;
+    tab_tot += (plans[g].table_bytes + 255) & ~(size_t)255;
+  }
+  unsigned char* ws = (unsigned char*)ws_get(ctx, kWsBatch, ws_tot);
+  unsigned char* tab = (unsigned char*)ws_get(ctx, kWsBatchTab, tab_tot);
+  if (!ws || !tab) return IDL_ENOMEM;
+  if (bs->pin_bytes < tab_tot) {      // reused by later calls: each call ends synchronised
+    if (bs->pin) cudaFreeHost(bs->pin);
+    bs->pin = nullptr;
+    bs->pin_bytes = 0;
+    if (cudaMallocHost((void**)&bs->pin, tab_tot) != cudaSuccess) {
+      (void)cudaGetLastError();
+      bs->pin = nullptr;
+      return fail(ctx, IDL_ENOMEM, "batch: pinned table staging");
+    }
+    bs->pin_bytes = tab_tot;
+  }
+  // every group's tables before the input copies: host-to-device copies are served in
+  // the order they are queued, so a table queued behind the inputs would wait for all
+  // of them (measured: the first group then started after the last input landed)
+  for (size_t g = 0; g < G; ++g)
+    BTRY(upload(ctx, plans[g], ws + ws_off[g], tab + tab_off[g], (int)subs[g].size(), false, bs->pin + tab_off[g]));
+  // copies: the CP group's first, then each dense group's, an event after each group
+  if (!bs->cstream) TRYC(cudaStreamCreateWithFlags(&bs->cstream, cudaStreamNonBlocking), "batch copy stream");
+  cudaEvent_t ev0 = stage_event(bs, 0);
+  if (!ev0) return fail(ctx, IDL_ECUDA, "batch: event creation failed");
+  TRYC(cudaEventRecord(ev0, ctx->stream), "batch stage order");
+  TRYC(cudaStreamWaitEvent(bs->cstream, ev0, 0), "batch stage order");
+  std::vector<cudaEvent_t> gev;
+  size_t ne = 1;
+  auto group_event = [&]() -> int {
+    cudaEvent_t e = stage_event(bs, ne++);
+    if (!e) return fail(ctx, IDL_ECUDA, "batch: event creation failed");
+    TRYC(cudaEventRecord(e, bs->cstream), "batch copy event");
+    gev.push_back(e);
+    return IDL_OK;
+  };
+  if (first_dense == 1) {
+    for (const auto& c : hs.in_cp)
+      TRYC(cudaMemcpyAsync(hs.base + c.off, c.host, c.bytes, cudaMemcpyDefault, bs->cstream), "batch copy in");
+    BTRY(group_event());
+  }
+  {
+    size_t q = 0;
+    for (size_t g = first_dense; g < groups.size(); ++g) {
+      for (size_t k = 0; k < groups[g].size(); ++k, ++q) {
+        const auto& c = hs.in_dense[q];
+        TRYC(cudaMemcpyAsync(hs.base + c.off, c.host, c.bytes, cudaMemcpyDefault, bs->cstream), "batch copy in");
+      }
+      BTRY(group_event());
+    }
+  }
+  bs->flag_sets.clear();
+  bs->d_flags = nullptr;
+  bs->nflags = 0;
+  for (size_t g = 0; g < G; ++g) {
+    const int ng = (int)subs[g].size();
+    const BatchPlan& Q = plans[g];
+    unsigned char* w = ws + ws_off[g];
+    unsigned char* t = tab + tab_off[g];
+    TRYC(cudaStreamWaitEvent(ctx->stream, gev[g], 0), "batch group wait");
+    int nl = 0;
+    BTRY(run_stages(ctx, Q, (const BItem*)(t + Q.off_items), (const int64_t*)(t + Q.off_pre),
+                    (const int32_t*)(t + Q.off_lists), ng, tn.sketch_threads, nl, nullptr));
+    bs->flag_sets.push_back({(const int*)(w + Q.off_flags), ng});
+  }
   return IDL_OK;
 }
 
@@ -1148,12 +1230,7 @@ extern "C" int idl_batch_run(idl_ctx* ctx, const idl_batch_item* items, int n) {
   const int32_t* d_lists = (const int32_t*)(tab + P.off_lists);
   int nlaunch = 0;
   if (!known && !ctx->batch_no_tune) {
-    if (host) {       // the tuning runs read the inputs: stage them all first
-      HostFeed f0;
-      BTRY(stage_inputs(ctx, bs, hs, P, n, 1, &f0));
-      for (const auto& g : f0.dense) TRYC(cudaStreamWaitEvent(ctx->stream, g.second, 0), "batch stage wait");
-      TRYC(cudaStreamWaitEvent(ctx->stream, f0.ev_cp, 0), "batch stage wait");
-    }
+    if (host) BTRY(stage_all_inputs(ctx, bs, hs));      // the tuning runs read the inputs
     // autotune, one knob at a time on whole-batch runs timed per stage group: the dense
     // sketch's block width, the Gaussian split-K factor, the QR cluster sizes
     auto trial = [&](const Tune& t, int stage, float* out) -> int {
@@ -1196,15 +1273,14 @@ extern "C" int idl_batch_run(idl_ctx* ctx, const idl_batch_item* items, int n) {
     d_pre = (const int64_t*)(tab + P.off_pre);
     d_lists = (const int32_t*)(tab + P.off_lists);
   }
+  if (host) {         // item groups run as their inputs land
+    BTRY(run_host_groups(ctx, bs, hs, items, n, tn, P));
+    return stage_outputs(ctx, hs);
+  }
   BTRY(upload(ctx, P, ws, tab, n));
   bs->d_flags = (const int*)(ws + P.off_flags);
   bs->nflags = n;
-  if (host) {         // eager launches that wait for their inputs group by group
-    HostFeed feed;
-    BTRY(stage_inputs(ctx, bs, hs, P, n, 8, &feed));
-    BTRY(run_stages(ctx, P, d_items, d_pre, d_lists, n, tn.sketch_threads, nlaunch, nullptr, &feed));
-    return stage_outputs(ctx, hs);
-  }
+  bs->flag_sets.clear();
   if (ctx->batch_no_graph) return run_stages(ctx, P, d_items, d_pre, d_lists, n, tn.sketch_threads, nlaunch, nullptr);
   // graph: captured once per (shape, workspace address) on a private stream, replayed afterwards;
   // events order it after the caller's stream and the caller's stream after it
@@ -1307,13 +1383,16 @@ extern "C" int idl_debug_batch_timing(idl_ctx* ctx, const idl_batch_item* items,
 extern "C" int idl_batch_fallbacks(idl_ctx* ctx) {
   if (!ctx) return -IDL_EINVAL;
   idl_batch_state* bs = bstate(ctx);
-  if (!bs->d_flags || bs->nflags < 1) return 0;
-  std::vector<int> h((size_t)bs->nflags);
-  cudaError_t e = cudaMemcpyAsync(h.data(), bs->d_flags, sizeof(int) * h.size(), cudaMemcpyDeviceToHost, ctx->stream);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
-  if (e != cudaSuccess) return -cuda_check(ctx, e, "batch fallbacks");
+  std::vector<std::pair<const int*, int>> sets = bs->flag_sets;
+  if (sets.empty() && bs->d_flags && bs->nflags > 0) sets.push_back({bs->d_flags, bs->nflags});
   int c = 0;
-  for (int v : h) c += v != 0;
+  for (const auto& fs : sets) {
+    std::vector<int> h((size_t)fs.second);
+    cudaError_t e = cudaMemcpyAsync(h.data(), fs.first, sizeof(int) * h.size(), cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return -cuda_check(ctx, e, "batch fallbacks");
+    for (int v : h) c += v != 0;
+  }
   return c;
 }
 
