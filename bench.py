@@ -259,6 +259,24 @@ def make_batch(seed, rank=0, n_dense=256, n_cp=64):
     return dense, cps
 
 
+def copy_floor_ms(host_tensors, reps: int = 2) -> float:
+    """Milliseconds to copy these pinned host tensors to the device with plain copies,
+    one after another into a reused device buffer: the host link's floor under the
+    end-to-end number (untimed for the metric itself)."""
+    import torch
+    srcs = [t.contiguous().view(torch.uint8).reshape(-1) for t in host_tensors]
+    dst = torch.empty(max(x.numel() for x in srcs), dtype=torch.uint8, device="cuda")
+    for x in srcs:
+        dst[:x.numel()].copy_(x, non_blocking=True)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        for x in srcs:
+            dst[:x.numel()].copy_(x, non_blocking=True)
+    torch.cuda.synchronize()
+    return (time.perf_counter() - t0) / reps * 1e3
+
+
 def precision_code(idl, name):
     """IDL_PREC_* of a precision mode's name."""
     return {"FP64": idl.PREC_FP64, "FP32": idl.PREC_FP32, "BF16X3": idl.PREC_BF16X3, "BF16": idl.PREC_BF16,
@@ -320,6 +338,7 @@ def run_ours(args, ws, rank, local):
         h_rp, h_ci, h_v = (torch.from_numpy(c.rowptr).pin_memory(), torch.from_numpy(c.colidx).pin_memory(),
                            torch.from_numpy(c.vals).pin_memory())
         in_bytes = c.rowptr.nbytes + c.colidx.nbytes + c.vals.nbytes
+        host_inputs = [h_rp, h_ci, h_v]
 
         def step(J, T, lh, host_in=False):
             if host_in:
@@ -331,6 +350,7 @@ def run_ours(args, ws, rank, local):
         d_A = torch.from_numpy(A).cuda()
         h_A = torch.from_numpy(A).pin_memory()
         in_bytes = A.nbytes
+        host_inputs = [h_A]
 
         def step(J, T, lh, host_in=False):
             idl.id_matrix(ctx, h_A if host_in else d_A, K, p, J, T)
@@ -341,6 +361,7 @@ def run_ours(args, ws, rank, local):
         d_lam = torch.from_numpy(lam).cuda()
         h_lam = torch.from_numpy(lam).pin_memory()
         in_bytes = sum(F.nbytes for F in facs) + lam.nbytes
+        host_inputs = h_f + [h_lam]
 
         def step(J, T, lh, host_in=False):
             if host_in:     # host factors and s-values: the call stages them itself
@@ -448,6 +469,7 @@ def run_ours(args, ws, rank, local):
     e2e_s = max_over_ranks(e2e_s, dist, "cuda")
     e2e_val = job_value(ws, e2e_steps, solves_per_step, e2e_s)
     d2h = 4 * K + 8 * K * (R - K) + (8 * K if name == "cp" else 0)
+    floor_ms = copy_floor_ms(host_inputs)
 
     if rank != 0:
         ctx.close()
@@ -510,7 +532,10 @@ def run_ours(args, ws, rank, local):
         "stage_us": stages,
         "roofline": roof,
         "e2e": {"value": round(e2e_val, 3), "unit": "solves/s", "h2d_bytes_per_step": int(in_bytes),
-                "d2h_bytes_per_step": int(d2h), "steps": e2e_steps},
+                "d2h_bytes_per_step": int(d2h), "steps": e2e_steps,
+                "h2d_copy_floor_ms": round(floor_ms, 2), "link_gbs": round(in_bytes / floor_ms / 1e6, 1),
+                "floor_note": "plain copies of the same pinned inputs, untimed for the metric: the host "
+                              "link's limit under the end-to-end number"},
         "gpu_launches": int(n1 - n0),
         "clocks": clk,
         "learned_vs_plain": lvp,
@@ -726,6 +751,10 @@ def run_batched(args, ws, rank, local):
     e2e_s = max_over_ranks(time.perf_counter() - t0, dist, "cuda")
     e2e_val = job_value(ws, e2e_steps, n_items, e2e_s)
     e2e_same = all(torch.equal(a[0].cpu(), b[0]) for a, b in zip(bouts, h_outs))
+    h_tensors = []
+    for k in h_keep:
+        h_tensors += (list(k[0]) + [k[1]]) if isinstance(k, tuple) else [k]
+    floor_ms = copy_floor_ms(h_tensors)
 
     if rank != 0:
         ctx.close()
@@ -773,6 +802,9 @@ def run_batched(args, ws, rank, local):
         "rooflines": roofs,
         "e2e": {"value": round(e2e_val, 3), "unit": "solves/s", "h2d_bytes_per_step": int(in_bytes),
                 "d2h_bytes_per_step": int(out_bytes), "steps": e2e_steps, "pivots_match_device_run": bool(e2e_same),
+                "h2d_copy_floor_ms": round(floor_ms, 2), "link_gbs": round(in_bytes / floor_ms / 1e6, 1),
+                "floor_note": "plain copies of the same pinned inputs, untimed for the metric: the host link's "
+                              "limit under the end-to-end number",
                 "how": "idl_batch_run with pinned host arrays: the call copies inputs in and outputs out"},
         "gpu_launches": int(n1 - n0),
         "clocks": clk,

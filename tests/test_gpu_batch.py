@@ -212,3 +212,39 @@ def test_batch_host_arrays_match_device_arrays(ctx):
             if ld is not None:
                 assert np.array_equal(host(ld), lh.numpy())
     assert ctx.sync() == idl.IDL_OK
+
+
+@pytest.mark.parametrize("which", ["dense", "cp"])
+def test_batch_host_arrays_single_kind(ctx, which):
+    """Host-array batches of one kind only (the item groups are then the CP items alone,
+    or the dense groups alone): results equal the device-array call's."""
+    dense, cps = (_dense_problems(23)[:3], []) if which == "dense" else ([], _cp_problems(29))
+    items, outs, keep = _build(dense, cps)
+    idl.idl_batch_run(ctx, items)
+    assert ctx.sync() == idl.IDL_OK
+    hitems, houts = [], []
+    for it, pr in zip(items[:len(dense)], dense):
+        A = torch.from_numpy(pr["A"]).pin_memory()
+        K, R = pr["K"], pr["A"].shape[1]
+        J = torch.full((K,), -1, dtype=torch.int32).pin_memory()
+        T = torch.empty(K * (R - K), dtype=torch.float64).pin_memory()
+        hitems.append(idl.dense_item(A, K, it.params, J, T))
+        houts.append((J, T, None, A))
+    for it, pr in zip(items[len(dense):], cps):
+        fs = [torch.from_numpy(np.ascontiguousarray(F.T)).pin_memory() for F in pr["facs"]]
+        lam = torch.from_numpy(pr["lam"]).pin_memory()
+        K, R = pr["K"], pr["facs"][0].shape[1]
+        J = torch.full((K,), -1, dtype=torch.int32).pin_memory()
+        T = torch.empty(K * (R - K), dtype=torch.float64).pin_memory()
+        lh = torch.empty(K, dtype=torch.float64).pin_memory()
+        hitems.append(idl.cp_item(fs, lam, K, it.params, J, T, lh))
+        houts.append((J, T, lh, fs, lam))
+    idl.idl_batch_run(ctx, hitems)
+    for (Jd, Td, ld), (Jh, Th, lh, *_) in zip(outs, houts):
+        assert np.array_equal(host(Jd), Jh.numpy())
+        if which == "dense":       # the CP sketch's shared-memory atomics may reorder colliding entries
+            assert np.array_equal(host(Td), Th.numpy())
+        else:
+            assert np.allclose(host(Td), Th.numpy(), rtol=1e-4, atol=1e-6)
+            assert np.allclose(host(ld), lh.numpy(), rtol=1e-4, atol=1e-9)
+    assert ctx.sync() == idl.IDL_OK
