@@ -3,6 +3,7 @@
 // stage).  Host code only; every arithmetic step runs in the kernels of the
 // other translation units.
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
 #include <cmath>
@@ -130,6 +131,10 @@ void* ws_get(idl_ctx* ctx, int slot, size_t bytes) {
 // ---- per-stage event profiling ----
 enum { kStDraw = 0, kStBucket, kStSketch, kStGauss, kStQR, kStSolve, kStCheck, kStCopy, kStCount };
 
+// NVTX range names of the stages (header-only NVTX v3: a no-op unless a profiler is attached)
+static const char* const kStageNames[kStCount] = {"idl:draws", "idl:buckets", "idl:sketch", "idl:gaussian",
+                                                   "idl:cpqr",  "idl:tsolve",  "idl:check",  "idl:copy"};
+
 static int prof_begin(idl_ctx* ctx, int stage) {
   if (!ctx->prof_on) return -1;
   if (ctx->prof_used == ctx->prof.size()) {
@@ -150,9 +155,11 @@ static void prof_end(idl_ctx* ctx, int idx) {
 }
 #define STAGE(stage, expr)                  \
   do {                                      \
+    nvtxRangePushA(kStageNames[stage]);     \
     int _pi = prof_begin(ctx, stage);       \
     int _rc = (expr);                       \
     prof_end(ctx, _pi);                     \
+    nvtxRangePop();                         \
     if (_rc != IDL_OK) return _rc;          \
   } while (0)
 

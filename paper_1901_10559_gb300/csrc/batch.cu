@@ -23,6 +23,7 @@
 // idl_tune_load).
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
 #include <initializer_list>
@@ -865,7 +866,15 @@ static int run_stages(idl_ctx* ctx, const BatchPlan& P, const BItem* d_items, co
   const bool timed = ms != nullptr;
   if (timed)
     for (auto& x : ev) cudaEventCreate(&x);
-  auto mark = [&](int i) { if (timed) cudaEventRecord(ev[i], ctx->stream); };
+  // stage groups as NVTX ranges (a no-op unless a profiler is attached) and, when timed, events
+  static const char* const names[kBTimedStages] = {"idl:batch draws+buckets", "idl:batch sketch cp",
+                                                   "idl:batch sketch dense", "idl:batch gaussian",
+                                                   "idl:batch proposal", "idl:batch cpqr", "idl:batch tsolve"};
+  auto mark = [&](int i) {
+    if (i > 0) nvtxRangePop();
+    if (i < kBTimedStages) nvtxRangePushA(names[i]);
+    if (timed) cudaEventRecord(ev[i], ctx->stream);
+  };
   mark(0);
   BLAUNCH(b_draw_kernel, kBDraw, 256, 0, ctx->d_status);
   BLAUNCH(b_gauss_draw_kernel, kBGauss, 256, 0);
