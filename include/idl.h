@@ -401,10 +401,14 @@ int idl_id_error_csr(idl_ctx* ctx, const int64_t* rowptr, const int32_t* colidx,
  * per item in one launch.  The launch sequence of a batch shape is captured
  * once into a CUDA graph and replayed on later calls with the same shape.  On
  * the first call of a shape the dense sketch's block width, the Gaussian
- * stage's split-K factor and the QR stage's cluster sizes (16, 8 or 4 CTAs per
- * item, dense and CP items separately) are chosen by timing the candidates
+ * stage's split-K rule (each item split to fill the SMs once or twice by
+ * itself, or -- tune-file value 0 -- split only as far as the whole batch needs
+ * for eight waves of CTAs) and the QR stage's cluster sizes (16, 8 or 4 CTAs
+ * per item, dense and CP items separately) are chosen by timing the candidates
  * (the call then runs the batch several times); idl_tune_save / idl_tune_load
- * keep those choices in a text file.
+ * keep those choices in a text file.  In the bf16 precision modes the
+ * TensorSketch of a CP item with L = 8192 writes the Gaussian stage's bf16
+ * operand planes directly, in the tile layout the tensor cores read.
  *   Items: IDL_ITEM_DENSE (Algorithm 2 on a dense FP32 matrix) or IDL_ITEM_CP
  *   (Algorithm 3 on a CP tensor), FP32 data, one precision mode per batch
  *   (IDL_PREC_FP32 / BF16X3 / BF16 / TF32X3), Gaussian stage required with

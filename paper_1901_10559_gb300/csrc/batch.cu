@@ -57,6 +57,7 @@ constexpr int kNPTf32 = 4;      // BatchPlan::NP of the TF32X3 mode (two TF32 pl
 // ---------------------------------------------------------------------------
 struct BItem {
   int kind, N, modified, K, vec;
+  int pt;                         // CP, L = 8192: Y1 holds the pre-tiled bf16 planes (gauss_tc_block_pretiled)
   int64_t I, R, lda, m1, m2, ldy1, nkb, NT, mtiles, splits, kbpc, ntiles, mode_tot;
   const float* A;
   TsArgs ts;                      // CP: factors (column-contiguous), mode maps, dims
@@ -198,6 +199,10 @@ __global__ void __launch_bounds__(kTsMaxThreads, 1) b_sketch_cp_kernel(const BIt
 
 // CP items with L = 8192: persistent blocks (one per SM) over the column pairs of all
 // such items; pre counts pairs, not blocks
+// PT = 0: Y1 column-major FP32 (column r at Y1 + r m1); PT = 1..3: Y1 holds the
+// Gaussian stage's PT bf16 operand planes, pre-tiled (pretiled_store_pair), so that stage
+// fetches them with bulk copies and converts nothing
+template <int PT>
 __global__ void __launch_bounds__(ts8::kT, 1) b_sketch_cp8k_kernel(const BItem* __restrict__ items,
                                                                    const int64_t* __restrict__ pre, int n,
                                                                    const float2* __restrict__ tab) {
@@ -210,9 +215,17 @@ __global__ void __launch_bounds__(ts8::kT, 1) b_sketch_cp8k_kernel(const BItem* 
     const int p = find_item(pre, n, g);
     const BItem& it = items[p];
     const int64_t r0 = 2 * (g - pre[p]);
-    ts8::load_mode(it.ts, 0, r0, r0 + 1 < it.R, pf);
-    // column-major: column r at Y1 + r * m1 (the Gaussian stage reads each column's K values contiguously)
-    ts8::pair_body(it.ts, it.R, r0, it.lam, it.Y1, it.m1, true, pf, z, tw1, tw2);
+    const bool two = r0 + 1 < it.R;
+    ts8::load_mode(it.ts, 0, r0, two, pf);
+    if constexpr (PT == 0) {
+      ts8::pair_body(it.ts, it.R, r0, it.lam, it.Y1, it.m1, true, pf, z, tw1, tw2);
+    } else {
+      float2 v[16];
+      float s0, s1;
+      ts8::pair_core(it.ts, it.R, r0, it.lam, pf, z, tw1, tw2, v, s0, s1);
+      pretiled_store_pair<PT, ts8::kT, 16>(reinterpret_cast<unsigned char*>(it.Y1), it.nkb, r0, v, s0, s1);
+      __syncthreads();              // every place of z is clear before the next pair's scatter
+    }
   }
 }
 
@@ -223,16 +236,21 @@ __global__ void b_planes_kernel(const BItem* __restrict__ items, const int64_t* 
   if (e < it.nkb * it.NT * 8) omega_planes_elem<NP>(e, it.Om, (int)it.m2, it.m1, (int)it.NT, it.Bpl);
 }
 
+// S: stages of the A ring of the pre-tiled items
 template <int NP>
 __global__ void __launch_bounds__(kTcThreads, 1) b_gemm_kernel(const BItem* __restrict__ items,
-                                                               const int64_t* __restrict__ pre, int n, int* status) {
+                                                               const int64_t* __restrict__ pre, int n, int* status,
+                                                               int S) {
   extern __shared__ unsigned char smem_raw[];
   ITEM_OF_BLOCK(pre, n);
   const int64_t mt = local / it.splits;
   const int sp = (int)(local % it.splits);
   const int kb0 = sp * (int)it.kbpc;
   const int nk = (int)std::min<int64_t>(it.nkb, kb0 + it.kbpc) - kb0;
-  if (it.kind == IDL_ITEM_CP)
+  if (it.pt)
+    gauss_tc_block_pretiled<NP>(reinterpret_cast<const unsigned char*>(it.Y1), it.nkb, it.R, it.Bpl, (int)it.NT,
+                                (int)it.NT, kb0, nk, mt, 0, S, it.part + (int64_t)sp * it.R * it.NT, status, smem_raw);
+  else if (it.kind == IDL_ITEM_CP)
     gauss_tc_block<NP, true>(it.Y1, it.m1, it.R, it.m1, it.Bpl, (int)it.NT, (int)it.NT, kb0, nk, mt, 0,
                              it.part + (int64_t)sp * it.R * it.NT, status, smem_raw);
   else
@@ -394,7 +412,10 @@ namespace {
 
 // Tuned per batch shape: the dense sketch's block width, the Gaussian stage's split-K
 // factor, and the thread-block cluster size of the pivoted QR of dense and of CP items.
+// split_mult >= 1: each item's K splits fill split_mult x the SMs by that item alone;
+// 0: K is split only as far as the whole batch needs to give kBatchWaves waves of CTAs
 struct Tune { int sketch_threads = 256; int split_mult = 1; int qr_cs_dense = 16; int qr_cs_cp = 16; };
+constexpr int kBatchWaves = 8, kMinKbPerCta = 8;
 
 // a batch shape: the sizes that decide every launch
 std::string signature(const idl_batch_item* items, int n) {
@@ -560,6 +581,8 @@ struct BatchPlan {
   std::vector<int32_t> dense_list, cp_list, prop_list;
   CpqrCfg cfg_dense, cfg_cp, cfg_cand;
   int NP = 3;
+  bool any_pt = false;             // some item's Y1 is pre-tiled
+  int64_t kbmax = 0;               // split_mult 0: K blocks per Gaussian-stage CTA at most
   int maxL_hist = 0, maxK = 0, maxNT = 0, maxL_cp = 0, maxm_prop = 0, maxKm_prop = 0;
   size_t ws_bytes = 0, zero_bytes = 0, off_flags = 0;
   size_t off_items = 0, off_pre = 0, off_lists = 0, table_bytes = 0;
@@ -617,6 +640,15 @@ static int plan_batch(idl_ctx* ctx, const idl_batch_item* items, int n, const Tu
   }
   P.zero_bytes = off;
   const int per_sm_gemm = 1;
+  if (tn.split_mult == 0) {
+    // the batch's output tiles times K blocks, in CTA-sized units; a group of a larger
+    // batch (like) takes that batch's cap, so each item is split as it is there
+    int64_t W = 0;
+    for (int i = 0; i < n; ++i)
+      W += cdiv(items[i].R, (int64_t)kBM) * cdiv(items[i].params.m1, (int64_t)(tf32 ? kBKt : kBK));
+    P.kbmax = like ? like->kbmax
+                   : std::max<int64_t>(kMinKbPerCta, cdiv(W, (int64_t)ctx->num_sms * kBatchWaves));
+  }
   for (int i = 0; i < n; ++i) {
     const idl_batch_item& x = items[i];
     BItem& b = P.it[i];
@@ -630,7 +662,9 @@ static int plan_batch(idl_ctx* ctx, const idl_batch_item* items, int n, const Tu
     b.nkb = cdiv(b.m1, tf32 ? kBKt : kBK);
     b.NT = round_up(b.m2, 16);
     b.mtiles = cdiv(b.R, kBM);
-    int64_t splits = std::max<int64_t>(1, cdiv((int64_t)ctx->num_sms * per_sm_gemm * tn.split_mult, b.mtiles));
+    int64_t splits = tn.split_mult == 0
+                         ? cdiv(b.nkb, P.kbmax)
+                         : std::max<int64_t>(1, cdiv((int64_t)ctx->num_sms * per_sm_gemm * tn.split_mult, b.mtiles));
     splits = std::min<int64_t>(splits, b.nkb);
     b.kbpc = cdiv(b.nkb, splits);
     b.splits = cdiv(b.nkb, b.kbpc);
@@ -667,7 +701,9 @@ static int plan_batch(idl_ctx* ctx, const idl_batch_item* items, int n, const Tu
     }
     o_Om[i] = take(sizeof(double) * (size_t)(b.m2 * b.m1));
     o_Bpl[i] = take(tf32 ? (size_t)b.nkb * 2 * b.NT * 128 : (size_t)b.nkb * P.NP * b.NT * kBK * 2);
-    o_Y1[i] = take(sizeof(float) * (size_t)(b.m1 * b.ldy1));
+    b.pt = x.kind == IDL_ITEM_CP && b.m1 == ts8::kL && !tf32;
+    P.any_pt = P.any_pt || b.pt;
+    o_Y1[i] = take(b.pt ? pretiled_bytes(b.R, b.m1, P.NP) : sizeof(float) * (size_t)(b.m1 * b.ldy1));
     o_part[i] = take(sizeof(float) * (size_t)(b.splits * b.R * b.NT));
     o_Y2[i] = take(sizeof(float) * (size_t)(b.R * b.m2));
     o_rest[i] = take(sizeof(int32_t) * (size_t)b.R);
@@ -806,12 +842,18 @@ static int plan_batch(idl_ctx* ctx, const idl_batch_item* items, int n, const Tu
 template <int NP>
 static int run_gemm_stage(idl_ctx* ctx, const BatchPlan& P, const BItem* d_items, const int64_t* d_pre, int n,
                           int& nlaunch) {
-  const size_t smem = 1024 + (size_t)kStages * NP * kBM * kBK * 2 + (size_t)kBSlots * NP * P.maxNT * kBK * 2 + 128;
+  size_t smem = 1024 + (size_t)kStages * NP * kBM * kBK * 2 + (size_t)kBSlots * NP * P.maxNT * kBK * 2 + 128;
+  // the pre-tiled items' A ring: as many stages as fit beside the B ring (2 at least)
+  int S = 2;
+  if (P.any_pt) {
+    while (S < kPtMaxStages && pretiled_smem_bytes(S + 1, NP, P.maxNT) <= (size_t)ctx->smem_optin) ++S;
+    smem = std::max(smem, pretiled_smem_bytes(S, NP, P.maxNT));
+  }
   if (smem > (size_t)ctx->smem_optin) return fail(ctx, IDL_ELIMIT, "batch gemm: shared memory");
   cudaError_t e = ensure_smem(ctx, (const void*)b_gemm_kernel<NP>, smem);
   if (e != cudaSuccess) return cuda_check(ctx, e, "batch gemm attribute");
   BLAUNCH(b_planes_kernel<NP>, kBPlanes, 256, 0);
-  BLAUNCH(b_gemm_kernel<NP>, kBGemm, kTcThreads, smem, ctx->d_status);
+  BLAUNCH(b_gemm_kernel<NP>, kBGemm, kTcThreads, smem, ctx->d_status, S);
   return launch_check(ctx, "batch gemm");
 }
 
@@ -892,11 +934,15 @@ static int run_stages(idl_ctx* ctx, const BatchPlan& P, const BItem* d_items, co
     BLAUNCH(b_sketch_cp_kernel, kBSketchT, ts_threads(P.maxL_cp), smem, (const float2*)ctx->ts_tw);
   }
   if (P.pre[kBSketchT8][n] > 0) {
-    cudaError_t e = ensure_smem(ctx, (const void*)b_sketch_cp8k_kernel, ts8::kSmemBytes);
+    // pre-tiled planes for the bf16 modes (every such item is pre-tiled), FP32 otherwise
+    const int pt = P.any_pt ? P.NP : 0;
+    auto kern = pt == 1 ? b_sketch_cp8k_kernel<1>
+                        : (pt == 2 ? b_sketch_cp8k_kernel<2> : (pt == 3 ? b_sketch_cp8k_kernel<3> : b_sketch_cp8k_kernel<0>));
+    cudaError_t e = ensure_smem(ctx, (const void*)kern, ts8::kSmemBytes);
     if (e != cudaSuccess) return cuda_check(ctx, e, "batch tensorsketch attribute");
     const int64_t grid = std::min<int64_t>(P.pre[kBSketchT8][n], ctx->num_sms);
-    b_sketch_cp8k_kernel<<<(unsigned)grid, ts8::kT, ts8::kSmemBytes, ctx->stream>>>(
-        d_items, d_pre + (size_t)kBSketchT8 * (n + 1), n, (const float2*)ctx->ts8_tw);
+    kern<<<(unsigned)grid, ts8::kT, ts8::kSmemBytes, ctx->stream>>>(d_items, d_pre + (size_t)kBSketchT8 * (n + 1), n,
+                                                                    (const float2*)ctx->ts8_tw);
     count_launch();
     ++nlaunch;
   }
@@ -1269,7 +1315,7 @@ extern "C" int idl_batch_run(idl_ctx* ctx, const idl_batch_item* items, int n) {
       return IDL_OK;
     };
     BTRY(tune_knob(&Tune::sketch_threads, {128, 256, 512}, kBTSketchDense));
-    BTRY(tune_knob(&Tune::split_mult, {1, 2}, kBTGauss));
+    BTRY(tune_knob(&Tune::split_mult, {1, 2, 0}, kBTGauss));
     if (!P.dense_list.empty()) BTRY(tune_knob(&Tune::qr_cs_dense, {16, 8, 4}, kBTQR));
     if (!P.cp_list.empty()) BTRY(tune_knob(&Tune::qr_cs_cp, {16, 8, 4}, kBTQR));
     bs->tune[key] = tn;
@@ -1353,7 +1399,7 @@ extern "C" int idl_tune_load(idl_ctx* ctx, const char* path) {
     int a, b, c = 16, d = 16;
     const int got = sscanf(line, "%llx %d %d %d %d", &k, &a, &b, &c, &d);
     auto cs_ok = [](int x) { return x == 4 || x == 8 || x == 16; };
-    if (got >= 3 && (a == 128 || a == 256 || a == 512) && (b == 1 || b == 2) && cs_ok(c) && cs_ok(d)) {
+    if (got >= 3 && (a == 128 || a == 256 || a == 512) && (b == 0 || b == 1 || b == 2) && cs_ok(c) && cs_ok(d)) {
       Tune t;
       t.sketch_threads = a;
       t.split_mult = b;

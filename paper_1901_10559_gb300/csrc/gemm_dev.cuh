@@ -407,3 +407,203 @@ __device__ __forceinline__ void gauss_tc_block(const float* __restrict__ Y1, int
 }
 
 }  // namespace idl
+
+namespace idl {
+
+// Pre-tiled A operand: the bf16 planes of Y1^T already in the swizzled K-major tile
+// layout, one 16 KB tile per (column tile mt, K block kb, plane p) at byte offset
+// ((mt * nkb + kb) * NP + p) * 16384 -- written by the producer of Y1 (the L = 8192
+// TensorSketch of the batch's CP items).  Row m of a tile is column mt * 128 + m;
+// within a row, the 16-byte chunk of K values 8 kc .. 8 kc + 7 at sw128_off(m, kc).
+constexpr int kTileBytes = tc::kBM * tc::kBK * 2;
+
+__host__ __device__ constexpr size_t pretiled_bytes(int64_t R, int64_t m1, int NP) {
+  return (size_t)((R + tc::kBM - 1) / tc::kBM) * (size_t)((m1 + tc::kBK - 1) / tc::kBK) * (size_t)NP * kTileBytes;
+}
+
+// shared memory of gauss_tc_block_pretiled with an A ring of S stages: the 1 KB
+// alignment slack, the rings, 2 S + 6 barriers and the TMEM address
+constexpr int kPtMaxStages = 6;
+__host__ __device__ constexpr size_t pretiled_smem_bytes(int S, int NP, int NT) {
+  return 1024 + (size_t)S * NP * kTileBytes + (size_t)kBSlots * NP * NT * tc::kBK * 2 + 8 * (size_t)(2 * S + 6) + 16;
+}
+
+// Pre-tiled store of the column pair (r0, r0 + 1), r0 even: thread t of a block of T
+// threads holds the pair's K entries l = T q + t (q < Q) as v[q] = (column r0, column
+// r0 + 1), each to be scaled by s0 / s1.  Lanes t and t ^ 1 hold one bf16 pair of
+// K entries: they swap the value of the column the other one stores, so the even
+// lane writes column r0's words and the odd lane column r0 + 1's, and each plane's
+// word is the split (split_bf16, same bits) of both values at once -- one 4-byte
+// store per plane and q.  Past the last column s1 = 0 and row r0 + 1 gets zeros.
+template <int NP, int T, int Q>
+__device__ __forceinline__ void pretiled_store_pair(unsigned char* __restrict__ base, int64_t nkb, int64_t r0,
+                                                    const float2* v, float s0, float s1) {
+  static_assert(T % tc::kBK == 0, "a thread keeps its place in the K block");
+  const int t = threadIdx.x;
+  const bool odd = t & 1;
+  const int64_t mt = r0 / tc::kBM;
+  const int row = (int)(r0 % tc::kBM) + (odd ? 1 : 0);
+  const int kk = t % tc::kBK;
+  unsigned char* dst = base + (size_t)((mt * nkb + t / tc::kBK) * NP) * kTileBytes + tc::sw128_off(row, kk >> 3) +
+                       2 * (kk & 6);
+  constexpr size_t step = (size_t)(T / tc::kBK) * NP * kTileBytes;   // q + 1: T / 64 K blocks on
+#pragma unroll
+  for (int q = 0; q < Q; ++q) {
+    const float x0 = v[q].x * s0, x1 = v[q].y * s1;
+    const float other = __shfl_xor_sync(0xffffffffu, odd ? x0 : x1, 1);
+    float lo = odd ? other : x0;          // the stored column's values at K entries 2j and 2j + 1
+    float hi = odd ? x1 : other;
+#pragma unroll
+    for (int p = 0; p < NP; ++p) {
+      uint32_t w;
+      if constexpr (NP == 3) {
+        // truncation split: the top halves of both remainders
+        const uint32_t ul = __float_as_uint(lo), uh = __float_as_uint(hi);
+        w = __byte_perm(ul, uh, 0x7632);
+        lo -= __uint_as_float(ul & 0xFFFF0000u);
+        hi -= __uint_as_float(uh & 0xFFFF0000u);
+      } else {
+        const __nv_bfloat162 b = __floats2bfloat162_rn(lo, hi);   // .x (low half) = rn(lo)
+        w = *reinterpret_cast<const uint32_t*>(&b);
+        if (p + 1 < NP) {
+          lo -= __low2float(b);
+          hi -= __high2float(b);
+        }
+      }
+      *reinterpret_cast<uint32_t*>(dst + q * step + (size_t)p * kTileBytes) = w;
+    }
+  }
+}
+
+// The Gaussian-stage CTA of gauss_tc_block with the A planes fetched by bulk copies from
+// the pre-tiled layout into a ring of S stages (no converter work): the elected lane of
+// warp 8 feeds both rings and issues the MMAs; the other warps only join the epilogue.
+template <int NP>
+__device__ __forceinline__ void gauss_tc_block_pretiled(const unsigned char* __restrict__ Apl, int64_t nkb_all,
+                                                        int64_t R, const __nv_bfloat16* __restrict__ Bpl, int NT,
+                                                        int NTc, int kb0, int nk, int64_t mt, int z, int S,
+                                                        float* __restrict__ part_base, int* status,
+                                                        unsigned char* smem_raw) {
+  using namespace tc;
+  unsigned char* sm = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  const int b_plane = NTc * kBK * 2;
+  const int n0 = z * NTc;
+  unsigned char* A = sm;                               // [stage][plane] 16 KB
+  unsigned char* B = A + (size_t)S * NP * kTileBytes;  // [slot][plane] b_plane
+  uint64_t* bars = (uint64_t*)(B + (size_t)kBSlots * NP * b_plane);
+  uint64_t* a_full = bars;                             // [S] bulk-copy bytes
+  uint64_t* mma_done = bars + S;                       // [S] tcgen05.commit
+  uint64_t* b_full = bars + 2 * S;                     // [3]
+  uint64_t* b_free = bars + 2 * S + 3;                 // [3]
+  uint32_t* tmem_slot = (uint32_t*)(bars + 2 * S + 6);
+  __shared__ int s_flag;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int64_t r0 = mt * kBM;
+  uint32_t tcols = 32;
+  while ((int)tcols < 2 * NTc) tcols <<= 1;
+  if (tid == 0) {
+    for (int q = 0; q < S; ++q) { mbar_init(&a_full[q], 1); mbar_init(&mma_done[q], 1); }
+    for (int q = 0; q < kBSlots; ++q) { mbar_init(&b_full[q], 1); mbar_init(&b_free[q], 1); }
+    fence_barrier_init();
+    s_flag = 0;
+  }
+  if (warp == 0) tmem_alloc(tmem_slot, tcols);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  if (warp == 8 && lane == 0) {
+    const unsigned char* atile = Apl + (size_t)(mt * nkb_all) * NP * kTileBytes;
+    auto fetch_a = [&](int kb, int st) {
+      mbar_expect_tx(&a_full[st], (uint32_t)(NP * kTileBytes));
+#pragma unroll
+      for (int p = 0; p < NP; ++p)
+        bulk_g2s(A + (size_t)(st * NP + p) * kTileBytes, atile + ((size_t)kb * NP + p) * kTileBytes,
+                 (uint32_t)kTileBytes, &a_full[st]);
+    };
+    auto fetch_b = [&](int kb, int sl) {
+      mbar_expect_tx(&b_full[sl], (uint32_t)(NP * b_plane));
+#pragma unroll
+      for (int p = 0; p < NP; ++p)
+        bulk_g2s(B + (size_t)(sl * NP + p) * b_plane, Bpl + ((size_t)kb * NP * NT + (size_t)p * NT + n0) * kBK,
+                 (uint32_t)b_plane, &b_full[sl]);
+    };
+    int last_commit = -1, a_issued = 0, b_issued = 0, done = 0;
+    for (int q = 0; q < S && q < nk; ++q) { fetch_a(kb0 + q, q); a_issued = q + 1; }
+    for (int q = 0; q < kBSlots && q < nk; ++q) { fetch_b(kb0 + q, q); b_issued = q + 1; }
+    const uint32_t idesc = idesc_bf16(NTc);
+    for (int i = 0; i < nk; ++i) {
+      const int s = i % S, sb = i % kBSlots;
+      if (!mbar_wait(&a_full[s], (uint32_t)((i / S) & 1))) { s_flag = 1; break; }
+      if (!mbar_wait(&b_full[sb], (uint32_t)((i / kBSlots) & 1))) { s_flag = 1; break; }
+      done = i + 1;
+      tc_fence_after();
+      const unsigned char* As = A + (size_t)s * NP * kTileBytes;
+      const unsigned char* Bs = B + (size_t)sb * NP * b_plane;
+#pragma unroll
+      for (int ks = 0; ks < kBK / 16; ++ks) {
+#pragma unroll
+        for (int q = 0; q < n_products(NP); ++q) {
+          const int u = (ks * n_products(NP) + q) & 1;
+          const uint64_t ad = sw128_desc(As + (size_t)prod_a(NP, q) * kTileBytes) + (uint64_t)(ks * 2);
+          const uint64_t bd = sw128_desc(Bs + (size_t)prod_b(NP, q) * b_plane) + (uint64_t)(ks * 2);
+          const bool first = i == 0 && ks * n_products(NP) + q < 2;
+          mma_bf16(tmem + (uint32_t)(u * NTc), ad, bd, idesc, first ? 0u : 1u);
+        }
+      }
+      mma_commit(&mma_done[s]);
+      mma_commit(&b_free[sb]);
+      last_commit = i;
+      // refill block i-1's A stage and B slot once its MMAs are done
+      if (i >= 1) {
+        const int so = (i - 1) % S, sbo = (i - 1) % kBSlots;
+        const bool need_a = i - 1 + S < nk, need_b = i - 1 + kBSlots < nk;
+        if (need_a) {
+          if (!mbar_wait(&mma_done[so], (uint32_t)(((i - 1) / S) & 1))) { s_flag = 1; break; }
+          fetch_a(kb0 + i - 1 + S, so);
+          a_issued = i + S;
+        }
+        if (need_b) {
+          if (!mbar_wait(&b_free[sbo], (uint32_t)(((i - 1) / kBSlots) & 1))) { s_flag = 1; break; }
+          fetch_b(kb0 + i - 1 + kBSlots, sbo);
+          b_issued = i + kBSlots;
+        }
+      }
+    }
+    if (last_commit >= 0 && !mbar_wait(&mma_done[last_commit % S], (uint32_t)((last_commit / S) & 1))) s_flag = 2;
+    if (last_commit < nk - 1 && !s_flag) s_flag = 1;
+    // after an early exit, wait (bounded) for the copies still in flight
+    for (int j = done; j < a_issued; ++j) (void)mbar_wait(&a_full[j % S], (uint32_t)((j / S) & 1));
+    for (int j = done; j < b_issued; ++j) (void)mbar_wait(&b_full[j % kBSlots], (uint32_t)((j / kBSlots) & 1));
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (s_flag == 0 && nk > 0 && warp < 8) {
+    const int lane_base = (warp & 3) * 32;
+    const int64_t r = r0 + lane_base + lane;
+    float* prow = part_base + r * NT + n0;
+    const int uses = 4 * n_products(NP) * nk;
+    for (int q = warp >> 2; q < NTc / 16; q += 2) {
+      float vals[16];
+      tmem_ld16(tmem + ((uint32_t)lane_base << 16) + (uint32_t)(q * 16), vals);
+      if (uses > 1) {
+        float v2[16];
+        tmem_ld16(tmem + ((uint32_t)lane_base << 16) + (uint32_t)(NTc + q * 16), v2);
+#pragma unroll
+        for (int j = 0; j < 16; ++j) vals[j] += v2[j];
+      }
+      if (r < R) {
+#pragma unroll
+        for (int j = 0; j < 16; j += 4)
+          *(float4*)(prow + q * 16 + j) = make_float4(vals[j], vals[j + 1], vals[j + 2], vals[j + 3]);
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (tid == 0 && s_flag) set_status(status, IDL_ETIMEOUT);
+  if (warp == 0) tmem_dealloc(tmem, tcols);
+}
+
+}  // namespace idl

@@ -347,12 +347,14 @@ __device__ __forceinline__ void inv_pass1(float2* z, const float2* tw1, float2* 
   dft16<true>(v);
 }
 
-// One pair of columns (r0, r0 + 1).  z must be zero on entry and is zero on exit.
-// pre: mode 0's entries (loaded by the caller); cm: Y column-major (column r at
-// Y + r ldy) or row-major (Y[l ldy + r]).
-__device__ __forceinline__ void pair_body(const TsArgs& a, int64_t R, int64_t r0, const double* __restrict__ lambda,
-                                          float* __restrict__ Y, int64_t ldy, bool cm, Pre& pre, float2* z,
-                                          const float2* tw1, const float2* tw2) {
+// The transforms of one pair of columns (r0, r0 + 1): on return v[q] holds entry
+// l = 512 q + t of column r0 (.x) and r0 + 1 (.y) before the scale s0 / s1 (lambda_r / L;
+// s1 = 0 past the last column).  z must be zero on entry and is zero on return, but
+// the caller synchronises the block before z is used again.  pre: mode 0's entries
+// (loaded by the caller).
+__device__ __forceinline__ void pair_core(const TsArgs& a, int64_t R, int64_t r0, const double* __restrict__ lambda,
+                                          Pre& pre, float2* z, const float2* tw1, const float2* tw2, float2* v,
+                                          float& s0, float& s1) {
   const bool two = r0 + 1 < R;
   // this thread's twiddle powers, held in registers for the pair's 2N + 2 passes
   float2 w1[4], w2[4];
@@ -381,10 +383,20 @@ __device__ __forceinline__ void pair_body(const TsArgs& a, int64_t R, int64_t r0
   __syncthreads();
   inv_pass32(z, w2);
   __syncthreads();
-  float2 v[16];
   inv_pass1(z, w1, v);
-  const float s0 = (float)(lambda[r0] / (double)kL);
-  const float s1 = two ? (float)(lambda[r0 + 1] / (double)kL) : 0.f;
+  s0 = (float)(lambda[r0] / (double)kL);
+  s1 = two ? (float)(lambda[r0 + 1] / (double)kL) : 0.f;
+}
+
+// One pair of columns (r0, r0 + 1) written to Y: column-major (cm: column r at
+// Y + r ldy) or row-major (Y[l ldy + r]).  z must be zero on entry and is zero on exit.
+__device__ __forceinline__ void pair_body(const TsArgs& a, int64_t R, int64_t r0, const double* __restrict__ lambda,
+                                          float* __restrict__ Y, int64_t ldy, bool cm, Pre& pre, float2* z,
+                                          const float2* tw1, const float2* tw2) {
+  const bool two = r0 + 1 < R;
+  float2 v[16];
+  float s0, s1;
+  pair_core(a, R, r0, lambda, pre, z, tw1, tw2, v, s0, s1);
   const int t = threadIdx.x;
   if (cm) {
     float* y0 = Y + r0 * ldy;

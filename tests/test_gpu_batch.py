@@ -7,7 +7,7 @@ import torch
 import paper_1901_10559_gb300 as idl
 from oracle import errors as oer
 from oracle import idmethods as oid
-from oracle.gaussian import FP32
+from oracle.gaussian import BF16, BF16X3, FP32
 from synth import cp_factors, lowrank_dense
 from tests.helpers import dev, host
 
@@ -64,9 +64,17 @@ def _build(dense, cps, prec=idl.PREC_FP32, learned=(idl.PROPOSAL_NONE,)):
     return items, outs, keep
 
 
-@pytest.mark.parametrize("graph,tune,prec", [(0, 0, idl.PREC_FP32), (1, 1, idl.PREC_FP32), (1, 0, idl.PREC_TF32X3)])
+# the oracle's mode of each precision (TF32X3 has FP32's definition)
+_ORACLE_PREC = {idl.PREC_FP32: FP32, idl.PREC_TF32X3: FP32, idl.PREC_BF16X3: BF16X3, idl.PREC_BF16: BF16}
+
+
+# FP32, BF16X3 and BF16 take the pre-tiled operand planes for the L = 8192 CP item
+# (R = 501: an odd last column and a partial last column tile); TF32X3 the FP32 sketch
+@pytest.mark.parametrize("graph,tune,prec", [(0, 0, idl.PREC_FP32), (1, 1, idl.PREC_FP32), (1, 0, idl.PREC_TF32X3),
+                                             (1, 1, idl.PREC_BF16X3), (0, 1, idl.PREC_BF16)])
 def test_batch_matches_single_item_calls(ctx, graph, tune, prec):
     dense, cps = _dense_problems(3), _cp_problems(5)
+    oprec = _ORACLE_PREC[prec]
     idl.lib().idl_debug_batch_mode(ctx.ptr, int(not graph), int(not tune))
     items, outs, keep = _build(dense, cps, prec=prec)
     for _ in range(2):                                   # second call replays the graph
@@ -82,7 +90,7 @@ def test_batch_matches_single_item_calls(ctx, graph, tune, prec):
         # T agrees to FP32 rounding of the sketch amplified by cond(R11); the batch may split
         # the Gaussian product's K range differently, so compare the ID errors instead
         # and the oracle's error gate
-        Jw, Tw, _ = oid.id_matrix(pr["A"], k=K, m1=pr["m1"], m2=pr["m2"], seed=pr["seed"], precision=FP32)
+        Jw, Tw, _ = oid.id_matrix(pr["A"], k=K, m1=pr["m1"], m2=pr["m2"], seed=pr["seed"], precision=oprec)
         e_g = oer.matrix_id_error(pr["A"], J=host(J), T=host(T).reshape(K, R - K), exact=False, iters=30)
         e_w = oer.matrix_id_error(pr["A"], J=Jw, T=Tw, exact=False, iters=30)
         assert e_g <= 1.1 * e_w + 1e-7
@@ -95,7 +103,7 @@ def test_batch_matches_single_item_calls(ctx, graph, tune, prec):
         assert np.array_equal(host(J), host(Js))
         assert np.allclose(host(lh), host(lhs), rtol=1e-3, atol=1e-9)
         Jw, Tw, lhw, _ = oid.id_cp_tensor(pr["facs"], pr["lam"], k=K, L=pr["L"], m2=pr["m2"], seed=pr["seed"],
-                                          precision=FP32)
+                                          precision=oprec)
         e_g = oer.tensor_id_error(pr["facs"], pr["lam"], host(J), host(lh))
         e_w = oer.tensor_id_error(pr["facs"], pr["lam"], Jw, lhw)
         assert e_g <= 1.1 * e_w + 1e-7
