@@ -1089,13 +1089,46 @@ def run_reference_batched(args, ws, rank):
             "e2e": {"value": round(value, 5), "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
+def run_batch_probe(args, spec):
+    """``batch:n_dense,n_cp``: the first n_dense dense matrices and n_cp CP tensors of
+    the batched workload's recipe as one batch; after --warmup calls (the first tunes
+    the shape), --steps event-timed un-graphed runs.  Prints the mean milliseconds of
+    each stage group -- a small case of the batch kernels for profilers."""
+    import torch
+    import paper_1901_10559_gb300 as idl
+    from paper_1901_10559_gb300 import build as b
+    b.build()
+    n_dense, n_cp = (int(x) for x in spec.split(","))
+    w = WORKLOADS["batched"]
+    dense, cps = make_batch(w["seed"], 0, n_dense, n_cp)
+    ctx = idl.Context(0)
+    items, _ = batch_items(idl, dense, cps, precision_code(idl, args.precision or w["precision"]))
+    arr = idl.batch_array(items)
+    for _ in range(args.warmup):
+        idl.idl_batch_run(ctx, arr)
+    torch.cuda.synchronize()
+    tot = {k: 0.0 for k in idl.BATCH_STAGES}
+    for _ in range(args.steps):
+        for k, v in idl.batch_stage_ms(ctx, items).items():
+            tot[k] += v / args.steps
+    if ctx.sync() != idl.IDL_OK:
+        raise SystemExit("probe: device status not OK")
+    gb = sum(4.0 * pr["A"].shape[0] * pr["A"].shape[1] for pr in dense) / 1e9
+    return {"probe": args.probe, "precision": args.precision or w["precision"],
+            "stage_ms": {k: round(v, 4) for k, v in tot.items()}, "dense_A_gb": round(gb, 3),
+            "dense_sketch_tbs": round(gb / tot["sketch_dense"], 2) if tot["sketch_dense"] > 0 else None}
+
+
 def run_probe(args):
     """One stage call timed alone (CUDA events, after warm-up) on seeded synthetic
     input: ``gaussian:<cm|rm>:m2,m1,R`` (Omega Y1 with column- or row-major FP32 Y1
-    of N(0,1) values, the mode of --precision, default BF16X3).  Prints one JSON
+    of N(0,1) values, the mode of --precision, default BF16X3), or the batch stages
+    of a smaller batch (``batch:n_dense,n_cp``, run_batch_probe).  Prints one JSON
     line with the average microseconds per call and the Y1 read rate."""
     import torch
     import paper_1901_10559_gb300 as idl
+    if args.probe.startswith("batch:"):
+        return run_batch_probe(args, args.probe.split(":", 1)[1])
     kind, layout, dims = args.probe.split(":")
     if kind != "gaussian" or layout not in ("cm", "rm"):
         raise SystemExit("probe: gaussian:<cm|rm>:m2,m1,R")

@@ -403,10 +403,14 @@ int idl_id_error_csr(idl_ctx* ctx, const int64_t* rowptr, const int32_t* colidx,
  * the first call of a shape the dense sketch's block width, the Gaussian
  * stage's split-K rule (each item split to fill the SMs once or twice by
  * itself, or -- tune-file value 0 -- split only as far as the whole batch needs
- * for eight waves of CTAs) and the QR stage's cluster sizes (16, 8 or 4 CTAs
- * per item, dense and CP items separately) are chosen by timing the candidates
- * (the call then runs the batch several times); idl_tune_save / idl_tune_load
- * keep those choices in a text file.  In the bf16 precision modes the
+ * for eight waves of CTAs), the QR stage's cluster sizes (16, 8 or 4 CTAs
+ * per item) and its cap on threads per CTA (dense items 1024, 256 or 128; CP
+ * items 1024, 512 or 320), dense and CP items separately, are chosen by timing
+ * the candidates (the call then runs the batch several times); idl_tune_save /
+ * idl_tune_load keep those choices in a text file (lines written before the
+ * thread caps existed load with caps of 1024).  The QR stage groups the items
+ * by the kernel shape each picks under those choices and launches the groups
+ * concurrently, on side streams of the context.  In the bf16 precision modes the
  * TensorSketch of a CP item with L = 8192 writes the Gaussian stage's bf16
  * operand planes directly, in the tile layout the tensor cores read.
  *   Items: IDL_ITEM_DENSE (Algorithm 2 on a dense FP32 matrix) or IDL_ITEM_CP

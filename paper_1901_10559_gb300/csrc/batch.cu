@@ -26,6 +26,7 @@
 #include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
+#include <array>
 #include <initializer_list>
 #include <cstdio>
 #include <cstring>
@@ -414,7 +415,12 @@ namespace {
 // factor, and the thread-block cluster size of the pivoted QR of dense and of CP items.
 // split_mult >= 1: each item's K splits fill split_mult x the SMs by that item alone;
 // 0: K is split only as far as the whole batch needs to give kBatchWaves waves of CTAs
-struct Tune { int sketch_threads = 256; int split_mult = 1; int qr_cs_dense = 16; int qr_cs_cp = 16; };
+// qr_cap_*: threads per QR CTA at most where an item's shape allows it (fewer lanes per
+// column, more clusters on the GPU at once)
+struct Tune {
+  int sketch_threads = 256; int split_mult = 1; int qr_cs_dense = 16; int qr_cs_cp = 16;
+  int qr_cap_dense = 1024, qr_cap_cp = 1024;
+};
 constexpr int kBatchWaves = 8, kMinKbPerCta = 8;
 
 // a batch shape: the sizes that decide every launch
@@ -442,6 +448,9 @@ uint64_t fnv1a(const std::string& s) {
 }
 
 struct CpqrCfg { int V = 0, TPC = 0, CS = 16, threads = 0; size_t smem = 0; };
+// one QR launch: the items at [off, off + count) of the device list array, one shape
+struct QrClass { CpqrCfg cfg; int off = 0, count = 0, maxK = 0; };
+constexpr int kQrSide = 15;         // side streams the QR classes are spread over
 
 }  // namespace
 
@@ -460,6 +469,8 @@ struct idl_batch_state {
   size_t pin_bytes = 0;
   cudaStream_t cstream = nullptr;    // host-staged batches: the copies run here
   std::vector<cudaEvent_t> cev;      // their events (reused)
+  cudaStream_t qs[kQrSide] = {};     // QR classes: side streams, forked from and joined to ctx->stream
+  cudaEvent_t qfork = nullptr, qjoin[kQrSide] = {};
 };
 
 extern "C" long long idl_launch_count(void);
@@ -478,6 +489,11 @@ void idl_batch_state_free(idl_batch_state* b) {
   if (b->ev_out) cudaEventDestroy(b->ev_out);
   if (b->cstream) { cudaStreamSynchronize(b->cstream); cudaStreamDestroy(b->cstream); }
   for (cudaEvent_t e : b->cev) cudaEventDestroy(e);
+  for (int k = 0; k < kQrSide; ++k) {
+    if (b->qs[k]) { cudaStreamSynchronize(b->qs[k]); cudaStreamDestroy(b->qs[k]); }
+    if (b->qjoin[k]) cudaEventDestroy(b->qjoin[k]);
+  }
+  if (b->qfork) cudaEventDestroy(b->qfork);
   delete b;
 }
 
@@ -497,7 +513,7 @@ static int launch_check(idl_ctx* ctx, const char* where) { return cuda_check(ctx
 
 template <int V, int TPC>
 static bool cpqr_cfg_fits(const std::vector<int>& list, const std::vector<BItem>& it, int CS, CpqrCfg* cfg,
-                          bool cand = false) {
+                          bool cand = false, int cap = 1 << 30) {
   int threads = 0, maxm = 0;
   for (int p : list) {
     const BItem& x = it[p];
@@ -507,7 +523,7 @@ static bool cpqr_cfg_fits(const std::vector<int>& list, const std::vector<BItem>
     maxm = std::max(maxm, (int)x.m2);
   }
   const int maxt = cand ? CtaCpqr<float, V, TPC>::kMaxThreads : RegCpqr<float, V, TPC>::kMaxThreads;
-  if (threads > maxt || threads < 32) return false;
+  if (threads > maxt || threads > cap || threads < 32) return false;
   cfg->V = V;
   cfg->TPC = TPC;
   cfg->CS = CS;
@@ -517,17 +533,61 @@ static bool cpqr_cfg_fits(const std::vector<int>& list, const std::vector<BItem>
 }
 
 static bool pick_cpqr(const std::vector<int>& list, const std::vector<BItem>& it, CpqrCfg* cfg, bool cand = false,
-                      int cluster = 16) {
+                      int cluster = 16, int cap = 1 << 30) {
   const int CS = cand ? 1 : cluster;
-#define PICK(VV, TT) if (cpqr_cfg_fits<VV, TT>(list, it, CS, cfg, cand)) return true;
+#define PICK(VV, TT) if (cpqr_cfg_fits<VV, TT>(list, it, CS, cfg, cand, cap)) return true;
   PICK(8, 32) PICK(8, 16) PICK(8, 8) PICK(16, 8) PICK(8, 4) PICK(16, 4) PICK(32, 4) PICK(16, 2) PICK(32, 2)
   PICK(16, 1) PICK(32, 1) PICK(64, 4) PICK(64, 2) PICK(64, 1) PICK(96, 1) PICK(128, 1)
 #undef PICK
   return false;
 }
 
+// The QR launches of one list (device list array offset base): items grouped by the
+// kernel shape each picks by itself (cluster size cs, at most cap threads per CTA where
+// a shape fits under it) -- values per lane V, lanes per column TPC, cluster size,
+// threads rounded up to a power of two -- larger CTAs first; the list is reordered
+// class by class.  An item's factorization depends only on its own V and TPC, so it
+// gets the same bits in every batch of the same tuning that contains it; and small
+// items no longer take the CTA size of the largest, so more clusters fit at once.
+static bool qr_classes(std::vector<int32_t>& list, std::vector<BItem>& it, int cs, int cap, int base,
+                       std::vector<QrClass>& out) {
+  std::map<std::array<int, 4>, std::pair<CpqrCfg, std::vector<int32_t>>> cls;
+  for (int32_t p : list) {
+    CpqrCfg c;
+    const std::vector<int> one{p};
+    if (!pick_cpqr(one, it, &c, false, cs, cap) && !pick_cpqr(one, it, &c, false, cs) &&
+        !pick_cpqr(one, it, &c, false, 16, cap) && !pick_cpqr(one, it, &c, false, 16))
+      return false;
+    int tb = 32;
+    while (tb < c.threads) tb *= 2;
+    auto& e = cls[{-tb, c.V, c.TPC, c.CS}];
+    if (e.second.empty()) {
+      e.first = c;
+    } else {
+      e.first.threads = std::max(e.first.threads, c.threads);
+      e.first.smem = std::max(e.first.smem, c.smem);
+    }
+    e.second.push_back(p);
+  }
+  list.clear();
+  for (auto& kv : cls) {
+    QrClass q;
+    q.cfg = kv.second.first;
+    q.off = base + (int)list.size();
+    q.count = (int)kv.second.second.size();
+    for (int32_t p : kv.second.second) {
+      list.push_back(p);
+      it[p].nc = (int)cdiv(it[p].R, q.cfg.CS);
+      q.maxK = std::max(q.maxK, it[p].K);
+    }
+    out.push_back(q);
+  }
+  return true;
+}
+
 template <int V, int TPC>
-static int launch_b_cpqr(idl_ctx* ctx, const BItem* d_items, const int32_t* d_list, int nlist, const CpqrCfg& c) {
+static int launch_b_cpqr(idl_ctx* ctx, const BItem* d_items, const int32_t* d_list, int nlist, const CpqrCfg& c,
+                         cudaStream_t stream) {
   auto kern = b_cpqr_kernel<V, TPC>;
   cudaError_t e = ensure_cluster_nonportable(ctx, (const void*)kern);
   if (e == cudaSuccess) e = ensure_smem(ctx, (const void*)kern, c.smem);
@@ -536,7 +596,7 @@ static int launch_b_cpqr(idl_ctx* ctx, const BItem* d_items, const int32_t* d_li
   cfg.gridDim = dim3((unsigned)(nlist * c.CS));
   cfg.blockDim = dim3((unsigned)c.threads);
   cfg.dynamicSmemBytes = c.smem;
-  cfg.stream = ctx->stream;
+  cfg.stream = stream;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeClusterDimension;
   attr[0].val.clusterDim.x = c.CS;
@@ -566,8 +626,10 @@ static int dispatch_b_cand(idl_ctx* ctx, const BItem* d_items, const int32_t* d_
   return fail(ctx, IDL_ELIMIT, "batch candidate QR: no configuration");
 }
 
-static int dispatch_b_cpqr(idl_ctx* ctx, const BItem* d_items, const int32_t* d_list, int nlist, const CpqrCfg& c) {
-#define CASE(VV, TT) if (c.V == VV && c.TPC == TT) return launch_b_cpqr<VV, TT>(ctx, d_items, d_list, nlist, c);
+static int dispatch_b_cpqr(idl_ctx* ctx, const BItem* d_items, const int32_t* d_list, int nlist, const CpqrCfg& c,
+                           cudaStream_t stream) {
+#define CASE(VV, TT) \
+  if (c.V == VV && c.TPC == TT) return launch_b_cpqr<VV, TT>(ctx, d_items, d_list, nlist, c, stream);
   CASE(8, 32) CASE(8, 16) CASE(8, 8) CASE(16, 8) CASE(8, 4) CASE(16, 4) CASE(32, 4) CASE(16, 2) CASE(32, 2)
   CASE(16, 1) CASE(32, 1) CASE(64, 4) CASE(64, 2) CASE(64, 1) CASE(96, 1) CASE(128, 1)
 #undef CASE
@@ -579,7 +641,8 @@ struct BatchPlan {
   std::vector<BItem> it;
   std::vector<int64_t> pre[kBNumStages];
   std::vector<int32_t> dense_list, cp_list, prop_list;
-  CpqrCfg cfg_dense, cfg_cp, cfg_cand;
+  CpqrCfg cfg_cand;
+  std::vector<QrClass> qr;         // QR launches: the dense list's classes, then the CP list's
   int NP = 3;
   bool any_pt = false;             // some item's Y1 is pre-tiled
   int64_t kbmax = 0;               // split_mult 0: K blocks per Gaussian-stage CTA at most
@@ -588,8 +651,8 @@ struct BatchPlan {
   size_t off_items = 0, off_pre = 0, off_lists = 0, table_bytes = 0;
 };
 
-// like (optional): a plan of a batch that contains these items; its QR kernel shapes are
-// kept, so that every item is factored by the same kernel as in that batch
+// like (optional): a plan of a batch that contains these items; its candidate-QR shape
+// and Gaussian-stage K-block cap are kept, so that every item is computed as in that batch
 static int plan_batch(idl_ctx* ctx, const idl_batch_item* items, int n, const Tune& tn, BatchPlan& P,
                       const BatchPlan* like = nullptr) {
   P.it.assign(n, BItem());
@@ -810,20 +873,11 @@ static int plan_batch(idl_ctx* ctx, const idl_batch_item* items, int n, const Tu
       return fail(ctx, IDL_ELIMIT, "batch: no candidate QR shape");
   }
   for (int i = 0; i < n; ++i) P.it[i].nc = 0;
-  if (!P.dense_list.empty()) {
-    if (like && !like->dense_list.empty()) P.cfg_dense = like->cfg_dense;
-    else if (!pick_cpqr(P.dense_list, P.it, &P.cfg_dense, false, tn.qr_cs_dense) &&
-             !pick_cpqr(P.dense_list, P.it, &P.cfg_dense, false, 16))
-      return fail(ctx, IDL_ELIMIT, "batch: no QR cluster shape");
-    for (int p : P.dense_list) P.it[p].nc = (int)cdiv(P.it[p].R, P.cfg_dense.CS);
-  }
-  if (!P.cp_list.empty()) {
-    if (like && !like->cp_list.empty()) P.cfg_cp = like->cfg_cp;
-    else if (!pick_cpqr(P.cp_list, P.it, &P.cfg_cp, false, tn.qr_cs_cp) &&
-             !pick_cpqr(P.cp_list, P.it, &P.cfg_cp, false, 16))
-      return fail(ctx, IDL_ELIMIT, "batch: no QR cluster shape");
-    for (int p : P.cp_list) P.it[p].nc = (int)cdiv(P.it[p].R, P.cfg_cp.CS);
-  }
+  if (!qr_classes(P.dense_list, P.it, tn.qr_cs_dense, tn.qr_cap_dense, 0, P.qr) ||
+      !qr_classes(P.cp_list, P.it, tn.qr_cs_cp, tn.qr_cap_cp, n + 1, P.qr))
+    return fail(ctx, IDL_ELIMIT, "batch: no QR cluster shape");
+  // launch order: the classes with the most pivot steps (the longest items) first
+  std::stable_sort(P.qr.begin(), P.qr.end(), [](const QrClass& a, const QrClass& b) { return a.maxK > b.maxK; });
   return IDL_OK;
 }
 
@@ -899,6 +953,36 @@ static int run_proposal(idl_ctx* ctx, const BatchPlan& P, const BItem* d_items, 
   return launch_check(ctx, "batch proposal");
 }
 
+// The QR classes' launches: the first on ctx->stream, the others on up to kQrSide
+// side streams (one per class while they last) forked from it and joined back
+// (under stream capture the fork and join become graph edges), so the classes
+// share the GPU.
+static int run_qr(idl_ctx* ctx, const BatchPlan& P, const BItem* d_items, const int32_t* d_lists, int& nlaunch) {
+  const int nq = (int)P.qr.size();
+  if (nq == 0) return IDL_OK;
+  idl_batch_state* bs = bstate(ctx);
+  const int ns = std::min(nq - 1, kQrSide);
+  if (ns > 0) {
+    if (!bs->qfork) TRYC(cudaEventCreateWithFlags(&bs->qfork, cudaEventDisableTiming), "batch QR fork event");
+    for (int k = 0; k < ns; ++k) {
+      if (!bs->qs[k]) TRYC(cudaStreamCreateWithFlags(&bs->qs[k], cudaStreamNonBlocking), "batch QR stream");
+      if (!bs->qjoin[k]) TRYC(cudaEventCreateWithFlags(&bs->qjoin[k], cudaEventDisableTiming), "batch QR join event");
+    }
+    TRYC(cudaEventRecord(bs->qfork, ctx->stream), "batch QR fork");
+    for (int k = 0; k < ns; ++k) TRYC(cudaStreamWaitEvent(bs->qs[k], bs->qfork, 0), "batch QR fork");
+  }
+  for (int c = 0; c < nq; ++c) {
+    const cudaStream_t st = c == 0 ? ctx->stream : bs->qs[(c - 1) % ns];
+    BTRY(dispatch_b_cpqr(ctx, d_items, d_lists + P.qr[c].off, P.qr[c].count, P.qr[c].cfg, st));
+    ++nlaunch;
+  }
+  for (int k = 0; k < ns; ++k) {
+    TRYC(cudaEventRecord(bs->qjoin[k], bs->qs[k]), "batch QR join");
+    TRYC(cudaStreamWaitEvent(ctx->stream, bs->qjoin[k], 0), "batch QR join");
+  }
+  return IDL_OK;
+}
+
 // All launches of a batch (the part that is captured into a graph).  ms (optional,
 // kBTimedStages floats): CUDA-event times of the stage groups (see BTimed).
 static int run_stages(idl_ctx* ctx, const BatchPlan& P, const BItem* d_items, const int64_t* d_pre,
@@ -966,14 +1050,7 @@ static int run_stages(idl_ctx* ctx, const BatchPlan& P, const BItem* d_items, co
   mark(4);
   if (!P.prop_list.empty()) BTRY(run_proposal(ctx, P, d_items, d_pre, d_lists + 2 * (n + 1), n, nlaunch));
   mark(5);
-  if (!P.dense_list.empty()) {
-    BTRY(dispatch_b_cpqr(ctx, d_items, d_lists, (int)P.dense_list.size(), P.cfg_dense));
-    ++nlaunch;
-  }
-  if (!P.cp_list.empty()) {
-    BTRY(dispatch_b_cpqr(ctx, d_items, d_lists + n + 1, (int)P.cp_list.size(), P.cfg_cp));
-    ++nlaunch;
-  }
+  BTRY(run_qr(ctx, P, d_items, d_lists, nlaunch));
   mark(6);
   BLAUNCH(b_rest_kernel, kBRest, 256, sizeof(int32_t) * (size_t)P.maxK);
   {
@@ -1318,6 +1395,8 @@ extern "C" int idl_batch_run(idl_ctx* ctx, const idl_batch_item* items, int n) {
     BTRY(tune_knob(&Tune::split_mult, {1, 2, 0}, kBTGauss));
     if (!P.dense_list.empty()) BTRY(tune_knob(&Tune::qr_cs_dense, {16, 8, 4}, kBTQR));
     if (!P.cp_list.empty()) BTRY(tune_knob(&Tune::qr_cs_cp, {16, 8, 4}, kBTQR));
+    if (!P.dense_list.empty()) BTRY(tune_knob(&Tune::qr_cap_dense, {1024, 256, 128}, kBTQR));
+    if (!P.cp_list.empty()) BTRY(tune_knob(&Tune::qr_cap_cp, {1024, 512, 320}, kBTQR));
     bs->tune[key] = tn;
     P = BatchPlan();
     BTRY(plan_batch(ctx, items, n, tn, P));
@@ -1379,10 +1458,12 @@ extern "C" int idl_tune_save(idl_ctx* ctx, const char* path) {
   if (!ctx || !path) return IDL_EINVAL;
   FILE* f = fopen(path, "w");
   if (!f) return fail(ctx, IDL_EINVAL, "tune_save: cannot open file");
-  fprintf(f, "# idl batch tuning: shape-hash sketch_threads split_mult qr_cluster_dense qr_cluster_cp\n");
+  fprintf(f, "# idl batch tuning: shape-hash sketch_threads split_mult qr_cluster_dense qr_cluster_cp "
+             "qr_threads_dense qr_threads_cp\n");
   for (auto& kv : bstate(ctx)->tune)
-    fprintf(f, "%016llx %d %d %d %d\n", (unsigned long long)kv.first, kv.second.sketch_threads, kv.second.split_mult,
-            kv.second.qr_cs_dense, kv.second.qr_cs_cp);
+    fprintf(f, "%016llx %d %d %d %d %d %d\n", (unsigned long long)kv.first, kv.second.sketch_threads,
+            kv.second.split_mult, kv.second.qr_cs_dense, kv.second.qr_cs_cp, kv.second.qr_cap_dense,
+            kv.second.qr_cap_cp);
   fclose(f);
   return IDL_OK;
 }
@@ -1396,15 +1477,19 @@ extern "C" int idl_tune_load(idl_ctx* ctx, const char* path) {
   while (fgets(line, sizeof(line), f)) {
     if (line[0] == '#') continue;
     unsigned long long k;
-    int a, b, c = 16, d = 16;
-    const int got = sscanf(line, "%llx %d %d %d %d", &k, &a, &b, &c, &d);
+    int a, b, c = 16, d = 16, e = 1024, g = 1024;      // the last four may be absent (older files)
+    const int got = sscanf(line, "%llx %d %d %d %d %d %d", &k, &a, &b, &c, &d, &e, &g);
     auto cs_ok = [](int x) { return x == 4 || x == 8 || x == 16; };
-    if (got >= 3 && (a == 128 || a == 256 || a == 512) && (b == 0 || b == 1 || b == 2) && cs_ok(c) && cs_ok(d)) {
+    auto cap_ok = [](int x) { return x == 128 || x == 256 || x == 320 || x == 512 || x == 1024; };
+    if (got >= 3 && (a == 128 || a == 256 || a == 512) && (b == 0 || b == 1 || b == 2) && cs_ok(c) && cs_ok(d) &&
+        cap_ok(e) && cap_ok(g)) {
       Tune t;
       t.sketch_threads = a;
       t.split_mult = b;
       t.qr_cs_dense = c;
       t.qr_cs_cp = d;
+      t.qr_cap_dense = e;
+      t.qr_cap_cp = g;
       bstate(ctx)->tune[(uint64_t)k] = t;
       ++loaded;
     }
