@@ -182,7 +182,7 @@ int idl_bucket_offsets_noalloc(void* stream, const int32_t* h, int64_t I, int64_
                                int32_t* bucket_ptr, int32_t* row_list);
 
 /* ---------------------------------------------------------------------------
- * CountSketch Y1 = S A (Sec. 1.3; Algorithm 2 line 4), as a segmented
+ * CountSketch Y1 = S A (Sec. 1.3; the sketch step of Algorithm 2), as a segmented
  * reduction over the bucket offsets: Y1[b, :] = sum over rows i of bucket b of
  * s[i] * A[i, :].  A: I x R row-major (lda >= R), dtype IDL_F32 or IDL_F64;
  * Y1: L x R row-major (ldy >= R), same dtype.  All device pointers.
@@ -202,7 +202,7 @@ int idl_countsketch_csr(idl_ctx* ctx, const int64_t* rowptr, const int32_t* coli
 
 /* ---------------------------------------------------------------------------
  * TensorSketch of M = (Khatri-Rao of A^(1..N)) diag(lambda) (Sec. 1.3,
- * Eq. TA-formula; Algorithm 3 line 5): Y[:, r] = lambda_r * real(IFFT(prod_n
+ * Eq. TA-formula; the sketch step of Algorithm 3): Y[:, r] = lambda_r * real(IFFT(prod_n
  * FFT(S^(n) a^(n)_r))).  factors[n]: device pointer to A^(n) stored column by
  * column (column r at factors[n] + r*ldf[n], ldf[n] >= dims[n]), IDL_F32.
  * lambda: R doubles (device).  hs[n], ss[n]: device maps of mode n (length
@@ -240,7 +240,7 @@ int idl_gaussian_stage_colmajor(idl_ctx* ctx, const double* Omega, int64_t m2, i
                                 float* Y2, int64_t ldy2);
 
 /* ---------------------------------------------------------------------------
- * Rank-K column-pivoted Householder QR of Y2 (Algorithm 1 line 3; Golub & Van
+ * Rank-K column-pivoted Householder QR of Y2 (the pivoted QR of Algorithm 1; Golub & Van
  * Loan Alg. 5.4.1): K steps, each taking the column of largest remaining norm
  * (ties: smallest index).  Y2 (m x R column-major, ldy2 >= m, dtype) is
  * overwritten: rows 0..K-1 of every column hold the triangular factor R
@@ -271,7 +271,7 @@ int idl_cpqr_srrqr(idl_ctx* ctx, const void* Y2, int64_t m, int64_t R, int64_t l
                    int32_t* J, double* T);
 
 /* ---------------------------------------------------------------------------
- * T = R11^{-1} R12 in FP64 by back substitution (Algorithm 1 lines 5-6), from
+ * T = R11^{-1} R12 in FP64 by back substitution (the solve step of Algorithm 1), from
  * the factored Y2 of idl_cpqr and its J.  T: K x (R-K) row-major FP64 (device);
  * column c of T belongs to the c-th non-skeleton column in ascending index.
  * rest (optional, R-K int32, device) receives those column indices.  K <= 128.
@@ -279,7 +279,7 @@ int idl_cpqr_srrqr(idl_ctx* ctx, const void* Y2, int64_t m, int64_t R, int64_t l
 int idl_t_solve(idl_ctx* ctx, const void* Y2, int64_t m, int64_t R, int64_t ldy2, int dtype,
                 int64_t K, const int32_t* J, double* T, int32_t* rest);
 
-/* lambda_hat_k = lambda_{J[k]} * (1 + sum_c T[k, c])  (Algorithm 3 line 7), FP64, device. */
+/* lambda_hat_k = lambda_{J[k]} * (1 + sum_c T[k, c])  (the s-value update of Algorithm 3), FP64, device. */
 int idl_lambda_hat(idl_ctx* ctx, const double* lambda, const int32_t* J, const double* T,
                    int64_t K, int64_t R, double* lambda_hat);
 

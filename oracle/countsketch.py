@@ -1,4 +1,4 @@
-"""CountSketch Y = S A, S = Phi D in R^{L x I} (Sec. 1.3; Algorithm 2, line 4).
+"""CountSketch Y = S A, S = Phi D in R^{L x I} (Sec. 1.3; the sketch step of Algorithm 2).
 
 TEST INFRASTRUCTURE (see ``oracle/__init__``).
 

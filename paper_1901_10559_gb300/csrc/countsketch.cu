@@ -1,4 +1,4 @@
-// countsketch.cu -- Y1 = S A for dense and CSR A (Sec. 1.3; Algorithm 2 line 4).
+// countsketch.cu -- Y1 = S A for dense and CSR A (Sec. 1.3; the sketch step of Algorithm 2).
 //
 // Both kernels are segmented reductions over the bucket offsets (one bucket
 // = one output row of Y1): every row of A is read once, every row of Y1 is

@@ -1,6 +1,6 @@
 // tensorsketch.cu -- TensorSketch of the Khatri-Rao matrix of CP factors,
 // Y = T M with M = (Khatri-Rao of A^(1..N)) diag(lambda), never forming M
-// (Sec. 1.3, Eq. TA-formula; Algorithm 3 line 5):
+// (Sec. 1.3, Eq. TA-formula; the sketch step of Algorithm 3):
 //   Y[:, r] = lambda_r * IFFT( prod_n FFT( S^(n) a^(n)_r ) ).
 //
 // One block per pair of columns (r, r+1): the two columns' CountSketches of

@@ -1,5 +1,5 @@
 // tsketch8k_dev.cuh -- TensorSketch for the sketch length L = 8192 (Sec. 1.3,
-// Eq. TA-formula; Algorithm 3 line 5):  Y[:, r] = lambda_r * IFFT(prod_n FFT(S^(n) a^(n)_r)).
+// Eq. TA-formula; the sketch step of Algorithm 3):  Y[:, r] = lambda_r * IFFT(prod_n FFT(S^(n) a^(n)_r)).
 //
 // Persistent blocks of 512 threads, one per SM; each block takes pairs of
 // columns (r, r+1) in turn.  The two columns of a pair are packed as the real

@@ -27,8 +27,10 @@ def _dense_problems(seed):
 
 def _cp_problems(seed):
     probs = []
-    # one item per TensorSketch kernel: L = 1024 (per-pair blocks) and L = 8192 (persistent blocks)
-    for b, (dims, R, K, L) in enumerate([((40, 30, 20), 300, 16, 1024), ((50, 50, 50, 50), 501, 32, 8192)]):
+    # L = 1024 (per-pair blocks) and L = 8192 (persistent blocks; one item with modes of
+    # uneven size and an odd column count)
+    for b, (dims, R, K, L) in enumerate([((40, 30, 20), 300, 16, 1024), ((50, 50, 50, 50), 501, 32, 8192),
+                                         ((400, 30, 300), 257, 8, 8192)]):
         facs, lam = cp_factors(dims, R, seed=seed + b, lam=10.0 ** (-6.0 * np.minimum(np.arange(R), K) / K))
         probs.append(dict(facs=facs, lam=lam, K=K, L=L, m2=K + 10, seed=2000 + b))
     return probs
