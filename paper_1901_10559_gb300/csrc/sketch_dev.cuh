@@ -35,21 +35,23 @@ __device__ __forceinline__ void cs_dense_block(const T* __restrict__ A, int64_t 
   if (VEC && c0 + W <= R) {
     V acc;
     if constexpr (W == 4) acc = make_float4(0.f, 0.f, 0.f, 0.f); else acc = make_double2(0.0, 0.0);
+    const T* Ab = A + c0;                      // column c0 of row 0
     int j = a0;
     for (; j + 4 <= a1; j += 4) {
       const int r0 = rows[j], r1 = rows[j + 1], r2 = rows[j + 2], r3 = rows[j + 3];
-      const V v0 = ldcs_vec<T>(A + (int64_t)r0 * lda + c0);
-      const V v1 = ldcs_vec<T>(A + (int64_t)r1 * lda + c0);
-      const V v2 = ldcs_vec<T>(A + (int64_t)r2 * lda + c0);
-      const V v3 = ldcs_vec<T>(A + (int64_t)r3 * lda + c0);
-      vadd(acc, v0, s[r0] < 0);
-      vadd(acc, v1, s[r1] < 0);
-      vadd(acc, v2, s[r2] < 0);
-      vadd(acc, v3, s[r3] < 0);
+      const V v0 = ldcs_vec<T>(Ab + (int64_t)r0 * lda);
+      const V v1 = ldcs_vec<T>(Ab + (int64_t)r1 * lda);
+      const V v2 = ldcs_vec<T>(Ab + (int64_t)r2 * lda);
+      const V v3 = ldcs_vec<T>(Ab + (int64_t)r3 * lda);
+      const bool n0 = s[r0] < 0, n1 = s[r1] < 0, n2 = s[r2] < 0, n3 = s[r3] < 0;
+      vadd(acc, v0, n0);
+      vadd(acc, v1, n1);
+      vadd(acc, v2, n2);
+      vadd(acc, v3, n3);
     }
     for (; j < a1; ++j) {
       const int r = rows[j];
-      vadd(acc, ldcs_vec<T>(A + (int64_t)r * lda + c0), s[r] < 0);
+      vadd(acc, ldcs_vec<T>(Ab + (int64_t)r * lda), s[r] < 0);
     }
     if (accum) vadd(acc, *(const V*)yrow, false);
     *(V*)yrow = acc;
