@@ -149,6 +149,41 @@ def test_batch_tuning_save_load(ctx, tmp_path):
     c2.close()
 
 
+@pytest.mark.parametrize("split,cs_dense,cap_dense,cap_cp", [(0, 16, 1024, 1024), (1, 8, 128, 320), (2, 4, 256, 512)])
+def test_batch_forced_tunings(ctx, tmp_path, split, cs_dense, cap_dense, cap_cp):
+    """Every choice the first-call tuner may make, forced through a tune file: the
+    Gaussian stage's K split (0 = only as far as the whole batch needs), the dense QR
+    cluster size and the QR thread caps.  Pivots match the tuned run's; the ID errors
+    stay within 1.1x of it (the choices reorder roundings only)."""
+    dense, cps = _dense_problems(13)[:3], _cp_problems(15)
+    items, outs, keep = _build(dense, cps, prec=idl.PREC_BF16X3)
+    idl.idl_batch_run(ctx, items)
+    assert ctx.sync() == idl.IDL_OK
+    path = tmp_path / "tune.txt"
+    idl.idl_tune_save(ctx, path)
+    key = [l for l in path.read_text().splitlines() if not l.startswith("#")][-1].split()[0]
+    path.write_text(f"{key} 256 {split} {cs_dense} 16 {cap_dense} {cap_cp}\n")
+    c2 = idl.Context(0)
+    try:
+        idl.idl_tune_load(c2, path)
+        items2, outs2, keep2 = _build(dense, cps, prec=idl.PREC_BF16X3)
+        idl.idl_batch_run(c2, items2)
+        assert c2.sync() == idl.IDL_OK
+    finally:
+        c2.close()
+    for pr, (J, T, _), (J2, T2, _) in zip(dense, outs, outs2):
+        K, R = pr["K"], pr["A"].shape[1]
+        assert np.array_equal(host(J2), host(J))
+        e1 = oer.matrix_id_error(pr["A"], J=host(J), T=host(T).reshape(K, R - K), exact=False, iters=30)
+        e2 = oer.matrix_id_error(pr["A"], J=host(J2), T=host(T2).reshape(K, R - K), exact=False, iters=30)
+        assert e2 <= 1.1 * e1 + 1e-7
+    for pr, (J, T, lh), (J2, T2, lh2) in zip(cps, outs[len(dense):], outs2[len(dense):]):
+        assert np.array_equal(host(J2), host(J))
+        e1 = oer.tensor_id_error(pr["facs"], pr["lam"], host(J), host(lh))
+        e2 = oer.tensor_id_error(pr["facs"], pr["lam"], host(J2), host(lh2))
+        assert e2 <= 1.1 * e1 + 1e-7
+
+
 def test_batch_rejects_mixed_precision(ctx):
     dense = _dense_problems(13)[:2]
     items, outs, keep = _build(dense, [])
