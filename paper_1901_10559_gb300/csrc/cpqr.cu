@@ -262,7 +262,7 @@ static int try_reg_cpqr(idl_ctx* ctx, const T* Yin, T* Yout, int64_t m, int64_t 
   return cuda_check(ctx, e, "cpqr reg launch");
 }
 
-// Largest cluster, then the most lanes per column whose register budget fits.
+// Largest cluster, then the first lane layout (reg_cpqr's order) whose register budget fits.
 template <typename T, int V, int TPC>
 static bool reg_try(idl_ctx* ctx, const T* Yin, T* Yout, int64_t m, int64_t R, int64_t ld, int64_t K, int32_t* J,
                     double* rnorm, int CS, int nc, const QrExtra& x, int* rc) {
@@ -287,7 +287,12 @@ static int reg_cpqr(idl_ctx* ctx, const T* Yin, T* Yout, int64_t m, int64_t R, i
     // (measured, 30 x 2000 sketch, 20 pivots: 431 us with 8 lanes per column,
     // 180 us with one lane and 32 values (some spilled), 156 us with two lanes).
     if constexpr (sizeof(T) == 8) { TRY_CFG(16, 1) TRY_CFG(16, 2) TRY_CFG(32, 1) TRY_CFG(32, 2) TRY_CFG(32, 4) }
-    // FP32: most lanes per column first (shortest serial chain per step)
+    // FP32: one lane per column first as well -- fewer threads per CTA make the two
+    // block barriers and candidate reductions of every step cheaper than the longer
+    // per-column chain costs (measured: 60 x 1000 sketch, K = 50: 173 -> 148 us with
+    // one lane and 64 values instead of 16 lanes and 8; 120 x 4096, K = 100:
+    // 422 -> 388 us); then the most lanes per column
+    if constexpr (sizeof(T) == 4) { TRY_CFG(16, 1) TRY_CFG(32, 1) TRY_CFG(64, 1) TRY_CFG(96, 1) TRY_CFG(128, 1) }
     TRY_CFG(8, 32) TRY_CFG(8, 16) TRY_CFG(8, 8) TRY_CFG(16, 8) TRY_CFG(8, 4) TRY_CFG(16, 4) TRY_CFG(32, 4)
     TRY_CFG(16, 2) TRY_CFG(32, 2) TRY_CFG(16, 1) TRY_CFG(32, 1)
     if constexpr (sizeof(T) == 4) { TRY_CFG(64, 4) TRY_CFG(64, 2) TRY_CFG(64, 1) TRY_CFG(96, 1) TRY_CFG(128, 1) }
