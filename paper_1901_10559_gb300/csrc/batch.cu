@@ -251,15 +251,18 @@ __global__ void __launch_bounds__(kTcThreads, 1) b_gemm_kernel(const BItem* __re
   const int sp = (int)(local % it.splits);
   const int kb0 = sp * (int)it.kbpc;
   const int nk = (int)std::min<int64_t>(it.nkb, kb0 + it.kbpc) - kb0;
+  // an item not split in K writes Y2 itself (no partial sums, no reduction launch)
+  float* out = it.splits == 1 ? it.Y2 : it.part + (int64_t)sp * it.R * it.NT;
+  const int64_t ldo = it.splits == 1 ? it.m2 : 0;
   if (it.pt)
     gauss_tc_block_pretiled<NP>(reinterpret_cast<const unsigned char*>(it.Y1), it.nkb, it.R, it.Bpl, (int)it.NT,
-                                (int)it.NT, kb0, nk, mt, 0, S, it.part + (int64_t)sp * it.R * it.NT, status, smem_raw);
+                                (int)it.NT, kb0, nk, mt, 0, S, out, status, smem_raw, ldo, (int)it.m2);
   else if (it.kind == IDL_ITEM_CP)
-    gauss_tc_block<NP, true>(it.Y1, it.m1, it.R, it.m1, it.Bpl, (int)it.NT, (int)it.NT, kb0, nk, mt, 0,
-                             it.part + (int64_t)sp * it.R * it.NT, status, smem_raw);
+    gauss_tc_block<NP, true>(it.Y1, it.m1, it.R, it.m1, it.Bpl, (int)it.NT, (int)it.NT, kb0, nk, mt, 0, out, status,
+                             smem_raw, kBSlots, ldo, (int)it.m2);
   else
-    gauss_tc_block<NP, false>(it.Y1, it.ldy1, it.R, it.m1, it.Bpl, (int)it.NT, (int)it.NT, kb0, nk, mt, 0,
-                              it.part + (int64_t)sp * it.R * it.NT, status, smem_raw);
+    gauss_tc_block<NP, false>(it.Y1, it.ldy1, it.R, it.m1, it.Bpl, (int)it.NT, (int)it.NT, kb0, nk, mt, 0, out,
+                              status, smem_raw, kBSlots, ldo, (int)it.m2);
 }
 
 __global__ void b_planes_tf32_kernel(const BItem* __restrict__ items, const int64_t* __restrict__ pre, int n) {
@@ -851,7 +854,7 @@ static int plan_batch(idl_ctx* ctx, const idl_batch_item* items, int n, const Tu
     nb[kBSketchT8] = cp && b.m1 == ts8::kL ? cdiv(b.R, 2) : 0;    // column pairs
     nb[kBPlanes] = cdiv(b.nkb * b.NT * 8, 256);
     nb[kBGemm] = b.mtiles * b.splits;
-    nb[kBReduce] = cdiv(b.R * b.m2, 256);
+    nb[kBReduce] = b.splits > 1 || tf32 ? cdiv(b.R * b.m2, 256) : 0;   // bf16 modes: unsplit items write Y2
     const bool mlp = b.learned == IDL_PROPOSAL_MLP, nrm = b.learned == IDL_PROPOSAL_NORM;
     nb[kBPGram] = mlp ? b.nsplit : 0;
     nb[kBPGRed] = mlp ? cdiv(b.m2 * b.m2, prop::kThreads) : 0;

@@ -190,7 +190,9 @@ constexpr int kBSlots = 3;     // Omega^T ring slots (at most; the launcher may 
 // avoid splitting N); the batch and column-major Y1 use three.
 
 // One CTA: rows [mt*128, +128) of D, columns [z*NTc, +NTc), K blocks [kb0, kb0 + nk);
-// partial result rows go to part_base[r * NT + column].  smem_raw: the dynamic
+// partial result rows go to part_base[r * NT + column]; with ldo > 0 (a CTA that
+// covers all of K) the result goes straight to the output instead,
+// part_base[r * ldo + column] for columns < ncols.  smem_raw: the dynamic
 // shared memory (1 KB alignment slack included by the launcher).
 // CM = false: Y1 row-major (Y1[b * ldy1 + r]); CM = true: column-major
 // (Y1[r * ldy1 + b]), each converter thread then reads 32 consecutive K values
@@ -199,7 +201,8 @@ template <int NP, bool CM = false>
 __device__ __forceinline__ void gauss_tc_block(const float* __restrict__ Y1, int64_t ldy1, int64_t R, int64_t m1,
                                                const __nv_bfloat16* __restrict__ Bpl, int NT, int NTc, int kb0, int nk,
                                                int64_t mt, int z, float* __restrict__ part_base, int* status,
-                                               unsigned char* smem_raw, int BS = kBSlots) {
+                                               unsigned char* smem_raw, int BS = kBSlots, int64_t ldo = 0,
+                                               int ncols = 0) {
   using namespace tc;
   unsigned char* sm = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   const int a_plane = kBM * kBK * 2;                   // 16 KB
@@ -382,7 +385,7 @@ __device__ __forceinline__ void gauss_tc_block(const float* __restrict__ Y1, int
     // epilogue: warp w reads TMEM lanes 32*(w%4).. (rows of D); warps 0-3 and 4-7 split the columns
     const int lane_base = (warp & 3) * 32;
     const int64_t r = r0 + lane_base + lane;
-    float* prow = part_base + r * NT + n0;
+    float* prow = part_base + r * (ldo ? ldo : NT) + n0;
     const int uses = 4 * n_products(NP) * nk;        // MMAs issued; the second accumulator is used if > 1
     for (int q = warp >> 2; q < NTc / 16; q += 2) {
       float vals[16];
@@ -393,10 +396,14 @@ __device__ __forceinline__ void gauss_tc_block(const float* __restrict__ Y1, int
 #pragma unroll
         for (int j = 0; j < 16; ++j) vals[j] += v2[j];
       }
-      if (r < R) {
+      if (r < R && ldo == 0) {
 #pragma unroll
         for (int j = 0; j < 16; j += 4)
           *(float4*)(prow + q * 16 + j) = make_float4(vals[j], vals[j + 1], vals[j + 2], vals[j + 3]);
+      } else if (r < R) {                            // straight to Y2 (row stride ldo, ncols columns)
+#pragma unroll
+        for (int j = 0; j < 16; ++j)
+          if (n0 + q * 16 + j < ncols) prow[q * 16 + j] = vals[j];
       }
     }
   }
@@ -483,7 +490,7 @@ __device__ __forceinline__ void gauss_tc_block_pretiled(const unsigned char* __r
                                                         int64_t R, const __nv_bfloat16* __restrict__ Bpl, int NT,
                                                         int NTc, int kb0, int nk, int64_t mt, int z, int S,
                                                         float* __restrict__ part_base, int* status,
-                                                        unsigned char* smem_raw) {
+                                                        unsigned char* smem_raw, int64_t ldo = 0, int ncols = 0) {
   using namespace tc;
   unsigned char* sm = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   const int b_plane = NTc * kBK * 2;
@@ -582,7 +589,7 @@ __device__ __forceinline__ void gauss_tc_block_pretiled(const unsigned char* __r
   if (s_flag == 0 && nk > 0 && warp < 8) {
     const int lane_base = (warp & 3) * 32;
     const int64_t r = r0 + lane_base + lane;
-    float* prow = part_base + r * NT + n0;
+    float* prow = part_base + r * (ldo ? ldo : NT) + n0;
     const int uses = 4 * n_products(NP) * nk;
     for (int q = warp >> 2; q < NTc / 16; q += 2) {
       float vals[16];
@@ -593,10 +600,14 @@ __device__ __forceinline__ void gauss_tc_block_pretiled(const unsigned char* __r
 #pragma unroll
         for (int j = 0; j < 16; ++j) vals[j] += v2[j];
       }
-      if (r < R) {
+      if (r < R && ldo == 0) {
 #pragma unroll
         for (int j = 0; j < 16; j += 4)
           *(float4*)(prow + q * 16 + j) = make_float4(vals[j], vals[j + 1], vals[j + 2], vals[j + 3]);
+      } else if (r < R) {                            // straight to Y2 (row stride ldo, ncols columns)
+#pragma unroll
+        for (int j = 0; j < 16; ++j)
+          if (n0 + q * 16 + j < ncols) prow[q * 16 + j] = vals[j];
       }
     }
   }
